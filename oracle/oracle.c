@@ -1,0 +1,421 @@
+/*
+ * FP64 CPU oracle for the IVF-PQ filtering path of FusionANNS (arXiv 2409.16576).
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check and the benchmark's CPU
+ * baseline leg may load this library. It shares no code, header, table or
+ * helper with the CUDA path, and the CUDA path never calls it.
+ *
+ * It works on the *logical* index: each posting list is a plain array of
+ * vector ids (the paper's list metadata, §4.1 "In-memory Indices"), PQ codes
+ * are an [n][M] byte matrix indexed by vector id (§4.1 "PQ-based Vectors in
+ * GPU's HBM"), and the M sub-codebooks hold 256 centroids of d/M dimensions
+ * each (§2.2). Every step below follows the online processing order of §3
+ * (steps 1-8) and is written as its plain definition in double precision:
+ *
+ *   coarse probe   the m = nprobe lists whose centroids are nearest to q
+ *                  (step 2; exact top-m, where the paper walks a graph)
+ *   gather         the ids of the probed lists (steps 3-4)
+ *   dedup          the set of distinct ids, emitted sorted ascending (step 5)
+ *   LUT            dist(q_i, c) for every subspace i and centroid c (step 1)
+ *   ADC            Eq. 1: sum over the M subspaces of LUT[i][code_i(v)] (step 6)
+ *   top-n          the n smallest (distance, id) pairs, ascending (step 7)
+ *   re-rank        Algorithm 1 with the change rate of Eq. 3 (step 8, §4.2)
+ *
+ * Readings of points the paper leaves open (all used consistently here):
+ *   - dist() in Eq. 1 is the squared L2 distance; it is the form that splits
+ *     into a sum over subspaces.
+ *   - subspaces are contiguous blocks of dsub = d / M coordinates (§2.2
+ *     "divided evenly").
+ *   - ties are broken by the smaller vector (or list) id everywhere.
+ *   - a heap insertion needs (dist, id) strictly below the heap maximum
+ *     (§4.2, "less than the current maximum"); while the heap holds fewer
+ *     than k entries every candidate is inserted.
+ *   - the stop test is the one Algorithm 1 writes: Delta <= eps increments
+ *     the stability counter and counter >= beta ends the loop; a ragged last
+ *     mini-batch stops at the end of the task list.
+ *   - Delta keeps k as its denominator even while the heap holds fewer than k.
+ *   - rows with fewer than k results are padded with (id -1, +inf).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_RAW_U8 1
+#define OR_RAW_F32 0
+
+typedef struct {
+    double d;
+    int64_t id;
+} pair_t;
+
+static int pair_less(const pair_t *a, const pair_t *b)
+{
+    if (a->d < b->d) return 1;
+    if (a->d > b->d) return 0;
+    return a->id < b->id;
+}
+
+static int pair_cmp(const void *pa, const void *pb)
+{
+    const pair_t *a = (const pair_t *)pa, *b = (const pair_t *)pb;
+    if (pair_less(a, b)) return -1;
+    if (pair_less(b, a)) return 1;
+    return 0;
+}
+
+static int u32_cmp(const void *pa, const void *pb)
+{
+    uint32_t a = *(const uint32_t *)pa, b = *(const uint32_t *)pb;
+    return (a > b) - (a < b);
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* ---------------------------------------------------------------------------
+ * Step 2 (coarse probe): squared L2 from q to every list centroid, in FP64,
+ * and the nprobe smallest by (distance, list id).
+ * ------------------------------------------------------------------------- */
+static void coarse_one(const float *q, int32_t d, const float *cent, int32_t nlist,
+                       int32_t nprobe, int32_t *probes, double *d2out, pair_t *scratch)
+{
+    for (int32_t l = 0; l < nlist; ++l) {
+        double s = 0.0;
+        const float *c = cent + (int64_t)l * d;
+        for (int32_t j = 0; j < d; ++j) {
+            double t = (double)q[j] - (double)c[j];
+            s += t * t;
+        }
+        scratch[l].d = s;
+        scratch[l].id = l;
+    }
+    qsort(scratch, (size_t)nlist, sizeof(pair_t), pair_cmp);
+    for (int32_t i = 0; i < nprobe; ++i) {
+        probes[i] = (int32_t)scratch[i].id;
+        if (d2out) d2out[i] = scratch[i].d;
+    }
+}
+
+void or_coarse(const float *q, int64_t nq, int32_t d, const float *cent, int32_t nlist,
+               int32_t nprobe, int32_t *probes, double *d2out)
+{
+#pragma omp parallel
+    {
+        pair_t *scratch = (pair_t *)malloc(sizeof(pair_t) * (size_t)nlist);
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t i = 0; i < nq; ++i)
+            coarse_one(q + i * d, d, cent, nlist, nprobe, probes + i * nprobe,
+                       d2out ? d2out + i * nprobe : NULL, scratch);
+        free(scratch);
+    }
+}
+
+/* ---------------------------------------------------------------------------
+ * Step 1 (distance table): LUT[i][c] = sum over the coordinates j of subspace
+ * i of (q_j - C_i[c][j])^2, the dist(q_i, c_i) terms that Eq. 1 adds up.
+ * codebooks is [M][256][dsub]; lut is [M][256].
+ * ------------------------------------------------------------------------- */
+void or_lut(const float *q, int32_t d, int32_t M, const float *codebooks, double *lut)
+{
+    int32_t dsub = d / M;
+    for (int32_t i = 0; i < M; ++i)
+        for (int32_t c = 0; c < 256; ++c) {
+            const float *cw = codebooks + ((int64_t)i * 256 + c) * dsub;
+            double s = 0.0;
+            for (int32_t j = 0; j < dsub; ++j) {
+                double t = (double)q[i * dsub + j] - (double)cw[j];
+                s += t * t;
+            }
+            lut[i * 256 + c] = s;
+        }
+}
+
+/* ---------------------------------------------------------------------------
+ * Steps 3-5 (gather, dedup): concatenate the id arrays of the probed lists,
+ * then sort and keep each distinct id once. Returns the number of distinct
+ * ids (written ascending to out, which must hold the gathered count);
+ * *gathered receives the size of the concatenation.
+ * ------------------------------------------------------------------------- */
+int64_t or_candidates(const int32_t *probes, int32_t nprobe, const int64_t *list_off,
+                      const int64_t *list_ids, uint32_t *out, int64_t cap, int64_t *gathered)
+{
+    int64_t g = 0;
+    for (int32_t p = 0; p < nprobe; ++p) {
+        int32_t l = probes[p];
+        for (int64_t e = list_off[l]; e < list_off[l + 1]; ++e) {
+            if (g < cap) out[g] = (uint32_t)list_ids[e];
+            ++g;
+        }
+    }
+    if (gathered) *gathered = g;
+    if (g > cap) return -1;
+    qsort(out, (size_t)g, sizeof(uint32_t), u32_cmp);
+    int64_t u = 0;
+    for (int64_t i = 0; i < g; ++i)
+        if (u == 0 || out[i] != out[u - 1]) out[u++] = out[i];
+    return u;
+}
+
+/* Step 6, Eq. 1: ADC distance of vector v = sum_i LUT[i][code[v][i]]. */
+void or_adc(const double *lut, int32_t M, const uint8_t *codes, const uint32_t *ids,
+            int64_t n, double *dist)
+{
+    for (int64_t t = 0; t < n; ++t) {
+        const uint8_t *cv = codes + (int64_t)ids[t] * M;
+        double s = 0.0;
+        for (int32_t i = 0; i < M; ++i) s += lut[i * 256 + cv[i]];
+        dist[t] = s;
+    }
+}
+
+/* Step 7: the n smallest (dist, id) pairs in ascending order; rows shorter
+ * than n are padded with (-1, +inf). */
+void or_topn(const double *dist, const uint32_t *ids, int64_t cnt, int32_t n,
+             int64_t *out_ids, double *out_dist)
+{
+    pair_t *p = (pair_t *)malloc(sizeof(pair_t) * (size_t)(cnt > 0 ? cnt : 1));
+    for (int64_t i = 0; i < cnt; ++i) {
+        p[i].d = dist[i];
+        p[i].id = ids[i];
+    }
+    qsort(p, (size_t)cnt, sizeof(pair_t), pair_cmp);
+    for (int32_t i = 0; i < n; ++i) {
+        if (i < cnt) {
+            out_ids[i] = p[i].id;
+            out_dist[i] = p[i].d;
+        } else {
+            out_ids[i] = -1;
+            out_dist[i] = INFINITY;
+        }
+    }
+    free(p);
+}
+
+/* Exact squared L2 between q and raw vector v (uint8 or float32 rows). */
+static double exact_l2(const float *q, int32_t d, const void *raw, int32_t raw_dtype, int64_t v)
+{
+    double s = 0.0;
+    if (raw_dtype == OR_RAW_U8) {
+        const uint8_t *x = (const uint8_t *)raw + v * d;
+        for (int32_t j = 0; j < d; ++j) {
+            double t = (double)q[j] - (double)x[j];
+            s += t * t;
+        }
+    } else {
+        const float *x = (const float *)raw + v * d;
+        for (int32_t j = 0; j < d; ++j) {
+            double t = (double)q[j] - (double)x[j];
+            s += t * t;
+        }
+    }
+    return s;
+}
+
+void or_exact_l2(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
+                 const int64_t *ids, int64_t n, double *out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = exact_l2(q, d, raw, raw_dtype, ids[i]);
+}
+
+/* ---------------------------------------------------------------------------
+ * Step 8, Algorithm 1 (heuristic re-ranking) with Eq. 3. The max-heap Q is
+ * kept as a small array sorted ascending; its last element is the maximum.
+ * tasks: candidate ids in ascending ADC order (entries < 0 are skipped as
+ * padding). Returns the number of mini-batches processed.
+ * ------------------------------------------------------------------------- */
+static int in_set(const int64_t *s, int32_t n, int64_t id)
+{
+    for (int32_t i = 0; i < n; ++i)
+        if (s[i] == id) return 1;
+    return 0;
+}
+
+int32_t or_rerank(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
+                  const int64_t *tasks, int32_t ntasks, int32_t k, int32_t batch,
+                  float eps, int32_t beta, int64_t *out_ids, double *out_dist)
+{
+    pair_t *Q = (pair_t *)malloc(sizeof(pair_t) * (size_t)(k + 1));
+    int64_t *prev = (int64_t *)malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
+    int32_t qn = 0, counter = 0, batches = 0;
+    int32_t valid = 0;
+    while (valid < ntasks && tasks[valid] >= 0) ++valid;
+
+    for (int32_t i = 0; i < valid; i += batch) {
+        /* S_{n-1} <- ids currently in Q */
+        int32_t pn = qn;
+        for (int32_t t = 0; t < qn; ++t) prev[t] = Q[t].id;
+        int32_t end = i + batch < valid ? i + batch : valid;
+        for (int32_t j = i; j < end; ++j) {
+            pair_t c;
+            c.id = tasks[j];
+            c.d = exact_l2(q, d, raw, raw_dtype, tasks[j]);
+            if (qn < k || pair_less(&c, &Q[qn - 1])) {
+                /* insert in order, drop the maximum when over k */
+                int32_t pos = qn < k ? qn : k - 1;
+                if (qn < k) ++qn;
+                while (pos > 0 && pair_less(&c, &Q[pos - 1])) {
+                    Q[pos] = Q[pos - 1];
+                    --pos;
+                }
+                Q[pos] = c;
+            }
+        }
+        ++batches;
+        /* Eq. 3: Delta = |S_n - S_n intersect S_{n-1}| / k */
+        int32_t changed = 0;
+        for (int32_t t = 0; t < qn; ++t)
+            if (!in_set(prev, pn, Q[t].id)) ++changed;
+        double delta = (double)changed / (double)k;
+        if (delta <= (double)eps) {
+            ++counter;
+            if (counter >= beta) break;
+        } else {
+            counter = 0;
+        }
+    }
+    for (int32_t t = 0; t < k; ++t) {
+        if (t < qn) {
+            out_ids[t] = Q[t].id;
+            out_dist[t] = Q[t].d;
+        } else {
+            out_ids[t] = -1;
+            out_dist[t] = INFINITY;
+        }
+    }
+    free(Q);
+    free(prev);
+    return batches;
+}
+
+/* ---------------------------------------------------------------------------
+ * The whole filtering path for nq queries (steps 1-8 of §3), one query per
+ * OpenMP iteration.
+ *
+ *   probes_in  optional [nq][nprobe] probe lists; NULL runs the coarse probe.
+ *   rerank_n   0: return the ADC top-k. >0: take the ADC top-rerank_n and
+ *              re-rank them with Algorithm 1 (needs raw vectors).
+ *   stats      optional [nq][4]: gathered ids, distinct ids, mini-batches run,
+ *              candidates handed to the re-rank.
+ * ------------------------------------------------------------------------- */
+int32_t or_search(const float *queries, int64_t nq, int32_t d, const float *cent, int32_t nlist,
+                  int32_t M, const float *codebooks, const uint8_t *codes, const int64_t *list_off,
+                  const int64_t *list_ids, const void *raw, int32_t raw_dtype, int32_t nprobe,
+                  int32_t k, const int32_t *probes_in, int32_t rerank_n, int32_t batch, float eps,
+                  int32_t beta, int64_t *out_ids, double *out_dist, int64_t *stats)
+{
+    if (nprobe > nlist) nprobe = nlist;
+    if (nprobe < 1) nprobe = 1;
+    int64_t maxlist = 0;
+    for (int32_t l = 0; l < nlist; ++l)
+        if (list_off[l + 1] - list_off[l] > maxlist) maxlist = list_off[l + 1] - list_off[l];
+    int64_t cap = maxlist * nprobe;
+    int32_t n_top = rerank_n > 0 ? rerank_n : k;
+    int32_t err = 0;
+
+#pragma omp parallel
+    {
+        pair_t *scratch = (pair_t *)malloc(sizeof(pair_t) * (size_t)nlist);
+        int32_t *probes = (int32_t *)malloc(sizeof(int32_t) * (size_t)nprobe);
+        uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(cap > 0 ? cap : 1));
+        double *dist = (double *)malloc(sizeof(double) * (size_t)(cap > 0 ? cap : 1));
+        double *lut = (double *)malloc(sizeof(double) * (size_t)M * 256);
+        int64_t *top_ids = (int64_t *)malloc(sizeof(int64_t) * (size_t)n_top);
+        double *top_d = (double *)malloc(sizeof(double) * (size_t)n_top);
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            const float *q = queries + qi * d;
+            if (probes_in)
+                memcpy(probes, probes_in + qi * nprobe, sizeof(int32_t) * (size_t)nprobe);
+            else
+                coarse_one(q, d, cent, nlist, nprobe, probes, NULL, scratch);
+            or_lut(q, d, M, codebooks, lut);
+            int64_t gathered = 0;
+            int64_t u = or_candidates(probes, nprobe, list_off, list_ids, cand, cap, &gathered);
+            if (u < 0) {
+                err = 1;
+                continue;
+            }
+            or_adc(lut, M, codes, cand, u, dist);
+            or_topn(dist, cand, u, n_top, top_ids, top_d);
+            int32_t batches = 0;
+            if (rerank_n > 0) {
+                batches = or_rerank(q, d, raw, raw_dtype, top_ids, n_top, k, batch, eps, beta,
+                                    out_ids + qi * k, out_dist + qi * k);
+            } else {
+                memcpy(out_ids + qi * k, top_ids, sizeof(int64_t) * (size_t)k);
+                memcpy(out_dist + qi * k, top_d, sizeof(double) * (size_t)k);
+            }
+            if (stats) {
+                stats[qi * 4 + 0] = gathered;
+                stats[qi * 4 + 1] = u;
+                stats[qi * 4 + 2] = batches;
+                stats[qi * 4 + 3] = u < n_top ? u : n_top;
+            }
+        }
+        free(scratch);
+        free(probes);
+        free(cand);
+        free(dist);
+        free(lut);
+        free(top_ids);
+        free(top_d);
+    }
+    return err ? -1 : 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Ground truth: brute-force k nearest neighbours by exact squared L2 in FP64
+ * (exact for uint8 data), ties by smaller id. Used for Recall@k (§6).
+ * ------------------------------------------------------------------------- */
+void or_knn(const float *queries, int64_t nq, const void *base, int32_t raw_dtype, int64_t n,
+            int32_t d, int32_t k, int64_t *out_ids, double *out_dist)
+{
+#pragma omp parallel
+    {
+        pair_t *Q = (pair_t *)malloc(sizeof(pair_t) * (size_t)(k + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int64_t qi = 0; qi < nq; ++qi) {
+            const float *q = queries + qi * d;
+            int32_t qn = 0;
+            for (int64_t v = 0; v < n; ++v) {
+                pair_t c;
+                c.id = v;
+                c.d = exact_l2(q, d, base, raw_dtype, v);
+                if (qn < k || pair_less(&c, &Q[qn - 1])) {
+                    int32_t pos = qn < k ? qn : k - 1;
+                    if (qn < k) ++qn;
+                    while (pos > 0 && pair_less(&c, &Q[pos - 1])) {
+                        Q[pos] = Q[pos - 1];
+                        --pos;
+                    }
+                    Q[pos] = c;
+                }
+            }
+            for (int32_t t = 0; t < k; ++t) {
+                out_ids[qi * k + t] = t < qn ? Q[t].id : -1;
+                out_dist[qi * k + t] = t < qn ? Q[t].d : INFINITY;
+            }
+        }
+        free(Q);
+    }
+}

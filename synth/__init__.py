@@ -1,0 +1,177 @@
+"""Seeded synthetic inputs for the IVF-PQ filtering path.
+
+This module only draws random numbers and shapes them into base vectors and
+queries. It holds none of the search arithmetic (no distances, lookup tables,
+clustering or selection), so that both the CPU oracle and the CUDA path can be
+fed from it without sharing any code of the method.
+
+Every draw comes from a Philox-4x64 counter-based generator (Salmon et al.,
+SC'11) keyed by (seed, stream, chunk of rows). Any chunk-aligned row range can
+therefore be regenerated on its own and yields the same rows as a full draw.
+Rows are produced in chunks of ``CHUNK`` rows.
+
+The workload shapes follow the paper's billion-scale datasets (Table 1):
+SIFT-like d=128 uint8 and DEEP-like d=96 float32 unit-norm data, here drawn
+from isotropic Gaussian mixtures because the datasets themselves are not used.
+"""
+from __future__ import annotations
+
+import os
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass
+
+import numpy as np
+
+BASE_SEED = 20240916
+# stream ids (the generator key's second word)
+STREAM_MEANS = 0
+STREAM_BASE = 1
+STREAM_QUERIES = 2
+STREAM_KMEANS = 3
+STREAM_PQ = 4
+STREAM_ARRIVALS = 5
+STREAM_PARAMS = 6
+
+CHUNK = 4096
+
+
+def philox(seed: int, stream: int, chunk: int) -> np.random.Generator:
+    """A numpy Generator on Philox keyed by (seed, stream, chunk)."""
+    key = np.array([seed & 0xFFFFFFFFFFFFFFFF,
+                    ((stream & 0xFFFF) << 48) | (chunk & 0xFFFFFFFFFFFF)],
+                   dtype=np.uint64)
+    return np.random.Generator(np.random.Philox(key=key))
+
+
+def _threads() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+@dataclass(frozen=True)
+class Mixture:
+    """Isotropic Gaussian mixture: ``ncomp`` means drawn U[lo, hi]^d,
+    per-coordinate std ``sigma``, uniform weights.
+
+    ``kind`` selects the output form:
+      * ``"f32"``   plain float32 samples;
+      * ``"u8"``    samples clipped to [0, 255] and rounded (SIFT-like);
+      * ``"unit"``  float32 samples scaled to unit L2 norm (DEEP-like).
+    """
+    d: int
+    ncomp: int
+    sigma: float = 8.0
+    lo: float = 0.0
+    hi: float = 100.0
+    kind: str = "f32"
+    seed: int = BASE_SEED
+
+    def means(self) -> np.ndarray:
+        g = philox(self.seed, STREAM_MEANS, 0)
+        return g.uniform(self.lo, self.hi, size=(self.ncomp, self.d))
+
+    def _chunk(self, stream: int, c: int, rows: int, means: np.ndarray):
+        g = philox(self.seed, stream, c)
+        comp = g.integers(0, self.ncomp, size=rows)
+        x = g.standard_normal(size=(rows, self.d), dtype=np.float64)
+        x *= self.sigma
+        x += means[comp]
+        if self.kind == "u8":
+            np.clip(x, 0.0, 255.0, out=x)
+            return np.rint(x).astype(np.uint8)
+        if self.kind == "unit":
+            x /= np.linalg.norm(x, axis=1, keepdims=True)
+        return x.astype(np.float32)
+
+    def rows(self, start: int, stop: int, stream: int = STREAM_BASE) -> np.ndarray:
+        """Rows [start, stop) of the given stream (chunk-aligned regeneration)."""
+        if stop <= start:
+            return np.zeros((0, self.d), dtype=self.dtype)
+        means = self.means()
+        c0, c1 = start // CHUNK, (stop - 1) // CHUNK
+        out = np.empty((stop - start, self.d), dtype=self.dtype)
+
+        def work(c):
+            lo = c * CHUNK
+            blk = self._chunk(stream, c, CHUNK, means)
+            a, b = max(lo, start), min(lo + CHUNK, stop)
+            out[a - start:b - start] = blk[a - lo:b - lo]
+
+        chunks = range(c0, c1 + 1)
+        if len(chunks) > 4:
+            with ThreadPoolExecutor(_threads()) as ex:
+                list(ex.map(work, chunks))
+        else:
+            for c in chunks:
+                work(c)
+        return out
+
+    @property
+    def dtype(self):
+        return np.uint8 if self.kind == "u8" else np.float32
+
+    def base(self, n: int) -> np.ndarray:
+        return self.rows(0, n, STREAM_BASE)
+
+    def queries(self, nq: int) -> np.ndarray:
+        """Queries drawn like the base, returned as float32 (uint8 values are
+        exact in float32)."""
+        return self.rows(0, nq, STREAM_QUERIES).astype(np.float32)
+
+
+# ---------------------------------------------------------------------------
+# Named workloads (the paper's dataset shapes, Table 1; sizes of the study's
+# five configurations).
+# ---------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    mix: Mixture
+    n: int
+    nq: int
+    nlist: int
+    M: int
+    nprobe: int
+    k: int
+
+
+def plain_f32_100k() -> Workload:
+    """100k float32 d=128 vectors, 64-component mixture (means U[0,100],
+    sigma 8), 256 lists, M=16, 100 queries, nprobe 8, k 10."""
+    return Workload("ivfpq-f32-100k-d128-nlist256-M16", Mixture(128, 64, 8.0),
+                    100_000, 100, 256, 16, 8, 10)
+
+
+def sift_like_10m() -> Workload:
+    """10M uint8 d=128 vectors (mixture clipped to 0..255 and rounded),
+    16384 lists, M=32, 10k queries, nprobe 64, k 10."""
+    return Workload("ivfpq-u8-10m-d128-nlist16384-M32", Mixture(128, 64, 8.0, kind="u8"),
+                    10_000_000, 10_000, 16384, 32, 64, 10)
+
+
+def zipf_sizes(nlist: int, n: int, s: float = 1.1) -> np.ndarray:
+    """List sizes proportional to i^-s (i = 1..nlist), largest-remainder
+    rounding to sum n, each at least 1."""
+    w = np.arange(1, nlist + 1, dtype=np.float64) ** (-s)
+    w /= w.sum()
+    raw = w * (n - nlist)
+    base = np.floor(raw).astype(np.int64)
+    rem = (n - nlist) - int(base.sum())
+    order = np.argsort(-(raw - base), kind="stable")
+    base[order[:rem]] += 1
+    return base + 1
+
+
+def poisson_arrivals(rate_qps: float, count: int, seed: int = BASE_SEED) -> np.ndarray:
+    """Arrival times (s) of an open-loop Poisson process: exponential gaps."""
+    g = philox(seed, STREAM_ARRIVALS, int(rate_qps) & 0xFFFFFFFF)
+    return np.cumsum(g.exponential(1.0 / rate_qps, size=count))
+
+
+def uniform_ints(lo: int, hi: int, count: int, tag: int, seed: int = BASE_SEED) -> np.ndarray:
+    """``count`` integers uniform on [lo, hi] (inclusive), stream PARAMS/tag."""
+    g = philox(seed, STREAM_PARAMS, tag)
+    return g.integers(lo, hi + 1, size=count).astype(np.int32)
