@@ -1,0 +1,406 @@
+"""Benchmark of the IVF-PQ filtering path on one B300 (or N replicas).
+
+Workload (default): 10M uint8 d=128 vectors from a 64-component Gaussian
+mixture clipped to 0..255 (SIFT-like, the paper's Table 1 shape), 16384 lists,
+PQ M=32 x 256, 10k queries, nprobe 64, k 10, the precision form (FP16 LUT with
+a per-query scale, exact FP32 re-rank of the ADC top 100 in mini-batches of
+32, Algorithm 1) with raw vectors in pinned host memory.
+
+A step is one batch of 10k queries through the whole path: coarse probe, LUT,
+gather + dedup, ADC scan + top-n, re-rank. ``value`` is queries per second
+with the queries already in HBM; ``e2e`` is the same through the C ABI with
+host buffers (host->device copy of the queries and device->host copy of the
+results inside the timed region). ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+L2_BYTES = 126 * 1024 * 1024
+SCAN_SOURCES = ["paper_2409_16576_b300/csrc/kernels/k_scan.cu",
+                "paper_2409_16576_b300/csrc/kernels/warp_topk.cuh"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--form", default="lowp", choices=["lowp", "plain"],
+                    help="lowp: FP16 LUT + re-rank (precision form); plain: FP32 LUT, no re-rank")
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--nprobe", type=int, default=64)
+    ap.add_argument("--cpu-sample", type=int, default=0, help="queries in the CPU baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--recall", type=int, default=1000, help="queries in the recall subsample (0 = off)")
+    return ap.parse_args()
+
+
+def workload(args):
+    w = synth.sift_like_10m()
+    return dict(name=w.name if args.n == w.n else "ivfpq-u8-%d-d128-nlist16384-M32" % args.n,
+                mix=w.mix, n=args.n, nq=args.nq, nlist=w.nlist, M=w.M, nprobe=args.nprobe, k=w.k,
+                rerank_n=100 if args.form == "lowp" else 0)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def src_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        h.update(open(os.path.join(ROOT, p), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel_hash):
+    """DRAM bytes per scan launch recorded by an ncu capture of this exact
+    kernel source (profiles/*.md carries 'traffic_bytes_per_launch: N' and
+    'kernel_src_hash: H'), or None."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    for fn in sorted(os.listdir(d)):
+        if not fn.endswith(".md"):
+            continue
+        txt = open(os.path.join(d, fn)).read()
+        mh = re.search(r"kernel_src_hash:\s*([0-9a-f]+)", txt)
+        mt = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+        if mh and mt and mh.group(1) == kernel_hash:
+            return float(mt.group(1))
+    return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return j.get("hbm_gbs", 6400.0), "measured"
+    return 6400.0, "fallback"
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_oracle_sample(wl, base, queries, parts, nsample):
+    """The FP64 oracle (as it stands) on the first nsample queries, all host
+    cores; returns (seconds, cores, ids)."""
+    import oracle
+    off, ids = oracle.lists_from_parts(parts["primary"], parts["rep_off"], parts["rep_ids"],
+                                       parts["nlist"])
+    cores = cpu_cores()
+    oracle.set_threads(cores)
+    q = queries[:nsample]
+    t0 = time.perf_counter()
+    oi, od = oracle.search(q, parts["centroids"], parts["codebooks"], parts["codes"], off, ids,
+                           wl["nprobe"], wl["k"], raw=base, rerank_n=wl["rerank_n"], batch=32,
+                           eps=0.0, beta=2)
+    return time.perf_counter() - t0, cores, oi
+
+
+def ground_truth(base, q, k):
+    """Brute-force k-NN by exact squared L2 in FP64 on the GPU (exact for
+    uint8 data), block by block with a running top-k."""
+    import torch
+    qs = torch.as_tensor(q, device="cuda", dtype=torch.float64)
+    qn = (qs * qs).sum(1, keepdim=True)
+    best_d = torch.full((q.shape[0], k), float("inf"), dtype=torch.float64, device="cuda")
+    best_i = torch.full((q.shape[0], k), -1, dtype=torch.int64, device="cuda")
+    blk = 1 << 18
+    for s0 in range(0, base.shape[0], blk):
+        x = torch.as_tensor(base[s0:s0 + blk], device="cuda").to(torch.float64)
+        dd = qn - 2.0 * (qs @ x.T) + (x * x).sum(1)[None]
+        v, i = torch.topk(dd, min(k, x.shape[0]), dim=1, largest=False)
+        cd = torch.cat([best_d, v], 1)
+        ci = torch.cat([best_i, i + s0], 1)
+        o = torch.topk(cd, k, dim=1, largest=False).indices
+        best_d, best_i = torch.gather(cd, 1, o), torch.gather(ci, 1, o)
+    return best_i.cpu().numpy(), best_d.cpu().numpy()
+
+
+def exact_dists(base, q, ids):
+    out = np.full(ids.shape, np.inf)
+    for i in range(ids.shape[0]):
+        ok = ids[i] >= 0
+        x = base[ids[i][ok]].astype(np.float64)
+        out[i, ok] = ((x - q[i].astype(np.float64)) ** 2).sum(1)
+    return out
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    wl = workload(args)
+
+    if args.impl == "reference":
+        return reference_arm(args, wl, rank, world)
+
+    import torch
+    import paper_2409_16576_b300 as fa
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # ---- index (synthetic, seeded; the same on every replica) ----
+    t0 = time.perf_counter()
+    base = wl["mix"].base(wl["n"])
+    queries = wl["mix"].queries(wl["nq"])
+    t_gen = time.perf_counter() - t0
+    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=8,
+                         raw_location=fa.FA_RAW_HOST_PINNED if wl["rerank_n"] else fa.FA_RAW_NONE)
+    t0 = time.perf_counter()
+    ix = fa.fa_build_index(base, bp)
+    t_build = time.perf_counter() - t0
+    info = ix.info()
+
+    lowp = args.form == "lowp"
+    sp = fa.search_params(lut_prec=fa.FA_LUT_F16 if lowp else fa.FA_LUT_F32,
+                          rerank_n=wl["rerank_n"], rerank_batch=32, rerank_beta=2, rerank_eps=0.0)
+    k, nq, d = wl["k"], wl["nq"], 128
+    stream = torch.cuda.current_stream()
+    qd = torch.as_tensor(queries, device="cuda")
+    oid = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    odist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    # candidate counts (algorithmic bytes of the scan)
+    _, _, st = fa.fa_search_ex(ix, queries, k, wl["nprobe"], sp, stats=True)
+    uniq = int(st[:, 1].sum())
+    gathered = int(st[:, 0].sum())
+    rep_entries = gathered - uniq  # primaries are all distinct; the rest are replica entries
+    lut_b = wl["M"] * 256 * (2 if lowp else 0)
+    scan_bytes = uniq * wl["M"] + rep_entries * 9 + nq * lut_b + nq * (100 if lowp else k) * 8
+
+    def step(trace=None):
+        return fa.fa_search_ex(ix, qd, k, wl["nprobe"], sp, out_ids=oid, out_dist=odist,
+                               stream=stream.cuda_stream, trace=trace)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+
+    # ---- timed region: per-step CUDA events on the launching stream ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    traces = []
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        tr = fa.fa_search_trace()
+        ev[i][0].record(stream)
+        step(tr)
+        ev[i][1].record(stream)
+        traces.append(tr)
+    torch.cuda.synchronize()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    clk = clocks.stop()
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * nq / (ms / 1e3)
+    scan_ms = statistics.mean(t.scan_ms for t in traces)
+    launches = int(traces[0].launches) * args.steps
+
+    # ---- e2e: host buffers through the C ABI, copies inside the region ----
+    qh = torch.as_tensor(queries).pin_memory()
+    ih = torch.empty((nq, k), dtype=torch.int64).pin_memory()
+    dh = torch.empty((nq, k), dtype=torch.float32).pin_memory()
+    qn, in_, dn = qh.numpy(), ih.numpy(), dh.numpy()
+    for _ in range(2):
+        fa.fa_search_ex(ix, qn, k, wl["nprobe"], sp, out_ids=in_, out_dist=dn)
+    e2e_ms = []
+    for _ in range(max(3, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fa.fa_search_ex(ix, qn, k, wl["nprobe"], sp, out_ids=in_, out_dist=dn)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_value = world * nq / (statistics.mean(e2e_ms) / 1e3)
+
+    # ---- recall@10 on a subsample (ground truth: exact L2 on the GPU in FP64) ----
+    recall = None
+    if args.recall > 0:
+        import oracle
+        ns = min(args.recall, nq)
+        gt_i, gt_d = ground_truth(base, queries[:ns], 10)
+        found = oid[:ns].cpu().numpy()
+        ex = exact_dists(base, queries[:ns], found)
+        recall = oracle.recall_at(found, gt_i, gt_d, exact_found_dist=ex, at=10)
+
+    # ---- roofline of the scan (dominant kernel) ----
+    peak, peak_src = measured_peaks()
+    achieved = scan_bytes / (scan_ms / 1e3) / 1e9
+    khash = src_hash(SCAN_SOURCES)
+    traffic = profile_traffic(khash)
+
+    # ---- CPU baseline: the oracle as it stands on a bounded sample ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        parts = ix.parts()
+        ns = args.cpu_sample or 200
+        secs, cores, _ = run_oracle_sample(wl, base, queries, parts, ns)
+        cpu = {"value": ns / secs, "unit": "queries/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d of the %d queries, same index and parameters, FP64" % (ns, nq)}
+
+    if rank == 0:
+        line = {
+            "metric": "QPS at recall@10=0.9 on 1 B300, low-prec batched vs FP32 plain; % HBM roofline",
+            "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f16-lut/f32-acc" if lowp else "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["name"], "n": wl["n"], "nq": nq, "d": d, "nlist": wl["nlist"],
+                       "M": wl["M"], "nprobe": wl["nprobe"], "k": k, "form": args.form,
+                       "rerank_n": wl["rerank_n"], "rerank": "Algorithm 1, BatchSize 32, eps 0, beta 2",
+                       "raw_vectors": "pinned host" if wl["rerank_n"] else "none",
+                       "l2": "flushed between timed steps (256 MB write); codes 320 MB > L2",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "recall_at_10": recall,
+            "candidates_per_query": uniq / nq,
+            "stage_ms": {"coarse": statistics.mean(t.coarse_ms for t in traces),
+                         "lut": statistics.mean(t.lut_ms for t in traces), "scan": scan_ms,
+                         "post": statistics.mean(t.post_ms for t in traces)},
+            "roofline": {"bound": "hbm", "kernel": "k_scan", "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": traffic, "algorithmic_bytes_per_launch": scan_bytes,
+                         "kernel_src_hash": khash},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
+                    "d2h_bytes_per_step": nq * k * 12},
+            "gpu_launches": launches,
+            "clocks": clk,
+            "build_s": t_build, "gen_s": t_gen, "index_device_bytes": info.device_bytes,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference_arm(args, wl, rank, world):
+    """The FP64 CPU oracle as the reference implementation: each step is a
+    bounded sample of the workload's queries against the same index."""
+    if rank != 0:
+        return
+    import oracle
+    import paper_2409_16576_b300 as fa  # only to build the index both arms search
+    import torch
+    torch.cuda.set_device(0)
+    base = wl["mix"].base(wl["n"])
+    queries = wl["mix"].queries(wl["nq"])
+    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=8,
+                         raw_location=fa.FA_RAW_HOST_PINNED if wl["rerank_n"] else fa.FA_RAW_NONE)
+    ix = fa.fa_build_index(base, bp)
+    parts = ix.parts()
+    ns = args.cpu_sample or 64
+    times = []
+    for i in range(max(3, args.warmup) + args.steps):
+        secs, cores, _ = run_oracle_sample(wl, base, queries[(i * ns) % wl["nq"]:], parts, ns)
+        if i >= max(3, args.warmup):
+            times.append(secs)
+    ms = statistics.mean(times) * 1e3
+    v = ns / (ms / 1e3)
+    print(json.dumps({
+        "impl": "reference",
+        "metric": "QPS at recall@10=0.9 on 1 B300, low-prec batched vs FP32 plain; % HBM roofline",
+        "value": v, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl["name"], "n": wl["n"], "nq": wl["nq"], "nlist": wl["nlist"],
+                   "M": wl["M"], "nprobe": wl["nprobe"], "k": wl["k"], "form": args.form},
+        "cpu_baseline": {"value": v, "unit": "queries/s", "kind": "oracle", "cores": cpu_cores(),
+                         "sample": "%d queries per step" % ns},
+        "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+/*
+ * fa.h - C ABI of a B300 (sm_103a) implementation of the GPU filtering path of
+ * FusionANNS-style IVF-PQ search (Tian et al., "FusionANNS", arXiv 2409.16576).
+ *
+ * The path for one query (the online steps of Section 3):
+ *   coarse probe  the nprobe posting lists nearest to the query (step 2; the
+ *                 paper walks an in-memory graph, this library computes the
+ *                 exact top-nprobe on the GPU)
+ *   LUT           dist(q_i, c) for every subspace i and centroid c (step 1)
+ *   gather        the vector ids of the probed lists (steps 3-4)
+ *   dedup         every distinct id once (step 5)
+ *   ADC           Eq. 1 over the uint8 PQ codes held in HBM (step 6)
+ *   top-n         the n smallest ADC distances (step 7)
+ *   re-rank       optional, Algorithm 1 / Eq. 3 on exact distances over raw
+ *                 vectors held in pinned host memory or HBM (step 8, §4.2)
+ *
+ * Conventions shared by every call:
+ *   - Distances are squared L2 (the form of Eq. 1 that splits into a sum over
+ *     subspaces). Without re-rank they are ADC distances; with re-rank they
+ *     are exact FP32 distances on the raw vectors.
+ *   - Result rows are row-major [nq][k], ascending by (distance, id); ids are
+ *     the caller's 0-based vector ids. A query with fewer than k distinct
+ *     candidates gets rows padded with id -1 and distance +inf.
+ *   - The caller owns every buffer it passes; the library copies what it keeps.
+ *     The library owns the index (host copies, device memory, pinned memory).
+ *   - Functions return fa_status and never throw across this boundary. After a
+ *     failure the outputs are undefined; fa_last_error() gives a message
+ *     (per calling thread). A CUDA error that leaves the context unusable marks
+ *     the index FA_ERR_STATE for every later call.
+ *   - fa_search / fa_search_ex may be called from several host threads on one
+ *     index at once; each call takes a workspace slot from the index's pool.
+ *   - Every device-side wait is bounded; exceeding a bound returns
+ *     FA_ERR_TIMEOUT, an internal capacity overflow returns FA_ERR_OVERFLOW.
+ */
+#ifndef FA_H
+#define FA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fa_index fa_index; /* opaque, owned by the library */
+
+typedef enum fa_status {
+    FA_OK = 0,
+    FA_ERR_ARG = 1,      /* an argument is out of range or inconsistent */
+    FA_ERR_OOM = 2,      /* device or host allocation failed */
+    FA_ERR_CUDA = 3,     /* a CUDA call failed */
+    FA_ERR_TIMEOUT = 4,  /* a bounded device-side wait ran out */
+    FA_ERR_OVERFLOW = 5, /* an internal buffer bound was exceeded */
+    FA_ERR_STATE = 6,    /* the index is unusable after an earlier fatal error */
+    FA_ERR_BUSY = 7,     /* non-blocking admission found no free slot */
+    FA_ERR_IO = 8,       /* file read/write failed (save/load) */
+    FA_ERR_NODEV = 9     /* no usable CUDA device */
+} fa_status;
+
+typedef enum fa_dtype { FA_F32 = 0, FA_U8 = 1 } fa_dtype;
+
+/* Where the raw vectors used by the re-rank live. The paper keeps them on SSD
+ * (§4.1 "Raw Vectors on SSDs"); pinned host memory read by the GPU over the
+ * host link stands in for that tier. */
+typedef enum fa_raw_location {
+    FA_RAW_NONE = 0,
+    FA_RAW_HOST_PINNED = 1,
+    FA_RAW_DEVICE = 2
+} fa_raw_location;
+
+/* Storage precision of the per-query lookup table (step 1). The scan always
+ * accumulates in FP32; F16 and FP8 (e4m3) tables carry a per-query scale and
+ * a per-subspace offset. */
+typedef enum fa_lut_prec { FA_LUT_F32 = 0, FA_LUT_F16 = 1, FA_LUT_FP8 = 2 } fa_lut_prec;
+
+/* How the LUT (step 1) and the coarse probe (step 2) are computed.
+ *   FA_GEMM_SIMT_F32  FP32 direct differences on the CUDA cores; for the LUT
+ *                     this is built straight into the scan CTA's shared memory.
+ *   FA_GEMM_BF16_TC   the expanded form |q|^2 - 2 q.c + |c|^2 with the dot
+ *                     products on the tcgen05 tensor cores (BF16 operands,
+ *                     FP32 accumulation in tensor memory). */
+typedef enum fa_gemm { FA_GEMM_SIMT_F32 = 0, FA_GEMM_BF16_TC = 1 } fa_gemm;
+
+/* ------------------------------------------------------------------------- */
+/* Index build (offline processing of Section 3, multi-tiered index of §4.1) */
+/* ------------------------------------------------------------------------- */
+
+typedef struct fa_build_params {
+    int32_t nlist;             /* posting lists (IVF cells), >= 1 */
+    int32_t M;                 /* PQ subspaces; d % M == 0; M in {8,16,32,48,64} */
+    int32_t kmeans_iters;      /* Lloyd iterations of the coarse and PQ k-means */
+    int32_t max_lists_per_vec; /* Eq. 2 cap on lists per vector, 1..8 */
+    int64_t train_sample;      /* rows sampled for training; 0 = automatic */
+    uint64_t seed;             /* seed of every random choice of the build */
+    float repl_eps;            /* Eq. 2 epsilon; 0 = each vector in one list */
+    int32_t raw_location;      /* fa_raw_location: keep raw vectors for re-rank */
+    int32_t use_gpu;           /* 1 = run assignment and encoding on the GPU */
+} fa_build_params;
+
+/* Fills p with defaults: nlist 256, M 16, 10 iterations, 1 list per vector,
+ * automatic sample, seed 20240916, no replication, raw vectors not kept,
+ * GPU-assisted build. */
+void fa_build_params_init(fa_build_params *p);
+
+/* Trains an IVF-PQ index on n host vectors base[n][d] of type dt and uploads
+ * it to the current CUDA device: coarse k-means (nlist centroids), Eq. 2
+ * boundary replication (a vector joins every list C_i with
+ * |v - C_i| <= (1 + repl_eps) |v - C_1|, at most max_lists_per_vec lists),
+ * PQ training (M sub-codebooks of 256 centroids over contiguous blocks of
+ * d/M coordinates, §2.2) and encoding. n must be below 2^32.
+ * Returns FA_ERR_ARG for bad shapes, FA_ERR_OOM / FA_ERR_CUDA on failure. */
+fa_status fa_build_index(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                         const fa_build_params *p, fa_index **out);
+
+/* The logical content of an index. Every pointer is host memory. */
+typedef struct fa_index_parts {
+    int64_t n;                /* vectors */
+    int32_t d;                /* dimension */
+    int32_t nlist;            /* posting lists */
+    int32_t M;                /* subspaces (d % M == 0) */
+    int32_t raw_dtype;        /* fa_dtype of raw */
+    int32_t raw_location;     /* fa_raw_location */
+    int32_t pad0;
+    const float *centroids;   /* [nlist][d] list centroids */
+    const float *codebooks;   /* [M][256][d/M] PQ sub-codebooks */
+    const uint8_t *codes;     /* [n][M] PQ code of each vector */
+    const int32_t *primary;   /* [n] the list each vector belongs to first */
+    const int64_t *rep_off;   /* [nlist+1] replica slice offsets, or NULL */
+    const int64_t *rep_ids;   /* [rep_off[nlist]] replicated vector ids */
+    const void *raw;          /* [n][d] raw vectors, or NULL */
+} fa_index_parts;
+
+/* Builds an index from given parts (no training): list l holds the vectors
+ * whose primary list is l followed by rep_ids[rep_off[l] .. rep_off[l+1]).
+ * A vector may appear in a list at most once. The library copies every array.
+ * Returns FA_ERR_ARG for an inconsistent description. */
+fa_status fa_index_from_parts(const fa_index_parts *parts, fa_index **out);
+
+/* A read-only view of the index's host copies (valid until fa_free_index). */
+fa_status fa_index_get_parts(const fa_index *ix, fa_index_parts *out);
+
+typedef struct fa_index_info {
+    int64_t n, n_rep_entries, max_list_len, max_rep_len;
+    int64_t device_bytes, pinned_bytes;
+    int32_t d, nlist, M, device;
+} fa_index_info;
+
+fa_status fa_index_info_get(const fa_index *ix, fa_index_info *out);
+
+/* Checkpoint: a versioned binary file holding the parts of the index. */
+fa_status fa_save_index(const fa_index *ix, const char *path);
+fa_status fa_load_index(const char *path, int32_t raw_location, fa_index **out);
+
+void fa_free_index(fa_index *ix);
+
+/* ------------------------------------------------------------------------- */
+/* Search                                                                    */
+/* ------------------------------------------------------------------------- */
+
+/* flags of fa_search_params */
+#define FA_QUERIES_ON_DEVICE 0x1 /* queries is a device pointer */
+#define FA_OUTPUTS_ON_DEVICE 0x2 /* out_ids / out_dist are device pointers */
+#define FA_NONBLOCKING 0x4       /* FA_ERR_BUSY instead of waiting for a slot */
+#define FA_PERSISTENT 0x8        /* batching form: persistent tile kernel */
+#define FA_NO_SYNC 0x10          /* return without synchronizing sp->stream
+                                  * (device outputs only) */
+
+/* Optional per-call trace, measured with CUDA events on the call's stream
+ * (ms of device time per stage; launches = kernels this call launched). */
+typedef struct fa_search_trace {
+    float coarse_ms, lut_ms, scan_ms, post_ms, total_ms;
+    int32_t launches;
+} fa_search_trace;
+
+typedef struct fa_search_params {
+    int32_t lut_prec;     /* fa_lut_prec */
+    int32_t lut_gemm;     /* fa_gemm for the LUT */
+    int32_t probe_gemm;   /* fa_gemm for the coarse probe */
+    int32_t rerank_n;     /* 0: ADC top-k. >0: re-rank the ADC top-rerank_n */
+    int32_t rerank_batch; /* Algorithm 1 BatchSize, 1..256 */
+    int32_t rerank_beta;  /* Algorithm 1 beta (>= 1) */
+    float rerank_eps;     /* Algorithm 1 epsilon (< 0: never stop early) */
+    int32_t flags;        /* FA_* flags above */
+    const int32_t *k_per_query;      /* optional [nq]; each <= k */
+    const int32_t *nprobe_per_query; /* optional [nq]; each clamped to [1, nprobe] */
+    const int32_t *probes;           /* optional [nq][nprobe] given probe lists */
+    void *stream;                    /* cudaStream_t to run on, or NULL */
+    int64_t *stats;                  /* optional host [nq][4]: gathered ids,
+                                        distinct ids, re-rank mini-batches run,
+                                        candidates handed to the re-rank */
+    fa_search_trace *trace;          /* optional host trace (forces a sync) */
+} fa_search_params;
+
+/* Fills sp with the plain FP32 form: F32 LUT built in the scan CTA, FP32 coarse
+ * probe, no re-rank (BatchSize 32, beta 2, eps 0 when enabled), no flags. */
+void fa_search_params_init(fa_search_params *sp);
+
+/* Top-k search for nq host queries[nq][d] (float32) with the plain FP32 form.
+ * out_ids [nq][k] and out_dist [nq][k] are host buffers. nprobe is clamped to
+ * [1, nlist]. nq == 0 returns FA_OK. d must equal the index's d, k >= 1. */
+fa_status fa_search(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
+                    int32_t nprobe, int64_t *out_ids, float *out_dist);
+
+/* Top-k search with explicit parameters (precision, re-rank, per-query k and
+ * nprobe, device-resident buffers, stream). With FA_QUERIES_ON_DEVICE /
+ * FA_OUTPUTS_ON_DEVICE the pointers are device pointers on the index's device;
+ * otherwise host pointers (pinned memory gives overlapped copies). */
+fa_status fa_search_ex(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
+                       int32_t nprobe, const fa_search_params *sp, int64_t *out_ids,
+                       float *out_dist);
+
+/* ------------------------------------------------------------------------- */
+/* Test hooks (host buffers)                                                 */
+/* ------------------------------------------------------------------------- */
+
+/* Coarse probe (step 2) only: out_probes[nq][nprobe] ascending by distance. */
+fa_status fa_debug_probes(fa_index *ix, const float *queries, int64_t nq, int32_t nprobe,
+                          const fa_search_params *sp, int32_t *out_probes);
+
+/* Gather + dedup (steps 3-5) of one query as run on the GPU: the distinct
+ * vector ids of the probed lists, ascending. probes[nprobe] gives the lists
+ * (NULL runs the coarse probe). *out_n receives the count; FA_ERR_OVERFLOW
+ * if it exceeds cap. */
+fa_status fa_debug_candidates(fa_index *ix, const float *query, int32_t nprobe,
+                              const int32_t *probes, int64_t *out_ids, int64_t cap,
+                              int64_t *out_n);
+
+/* The lookup table of one query (step 1) as the scan reads it, dequantized to
+ * float: out_lut[M][256]. */
+fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params *sp,
+                       float *out_lut);
+
+/* ------------------------------------------------------------------------- */
+/* Errors and version                                                        */
+/* ------------------------------------------------------------------------- */
+
+const char *fa_last_error(void);          /* message of this thread's last failure */
+const char *fa_status_str(fa_status s);   /* static name of a status */
+const char *fa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FA_H */

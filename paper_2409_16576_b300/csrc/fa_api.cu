@@ -1,0 +1,1025 @@
+// C ABI of libfa (declared in include/fa.h): argument checks, the device
+// index (upload, renumbering, rotated code rows, replica tables), the
+// workspace pool and the search pipeline.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "fa_internal.h"
+
+namespace fa {
+
+static float half_bits_to_float(uint16_t h) {
+    __half_raw r;
+    r.x = h;
+    return __half2float(__half(r));
+}
+
+static float e4m3_bits_to_float(uint8_t b) {
+    __nv_fp8_e4m3 v;
+    v.__x = b;
+    return float(v);
+}
+
+static thread_local std::string g_err;
+
+void set_error(const char *fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+const char *last_error() { return g_err.c_str(); }
+
+template <class F>
+static fa_status guarded(fa_index *ix, F &&f) {
+    try {
+        if (ix && ix->sticky.load()) {
+            set_error("index unusable after an earlier fatal CUDA error");
+            return FA_ERR_STATE;
+        }
+        f();
+        return FA_OK;
+    } catch (const Error &e) {
+        set_error("%s", e.msg.c_str());
+        if (e.st == FA_ERR_CUDA && ix) {
+            // a sticky error poisons the context: mark the index unusable
+            cudaError_t s = cudaDeviceSynchronize();
+            if (s != cudaSuccess) ix->sticky.store(1);
+            cudaGetLastError();
+        }
+        return e.st;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return FA_ERR_OOM;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return FA_ERR_CUDA;
+    }
+}
+
+template <class T>
+static T *dev_upload(const T *src, size_t count, int64_t &bytes) {
+    T *p = nullptr;
+    const size_t b = sizeof(T) * (count ? count : 1);
+    if (cudaMalloc(&p, b) != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{FA_ERR_OOM, "device allocation of " + std::to_string(b) + " bytes failed"};
+    }
+    bytes += (int64_t)b;
+    if (count) FA_CHECK_CUDA(cudaMemcpy(p, src, sizeof(T) * count, cudaMemcpyHostToDevice));
+    return p;
+}
+
+void free_device_index(fa_index *ix) {
+    DeviceIndex &d = ix->dev;
+    void *ptrs[] = {d.centroids, d.cnorm, d.codebooks, d.codes, d.list_beg, d.rep_off,
+                    d.rep_v, d.rep_mo, d.rep_t, d.mem, d.perm, d.raw_dev_alloc,
+                    d.centroids_bf16, d.codebooks_bf16, d.cbnorm};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    d = DeviceIndex{};
+}
+
+// Renumbers vectors by primary list, rotates code rows, builds the replica
+// tables and uploads everything.
+void upload_index(fa_index *ix) {
+    FA_CHECK_CUDA(cudaSetDevice(ix->device));
+    DeviceIndex &D = ix->dev;
+    const int64_t n = ix->n;
+    const int d = ix->d, nlist = ix->nlist, M = ix->M;
+    D.n = n;
+    D.d = d;
+    D.nlist = nlist;
+    D.M = M;
+    D.dsub = d / M;
+    D.raw_dtype = ix->raw_dtype;
+    D.raw_location = ix->raw_location;
+    int64_t bytes = 0;
+
+    // internal order: stable by primary list
+    std::vector<int64_t> cnt(nlist + 1, 0);
+    for (int64_t v = 0; v < n; ++v) cnt[ix->primary[v] + 1]++;
+    std::vector<uint32_t> beg(nlist + 1, 0);
+    for (int l = 0; l < nlist; ++l) beg[l + 1] = (uint32_t)(beg[l] + cnt[l + 1]);
+    std::vector<int64_t> perm(n), inv(n);
+    {
+        std::vector<uint32_t> fill(beg.begin(), beg.end() - 1);
+        for (int64_t v = 0; v < n; ++v) {
+            const uint32_t iv = fill[ix->primary[v]]++;
+            perm[iv] = v;
+            inv[v] = iv;
+        }
+    }
+    D.max_list = 0;
+    for (int l = 0; l < nlist; ++l) D.max_list = std::max<int64_t>(D.max_list, beg[l + 1] - beg[l]);
+
+    // rotated code rows: byte s of row iv = code of subspace (s + iv mod 32) mod M
+    const int64_t n_pad = ((n + 31) / 32) * 32 + 32;
+    std::vector<uint8_t> rot((size_t)n_pad * M, 0);
+#pragma omp parallel for schedule(static)
+    for (int64_t iv = 0; iv < n; ++iv) {
+        const uint8_t *src = ix->codes.data() + (size_t)perm[iv] * M;
+        uint8_t *dst = rot.data() + (size_t)iv * M;
+        const int r = (int)(iv & 31);
+        for (int s = 0; s < M; ++s) dst[s] = src[(s + r) % M];
+    }
+
+    // replica tables
+    const bool has_rep = !ix->rep_off.empty() && ix->rep_off[nlist] > 0;
+    std::vector<uint64_t> roff(nlist + 1, 0);
+    std::vector<uint32_t> rv, rmo, mem;
+    std::vector<uint8_t> rt;
+    D.max_rep = 0;
+    if (has_rep) {
+        const int64_t nr = ix->rep_off[nlist];
+        // replica lists of each vector, ascending
+        std::vector<std::vector<int32_t>> reps;
+        std::vector<int64_t> rep_vecs;
+        std::vector<int32_t> slot(n, -1);
+        for (int l = 0; l < nlist; ++l)
+            for (int64_t e = ix->rep_off[l]; e < ix->rep_off[l + 1]; ++e) {
+                const int64_t v = ix->rep_ids[e];
+                if (slot[v] < 0) {
+                    slot[v] = (int32_t)reps.size();
+                    reps.emplace_back();
+                    rep_vecs.push_back(v);
+                }
+                reps[slot[v]].push_back(l);
+            }
+        std::vector<uint32_t> mo_of(reps.size());
+        for (size_t i = 0; i < reps.size(); ++i) {
+            std::sort(reps[i].begin(), reps[i].end());
+            mo_of[i] = (uint32_t)mem.size();
+            mem.push_back((uint32_t)ix->primary[rep_vecs[i]]);
+            for (int32_t l : reps[i]) mem.push_back((uint32_t)l);
+        }
+        FA_REQUIRE(mem.size() < (1ull << 32), FA_ERR_ARG, "replica table too large");
+        FA_REQUIRE(nr < (1ll << 32), FA_ERR_ARG, "too many replica entries");
+        rv.resize(nr);
+        rmo.resize(nr);
+        rt.resize(nr);
+        for (int l = 0; l < nlist; ++l) {
+            // entries of list l sorted by internal id
+            std::vector<std::pair<uint32_t, int64_t>> ent;
+            for (int64_t e = ix->rep_off[l]; e < ix->rep_off[l + 1]; ++e)
+                ent.push_back({(uint32_t)inv[ix->rep_ids[e]], ix->rep_ids[e]});
+            std::sort(ent.begin(), ent.end());
+            int64_t o = ix->rep_off[l];
+            for (auto &pr : ent) {
+                const int32_t s = slot[pr.second];
+                const auto &rl = reps[s];
+                const int t = 1 + (int)(std::lower_bound(rl.begin(), rl.end(), l) - rl.begin());
+                rv[o] = pr.first;
+                rmo[o] = mo_of[s];
+                rt[o] = (uint8_t)t;
+                ++o;
+            }
+            roff[l + 1] = (uint64_t)ix->rep_off[l + 1];
+            D.max_rep = std::max<int64_t>(D.max_rep, ix->rep_off[l + 1] - ix->rep_off[l]);
+        }
+        D.n_rep = nr;
+        D.n_mem = (int64_t)mem.size();
+    }
+
+    std::vector<float> cnorm(nlist);
+    for (int l = 0; l < nlist; ++l) {
+        double s = 0;
+        for (int j = 0; j < d; ++j) s += (double)ix->centroids[(size_t)l * d + j] * ix->centroids[(size_t)l * d + j];
+        cnorm[l] = (float)s;
+    }
+
+    D.centroids = dev_upload(ix->centroids.data(), ix->centroids.size(), bytes);
+    D.cnorm = dev_upload(cnorm.data(), cnorm.size(), bytes);
+    D.codebooks = dev_upload(ix->codebooks.data(), ix->codebooks.size(), bytes);
+    D.codes = dev_upload(rot.data(), rot.size(), bytes);
+    D.list_beg = dev_upload(beg.data(), beg.size(), bytes);
+    D.rep_off = dev_upload(roff.data(), roff.size(), bytes);
+    D.rep_v = dev_upload(rv.data(), rv.size(), bytes);
+    D.rep_mo = dev_upload(rmo.data(), rmo.size(), bytes);
+    D.rep_t = dev_upload(rt.data(), rt.size(), bytes);
+    D.mem = dev_upload(mem.data(), mem.size(), bytes);
+    D.perm = dev_upload(perm.data(), perm.size(), bytes);
+
+    if (ix->h_raw) {
+        const size_t rb = (size_t)n * d * (ix->raw_dtype == FA_U8 ? 1 : 4);
+        if (ix->raw_location == FA_RAW_DEVICE) {
+            D.raw_dev_alloc = dev_upload((const uint8_t *)ix->h_raw, rb, bytes);
+            D.raw = D.raw_dev_alloc;
+        } else {
+            void *dp = nullptr;
+            FA_CHECK_CUDA(cudaHostGetDevicePointer(&dp, ix->h_raw, 0));
+            D.raw = dp;
+            D.pinned_bytes = (int64_t)rb;
+        }
+    }
+    D.device_bytes = bytes;
+}
+
+// ---------------------------------------------------------------------------
+// workspace pool
+// ---------------------------------------------------------------------------
+static void ws_free_buffers(Workspace *w) {
+    void *dp[] = {w->q, w->probes, w->kq, w->npq, w->topkeys, w->out_ids, w->out_dist,
+                  w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr};
+    for (void *p : dp)
+        if (p) cudaFree(p);
+    void *hp[] = {w->h_err, w->h_stats, w->h_small};
+    for (void *p : hp)
+        if (p) cudaFreeHost(p);
+    w->q = nullptr;
+    w->probes = w->kq = w->npq = nullptr;
+    w->topkeys = nullptr;
+    w->out_ids = nullptr;
+    w->out_dist = nullptr;
+    w->stats = nullptr;
+    w->lut = nullptr;
+    w->lut_scale = nullptr;
+    w->coarse_d = nullptr;
+    w->err = w->tile_ctr = nullptr;
+    w->h_err = nullptr;
+    w->h_stats = nullptr;
+    w->h_small = nullptr;
+    w->cap_nq = 0;
+}
+
+template <class T>
+static void dalloc(T *&p, size_t count) {
+    if (cudaMalloc(&p, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+        throw Error{FA_ERR_OOM, "workspace allocation failed"};
+    }
+}
+
+static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t nprobe,
+                      int32_t ntop, int lut_bytes) {
+    const DeviceIndex &D = ix->dev;
+    if (w->cap_nq >= nq && w->cap_k >= k && w->cap_nprobe >= nprobe && w->cap_ntop >= ntop &&
+        w->cap_lut_bytes >= lut_bytes)
+        return;
+    if (w->pending) FA_CHECK_CUDA(cudaEventSynchronize(w->done));
+    w->pending = false;
+    FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
+    const int64_t cq = std::max(nq, w->cap_nq);
+    const int32_t ck = std::max(k, w->cap_k), cp = std::max(nprobe, w->cap_nprobe),
+                  ct = std::max(ntop, w->cap_ntop), cl = std::max(lut_bytes, w->cap_lut_bytes);
+    ws_free_buffers(w);
+    dalloc(w->q, (size_t)cq * D.d);
+    dalloc(w->probes, (size_t)cq * cp);
+    dalloc(w->kq, (size_t)cq);
+    dalloc(w->npq, (size_t)cq);
+    dalloc(w->topkeys, (size_t)cq * ct);
+    dalloc(w->out_ids, (size_t)cq * ck);
+    dalloc(w->out_dist, (size_t)cq * ck);
+    dalloc(w->stats, (size_t)cq * 4);
+    dalloc(w->lut_scale, (size_t)cq * (2 + D.M));
+    if (cl > 0) {
+        char *p = nullptr;
+        dalloc(p, (size_t)cq * cl);
+        w->lut = p;
+    }
+    w->coarse_rows = std::max<int64_t>(64, std::min<int64_t>(cq, (256ll << 20) / (4ll * D.nlist)));
+    dalloc(w->coarse_d, (size_t)w->coarse_rows * D.nlist);
+    dalloc(w->err, 4);
+    dalloc(w->tile_ctr, 4);
+    FA_CHECK_CUDA(cudaHostAlloc((void **)&w->h_err, 16, cudaHostAllocDefault));
+    FA_CHECK_CUDA(cudaHostAlloc((void **)&w->h_stats, sizeof(int32_t) * (size_t)cq * 4, cudaHostAllocDefault));
+    FA_CHECK_CUDA(cudaHostAlloc((void **)&w->h_small, sizeof(int32_t) * (size_t)cq * 2, cudaHostAllocDefault));
+    w->cap_nq = cq;
+    w->cap_k = ck;
+    w->cap_nprobe = cp;
+    w->cap_ntop = ct;
+    w->cap_lut_bytes = cl;
+}
+
+struct WsLease {
+    fa_index *ix;
+    Workspace *w = nullptr;
+    cudaEvent_t done = nullptr;
+    WsLease(fa_index *i, bool nonblocking) : ix(i) {
+        std::unique_lock<std::mutex> lk(ix->mu);
+        for (;;) {
+            if (!ix->free_ws.empty()) {
+                w = ix->free_ws.back();
+                ix->free_ws.pop_back();
+                break;
+            }
+            if ((int)ix->all_ws.size() < ix->max_ws) {
+                w = new Workspace();
+                w->device = ix->device;
+                if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) != cudaSuccess) {
+                    cudaGetLastError();
+                    delete w;
+                    w = nullptr;
+                    throw Error{FA_ERR_CUDA, "stream creation failed"};
+                }
+                ix->all_ws.push_back(w);
+                break;
+            }
+            if (nonblocking) throw Error{FA_ERR_BUSY, "no free workspace slot"};
+            ix->cv.wait(lk);
+        }
+    }
+    ~WsLease() {
+        if (!w) return;
+        std::lock_guard<std::mutex> lk(ix->mu);
+        ix->free_ws.push_back(w);
+        ix->cv.notify_one();
+    }
+};
+
+static int32_t max_changed_for(float eps, int32_t k) {
+    // largest c in [0, k] with c / k <= eps (Algorithm 1's test on Eq. 3)
+    int32_t best = -1;
+    for (int32_t c = 0; c <= k; ++c)
+        if ((double)c / (double)k <= (double)eps) best = c;
+    return best;
+}
+
+// CUDA-event marks between the stages of one call (only when a trace is asked).
+struct Tracer {
+    fa_search_trace *out;
+    cudaStream_t st;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    int32_t launches = 0;
+    Tracer(fa_search_trace *o, cudaStream_t s) : out(o), st(s) {
+        if (!out) return;
+        for (auto &e : ev) FA_CHECK_CUDA(cudaEventCreate(&e));
+    }
+    void mark(int i) {
+        if (out) FA_CHECK_CUDA(cudaEventRecord(ev[i], st));
+    }
+    void finish() {
+        if (!out) return;
+        FA_CHECK_CUDA(cudaEventSynchronize(ev[4]));
+        float t[4];
+        for (int i = 0; i < 4; ++i) FA_CHECK_CUDA(cudaEventElapsedTime(&t[i], ev[i], ev[i + 1]));
+        out->coarse_ms = t[0];
+        out->lut_ms = t[1];
+        out->scan_ms = t[2];
+        out->post_ms = t[3];
+        FA_CHECK_CUDA(cudaEventElapsedTime(&out->total_ms, ev[0], ev[4]));
+        out->launches = launches;
+    }
+    ~Tracer() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+
+static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
+                        int32_t nprobe, const fa_search_params *spp, int64_t *out_ids,
+                        float *out_dist) {
+    fa_search_params sp;
+    if (spp)
+        sp = *spp;
+    else
+        fa_search_params_init(&sp);
+    FA_REQUIRE(d == ix->d, FA_ERR_ARG, "query dimension differs from the index");
+    FA_REQUIRE(k >= 1 && k <= 256, FA_ERR_ARG, "k must be in 1..256");
+    FA_REQUIRE(nq >= 0, FA_ERR_ARG, "nq < 0");
+    if (nq == 0) return;
+    FA_REQUIRE(queries && out_ids && out_dist, FA_ERR_ARG, "null buffer");
+    nprobe = std::max(1, std::min(nprobe, ix->nlist));
+    FA_REQUIRE(nprobe <= 512, FA_ERR_ARG, "nprobe above 512");
+    FA_REQUIRE(sp.lut_prec >= FA_LUT_F32 && sp.lut_prec <= FA_LUT_FP8, FA_ERR_ARG, "bad lut_prec");
+    const bool rerank = sp.rerank_n > 0;
+    int32_t ntop = k;
+    if (rerank) {
+        FA_REQUIRE(ix->dev.raw != nullptr, FA_ERR_ARG, "re-rank needs raw vectors in the index");
+        FA_REQUIRE(k <= 128, FA_ERR_ARG, "re-rank supports k <= 128");
+        FA_REQUIRE(sp.rerank_batch >= 1 && sp.rerank_batch <= 256, FA_ERR_ARG, "bad rerank_batch");
+        FA_REQUIRE(sp.rerank_beta >= 1, FA_ERR_ARG, "rerank_beta < 1");
+        ntop = std::max(sp.rerank_n, k);
+        FA_REQUIRE(ntop <= 256, FA_ERR_ARG, "rerank_n above 256");
+    }
+    const bool qdev = sp.flags & FA_QUERIES_ON_DEVICE, odev = sp.flags & FA_OUTPUTS_ON_DEVICE;
+    const bool global_lut = sp.lut_prec != FA_LUT_F32 || sp.lut_gemm == FA_GEMM_BF16_TC;
+    const int elem = sp.lut_prec == FA_LUT_F32 ? 4 : (sp.lut_prec == FA_LUT_F16 ? 2 : 1);
+    const int lut_bytes = global_lut ? ix->M * 256 * elem : 0;
+
+    FA_CHECK_CUDA(cudaSetDevice(ix->device));
+    WsLease lease(ix, sp.flags & FA_NONBLOCKING);
+    Workspace *w = lease.w;
+    ws_ensure(ix, w, nq, k, nprobe, ntop, lut_bytes);
+    cudaStream_t st = sp.stream ? (cudaStream_t)sp.stream : w->stream;
+    if (w->pending) FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->done, 0));
+    const DeviceIndex &D = ix->dev;
+
+    Tracer tr(sp.trace, st);
+    tr.mark(0);
+    FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
+    const float *qd = queries;
+    if (!qdev) {
+        FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * d, cudaMemcpyHostToDevice, st));
+        qd = w->q;
+    }
+    const int32_t *kq = nullptr, *npq = nullptr;
+    if (sp.k_per_query) {
+        if (qdev) kq = sp.k_per_query;
+        else {
+            FA_CHECK_CUDA(cudaMemcpyAsync(w->kq, sp.k_per_query, 4 * nq, cudaMemcpyHostToDevice, st));
+            kq = w->kq;
+        }
+    }
+    if (sp.nprobe_per_query) {
+        if (qdev) npq = sp.nprobe_per_query;
+        else {
+            FA_CHECK_CUDA(cudaMemcpyAsync(w->npq, sp.nprobe_per_query, 4 * nq, cudaMemcpyHostToDevice, st));
+            npq = w->npq;
+        }
+    }
+    const int32_t *probes = w->probes;
+    if (sp.probes) {
+        if (qdev) probes = sp.probes;
+        else FA_CHECK_CUDA(cudaMemcpyAsync(w->probes, sp.probes, sizeof(int32_t) * nq * nprobe,
+                                           cudaMemcpyHostToDevice, st));
+    } else {
+        launch_coarse(D, qd, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, st);
+        tr.launches += coarse_launches(D, nq, *w);
+    }
+    tr.mark(1);
+    if (global_lut) {
+        launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, st);
+        tr.launches += 1;
+    }
+    tr.mark(2);
+
+    ScanLaunch sl{};
+    sl.q = qd;
+    sl.probes = probes;
+    sl.npq = npq;
+    sl.ntopq = rerank ? nullptr : kq;
+    sl.nq = nq;
+    sl.nprobe = nprobe;
+    sl.probe_stride = nprobe;
+    sl.ntop = ntop;
+    sl.lut_prec = global_lut ? sp.lut_prec : -1;
+    sl.lut = w->lut;
+    sl.lut_scale = w->lut_scale;
+    sl.topkeys = w->topkeys;
+    sl.stats = sp.stats ? w->stats : nullptr;
+    sl.err = w->err;
+    sl.tile_ctr = w->tile_ctr;
+    sl.persistent = (sp.flags & FA_PERSISTENT) ? 1 : 0;
+    if (sl.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
+    if (sp.stats) FA_CHECK_CUDA(cudaMemsetAsync(w->stats, 0, sizeof(int32_t) * 4 * nq, st));
+    launch_scan(D, sl, st);
+    tr.launches += 1;
+    tr.mark(3);
+
+    int64_t *oid = odev ? out_ids : w->out_ids;
+    float *odist = odev ? out_dist : w->out_dist;
+    if (rerank)
+        launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
+                      max_changed_for(sp.rerank_eps, k), oid, odist, sp.stats ? w->stats : nullptr, st);
+    else
+        launch_finish(D, w->topkeys, nq, ntop, k, kq, oid, odist, st);
+    tr.launches += 1;
+    tr.mark(4);
+    if (!odev) {
+        FA_CHECK_CUDA(cudaMemcpyAsync(out_ids, oid, sizeof(int64_t) * nq * k, cudaMemcpyDeviceToHost, st));
+        FA_CHECK_CUDA(cudaMemcpyAsync(out_dist, odist, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, st));
+    }
+    if (sp.stats)
+        FA_CHECK_CUDA(cudaMemcpyAsync(w->h_stats, w->stats, sizeof(int32_t) * 4 * nq, cudaMemcpyDeviceToHost, st));
+    if (!((sp.flags & FA_NO_SYNC) && odev && !sp.stats && !sp.trace))
+        FA_CHECK_CUDA(cudaMemcpyAsync(w->h_err, w->err, 4, cudaMemcpyDeviceToHost, st));
+    if ((sp.flags & FA_NO_SYNC) && odev && !sp.stats && !sp.trace) {
+        // the next user of this slot waits for the event before touching it
+        FA_CHECK_CUDA(cudaEventRecord(w->done, st));
+        w->pending = true;
+        return;
+    }
+    FA_CHECK_CUDA(cudaStreamSynchronize(st));
+    w->pending = false;
+    const uint32_t e = *w->h_err;
+    if (e & DEV_ERR_TIMEOUT) throw Error{FA_ERR_TIMEOUT, "a device-side wait ran out"};
+    if (e & DEV_ERR_OVERFLOW) throw Error{FA_ERR_OVERFLOW, "an internal buffer bound was exceeded"};
+    if (e & DEV_ERR_BOUNDS) throw Error{FA_ERR_ARG, "a probe list id is out of range"};
+    if (sp.stats)
+        for (int64_t i = 0; i < nq * 4; ++i) sp.stats[i] = w->h_stats[i];
+    tr.finish();
+}
+
+static void check_parts(const fa_index_parts *p) {
+    FA_REQUIRE(p != nullptr, FA_ERR_ARG, "null parts");
+    FA_REQUIRE(p->n >= 1 && p->n < (1ll << 32) - 64, FA_ERR_ARG, "n must be in 1 .. 2^32-65");
+    FA_REQUIRE(p->d >= 1 && p->d <= 1024, FA_ERR_ARG, "d must be in 1..1024");
+    FA_REQUIRE(p->nlist >= 1, FA_ERR_ARG, "nlist must be >= 1");
+    FA_REQUIRE(p->M == 8 || p->M == 16 || p->M == 32 || p->M == 48 || p->M == 64, FA_ERR_ARG,
+               "M must be one of 8, 16, 32, 48, 64");
+    FA_REQUIRE(p->d % p->M == 0, FA_ERR_ARG, "d must be a multiple of M");
+    FA_REQUIRE(p->d / p->M <= 16, FA_ERR_ARG, "d / M must be <= 16");
+    FA_REQUIRE(p->centroids && p->codebooks && p->codes && p->primary, FA_ERR_ARG, "null part");
+    FA_REQUIRE(p->raw_dtype == FA_F32 || p->raw_dtype == FA_U8, FA_ERR_ARG, "bad raw dtype");
+    for (int64_t v = 0; v < p->n; ++v)
+        FA_REQUIRE(p->primary[v] >= 0 && p->primary[v] < p->nlist, FA_ERR_ARG, "primary list out of range");
+    if (p->rep_off) {
+        FA_REQUIRE(p->rep_off[0] == 0, FA_ERR_ARG, "rep_off[0] != 0");
+        for (int l = 0; l < p->nlist; ++l)
+            FA_REQUIRE(p->rep_off[l + 1] >= p->rep_off[l], FA_ERR_ARG, "rep_off not ascending");
+        const int64_t nr = p->rep_off[p->nlist];
+        FA_REQUIRE(nr == 0 || p->rep_ids, FA_ERR_ARG, "null rep_ids");
+        std::vector<std::pair<int64_t, int32_t>> seen;
+        seen.reserve(nr);
+        for (int l = 0; l < p->nlist; ++l)
+            for (int64_t e = p->rep_off[l]; e < p->rep_off[l + 1]; ++e) {
+                const int64_t v = p->rep_ids[e];
+                FA_REQUIRE(v >= 0 && v < p->n, FA_ERR_ARG, "replica id out of range");
+                FA_REQUIRE(p->primary[v] != l, FA_ERR_ARG, "a vector is replicated into its own primary list");
+                seen.push_back({v, l});
+            }
+        std::sort(seen.begin(), seen.end());
+        for (size_t i = 1; i < seen.size(); ++i)
+            FA_REQUIRE(seen[i] != seen[i - 1], FA_ERR_ARG, "a vector appears twice in one list");
+        std::vector<int32_t> per(p->n, 0);
+        for (auto &s : seen) FA_REQUIRE(++per[s.first] <= 7, FA_ERR_ARG, "a vector is in more than 8 lists");
+    }
+}
+
+static void copy_parts(fa_index *ix, const fa_index_parts *p) {
+    ix->n = p->n;
+    ix->d = p->d;
+    ix->nlist = p->nlist;
+    ix->M = p->M;
+    ix->raw_dtype = p->raw_dtype;
+    ix->raw_location = p->raw ? (p->raw_location ? p->raw_location : FA_RAW_HOST_PINNED) : FA_RAW_NONE;
+    ix->centroids.assign(p->centroids, p->centroids + (size_t)p->nlist * p->d);
+    ix->codebooks.assign(p->codebooks, p->codebooks + (size_t)p->d * 256);
+    ix->codes.assign(p->codes, p->codes + (size_t)p->n * p->M);
+    ix->primary.assign(p->primary, p->primary + p->n);
+    if (p->rep_off) {
+        ix->rep_off.assign(p->rep_off, p->rep_off + p->nlist + 1);
+        ix->rep_ids.assign(p->rep_ids, p->rep_ids + p->rep_off[p->nlist]);
+    } else {
+        ix->rep_off.assign(p->nlist + 1, 0);
+    }
+    if (p->raw) {
+        const size_t rb = (size_t)p->n * p->d * (p->raw_dtype == FA_U8 ? 1 : 4);
+        if (ix->raw_location == FA_RAW_HOST_PINNED) {
+            FA_CHECK_CUDA(cudaHostAlloc(&ix->h_raw, rb, cudaHostAllocMapped | cudaHostAllocPortable));
+            ix->h_raw_pinned = true;
+        } else {
+            ix->h_raw = malloc(rb);
+            FA_REQUIRE(ix->h_raw, FA_ERR_OOM, "host allocation of raw vectors failed");
+        }
+        memcpy(ix->h_raw, p->raw, rb);
+    }
+}
+
+static void destroy(fa_index *ix) {
+    if (!ix) return;
+    cudaSetDevice(ix->device);
+    for (Workspace *w : ix->all_ws) {
+        if (w->pending) cudaEventSynchronize(w->done);
+        if (w->stream) cudaStreamSynchronize(w->stream);
+        ws_free_buffers(w);
+        if (w->stream) cudaStreamDestroy(w->stream);
+        if (w->done) cudaEventDestroy(w->done);
+        delete w;
+    }
+    free_device_index(ix);
+    if (ix->h_raw) {
+        if (ix->h_raw_pinned) cudaFreeHost(ix->h_raw);
+        else free(ix->h_raw);
+    }
+    delete ix;
+}
+
+static int current_device() {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{FA_ERR_NODEV, std::string("no usable CUDA device: ") + cudaGetErrorString(e)};
+    }
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+        cudaGetLastError();
+        throw Error{FA_ERR_NODEV, "no usable CUDA device"};
+    }
+    return dev;
+}
+
+}  // namespace fa
+
+using namespace fa;
+
+extern "C" {
+
+void fa_build_params_init(fa_build_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->nlist = 256;
+    p->M = 16;
+    p->kmeans_iters = 10;
+    p->max_lists_per_vec = 1;
+    p->train_sample = 0;
+    p->seed = 20240916ull;
+    p->repl_eps = 0.f;
+    p->raw_location = FA_RAW_NONE;
+    p->use_gpu = 1;
+}
+
+void fa_search_params_init(fa_search_params *sp) {
+    if (!sp) return;
+    memset(sp, 0, sizeof *sp);
+    sp->lut_prec = FA_LUT_F32;
+    sp->lut_gemm = FA_GEMM_SIMT_F32;
+    sp->probe_gemm = FA_GEMM_SIMT_F32;
+    sp->rerank_n = 0;
+    sp->rerank_batch = 32;
+    sp->rerank_beta = 2;
+    sp->rerank_eps = 0.f;
+}
+
+fa_status fa_index_from_parts(const fa_index_parts *parts, fa_index **out) {
+    if (!out) {
+        set_error("null output pointer");
+        return FA_ERR_ARG;
+    }
+    *out = nullptr;
+    fa_index *ix = nullptr;
+    fa_status s = guarded(nullptr, [&] {
+        check_parts(parts);
+        ix = new fa_index();
+        ix->device = current_device();
+        copy_parts(ix, parts);
+        upload_index(ix);
+    });
+    if (s != FA_OK) {
+        destroy(ix);
+        return s;
+    }
+    *out = ix;
+    return FA_OK;
+}
+
+fa_status fa_build_index(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                         const fa_build_params *p, fa_index **out) {
+    if (!out) {
+        set_error("null output pointer");
+        return FA_ERR_ARG;
+    }
+    *out = nullptr;
+    fa_build_params bp;
+    if (p)
+        bp = *p;
+    else
+        fa_build_params_init(&bp);
+    fa_index *ix = nullptr;
+    fa_status s = guarded(nullptr, [&] {
+        FA_REQUIRE(base != nullptr, FA_ERR_ARG, "null base");
+        FA_REQUIRE(dt == FA_F32 || dt == FA_U8, FA_ERR_ARG, "bad dtype");
+        FA_REQUIRE(n >= 1 && n < (1ll << 32) - 64, FA_ERR_ARG, "n out of range");
+        FA_REQUIRE(bp.nlist >= 1 && bp.nlist <= n, FA_ERR_ARG, "nlist must be in 1..n");
+        FA_REQUIRE(bp.max_lists_per_vec >= 1 && bp.max_lists_per_vec <= 8, FA_ERR_ARG,
+                   "max_lists_per_vec must be in 1..8");
+        FA_REQUIRE(bp.M >= 1 && d % bp.M == 0, FA_ERR_ARG, "d must be a multiple of M");
+        FA_REQUIRE(bp.kmeans_iters >= 0, FA_ERR_ARG, "kmeans_iters < 0");
+        if (bp.use_gpu) current_device();
+        BuildOut bo;
+        train_and_encode(base, n, d, dt, bp, bo);
+        fa_index_parts parts{};
+        parts.n = n;
+        parts.d = d;
+        parts.nlist = bp.nlist;
+        parts.M = bp.M;
+        parts.raw_dtype = dt;
+        parts.raw_location = bp.raw_location;
+        parts.centroids = bo.centroids.data();
+        parts.codebooks = bo.codebooks.data();
+        parts.codes = bo.codes.data();
+        parts.primary = bo.primary.data();
+        parts.rep_off = bo.rep_off.data();
+        parts.rep_ids = bo.rep_ids.data();
+        parts.raw = bp.raw_location != FA_RAW_NONE ? base : nullptr;
+        check_parts(&parts);
+        ix = new fa_index();
+        ix->device = current_device();
+        copy_parts(ix, &parts);
+        upload_index(ix);
+    });
+    if (s != FA_OK) {
+        destroy(ix);
+        return s;
+    }
+    *out = ix;
+    return FA_OK;
+}
+
+fa_status fa_index_get_parts(const fa_index *ix, fa_index_parts *out) {
+    if (!ix || !out) {
+        set_error("null argument");
+        return FA_ERR_ARG;
+    }
+    memset(out, 0, sizeof *out);
+    out->n = ix->n;
+    out->d = ix->d;
+    out->nlist = ix->nlist;
+    out->M = ix->M;
+    out->raw_dtype = ix->raw_dtype;
+    out->raw_location = ix->raw_location;
+    out->centroids = ix->centroids.data();
+    out->codebooks = ix->codebooks.data();
+    out->codes = ix->codes.data();
+    out->primary = ix->primary.data();
+    out->rep_off = ix->rep_off.data();
+    out->rep_ids = ix->rep_ids.data();
+    out->raw = ix->h_raw;
+    return FA_OK;
+}
+
+fa_status fa_index_info_get(const fa_index *ix, fa_index_info *out) {
+    if (!ix || !out) {
+        set_error("null argument");
+        return FA_ERR_ARG;
+    }
+    memset(out, 0, sizeof *out);
+    out->n = ix->n;
+    out->n_rep_entries = ix->dev.n_rep;
+    out->max_list_len = ix->dev.max_list;
+    out->max_rep_len = ix->dev.max_rep;
+    out->device_bytes = ix->dev.device_bytes;
+    out->pinned_bytes = ix->dev.pinned_bytes;
+    out->d = ix->d;
+    out->nlist = ix->nlist;
+    out->M = ix->M;
+    out->device = ix->device;
+    return FA_OK;
+}
+
+static const char MAGIC[8] = {'F', 'A', 'I', 'D', 'X', '0', '0', '1'};
+
+fa_status fa_save_index(const fa_index *ix, const char *path) {
+    if (!ix || !path) {
+        set_error("null argument");
+        return FA_ERR_ARG;
+    }
+    FILE *f = fopen(path, "wb");
+    if (!f) {
+        set_error("cannot open %s for writing", path);
+        return FA_ERR_IO;
+    }
+    bool ok = true;
+    auto W = [&](const void *p, size_t b) { ok = ok && (b == 0 || fwrite(p, 1, b, f) == b); };
+    const int64_t hdr[8] = {1, ix->n, ix->d, ix->nlist, ix->M, ix->raw_dtype,
+                            ix->h_raw ? 1 : 0, (int64_t)ix->rep_ids.size()};
+    W(MAGIC, 8);
+    W(hdr, sizeof hdr);
+    W(ix->centroids.data(), 4 * ix->centroids.size());
+    W(ix->codebooks.data(), 4 * ix->codebooks.size());
+    W(ix->codes.data(), ix->codes.size());
+    W(ix->primary.data(), 4 * ix->primary.size());
+    W(ix->rep_off.data(), 8 * ix->rep_off.size());
+    W(ix->rep_ids.data(), 8 * ix->rep_ids.size());
+    if (ix->h_raw) W(ix->h_raw, (size_t)ix->n * ix->d * (ix->raw_dtype == FA_U8 ? 1 : 4));
+    ok = (fclose(f) == 0) && ok;
+    if (!ok) {
+        set_error("write to %s failed", path);
+        return FA_ERR_IO;
+    }
+    return FA_OK;
+}
+
+fa_status fa_load_index(const char *path, int32_t raw_location, fa_index **out) {
+    if (!path || !out) {
+        set_error("null argument");
+        return FA_ERR_ARG;
+    }
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    if (!f) {
+        set_error("cannot open %s", path);
+        return FA_ERR_IO;
+    }
+    bool ok = true;
+    auto R = [&](void *p, size_t b) { ok = ok && (b == 0 || fread(p, 1, b, f) == b); };
+    char magic[8];
+    int64_t hdr[8];
+    R(magic, 8);
+    R(hdr, sizeof hdr);
+    if (!ok || memcmp(magic, MAGIC, 8) != 0 || hdr[0] != 1 || hdr[1] < 1 || hdr[2] < 1 ||
+        hdr[2] > 1024 || hdr[3] < 1 || hdr[4] < 1 || hdr[7] < 0) {
+        fclose(f);
+        set_error("%s is not an index file of this version", path);
+        return FA_ERR_IO;
+    }
+    const int64_t n = hdr[1], nr = hdr[7];
+    const int32_t d = (int32_t)hdr[2], nlist = (int32_t)hdr[3], M = (int32_t)hdr[4];
+    const int32_t rdt = (int32_t)hdr[5];
+    std::vector<float> cent, cb;
+    std::vector<uint8_t> codes, raw;
+    std::vector<int32_t> prim;
+    std::vector<int64_t> roff, rids;
+    try {
+        cent.resize((size_t)nlist * d);
+        cb.resize((size_t)d * 256);
+        codes.resize((size_t)n * M);
+        prim.resize(n);
+        roff.resize(nlist + 1);
+        rids.resize(nr);
+        if (hdr[6]) raw.resize((size_t)n * d * (rdt == FA_U8 ? 1 : 4));
+    } catch (...) {
+        fclose(f);
+        set_error("host allocation failed");
+        return FA_ERR_OOM;
+    }
+    R(cent.data(), 4 * cent.size());
+    R(cb.data(), 4 * cb.size());
+    R(codes.data(), codes.size());
+    R(prim.data(), 4 * prim.size());
+    R(roff.data(), 8 * roff.size());
+    R(rids.data(), 8 * rids.size());
+    if (hdr[6]) R(raw.data(), raw.size());
+    fclose(f);
+    if (!ok) {
+        set_error("%s is truncated", path);
+        return FA_ERR_IO;
+    }
+    fa_index_parts p{};
+    p.n = n;
+    p.d = d;
+    p.nlist = nlist;
+    p.M = M;
+    p.raw_dtype = rdt;
+    p.raw_location = hdr[6] ? (raw_location ? raw_location : FA_RAW_HOST_PINNED) : FA_RAW_NONE;
+    p.centroids = cent.data();
+    p.codebooks = cb.data();
+    p.codes = codes.data();
+    p.primary = prim.data();
+    p.rep_off = roff.data();
+    p.rep_ids = rids.data();
+    p.raw = (hdr[6] && raw_location != FA_RAW_NONE) ? raw.data() : nullptr;
+    if (!p.raw) p.raw_location = FA_RAW_NONE;
+    return fa_index_from_parts(&p, out);
+}
+
+void fa_free_index(fa_index *ix) { destroy(ix); }
+
+fa_status fa_search_ex(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
+                       int32_t nprobe, const fa_search_params *sp, int64_t *out_ids,
+                       float *out_dist) {
+    if (!ix) {
+        set_error("null index");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] { search_impl(ix, queries, nq, d, k, nprobe, sp, out_ids, out_dist); });
+}
+
+fa_status fa_search(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
+                    int32_t nprobe, int64_t *out_ids, float *out_dist) {
+    return fa_search_ex(ix, queries, nq, d, k, nprobe, nullptr, out_ids, out_dist);
+}
+
+fa_status fa_debug_probes(fa_index *ix, const float *queries, int64_t nq, int32_t nprobe,
+                          const fa_search_params *spp, int32_t *out_probes) {
+    if (!ix) {
+        set_error("null index");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] {
+        FA_REQUIRE(nq >= 0 && queries && out_probes, FA_ERR_ARG, "bad arguments");
+        FA_REQUIRE(nprobe >= 1 && nprobe <= std::min(ix->nlist, 512), FA_ERR_ARG,
+                   "nprobe must be in 1..min(nlist, 512)");
+        if (nq == 0) return;
+        fa_search_params sp;
+        if (spp) sp = *spp; else fa_search_params_init(&sp);
+        FA_CHECK_CUDA(cudaSetDevice(ix->device));
+        WsLease lease(ix, false);
+        Workspace *w = lease.w;
+        ws_ensure(ix, w, nq, 1, nprobe, 1, 0);
+        FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * ix->d, cudaMemcpyHostToDevice, w->stream));
+        launch_coarse(ix->dev, w->q, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, w->stream);
+        FA_CHECK_CUDA(cudaMemcpyAsync(out_probes, w->probes, sizeof(int32_t) * nq * nprobe,
+                                      cudaMemcpyDeviceToHost, w->stream));
+        FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
+    });
+}
+
+fa_status fa_debug_candidates(fa_index *ix, const float *query, int32_t nprobe,
+                              const int32_t *probes, int64_t *out_ids, int64_t cap,
+                              int64_t *out_n) {
+    if (!ix) {
+        set_error("null index");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] {
+        FA_REQUIRE(out_ids && out_n && (query || probes), FA_ERR_ARG, "bad arguments");
+        FA_REQUIRE(nprobe >= 1 && nprobe <= std::min(ix->nlist, 512), FA_ERR_ARG,
+                   "nprobe must be in 1..min(nlist, 512)");
+        FA_CHECK_CUDA(cudaSetDevice(ix->device));
+        WsLease lease(ix, false);
+        Workspace *w = lease.w;
+        ws_ensure(ix, w, 1, 1, nprobe, 1, 0);
+        cudaStream_t st = w->stream;
+        if (probes) {
+            FA_CHECK_CUDA(cudaMemcpyAsync(w->probes, probes, 4 * nprobe, cudaMemcpyHostToDevice, st));
+        } else {
+            FA_CHECK_CUDA(cudaMemcpyAsync(w->q, query, sizeof(float) * ix->d, cudaMemcpyHostToDevice, st));
+            launch_coarse(ix->dev, w->q, 1, nprobe, nprobe, FA_GEMM_SIMT_F32, *w, w->probes, st);
+        }
+        const int64_t bound = (ix->dev.max_list + ix->dev.max_rep) * (int64_t)nprobe;
+        uint32_t *buf = nullptr, *cnt = nullptr;
+        dalloc(buf, (size_t)std::max<int64_t>(bound, 1));
+        dalloc(cnt, 2);
+        struct Free {
+            void *a, *b;
+            ~Free() { cudaFree(a); cudaFree(b); }
+        } fr{buf, cnt};
+        FA_CHECK_CUDA(cudaMemsetAsync(cnt, 0, 8, st));
+        launch_debug_candidates(ix->dev, w->probes, nprobe, buf, cnt, (uint32_t)bound, st);
+        uint32_t hc[2];
+        FA_CHECK_CUDA(cudaMemcpyAsync(hc, cnt, 8, cudaMemcpyDeviceToHost, st));
+        FA_CHECK_CUDA(cudaStreamSynchronize(st));
+        FA_REQUIRE(hc[1] == 0, FA_ERR_OVERFLOW, "candidate buffer overflow");
+        std::vector<uint32_t> iv(hc[0]);
+        FA_CHECK_CUDA(cudaMemcpy(iv.data(), buf, 4 * (size_t)hc[0], cudaMemcpyDeviceToHost));
+        std::vector<int64_t> perm(ix->n);
+        FA_CHECK_CUDA(cudaMemcpy(perm.data(), ix->dev.perm, 8 * (size_t)ix->n, cudaMemcpyDeviceToHost));
+        std::vector<int64_t> ids(hc[0]);
+        for (size_t i = 0; i < iv.size(); ++i) ids[i] = perm[iv[i]];
+        std::sort(ids.begin(), ids.end());
+        *out_n = (int64_t)ids.size();
+        FA_REQUIRE((int64_t)ids.size() <= cap, FA_ERR_OVERFLOW, "output capacity too small");
+        std::copy(ids.begin(), ids.end(), out_ids);
+    });
+}
+
+fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params *spp,
+                       float *out_lut) {
+    if (!ix) {
+        set_error("null index");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] {
+        FA_REQUIRE(query && out_lut, FA_ERR_ARG, "bad arguments");
+        fa_search_params sp;
+        if (spp) sp = *spp; else fa_search_params_init(&sp);
+        FA_CHECK_CUDA(cudaSetDevice(ix->device));
+        WsLease lease(ix, false);
+        Workspace *w = lease.w;
+        const int elem = sp.lut_prec == FA_LUT_F32 ? 4 : (sp.lut_prec == FA_LUT_F16 ? 2 : 1);
+        const int M = ix->M;
+        ws_ensure(ix, w, 1, 1, 1, 1, M * 256 * elem);
+        cudaStream_t st = w->stream;
+        FA_CHECK_CUDA(cudaMemcpyAsync(w->q, query, sizeof(float) * ix->d, cudaMemcpyHostToDevice, st));
+        launch_lut_global(ix->dev, w->q, 1, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, st);
+        std::vector<uint8_t> raw((size_t)M * 256 * elem);
+        std::vector<float> sc(2 + M);
+        FA_CHECK_CUDA(cudaMemcpyAsync(raw.data(), w->lut, raw.size(), cudaMemcpyDeviceToHost, st));
+        FA_CHECK_CUDA(cudaMemcpyAsync(sc.data(), w->lut_scale, 4 * sc.size(), cudaMemcpyDeviceToHost, st));
+        FA_CHECK_CUDA(cudaStreamSynchronize(st));
+        for (int m = 0; m < M; ++m)
+            for (int c = 0; c < 256; ++c) {
+                const size_t i = (size_t)m * 256 + c;
+                float v;
+                if (sp.lut_prec == FA_LUT_F32) {
+                    memcpy(&v, raw.data() + 4 * i, 4);
+                } else if (sp.lut_prec == FA_LUT_F16) {
+                    uint16_t h;
+                    memcpy(&h, raw.data() + 2 * i, 2);
+                    v = half_bits_to_float(h) * sc[0] + sc[2 + m];
+                } else {
+                    v = e4m3_bits_to_float(raw[i]) * sc[0] + sc[2 + m];
+                }
+                out_lut[i] = v;
+            }
+    });
+}
+
+const char *fa_last_error(void) { return fa::last_error(); }
+
+const char *fa_status_str(fa_status s) {
+    switch (s) {
+        case FA_OK: return "FA_OK";
+        case FA_ERR_ARG: return "FA_ERR_ARG";
+        case FA_ERR_OOM: return "FA_ERR_OOM";
+        case FA_ERR_CUDA: return "FA_ERR_CUDA";
+        case FA_ERR_TIMEOUT: return "FA_ERR_TIMEOUT";
+        case FA_ERR_OVERFLOW: return "FA_ERR_OVERFLOW";
+        case FA_ERR_STATE: return "FA_ERR_STATE";
+        case FA_ERR_BUSY: return "FA_ERR_BUSY";
+        case FA_ERR_IO: return "FA_ERR_IO";
+        case FA_ERR_NODEV: return "FA_ERR_NODEV";
+    }
+    return "FA_ERR_UNKNOWN";
+}
+
+const char *fa_version(void) { return "fa 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// Internal structures of libfa: the device-resident index, per-call
+// workspaces and the kernel launch interfaces.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <condition_variable>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/fa.h"
+
+namespace fa {
+
+// -------------------------------------------------------------------------
+// error plumbing (no exceptions cross the C boundary)
+// -------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+const char *last_error();
+
+struct Error {
+    fa_status st;
+    std::string msg;
+};
+
+#define FA_CHECK_CUDA(expr)                                                        \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess)                                                     \
+            throw ::fa::Error{FA_ERR_CUDA, std::string(#expr) + ": " +             \
+                                               cudaGetErrorString(_e)};            \
+    } while (0)
+
+#define FA_REQUIRE(cond, status, msg)                                              \
+    do {                                                                           \
+        if (!(cond)) throw ::fa::Error{(status), std::string(msg)};                \
+    } while (0)
+
+// device error flags written by kernels (bit set = condition seen)
+enum DevErr : uint32_t {
+    DEV_ERR_OVERFLOW = 1u,
+    DEV_ERR_TIMEOUT = 2u,
+    DEV_ERR_BOUNDS = 4u,
+};
+
+// LUT row stride (floats) in shared memory for M subspaces: every position
+// p = r + s (r = v mod 32, s < M) must exist, so the row holds M + 31 entries.
+inline int lut_row_words(int M) {
+    int w = M + 32;
+    return w <= 64 ? 64 : (w <= 80 ? 80 : 128);
+}
+
+// -------------------------------------------------------------------------
+// device index
+// -------------------------------------------------------------------------
+struct DeviceIndex {
+    int64_t n = 0;
+    int32_t d = 0, nlist = 0, M = 0, dsub = 0;
+    int32_t raw_dtype = FA_U8, raw_location = FA_RAW_NONE;
+    int64_t n_rep = 0;        // replica entries
+    int64_t n_mem = 0;        // membership table entries
+    int64_t max_list = 0;     // longest primary range
+    int64_t max_rep = 0;      // longest replica slice
+
+    float *centroids = nullptr;   // [nlist][d]
+    float *cnorm = nullptr;       // [nlist] |c|^2
+    float *codebooks = nullptr;   // [M][256][dsub]
+    uint8_t *codes = nullptr;     // [n_pad][M], internal order, rotated rows
+    uint32_t *list_beg = nullptr; // [nlist+1] primary ranges in internal ids
+    uint64_t *rep_off = nullptr;  // [nlist+1]
+    uint32_t *rep_v = nullptr;    // [n_rep] internal id of each replica entry
+    uint32_t *rep_mo = nullptr;   // [n_rep] offset of the vector's membership row
+    uint8_t *rep_t = nullptr;     // [n_rep] position of this list in that row (>= 1)
+    uint32_t *mem = nullptr;      // [n_mem] membership rows: primary, then replicas
+    int64_t *perm = nullptr;      // [n] internal id -> caller id
+    const void *raw = nullptr;    // [n][d] raw vectors (caller order), device-visible
+    void *raw_dev_alloc = nullptr;
+    void *raw_host_alloc = nullptr;
+    // bf16 operands for the tensor-core paths (allocated on first use)
+    void *centroids_bf16 = nullptr; // [nlist][d] hi + [nlist][d] lo
+    void *codebooks_bf16 = nullptr;
+    float *cbnorm = nullptr;        // [M][256] |C_m[c]|^2 of the bf16-rounded codebook
+    int64_t device_bytes = 0;
+    int64_t pinned_bytes = 0;
+};
+
+// -------------------------------------------------------------------------
+// per-call workspace (one slot of the index's pool, §5's per-query blocks)
+// -------------------------------------------------------------------------
+struct Workspace {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;    // end of the last no-sync call on this slot
+    bool pending = false;
+    int64_t cap_nq = 0;
+    int32_t cap_k = 0, cap_nprobe = 0, cap_ntop = 0, cap_lut_bytes = 0;
+    float *q = nullptr;            // [cap_nq][d]
+    int32_t *probes = nullptr;     // [cap_nq][cap_nprobe]
+    int32_t *kq = nullptr;         // [cap_nq]
+    int32_t *npq = nullptr;        // [cap_nq]
+    uint64_t *topkeys = nullptr;   // [cap_nq][cap_ntop]
+    int64_t *out_ids = nullptr;    // [cap_nq][cap_k]
+    float *out_dist = nullptr;     // [cap_nq][cap_k]
+    int32_t *stats = nullptr;      // [cap_nq][4]
+    void *lut = nullptr;           // [cap_nq][lut_bytes] global LUT (precision form)
+    float *lut_scale = nullptr;    // [cap_nq][2 + M] scale, offset sum, per-subspace offsets
+    float *coarse_d = nullptr;     // coarse distance scratch [coarse_rows][nlist]
+    int64_t coarse_rows = 0;
+    uint32_t *err = nullptr;       // device error word
+    uint32_t *tile_ctr = nullptr;  // persistent-kernel work counters
+    // pinned host staging for host-buffer calls
+    float *h_q = nullptr;
+    int64_t *h_ids = nullptr;
+    float *h_dist = nullptr;
+    int32_t *h_small = nullptr;    // per-query k / nprobe staging
+    uint32_t *h_err = nullptr;
+    int32_t *h_stats = nullptr;
+    int64_t h_cap_nq = 0;
+    int32_t h_cap_k = 0;
+};
+
+}  // namespace fa
+
+struct fa_index {
+    // logical host copies (caller order)
+    int64_t n = 0;
+    int32_t d = 0, nlist = 0, M = 0;
+    int32_t raw_dtype = FA_U8, raw_location = FA_RAW_NONE;
+    std::vector<float> centroids, codebooks;
+    std::vector<uint8_t> codes;
+    std::vector<int32_t> primary;
+    std::vector<int64_t> rep_off, rep_ids;
+    void *h_raw = nullptr;        // caller-order raw copy (pinned when HOST_PINNED)
+    bool h_raw_pinned = false;
+    int device = 0;
+    fa::DeviceIndex dev;
+    // workspace pool
+    std::mutex mu;
+    std::condition_variable cv;
+    std::vector<fa::Workspace *> all_ws, free_ws;
+    int max_ws = 8;
+    std::atomic<int> sticky{0};
+};
+
+namespace fa {
+
+// -------------------------------------------------------------------------
+// host-side building blocks
+// -------------------------------------------------------------------------
+struct BuildOut {
+    std::vector<float> centroids, codebooks;
+    std::vector<uint8_t> codes;
+    std::vector<int32_t> primary;
+    std::vector<int64_t> rep_off, rep_ids;
+};
+
+// Trains and encodes (host threads, optionally GPU-assisted).
+void train_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                      const fa_build_params &p, BuildOut &out);
+
+// Uploads the logical parts to the device (renumbering, rotated codes, CSR).
+void upload_index(fa_index *ix);
+void free_device_index(fa_index *ix);
+
+// GPU helpers used by the build: nearest-r centroids of rows (float or u8).
+void gpu_assign_topr(const void *rows, int64_t n, int32_t d, fa_dtype dt, const float *centroids,
+                     int32_t nlist, int32_t r, int32_t *out_ids, float *out_d2);
+void gpu_encode(const void *rows, int64_t n, int32_t d, fa_dtype dt, const float *codebooks,
+                int32_t M, uint8_t *out_codes);
+
+// -------------------------------------------------------------------------
+// kernel launchers (kernels/*.cu)
+// -------------------------------------------------------------------------
+struct ScanLaunch {
+    const float *q;          // [nq][d]
+    const int32_t *probes;   // [nq][probe_stride]
+    const int32_t *npq;      // [nq] or null (uniform nprobe)
+    const int32_t *ntopq;    // [nq] or null (uniform ntop)
+    int64_t nq;
+    int32_t nprobe, probe_stride, ntop;
+    int32_t lut_prec;        // FA_LUT_* of a precomputed global LUT, or -1 to build in smem
+    const void *lut;         // global LUT [nq][M][256] (when lut_prec >= 0)
+    const float *lut_scale;  // [nq][2 + M]
+    uint64_t *topkeys;       // [nq][ntop] out
+    int32_t *stats;          // [nq][4] or null
+    uint32_t *err;
+    int persistent;
+    uint32_t *tile_ctr;
+};
+
+void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
+                   int32_t probe_stride, int gemm, Workspace &ws, int32_t *probes,
+                   cudaStream_t st);
+int coarse_launches(const DeviceIndex &ix, int64_t nq, const Workspace &ws);
+void launch_scan(const DeviceIndex &ix, const ScanLaunch &a, cudaStream_t st);
+void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int prec, int gemm,
+                       void *lut, float *lut_scale, cudaStream_t st);
+void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, int32_t ntop,
+                   int32_t k, const int32_t *kq, int64_t *out_ids, float *out_dist,
+                   cudaStream_t st);
+void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
+                   int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
+                   int32_t max_changed, int64_t *out_ids, float *out_dist, int32_t *stats,
+                   cudaStream_t st);
+void launch_debug_candidates(const DeviceIndex &ix, const int32_t *probes, int32_t nprobe,
+                             uint32_t *out, uint32_t *count, uint32_t cap, cudaStream_t st);
+
+int num_sms(int device);
+
+}  // namespace fa

@@ -1,0 +1,272 @@
+// Step 2 of the filtering path (coarse probe): the nprobe posting lists whose
+// centroids are nearest to each query. The paper walks an SPTAG graph on the
+// CPU (§4.1 "In-memory Indices"); here the exact top-nprobe is computed on the
+// GPU. This file holds the FP32 direct-difference form:
+//   k_l2_tile   squared L2 between a tile of rows and a tile of centroids
+//               (FP32, sum of (x_j - c_j)^2, no cancellation)
+//   k_select    per-row top-n of those distances by (distance, column)
+// The same two kernels serve the GPU-assisted index build (nearest-r lists of
+// every base vector for Eq. 2, k-means assignment). k_encode picks the PQ
+// code of every subspace (nearest of the 256 sub-centroids).
+#include <algorithm>
+
+#include "../fa_internal.h"
+#include "warp_topk.cuh"
+
+namespace fa {
+
+constexpr int TILE = 64;
+constexpr int KC = 32;  // dimensions per smem stage
+constexpr int LDS = TILE + 4;
+
+__global__ void __launch_bounds__(256) k_l2_tile(const float *__restrict__ X, int64_t nx,
+                                                 const float *__restrict__ C, int32_t nc,
+                                                 int32_t d, float *__restrict__ D, int64_t ldd) {
+    __shared__ __align__(16) float xs[KC][LDS];
+    __shared__ __align__(16) float cs[KC][LDS];
+    const int t = threadIdx.x;
+    const int ty = t >> 4, tx = t & 15;
+    const int64_t row0 = (int64_t)blockIdx.y * TILE;
+    const int64_t col0 = (int64_t)blockIdx.x * TILE;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+
+    for (int k0 = 0; k0 < d; k0 += KC) {
+        // stage a 64 x 32 slice of rows and of centroids, transposed
+        for (int e = t; e < TILE * KC; e += 256) {
+            const int r = e / KC, k = e % KC;
+            const int64_t xr = row0 + r, cr = col0 + r;
+            const int kk = k0 + k;
+            xs[k][r] = (xr < nx && kk < d) ? X[xr * d + kk] : 0.f;
+            cs[k][r] = (cr < nc && kk < d) ? C[cr * d + kk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int k = 0; k < KC; ++k) {
+            const float4 a = *reinterpret_cast<const float4 *>(&xs[k][ty * 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&cs[k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float df = av[i] - bv[j];
+                    acc[i][j] = fmaf(df, df, acc[i][j]);
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int64_t r = row0 + ty * 4 + i;
+        if (r >= nx) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t c = col0 + tx * 4 + j;
+            if (c < nc) D[r * ldd + c] = acc[i][j];
+        }
+    }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_select(const float *__restrict__ D, int64_t ldd,
+                                                int64_t nrows, int32_t nc, int32_t ntop,
+                                                int32_t *__restrict__ out_ids, int32_t out_stride,
+                                                float *__restrict__ out_d2) {
+    __shared__ uint64_t wbuf[8][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= nrows) return;
+    WarpTopK<R> tk;
+    tk.init(wbuf[warp], ntop);
+    const float *dr = D + row * ldd;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+        const int c = c0 + lane;
+        const bool ok = c < nc;
+        const float v = ok ? dr[c] : 0.f;
+        tk.push(make_key(v, (uint32_t)c), ok);
+    }
+    tk.finish();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        if (e < ntop) {
+            const uint64_t k = tk.L[r];
+            out_ids[row * out_stride + e] = k == KEY_INF ? -1 : (int32_t)(k & 0xffffffffu);
+            if (out_d2) out_d2[row * out_stride + e] = k == KEY_INF ? INFINITY : o2f((uint32_t)(k >> 32));
+        }
+    }
+}
+
+static void select_rows(const float *D, int64_t ldd, int64_t nrows, int32_t nc, int32_t ntop,
+                        int32_t *out_ids, int32_t out_stride, float *out_d2, cudaStream_t st) {
+    const dim3 grid((unsigned)((nrows + 7) / 8));
+    if (ntop <= 32)
+        k_select<1><<<grid, 256, 0, st>>>(D, ldd, nrows, nc, ntop, out_ids, out_stride, out_d2);
+    else if (ntop <= 64)
+        k_select<2><<<grid, 256, 0, st>>>(D, ldd, nrows, nc, ntop, out_ids, out_stride, out_d2);
+    else if (ntop <= 128)
+        k_select<4><<<grid, 256, 0, st>>>(D, ldd, nrows, nc, ntop, out_ids, out_stride, out_d2);
+    else if (ntop <= 256)
+        k_select<8><<<grid, 256, 0, st>>>(D, ldd, nrows, nc, ntop, out_ids, out_stride, out_d2);
+    else if (ntop <= 512)
+        k_select<16><<<grid, 256, 0, st>>>(D, ldd, nrows, nc, ntop, out_ids, out_stride, out_d2);
+    else
+        FA_REQUIRE(false, FA_ERR_ARG, "top-n of the coarse probe above 512");
+    FA_CHECK_CUDA(cudaGetLastError());
+}
+
+// rows x centroids -> top-ntop columns per row, in blocks of rows so that the
+// distance scratch stays within the workspace's coarse buffer.
+static void l2_topn(const float *X, int64_t nx, int32_t d, const float *C, int32_t nc,
+                    int32_t ntop, float *scratch, int64_t scratch_rows, int32_t *out_ids,
+                    int32_t out_stride, float *out_d2, cudaStream_t st) {
+    for (int64_t r0 = 0; r0 < nx; r0 += scratch_rows) {
+        const int64_t rows = nx - r0 < scratch_rows ? nx - r0 : scratch_rows;
+        const dim3 grid((unsigned)((nc + TILE - 1) / TILE), (unsigned)((rows + TILE - 1) / TILE));
+        k_l2_tile<<<grid, 256, 0, st>>>(X + r0 * d, rows, C, nc, d, scratch, nc);
+        FA_CHECK_CUDA(cudaGetLastError());
+        select_rows(scratch, nc, rows, nc, ntop, out_ids + r0 * out_stride, out_stride,
+                    out_d2 ? out_d2 + r0 * out_stride : nullptr, st);
+    }
+}
+
+void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
+                   int32_t probe_stride, int gemm, Workspace &ws, int32_t *probes,
+                   cudaStream_t st) {
+    (void)gemm;
+    if (nq == 0) return;
+    l2_topn(q, nq, ix.d, ix.centroids, ix.nlist, nprobe, ws.coarse_d, ws.coarse_rows, probes,
+            probe_stride, nullptr, st);
+}
+
+int coarse_launches(const DeviceIndex &ix, int64_t nq, const Workspace &ws) {
+    (void)ix;
+    return nq == 0 ? 0 : (int)(2 * ((nq + ws.coarse_rows - 1) / ws.coarse_rows));
+}
+
+// ---------------------------------------------------------------------------
+// build helpers
+// ---------------------------------------------------------------------------
+__global__ void k_u8_to_f32(const uint8_t *__restrict__ src, float *__restrict__ dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+__global__ void k_encode(const float *__restrict__ X, int64_t n, int32_t d,
+                         const float *__restrict__ cb, int32_t M, uint8_t *__restrict__ codes) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * M) return;
+    const int64_t row = idx / M;
+    const int m = (int)(idx - row * M);
+    const int dsub = d / M;
+    const float *x = X + row * d + m * dsub;
+    float xv[16];
+    for (int j = 0; j < dsub; ++j) xv[j] = x[j];
+    float best = INFINITY;
+    int bc = 0;
+    for (int c = 0; c < 256; ++c) {
+        const float *w = cb + ((int64_t)m * 256 + c) * dsub;
+        float s = 0.f;
+        for (int j = 0; j < dsub; ++j) {
+            const float t = xv[j] - w[j];
+            s = fmaf(t, t, s);
+        }
+        if (s < best) {
+            best = s;
+            bc = c;
+        }
+    }
+    codes[idx] = (uint8_t)bc;
+}
+
+namespace {
+struct DevBuf {
+    void *p = nullptr;
+    explicit DevBuf(size_t bytes) { FA_CHECK_CUDA(cudaMalloc(&p, bytes ? bytes : 1)); }
+    ~DevBuf() { cudaFree(p); }
+    template <class T> T *as() { return reinterpret_cast<T *>(p); }
+};
+}  // namespace
+
+static void rows_to_f32(const void *rows, int64_t r0, int64_t cnt, int32_t d, fa_dtype dt,
+                        float *dst, uint8_t *stage, cudaStream_t st) {
+    if (dt == FA_F32) {
+        FA_CHECK_CUDA(cudaMemcpyAsync(dst, (const float *)rows + r0 * d, sizeof(float) * cnt * d,
+                                      cudaMemcpyHostToDevice, st));
+    } else {
+        FA_CHECK_CUDA(cudaMemcpyAsync(stage, (const uint8_t *)rows + r0 * d, (size_t)cnt * d,
+                                      cudaMemcpyHostToDevice, st));
+        k_u8_to_f32<<<1024, 256, 0, st>>>(stage, dst, cnt * d);
+        FA_CHECK_CUDA(cudaGetLastError());
+    }
+}
+
+void gpu_assign_topr(const void *rows, int64_t n, int32_t d, fa_dtype dt, const float *centroids,
+                     int32_t nlist, int32_t r, int32_t *out_ids, float *out_d2) {
+    cudaStream_t st;
+    FA_CHECK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    const int64_t chunk = 1 << 18;
+    const int64_t srows = std::max<int64_t>(64, std::min<int64_t>(chunk, (256ll << 20) / (4ll * nlist)));
+    DevBuf dc(sizeof(float) * (size_t)nlist * d), dx(sizeof(float) * chunk * d),
+        ds((size_t)chunk * d), dd(sizeof(float) * srows * nlist), di(sizeof(int32_t) * chunk * r),
+        dd2(sizeof(float) * chunk * r);
+    FA_CHECK_CUDA(cudaMemcpyAsync(dc.p, centroids, sizeof(float) * (size_t)nlist * d,
+                                  cudaMemcpyHostToDevice, st));
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t cnt = std::min(chunk, n - r0);
+        rows_to_f32(rows, r0, cnt, d, dt, dx.as<float>(), ds.as<uint8_t>(), st);
+        l2_topn(dx.as<float>(), cnt, d, dc.as<float>(), nlist, r, dd.as<float>(), srows,
+                di.as<int32_t>(), r, dd2.as<float>(), st);
+        FA_CHECK_CUDA(cudaMemcpyAsync(out_ids + r0 * r, di.p, sizeof(int32_t) * cnt * r,
+                                      cudaMemcpyDeviceToHost, st));
+        if (out_d2)
+            FA_CHECK_CUDA(cudaMemcpyAsync(out_d2 + r0 * r, dd2.p, sizeof(float) * cnt * r,
+                                          cudaMemcpyDeviceToHost, st));
+        FA_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    cudaStreamDestroy(st);
+}
+
+void gpu_encode(const void *rows, int64_t n, int32_t d, fa_dtype dt, const float *codebooks,
+                int32_t M, uint8_t *out_codes) {
+    FA_REQUIRE(d / M <= 16, FA_ERR_ARG, "d/M above 16");
+    cudaStream_t st;
+    FA_CHECK_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    const int64_t chunk = 1 << 18;
+    DevBuf dcb(sizeof(float) * (size_t)d * 256), dx(sizeof(float) * chunk * d), ds((size_t)chunk * d),
+        dcode((size_t)chunk * M);
+    FA_CHECK_CUDA(cudaMemcpyAsync(dcb.p, codebooks, sizeof(float) * (size_t)d * 256,
+                                  cudaMemcpyHostToDevice, st));
+    for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+        const int64_t cnt = std::min(chunk, n - r0);
+        rows_to_f32(rows, r0, cnt, d, dt, dx.as<float>(), ds.as<uint8_t>(), st);
+        const int64_t tot = cnt * M;
+        k_encode<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(dx.as<float>(), cnt, d,
+                                                               dcb.as<float>(), M, dcode.as<uint8_t>());
+        FA_CHECK_CUDA(cudaGetLastError());
+        FA_CHECK_CUDA(cudaMemcpyAsync(out_codes + r0 * M, dcode.p, (size_t)cnt * M,
+                                      cudaMemcpyDeviceToHost, st));
+        FA_CHECK_CUDA(cudaStreamSynchronize(st));
+    }
+    cudaStreamDestroy(st);
+}
+
+int num_sms(int device) {
+    static int cached[64] = {0};
+    if (device < 0 || device >= 64) device = 0;
+    if (!cached[device]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0)
+            v = 148;
+        cached[device] = v;
+    }
+    return cached[device];
+}
+
+}  // namespace fa

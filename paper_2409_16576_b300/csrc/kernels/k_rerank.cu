@@ -1,0 +1,256 @@
+// Output stage of the filtering path and the heuristic re-rank (step 8).
+//
+// k_finish   the ADC top-k of each query mapped to the caller's ids and
+//            ordered by (distance, caller id)
+// k_rerank   Algorithm 1 (§4.2): the ADC top-n candidates, in ascending ADC
+//            order, are re-ranked in mini-batches of BatchSize on exact
+//            squared L2 distances over the raw vectors. Q (the max-heap of
+//            the paper) holds the k smallest (distance, id) pairs seen; after
+//            each mini-batch the change rate of Eq. 3,
+//               Delta = |S_n - S_n intersect S_{n-1}| / k,
+//            is compared with eps: Delta <= eps increments a stability
+//            counter, otherwise it is reset, and the loop ends when the
+//            counter reaches beta.
+// One warp handles one query. Each candidate's raw row is read by the whole
+// warp as one coalesced line (a 128-byte request for d = 128 uint8), so rows in
+// pinned host memory cross the host link in full-line reads; the 32 rows of a
+// mini-batch step are issued back to back before any is summed.
+#include "../fa_internal.h"
+#include "warp_topk.cuh"
+
+namespace fa {
+
+template <int R>
+__global__ void __launch_bounds__(256) k_finish(const uint64_t *__restrict__ topkeys, int64_t nq,
+                                                int32_t ntop, int32_t k, const int32_t *kq,
+                                                const int64_t *__restrict__ perm,
+                                                int64_t *__restrict__ out_ids,
+                                                float *__restrict__ out_dist) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t qi = (int64_t)blockIdx.x * 8 + warp;
+    if (qi >= nq) return;
+    int kk = kq ? kq[qi] : k;
+    kk = kk < 1 ? 1 : (kk > k ? k : kk);
+    uint64_t L[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        uint64_t key = KEY_INF;
+        if (e < kk && e < ntop) key = topkeys[qi * ntop + e];
+        if (key != KEY_INF) {
+            const uint32_t internal = (uint32_t)(key & 0xffffffffu);
+            key = (key & 0xffffffff00000000ull) | (uint32_t)perm[internal];
+        }
+        L[r] = key;
+    }
+    bitonic_sort<R>(L);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        if (e < k) {
+            const uint64_t key = (e < kk) ? L[r] : KEY_INF;
+            out_ids[qi * k + e] = key == KEY_INF ? -1 : (int64_t)(key & 0xffffffffu);
+            out_dist[qi * k + e] = key == KEY_INF ? INFINITY : o2f((uint32_t)(key >> 32));
+        }
+    }
+}
+
+void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, int32_t ntop,
+                   int32_t k, const int32_t *kq, int64_t *out_ids, float *out_dist,
+                   cudaStream_t st) {
+    if (nq == 0) return;
+    const dim3 grid((unsigned)((nq + 7) / 8));
+    if (k <= 32)
+        k_finish<1><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
+    else if (k <= 64)
+        k_finish<2><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
+    else if (k <= 128)
+        k_finish<4><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
+    else if (k <= 256)
+        k_finish<8><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
+    else
+        FA_REQUIRE(false, FA_ERR_ARG, "k above 256");
+    FA_CHECK_CUDA(cudaGetLastError());
+}
+
+// Exact squared L2 of the 32 rows ids[0..31] (one per lane, id < 0 = none)
+// against the query in shared memory; lane j returns row j's distance.
+template <typename T>
+__device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d, const float *qs,
+                                            int64_t my_id) {
+    const int lane = threadIdx.x & 31;
+    float p[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) p[j] = 0.f;
+    constexpr int EPW = sizeof(T) == 1 ? 4 : 1;  // elements per 32-bit word
+    const int words = d / EPW;
+    for (int w0 = 0; w0 < words; w0 += 32) {
+        const int w = w0 + lane;
+        const bool wok = w < words;
+        float qv[EPW];
+#pragma unroll
+        for (int e = 0; e < EPW; ++e) qv[e] = wok ? qs[w * EPW + e] : 0.f;
+        uint32_t x[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int64_t id = __shfl_sync(FULL, (long long)my_id, j);
+            x[j] = (id >= 0 && wok)
+                       ? reinterpret_cast<const unsigned int *>(raw + id * (int64_t)d)[w]
+                       : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+            const int64_t id = __shfl_sync(FULL, (long long)my_id, j);
+            if (id < 0 || !wok) continue;
+            if (EPW == 4) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float t = qv[e] - (float)((x[j] >> (8 * e)) & 0xffu);
+                    p[j] = fmaf(t, t, p[j]);
+                }
+            } else {
+                const float t = qv[0] - __uint_as_float(x[j]);
+                p[j] = fmaf(t, t, p[j]);
+            }
+        }
+    }
+    // transpose-reduce: lane l ends with the sum over lanes of p[l]
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < o; ++i) {
+            const bool upper = (lane & o) != 0;
+            const float send = upper ? p[i] : p[i + o];
+            const float keep = upper ? p[i + o] : p[i];
+            p[i] = keep + __shfl_xor_sync(FULL, send, o);
+        }
+    }
+    return p[0];
+}
+
+template <int R, typename T>
+__global__ void __launch_bounds__(256) k_rerank(
+    const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
+    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, int32_t max_changed,
+    const int64_t *__restrict__ perm, const T *__restrict__ raw, int64_t *__restrict__ out_ids,
+    float *__restrict__ out_dist, int32_t *stats) {
+    extern __shared__ float qsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t qi = (int64_t)blockIdx.x * 8 + warp;
+    if (qi >= nq) return;
+    float *qs = qsm + warp * d;
+    for (int j = lane; j < d; j += 32) qs[j] = q[qi * d + j];
+    __syncwarp();
+    int kk = kq ? kq[qi] : k;
+    kk = kk < 1 ? 1 : (kk > k ? k : kk);
+    const uint64_t *tk = topkeys + qi * ntop;
+    // tasks: ADC top-n in ascending order; count the valid ones
+    int valid = 0;
+    for (int e0 = 0; e0 < ntop; e0 += 32) {
+        const int e = e0 + lane;
+        const bool ok = e < ntop && tk[e] != KEY_INF;
+        valid += __popc(__ballot_sync(FULL, ok));
+    }
+    uint64_t Q[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) Q[r] = KEY_INF;
+    int counter = 0, batches = 0;
+    for (int i = 0; i < valid; i += batch) {
+        uint64_t old[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) old[r] = Q[r];
+        const int end = i + batch < valid ? i + batch : valid;
+        for (int s = i; s < end; s += 32) {
+            const int e = s + lane;
+            int64_t uid = -1;
+            if (e < end) uid = perm[(uint32_t)(tk[e] & 0xffffffffu)];
+            const float dist = exact_rows<T>(raw, d, qs, uid);
+            uint64_t key[1] = {uid >= 0 ? make_key(dist, (uint32_t)uid) : KEY_INF};
+            bitonic_sort<1>(key);
+            merge_sorted32<R>(Q, key[0]);
+        }
+        ++batches;
+        // Eq. 3: members of the new top-k that were not in the previous one
+        int changed = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = r * 32 + lane;
+            const uint64_t nk = Q[r];
+            bool fresh = (e < kk) && nk != KEY_INF;
+            const uint32_t nid = (uint32_t)(nk & 0xffffffffu);
+#pragma unroll
+            for (int rr = 0; rr < R; ++rr)
+                for (int j = 0; j < 32; ++j) {
+                    const uint64_t ok = shfl64(old[rr], j);
+                    if (rr * 32 + j < kk && ok != KEY_INF && (uint32_t)(ok & 0xffffffffu) == nid)
+                        fresh = false;
+                }
+            changed += __popc(__ballot_sync(FULL, fresh));
+        }
+        if (changed <= max_changed) {
+            ++counter;
+            if (counter >= beta) break;
+        } else {
+            counter = 0;
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        if (e < k) {
+            const uint64_t key = e < kk ? Q[r] : KEY_INF;
+            out_ids[qi * k + e] = key == KEY_INF ? -1 : (int64_t)(key & 0xffffffffu);
+            out_dist[qi * k + e] = key == KEY_INF ? INFINITY : o2f((uint32_t)(key >> 32));
+        }
+    }
+    if (stats && lane == 0) {
+        stats[qi * 4 + 2] = batches;
+        stats[qi * 4 + 3] = valid;
+    }
+}
+
+template <typename T>
+static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_t *topkeys,
+                            int64_t nq, int32_t ntop, int32_t k, const int32_t *kq, int32_t batch,
+                            int32_t beta, int32_t max_changed, int64_t *out_ids, float *out_dist,
+                            int32_t *stats, cudaStream_t st) {
+    const dim3 grid((unsigned)((nq + 7) / 8));
+    const int smem = 8 * ix.d * 4;
+    const T *raw = reinterpret_cast<const T *>(ix.raw);
+#define FA_RR(RR)                                                                                 \
+    do {                                                                                          \
+        FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T>,                                       \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
+        k_rerank<RR, T><<<grid, 256, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, batch, beta,  \
+                                                 max_changed, ix.perm, raw, out_ids, out_dist,    \
+                                                 stats);                                          \
+    } while (0)
+    if (k <= 32)
+        FA_RR(1);
+    else if (k <= 64)
+        FA_RR(2);
+    else if (k <= 128)
+        FA_RR(4);
+    else
+        FA_REQUIRE(false, FA_ERR_ARG, "re-rank supports k <= 128");
+#undef FA_RR
+    FA_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
+                   int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
+                   int32_t max_changed, int64_t *out_ids, float *out_dist, int32_t *stats,
+                   cudaStream_t st) {
+    if (nq == 0) return;
+    FA_REQUIRE(ix.raw != nullptr, FA_ERR_ARG, "re-rank needs raw vectors in the index");
+    if (ix.raw_dtype == FA_U8) {
+        FA_REQUIRE(ix.d % 4 == 0, FA_ERR_ARG, "uint8 re-rank needs d % 4 == 0");
+        launch_rerank_t<uint8_t>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, max_changed,
+                                 out_ids, out_dist, stats, st);
+    } else {
+        launch_rerank_t<float>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, max_changed,
+                               out_ids, out_dist, stats, st);
+    }
+}
+
+}  // namespace fa

@@ -1,0 +1,173 @@
+// Warp-level selection of the n smallest (distance, id) pairs (step 7 of the
+// filtering path: the GPU "sorts all distances and returns the top-n").
+//
+// A pair is packed into one 64-bit key: the high word is the distance mapped
+// to an unsigned integer that orders like the float, the low word the id. Key
+// order is therefore (distance asc, id asc), which makes every selection
+// deterministic. Selection is a bitonic network held in registers: element e
+// of a warp-wide array of 32*R keys sits in register e / 32 of lane e % 32.
+#pragma once
+#include <stdint.h>
+
+namespace fa {
+
+constexpr uint64_t KEY_INF = ~0ull;
+constexpr uint32_t FULL = 0xffffffffu;
+
+__device__ __forceinline__ uint32_t f2o(float f) {
+    uint32_t u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float o2f(uint32_t o) {
+    uint32_t u = (o & 0x80000000u) ? (o & 0x7fffffffu) : ~o;
+    return __uint_as_float(u);
+}
+
+__device__ __forceinline__ uint64_t make_key(float d, uint32_t id) {
+    return ((uint64_t)f2o(d) << 32) | id;
+}
+
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+    uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    lo = __shfl_xor_sync(FULL, lo, m);
+    hi = __shfl_xor_sync(FULL, hi, m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
+    uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    lo = __shfl_sync(FULL, lo, src);
+    hi = __shfl_sync(FULL, hi, src);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+__device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
+
+// One bitonic stage over 32*R keys: compare element e with e ^ stride,
+// ascending where (e & size) == 0.
+template <int R>
+__device__ __forceinline__ void bitonic_stage(uint64_t (&v)[R], int size, int stride) {
+    const int lane = threadIdx.x & 31;
+    if (stride >= 32) {
+        const int rs = stride >> 5;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if ((r & rs) == 0) {
+                const bool up = (((r << 5) & size) == 0);
+                uint64_t a = v[r], b = v[r | rs];
+                uint64_t lo = umin64(a, b), hi = umax64(a, b);
+                v[r] = up ? lo : hi;
+                v[r | rs] = up ? hi : lo;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = (r << 5) | lane;
+            const bool up = ((e & size) == 0);
+            uint64_t o = shfl_xor64(v[r], stride);
+            const bool lower = (lane & stride) == 0;
+            v[r] = (lower == up) ? umin64(v[r], o) : umax64(v[r], o);
+        }
+    }
+}
+
+// Sorts 32*R keys ascending.
+template <int R>
+__device__ __forceinline__ void bitonic_sort(uint64_t (&v)[R]) {
+#pragma unroll
+    for (int size = 2; size <= 32 * R; size <<= 1)
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) bitonic_stage<R>(v, size, stride);
+}
+
+// Sorts a bitonic sequence of 32*R keys ascending.
+template <int R>
+__device__ __forceinline__ void bitonic_merge(uint64_t (&v)[R]) {
+#pragma unroll
+    for (int stride = 16 * R; stride > 0; stride >>= 1) bitonic_stage<R>(v, 64 * R, stride);
+}
+
+// L (sorted, 32*R keys) <- the 32*R smallest of L and B (sorted, 32*R keys).
+// min(L[i], B[32R-1-i]) is bitonic and holds exactly those keys.
+template <int R>
+__device__ __forceinline__ void merge_sorted(uint64_t (&L)[R], const uint64_t (&B)[R]) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) L[r] = umin64(L[r], shfl_xor64(B[R - 1 - r], 31));
+    bitonic_merge<R>(L);
+}
+
+// L (sorted, 32*R) <- smallest 32*R of L and 32 sorted keys b (one per lane).
+template <int R>
+__device__ __forceinline__ void merge_sorted32(uint64_t (&L)[R], uint64_t b) {
+    L[R - 1] = umin64(L[R - 1], shfl_xor64(b, 31));
+    bitonic_merge<R>(L);
+}
+
+// Element e of a warp-wide array (same value on every lane).
+template <int R>
+__device__ __forceinline__ uint64_t warp_elem(const uint64_t (&v)[R], int e) {
+    uint64_t t = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r)
+        if ((e >> 5) == r) t = v[r];
+    return shfl64(t, e & 31);
+}
+
+// Running top-n of a stream of keys for one warp. The sorted list lives in
+// registers; keys below the current n-th best are appended to a 64-entry
+// shared-memory buffer and merged in blocks of 32.
+template <int R>
+struct WarpTopK {
+    uint64_t L[R];
+    uint64_t thr;   // current n-th smallest key (KEY_INF until n keys are held)
+    uint64_t *buf;  // 64 keys in shared memory, private to the warp
+    int cnt;        // keys in buf (warp-uniform)
+    int n;          // keys wanted, 1 <= n <= 32*R
+
+    __device__ __forceinline__ void init(uint64_t *wbuf, int n_) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) L[r] = KEY_INF;
+        thr = KEY_INF;
+        buf = wbuf;
+        cnt = 0;
+        n = n_;
+    }
+
+    __device__ __forceinline__ void merge32() {
+        const int lane = threadIdx.x & 31;
+        __syncwarp();
+        uint64_t b = lane < cnt ? buf[lane] : KEY_INF;
+        uint64_t bb[1] = {b};
+        bitonic_sort<1>(bb);
+        merge_sorted32<R>(L, bb[0]);
+        thr = warp_elem<R>(L, n - 1);
+        int rem = cnt - 32;
+        uint64_t x = (rem > 0 && lane < rem) ? buf[32 + lane] : 0;
+        __syncwarp();
+        if (rem > 0 && lane < rem) buf[lane] = x;
+        cnt = rem > 0 ? rem : 0;
+        __syncwarp();
+    }
+
+    // Offers one key per lane (pass = false lanes offer nothing).
+    __device__ __forceinline__ void push(uint64_t key, bool valid) {
+        const int lane = threadIdx.x & 31;
+        const bool pass = valid && key < thr;
+        const uint32_t m = __ballot_sync(FULL, pass);
+        if (m) {
+            const int pos = cnt + __popc(m & ((1u << lane) - 1u));
+            if (pass) buf[pos] = key;
+            cnt += __popc(m);
+            if (cnt >= 32) merge32();
+        }
+    }
+
+    __device__ __forceinline__ void finish() {
+        if (cnt > 0) merge32();
+    }
+};
+
+}  // namespace fa

@@ -1,0 +1,407 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars (FP32 form): gather + dedup bit-exact; distances within 1e-4 relative;
+top-k id sets equal except where the oracle's distances at the k boundary are
+closer than that tolerance (several answers are then correct; the test checks
+that the returned ones are valid). Inputs are seeded synthetic data shaped
+like the paper's workloads (Table 1): clustered float32 and uint8 vectors.
+"""
+import threading
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def fa():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2409_16576_b300 as m
+    return m
+
+
+def _oracle_lists(parts):
+    return oracle.lists_from_parts(parts["primary"], parts["rep_off"], parts["rep_ids"],
+                                   parts["nlist"])
+
+
+def _check_topk(gi, gd, oi, od, o_next, k, rtol=RTOL, what=""):
+    """gi/gd: GPU ids/dists of one query; oi/od: oracle's top-k; o_next: the
+    oracle's (k+1)-th distance (inf if none)."""
+    gd = np.asarray(gd, dtype=np.float64)
+    fin = np.isfinite(od)
+    assert np.array_equal(np.isfinite(gd), fin), what
+    np.testing.assert_allclose(gd[fin], od[fin], rtol=rtol, atol=1e-3, err_msg=what)
+    assert np.all(gi[~fin] == -1), what
+    # ids: equal sets unless the boundary is a near tie
+    kth = od[fin][-1] if fin.any() else np.inf
+    if set(gi[fin].tolist()) != set(oi[fin].tolist()):
+        assert np.isfinite(o_next) and abs(o_next - kth) <= rtol * max(kth, 1.0) + 1e-3, what
+        # every id that is not in the oracle's set must sit at the boundary distance
+        extra = set(gi[fin].tolist()) - set(oi[fin].tolist())
+        for t, x in enumerate(gi):
+            if x in extra:
+                assert abs(gd[t] - kth) <= rtol * max(kth, 1.0) + 1e-3, what
+
+
+# ---------------------------------------------------------------------------
+# fixtures
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def f32_small(fa):
+    """100k float32 d=128 vectors, 256 lists, M=16, nprobe 8, k 10 (the plain
+    FP32 workload), 100 queries."""
+    w = synth.plain_f32_100k()
+    base = w.mix.base(w.n)
+    q = w.mix.queries(w.nq)
+    ix = fa.fa_build_index(base, fa.build_params(nlist=w.nlist, M=w.M, kmeans_iters=8,
+                                                 raw_location=fa.FA_RAW_DEVICE))
+    parts = ix.parts()
+    off, ids = _oracle_lists(parts)
+    return dict(w=w, base=base, q=q, ix=ix, parts=parts, off=off, ids=ids)
+
+
+@pytest.fixture(scope="module")
+def u8_repl(fa):
+    """uint8 d=128 vectors with Eq. 2 replication (up to 4 lists per vector),
+    raw vectors in pinned host memory."""
+    mix = synth.Mixture(128, 16, 8.0, kind="u8")
+    base = mix.base(30_000)
+    q = mix.queries(40)
+    ix = fa.fa_build_index(base, fa.build_params(nlist=64, M=32, kmeans_iters=6, repl_eps=0.08,
+                                                 max_lists_per_vec=4,
+                                                 raw_location=fa.FA_RAW_HOST_PINNED))
+    parts = ix.parts()
+    assert parts["rep_off"][-1] > 0, "the build produced no replicas"
+    off, ids = _oracle_lists(parts)
+    return dict(base=base, q=q, ix=ix, parts=parts, off=off, ids=ids)
+
+
+# ---------------------------------------------------------------------------
+# step 2: coarse probe
+# ---------------------------------------------------------------------------
+
+def test_coarse_probe_matches_oracle(fa, f32_small):
+    s = f32_small
+    npb = 8
+    got = fa.fa_debug_probes(s["ix"], s["q"], npb)
+    ref, d2 = oracle.coarse(s["q"], s["parts"]["centroids"], npb + 1, with_d2=True)
+    for i in range(s["q"].shape[0]):
+        if got[i].tolist() != ref[i, :npb].tolist():
+            # only a near tie at the boundary may reorder the probe set
+            assert abs(d2[i, npb] - d2[i, npb - 1]) <= 1e-5 * d2[i, npb - 1], i
+            assert set(got[i].tolist()) - set(ref[i, :npb + 1].tolist()) == set(), i
+
+
+# ---------------------------------------------------------------------------
+# step 1: LUT
+# ---------------------------------------------------------------------------
+
+def test_lut_f32_matches_oracle(fa, f32_small):
+    s = f32_small
+    for i in range(5):
+        got = fa.fa_debug_lut(s["ix"], s["q"][i])
+        ref = oracle.lut(s["q"][i], s["parts"]["codebooks"])
+        np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-2)
+
+
+@pytest.mark.parametrize("prec,rel", [("F16", 2.0 ** -11), ("FP8", 2.0 ** -4)])
+def test_lut_lowp_error_bound(fa, u8_repl, prec, rel):
+    """FP16 / FP8 table: each entry is within half a unit in the last place of
+    its stored residual (times the per-query scale) of the FP64 value."""
+    s = u8_repl
+    p = fa.search_params(lut_prec=getattr(fa, "FA_LUT_" + prec))
+    for i in range(4):
+        got = fa.fa_debug_lut(s["ix"], s["q"][i], p).astype(np.float64)
+        ref = oracle.lut(s["q"][i], s["parts"]["codebooks"])
+        resid = ref - ref.min(axis=1, keepdims=True)
+        # half-ulp of the stored value (relative), an FP32 rounding margin, and
+        # the FP8 subnormal step (2^-9 of the scale) for tiny residuals
+        scale = resid.max() / (65504.0 if prec == "F16" else 448.0)
+        bound = resid * rel + 1e-5 * np.abs(ref) + scale * (2.0 ** -9 if prec == "FP8" else 2.0 ** -24) + 1e-3
+        assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) - bound)
+
+
+# ---------------------------------------------------------------------------
+# steps 3-5: gather + dedup (bit-exact)
+# ---------------------------------------------------------------------------
+
+def test_candidates_bit_exact_with_replication(fa, u8_repl):
+    s = u8_repl
+    nl = s["parts"]["nlist"]
+    rng = np.random.default_rng(5)
+    for t in range(30):
+        npb = int(rng.integers(1, 24))
+        probes = rng.choice(nl, size=npb, replace=False).astype(np.int32)
+        got = fa.fa_debug_candidates(s["ix"], probes=probes)
+        ref, gathered = oracle.candidates(probes, s["off"], s["ids"])
+        assert got.dtype == np.int64
+        assert got.tolist() == ref.astype(np.int64).tolist(), t
+    # every list probed: each vector exactly once
+    got = fa.fa_debug_candidates(s["ix"], probes=np.arange(nl, dtype=np.int32))
+    assert got.tolist() == list(range(s["parts"]["n"]))
+
+
+def test_candidate_counts_in_stats(fa, u8_repl):
+    s = u8_repl
+    nl = s["parts"]["nlist"]
+    probes = np.tile(np.arange(12, dtype=np.int32), (3, 1))
+    _, _, st = fa.fa_search_ex(s["ix"], s["q"][:3], 10, 12, probes=probes, stats=True)
+    ref, gathered = oracle.candidates(probes[0], s["off"], s["ids"])
+    assert np.all(st[:, 0] == gathered) and np.all(st[:, 1] == ref.shape[0])
+    _, _, st = fa.fa_search_ex(s["ix"], s["q"][:1], 10, nl, probes=np.arange(nl)[None], stats=True)
+    assert st[0, 1] == s["parts"]["n"] and st[0, 0] == s["off"][-1]
+
+
+# ---------------------------------------------------------------------------
+# steps 6-7: ADC + top-k through fa_search_ex
+# ---------------------------------------------------------------------------
+
+def _search_vs_oracle(fa, s, k, npb, params=None, nq=None, rerank=0):
+    q = s["q"][:nq] if nq else s["q"]
+    probes = oracle.coarse(q, s["parts"]["centroids"], npb)
+    gi, gd = fa.fa_search_ex(s["ix"], q, k, npb, params, probes=probes)
+    kk = rerank if rerank else k + 1
+    oi, od = oracle.search(q, s["parts"]["centroids"], s["parts"]["codebooks"], s["parts"]["codes"],
+                           s["off"], s["ids"], npb, kk, probes=probes)
+    return gi, gd, oi, od
+
+
+@pytest.mark.parametrize("k", [1, 10, 100])
+def test_search_given_probes_matches_oracle(fa, f32_small, k):
+    s = f32_small
+    gi, gd, oi, od = _search_vs_oracle(fa, s, k, 8)
+    for i in range(gi.shape[0]):
+        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
+        # rows ascending by (distance, id)
+        fin = np.isfinite(gd[i])
+        keys = list(zip(gd[i][fin].tolist(), gi[i][fin].tolist()))
+        assert keys == sorted(keys)
+
+
+def test_search_with_replication_matches_oracle(fa, u8_repl):
+    gi, gd, oi, od = _search_vs_oracle(fa, u8_repl, 10, 16)
+    for i in range(gi.shape[0]):
+        _check_topk(gi[i], gd[i], oi[i, :10], od[i, :10], od[i, 10], 10, what=str(i))
+        assert len(set(gi[i].tolist())) == 10  # no duplicate ids
+
+
+def test_end_to_end_recall_matches_oracle(fa, f32_small):
+    """Whole path (coarse probe included) on the plain FP32 workload: recall@10
+    against brute force within 0.005 of the oracle's."""
+    s = f32_small
+    w = s["w"]
+    gi, gd = fa.fa_search(s["ix"], s["q"], w.k, w.nprobe)
+    oi, od = oracle.search(s["q"], s["parts"]["centroids"], s["parts"]["codebooks"],
+                           s["parts"]["codes"], s["off"], s["ids"], w.nprobe, w.k)
+    ti, td = oracle.knn(s["q"], s["base"], w.k)
+    r_gpu = oracle.recall_at(gi, ti, td, at=w.k)
+    r_ora = oracle.recall_at(oi, ti, td, at=w.k)
+    assert abs(r_gpu - r_ora) <= 0.005, (r_gpu, r_ora)
+
+
+def test_persistent_and_device_buffers_match(fa, f32_small):
+    import torch
+    s = f32_small
+    gi, gd = fa.fa_search(s["ix"], s["q"], 10, 8)
+    pi, pd = fa.fa_search_ex(s["ix"], s["q"], 10, 8, fa.search_params(flags=fa.FA_PERSISTENT))
+    assert np.array_equal(gi, pi) and np.array_equal(gd, pd)
+    qd = torch.as_tensor(s["q"], device="cuda")
+    di, dd = fa.fa_search_ex(s["ix"], qd, 10, 8)
+    torch.cuda.synchronize()
+    assert np.array_equal(gi, di.cpu().numpy()) and np.array_equal(gd, dd.cpu().numpy())
+
+
+def test_per_query_k_and_nprobe(fa, f32_small):
+    s = f32_small
+    q = s["q"][:20]
+    rng = np.random.default_rng(9)
+    kq = rng.integers(1, 11, size=20).astype(np.int32)
+    npq = rng.integers(1, 9, size=20).astype(np.int32)
+    gi, gd = fa.fa_search_ex(s["ix"], q, 10, 8, k_per_query=kq, nprobe_per_query=npq)
+    probes = oracle.coarse(q, s["parts"]["centroids"], 8)
+    for i in range(20):
+        oi, od = oracle.search(q[i:i + 1], s["parts"]["centroids"], s["parts"]["codebooks"],
+                               s["parts"]["codes"], s["off"], s["ids"], int(npq[i]), int(kq[i]) + 1,
+                               probes=probes[i:i + 1, :npq[i]])
+        gprobe = fa.fa_debug_probes(s["ix"], q[i:i + 1], 8)[0]
+        if gprobe[:npq[i]].tolist() != probes[i, :npq[i]].tolist():
+            continue  # a near tie in the probe order changes the scanned lists
+        _check_topk(gi[i, :kq[i]], gd[i, :kq[i]], oi[0, :kq[i]], od[0, :kq[i]], od[0, kq[i]], kq[i])
+        assert np.all(gi[i, kq[i]:] == -1) and np.all(np.isinf(gd[i, kq[i]:]))
+
+
+# ---------------------------------------------------------------------------
+# invariants and edge cases on hand-made indexes
+# ---------------------------------------------------------------------------
+
+def _identity_parts(rng, n, d, M, nlist, rep_frac):
+    x = (rng.normal(size=(n, d)) * 6).astype(np.float32)
+    dsub = d // M
+    cb = np.zeros((M, 256, dsub), np.float32)
+    for m in range(M):
+        cb[m, :n] = x[:, m * dsub:(m + 1) * dsub]
+    codes = np.repeat(np.arange(n, dtype=np.uint8)[:, None], M, axis=1)
+    primary = rng.integers(0, nlist, size=n).astype(np.int32)
+    primary[:nlist // 4] = 0  # leave some lists empty
+    rep = [[] for _ in range(nlist)]
+    for v in np.nonzero(rng.random(n) < rep_frac)[0]:
+        for l in rng.choice(nlist, size=3, replace=False):
+            if l != primary[v]:
+                rep[l].append(int(v))
+    rep_off = np.zeros(nlist + 1, np.int64)
+    rep_off[1:] = np.cumsum([len(a) for a in rep])
+    rep_ids = np.array([v for a in rep for v in a], np.int64)
+    cent = rng.normal(size=(nlist, d)).astype(np.float32)
+    return x, cent, cb, codes, primary, rep_off, rep_ids
+
+
+@pytest.mark.parametrize("M", [8, 16, 32, 48, 64])
+def test_identity_codebook_full_probe_equals_knn(fa, M):
+    """Every vector is its own PQ centroid and every list is probed: the GPU's
+    IVF-PQ top-k is exact k-NN (pins gather, dedup, LUT, ADC, top-k)."""
+    rng = np.random.default_rng(100 + M)
+    d = 2 * M if M != 64 else 128
+    x, cent, cb, codes, primary, ro, ri = _identity_parts(rng, 250, d, M, 16, 0.3)
+    ix = fa.fa_index_from_parts(cent, cb, codes, primary, ro, ri)
+    q = (rng.normal(size=(12, d)) * 6).astype(np.float32)
+    gi, gd = fa.fa_search(ix, q, 10, 16)
+    ti, td = oracle.knn(q, x, 11)
+    for i in range(q.shape[0]):
+        _check_topk(gi[i], gd[i], ti[i, :10], td[i, :10], td[i, 10], 10, what="M%d q%d" % (M, i))
+
+
+def test_fewer_candidates_than_k_and_empty_lists(fa):
+    rng = np.random.default_rng(3)
+    x, cent, cb, codes, primary, ro, ri = _identity_parts(rng, 40, 32, 16, 8, 0.0)
+    ix = fa.fa_index_from_parts(cent, cb, codes, primary, ro, ri)
+    counts = np.bincount(primary, minlength=8)
+    empty = int(np.argmin(counts))
+    assert counts[empty] == 0
+    small = int(np.argmin(np.where(counts > 0, counts, 10 ** 9)))
+    q = x[:3]
+    probes = np.array([[empty, small]] * 3, np.int32)
+    k = int(counts[small]) + 5
+    gi, gd = fa.fa_search_ex(ix, q, k, 2, probes=probes)
+    members = sorted(np.nonzero(primary == small)[0].tolist())
+    for i in range(3):
+        assert sorted(gi[i, :counts[small]].tolist()) == members
+        assert np.all(gi[i, counts[small]:] == -1) and np.all(np.isinf(gd[i, counts[small]:]))
+    # only empty lists probed: every row is padding
+    gi, gd = fa.fa_search_ex(ix, q, 4, 1, probes=np.full((3, 1), empty, np.int32))
+    assert np.all(gi == -1) and np.all(np.isinf(gd))
+
+
+def test_argument_errors_and_empty_batch(fa, f32_small):
+    s = f32_small
+    gi, gd = fa.fa_search(s["ix"], s["q"][:0], 10, 8)
+    assert gi.shape == (0, 10)
+    with pytest.raises(fa.FaError) as e:
+        fa.fa_search(s["ix"], s["q"][:, :64], 10, 8)
+    assert e.value.status == fa.FA_ERR_ARG
+    with pytest.raises(fa.FaError) as e:
+        fa.fa_search(s["ix"], s["q"], 0, 8)
+    assert e.value.status == fa.FA_ERR_ARG
+    # nprobe above nlist is clamped, not an error
+    gi, gd = fa.fa_search(s["ix"], s["q"][:2], 5, 100000)
+    assert gi.shape == (2, 5)
+    bad = np.full((2, 8), 99999, np.int32)
+    with pytest.raises(fa.FaError) as e:
+        fa.fa_search_ex(s["ix"], s["q"][:2], 5, 8, probes=bad)
+    assert e.value.status == fa.FA_ERR_ARG
+    # the index stays usable after argument errors
+    gi2, _ = fa.fa_search(s["ix"], s["q"][:2], 5, 8)
+    assert gi2.shape == (2, 5)
+
+
+# ---------------------------------------------------------------------------
+# step 8: Algorithm 1 on the GPU
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("eps,beta,batch", [(0.0, 2, 32), (-1.0, 1, 32), (1.0, 1, 32),
+                                            (0.1, 1, 16), (0.0, 3, 8)])
+def test_rerank_matches_oracle(fa, u8_repl, eps, beta, batch):
+    s = u8_repl
+    k, npb, n = 10, 16, 100
+    q = s["q"][:24]
+    probes = oracle.coarse(q, s["parts"]["centroids"], npb)
+    p = fa.search_params(rerank_n=n, rerank_batch=batch, rerank_beta=beta, rerank_eps=eps)
+    gi, gd, st = fa.fa_search_ex(s["ix"], q, k, npb, p, probes=probes, stats=True)
+    oi, od, ost = oracle.search(q, s["parts"]["centroids"], s["parts"]["codebooks"],
+                                s["parts"]["codes"], s["off"], s["ids"], npb, k, raw=s["parts"]["raw"],
+                                probes=probes, rerank_n=n, batch=batch, eps=eps, beta=beta, stats=True)
+    # re-rank inputs (the ADC top-n) may differ at an ADC near tie; compare
+    # where the GPU's ADC top-n equals the oracle's
+    an_i, an_d = fa.fa_search_ex(s["ix"], q, n, npb, probes=probes)
+    ao_i, ao_d = oracle.search(q, s["parts"]["centroids"], s["parts"]["codebooks"],
+                               s["parts"]["codes"], s["off"], s["ids"], npb, n, probes=probes)
+    compared = 0
+    for i in range(q.shape[0]):
+        if an_i[i].tolist() != ao_i[i].tolist():
+            continue
+        compared += 1
+        # uint8 data and integral queries: exact distances are integers in FP32
+        assert gd[i].tolist() == od[i].astype(np.float32).tolist(), i
+        assert gi[i].tolist() == oi[i].tolist(), i
+        assert st[i, 2] == ost[i, 2], (i, st[i], ost[i])
+    assert compared >= q.shape[0] // 2
+
+
+def test_rerank_device_raw_equals_pinned(fa, f32_small):
+    s = f32_small
+    q = s["q"][:30]
+    p = fa.search_params(rerank_n=64, rerank_eps=-1.0)
+    gi, gd = fa.fa_search_ex(s["ix"], q, 10, 8, p)
+    # never stopping early: the result is the exact top-k of the ADC top-64
+    ai, ad = fa.fa_search_ex(s["ix"], q, 64, 8)
+    for i in range(q.shape[0]):
+        cand = ai[i][ai[i] >= 0]
+        ex = cdist(q[i:i + 1].astype(np.float64), s["base"][cand].astype(np.float64), "sqeuclidean")[0]
+        order = np.lexsort((cand, ex))[:10]
+        np.testing.assert_allclose(gd[i], ex[order], rtol=1e-5)
+        assert set(gi[i].tolist()) == set(cand[order].tolist()) or \
+            abs(ex[order][-1] - np.sort(ex)[min(10, len(ex) - 1)]) <= 1e-4 * ex[order][-1]
+
+
+# ---------------------------------------------------------------------------
+# lifecycle: save / load, concurrent callers
+# ---------------------------------------------------------------------------
+
+def test_save_load_roundtrip(fa, u8_repl, tmp_path):
+    s = u8_repl
+    path = str(tmp_path / "ix.fa")
+    fa.fa_save_index(s["ix"], path)
+    ix2 = fa.fa_load_index(path)
+    a = fa.fa_search(s["ix"], s["q"], 10, 8)
+    b = fa.fa_search(ix2, s["q"], 10, 8)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    p2 = ix2.parts()
+    assert np.array_equal(p2["codes"], s["parts"]["codes"])
+    assert np.array_equal(p2["raw"], s["parts"]["raw"])
+
+
+def test_concurrent_callers_get_their_own_results(fa, f32_small):
+    s = f32_small
+    ref = [fa.fa_search(s["ix"], s["q"][i * 10:(i + 1) * 10], 10, 8) for i in range(8)]
+    out = [None] * 8
+
+    def run(i):
+        out[i] = fa.fa_search(s["ix"], s["q"][i * 10:(i + 1) * 10], 10, 8)
+
+    ts = [threading.Thread(target=run, args=(i,)) for i in range(8)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for i in range(8):
+        assert np.array_equal(out[i][0], ref[i][0]) and np.array_equal(out[i][1], ref[i][1])
