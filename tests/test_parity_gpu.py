@@ -252,8 +252,8 @@ def _identity_parts(rng, n, d, M, nlist, rep_frac):
     for m in range(M):
         cb[m, :n] = x[:, m * dsub:(m + 1) * dsub]
     codes = np.repeat(np.arange(n, dtype=np.uint8)[:, None], M, axis=1)
-    primary = rng.integers(0, nlist, size=n).astype(np.int32)
-    primary[:nlist // 4] = 0  # leave some lists empty
+    # the last quarter of the lists gets no primary members
+    primary = rng.integers(0, nlist - nlist // 4, size=n).astype(np.int32)
     rep = [[] for _ in range(nlist)]
     for v in np.nonzero(rng.random(n) < rep_frac)[0]:
         for l in rng.choice(nlist, size=3, replace=False):
