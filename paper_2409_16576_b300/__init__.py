@@ -5,7 +5,7 @@ Argument marshalling only: every step of the search runs in the library's
 CUDA kernels. The functions carry the C names; numpy arrays are passed as host
 buffers and CUDA torch tensors as device buffers (the matching FA_* flags are
 set and torch's current stream is used). Importing fails loudly when
-``libfa.so`` has not been built (``python -m paper_2409_16576_b300._build``).
+``libfa.so`` has not been built (``python paper_2409_16576_b300/_build.py``).
 """
 from __future__ import annotations
 
@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libfa.so")
 
 if not os.path.exists(LIB_PATH):
-    raise ImportError("libfa.so is missing: build it with `python -m paper_2409_16576_b300._build`")
+    raise ImportError("libfa.so is missing: build it with `python paper_2409_16576_b300/_build.py`")
 
 _lib = C.CDLL(LIB_PATH)
 

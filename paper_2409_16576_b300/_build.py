@@ -1,7 +1,8 @@
 """Compiles libfa.so (the C-ABI library) in-tree for sm_103a with nvcc.
 
 Every translation unit is compiled separately (in parallel) into _build/ and
-linked with ``nvcc -shared``. Run ``python -m paper_2409_16576_b300._build``.
+linked with ``nvcc -shared``. Run it as a file, ``python paper_2409_16576_b300/_build.py``
+(importing the package needs the library it builds).
 """
 from __future__ import annotations
 
