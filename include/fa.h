@@ -230,6 +230,38 @@ fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params 
                        float *out_lut);
 
 /* ------------------------------------------------------------------------- */
+/* Coarse probe without allocation                                           */
+/* ------------------------------------------------------------------------- */
+
+/* The coarse probe (step 2) for callers that cannot allocate device memory
+ * (the paper has no counterpart; it is an addition of this library). Such
+ * callers are processes whose device memory is owned in full by another
+ * allocator or a fixed budget, and latency-bound code that cannot afford the
+ * synchronisation and unbounded time of a cudaMalloc in the middle of its work.
+ *
+ * queries[nq][d] and centroids[nlist][d] are float32 device pointers;
+ * probes[nq][nprobe] (int32, device) receives each query's nprobe nearest
+ * centroids by squared L2, ascending by (distance, centroid index), computed
+ * by the same kernels as the coarse probe of fa_search. The work is enqueued
+ * on `stream` (a cudaStream_t, NULL = legacy default stream); results are
+ * ready when the stream is.
+ *
+ * Scratch: a 16 MiB array in this library's device image (4194304 float
+ * distances), held by every GPU that loads the library until the process
+ * exits. No cudaMalloc, cudaFree or allocating library routine is called. The
+ * first call on each device looks the array's device address up (once, with
+ * that device current); make that first call before any stream capture.
+ * Every call shares the array and overwrites what it reads, so calls that
+ * overlap on the GPU race: serialise them.
+ *
+ * Errors: FA_ERR_ARG for nq < 0, d < 1, nprobe outside 1..min(nlist, 512),
+ * null buffers, or nlist above 4194304 (the scratch capacity); FA_ERR_CUDA if
+ * a launch fails. nq == 0 returns FA_OK without touching the GPU. */
+fa_status fa_coarse_probe_noalloc(const float *queries, int64_t nq, int32_t d,
+                                  const float *centroids, int32_t nlist, int32_t nprobe,
+                                  int32_t *probes, void *stream);
+
+/* ------------------------------------------------------------------------- */
 /* Errors and version                                                        */
 /* ------------------------------------------------------------------------- */
 

@@ -87,6 +87,7 @@ _sig("fa_search_ex", i32, P, P, i64, i32, i32, i32, P, P, P)
 _sig("fa_debug_probes", i32, P, P, i64, i32, P, P)
 _sig("fa_debug_candidates", i32, P, P, i32, P, P, i64, P)
 _sig("fa_debug_lut", i32, P, P, P, P)
+_sig("fa_coarse_probe_noalloc", i32, P, i64, i32, P, i32, i32, P, P)
 _sig("fa_last_error", C.c_char_p)
 _sig("fa_status_str", C.c_char_p, i32)
 _sig("fa_version", C.c_char_p)
@@ -95,7 +96,8 @@ _sig("fa_version", C.c_char_p)
 EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_index_from_parts", "fa_index_get_parts",
            "fa_index_info_get", "fa_save_index", "fa_load_index", "fa_free_index",
            "fa_search_params_init", "fa_search", "fa_search_ex", "fa_debug_probes",
-           "fa_debug_candidates", "fa_debug_lut", "fa_last_error", "fa_status_str", "fa_version")
+           "fa_debug_candidates", "fa_debug_lut", "fa_coarse_probe_noalloc", "fa_last_error",
+           "fa_status_str", "fa_version")
 
 
 class FaError(RuntimeError):
@@ -327,6 +329,25 @@ def fa_debug_lut(ix: Index, query, params=None) -> np.ndarray:
     out = np.empty((M, 256), dtype=np.float32)
     _check(_lib.fa_debug_lut(ix.handle, _ptr(q), C.byref(params) if params is not None else None,
                              _ptr(out)))
+    return out
+
+
+def fa_coarse_probe_noalloc(queries, centroids, nprobe: int, out=None, stream=None, nlist=None):
+    """Coarse probe that allocates nothing inside the library, for callers
+    that cannot allocate device memory. CUDA torch tensors queries [nq][d] and
+    centroids [nlist][d] (float32); output int32 [nq][nprobe] in ``out`` (a
+    caller that cannot allocate passes its own; None lets torch allocate one
+    here). Runs on ``stream`` (default: torch's current stream). ``nlist``
+    overrides the row count passed to the C call (used to test its checks)."""
+    import torch
+    nq, d = queries.shape
+    nl = centroids.shape[0] if nlist is None else nlist
+    if out is None:
+        out = torch.empty((nq, nprobe), dtype=torch.int32, device=queries.device)
+    if stream is None:
+        stream = torch.cuda.current_stream(queries.device).cuda_stream
+    _check(_lib.fa_coarse_probe_noalloc(_ptr(queries), nq, d, _ptr(centroids), nl, nprobe,
+                                        _ptr(out), stream))
     return out
 
 

@@ -9,6 +9,8 @@
 // every base vector for Eq. 2, k-means assignment). k_encode picks the PQ
 // code of every subspace (nearest of the 256 sub-centroids).
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "../fa_internal.h"
 #include "warp_topk.cuh"
@@ -269,4 +271,70 @@ int num_sms(int device) {
     return cached[device];
 }
 
+// ---------------------------------------------------------------------------
+// Coarse probe that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: processes whose device memory is owned
+// in full by another allocator (a framework's caching pool, a fixed memory
+// budget carved up at start-up), and latency-bound callers that cannot afford
+// the device-wide synchronisation and unbounded time an allocation may take in
+// the middle of their work. For them the distance block of the coarse probe
+// lives in the file-scope array below, which every GPU that loads this library
+// keeps for the life of the process (16 MiB). The caller still passes the
+// queries, the centroids and the output.
+//
+// The array is shared by every call and keeps the last call's contents; each
+// call overwrites every element it later reads, so nothing has to start at
+// zero. Calls that overlap on the GPU (two streams, or two host threads) race
+// on the array and may return wrong probe lists: serialise them.
+// ---------------------------------------------------------------------------
+constexpr int64_t NOALLOC_SCRATCH_FLOATS = 4ll << 20;
+static __device__ __align__(256) float g_noalloc_scratch[NOALLOC_SCRATCH_FLOATS];
+
+// Device address of the array on the current device, looked up once per device
+// with that device current (in host code the symbol is only a stand-in).
+static float *noalloc_scratch() {
+    static std::mutex mu;
+    static float *addr[64] = {nullptr};
+    int dev = 0;
+    FA_CHECK_CUDA(cudaGetDevice(&dev));
+    FA_REQUIRE(dev >= 0 && dev < 64, FA_ERR_NODEV, "device ordinal above 63");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!addr[dev]) {
+        float *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_noalloc_scratch);
+        if (e != cudaSuccess)
+            throw Error{FA_ERR_CUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch: ") +
+                                         cudaGetErrorString(e)};
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+
 }  // namespace fa
+
+extern "C" fa_status fa_coarse_probe_noalloc(const float *queries, int64_t nq, int32_t d,
+                                             const float *centroids, int32_t nlist, int32_t nprobe,
+                                             int32_t *probes, void *stream) {
+    using namespace fa;
+    try {
+        FA_REQUIRE(nq >= 0 && d >= 1 && nlist >= 1, FA_ERR_ARG, "bad shape");
+        FA_REQUIRE(nprobe >= 1 && nprobe <= 512 && nprobe <= nlist, FA_ERR_ARG,
+                   "nprobe must be in 1..min(nlist, 512)");
+        FA_REQUIRE((int64_t)nlist <= NOALLOC_SCRATCH_FLOATS, FA_ERR_ARG,
+                   "nlist above the no-alloc scratch capacity of 4194304 distances");
+        if (nq == 0) return FA_OK;
+        FA_REQUIRE(queries && centroids && probes, FA_ERR_ARG, "null buffer");
+        float *scratch = noalloc_scratch();
+        const int64_t rows = NOALLOC_SCRATCH_FLOATS / nlist;  // query rows per block
+        l2_topn(queries, nq, d, centroids, nlist, nprobe, scratch, rows, probes, nprobe, nullptr,
+                (cudaStream_t)stream);
+        return FA_OK;
+    } catch (const Error &e) {
+        set_error("%s", e.msg.c_str());
+        return e.st;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return FA_ERR_CUDA;
+    }
+}
