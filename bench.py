@@ -3,8 +3,12 @@
 Workload (default): 10M uint8 d=128 vectors from a 64-component Gaussian
 mixture clipped to 0..255 (SIFT-like, the paper's Table 1 shape), 16384 lists,
 PQ M=32 x 256, 10k queries, nprobe 64, k 10, the precision form (FP16 LUT with
-a per-query scale, exact FP32 re-rank of the ADC top 100 in mini-batches of
-32, Algorithm 1) with raw vectors in pinned host memory.
+a per-query scale, exact FP32 re-rank of the ADC top 10k = 100 in mini-batches
+of 32 with Algorithm 1, raw vectors in pinned host memory). recall@10 is
+measured on a 1k-query subsample in every run and reported beside the QPS;
+``--sweep`` prints the recall/QPS curve over nprobe, n and Algorithm 1's
+parameters (on this isotropic mixture recall@10 stays far below 0.9 at these
+PQ settings, see the design notes).
 
 A step is one batch of 10k queries through the whole path: coarse probe, LUT,
 gather + dedup, ADC scan + top-n, re-rank. ``value`` is queries per second
@@ -49,9 +53,17 @@ def parse():
     ap.add_argument("--n", type=int, default=10_000_000)
     ap.add_argument("--nq", type=int, default=10_000)
     ap.add_argument("--nprobe", type=int, default=64)
+    ap.add_argument("--rerank-n", type=int, default=100, help="re-rank the ADC top-n (10 k)")
+    ap.add_argument("--batch", type=int, default=32, help="Algorithm 1 BatchSize")
+    ap.add_argument("--eps", type=float, default=0.0, help="Algorithm 1 epsilon")
+    ap.add_argument("--beta", type=int, default=2, help="Algorithm 1 beta")
+    ap.add_argument("--raw", default="host", choices=["device", "host"],
+                    help="raw vectors for the re-rank: HBM or pinned host memory")
+    ap.add_argument("--persistent", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=0, help="queries in the CPU baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recall", type=int, default=1000, help="queries in the recall subsample (0 = off)")
+    ap.add_argument("--sweep", action="store_true", help="recall/QPS grid instead of one bench line")
     return ap.parse_args()
 
 
@@ -59,7 +71,8 @@ def workload(args):
     w = synth.sift_like_10m()
     return dict(name=w.name if args.n == w.n else "ivfpq-u8-%d-d128-nlist16384-M32" % args.n,
                 mix=w.mix, n=args.n, nq=args.nq, nlist=w.nlist, M=w.M, nprobe=args.nprobe, k=w.k,
-                rerank_n=100 if args.form == "lowp" else 0)
+                rerank_n=args.rerank_n if args.form == "lowp" else 0, batch=args.batch,
+                eps=args.eps, beta=args.beta)
 
 
 def dist_env():
@@ -173,8 +186,8 @@ def run_oracle_sample(wl, base, queries, parts, nsample):
     q = queries[:nsample]
     t0 = time.perf_counter()
     oi, od = oracle.search(q, parts["centroids"], parts["codebooks"], parts["codes"], off, ids,
-                           wl["nprobe"], wl["k"], raw=base, rerank_n=wl["rerank_n"], batch=32,
-                           eps=0.0, beta=2)
+                           wl["nprobe"], wl["k"], raw=base, rerank_n=wl["rerank_n"],
+                           batch=wl["batch"], eps=wl["eps"], beta=wl["beta"])
     return time.perf_counter() - t0, cores, oi
 
 
@@ -207,6 +220,46 @@ def exact_dists(base, q, ids):
     return out
 
 
+def search_params(fa, form, wl, persistent=False):
+    lowp = form == "lowp"
+    return fa.search_params(lut_prec=fa.FA_LUT_F16 if lowp else fa.FA_LUT_F32,
+                            rerank_n=wl["rerank_n"] if lowp else 0, rerank_batch=wl["batch"],
+                            rerank_beta=wl["beta"], rerank_eps=wl["eps"],
+                            flags=fa.FA_PERSISTENT if persistent else 0)
+
+
+def timed_steps(fa, torch, ix, qd, k, nprobe, sp, steps, warmup, flush, oid, odist):
+    """Per-step CUDA events on the launching stream, L2 flushed between steps
+    outside the events; returns (step ms list, traces)."""
+    stream = torch.cuda.current_stream()
+
+    def step(trace=None):
+        fa.fa_search_ex(ix, qd, k, nprobe, sp, out_ids=oid, out_dist=odist,
+                        stream=stream.cuda_stream, trace=trace)
+
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    traces = []
+    for i in range(steps):
+        flush.zero_()
+        tr = fa.fa_search_trace()
+        ev[i][0].record(stream)
+        step(tr)
+        ev[i][1].record(stream)
+        traces.append(tr)
+    torch.cuda.synchronize()
+    return [x.elapsed_time(y) for x, y in ev], traces
+
+
+def recall_of(oracle, base, queries, found, gt):
+    ns = gt[0].shape[0]
+    ex = exact_dists(base, queries[:ns], found[:ns])
+    return oracle.recall_at(found[:ns], gt[0], gt[1], exact_found_dist=ex, at=10)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -216,6 +269,7 @@ def main():
         return reference_arm(args, wl, rank, world)
 
     import torch
+    import oracle
     import paper_2409_16576_b300 as fa
     torch.cuda.set_device(local)
     if world > 1:
@@ -227,57 +281,42 @@ def main():
     base = wl["mix"].base(wl["n"])
     queries = wl["mix"].queries(wl["nq"])
     t_gen = time.perf_counter() - t0
-    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=8,
-                         raw_location=fa.FA_RAW_HOST_PINNED if wl["rerank_n"] else fa.FA_RAW_NONE)
+    raw_loc = fa.FA_RAW_DEVICE if args.raw == "device" else fa.FA_RAW_HOST_PINNED
+    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=10, raw_location=raw_loc)
     t0 = time.perf_counter()
     ix = fa.fa_build_index(base, bp)
     t_build = time.perf_counter() - t0
     info = ix.info()
 
-    lowp = args.form == "lowp"
-    sp = fa.search_params(lut_prec=fa.FA_LUT_F16 if lowp else fa.FA_LUT_F32,
-                          rerank_n=wl["rerank_n"], rerank_batch=32, rerank_beta=2, rerank_eps=0.0)
     k, nq, d = wl["k"], wl["nq"], 128
-    stream = torch.cuda.current_stream()
     qd = torch.as_tensor(queries, device="cuda")
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    gt = ground_truth(base, queries[:min(args.recall, nq)], 10) if args.recall > 0 else None
+
+    if args.sweep:
+        return sweep(args, wl, fa, torch, oracle, ix, base, queries, qd, flush, gt, t_build)
+
+    lowp = args.form == "lowp"
+    sp = search_params(fa, args.form, wl, args.persistent)
     oid = torch.empty((nq, k), dtype=torch.int64, device="cuda")
     odist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     # candidate counts (algorithmic bytes of the scan)
     _, _, st = fa.fa_search_ex(ix, queries, k, wl["nprobe"], sp, stats=True)
     uniq = int(st[:, 1].sum())
     gathered = int(st[:, 0].sum())
     rep_entries = gathered - uniq  # primaries are all distinct; the rest are replica entries
+    ntop = max(wl["rerank_n"], k) if lowp else k
     lut_b = wl["M"] * 256 * (2 if lowp else 0)
-    scan_bytes = uniq * wl["M"] + rep_entries * 9 + nq * lut_b + nq * (100 if lowp else k) * 8
+    scan_bytes = uniq * wl["M"] + rep_entries * 9 + nq * lut_b + nq * ntop * 8
+    reranked = int(st[:, 3].sum())
 
-    def step(trace=None):
-        return fa.fa_search_ex(ix, qd, k, wl["nprobe"], sp, out_ids=oid, out_dist=odist,
-                               stream=stream.cuda_stream, trace=trace)
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-
-    # ---- timed region: per-step CUDA events on the launching stream ----
     clocks = ClockSampler(local)
     clocks.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    traces = []
-    torch.cuda.synchronize()
-    for i in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps (outside the events)
-        tr = fa.fa_search_trace()
-        ev[i][0].record(stream)
-        step(tr)
-        ev[i][1].record(stream)
-        traces.append(tr)
-    torch.cuda.synchronize()
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    step_ms, traces = timed_steps(fa, torch, ix, qd, k, wl["nprobe"], sp, args.steps, args.warmup,
+                                  flush, oid, odist)
     clk = clocks.stop()
     ms = statistics.mean(step_ms)
     if world > 1:
@@ -304,15 +343,7 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_value = world * nq / (statistics.mean(e2e_ms) / 1e3)
 
-    # ---- recall@10 on a subsample (ground truth: exact L2 on the GPU in FP64) ----
-    recall = None
-    if args.recall > 0:
-        import oracle
-        ns = min(args.recall, nq)
-        gt_i, gt_d = ground_truth(base, queries[:ns], 10)
-        found = oid[:ns].cpu().numpy()
-        ex = exact_dists(base, queries[:ns], found)
-        recall = oracle.recall_at(found, gt_i, gt_d, exact_found_dist=ex, at=10)
+    recall = recall_of(oracle, base, queries, oid.cpu().numpy(), gt) if gt is not None else None
 
     # ---- roofline of the scan (dominant kernel) ----
     peak, peak_src = measured_peaks()
@@ -324,7 +355,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         parts = ix.parts()
-        ns = args.cpu_sample or 200
+        ns = args.cpu_sample or 100
         secs, cores, _ = run_oracle_sample(wl, base, queries, parts, ns)
         cpu = {"value": ns / secs, "unit": "queries/s", "cores": cores, "kind": "oracle",
                "sample": "first %d of the %d queries, same index and parameters, FP64" % (ns, nq)}
@@ -339,12 +370,17 @@ def main():
             "data": "synthetic",
             "config": {"workload": wl["name"], "n": wl["n"], "nq": nq, "d": d, "nlist": wl["nlist"],
                        "M": wl["M"], "nprobe": wl["nprobe"], "k": k, "form": args.form,
-                       "rerank_n": wl["rerank_n"], "rerank": "Algorithm 1, BatchSize 32, eps 0, beta 2",
-                       "raw_vectors": "pinned host" if wl["rerank_n"] else "none",
+                       "rerank_n": wl["rerank_n"] if lowp else 0,
+                       "rerank": "Algorithm 1, BatchSize %d, eps %g, beta %d" % (
+                           wl["batch"], wl["eps"], wl["beta"]) if lowp else "none",
+                       "raw_vectors": ("HBM" if args.raw == "device" else "pinned host")
+                       if lowp else "none",
+                       "launch": "persistent" if args.persistent else "one CTA per query",
                        "l2": "flushed between timed steps (256 MB write); codes 320 MB > L2",
                        "parallelism": "replicas" if world > 1 else "single"},
             "recall_at_10": recall,
             "candidates_per_query": uniq / nq,
+            "reranked_per_query": reranked / nq,
             "stage_ms": {"coarse": statistics.mean(t.coarse_ms for t in traces),
                          "lut": statistics.mean(t.lut_ms for t in traces), "scan": scan_ms,
                          "post": statistics.mean(t.post_ms for t in traces)},
@@ -365,6 +401,45 @@ def main():
         dist.destroy_process_group()
 
 
+def sweep(args, wl, fa, torch, oracle, ix, base, queries, qd, flush, gt, t_build):
+    """QPS and recall@10 over a grid of operating points (one index build)."""
+    k, nq = wl["k"], wl["nq"]
+    oid = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    odist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    # IVF coverage: share of the true 10-NN inside the nprobe nearest lists
+    ns = gt[0].shape[0]
+    primary = ix.parts()["primary"]
+    probes = fa.fa_debug_probes(ix, queries[:ns], 512)
+    for npb in (8, 16, 32, 64, 128, 256, 512):
+        cov = np.mean([np.isin(primary[gt[0][i]], probes[i, :npb]).mean() for i in range(ns)])
+        print(json.dumps({"coverage_nprobe": npb, "coverage": float(cov)}), flush=True)
+    grid = [("lowp", 64, 100, 32, 0.0, 2)]  # the configured operating point
+    for npb in (8, 16, 32, 64, 128, 256):
+        grid.append(("plain", npb, 0, 32, 0.0, 2))
+    for npb in (8, 16, 32, 64):
+        for n in (256, 512, 1024, 2048, 4096):
+            grid.append(("lowp", npb, n, 32, -1.0, 1))
+    for npb in (128, 256, 512):
+        for n in (1024, 4096):
+            grid.append(("lowp", npb, n, 32, -1.0, 1))
+    for npb in (64, 256):
+        for n in (1024, 4096):
+            for batch, beta in ((256, 2), (128, 3), (512, 1)):
+                grid.append(("lowp", npb, n, batch, 0.0, beta))
+    for form, npb, n, batch, eps, beta in grid:
+        w = dict(wl, rerank_n=n, batch=batch, eps=eps, beta=beta)
+        sp = search_params(fa, form, w)
+        ms, tr = timed_steps(fa, torch, ix, qd, k, npb, sp, 3, 3, flush, oid, odist)
+        r = recall_of(oracle, base, queries, oid.cpu().numpy(), gt)
+        print(json.dumps({"form": form, "nprobe": npb, "rerank_n": n, "batch": batch, "eps": eps,
+                          "beta": beta, "qps": nq / (statistics.mean(ms) / 1e3),
+                          "ms": statistics.mean(ms), "recall_at_10": r,
+                          "stage_ms": [statistics.mean(t.coarse_ms for t in tr),
+                                       statistics.mean(t.lut_ms for t in tr),
+                                       statistics.mean(t.scan_ms for t in tr),
+                                       statistics.mean(t.post_ms for t in tr)]}), flush=True)
+
+
 def reference_arm(args, wl, rank, world):
     """The FP64 CPU oracle as the reference implementation: each step is a
     bounded sample of the workload's queries against the same index."""
@@ -376,11 +451,11 @@ def reference_arm(args, wl, rank, world):
     torch.cuda.set_device(0)
     base = wl["mix"].base(wl["n"])
     queries = wl["mix"].queries(wl["nq"])
-    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=8,
-                         raw_location=fa.FA_RAW_HOST_PINNED if wl["rerank_n"] else fa.FA_RAW_NONE)
+    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=10,
+                         raw_location=fa.FA_RAW_HOST_PINNED)
     ix = fa.fa_build_index(base, bp)
     parts = ix.parts()
-    ns = args.cpu_sample or 64
+    ns = args.cpu_sample or 32
     times = []
     for i in range(max(3, args.warmup) + args.steps):
         secs, cores, _ = run_oracle_sample(wl, base, queries[(i * ns) % wl["nq"]:], parts, ns)

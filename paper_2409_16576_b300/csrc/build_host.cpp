@@ -184,7 +184,7 @@ void train_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
     const int iters = p.kmeans_iters;
     // training sample: evenly strided rows
     int64_t S = p.train_sample > 0 ? std::min<int64_t>(n, p.train_sample)
-                                   : std::min<int64_t>(n, std::max<int64_t>(32768, 16ll * nlist));
+                                   : std::min<int64_t>(n, std::max<int64_t>(65536, 64ll * nlist));
     std::vector<float> X((size_t)S * d);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < S; ++i) row_f32(base, dt, d, (i * n) / S, &X[(size_t)i * d]);

@@ -389,7 +389,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     else
         fa_search_params_init(&sp);
     FA_REQUIRE(d == ix->d, FA_ERR_ARG, "query dimension differs from the index");
-    FA_REQUIRE(k >= 1 && k <= 256, FA_ERR_ARG, "k must be in 1..256");
+    FA_REQUIRE(k >= 1 && k <= 4096, FA_ERR_ARG, "k must be in 1..4096");
     FA_REQUIRE(nq >= 0, FA_ERR_ARG, "nq < 0");
     if (nq == 0) return;
     FA_REQUIRE(queries && out_ids && out_dist, FA_ERR_ARG, "null buffer");
@@ -401,10 +401,10 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     if (rerank) {
         FA_REQUIRE(ix->dev.raw != nullptr, FA_ERR_ARG, "re-rank needs raw vectors in the index");
         FA_REQUIRE(k <= 128, FA_ERR_ARG, "re-rank supports k <= 128");
-        FA_REQUIRE(sp.rerank_batch >= 1 && sp.rerank_batch <= 256, FA_ERR_ARG, "bad rerank_batch");
+        FA_REQUIRE(sp.rerank_batch >= 1 && sp.rerank_batch <= 4096, FA_ERR_ARG, "bad rerank_batch");
         FA_REQUIRE(sp.rerank_beta >= 1, FA_ERR_ARG, "rerank_beta < 1");
         ntop = std::max(sp.rerank_n, k);
-        FA_REQUIRE(ntop <= 256, FA_ERR_ARG, "rerank_n above 256");
+        FA_REQUIRE(ntop <= 4096, FA_ERR_ARG, "rerank_n above 4096");
     }
     const bool qdev = sp.flags & FA_QUERIES_ON_DEVICE, odev = sp.flags & FA_OUTPUTS_ON_DEVICE;
     const bool global_lut = sp.lut_prec != FA_LUT_F32 || sp.lut_gemm == FA_GEMM_BF16_TC;

@@ -55,10 +55,62 @@ __global__ void __launch_bounds__(256) k_finish(const uint64_t *__restrict__ top
     }
 }
 
+// k > 256: one CTA per query sorts the row by (distance, caller id) in shared memory.
+__global__ void __launch_bounds__(512) k_finish_big(const uint64_t *__restrict__ topkeys, int64_t nq,
+                                                    int32_t ntop, int32_t k, const int32_t *kq,
+                                                    const int64_t *__restrict__ perm, int KP,
+                                                    int64_t *__restrict__ out_ids,
+                                                    float *__restrict__ out_dist) {
+    extern __shared__ uint64_t keys[];
+    const int64_t qi = blockIdx.x;
+    int kk = kq ? kq[qi] : k;
+    kk = kk < 1 ? 1 : (kk > k ? k : kk);
+    for (int e = threadIdx.x; e < KP; e += blockDim.x) {
+        uint64_t key = KEY_INF;
+        if (e < kk && e < ntop) key = topkeys[qi * ntop + e];
+        if (key != KEY_INF) {
+            const uint32_t internal = (uint32_t)(key & 0xffffffffu);
+            key = (key & 0xffffffff00000000ull) | (uint32_t)perm[internal];
+        }
+        keys[e] = key;
+    }
+    __syncthreads();
+    for (int size = 2; size <= KP; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < KP / 2; i += blockDim.x) {
+                const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t p = keys[lo], q = keys[hi];
+                if ((p > q) == up) {
+                    keys[lo] = q;
+                    keys[hi] = p;
+                }
+            }
+            __syncthreads();
+        }
+    for (int e = threadIdx.x; e < k; e += blockDim.x) {
+        const uint64_t key = e < kk ? keys[e] : KEY_INF;
+        out_ids[qi * k + e] = key == KEY_INF ? -1 : (int64_t)(key & 0xffffffffu);
+        out_dist[qi * k + e] = key == KEY_INF ? INFINITY : o2f((uint32_t)(key >> 32));
+    }
+}
+
 void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, int32_t ntop,
                    int32_t k, const int32_t *kq, int64_t *out_ids, float *out_dist,
                    cudaStream_t st) {
     if (nq == 0) return;
+    if (k > 256) {
+        FA_REQUIRE(k <= 4096, FA_ERR_ARG, "k above 4096");
+        int KP = 1;
+        while (KP < k) KP <<= 1;
+        FA_CHECK_CUDA(cudaFuncSetAttribute(k_finish_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           KP * 8));
+        k_finish_big<<<(unsigned)nq, 512, KP * 8, st>>>(topkeys, nq, ntop, k, kq, ix.perm, KP,
+                                                          out_ids, out_dist);
+        FA_CHECK_CUDA(cudaGetLastError());
+        return;
+    }
     const dim3 grid((unsigned)((nq + 7) / 8));
     if (k <= 32)
         k_finish<1><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
@@ -66,10 +118,8 @@ void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, i
         k_finish<2><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
     else if (k <= 128)
         k_finish<4><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
-    else if (k <= 256)
-        k_finish<8><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
     else
-        FA_REQUIRE(false, FA_ERR_ARG, "k above 256");
+        k_finish<8><<<grid, 256, 0, st>>>(topkeys, nq, ntop, k, kq, ix.perm, out_ids, out_dist);
     FA_CHECK_CUDA(cudaGetLastError());
 }
 

@@ -29,10 +29,13 @@
 
 namespace fa {
 
-constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_THREADS = 256;  // warp-top-n variant (n <= 256)
 constexpr int SCAN_WARPS = SCAN_THREADS / 32;
+constexpr int BIG_THREADS = 512;   // CTA-top-n variant (256 < n <= 4096)
+constexpr int BIG_WARPS = BIG_THREADS / 32;
 constexpr int MAX_PROBE = 512;
 constexpr int MAX_D = 1024;
+constexpr int MAX_TOPN = 4096;
 
 struct ScanArgs {
     // index
@@ -62,18 +65,33 @@ struct ScanArgs {
     int32_t persistent;
 };
 
-// Shared memory plan (bytes), shared by host and device.
+// Shared memory plan (bytes), shared by host and device. `tail` is the
+// per-variant region: per-warp merge buffers, or the CTA key buffer.
 struct ScanSmem {
-    int lut, qv, seg, bitmap, wbuf, total, npmax;
-    __host__ __device__ ScanSmem(int M, int W, int d, int nlist, int has_rep, int nprobe) {
-        (void)M;
-        npmax = nprobe;
+    int lut, qv, pref, seg, bitmap, tail, total;
+    __host__ __device__ ScanSmem(int W, int d, int nlist, int has_rep, int nprobe, int tail_bytes) {
         lut = 256 * W * 4;
         qv = ((d + 3) & ~3) * 4;
-        seg = ((2 * nprobe + 1) * 4 + 15) / 16 * 16 /*pref*/ + 2 * nprobe * 4 * 2 /*beg,end*/;
+        pref = ((2 * nprobe + 1) * 4 + 15) / 16 * 16;
+        seg = 2 * nprobe * 4 * 2;
         bitmap = has_rep ? ((nlist + 127) / 128) * 16 : 0;
-        wbuf = SCAN_WARPS * 64 * 8;
-        total = lut + qv + seg + bitmap + wbuf;
+        tail = tail_bytes;
+        total = lut + qv + pref + seg + bitmap + tail;
+    }
+};
+
+struct ScanPtrs {
+    float *lut, *qv;
+    uint32_t *pref, *seg_beg, *seg_end, *bitmap;
+    unsigned char *tail;
+    __device__ ScanPtrs(unsigned char *smem, const ScanSmem &p, int nprobe) {
+        lut = reinterpret_cast<float *>(smem);
+        qv = reinterpret_cast<float *>(smem + p.lut);
+        pref = reinterpret_cast<uint32_t *>(smem + p.lut + p.qv);
+        seg_beg = reinterpret_cast<uint32_t *>(smem + p.lut + p.qv + p.pref);
+        seg_end = seg_beg + 2 * nprobe;
+        bitmap = reinterpret_cast<uint32_t *>(smem + p.lut + p.qv + p.pref + p.seg);
+        tail = smem + p.lut + p.qv + p.pref + p.seg + p.bitmap;
     }
 };
 
@@ -88,13 +106,14 @@ __device__ __forceinline__ float lut_entry_global(const ScanArgs &a, int64_t qi,
     return float(v) * sc[0] + sc[2 + m];
 }
 
-// Builds the LUT of query qi in shared memory (rows of W floats).
-template <int W>
+// Builds the LUT of query qi in shared memory (rows of W floats; entry
+// p of row c is LUT[p mod M][c] for p < M + 31).
+template <int M, int W>
 __device__ __forceinline__ void build_lut(const ScanArgs &a, int64_t qi, float *lut, const float *qv) {
-    const int M = a.M, dsub = a.dsub;
-    const int P = M + 31;  // positions used per row
+    const int dsub = a.dsub;
+    constexpr int P = M + 31;
     for (int idx = threadIdx.x; idx < 256 * M; idx += blockDim.x) {
-        const int c = idx / M, m = idx - c * M;
+        const int c = idx / M, m = idx - c * M;  // M is a compile-time constant
         float val;
         if (a.lut_prec < 0) {
             const float *cw = a.codebooks + ((int64_t)m * 256 + c) * dsub;
@@ -108,15 +127,16 @@ __device__ __forceinline__ void build_lut(const ScanArgs &a, int64_t qi, float *
         } else {
             val = lut_entry_global(a, qi, m, c);
         }
-        for (int p = m; p < P; p += M) lut[c * W + p] = val;
+#pragma unroll
+        for (int p = 0; p < P; p += M)
+            if (p + m < P) lut[c * W + p + m] = val;
     }
 }
 
-// ADC distance of one code row (rotation r = v mod 32) against the smem LUT.
-template <int M, int W>
-__device__ __forceinline__ float adc_row(const uint8_t *row, uint32_t v, const float *lut, bool valid) {
-    constexpr int NW = M / 4;
-    uint32_t w[NW];
+template <int M>
+__device__ __forceinline__ void load_codes(const uint8_t *codes, uint32_t v, bool valid,
+                                           uint32_t (&w)[M / 4]) {
+    const uint8_t *row = codes + (size_t)v * M;
     if (valid) {
         if (M % 16 == 0) {
             const uint4 *p = reinterpret_cast<const uint4 *>(row);
@@ -139,8 +159,13 @@ __device__ __forceinline__ float adc_row(const uint8_t *row, uint32_t v, const f
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < NW; ++i) w[i] = 0;
+        for (int i = 0; i < M / 4; ++i) w[i] = 0;
     }
+}
+
+// ADC distance (Eq. 1) of one rotated code row (rotation r = v mod 32).
+template <int M, int W>
+__device__ __forceinline__ float adc_words(const uint32_t (&w)[M / 4], uint32_t v, const float *lut) {
     const uint32_t r4 = (v & 31u) * 4u;
     const char *lb = reinterpret_cast<const char *>(lut);
     float acc0 = 0.f, acc1 = 0.f;
@@ -163,121 +188,157 @@ __device__ __forceinline__ float adc_row(const uint8_t *row, uint32_t v, const f
     return acc0 + acc1;
 }
 
+// Candidate of this lane in chunk g (32 consecutive entries of one segment):
+// primary segments give internal ids directly; replica entries apply the dedup
+// rule. sg walks forward (chunks of a warp are visited in increasing order).
+__device__ __forceinline__ void locate(const ScanArgs &a, const ScanPtrs &S, int np, uint32_t g,
+                                       int &sg, uint32_t &v, bool &valid) {
+    const int lane = threadIdx.x & 31;
+    while (g >= S.pref[sg + 1]) ++sg;
+    const uint32_t pos = S.seg_beg[sg] + ((g - S.pref[sg]) << 5) + lane;
+    valid = pos < S.seg_end[sg];
+    v = pos;
+    if (sg >= np && valid) {
+        v = a.rep_v[pos];
+        const uint32_t mo = a.rep_mo[pos];
+        const int t = a.rep_t[pos];
+        for (int u = 0; u < t; ++u) {
+            const uint32_t l = a.mem[mo + u];
+            if (S.bitmap[l >> 5] & (1u << (l & 31))) valid = false;
+        }
+    }
+}
+
+// Per-query set-up shared by both variants: query, segment bounds, probed-list
+// bitmap, chunk prefix over 2*np segments, LUT. Ends with a CTA barrier.
+template <int M, int W>
+__device__ __forceinline__ void query_setup(const ScanArgs &a, const ScanPtrs &S, int64_t qi,
+                                            int np) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t *pr = a.probes + qi * a.probe_stride;
+    for (int j = threadIdx.x; j < a.d; j += blockDim.x) S.qv[j] = a.q[qi * a.d + j];
+    if (a.has_rep)
+        for (int j = threadIdx.x; j < (a.nlist + 31) / 32; j += blockDim.x) S.bitmap[j] = 0u;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        const int l = pr[i];
+        if (l < 0 || l >= a.nlist) {
+            atomicOr(a.err, DEV_ERR_BOUNDS);
+            S.seg_beg[i] = S.seg_end[i] = 0;
+            S.seg_beg[np + i] = S.seg_end[np + i] = 0;
+            continue;
+        }
+        S.seg_beg[i] = a.list_beg[l];
+        S.seg_end[i] = a.list_beg[l + 1];
+        if (a.has_rep) {
+            S.seg_beg[np + i] = (uint32_t)a.rep_off[l];
+            S.seg_end[np + i] = (uint32_t)a.rep_off[l + 1];
+        } else {
+            S.seg_beg[np + i] = S.seg_end[np + i] = 0;
+        }
+    }
+    __syncthreads();
+    if (a.has_rep)
+        for (int i = threadIdx.x; i < np; i += blockDim.x) {
+            const int l = pr[i];
+            if (l >= 0 && l < a.nlist) atomicOr(&S.bitmap[l >> 5], 1u << (l & 31));
+        }
+    if (warp == 0) {
+        const int nseg = 2 * np;
+        const int per = (nseg + 31) / 32;
+        uint32_t loc = 0;
+        for (int t = 0; t < per; ++t) {
+            const int s = lane * per + t;
+            if (s < nseg) loc += (S.seg_end[s] - S.seg_beg[s] + 31u) >> 5;
+        }
+        uint32_t inc = loc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        uint32_t run = inc - loc;
+        for (int t = 0; t < per; ++t) {
+            const int s = lane * per + t;
+            if (s < nseg) {
+                S.pref[s] = run;
+                run += (S.seg_end[s] - S.seg_beg[s] + 31u) >> 5;
+            }
+        }
+        if (lane == 31) S.pref[nseg] = inc;
+    }
+    build_lut<M, W>(a, qi, S.lut, S.qv);
+    __syncthreads();
+}
+
+__device__ __forceinline__ void write_stats(const ScanArgs &a, const ScanPtrs &S, int64_t qi,
+                                            int np, uint32_t kept) {
+    int64_t gathered = 0;
+    for (int s = 0; s < 2 * np; ++s) gathered += S.seg_end[s] - S.seg_beg[s];
+    a.stats[qi * 4 + 0] = (int32_t)gathered;
+    a.stats[qi * 4 + 1] = (int32_t)kept;
+}
+
+__device__ __forceinline__ int64_t next_query(const ScanArgs &a, int64_t it) {
+    return a.persistent ? (int64_t)atomicAdd(a.tile_ctr, 1u) : (int64_t)blockIdx.x + it * gridDim.x;
+}
+
+// ---------------------------------------------------------------------------
+// Variant 1: n <= 256. Each warp keeps its own top-n in registers; the warps
+// share the best n-th key seen by any of them as a common filter threshold.
+// Code rows of the next chunk are loaded while the current one is scanned.
+// ---------------------------------------------------------------------------
 template <int M, int W, int R>
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const ScanArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const ScanSmem plan(M, W, a.d, a.nlist, a.has_rep, a.nprobe);
-    float *lut = reinterpret_cast<float *>(smem);
-    float *qv = reinterpret_cast<float *>(smem + plan.lut);
-    uint32_t *pref = reinterpret_cast<uint32_t *>(smem + plan.lut + plan.qv);
-    uint32_t *seg_beg = reinterpret_cast<uint32_t *>(smem + plan.lut + plan.qv +
-                                                     ((2 * a.nprobe + 1) * 4 + 15) / 16 * 16);
-    uint32_t *seg_end = seg_beg + 2 * a.nprobe;
-    uint32_t *bitmap = reinterpret_cast<uint32_t *>(smem + plan.lut + plan.qv + plan.seg);
-    uint64_t *wbuf = reinterpret_cast<uint64_t *>(smem + plan.lut + plan.qv + plan.seg + plan.bitmap);
+    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, SCAN_WARPS * 64 * 8);
+    const ScanPtrs S(smem, plan, a.nprobe);
+    uint64_t *wbuf = reinterpret_cast<uint64_t *>(S.tail);
     __shared__ int64_t s_q;
     __shared__ uint32_t s_kept;
-
+    __shared__ unsigned long long s_thr;
+    constexpr int NW = M / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     for (int64_t it = 0;; ++it) {
         if (threadIdx.x == 0) {
-            if (a.persistent)
-                s_q = (int64_t)atomicAdd(a.tile_ctr, 1u);
-            else
-                s_q = (int64_t)blockIdx.x + it * gridDim.x;
+            s_q = next_query(a, it);
             s_kept = 0;
+            s_thr = KEY_INF;
         }
         __syncthreads();
         const int64_t qi = s_q;
         if (qi >= a.nq) break;
-
         int np = a.npq ? a.npq[qi] : a.nprobe;
         np = np < 1 ? 1 : (np > a.nprobe ? a.nprobe : np);
         const int ntop = a.ntopq ? a.ntopq[qi] : a.ntop;
-        const int32_t *pr = a.probes + qi * a.probe_stride;
+        query_setup<M, W>(a, S, qi, np);
 
-        // query, segment bounds, probed-list bitmap
-        for (int j = threadIdx.x; j < a.d; j += blockDim.x) qv[j] = a.q[qi * a.d + j];
-        if (a.has_rep)
-            for (int j = threadIdx.x; j < (a.nlist + 31) / 32; j += blockDim.x) bitmap[j] = 0u;
-        for (int i = threadIdx.x; i < np; i += blockDim.x) {
-            int l = pr[i];
-            if (l < 0 || l >= a.nlist) {
-                atomicOr(a.err, DEV_ERR_BOUNDS);
-                l = 0;
-                seg_beg[i] = seg_end[i] = 0;
-                seg_beg[np + i] = seg_end[np + i] = 0;
-                continue;
-            }
-            seg_beg[i] = a.list_beg[l];
-            seg_end[i] = a.list_beg[l + 1];
-            if (a.has_rep) {
-                seg_beg[np + i] = (uint32_t)a.rep_off[l];
-                seg_end[np + i] = (uint32_t)a.rep_off[l + 1];
-            } else {
-                seg_beg[np + i] = seg_end[np + i] = 0;
-            }
-        }
-        __syncthreads();
-        if (a.has_rep)
-            for (int i = threadIdx.x; i < np; i += blockDim.x) {
-                const int l = pr[i];
-                if (l >= 0 && l < a.nlist) atomicOr(&bitmap[l >> 5], 1u << (l & 31));
-            }
-        // chunk prefix over 2*np segments (warp 0)
-        if (warp == 0) {
-            const int nseg = 2 * np;
-            const int per = (nseg + 31) / 32;
-            uint32_t loc = 0;
-            for (int t = 0; t < per; ++t) {
-                const int s = lane * per + t;
-                if (s < nseg) loc += (seg_end[s] - seg_beg[s] + 31u) >> 5;
-            }
-            uint32_t inc = loc;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(FULL, inc, o);
-                if (lane >= o) inc += y;
-            }
-            uint32_t run = inc - loc;
-            for (int t = 0; t < per; ++t) {
-                const int s = lane * per + t;
-                if (s < nseg) {
-                    pref[s] = run;
-                    run += (seg_end[s] - seg_beg[s] + 31u) >> 5;
-                }
-            }
-            if (lane == 31) pref[nseg] = inc;
-        }
-        build_lut<W>(a, qi, lut, qv);
-        __syncthreads();
-
-        // scan
         WarpTopK<R> tk;
         tk.init(wbuf + warp * 64, ntop);
-        const int nseg = 2 * np;
-        const uint32_t total = pref[nseg];
+        tk.sthr = &s_thr;
+        const uint32_t total = S.pref[2 * np];
         uint32_t kept = 0;
         int sg = 0;
-        for (uint32_t g = warp; g < total; g += SCAN_WARPS) {
-            while (g >= pref[sg + 1]) ++sg;
-            const uint32_t pos = seg_beg[sg] + ((g - pref[sg]) << 5) + lane;
-            bool valid = pos < seg_end[sg];
-            uint32_t v = pos;
-            if (sg >= np && valid) {
-                // replica entry: scanned only if no earlier list of v is probed
-                v = a.rep_v[pos];
-                const uint32_t mo = a.rep_mo[pos];
-                const int t = a.rep_t[pos];
-                for (int u = 0; u < t; ++u) {
-                    const uint32_t l = a.mem[mo + u];
-                    if (bitmap[l >> 5] & (1u << (l & 31))) valid = false;
-                }
-            }
-            const float dist = adc_row<M, W>(a.codes + (size_t)v * M, v, lut, valid);
-            kept += valid ? 1u : 0u;
-            tk.push(make_key(dist, v), valid);
+        uint32_t g = warp;
+        uint32_t vc = 0;
+        bool okc = false;
+        uint32_t wc[NW];
+        if (g < total) locate(a, S, np, g, sg, vc, okc);
+        load_codes<M>(a.codes, vc, okc && g < total, wc);
+        for (; g < total; g += SCAN_WARPS) {
+            const uint32_t gn = g + SCAN_WARPS;
+            uint32_t vn = 0;
+            bool okn = false;
+            if (gn < total) locate(a, S, np, gn, sg, vn, okn);
+            uint32_t wn[NW];
+            load_codes<M>(a.codes, vn, okn, wn);
+            const float dist = adc_words<M, W>(wc, vc, S.lut);
+            kept += okc ? 1u : 0u;
+            tk.push(make_key(dist, vc), okc);
+            vc = vn;
+            okc = okn;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) wc[i] = wn[i];
         }
         tk.finish();
         if (a.stats) {
@@ -305,43 +366,201 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const ScanArgs a) {
                 const int e = r * 32 + lane;
                 if (e < a.ntop) out[e] = e < ntop ? L[r] : KEY_INF;
             }
-            if (a.stats && lane == 0) {
-                int64_t gathered = 0;
-                for (int s = 0; s < np; ++s) gathered += seg_end[s] - seg_beg[s];
-                for (int s = np; s < 2 * np; ++s) gathered += seg_end[s] - seg_beg[s];
-                a.stats[qi * 4 + 0] = (int32_t)gathered;
-                a.stats[qi * 4 + 1] = (int32_t)s_kept;
+            if (a.stats && lane == 0) write_stats(a, S, qi, np, s_kept);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Variant 2: 256 < n <= 4096. The CTA keeps region A = its current top-n
+// (sorted, NP = next power of two >= n keys) and region B = new keys below the
+// threshold (the n-th key of A). When B may overflow in the next round, B is
+// sorted and merged into A (min(A[i], B[NP-1-i]) is bitonic and holds the NP
+// smallest; a bitonic merge sorts it). Warps scan in lock-step rounds so that
+// every thread reaches the same barriers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void smem_bitonic_sort(uint64_t *x, int n) {
+    for (int size = 2; size <= n; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+                const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const uint64_t p = x[lo], q = x[hi];
+                if ((p > q) == up) {
+                    x[lo] = q;
+                    x[hi] = p;
+                }
+            }
+            __syncthreads();
+        }
+}
+
+__device__ __forceinline__ void smem_bitonic_merge(uint64_t *x, int n) {
+    for (int stride = n >> 1; stride > 0; stride >>= 1) {
+        for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+            const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
+            const int hi = lo + stride;
+            const uint64_t p = x[lo], q = x[hi];
+            if (p > q) {
+                x[lo] = q;
+                x[hi] = p;
             }
         }
         __syncthreads();
     }
 }
 
-template <int M, int W, int R>
-static void launch_scan_t(const ScanArgs &a, int smem_bytes, int grid, cudaStream_t st) {
-    auto kfn = k_scan<M, W, R>;
-    FA_CHECK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes));
-    kfn<<<grid, SCAN_THREADS, smem_bytes, st>>>(a);
-    FA_CHECK_CUDA(cudaGetLastError());
+// Merges the first cntB keys of B into A (both NP long); updates the threshold.
+__device__ __forceinline__ void cta_merge(uint64_t *A, uint64_t *B, int NP, uint32_t cntB, int ntop,
+                                          unsigned long long *s_thr, uint32_t *s_cnt) {
+    for (int i = cntB + threadIdx.x; i < NP; i += blockDim.x) B[i] = KEY_INF;
+    __syncthreads();
+    smem_bitonic_sort(B, NP);
+    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
+        const uint64_t b = B[NP - 1 - i];
+        if (b < A[i]) A[i] = b;
+    }
+    __syncthreads();
+    smem_bitonic_merge(A, NP);
+    if (threadIdx.x == 0) {
+        *s_thr = A[ntop - 1];
+        *s_cnt = 0;
+    }
+    __syncthreads();
 }
 
 template <int M, int W>
-static void launch_scan_r(const ScanArgs &a, int smem, int grid, cudaStream_t st) {
-    if (a.ntop <= 32)
-        launch_scan_t<M, W, 1>(a, smem, grid, st);
-    else if (a.ntop <= 64)
-        launch_scan_t<M, W, 2>(a, smem, grid, st);
-    else if (a.ntop <= 128)
-        launch_scan_t<M, W, 4>(a, smem, grid, st);
-    else
-        launch_scan_t<M, W, 8>(a, smem, grid, st);
+__global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int NP) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, 2 * NP * 8);
+    const ScanPtrs S(smem, plan, a.nprobe);
+    uint64_t *A = reinterpret_cast<uint64_t *>(S.tail);
+    uint64_t *B = A + NP;
+    __shared__ int64_t s_q;
+    __shared__ uint32_t s_kept, s_cnt;
+    __shared__ unsigned long long s_thr;
+    constexpr int NW = M / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t round = BIG_WARPS * 32;  // keys one round can add
+
+    for (int64_t it = 0;; ++it) {
+        if (threadIdx.x == 0) {
+            s_q = next_query(a, it);
+            s_kept = 0;
+            s_cnt = 0;
+            s_thr = KEY_INF;
+        }
+        for (int i = threadIdx.x; i < NP; i += blockDim.x) A[i] = KEY_INF;
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi >= a.nq) break;
+        int np = a.npq ? a.npq[qi] : a.nprobe;
+        np = np < 1 ? 1 : (np > a.nprobe ? a.nprobe : np);
+        int ntop = a.ntopq ? a.ntopq[qi] : a.ntop;
+        ntop = ntop < 1 ? 1 : (ntop > NP ? NP : ntop);
+        query_setup<M, W>(a, S, qi, np);
+
+        const uint32_t total = S.pref[2 * np];
+        uint32_t kept = 0;
+        int sg = 0;
+        for (uint32_t base = 0; base < total; base += BIG_WARPS) {
+            const uint32_t g = base + warp;
+            if (g < total) {
+                uint32_t v;
+                bool ok;
+                locate(a, S, np, g, sg, v, ok);
+                uint32_t w[NW];
+                load_codes<M>(a.codes, v, ok, w);
+                const float dist = adc_words<M, W>(w, v, S.lut);
+                kept += ok ? 1u : 0u;
+                const uint64_t key = make_key(dist, v);
+                const bool pass = ok && key < *(volatile unsigned long long *)&s_thr;
+                const uint32_t m = __ballot_sync(FULL, pass);
+                if (m) {
+                    uint32_t p0 = 0;
+                    if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+                    p0 = __shfl_sync(FULL, p0, 0);
+                    if (pass) B[p0 + __popc(m & ((1u << lane) - 1u))] = key;
+                }
+            }
+            __syncthreads();
+            const uint32_t c = s_cnt;
+            __syncthreads();  // every thread has read c before the next round adds to it
+            if (c + round > (uint32_t)NP) cta_merge(A, B, NP, c, ntop, &s_thr, &s_cnt);
+        }
+        __syncthreads();
+        const uint32_t c = s_cnt;
+        if (c > 0) cta_merge(A, B, NP, c, ntop, &s_thr, &s_cnt);
+        if (a.stats) {
+            for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
+            if (lane == 0) atomicAdd(&s_kept, kept);
+        }
+        uint64_t *out = a.topkeys + qi * (int64_t)a.ntop;
+        for (int e = threadIdx.x; e < a.ntop; e += blockDim.x) out[e] = e < ntop ? A[e] : KEY_INF;
+        __syncthreads();
+        if (a.stats && threadIdx.x == 0) write_stats(a, S, qi, np, s_kept);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int pow2_at_least(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+template <class K>
+static void set_smem(K kfn, int bytes) {
+    FA_CHECK_CUDA(cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+}
+
+static int scan_grid(const ScanLaunch &l, int smem_total) {
+    if (!l.persistent) return (int)(l.nq < (int64_t)INT32_MAX ? l.nq : INT32_MAX);
+    int per_sm = (227 * 1024) / (smem_total + 1024);
+    per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
+    int grid = num_sms(0) * per_sm;
+    return (int64_t)grid > l.nq ? (int)l.nq : grid;
+}
+
+template <int M, int W>
+static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t st) {
+    if (a.ntop <= 256) {
+        const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, SCAN_WARPS * 64 * 8);
+        FA_REQUIRE(SCAN_WARPS * 256 * 8 <= plan.lut, FA_ERR_ARG, "LUT region too small for merge");
+        FA_REQUIRE(plan.total <= 227 * 1024, FA_ERR_ARG, "scan shared memory above 227 KB");
+        const int grid = scan_grid(l, plan.total);
+#define FA_SCAN(RR)                                                                 \
+    do {                                                                            \
+        set_smem(k_scan<M, W, RR>, plan.total);                                     \
+        k_scan<M, W, RR><<<grid, SCAN_THREADS, plan.total, st>>>(a);                \
+    } while (0)
+        if (a.ntop <= 32) FA_SCAN(1);
+        else if (a.ntop <= 64) FA_SCAN(2);
+        else if (a.ntop <= 128) FA_SCAN(4);
+        else FA_SCAN(8);
+#undef FA_SCAN
+    } else {
+        const int NP = pow2_at_least(a.ntop < 2 * BIG_WARPS * 32 ? 2 * BIG_WARPS * 32 : a.ntop);
+        const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, 2 * NP * 8);
+        FA_REQUIRE(plan.total <= 227 * 1024, FA_ERR_ARG,
+                   "scan shared memory above 227 KB (top-n too large for this M)");
+        const int grid = scan_grid(l, plan.total);
+        set_smem(k_scan_cta<M, W>, plan.total);
+        k_scan_cta<M, W><<<grid, BIG_THREADS, plan.total, st>>>(a, NP);
+    }
+    FA_CHECK_CUDA(cudaGetLastError());
 }
 
 void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     if (l.nq == 0) return;
     FA_REQUIRE(l.nprobe <= MAX_PROBE, FA_ERR_ARG, "nprobe above 512");
     FA_REQUIRE(ix.d <= MAX_D, FA_ERR_ARG, "d above 1024");
-    FA_REQUIRE(l.ntop >= 1 && l.ntop <= 256, FA_ERR_ARG, "top-n must be in 1..256");
+    FA_REQUIRE(l.ntop >= 1 && l.ntop <= MAX_TOPN, FA_ERR_ARG, "top-n must be in 1..4096");
     ScanArgs a{};
     a.codes = ix.codes;
     a.list_beg = ix.list_beg;
@@ -372,27 +591,12 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     a.err = l.err;
     a.tile_ctr = l.tile_ctr;
     a.persistent = l.persistent;
-    const int W = lut_row_words(ix.M);
-    const ScanSmem plan(ix.M, W, ix.d, ix.nlist, a.has_rep, l.nprobe);
-    // the merge area reuses the LUT region: SCAN_WARPS * 32R keys
-    FA_REQUIRE(SCAN_WARPS * 256 * 8 <= plan.lut, FA_ERR_ARG, "LUT region too small for merge");
-    FA_REQUIRE(plan.total <= 227 * 1024, FA_ERR_ARG, "scan shared memory above 227 KB");
-    int grid;
-    if (l.persistent) {
-        int per_sm = (227 * 1024) / (plan.total + 1024);
-        if (per_sm < 1) per_sm = 1;
-        if (per_sm > 8) per_sm = 8;
-        grid = num_sms(0) * per_sm;
-        if ((int64_t)grid > l.nq) grid = (int)l.nq;
-    } else {
-        grid = (int)(l.nq < (int64_t)INT32_MAX ? l.nq : INT32_MAX);
-    }
     switch (ix.M) {
-        case 8: launch_scan_r<8, 64>(a, plan.total, grid, st); break;
-        case 16: launch_scan_r<16, 64>(a, plan.total, grid, st); break;
-        case 32: launch_scan_r<32, 64>(a, plan.total, grid, st); break;
-        case 48: launch_scan_r<48, 80>(a, plan.total, grid, st); break;
-        case 64: launch_scan_r<64, 128>(a, plan.total, grid, st); break;
+        case 8: launch_scan_m<8, 64>(a, l, st); break;
+        case 16: launch_scan_m<16, 64>(a, l, st); break;
+        case 32: launch_scan_m<32, 64>(a, l, st); break;
+        case 48: launch_scan_m<48, 80>(a, l, st); break;
+        case 64: launch_scan_m<64, 128>(a, l, st); break;
         default: FA_REQUIRE(false, FA_ERR_ARG, "M must be one of 8, 16, 32, 48, 64");
     }
 }

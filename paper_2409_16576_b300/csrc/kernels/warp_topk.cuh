@@ -126,8 +126,10 @@ struct WarpTopK {
     uint64_t *buf;  // 64 keys in shared memory, private to the warp
     int cnt;        // keys in buf (warp-uniform)
     int n;          // keys wanted, 1 <= n <= 32*R
+    unsigned long long *sthr;  // optional threshold shared by the CTA's warps
 
     __device__ __forceinline__ void init(uint64_t *wbuf, int n_) {
+        sthr = nullptr;
 #pragma unroll
         for (int r = 0; r < R; ++r) L[r] = KEY_INF;
         thr = KEY_INF;
@@ -144,6 +146,8 @@ struct WarpTopK {
         bitonic_sort<1>(bb);
         merge_sorted32<R>(L, bb[0]);
         thr = warp_elem<R>(L, n - 1);
+        // any warp's n-th best bounds the CTA's n-th best from above
+        if (sthr && thr != KEY_INF && (threadIdx.x & 31) == 0) atomicMin(sthr, (unsigned long long)thr);
         int rem = cnt - 32;
         uint64_t x = (rem > 0 && lane < rem) ? buf[32 + lane] : 0;
         __syncwarp();
@@ -155,7 +159,9 @@ struct WarpTopK {
     // Offers one key per lane (pass = false lanes offer nothing).
     __device__ __forceinline__ void push(uint64_t key, bool valid) {
         const int lane = threadIdx.x & 31;
-        const bool pass = valid && key < thr;
+        uint64_t t = thr;
+        if (sthr) t = umin64(t, *(volatile unsigned long long *)sthr);
+        const bool pass = valid && key < t;
         const uint32_t m = __ballot_sync(FULL, pass);
         if (m) {
             const int pos = cnt + __popc(m & ((1u << lane) - 1u));

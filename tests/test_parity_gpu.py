@@ -177,8 +177,9 @@ def _search_vs_oracle(fa, s, k, npb, params=None, nq=None, rerank=0):
     return gi, gd, oi, od
 
 
-@pytest.mark.parametrize("k", [1, 10, 100])
+@pytest.mark.parametrize("k", [1, 10, 100, 300, 1000])
 def test_search_given_probes_matches_oracle(fa, f32_small, k):
+    """k <= 256 runs the per-warp top-n, larger k the CTA-wide top-n."""
     s = f32_small
     gi, gd, oi, od = _search_vs_oracle(fa, s, k, 8)
     for i in range(gi.shape[0]):
@@ -189,11 +190,12 @@ def test_search_given_probes_matches_oracle(fa, f32_small, k):
         assert keys == sorted(keys)
 
 
-def test_search_with_replication_matches_oracle(fa, u8_repl):
-    gi, gd, oi, od = _search_vs_oracle(fa, u8_repl, 10, 16)
+@pytest.mark.parametrize("k", [10, 600])
+def test_search_with_replication_matches_oracle(fa, u8_repl, k):
+    gi, gd, oi, od = _search_vs_oracle(fa, u8_repl, k, 16)
     for i in range(gi.shape[0]):
-        _check_topk(gi[i], gd[i], oi[i, :10], od[i, :10], od[i, 10], 10, what=str(i))
-        assert len(set(gi[i].tolist())) == 10  # no duplicate ids
+        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
+        assert len(set(gi[i].tolist())) == k  # no duplicate ids
 
 
 def test_end_to_end_recall_matches_oracle(fa, f32_small):
@@ -328,11 +330,13 @@ def test_argument_errors_and_empty_batch(fa, f32_small):
 # step 8: Algorithm 1 on the GPU
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("eps,beta,batch", [(0.0, 2, 32), (-1.0, 1, 32), (1.0, 1, 32),
-                                            (0.1, 1, 16), (0.0, 3, 8)])
-def test_rerank_matches_oracle(fa, u8_repl, eps, beta, batch):
+@pytest.mark.parametrize("eps,beta,batch,n", [(0.0, 2, 32, 100), (-1.0, 1, 32, 100),
+                                              (1.0, 1, 32, 100), (0.1, 1, 16, 100),
+                                              (0.0, 3, 8, 100), (-1.0, 1, 32, 1000),
+                                              (0.0, 2, 256, 1000)])
+def test_rerank_matches_oracle(fa, u8_repl, eps, beta, batch, n):
     s = u8_repl
-    k, npb, n = 10, 16, 100
+    k, npb = 10, 16
     q = s["q"][:24]
     probes = oracle.coarse(q, s["parts"]["centroids"], npb)
     p = fa.search_params(rerank_n=n, rerank_batch=batch, rerank_beta=beta, rerank_eps=eps)
