@@ -211,6 +211,17 @@ void upload_index(fa_index *ix) {
     D.rep_t = dev_upload(rt.data(), rt.size(), bytes);
     D.mem = dev_upload(mem.data(), mem.size(), bytes);
     D.perm = dev_upload(perm.data(), perm.size(), bytes);
+    if (d <= 128) {  // tensor-core operand tiles (BF16 hi/lo) for the coarse probe and the LUT
+        std::vector<uint16_t> tiles;
+        prepare_centroid_tiles(ix->centroids.data(), nlist, d, tiles, D.tc_kp, D.tc_ntiles);
+        D.centroids_bf16 = dev_upload(tiles.data(), tiles.size(), bytes);
+        if (16 % D.dsub == 0) {
+            std::vector<float> norms;
+            prepare_codebook_tiles(ix->codebooks.data(), M, d, tiles, norms);
+            D.codebooks_bf16 = dev_upload(tiles.data(), tiles.size(), bytes);
+            D.cbnorm = dev_upload(norms.data(), norms.size(), bytes);
+        }
+    }
 
     if (ix->h_raw) {
         const size_t rb = (size_t)n * d * (ix->raw_dtype == FA_U8 ? 1 : 4);
@@ -284,7 +295,7 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
     dalloc(w->out_ids, (size_t)cq * ck);
     dalloc(w->out_dist, (size_t)cq * ck);
     dalloc(w->stats, (size_t)cq * 4);
-    dalloc(w->lut_scale, (size_t)cq * (2 + D.M));
+    dalloc(w->lut_scale, (size_t)cq * 2 * D.M);
     if (cl > 0) {
         char *p = nullptr;
         dalloc(p, (size_t)cq * cl);
@@ -453,7 +464,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     }
     tr.mark(1);
     if (global_lut) {
-        launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, st);
+        launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st);
         tr.launches += 1;
     }
     tr.mark(2);
@@ -978,9 +989,10 @@ fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params 
         ws_ensure(ix, w, 1, 1, 1, 1, M * 256 * elem);
         cudaStream_t st = w->stream;
         FA_CHECK_CUDA(cudaMemcpyAsync(w->q, query, sizeof(float) * ix->d, cudaMemcpyHostToDevice, st));
-        launch_lut_global(ix->dev, w->q, 1, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, st);
+        FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
+        launch_lut_global(ix->dev, w->q, 1, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st);
         std::vector<uint8_t> raw((size_t)M * 256 * elem);
-        std::vector<float> sc(2 + M);
+        std::vector<float> sc(2 * M);
         FA_CHECK_CUDA(cudaMemcpyAsync(raw.data(), w->lut, raw.size(), cudaMemcpyDeviceToHost, st));
         FA_CHECK_CUDA(cudaMemcpyAsync(sc.data(), w->lut_scale, 4 * sc.size(), cudaMemcpyDeviceToHost, st));
         FA_CHECK_CUDA(cudaStreamSynchronize(st));
@@ -993,9 +1005,9 @@ fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params 
                 } else if (sp.lut_prec == FA_LUT_F16) {
                     uint16_t h;
                     memcpy(&h, raw.data() + 2 * i, 2);
-                    v = half_bits_to_float(h) * sc[0] + sc[2 + m];
+                    v = half_bits_to_float(h) * sc[2 * m] + sc[2 * m + 1];
                 } else {
-                    v = e4m3_bits_to_float(raw[i]) * sc[0] + sc[2 + m];
+                    v = e4m3_bits_to_float(raw[i]) * sc[2 * m] + sc[2 * m + 1];
                 }
                 out_lut[i] = v;
             }

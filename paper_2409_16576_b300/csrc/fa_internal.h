@@ -80,9 +80,10 @@ struct DeviceIndex {
     void *raw_dev_alloc = nullptr;
     void *raw_host_alloc = nullptr;
     // bf16 operands for the tensor-core paths (allocated on first use)
-    void *centroids_bf16 = nullptr; // [nlist][d] hi + [nlist][d] lo
-    void *codebooks_bf16 = nullptr;
-    float *cbnorm = nullptr;        // [M][256] |C_m[c]|^2 of the bf16-rounded codebook
+    void *centroids_bf16 = nullptr; // tensor-core tiles [ntiles][hi, lo][256 x tc_kp]
+    int32_t tc_kp = 0, tc_ntiles = 0;
+    void *codebooks_bf16 = nullptr; // tensor-core B tiles [M][hi, lo][256 x 16]
+    float *cbnorm = nullptr;        // [M][256] |C_m[c]|^2 (FP32)
     int64_t device_bytes = 0;
     int64_t pinned_bytes = 0;
 };
@@ -106,7 +107,7 @@ struct Workspace {
     float *out_dist = nullptr;     // [cap_nq][cap_k]
     int32_t *stats = nullptr;      // [cap_nq][4]
     void *lut = nullptr;           // [cap_nq][lut_bytes] global LUT (precision form)
-    float *lut_scale = nullptr;    // [cap_nq][2 + M] scale, offset sum, per-subspace offsets
+    float *lut_scale = nullptr;    // [cap_nq][2M] per subspace: scale, offset
     float *coarse_d = nullptr;     // coarse distance scratch [coarse_rows][nlist]
     int64_t coarse_rows = 0;
     uint32_t *err = nullptr;       // device error word
@@ -183,7 +184,7 @@ struct ScanLaunch {
     int32_t nprobe, probe_stride, ntop;
     int32_t lut_prec;        // FA_LUT_* of a precomputed global LUT, or -1 to build in smem
     const void *lut;         // global LUT [nq][M][256] (when lut_prec >= 0)
-    const float *lut_scale;  // [nq][2 + M]
+    const float *lut_scale;  // [nq][2M]
     uint64_t *topkeys;       // [nq][ntop] out
     int32_t *stats;          // [nq][4] or null
     uint32_t *err;
@@ -195,9 +196,15 @@ void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t np
                    int32_t probe_stride, int gemm, Workspace &ws, int32_t *probes,
                    cudaStream_t st);
 int coarse_launches(const DeviceIndex &ix, int64_t nq, const Workspace &ws);
+void prepare_centroid_tiles(const float *cent, int32_t nlist, int32_t d, std::vector<uint16_t> &out,
+                            int32_t &Kp, int32_t &ntiles);
+void prepare_codebook_tiles(const float *cb, int32_t M, int32_t d, std::vector<uint16_t> &tiles,
+                            std::vector<float> &norms);
+void launch_coarse_tc_dist(const DeviceIndex &ix, const float *q, int64_t rows, float *D,
+                           int64_t ldd, uint32_t *err, cudaStream_t st);
 void launch_scan(const DeviceIndex &ix, const ScanLaunch &a, cudaStream_t st);
 void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int prec, int gemm,
-                       void *lut, float *lut_scale, cudaStream_t st);
+                       void *lut, float *lut_scale, uint32_t *err, cudaStream_t st);
 void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, int32_t ntop,
                    int32_t k, const int32_t *kq, int64_t *out_ids, float *out_dist,
                    cudaStream_t st);

@@ -140,8 +140,17 @@ static void l2_topn(const float *X, int64_t nx, int32_t d, const float *C, int32
 void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
                    int32_t probe_stride, int gemm, Workspace &ws, int32_t *probes,
                    cudaStream_t st) {
-    (void)gemm;
     if (nq == 0) return;
+    if (gemm == FA_GEMM_BF16_TC && ix.centroids_bf16) {
+        // distances on the tensor cores, then the same top-nprobe selection
+        for (int64_t r0 = 0; r0 < nq; r0 += ws.coarse_rows) {
+            const int64_t rows = std::min(ws.coarse_rows, nq - r0);
+            launch_coarse_tc_dist(ix, q + r0 * ix.d, rows, ws.coarse_d, ix.nlist, ws.err, st);
+            select_rows(ws.coarse_d, ix.nlist, rows, ix.nlist, nprobe, probes + r0 * probe_stride,
+                        probe_stride, nullptr, st);
+        }
+        return;
+    }
     l2_topn(q, nq, ix.d, ix.centroids, ix.nlist, nprobe, ws.coarse_d, ws.coarse_rows, probes,
             probe_stride, nullptr, st);
 }

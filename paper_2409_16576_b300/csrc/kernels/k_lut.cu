@@ -2,14 +2,14 @@
 // (the precision form): LUT[m][c] = dist(q_m, C_m[c]) for every subspace m and
 // centroid c, stored as FP32, FP16 or FP8 (e4m3).
 //
-// Quantised tables keep, per query, one scale s and per subspace an offset
-// o_m = min_c LUT[m][c]:  LUT[m][c] ~= s * stored[m][c] + o_m,
-// stored = round(( LUT[m][c] - o_m ) / s) with s = max residual / format max.
+// Quantised tables keep, per query and subspace m, a scale s_m and an offset
+// o_m = min_c LUT[m][c]:  LUT[m][c] ~= s_m * stored[m][c] + o_m, with
+// stored = round((LUT[m][c] - o_m) / s_m) and s_m = (max - min) / format max.
 // The ADC scan dequantises into its FP32 shared-memory table, so sums stay
 // FP32; each entry is off by at most half a unit in the last place of the
-// stored value times s.
+// stored value times s_m.
 //
-// lut_scale row layout per query: [0] = s, [1] = sum_m o_m, [2 + m] = o_m.
+// lut_scale row layout per query: [2m] = s_m, [2m + 1] = o_m.
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -20,56 +20,47 @@ namespace fa {
 constexpr float F16_MAX = 65504.f;
 constexpr float FP8_MAX = 448.f;
 
-__device__ __forceinline__ float block_reduce_max(float v, float *red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        v = lane < (int)(blockDim.x >> 5) ? red[lane] : -INFINITY;
-        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) red[0] = v;
-    }
-    __syncthreads();
-    v = red[0];
-    __syncthreads();
-    return v;
-}
-
 // Stores a FP32 table held in shared memory (t[m*256 + c]) in the requested
-// precision, with per-subspace offsets and a per-query scale.
+// precision with a per-subspace scale and offset.
 __device__ void store_lut(const float *t, int M, int prec, void *lut, float *scale, int64_t qi,
-                          float *red, float *offs) {
+                          float *offs, float *scl) {
     const int64_t base = qi * (int64_t)M * 256;
-    float *sc = scale + qi * (2 + M);
+    float *sc = scale + qi * 2 * M;
     if (prec == FA_LUT_F32) {
         for (int i = threadIdx.x; i < M * 256; i += blockDim.x)
             reinterpret_cast<float *>(lut)[base + i] = t[i];
-        if (threadIdx.x == 0) {
-            sc[0] = 1.f;
-            sc[1] = 0.f;
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            sc[2 * m] = 1.f;
+            sc[2 * m + 1] = 0.f;
         }
-        for (int m = threadIdx.x; m < M; m += blockDim.x) sc[2 + m] = 0.f;
         return;
     }
-    // per-subspace minimum: one warp per subspace
+    // per-subspace minimum and maximum: one warp per subspace
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const float fmax = prec == FA_LUT_F16 ? F16_MAX : FP8_MAX;
     for (int m = warp; m < M; m += nw) {
-        float v = INFINITY;
-        for (int c = lane; c < 256; c += 32) v = fminf(v, t[m * 256 + c]);
-        for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) offs[m] = v;
+        float lo = INFINITY, hi = -INFINITY;
+        for (int c = lane; c < 256; c += 32) {
+            lo = fminf(lo, t[m * 256 + c]);
+            hi = fmaxf(hi, t[m * 256 + c]);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        float s = (hi - lo) / fmax;
+        if (!(s > 0.f)) s = 1.f;
+        if (lane == 0) {
+            offs[m] = lo;
+            scl[m] = s;
+            sc[2 * m] = s;
+            sc[2 * m + 1] = lo;
+        }
     }
     __syncthreads();
-    float mx = 0.f;
-    for (int i = threadIdx.x; i < M * 256; i += blockDim.x) mx = fmaxf(mx, t[i] - offs[i >> 8]);
-    mx = block_reduce_max(mx, red);
-    const float fmax = prec == FA_LUT_F16 ? F16_MAX : FP8_MAX;
-    float s = mx / fmax;
-    if (!(s > 0.f)) s = 1.f;
-    const float inv = 1.f / s;
     for (int i = threadIdx.x; i < M * 256; i += blockDim.x) {
-        const float r = fminf((t[i] - offs[i >> 8]) * inv, fmax);
+        const int m = i >> 8;
+        const float r = fminf((t[i] - offs[m]) / scl[m], fmax);
         if (prec == FA_LUT_F16) {
             reinterpret_cast<__half *>(lut)[base + i] = __float2half_rn(r);
         } else {
@@ -77,13 +68,6 @@ __device__ void store_lut(const float *t, int M, int prec, void *lut, float *sca
             reinterpret_cast<uint8_t *>(lut)[base + i] = v.__x;
         }
     }
-    if (threadIdx.x == 0) {
-        float so = 0.f;
-        for (int m = 0; m < M; ++m) so += offs[m];
-        sc[0] = s;
-        sc[1] = so;
-    }
-    for (int m = threadIdx.x; m < M; m += blockDim.x) sc[2 + m] = offs[m];
 }
 
 // FP32 direct differences, one CTA per query.
@@ -94,7 +78,7 @@ __global__ void __launch_bounds__(256) k_lut_simt(const float *__restrict__ q, i
     float *t = sm;                 // [M][256]
     float *qv = t + M * 256;       // [d]
     float *offs = qv + d;          // [M]
-    __shared__ float red[32];
+    float *scl = offs + M;         // [M]
     const int dsub = d / M;
     for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
         for (int j = threadIdx.x; j < d; j += blockDim.x) qv[j] = q[qi * d + j];
@@ -110,22 +94,22 @@ __global__ void __launch_bounds__(256) k_lut_simt(const float *__restrict__ q, i
             t[i] = s;
         }
         __syncthreads();
-        store_lut(t, M, prec, lut, scale, qi, red, offs);
+        store_lut(t, M, prec, lut, scale, qi, offs, scl);
         __syncthreads();
     }
 }
 
 void launch_lut_tc(const DeviceIndex &ix, const float *q, int64_t nq, int prec, void *lut,
-                   float *lut_scale, cudaStream_t st);
+                   float *lut_scale, uint32_t *err, cudaStream_t st);
 
 void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int prec, int gemm,
-                       void *lut, float *lut_scale, cudaStream_t st) {
+                       void *lut, float *lut_scale, uint32_t *err, cudaStream_t st) {
     if (nq == 0) return;
     if (gemm == FA_GEMM_BF16_TC) {
-        launch_lut_tc(ix, q, nq, prec, lut, lut_scale, st);
+        launch_lut_tc(ix, q, nq, prec, lut, lut_scale, err, st);
         return;
     }
-    const int smem = (ix.M * 256 + ix.d + ix.M) * 4;
+    const int smem = (ix.M * 256 + ix.d + 2 * ix.M) * 4;
     FA_CHECK_CUDA(cudaFuncSetAttribute(k_lut_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int grid = (int)std::min<int64_t>(nq, (int64_t)num_sms(0) * 4);
     k_lut_simt<<<grid, 256, smem, st>>>(q, nq, ix.d, ix.codebooks, ix.M, prec, lut, lut_scale);

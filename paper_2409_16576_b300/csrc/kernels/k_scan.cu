@@ -97,13 +97,13 @@ struct ScanPtrs {
 
 __device__ __forceinline__ float lut_entry_global(const ScanArgs &a, int64_t qi, int m, int c) {
     const int64_t base = qi * (int64_t)a.M * 256 + (int64_t)m * 256 + c;
-    const float *sc = a.lut_scale + qi * (2 + a.M);
+    const float *sc = a.lut_scale + qi * 2 * a.M + 2 * m;  // (scale, offset) of subspace m
     if (a.lut_prec == FA_LUT_F32) return reinterpret_cast<const float *>(a.lut)[base];
     if (a.lut_prec == FA_LUT_F16)
-        return __half2float(reinterpret_cast<const __half *>(a.lut)[base]) * sc[0] + sc[2 + m];
+        return __half2float(reinterpret_cast<const __half *>(a.lut)[base]) * sc[0] + sc[1];
     __nv_fp8_e4m3 v;
     v.__x = reinterpret_cast<const uint8_t *>(a.lut)[base];
-    return float(v) * sc[0] + sc[2 + m];
+    return float(v) * sc[0] + sc[1];
 }
 
 // Builds the LUT of query qi in shared memory (rows of W floats; entry
