@@ -115,21 +115,84 @@ def test_lut_f32_matches_oracle(fa, f32_small):
         np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-2)
 
 
+def _expanded_magnitude(q, cb):
+    """|q_m|^2 + |C_m[c]|^2 per entry: the size of the terms the expanded
+    (tensor-core) form adds, which bounds its rounding."""
+    M, _, dsub = cb.shape
+    qn = np.array([(q[m * dsub:(m + 1) * dsub].astype(np.float64) ** 2).sum() for m in range(M)])
+    return qn[:, None] + (cb.astype(np.float64) ** 2).sum(2)
+
+
+@pytest.mark.parametrize("which", ["f32", "u8"])
+def test_lut_tc_matches_oracle(fa, f32_small, u8_repl, which):
+    """BF16 tensor-core LUT (hi/lo split, FP32 accumulation) against the FP64
+    table: within 4e-5 of the magnitude of the expanded form's terms."""
+    s = f32_small if which == "f32" else u8_repl
+    p = fa.search_params(lut_gemm=fa.FA_GEMM_BF16_TC)
+    for i in range(4):
+        got = fa.fa_debug_lut(s["ix"], s["q"][i], p).astype(np.float64)
+        ref = oracle.lut(s["q"][i], s["parts"]["codebooks"])
+        tol = 4e-5 * _expanded_magnitude(s["q"][i], s["parts"]["codebooks"]) + 1e-3
+        assert np.all(np.abs(got - ref) <= tol), np.max(np.abs(got - ref) - tol)
+
+
+@pytest.mark.parametrize("gemm", ["SIMT_F32", "BF16_TC"])
 @pytest.mark.parametrize("prec,rel", [("F16", 2.0 ** -11), ("FP8", 2.0 ** -4)])
-def test_lut_lowp_error_bound(fa, u8_repl, prec, rel):
+def test_lut_lowp_error_bound(fa, u8_repl, prec, rel, gemm):
     """FP16 / FP8 table: each entry is within half a unit in the last place of
-    its stored residual (times the per-query scale) of the FP64 value."""
+    its stored residual (times its subspace's scale) of the FP64 value, plus
+    the tensor-core form's rounding when the table comes from the GEMM."""
     s = u8_repl
-    p = fa.search_params(lut_prec=getattr(fa, "FA_LUT_" + prec))
+    p = fa.search_params(lut_prec=getattr(fa, "FA_LUT_" + prec), lut_gemm=getattr(fa, "FA_GEMM_" + gemm))
     for i in range(4):
         got = fa.fa_debug_lut(s["ix"], s["q"][i], p).astype(np.float64)
         ref = oracle.lut(s["q"][i], s["parts"]["codebooks"])
         resid = ref - ref.min(axis=1, keepdims=True)
         # half-ulp of the stored value (relative), an FP32 rounding margin, and
         # the FP8 subnormal step (2^-9 of the scale) for tiny residuals
-        scale = resid.max() / (65504.0 if prec == "F16" else 448.0)
+        scale = resid.max(axis=1, keepdims=True) / (65504.0 if prec == "F16" else 448.0)
         bound = resid * rel + 1e-5 * np.abs(ref) + scale * (2.0 ** -9 if prec == "FP8" else 2.0 ** -24) + 1e-3
+        if gemm == "BF16_TC":
+            bound = bound + 4e-5 * _expanded_magnitude(s["q"][i], s["parts"]["codebooks"]) * (1 + rel)
         assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) - bound)
+
+
+@pytest.mark.parametrize("prec,gemm", [("F32", "SIMT_F32"), ("F16", "SIMT_F32"), ("FP8", "SIMT_F32"),
+                                       ("F32", "BF16_TC"), ("F16", "BF16_TC"), ("FP8", "BF16_TC")])
+def test_adc_equals_sum_of_lut_entries(fa, u8_repl, prec, gemm):
+    """Invariant of Eq. 1: every returned ADC distance is the sum of the M
+    entries of the query's table (as the scan reads it) picked by the
+    vector's codes, up to FP32 summation order."""
+    s = u8_repl
+    p = fa.search_params(lut_prec=getattr(fa, "FA_LUT_" + prec), lut_gemm=getattr(fa, "FA_GEMM_" + gemm))
+    q = s["q"][:8]
+    probes = oracle.coarse(q, s["parts"]["centroids"], 8)
+    gi, gd = fa.fa_search_ex(s["ix"], q, 50, 8, p, probes=probes)
+    codes = s["parts"]["codes"]
+    M = codes.shape[1]
+    for i in range(q.shape[0]):
+        lut = fa.fa_debug_lut(s["ix"], q[i], p).astype(np.float64)
+        ok = gi[i] >= 0
+        ref = lut[np.arange(M)[None, :], codes[gi[i][ok]]].sum(1)
+        np.testing.assert_allclose(gd[i][ok], ref, rtol=2e-6, atol=1e-3)
+
+
+@pytest.mark.parametrize("which", ["f32", "u8"])
+def test_coarse_probe_tc_matches_oracle(fa, f32_small, u8_repl, which):
+    """Tensor-core coarse probe: the oracle's probe list except where the
+    boundary distances are closer than the expanded form's rounding."""
+    s = f32_small if which == "f32" else u8_repl
+    npb = 8
+    got = fa.fa_debug_probes(s["ix"], s["q"], npb, fa.search_params(probe_gemm=fa.FA_GEMM_BF16_TC))
+    ref, d2 = oracle.coarse(s["q"], s["parts"]["centroids"], npb + 4, with_d2=True)
+    cent = s["parts"]["centroids"].astype(np.float64)
+    for i in range(s["q"].shape[0]):
+        if got[i].tolist() == ref[i, :npb].tolist():
+            continue
+        mag = (s["q"][i].astype(np.float64) ** 2).sum() + (cent ** 2).sum(1).max()
+        gd2 = ((cent[got[i]] - s["q"][i].astype(np.float64)) ** 2).sum(1)
+        # every chosen list is within the rounding of the boundary distance
+        assert np.all(gd2 <= d2[i, npb - 1] + 4e-5 * mag), i
 
 
 # ---------------------------------------------------------------------------
