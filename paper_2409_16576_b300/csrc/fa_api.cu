@@ -242,7 +242,7 @@ void upload_index(fa_index *ix) {
 // workspace pool
 // ---------------------------------------------------------------------------
 static void ws_free_buffers(Workspace *w) {
-    void *dp[] = {w->q, w->probes, w->kq, w->npq, w->topkeys, w->out_ids, w->out_dist,
+    void *dp[] = {w->q, w->probes, w->kq, w->npq, w->order, w->bucket, w->topkeys, w->out_ids, w->out_dist,
                   w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr};
     for (void *p : dp)
         if (p) cudaFree(p);
@@ -250,7 +250,8 @@ static void ws_free_buffers(Workspace *w) {
     for (void *p : hp)
         if (p) cudaFreeHost(p);
     w->q = nullptr;
-    w->probes = w->kq = w->npq = nullptr;
+    w->probes = w->kq = w->npq = w->order = nullptr;
+    w->bucket = nullptr;
     w->topkeys = nullptr;
     w->out_ids = nullptr;
     w->out_dist = nullptr;
@@ -291,6 +292,8 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
     dalloc(w->probes, (size_t)cq * cp);
     dalloc(w->kq, (size_t)cq);
     dalloc(w->npq, (size_t)cq);
+    dalloc(w->order, (size_t)cq);
+    dalloc(w->bucket, (size_t)D.nlist);
     dalloc(w->topkeys, (size_t)cq * ct);
     dalloc(w->out_ids, (size_t)cq * ck);
     dalloc(w->out_dist, (size_t)cq * ck);
@@ -486,6 +489,9 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     sl.err = w->err;
     sl.tile_ctr = w->tile_ctr;
     sl.persistent = (sp.flags & FA_PERSISTENT) ? 1 : 0;
+    launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
+    tr.launches += 3;
+    sl.order = w->order;
     if (sl.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
     if (sp.stats) FA_CHECK_CUDA(cudaMemsetAsync(w->stats, 0, sizeof(int32_t) * 4 * nq, st));
     launch_scan(D, sl, st);

@@ -102,6 +102,8 @@ struct Workspace {
     int32_t *probes = nullptr;     // [cap_nq][cap_nprobe]
     int32_t *kq = nullptr;         // [cap_nq]
     int32_t *npq = nullptr;        // [cap_nq]
+    int32_t *order = nullptr;      // [cap_nq] scan order
+    uint32_t *bucket = nullptr;    // [nlist] counting-sort buckets
     uint64_t *topkeys = nullptr;   // [cap_nq][cap_ntop]
     int64_t *out_ids = nullptr;    // [cap_nq][cap_k]
     float *out_dist = nullptr;     // [cap_nq][cap_k]
@@ -190,6 +192,7 @@ struct ScanLaunch {
     uint32_t *err;
     int persistent;
     uint32_t *tile_ctr;
+    const int32_t *order;    // [nq] processing order (queries grouped by first probe), or null
 };
 
 void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
@@ -202,6 +205,8 @@ void prepare_codebook_tiles(const float *cb, int32_t M, int32_t d, std::vector<u
                             std::vector<float> &norms);
 void launch_coarse_tc_dist(const DeviceIndex &ix, const float *q, int64_t rows, float *D,
                            int64_t ldd, uint32_t *err, cudaStream_t st);
+void launch_query_order(const int32_t *probes, int64_t nq, int32_t stride, int32_t nlist,
+                        uint32_t *cnt, int32_t *order, cudaStream_t st);
 void launch_scan(const DeviceIndex &ix, const ScanLaunch &a, cudaStream_t st);
 void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int prec, int gemm,
                        void *lut, float *lut_scale, uint32_t *err, cudaStream_t st);

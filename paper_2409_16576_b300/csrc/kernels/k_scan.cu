@@ -24,6 +24,8 @@
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
+
 #include "../fa_internal.h"
 #include "warp_topk.cuh"
 
@@ -63,6 +65,7 @@ struct ScanArgs {
     uint32_t *err;
     uint32_t *tile_ctr;
     int32_t persistent;
+    const int32_t *order;  // [nq] processing order, or null
 };
 
 // Shared memory plan (bytes), shared by host and device. `tail` is the
@@ -278,8 +281,13 @@ __device__ __forceinline__ void write_stats(const ScanArgs &a, const ScanPtrs &S
     a.stats[qi * 4 + 1] = (int32_t)kept;
 }
 
+// Next work slot of this CTA; slot i scans query order[i] (queries grouped by
+// their nearest list so that CTAs running together share probed lists in L2).
 __device__ __forceinline__ int64_t next_query(const ScanArgs &a, int64_t it) {
-    return a.persistent ? (int64_t)atomicAdd(a.tile_ctr, 1u) : (int64_t)blockIdx.x + it * gridDim.x;
+    const int64_t slot =
+        a.persistent ? (int64_t)atomicAdd(a.tile_ctr, 1u) : (int64_t)blockIdx.x + it * gridDim.x;
+    if (slot >= a.nq) return a.nq;
+    return a.order ? (int64_t)a.order[slot] : slot;
 }
 
 // ---------------------------------------------------------------------------
@@ -591,6 +599,7 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     a.err = l.err;
     a.tile_ctr = l.tile_ctr;
     a.persistent = l.persistent;
+    a.order = l.order;
     switch (ix.M) {
         case 8: launch_scan_m<8, 64>(a, l, st); break;
         case 16: launch_scan_m<16, 64>(a, l, st); break;
@@ -599,6 +608,76 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
         case 64: launch_scan_m<64, 128>(a, l, st); break;
         default: FA_REQUIRE(false, FA_ERR_ARG, "M must be one of 8, 16, 32, 48, 64");
     }
+}
+
+// ---------------------------------------------------------------------------
+// Processing order: queries bucketed by their nearest (first) probed list.
+// Counting sort: histogram, exclusive scan, scatter. The order inside a
+// bucket depends on atomics, which does not matter: every query is scanned
+// whole by one CTA, whatever its slot.
+// ---------------------------------------------------------------------------
+__global__ void k_order_hist(const int32_t *probes, int64_t nq, int32_t stride, int32_t nlist,
+                             uint32_t *cnt) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int l = probes[q * stride];
+        atomicAdd(&cnt[(l >= 0 && l < nlist) ? l : 0], 1u);
+    }
+}
+
+__global__ void k_order_scan(uint32_t *cnt, int32_t nlist) {
+    // one CTA of 1024 threads: exclusive scan in place, chunk by chunk
+    __shared__ uint32_t part[32];
+    __shared__ uint32_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < nlist; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        const uint32_t v = i < nlist ? cnt[i] : 0u;
+        uint32_t inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) part[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t p = lane < (int)(blockDim.x >> 5) ? part[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, p, o);
+                if (lane >= o) p += y;
+            }
+            part[lane] = p;
+        }
+        __syncthreads();
+        const uint32_t excl = carry + (warp ? part[warp - 1] : 0u) + inc - v;
+        if (i < nlist) cnt[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+}
+
+__global__ void k_order_scatter(const int32_t *probes, int64_t nq, int32_t stride, int32_t nlist,
+                                uint32_t *off, int32_t *order) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int l = probes[q * stride];
+        const uint32_t p = atomicAdd(&off[(l >= 0 && l < nlist) ? l : 0], 1u);
+        order[p] = (int32_t)q;
+    }
+}
+
+void launch_query_order(const int32_t *probes, int64_t nq, int32_t stride, int32_t nlist,
+                        uint32_t *cnt, int32_t *order, cudaStream_t st) {
+    if (nq == 0) return;
+    FA_CHECK_CUDA(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (size_t)nlist, st));
+    const int grid = (int)std::min<int64_t>((nq + 255) / 256, 4096);
+    k_order_hist<<<grid, 256, 0, st>>>(probes, nq, stride, nlist, cnt);
+    k_order_scan<<<1, 1024, 0, st>>>(cnt, nlist);
+    k_order_scatter<<<grid, 256, 0, st>>>(probes, nq, stride, nlist, cnt, order);
+    FA_CHECK_CUDA(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------
