@@ -305,6 +305,8 @@ def main():
 
     lowp = args.form == "lowp"
     sp = search_params(fa, args.form, wl, args.persistent)
+    # autotuner: scan launch shape timed on a 2k-query sample of the batch
+    tuned = fa.fa_autotune(ix, queries[:2000], k, wl["nprobe"], sp)["chosen"]
     oid = torch.empty((nq, k), dtype=torch.int64, device="cuda")
     odist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
 
@@ -382,7 +384,9 @@ def main():
                            wl["batch"], wl["eps"], wl["beta"]) if lowp else "none",
                        "raw_vectors": ("HBM" if args.raw == "device" else "pinned host")
                        if lowp else "none",
-                       "launch": "persistent" if args.persistent else "one CTA per query",
+                       "launch": "autotuned: %d threads/CTA, %d chunk(s) in flight per warp, %s" % (
+                           tuned["threads"], tuned["ilp"],
+                           "persistent" if (tuned["persistent"] or args.persistent) else "one CTA per query"),
                        "l2": "flushed between timed steps (256 MB write); codes 320 MB > L2",
                        "parallelism": "replicas" if world > 1 else "single"},
             "recall_at_10": recall,

@@ -209,6 +209,22 @@ fa_status fa_search_ex(fa_index *ix, const float *queries, int64_t nq, int32_t d
                        int32_t nprobe, const fa_search_params *sp, int64_t *out_ids,
                        float *out_dist);
 
+/* Autotuning of the scan launch (the batching form's tile shape). */
+typedef struct fa_tune_result {
+    int32_t variants, chosen;         /* variants timed; index of the fastest */
+    int32_t threads[8], ilp[8], persistent[8];
+    float ms[8];                      /* median device time of the scan stage */
+} fa_tune_result;
+
+/* Times every launch shape of the ADC scan (threads per CTA 256 / 512, one or
+ * two 32-candidate chunks in flight per warp, one CTA per query or persistent
+ * CTAs pulling queries from a counter) on the given host queries with the
+ * given parameters, and keeps the fastest in the index for later calls of the
+ * same class (top-n above or below 256, LUT in the scan CTA or in HBM). Calls
+ * made before tuning use 256 threads, one chunk, one CTA per query. */
+fa_status fa_autotune(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
+                      int32_t nprobe, const fa_search_params *sp, fa_tune_result *out);
+
 /* ------------------------------------------------------------------------- */
 /* Test hooks (host buffers)                                                 */
 /* ------------------------------------------------------------------------- */

@@ -59,6 +59,11 @@ class fa_search_trace(C.Structure):
                 ("total_ms", f32), ("launches", i32)]
 
 
+class fa_tune_result(C.Structure):
+    _fields_ = [("variants", i32), ("chosen", i32), ("threads", i32 * 8), ("ilp", i32 * 8),
+                ("persistent", i32 * 8), ("ms", f32 * 8)]
+
+
 class fa_search_params(C.Structure):
     _fields_ = [("lut_prec", i32), ("lut_gemm", i32), ("probe_gemm", i32), ("rerank_n", i32),
                 ("rerank_batch", i32), ("rerank_beta", i32), ("rerank_eps", f32), ("flags", i32),
@@ -84,6 +89,7 @@ _sig("fa_load_index", i32, C.c_char_p, i32, P)
 _sig("fa_free_index", None, P)
 _sig("fa_search", i32, P, P, i64, i32, i32, i32, P, P)
 _sig("fa_search_ex", i32, P, P, i64, i32, i32, i32, P, P, P)
+_sig("fa_autotune", i32, P, P, i64, i32, i32, i32, P, P)
 _sig("fa_debug_probes", i32, P, P, i64, i32, P, P)
 _sig("fa_debug_candidates", i32, P, P, i32, P, P, i64, P)
 _sig("fa_debug_lut", i32, P, P, P, P)
@@ -95,7 +101,7 @@ _sig("fa_version", C.c_char_p)
 # every symbol include/fa.h declares
 EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_index_from_parts", "fa_index_get_parts",
            "fa_index_info_get", "fa_save_index", "fa_load_index", "fa_free_index",
-           "fa_search_params_init", "fa_search", "fa_search_ex", "fa_debug_probes",
+           "fa_search_params_init", "fa_search", "fa_search_ex", "fa_autotune", "fa_debug_probes",
            "fa_debug_candidates", "fa_debug_lut", "fa_coarse_probe_noalloc", "fa_last_error",
            "fa_status_str", "fa_version")
 
@@ -299,6 +305,18 @@ def fa_search_ex(ix: Index, queries, k: int, nprobe: int, params: fa_search_para
     _check(_lib.fa_search_ex(ix.handle, _ptr(queries), nq, d, k, nprobe, C.byref(sp),
                              _ptr(out_ids), _ptr(out_dist)))
     return (out_ids, out_dist, st) if stats else (out_ids, out_dist)
+
+
+def fa_autotune(ix: Index, queries: np.ndarray, k: int, nprobe: int, params=None) -> dict:
+    """Times the scan's launch shapes on host queries and keeps the fastest in
+    the index; returns the timings and the choice."""
+    q = np.ascontiguousarray(queries, dtype=np.float32)
+    r = fa_tune_result()
+    _check(_lib.fa_autotune(ix.handle, _ptr(q), q.shape[0], q.shape[1], k, nprobe,
+                            C.byref(params) if params is not None else None, C.byref(r)))
+    rows = [dict(threads=r.threads[i], ilp=r.ilp[i], persistent=r.persistent[i], scan_ms=r.ms[i])
+            for i in range(r.variants)]
+    return dict(variants=rows, chosen=rows[r.chosen])
 
 
 def fa_debug_probes(ix: Index, queries: np.ndarray, nprobe: int, params=None) -> np.ndarray:

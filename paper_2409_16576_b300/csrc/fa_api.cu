@@ -396,7 +396,7 @@ struct Tracer {
 
 static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
                         int32_t nprobe, const fa_search_params *spp, int64_t *out_ids,
-                        float *out_dist) {
+                        float *out_dist, const Tune *force = nullptr) {
     fa_search_params sp;
     if (spp)
         sp = *spp;
@@ -488,7 +488,19 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     sl.stats = sp.stats ? w->stats : nullptr;
     sl.err = w->err;
     sl.tile_ctr = w->tile_ctr;
-    sl.persistent = (sp.flags & FA_PERSISTENT) ? 1 : 0;
+    {
+        Tune t;
+        if (force) {
+            t = *force;
+        } else {
+            std::lock_guard<std::mutex> lk(ix->mu);
+            const Tune &c = ix->tune[tune_class(ntop, global_lut)];
+            if (c.set) t = c;
+        }
+        sl.threads = t.threads;
+        sl.ilp = t.ilp;
+        sl.persistent = ((sp.flags & FA_PERSISTENT) || t.persistent) ? 1 : 0;
+    }
     launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
     tr.launches += 3;
     sl.order = w->order;
@@ -896,6 +908,78 @@ fa_status fa_search_ex(fa_index *ix, const float *queries, int64_t nq, int32_t d
         return FA_ERR_ARG;
     }
     return guarded(ix, [&] { search_impl(ix, queries, nq, d, k, nprobe, sp, out_ids, out_dist); });
+}
+
+fa_status fa_autotune(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
+                      int32_t nprobe, const fa_search_params *spp, fa_tune_result *out) {
+    if (!ix || !out) {
+        set_error("null argument");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] {
+        FA_REQUIRE(nq >= 1 && queries, FA_ERR_ARG, "autotuning needs at least one query");
+        fa_search_params sp;
+        if (spp) sp = *spp; else fa_search_params_init(&sp);
+        FA_REQUIRE(!(sp.flags & (FA_QUERIES_ON_DEVICE | FA_OUTPUTS_ON_DEVICE)), FA_ERR_ARG,
+                   "autotuning takes host queries");
+        sp.flags &= ~FA_PERSISTENT;
+        sp.stats = nullptr;
+        const int32_t ntop = sp.rerank_n > 0 ? std::max(sp.rerank_n, k) : k;
+        const bool global_lut = sp.lut_prec != FA_LUT_F32 || sp.lut_gemm == FA_GEMM_BF16_TC;
+        std::vector<Tune> variants;
+        for (int per = 0; per < 2; ++per) {
+            if (ntop > 256) {
+                Tune t;
+                t.persistent = per;
+                variants.push_back(t);
+                continue;
+            }
+            for (int th : {256, 512})
+                for (int ilp : {1, 2}) {
+                    Tune t;
+                    t.threads = th;
+                    t.ilp = ilp;
+                    t.persistent = per;
+                    variants.push_back(t);
+                }
+        }
+        std::vector<int64_t> ids((size_t)nq * k);
+        std::vector<float> dist((size_t)nq * k);
+        fa_search_trace tr;
+        sp.trace = &tr;
+        memset(out, 0, sizeof *out);
+        int best = -1;
+        std::vector<int64_t> ref_ids;
+        std::vector<float> ref_dist;
+        for (size_t v = 0; v < variants.size() && v < 8; ++v) {
+            search_impl(ix, queries, nq, d, k, nprobe, &sp, ids.data(), dist.data(), &variants[v]);
+            // every launch shape must return the same rows, bit for bit
+            if (v == 0) {
+                ref_ids = ids;
+                ref_dist = dist;
+            } else if (ids != ref_ids || memcmp(dist.data(), ref_dist.data(), 4 * dist.size()) != 0) {
+                throw Error{FA_ERR_STATE, "scan launch shapes disagree (variant " +
+                                              std::to_string(v) + ")"};
+            }
+            float t3[3];
+            for (int r = 0; r < 3; ++r) {
+                search_impl(ix, queries, nq, d, k, nprobe, &sp, ids.data(), dist.data(), &variants[v]);
+                t3[r] = tr.scan_ms;
+            }
+            std::sort(t3, t3 + 3);
+            out->ms[v] = t3[1];
+            out->threads[v] = variants[v].threads;
+            out->ilp[v] = variants[v].ilp;
+            out->persistent[v] = variants[v].persistent;
+            if (best < 0 || t3[1] < out->ms[best]) best = (int)v;
+        }
+        out->variants = (int32_t)std::min<size_t>(variants.size(), 8);
+        out->chosen = best;
+        Tune t = variants[best];
+        t.set = true;
+        std::lock_guard<std::mutex> lk(ix->mu);
+        ix->tune[tune_class(ntop, global_lut)] = t;
+    });
 }
 
 fa_status fa_search(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,

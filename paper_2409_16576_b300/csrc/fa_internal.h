@@ -125,6 +125,13 @@ struct Workspace {
     int32_t h_cap_k = 0;
 };
 
+struct Tune {  // scan launch shape chosen by the autotuner for one class of calls
+    int threads = 256, ilp = 1, persistent = 0;
+    bool set = false;
+};
+// class of a call: top-n above 256 (CTA variant) x LUT built in the scan / read from HBM
+inline int tune_class(int ntop, bool global_lut) { return (ntop > 256 ? 2 : 0) + (global_lut ? 1 : 0); }
+
 }  // namespace fa
 
 struct fa_index {
@@ -146,6 +153,7 @@ struct fa_index {
     std::vector<fa::Workspace *> all_ws, free_ws;
     int max_ws = 8;
     std::atomic<int> sticky{0};
+    fa::Tune tune[4];  // autotuned scan launch per call class
 };
 
 namespace fa {
@@ -193,7 +201,10 @@ struct ScanLaunch {
     int persistent;
     uint32_t *tile_ctr;
     const int32_t *order;    // [nq] processing order (queries grouped by first probe), or null
+    int threads = 256;       // warp-top-n variant: threads per CTA (256 or 512)
+    int ilp = 1;             // chunks in flight per warp (1 or 2)
 };
+
 
 void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
                    int32_t probe_stride, int gemm, Workspace &ws, int32_t *probes,

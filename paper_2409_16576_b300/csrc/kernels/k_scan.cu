@@ -293,12 +293,15 @@ __device__ __forceinline__ int64_t next_query(const ScanArgs &a, int64_t it) {
 // ---------------------------------------------------------------------------
 // Variant 1: n <= 256. Each warp keeps its own top-n in registers; the warps
 // share the best n-th key seen by any of them as a common filter threshold.
-// Code rows of the next chunk are loaded while the current one is scanned.
+// A warp works on ILP chunks at a time and loads the code rows of its next
+// ILP chunks while scanning the current ones. NT (threads per CTA) and ILP
+// are picked per index by the autotuner.
 // ---------------------------------------------------------------------------
-template <int M, int W, int R>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan(const ScanArgs a) {
+template <int M, int W, int R, int NT, int ILP>
+__global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a) {
+    constexpr int NWARP = NT / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, SCAN_WARPS * 64 * 8);
+    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, NWARP * 64 * 8);
     const ScanPtrs S(smem, plan, a.nprobe);
     uint64_t *wbuf = reinterpret_cast<uint64_t *>(S.tail);
     __shared__ int64_t s_q;
@@ -327,26 +330,41 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const ScanArgs a) {
         const uint32_t total = S.pref[2 * np];
         uint32_t kept = 0;
         int sg = 0;
-        uint32_t g = warp;
-        uint32_t vc = 0;
-        bool okc = false;
-        uint32_t wc[NW];
-        if (g < total) locate(a, S, np, g, sg, vc, okc);
-        load_codes<M>(a.codes, vc, okc && g < total, wc);
-        for (; g < total; g += SCAN_WARPS) {
-            const uint32_t gn = g + SCAN_WARPS;
-            uint32_t vn = 0;
-            bool okn = false;
-            if (gn < total) locate(a, S, np, gn, sg, vn, okn);
-            uint32_t wn[NW];
-            load_codes<M>(a.codes, vn, okn, wn);
-            const float dist = adc_words<M, W>(wc, vc, S.lut);
-            kept += okc ? 1u : 0u;
-            tk.push(make_key(dist, vc), okc);
-            vc = vn;
-            okc = okn;
+        uint32_t vc[ILP];
+        bool okc[ILP];
+        uint32_t wc[ILP][NW];
 #pragma unroll
-            for (int i = 0; i < NW; ++i) wc[i] = wn[i];
+        for (int j = 0; j < ILP; ++j) {
+            const uint32_t gj = warp + j * NWARP;
+            vc[j] = 0;
+            okc[j] = false;
+            if (gj < total) locate(a, S, np, gj, sg, vc[j], okc[j]);
+            load_codes<M>(a.codes, vc[j], okc[j], wc[j]);
+        }
+        for (uint32_t g = warp; g < total; g += ILP * NWARP) {
+            uint32_t vn[ILP];
+            bool okn[ILP];
+            uint32_t wn[ILP][NW];
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) {
+                const uint32_t gn = g + (ILP + j) * NWARP;
+                vn[j] = 0;
+                okn[j] = false;
+                if (gn < total) locate(a, S, np, gn, sg, vn[j], okn[j]);
+                load_codes<M>(a.codes, vn[j], okn[j], wn[j]);
+            }
+            float dist[ILP];
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) dist[j] = adc_words<M, W>(wc[j], vc[j], S.lut);
+#pragma unroll
+            for (int j = 0; j < ILP; ++j) {
+                kept += okc[j] ? 1u : 0u;
+                tk.push(make_key(dist[j], vc[j]), okc[j]);
+                vc[j] = vn[j];
+                okc[j] = okn[j];
+#pragma unroll
+                for (int i = 0; i < NW; ++i) wc[j][i] = wn[j][i];
+            }
         }
         tk.finish();
         if (a.stats) {
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan(const ScanArgs a) {
             uint64_t L[R];
 #pragma unroll
             for (int r = 0; r < R; ++r) L[r] = mrg[r * 32 + lane];
-            for (int w = 1; w < SCAN_WARPS; ++w) {
+            for (int w = 1; w < NWARP; ++w) {
                 uint64_t B[R];
 #pragma unroll
                 for (int r = 0; r < R; ++r) B[r] = mrg[w * 32 * R + r * 32 + lane];
@@ -535,23 +553,35 @@ static int scan_grid(const ScanLaunch &l, int smem_total) {
     return (int64_t)grid > l.nq ? (int)l.nq : grid;
 }
 
+template <int M, int W, int R, int NT, int ILP>
+static void launch_warp_variant(const ScanArgs &a, const ScanLaunch &l, cudaStream_t st) {
+    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, (NT / 32) * 64 * 8);
+    FA_REQUIRE((NT / 32) * 32 * R * 8 <= plan.lut, FA_ERR_ARG, "LUT region too small for merge");
+    FA_REQUIRE(plan.total <= 227 * 1024, FA_ERR_ARG, "scan shared memory above 227 KB");
+    const int grid = scan_grid(l, plan.total);
+    set_smem(k_scan<M, W, R, NT, ILP>, plan.total);
+    k_scan<M, W, R, NT, ILP><<<grid, NT, plan.total, st>>>(a);
+}
+
+template <int M, int W, int R>
+static void launch_warp_r(const ScanArgs &a, const ScanLaunch &l, cudaStream_t st) {
+    const bool big = l.threads >= 512;
+    if (l.ilp >= 2) {
+        if (big) launch_warp_variant<M, W, R, 512, 2>(a, l, st);
+        else launch_warp_variant<M, W, R, 256, 2>(a, l, st);
+    } else {
+        if (big) launch_warp_variant<M, W, R, 512, 1>(a, l, st);
+        else launch_warp_variant<M, W, R, 256, 1>(a, l, st);
+    }
+}
+
 template <int M, int W>
 static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t st) {
     if (a.ntop <= 256) {
-        const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, SCAN_WARPS * 64 * 8);
-        FA_REQUIRE(SCAN_WARPS * 256 * 8 <= plan.lut, FA_ERR_ARG, "LUT region too small for merge");
-        FA_REQUIRE(plan.total <= 227 * 1024, FA_ERR_ARG, "scan shared memory above 227 KB");
-        const int grid = scan_grid(l, plan.total);
-#define FA_SCAN(RR)                                                                 \
-    do {                                                                            \
-        set_smem(k_scan<M, W, RR>, plan.total);                                     \
-        k_scan<M, W, RR><<<grid, SCAN_THREADS, plan.total, st>>>(a);                \
-    } while (0)
-        if (a.ntop <= 32) FA_SCAN(1);
-        else if (a.ntop <= 64) FA_SCAN(2);
-        else if (a.ntop <= 128) FA_SCAN(4);
-        else FA_SCAN(8);
-#undef FA_SCAN
+        if (a.ntop <= 32) launch_warp_r<M, W, 1>(a, l, st);
+        else if (a.ntop <= 64) launch_warp_r<M, W, 2>(a, l, st);
+        else if (a.ntop <= 128) launch_warp_r<M, W, 4>(a, l, st);
+        else launch_warp_r<M, W, 8>(a, l, st);
     } else {
         const int NP = pow2_at_least(a.ntop < 2 * BIG_WARPS * 32 ? 2 * BIG_WARPS * 32 : a.ntop);
         const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, 2 * NP * 8);

@@ -287,6 +287,21 @@ def test_persistent_and_device_buffers_match(fa, f32_small):
     assert np.array_equal(gi, di.cpu().numpy()) and np.array_equal(gd, dd.cpu().numpy())
 
 
+@pytest.mark.parametrize("k,rerank", [(10, 0), (100, 0), (10, 600)])
+def test_autotune_variants_agree_and_keep_results(fa, u8_repl, k, rerank):
+    """The autotuner times every scan launch shape (it fails if any returns
+    different rows) and the tuned index returns the same results."""
+    s = u8_repl
+    p = fa.search_params(rerank_n=rerank, rerank_eps=-1.0, lut_prec=fa.FA_LUT_F16,
+                         lut_gemm=fa.FA_GEMM_BF16_TC)
+    before = fa.fa_search_ex(s["ix"], s["q"], k, 16, p)
+    r = fa.fa_autotune(s["ix"], s["q"], k, 16, p)
+    assert len(r["variants"]) == (8 if k + rerank <= 256 else 2)
+    assert all(v["scan_ms"] > 0 for v in r["variants"])
+    after = fa.fa_search_ex(s["ix"], s["q"], k, 16, p)
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+
+
 def test_per_query_k_and_nprobe(fa, f32_small):
     s = f32_small
     q = s["q"][:20]
