@@ -141,7 +141,19 @@ __device__ __forceinline__ void load_codes(const uint8_t *codes, uint32_t v, boo
                                            uint32_t (&w)[M / 4]) {
     const uint8_t *row = codes + (size_t)v * M;
     if (valid) {
-        if (M % 16 == 0) {
+        if (M % 32 == 0) {
+            // one 256-bit load per 32 bytes: a warp reads 32 consecutive rows as
+            // one contiguous span (half the L1 wavefronts of 16-byte loads)
+#pragma unroll
+            for (int i = 0; i < M / 32; ++i) {
+                const uint32_t *p = reinterpret_cast<const uint32_t *>(row) + 8 * i;
+                asm("ld.global.nc.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                    : "=r"(w[8 * i + 0]), "=r"(w[8 * i + 1]), "=r"(w[8 * i + 2]),
+                      "=r"(w[8 * i + 3]), "=r"(w[8 * i + 4]), "=r"(w[8 * i + 5]),
+                      "=r"(w[8 * i + 6]), "=r"(w[8 * i + 7])
+                    : "l"(p));
+            }
+        } else if (M % 16 == 0) {
             const uint4 *p = reinterpret_cast<const uint4 *>(row);
 #pragma unroll
             for (int i = 0; i < M / 16; ++i) {

@@ -45,49 +45,58 @@ __device__ __forceinline__ uint64_t shfl64(uint64_t v, int src) {
 __device__ __forceinline__ uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 __device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a < b ? b : a; }
 
-// One bitonic stage over 32*R keys: compare element e with e ^ stride,
-// ascending where (e & size) == 0.
-template <int R>
-__device__ __forceinline__ void bitonic_stage(uint64_t (&v)[R], int size, int stride) {
+// One bitonic stage over 32*R keys: compare element e with e ^ STRIDE,
+// ascending where (e & SIZE) == 0. SIZE and STRIDE are compile-time constants
+// so that every register index below is static (no local memory).
+template <int R, int SIZE, int STRIDE>
+__device__ __forceinline__ void bitonic_stage(uint64_t (&v)[R]) {
     const int lane = threadIdx.x & 31;
-    if (stride >= 32) {
-        const int rs = stride >> 5;
+    if constexpr (STRIDE >= 32) {
+        constexpr int RS = STRIDE >> 5;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if ((r & rs) == 0) {
-                const bool up = (((r << 5) & size) == 0);
-                uint64_t a = v[r], b = v[r | rs];
-                uint64_t lo = umin64(a, b), hi = umax64(a, b);
+            if ((r & RS) == 0) {
+                const bool up = (((r << 5) & SIZE) == 0);
+                const uint64_t a = v[r], b = v[r | RS];
+                const uint64_t lo = umin64(a, b), hi = umax64(a, b);
                 v[r] = up ? lo : hi;
-                v[r | rs] = up ? hi : lo;
+                v[r | RS] = up ? hi : lo;
             }
         }
     } else {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int e = (r << 5) | lane;
-            const bool up = ((e & size) == 0);
-            uint64_t o = shfl_xor64(v[r], stride);
-            const bool lower = (lane & stride) == 0;
+            const bool up = ((e & SIZE) == 0);
+            const uint64_t o = shfl_xor64(v[r], STRIDE);
+            const bool lower = (lane & STRIDE) == 0;
             v[r] = (lower == up) ? umin64(v[r], o) : umax64(v[r], o);
         }
     }
 }
 
+template <int R, int SIZE, int STRIDE>
+__device__ __forceinline__ void bitonic_stages_from(uint64_t (&v)[R]) {
+    bitonic_stage<R, SIZE, STRIDE>(v);
+    if constexpr (STRIDE > 1) bitonic_stages_from<R, SIZE, STRIDE / 2>(v);
+}
+
+template <int R, int SIZE>
+__device__ __forceinline__ void bitonic_sort_from(uint64_t (&v)[R]) {
+    bitonic_stages_from<R, SIZE, SIZE / 2>(v);
+    if constexpr (SIZE < 32 * R) bitonic_sort_from<R, SIZE * 2>(v);
+}
+
 // Sorts 32*R keys ascending.
 template <int R>
 __device__ __forceinline__ void bitonic_sort(uint64_t (&v)[R]) {
-#pragma unroll
-    for (int size = 2; size <= 32 * R; size <<= 1)
-#pragma unroll
-        for (int stride = size >> 1; stride > 0; stride >>= 1) bitonic_stage<R>(v, size, stride);
+    bitonic_sort_from<R, 2>(v);
 }
 
 // Sorts a bitonic sequence of 32*R keys ascending.
 template <int R>
 __device__ __forceinline__ void bitonic_merge(uint64_t (&v)[R]) {
-#pragma unroll
-    for (int stride = 16 * R; stride > 0; stride >>= 1) bitonic_stage<R>(v, 64 * R, stride);
+    bitonic_stages_from<R, 64 * R, 16 * R>(v);
 }
 
 // L (sorted, 32*R keys) <- the 32*R smallest of L and B (sorted, 32*R keys).
@@ -107,12 +116,14 @@ __device__ __forceinline__ void merge_sorted32(uint64_t (&L)[R], uint64_t b) {
 }
 
 // Element e of a warp-wide array (same value on every lane).
+// (a mask blend rather than a select on e / 32, which the compiler may turn
+// into an indexed array in local memory)
 template <int R>
 __device__ __forceinline__ uint64_t warp_elem(const uint64_t (&v)[R], int e) {
-    uint64_t t = v[0];
+    uint64_t t = 0;
+    const int re = e >> 5;
 #pragma unroll
-    for (int r = 1; r < R; ++r)
-        if ((e >> 5) == r) t = v[r];
+    for (int r = 0; r < R; ++r) t |= v[r] & (0ull - (uint64_t)(re == r));
     return shfl64(t, e & 31);
 }
 
