@@ -203,17 +203,33 @@ __device__ __forceinline__ float adc_words(const uint32_t (&w)[M / 4], uint32_t 
     return acc0 + acc1;
 }
 
+// Segment walk state of one warp: the bounds of its current segment, kept in
+// registers and refreshed only when a chunk crosses into a later segment.
+struct SegCursor {
+    int sg = -1;
+    uint32_t p0 = 0, p1 = 0, beg = 0, end = 0;
+};
+
 // Candidate of this lane in chunk g (32 consecutive entries of one segment):
 // primary segments give internal ids directly; replica entries apply the dedup
-// rule. sg walks forward (chunks of a warp are visited in increasing order).
+// rule. Chunks of a warp are visited in increasing order, so the cursor only
+// moves forward.
 __device__ __forceinline__ void locate(const ScanArgs &a, const ScanPtrs &S, int np, uint32_t g,
-                                       int &sg, uint32_t &v, bool &valid) {
+                                       SegCursor &c, uint32_t &v, bool &valid) {
     const int lane = threadIdx.x & 31;
-    while (g >= S.pref[sg + 1]) ++sg;
-    const uint32_t pos = S.seg_beg[sg] + ((g - S.pref[sg]) << 5) + lane;
-    valid = pos < S.seg_end[sg];
+    if (c.sg < 0 || g >= c.p1) {
+        int sg = c.sg < 0 ? 0 : c.sg;
+        while (g >= S.pref[sg + 1]) ++sg;
+        c.sg = sg;
+        c.p0 = S.pref[sg];
+        c.p1 = S.pref[sg + 1];
+        c.beg = S.seg_beg[sg];
+        c.end = S.seg_end[sg];
+    }
+    const uint32_t pos = c.beg + ((g - c.p0) << 5) + lane;
+    valid = pos < c.end;
     v = pos;
-    if (sg >= np && valid) {
+    if (c.sg >= np && valid) {
         v = a.rep_v[pos];
         const uint32_t mo = a.rep_mo[pos];
         const int t = a.rep_t[pos];
@@ -341,7 +357,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
         tk.sthr = &s_thr;
         const uint32_t total = S.pref[2 * np];
         uint32_t kept = 0;
-        int sg = 0;
+        SegCursor sg;
         uint32_t vc[ILP];
         bool okc[ILP];
         uint32_t wc[ILP][NW];
@@ -502,7 +518,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
 
         const uint32_t total = S.pref[2 * np];
         uint32_t kept = 0;
-        int sg = 0;
+        SegCursor sg;
         for (uint32_t base = 0; base < total; base += BIG_WARPS) {
             const uint32_t g = base + warp;
             if (g < total) {
