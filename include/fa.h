@@ -160,7 +160,8 @@ void fa_free_index(fa_index *ix);
 #define FA_QUERIES_ON_DEVICE 0x1 /* queries is a device pointer */
 #define FA_OUTPUTS_ON_DEVICE 0x2 /* out_ids / out_dist are device pointers */
 #define FA_NONBLOCKING 0x4       /* FA_ERR_BUSY instead of waiting for a slot */
-#define FA_PERSISTENT 0x8        /* batching form: persistent tile kernel */
+#define FA_PERSISTENT 0x8        /* batching form: persistent CTAs over tiles of
+                                  * uneven queries (top-n <= 256) */
 #define FA_NO_SYNC 0x10          /* return without synchronizing sp->stream
                                   * (device outputs only) */
 
@@ -213,15 +214,20 @@ fa_status fa_search_ex(fa_index *ix, const float *queries, int64_t nq, int32_t d
 typedef struct fa_tune_result {
     int32_t variants, chosen;         /* variants timed; index of the fastest */
     int32_t threads[8], ilp[8], persistent[8];
+    int32_t tile_chunks[8];           /* > 0: tiled form, 32-candidate chunks per tile */
     float ms[8];                      /* median device time of the scan stage */
 } fa_tune_result;
 
-/* Times every launch shape of the ADC scan (threads per CTA 256 / 512, one or
- * two 32-candidate chunks in flight per warp, one CTA per query or persistent
- * CTAs pulling queries from a counter) on the given host queries with the
- * given parameters, and keeps the fastest in the index for later calls of the
- * same class (top-n above or below 256, LUT in the scan CTA or in HBM). Calls
- * made before tuning use 256 threads, one chunk, one CTA per query. */
+/* Times the launch shapes of the ADC scan on the given host queries with the
+ * given parameters and keeps the fastest in the index for later calls of the
+ * same class (top-n above or below 256, LUT in the scan CTA or in HBM):
+ *   - one CTA per query: 256 or 512 threads per CTA, one or two 32-candidate
+ *     chunks in flight per warp;
+ *   - the tiled batching form: persistent CTAs pull tiles of T chunks of one
+ *     query (T = 64, 256, 1024), each tile's top-n is merged per query.
+ * Every variant must return the same rows bit for bit (else FA_ERR_STATE).
+ * Calls made before tuning use 256 threads, one chunk, one CTA per query;
+ * FA_PERSISTENT selects the tiled form with T = 256 unless tuned. */
 fa_status fa_autotune(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
                       int32_t nprobe, const fa_search_params *sp, fa_tune_result *out);
 

@@ -61,7 +61,7 @@ class fa_search_trace(C.Structure):
 
 class fa_tune_result(C.Structure):
     _fields_ = [("variants", i32), ("chosen", i32), ("threads", i32 * 8), ("ilp", i32 * 8),
-                ("persistent", i32 * 8), ("ms", f32 * 8)]
+                ("persistent", i32 * 8), ("tile_chunks", i32 * 8), ("ms", f32 * 8)]
 
 
 class fa_search_params(C.Structure):
@@ -314,8 +314,8 @@ def fa_autotune(ix: Index, queries: np.ndarray, k: int, nprobe: int, params=None
     r = fa_tune_result()
     _check(_lib.fa_autotune(ix.handle, _ptr(q), q.shape[0], q.shape[1], k, nprobe,
                             C.byref(params) if params is not None else None, C.byref(r)))
-    rows = [dict(threads=r.threads[i], ilp=r.ilp[i], persistent=r.persistent[i], scan_ms=r.ms[i])
-            for i in range(r.variants)]
+    rows = [dict(threads=r.threads[i], ilp=r.ilp[i], persistent=r.persistent[i],
+                 tile_chunks=r.tile_chunks[i], scan_ms=r.ms[i]) for i in range(r.variants)]
     return dict(variants=rows, chosen=rows[r.chosen])
 
 

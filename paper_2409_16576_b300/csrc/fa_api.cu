@@ -242,7 +242,8 @@ void upload_index(fa_index *ix) {
 // workspace pool
 // ---------------------------------------------------------------------------
 static void ws_free_buffers(Workspace *w) {
-    void *dp[] = {w->q, w->probes, w->kq, w->npq, w->order, w->bucket, w->topkeys, w->out_ids, w->out_dist,
+    void *dp[] = {w->q, w->probes, w->kq, w->npq, w->order, w->bucket, w->tchunks, w->tprefix,
+                  w->tmisc, w->partial, w->topkeys, w->out_ids, w->out_dist,
                   w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr};
     for (void *p : dp)
         if (p) cudaFree(p);
@@ -251,7 +252,9 @@ static void ws_free_buffers(Workspace *w) {
         if (p) cudaFreeHost(p);
     w->q = nullptr;
     w->probes = w->kq = w->npq = w->order = nullptr;
-    w->bucket = nullptr;
+    w->bucket = w->tchunks = w->tprefix = w->tmisc = nullptr;
+    w->partial = nullptr;
+    w->tile_cap = 0;
     w->topkeys = nullptr;
     w->out_ids = nullptr;
     w->out_dist = nullptr;
@@ -294,6 +297,9 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
     dalloc(w->npq, (size_t)cq);
     dalloc(w->order, (size_t)cq);
     dalloc(w->bucket, (size_t)D.nlist);
+    dalloc(w->tchunks, (size_t)cq);
+    dalloc(w->tprefix, (size_t)cq + 1);
+    dalloc(w->tmisc, 4);
     dalloc(w->topkeys, (size_t)cq * ct);
     dalloc(w->out_ids, (size_t)cq * ck);
     dalloc(w->out_dist, (size_t)cq * ck);
@@ -316,6 +322,19 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
     w->cap_nprobe = cp;
     w->cap_ntop = ct;
     w->cap_lut_bytes = cl;
+}
+
+// Per-tile top-n buffer of the tiled form: 16 tiles per query on average,
+// the tile size adapts on the device so the plan always fits.
+static void ws_ensure_partial(Workspace *w, int64_t nq, int32_t ntop) {
+    const int64_t cap = 16 * nq + 1024;
+    if (w->partial && w->tile_cap >= cap && w->cap_ntop >= ntop) return;
+    if (w->pending) FA_CHECK_CUDA(cudaEventSynchronize(w->done));
+    FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
+    if (w->partial) cudaFree(w->partial);
+    w->partial = nullptr;
+    dalloc(w->partial, (size_t)cap * std::max(ntop, w->cap_ntop));
+    w->tile_cap = cap;
 }
 
 struct WsLease {
@@ -473,6 +492,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     tr.mark(2);
 
     ScanLaunch sl{};
+    int tile_chunks = 0;
     sl.q = qd;
     sl.probes = probes;
     sl.npq = npq;
@@ -500,14 +520,32 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         sl.threads = t.threads;
         sl.ilp = t.ilp;
         sl.persistent = ((sp.flags & FA_PERSISTENT) || t.persistent) ? 1 : 0;
+        tile_chunks = t.tile_chunks;
+        if ((sp.flags & FA_PERSISTENT) && tile_chunks == 0) tile_chunks = 256;
+        if (ntop > 256) tile_chunks = 0;  // the CTA-wide top-n runs one CTA per query
     }
-    launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
-    tr.launches += 3;
-    sl.order = w->order;
-    if (sl.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
     if (sp.stats) FA_CHECK_CUDA(cudaMemsetAsync(w->stats, 0, sizeof(int32_t) * 4 * nq, st));
-    launch_scan(D, sl, st);
-    tr.launches += 1;
+    if (tile_chunks > 0) {
+        // batching form: uneven queries split into tiles of chunks, planned on the device
+        ws_ensure_partial(w, nq, ntop);
+        launch_tile_plan(D, probes, npq, nq, nprobe, nprobe, (uint32_t)tile_chunks,
+                         (uint32_t)w->tile_cap, w->tchunks,
+                         reinterpret_cast<unsigned long long *>(w->tmisc + 2), w->tmisc, w->tprefix, st);
+        sl.tile_prefix = w->tprefix;
+        sl.tile_T = w->tmisc;
+        sl.partial = w->partial;
+        sl.persistent = 1;
+        FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
+        launch_scan(D, sl, st);
+        launch_tile_merge(w->partial, w->tprefix, nq, ntop, w->topkeys, st);
+        tr.launches += 4;
+    } else {
+        launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
+        sl.order = w->order;
+        if (sl.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
+        launch_scan(D, sl, st);
+        tr.launches += 4;
+    }
     tr.mark(3);
 
     int64_t *oid = odev ? out_ids : w->out_ids;
@@ -927,21 +965,31 @@ fa_status fa_autotune(fa_index *ix, const float *queries, int64_t nq, int32_t d,
         const int32_t ntop = sp.rerank_n > 0 ? std::max(sp.rerank_n, k) : k;
         const bool global_lut = sp.lut_prec != FA_LUT_F32 || sp.lut_gemm == FA_GEMM_BF16_TC;
         std::vector<Tune> variants;
-        for (int per = 0; per < 2; ++per) {
-            if (ntop > 256) {
+        if (ntop > 256) {
+            for (int per = 0; per < 2; ++per) {
                 Tune t;
                 t.persistent = per;
                 variants.push_back(t);
-                continue;
             }
+        } else {
+            // one CTA per query: threads x chunks in flight
             for (int th : {256, 512})
                 for (int ilp : {1, 2}) {
                     Tune t;
                     t.threads = th;
                     t.ilp = ilp;
-                    t.persistent = per;
                     variants.push_back(t);
                 }
+            // tiled persistent form: tile size in 32-candidate chunks
+            const int tiles[4][3] = {{256, 2, 64}, {256, 2, 256}, {256, 2, 1024}, {512, 1, 256}};
+            for (auto &v : tiles) {
+                Tune t;
+                t.threads = v[0];
+                t.ilp = v[1];
+                t.persistent = 1;
+                t.tile_chunks = v[2];
+                variants.push_back(t);
+            }
         }
         std::vector<int64_t> ids((size_t)nq * k);
         std::vector<float> dist((size_t)nq * k);
@@ -971,6 +1019,7 @@ fa_status fa_autotune(fa_index *ix, const float *queries, int64_t nq, int32_t d,
             out->threads[v] = variants[v].threads;
             out->ilp[v] = variants[v].ilp;
             out->persistent[v] = variants[v].persistent;
+            out->tile_chunks[v] = variants[v].tile_chunks;
             if (best < 0 || t3[1] < out->ms[best]) best = (int)v;
         }
         out->variants = (int32_t)std::min<size_t>(variants.size(), 8);

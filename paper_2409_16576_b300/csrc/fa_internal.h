@@ -103,6 +103,11 @@ struct Workspace {
     int32_t *kq = nullptr;         // [cap_nq]
     int32_t *npq = nullptr;        // [cap_nq]
     int32_t *order = nullptr;      // [cap_nq] scan order
+    uint32_t *tchunks = nullptr;   // [cap_nq] chunks per query (tiled form)
+    uint32_t *tprefix = nullptr;   // [cap_nq + 1] tiles per query prefix
+    uint32_t *tmisc = nullptr;     // [4]: chunks per tile, total chunks (u64)
+    uint64_t *partial = nullptr;   // [tile_cap][cap_ntop] per-tile top-n
+    int64_t tile_cap = 0;
     uint32_t *bucket = nullptr;    // [nlist] counting-sort buckets
     uint64_t *topkeys = nullptr;   // [cap_nq][cap_ntop]
     int64_t *out_ids = nullptr;    // [cap_nq][cap_k]
@@ -127,6 +132,7 @@ struct Workspace {
 
 struct Tune {  // scan launch shape chosen by the autotuner for one class of calls
     int threads = 256, ilp = 1, persistent = 0;
+    int tile_chunks = 0;  // > 0: tiled form with tiles of this many 32-candidate chunks
     bool set = false;
 };
 // class of a call: top-n above 256 (CTA variant) x LUT built in the scan / read from HBM
@@ -203,6 +209,9 @@ struct ScanLaunch {
     const int32_t *order;    // [nq] processing order (queries grouped by first probe), or null
     int threads = 256;       // warp-top-n variant: threads per CTA (256 or 512)
     int ilp = 1;             // chunks in flight per warp (1 or 2)
+    const uint32_t *tile_prefix = nullptr;  // tiled form: [nq+1] tiles per query prefix
+    const uint32_t *tile_T = nullptr;       // chunks per tile (device scalar)
+    uint64_t *partial = nullptr;            // [tile capacity][ntop]
 };
 
 
@@ -218,6 +227,12 @@ void launch_coarse_tc_dist(const DeviceIndex &ix, const float *q, int64_t rows, 
                            int64_t ldd, uint32_t *err, cudaStream_t st);
 void launch_query_order(const int32_t *probes, int64_t nq, int32_t stride, int32_t nlist,
                         uint32_t *cnt, int32_t *order, cudaStream_t st);
+void launch_tile_plan(const DeviceIndex &ix, const int32_t *probes, const int32_t *npq, int64_t nq,
+                      int32_t nprobe, int32_t stride, uint32_t T_req, uint32_t cap,
+                      uint32_t *chunks, unsigned long long *total, uint32_t *T_out,
+                      uint32_t *prefix, cudaStream_t st);
+void launch_tile_merge(const uint64_t *partial, const uint32_t *prefix, int64_t nq, int32_t ntop,
+                       uint64_t *topkeys, cudaStream_t st);
 void launch_scan(const DeviceIndex &ix, const ScanLaunch &a, cudaStream_t st);
 void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int prec, int gemm,
                        void *lut, float *lut_scale, uint32_t *err, cudaStream_t st);

@@ -66,6 +66,18 @@ struct ScanArgs {
     uint32_t *tile_ctr;
     int32_t persistent;
     const int32_t *order;  // [nq] processing order, or null
+    // tiled (batching) form: tiles of at most *tile_T chunks of one query
+    const uint32_t *tile_prefix;  // [nq+1] first tile of each query, or null (one CTA per query)
+    const uint32_t *tile_T;       // chunks per tile (device scalar)
+    uint64_t *partial;            // [tile capacity][ntop] per-tile top-n
+};
+
+// One unit of scan work: the chunks [c0, climit) of query qi, written to row
+// `row` of the output (the query itself, or its tile in the partial buffer).
+struct Work {
+    int64_t qi, row;
+    uint32_t c0, climit;
+    int first;  // the query's first tile (writes the gathered count)
 };
 
 // Shared memory plan (bytes), shared by host and device. `tail` is the
@@ -318,6 +330,41 @@ __device__ __forceinline__ int64_t next_query(const ScanArgs &a, int64_t it) {
     return a.order ? (int64_t)a.order[slot] : slot;
 }
 
+// Next unit of work (thread 0 only). Tiled form: slot t is tile t; its query
+// is found by binary search in the per-query tile prefix.
+__device__ __forceinline__ Work next_work(const ScanArgs &a, int64_t it) {
+    Work w;
+    if (!a.tile_prefix) {
+        w.qi = next_query(a, it);
+        w.row = w.qi;
+        w.c0 = 0;
+        w.climit = 0xffffffffu;
+        w.first = 1;
+        return w;
+    }
+    const int64_t slot =
+        a.persistent ? (int64_t)atomicAdd(a.tile_ctr, 1u) : (int64_t)blockIdx.x + it * gridDim.x;
+    const uint32_t ntiles = a.tile_prefix[a.nq];
+    if (slot >= ntiles) {
+        w.qi = a.nq;
+        return w;
+    }
+    int64_t lo = 0, hi = a.nq - 1;  // largest q with prefix[q] <= slot
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (a.tile_prefix[mid] <= (uint32_t)slot) lo = mid;
+        else hi = mid - 1;
+    }
+    const uint32_t T = *a.tile_T;
+    const uint32_t j = (uint32_t)slot - a.tile_prefix[lo];
+    w.qi = lo;
+    w.row = slot;
+    w.c0 = j * T;
+    w.climit = w.c0 + T;
+    w.first = j == 0;
+    return w;
+}
+
 // ---------------------------------------------------------------------------
 // Variant 1: n <= 256. Each warp keeps its own top-n in registers; the warps
 // share the best n-th key seen by any of them as a common filter threshold.
@@ -332,7 +379,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
     const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, NWARP * 64 * 8);
     const ScanPtrs S(smem, plan, a.nprobe);
     uint64_t *wbuf = reinterpret_cast<uint64_t *>(S.tail);
-    __shared__ int64_t s_q;
+    __shared__ Work s_w;
     __shared__ uint32_t s_kept;
     __shared__ unsigned long long s_thr;
     constexpr int NW = M / 4;
@@ -340,12 +387,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
 
     for (int64_t it = 0;; ++it) {
         if (threadIdx.x == 0) {
-            s_q = next_query(a, it);
+            s_w = next_work(a, it);
             s_kept = 0;
             s_thr = KEY_INF;
         }
         __syncthreads();
-        const int64_t qi = s_q;
+        const Work wk = s_w;
+        const int64_t qi = wk.qi;
         if (qi >= a.nq) break;
         int np = a.npq ? a.npq[qi] : a.nprobe;
         np = np < 1 ? 1 : (np > a.nprobe ? a.nprobe : np);
@@ -356,6 +404,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
         tk.init(wbuf + warp * 64, ntop);
         tk.sthr = &s_thr;
         const uint32_t total = S.pref[2 * np];
+        const uint32_t cend = total < wk.climit ? total : wk.climit;
         uint32_t kept = 0;
         SegCursor sg;
         uint32_t vc[ILP];
@@ -363,13 +412,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
         uint32_t wc[ILP][NW];
 #pragma unroll
         for (int j = 0; j < ILP; ++j) {
-            const uint32_t gj = warp + j * NWARP;
+            const uint32_t gj = wk.c0 + warp + j * NWARP;
             vc[j] = 0;
             okc[j] = false;
-            if (gj < total) locate(a, S, np, gj, sg, vc[j], okc[j]);
+            if (gj < cend) locate(a, S, np, gj, sg, vc[j], okc[j]);
             load_codes<M>(a.codes, vc[j], okc[j], wc[j]);
         }
-        for (uint32_t g = warp; g < total; g += ILP * NWARP) {
+        for (uint32_t g = wk.c0 + warp; g < cend; g += ILP * NWARP) {
             uint32_t vn[ILP];
             bool okn[ILP];
             uint32_t wn[ILP][NW];
@@ -378,7 +427,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
                 const uint32_t gn = g + (ILP + j) * NWARP;
                 vn[j] = 0;
                 okn[j] = false;
-                if (gn < total) locate(a, S, np, gn, sg, vn[j], okn[j]);
+                if (gn < cend) locate(a, S, np, gn, sg, vn[j], okn[j]);
                 load_codes<M>(a.codes, vn[j], okn[j], wn[j]);
             }
             float dist[ILP];
@@ -414,13 +463,24 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
                 for (int r = 0; r < R; ++r) B[r] = mrg[w * 32 * R + r * 32 + lane];
                 merge_sorted<R>(L, B);
             }
-            uint64_t *out = a.topkeys + qi * (int64_t)a.ntop;
+            uint64_t *out = (a.tile_prefix ? a.partial : a.topkeys) + wk.row * (int64_t)a.ntop;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int e = r * 32 + lane;
                 if (e < a.ntop) out[e] = e < ntop ? L[r] : KEY_INF;
             }
-            if (a.stats && lane == 0) write_stats(a, S, qi, np, s_kept);
+            if (a.stats && lane == 0) {
+                if (!a.tile_prefix) {
+                    write_stats(a, S, qi, np, s_kept);
+                } else {
+                    atomicAdd(&a.stats[qi * 4 + 1], (int32_t)s_kept);
+                    if (wk.first) {
+                        int64_t gathered = 0;
+                        for (int sgi = 0; sgi < 2 * np; ++sgi) gathered += S.seg_end[sgi] - S.seg_beg[sgi];
+                        a.stats[qi * 4 + 0] = (int32_t)gathered;
+                    }
+                }
+            }
         }
         __syncthreads();
     }
@@ -578,6 +638,7 @@ static int scan_grid(const ScanLaunch &l, int smem_total) {
     int per_sm = (227 * 1024) / (smem_total + 1024);
     per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
     int grid = num_sms(0) * per_sm;
+    if (l.tile_prefix) return grid;  // tiles outnumber queries
     return (int64_t)grid > l.nq ? (int)l.nq : grid;
 }
 
@@ -658,6 +719,13 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     a.tile_ctr = l.tile_ctr;
     a.persistent = l.persistent;
     a.order = l.order;
+    a.tile_prefix = l.tile_prefix;
+    a.tile_T = l.tile_T;
+    a.partial = l.partial;
+    if (a.tile_prefix) {
+        FA_REQUIRE(l.ntop <= 256, FA_ERR_ARG, "the tiled form supports top-n <= 256");
+        FA_REQUIRE(l.persistent, FA_ERR_ARG, "the tiled form runs persistent CTAs");
+    }
     switch (ix.M) {
         case 8: launch_scan_m<8, 64>(a, l, st); break;
         case 16: launch_scan_m<16, 64>(a, l, st); break;
@@ -666,6 +734,133 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
         case 64: launch_scan_m<64, 128>(a, l, st); break;
         default: FA_REQUIRE(false, FA_ERR_ARG, "M must be one of 8, 16, 32, 48, 64");
     }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled (batching) form, planned on the device so the whole search can be
+// captured in a CUDA graph:
+//   k_tile_count  chunks of 32 candidates per query (and their total)
+//   k_tile_plan   one CTA: chunks per tile T = max(requested, total / room) so
+//                 the tiles fit the partial buffer, then the per-query tile
+//                 prefix (exclusive scan)
+//   k_tile_merge  one warp per query merges its tiles' sorted top-n lists
+// ---------------------------------------------------------------------------
+__global__ void k_tile_count(const int32_t *probes, const int32_t *npq, int64_t nq, int32_t nprobe,
+                             int32_t stride, const uint32_t *list_beg, const uint64_t *rep_off,
+                             int32_t nlist, int32_t has_rep, uint32_t *chunks,
+                             unsigned long long *total) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    if (q >= nq) return;
+    int np = npq ? npq[q] : nprobe;
+    np = np < 1 ? 1 : (np > nprobe ? nprobe : np);
+    uint32_t c = 0;
+    for (int i = lane; i < np; i += 32) {
+        const int l = probes[q * stride + i];
+        if (l < 0 || l >= nlist) continue;
+        c += (list_beg[l + 1] - list_beg[l] + 31u) >> 5;
+        if (has_rep) c += (uint32_t)((rep_off[l + 1] - rep_off[l] + 31u) >> 5);
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if (lane == 0) {
+        chunks[q] = c;
+        atomicAdd(total, (unsigned long long)c);
+    }
+}
+
+__global__ void k_tile_plan(const uint32_t *chunks, int64_t nq, uint32_t T_req, uint32_t cap,
+                            const unsigned long long *total, uint32_t *T_out, uint32_t *prefix) {
+    __shared__ uint32_t part[32];
+    __shared__ uint32_t carry;
+    __shared__ uint32_t sT;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        const unsigned long long room = cap > nq ? (unsigned long long)(cap - nq) : 1ull;
+        unsigned long long T = (*total + room - 1) / room;
+        if (T < T_req) T = T_req;
+        sT = (uint32_t)(T > 0xffffffull ? 0xffffffull : (T < 1 ? 1 : T));
+        *T_out = sT;
+        carry = 0;
+    }
+    __syncthreads();
+    const uint32_t T = sT;
+    for (int64_t base = 0; base < nq; base += blockDim.x) {
+        const int64_t i = base + threadIdx.x;
+        uint32_t v = 0;
+        if (i < nq) {
+            const uint32_t c = chunks[i];
+            v = c == 0 ? 1u : (c + T - 1) / T;
+        }
+        uint32_t inc = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) part[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t pp = lane < (int)(blockDim.x >> 5) ? part[lane] : 0u;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, pp, o);
+                if (lane >= o) pp += y;
+            }
+            part[lane] = pp;
+        }
+        __syncthreads();
+        const uint32_t excl = carry + (warp ? part[warp - 1] : 0u) + inc - v;
+        if (i < nq) prefix[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) prefix[nq] = carry;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_tile_merge(const uint64_t *partial, const uint32_t *prefix,
+                                                     int64_t nq, int32_t ntop, uint64_t *topkeys) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = (int64_t)blockIdx.x * 8 + warp;
+    if (q >= nq) return;
+    uint64_t L[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) L[r] = KEY_INF;
+    for (uint32_t t = prefix[q]; t < prefix[q + 1]; ++t) {
+        uint64_t B[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int e = r * 32 + lane;
+            B[r] = e < ntop ? partial[(int64_t)t * ntop + e] : KEY_INF;
+        }
+        merge_sorted<R>(L, B);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        if (e < ntop) topkeys[q * ntop + e] = L[r];
+    }
+}
+
+void launch_tile_plan(const DeviceIndex &ix, const int32_t *probes, const int32_t *npq, int64_t nq,
+                      int32_t nprobe, int32_t stride, uint32_t T_req, uint32_t cap,
+                      uint32_t *chunks, unsigned long long *total, uint32_t *T_out,
+                      uint32_t *prefix, cudaStream_t st) {
+    FA_CHECK_CUDA(cudaMemsetAsync(total, 0, sizeof(unsigned long long), st));
+    k_tile_count<<<(unsigned)((nq + 7) / 8), 256, 0, st>>>(probes, npq, nq, nprobe, stride,
+                                                            ix.list_beg, ix.rep_off, ix.nlist,
+                                                            ix.n_rep > 0, chunks, total);
+    k_tile_plan<<<1, 1024, 0, st>>>(chunks, nq, T_req, cap, total, T_out, prefix);
+    FA_CHECK_CUDA(cudaGetLastError());
+}
+
+void launch_tile_merge(const uint64_t *partial, const uint32_t *prefix, int64_t nq, int32_t ntop,
+                       uint64_t *topkeys, cudaStream_t st) {
+    const dim3 grid((unsigned)((nq + 7) / 8));
+    if (ntop <= 32) k_tile_merge<1><<<grid, 256, 0, st>>>(partial, prefix, nq, ntop, topkeys);
+    else if (ntop <= 64) k_tile_merge<2><<<grid, 256, 0, st>>>(partial, prefix, nq, ntop, topkeys);
+    else if (ntop <= 128) k_tile_merge<4><<<grid, 256, 0, st>>>(partial, prefix, nq, ntop, topkeys);
+    else k_tile_merge<8><<<grid, 256, 0, st>>>(partial, prefix, nq, ntop, topkeys);
+    FA_CHECK_CUDA(cudaGetLastError());
 }
 
 // ---------------------------------------------------------------------------

@@ -302,6 +302,46 @@ def test_autotune_variants_agree_and_keep_results(fa, u8_repl, k, rerank):
     assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
 
 
+@pytest.fixture(scope="module")
+def zipf_small(fa):
+    """Uneven lists: 64 lists with Zipf(1.1) sizes over 60k vectors (the
+    largest list holds about a third of them), random codes and codebooks."""
+    rng = np.random.default_rng(33)
+    n, d, M, nlist = 60_000, 32, 16, 64
+    sizes = synth.zipf_sizes(nlist, n)
+    primary = np.repeat(np.arange(nlist, dtype=np.int32), sizes)
+    rng.shuffle(primary)
+    cent = rng.normal(size=(nlist, d)).astype(np.float32)
+    cb = rng.normal(size=(M, 256, d // M)).astype(np.float32)
+    codes = rng.integers(0, 256, size=(n, M)).astype(np.uint8)
+    ix = fa.fa_index_from_parts(cent, cb, codes, primary)
+    parts = ix.parts()
+    off, ids = _oracle_lists(parts)
+    q = rng.normal(size=(200, d)).astype(np.float32)
+    return dict(ix=ix, parts=parts, off=off, ids=ids, q=q, sizes=sizes)
+
+
+@pytest.mark.parametrize("k", [10, 100])
+def test_tiled_batching_form_on_uneven_lists(fa, zipf_small, k):
+    """Persistent tiled form with per-query nprobe in 1..16 over Zipf-sized
+    lists: the oracle's top-k, and the same rows as one CTA per query."""
+    s = zipf_small
+    rng = np.random.default_rng(k)
+    nq = s["q"].shape[0]
+    npq = rng.integers(1, 17, size=nq).astype(np.int32)
+    probes = oracle.coarse(s["q"], s["parts"]["centroids"], 16)
+    tiled = fa.fa_search_ex(s["ix"], s["q"], k, 16, fa.search_params(flags=fa.FA_PERSISTENT),
+                            probes=probes, nprobe_per_query=npq)
+    plain = fa.fa_search_ex(s["ix"], s["q"], k, 16, probes=probes, nprobe_per_query=npq)
+    assert np.array_equal(tiled[0], plain[0]) and np.array_equal(tiled[1], plain[1])
+    assert s["sizes"].max() > 0.25 * s["parts"]["n"]
+    for i in range(0, nq, 7):
+        oi, od = oracle.search(s["q"][i:i + 1], s["parts"]["centroids"], s["parts"]["codebooks"],
+                               s["parts"]["codes"], s["off"], s["ids"], int(npq[i]), k + 1,
+                               probes=probes[i:i + 1, :npq[i]])
+        _check_topk(tiled[0][i], tiled[1][i], oi[0, :k], od[0, :k], od[0, k], k, what=str(i))
+
+
 def test_per_query_k_and_nprobe(fa, f32_small):
     s = f32_small
     q = s["q"][:20]
