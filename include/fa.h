@@ -164,6 +164,11 @@ void fa_free_index(fa_index *ix);
                                   * uneven queries (top-n <= 256) */
 #define FA_NO_SYNC 0x10          /* return without synchronizing sp->stream
                                   * (device outputs only) */
+#define FA_GRAPH 0x20            /* capture the call's kernels into a CUDA graph
+                                  * on first use and replay it on later calls
+                                  * with the same shape, parameters, pointers
+                                  * and stream (device queries and outputs, no
+                                  * stats or trace) */
 
 /* Optional per-call trace, measured with CUDA events on the call's stream
  * (ms of device time per stage; launches = kernels this call launched). */

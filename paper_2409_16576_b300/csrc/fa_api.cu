@@ -241,7 +241,13 @@ void upload_index(fa_index *ix) {
 // ---------------------------------------------------------------------------
 // workspace pool
 // ---------------------------------------------------------------------------
+static void ws_drop_graph(Workspace *w) {
+    if (w->gexec) cudaGraphExecDestroy(w->gexec);
+    w->gexec = nullptr;
+}
+
 static void ws_free_buffers(Workspace *w) {
+    ws_drop_graph(w);
     void *dp[] = {w->q, w->probes, w->kq, w->npq, w->order, w->bucket, w->tchunks, w->tprefix,
                   w->tmisc, w->partial, w->topkeys, w->out_ids, w->out_dist,
                   w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr};
@@ -331,6 +337,7 @@ static void ws_ensure_partial(Workspace *w, int64_t nq, int32_t ntop) {
     if (w->partial && w->tile_cap >= cap && w->cap_ntop >= ntop) return;
     if (w->pending) FA_CHECK_CUDA(cudaEventSynchronize(w->done));
     FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
+    ws_drop_graph(w);
     if (w->partial) cudaFree(w->partial);
     w->partial = nullptr;
     dalloc(w->partial, (size_t)cap * std::max(ntop, w->cap_ntop));
@@ -454,109 +461,165 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
 
     Tracer tr(sp.trace, st);
     tr.mark(0);
-    FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
-    const float *qd = queries;
-    if (!qdev) {
-        FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * d, cudaMemcpyHostToDevice, st));
-        qd = w->q;
-    }
-    const int32_t *kq = nullptr, *npq = nullptr;
-    if (sp.k_per_query) {
-        if (qdev) kq = sp.k_per_query;
-        else {
-            FA_CHECK_CUDA(cudaMemcpyAsync(w->kq, sp.k_per_query, 4 * nq, cudaMemcpyHostToDevice, st));
-            kq = w->kq;
-        }
-    }
-    if (sp.nprobe_per_query) {
-        if (qdev) npq = sp.nprobe_per_query;
-        else {
-            FA_CHECK_CUDA(cudaMemcpyAsync(w->npq, sp.nprobe_per_query, 4 * nq, cudaMemcpyHostToDevice, st));
-            npq = w->npq;
-        }
-    }
-    const int32_t *probes = w->probes;
-    if (sp.probes) {
-        if (qdev) probes = sp.probes;
-        else FA_CHECK_CUDA(cudaMemcpyAsync(w->probes, sp.probes, sizeof(int32_t) * nq * nprobe,
-                                           cudaMemcpyHostToDevice, st));
-    } else {
-        launch_coarse(D, qd, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, st);
-        tr.launches += coarse_launches(D, nq, *w);
-    }
-    tr.mark(1);
-    if (global_lut) {
-        launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st);
-        tr.launches += 1;
-    }
-    tr.mark(2);
-
-    ScanLaunch sl{};
-    int tile_chunks = 0;
-    sl.q = qd;
-    sl.probes = probes;
-    sl.npq = npq;
-    sl.ntopq = rerank ? nullptr : kq;
-    sl.nq = nq;
-    sl.nprobe = nprobe;
-    sl.probe_stride = nprobe;
-    sl.ntop = ntop;
-    sl.lut_prec = global_lut ? sp.lut_prec : -1;
-    sl.lut = w->lut;
-    sl.lut_scale = w->lut_scale;
-    sl.topkeys = w->topkeys;
-    sl.stats = sp.stats ? w->stats : nullptr;
-    sl.err = w->err;
-    sl.tile_ctr = w->tile_ctr;
-    {
-        Tune t;
-        if (force) {
-            t = *force;
-        } else {
-            std::lock_guard<std::mutex> lk(ix->mu);
-            const Tune &c = ix->tune[tune_class(ntop, global_lut)];
-            if (c.set) t = c;
-        }
-        sl.threads = t.threads;
-        sl.ilp = t.ilp;
-        sl.persistent = ((sp.flags & FA_PERSISTENT) || t.persistent) ? 1 : 0;
-        tile_chunks = t.tile_chunks;
-        if ((sp.flags & FA_PERSISTENT) && tile_chunks == 0) tile_chunks = 256;
-        if (ntop > 256) tile_chunks = 0;  // the CTA-wide top-n runs one CTA per query
-    }
-    if (sp.stats) FA_CHECK_CUDA(cudaMemsetAsync(w->stats, 0, sizeof(int32_t) * 4 * nq, st));
-    if (tile_chunks > 0) {
-        // batching form: uneven queries split into tiles of chunks, planned on the device
-        ws_ensure_partial(w, nq, ntop);
-        launch_tile_plan(D, probes, npq, nq, nprobe, nprobe, (uint32_t)tile_chunks,
-                         (uint32_t)w->tile_cap, w->tchunks,
-                         reinterpret_cast<unsigned long long *>(w->tmisc + 2), w->tmisc, w->tprefix, st);
-        sl.tile_prefix = w->tprefix;
-        sl.tile_T = w->tmisc;
-        sl.partial = w->partial;
-        sl.persistent = 1;
-        FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
-        launch_scan(D, sl, st);
-        launch_tile_merge(w->partial, w->tprefix, nq, ntop, w->topkeys, st);
-        tr.launches += 4;
-    } else {
-        launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
-        sl.order = w->order;
-        if (sl.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
-        launch_scan(D, sl, st);
-        tr.launches += 4;
-    }
-    tr.mark(3);
-
     int64_t *oid = odev ? out_ids : w->out_ids;
     float *odist = odev ? out_dist : w->out_dist;
-    if (rerank)
-        launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
-                      max_changed_for(sp.rerank_eps, k), oid, odist, sp.stats ? w->stats : nullptr, st);
-    else
-        launch_finish(D, w->topkeys, nq, ntop, k, kq, oid, odist, st);
-    tr.launches += 1;
-    tr.mark(4);
+    // launch shape (autotuned per call class unless forced)
+    Tune tune;
+    if (force) {
+        tune = *force;
+    } else {
+        std::lock_guard<std::mutex> lk(ix->mu);
+        const Tune &c = ix->tune[tune_class(ntop, global_lut)];
+        if (c.set) tune = c;
+    }
+    int tile_chunks = tune.tile_chunks;
+    if ((sp.flags & FA_PERSISTENT) && tile_chunks == 0) tile_chunks = 256;
+    if (ntop > 256) tile_chunks = 0;  // the CTA-wide top-n runs one CTA per query
+    if (tile_chunks > 0) ws_ensure_partial(w, nq, ntop);
+
+    auto enqueue = [&]() {
+        FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
+        const float *qd = queries;
+        if (!qdev) {
+            FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * d, cudaMemcpyHostToDevice, st));
+            qd = w->q;
+        }
+        const int32_t *kq = nullptr, *npq = nullptr;
+        if (sp.k_per_query) {
+            if (qdev) kq = sp.k_per_query;
+            else {
+                FA_CHECK_CUDA(cudaMemcpyAsync(w->kq, sp.k_per_query, 4 * nq, cudaMemcpyHostToDevice, st));
+                kq = w->kq;
+            }
+        }
+        if (sp.nprobe_per_query) {
+            if (qdev) npq = sp.nprobe_per_query;
+            else {
+                FA_CHECK_CUDA(cudaMemcpyAsync(w->npq, sp.nprobe_per_query, 4 * nq, cudaMemcpyHostToDevice, st));
+                npq = w->npq;
+            }
+        }
+        const int32_t *probes = w->probes;
+        if (sp.probes) {
+            if (qdev) probes = sp.probes;
+            else FA_CHECK_CUDA(cudaMemcpyAsync(w->probes, sp.probes, sizeof(int32_t) * nq * nprobe,
+                                               cudaMemcpyHostToDevice, st));
+        } else {
+            launch_coarse(D, qd, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, st);
+            tr.launches += coarse_launches(D, nq, *w);
+        }
+        tr.mark(1);
+        if (global_lut) {
+            launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st);
+            tr.launches += 1;
+        }
+        tr.mark(2);
+
+        ScanLaunch sl{};
+        sl.q = qd;
+        sl.probes = probes;
+        sl.npq = npq;
+        sl.ntopq = rerank ? nullptr : kq;
+        sl.nq = nq;
+        sl.nprobe = nprobe;
+        sl.probe_stride = nprobe;
+        sl.ntop = ntop;
+        sl.lut_prec = global_lut ? sp.lut_prec : -1;
+        sl.lut = w->lut;
+        sl.lut_scale = w->lut_scale;
+        sl.topkeys = w->topkeys;
+        sl.stats = sp.stats ? w->stats : nullptr;
+        sl.err = w->err;
+        sl.tile_ctr = w->tile_ctr;
+        sl.threads = tune.threads;
+        sl.ilp = tune.ilp;
+        sl.persistent = ((sp.flags & FA_PERSISTENT) || tune.persistent) ? 1 : 0;
+        if (sp.stats) FA_CHECK_CUDA(cudaMemsetAsync(w->stats, 0, sizeof(int32_t) * 4 * nq, st));
+        if (tile_chunks > 0) {
+            // batching form: uneven queries split into tiles of chunks, planned on the device
+            launch_tile_plan(D, probes, npq, nq, nprobe, nprobe, (uint32_t)tile_chunks,
+                             (uint32_t)w->tile_cap, w->tchunks,
+                             reinterpret_cast<unsigned long long *>(w->tmisc + 2), w->tmisc, w->tprefix, st);
+            sl.tile_prefix = w->tprefix;
+            sl.tile_T = w->tmisc;
+            sl.partial = w->partial;
+            sl.persistent = 1;
+            FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
+            launch_scan(D, sl, st);
+            launch_tile_merge(w->partial, w->tprefix, nq, ntop, w->topkeys, st);
+            tr.launches += 4;
+        } else {
+            launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
+            sl.order = w->order;
+            if (sl.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
+            launch_scan(D, sl, st);
+            tr.launches += 4;
+        }
+        tr.mark(3);
+
+        if (rerank)
+            launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
+                          max_changed_for(sp.rerank_eps, k), oid, odist, sp.stats ? w->stats : nullptr, st);
+        else
+            launch_finish(D, w->topkeys, nq, ntop, k, kq, oid, odist, st);
+        tr.launches += 1;
+        tr.mark(4);
+
+    };
+
+    if (sp.flags & FA_GRAPH) {
+        // capture once per (shape, parameters, pointers, stream), replay afterwards
+        FA_REQUIRE(qdev && odev && !sp.stats && !sp.trace, FA_ERR_ARG,
+                   "FA_GRAPH needs device queries and outputs and no stats or trace");
+        GraphKey key{};
+        key.q = queries;
+        key.oi = out_ids;
+        key.od = out_dist;
+        key.probes = sp.probes;
+        key.kq = sp.k_per_query;
+        key.npq = sp.nprobe_per_query;
+        key.st = st;
+        key.nq = nq;
+        key.k = k;
+        key.nprobe = nprobe;
+        key.lut_prec = sp.lut_prec;
+        key.lut_gemm = sp.lut_gemm;
+        key.probe_gemm = sp.probe_gemm;
+        key.rerank_n = sp.rerank_n;
+        key.rerank_batch = sp.rerank_batch;
+        key.rerank_beta = sp.rerank_beta;
+        key.rerank_eps = sp.rerank_eps;
+        key.flags = sp.flags & (FA_PERSISTENT);
+        key.threads = tune.threads;
+        key.ilp = tune.ilp;
+        key.persistent = tune.persistent;
+        key.tile_chunks = tile_chunks;
+        if (!(w->gexec && memcmp(&w->gkey, &key, sizeof key) == 0)) {
+            if (w->gexec) {
+                cudaGraphExecDestroy(w->gexec);
+                w->gexec = nullptr;
+            }
+            FA_CHECK_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+            try {
+                enqueue();
+            } catch (...) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(st, &g);
+                if (g) cudaGraphDestroy(g);
+                cudaGetLastError();
+                throw;
+            }
+            cudaGraph_t g = nullptr;
+            FA_CHECK_CUDA(cudaStreamEndCapture(st, &g));
+            const cudaError_t ie = cudaGraphInstantiate(&w->gexec, g, 0);
+            cudaGraphDestroy(g);
+            FA_CHECK_CUDA(ie);
+            w->gkey = key;
+        }
+        FA_CHECK_CUDA(cudaGraphLaunch(w->gexec, st));
+    } else {
+        enqueue();
+    }
     if (!odev) {
         FA_CHECK_CUDA(cudaMemcpyAsync(out_ids, oid, sizeof(int64_t) * nq * k, cudaMemcpyDeviceToHost, st));
         FA_CHECK_CUDA(cudaMemcpyAsync(out_dist, odist, sizeof(float) * nq * k, cudaMemcpyDeviceToHost, st));

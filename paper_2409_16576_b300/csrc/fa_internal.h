@@ -88,6 +88,16 @@ struct DeviceIndex {
     int64_t pinned_bytes = 0;
 };
 
+// identity of a captured search (FA_GRAPH): replayed only for an identical call
+struct GraphKey {
+    const void *q, *oi, *od, *probes, *kq, *npq;
+    cudaStream_t st;
+    int64_t nq;
+    int32_t k, nprobe, lut_prec, lut_gemm, probe_gemm, rerank_n, rerank_batch, rerank_beta;
+    float rerank_eps;
+    int32_t flags, threads, ilp, persistent, tile_chunks;
+};
+
 // -------------------------------------------------------------------------
 // per-call workspace (one slot of the index's pool, §5's per-query blocks)
 // -------------------------------------------------------------------------
@@ -96,6 +106,8 @@ struct Workspace {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;    // end of the last no-sync call on this slot
     bool pending = false;
+    cudaGraphExec_t gexec = nullptr;  // last captured search (FA_GRAPH)
+    GraphKey gkey{};
     int64_t cap_nq = 0;
     int32_t cap_k = 0, cap_nprobe = 0, cap_ntop = 0, cap_lut_bytes = 0;
     float *q = nullptr;            // [cap_nq][d]

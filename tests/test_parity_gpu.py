@@ -342,6 +342,32 @@ def test_tiled_batching_form_on_uneven_lists(fa, zipf_small, k):
         _check_topk(tiled[0][i], tiled[1][i], oi[0, :k], od[0, :k], od[0, k], k, what=str(i))
 
 
+@pytest.mark.parametrize("flags", ["eager_graph", "tiled_graph"])
+def test_graph_capture_replays_the_search(fa, zipf_small, flags):
+    """FA_GRAPH: the first call captures the kernels into a CUDA graph, later
+    calls with the same buffers replay it and read the buffers' new contents."""
+    import torch
+    s = zipf_small
+    f = fa.FA_GRAPH | (fa.FA_PERSISTENT if flags == "tiled_graph" else 0)
+    p = fa.search_params(flags=f, lut_prec=fa.FA_LUT_F16, lut_gemm=fa.FA_GEMM_BF16_TC,
+                         probe_gemm=fa.FA_GEMM_BF16_TC)
+    ref = fa.search_params(lut_prec=fa.FA_LUT_F16, lut_gemm=fa.FA_GEMM_BF16_TC,
+                           probe_gemm=fa.FA_GEMM_BF16_TC)
+    qd = torch.as_tensor(s["q"], device="cuda")
+    oi = torch.empty((qd.shape[0], 10), dtype=torch.int64, device="cuda")
+    od = torch.empty((qd.shape[0], 10), dtype=torch.float32, device="cuda")
+    for rnd in range(3):
+        if rnd == 2:
+            qd.mul_(-1.0)  # new query contents in the same buffer
+        fa.fa_search_ex(s["ix"], qd, 10, 8, p, out_ids=oi, out_dist=od)
+        torch.cuda.synchronize()
+        ei, ed = fa.fa_search_ex(s["ix"], qd.cpu().numpy(), 10, 8, ref)
+        assert np.array_equal(oi.cpu().numpy(), ei) and np.array_equal(od.cpu().numpy(), ed), rnd
+    with pytest.raises(fa.FaError) as e:
+        fa.fa_search_ex(s["ix"], s["q"], 10, 8, p)  # host buffers cannot be captured
+    assert e.value.status == fa.FA_ERR_ARG
+
+
 def test_per_query_k_and_nprobe(fa, f32_small):
     s = f32_small
     q = s["q"][:20]
