@@ -111,6 +111,14 @@ void fa_build_params_init(fa_build_params *p);
 fa_status fa_build_index(const void *base, int64_t n, int32_t d, fa_dtype dt,
                          const fa_build_params *p, fa_index **out);
 
+/* Builds an index whose posting lists the caller already has: centroids
+ * [nlist][d] and the list of every vector, primary[n] (no coarse k-means, no
+ * replication). Only the PQ sub-codebooks are trained (on a sample) and every
+ * vector encoded, as in fa_build_index; p->nlist is ignored. */
+fa_status fa_build_index_lists(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                               const float *centroids, int32_t nlist, const int32_t *primary,
+                               const fa_build_params *p, fa_index **out);
+
 /* The logical content of an index. Every pointer is host memory. */
 typedef struct fa_index_parts {
     int64_t n;                /* vectors */

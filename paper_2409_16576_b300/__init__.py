@@ -82,6 +82,7 @@ _sig("fa_build_params_init", None, P)
 _sig("fa_search_params_init", None, P)
 _sig("fa_build_index", i32, P, i64, i32, i32, P, P)
 _sig("fa_index_from_parts", i32, P, P)
+_sig("fa_build_index_lists", i32, P, i64, i32, i32, P, i32, P, P, P)
 _sig("fa_index_get_parts", i32, P, P)
 _sig("fa_index_info_get", i32, P, P)
 _sig("fa_save_index", i32, P, C.c_char_p)
@@ -99,7 +100,8 @@ _sig("fa_status_str", C.c_char_p, i32)
 _sig("fa_version", C.c_char_p)
 
 # every symbol include/fa.h declares
-EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_index_from_parts", "fa_index_get_parts",
+EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_build_index_lists", "fa_index_from_parts",
+           "fa_index_get_parts",
            "fa_index_info_get", "fa_save_index", "fa_load_index", "fa_free_index",
            "fa_search_params_init", "fa_search", "fa_search_ex", "fa_autotune", "fa_debug_probes",
            "fa_debug_candidates", "fa_debug_lut", "fa_coarse_probe_noalloc", "fa_last_error",
@@ -202,6 +204,22 @@ def fa_build_index(base: np.ndarray, params: fa_build_params | None = None) -> I
     h = P()
     _check(_lib.fa_build_index(_ptr(base), base.shape[0], base.shape[1], dt,
                                C.byref(params) if params is not None else None, C.byref(h)))
+    return Index(h.value)
+
+
+def fa_build_index_lists(base: np.ndarray, centroids: np.ndarray, primary: np.ndarray,
+                         params: fa_build_params | None = None) -> Index:
+    """Index over lists the caller already has (PQ trained and encoded here)."""
+    base = np.ascontiguousarray(base)
+    dt = FA_U8 if base.dtype == np.uint8 else FA_F32
+    if dt == FA_F32:
+        base = np.ascontiguousarray(base, dtype=np.float32)
+    cent = np.ascontiguousarray(centroids, dtype=np.float32)
+    prim = np.ascontiguousarray(primary, dtype=np.int32)
+    h = P()
+    _check(_lib.fa_build_index_lists(_ptr(base), base.shape[0], base.shape[1], dt, _ptr(cent),
+                                     cent.shape[0], _ptr(prim),
+                                     C.byref(params) if params is not None else None, C.byref(h)))
     return Index(h.value)
 
 

@@ -227,7 +227,16 @@ void train_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
     out.rep_ids.reserve(out.rep_off[nlist]);
     for (int l = 0; l < nlist; ++l) out.rep_ids.insert(out.rep_ids.end(), rep[l].begin(), rep[l].end());
 
-    // PQ sub-codebooks, one k-means per subspace on a sub-sample
+    train_pq_and_encode(base, n, d, dt, p, X.data(), S, out);
+}
+
+// PQ sub-codebooks (one k-means per subspace on a sub-sample of the training
+// rows X[S][d]) and the code of every base vector.
+void train_pq_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                         const fa_build_params &p, const float *X, int64_t S, BuildOut &out) {
+    const int32_t M = p.M, dsub = d / M;
+    const bool gpu = p.use_gpu != 0;
+    const int iters = p.kmeans_iters;
     const int64_t Sp = std::min<int64_t>(S, 32768);
     out.codebooks.assign((size_t)M * 256 * dsub, 0.f);
 #pragma omp parallel for schedule(dynamic, 1)
@@ -235,7 +244,8 @@ void train_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
         std::vector<float> sub((size_t)Sp * dsub);
         for (int64_t i = 0; i < Sp; ++i)
             memcpy(&sub[(size_t)i * dsub], &X[(size_t)((i * S) / Sp) * d + m * dsub], sizeof(float) * dsub);
-        std::vector<float> cb = kmeans(sub.data(), Sp, dsub, 256, iters, p.seed ^ (0x7071ull << 16) ^ (uint64_t)m, false);
+        std::vector<float> cb =
+            kmeans(sub.data(), Sp, dsub, 256, iters, p.seed ^ (0x7071ull << 16) ^ (uint64_t)m, false);
         memcpy(&out.codebooks[(size_t)m * 256 * dsub], cb.data(), sizeof(float) * 256 * dsub);
     }
 
@@ -244,6 +254,18 @@ void train_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
         gpu_encode(base, n, d, dt, out.codebooks.data(), M, out.codes.data());
     else
         host_encode(base, n, d, dt, out.codebooks.data(), M, out.codes.data());
+}
+
+// Lists given by the caller (centroids and the list of every vector): only the
+// PQ part is trained.
+void encode_with_lists(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                       const fa_build_params &p, BuildOut &out) {
+    const int64_t S = p.train_sample > 0 ? std::min<int64_t>(n, p.train_sample)
+                                         : std::min<int64_t>(n, 65536);
+    std::vector<float> X((size_t)S * d);
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < S; ++i) row_f32(base, dt, d, (i * n) / S, &X[(size_t)i * d]);
+    train_pq_and_encode(base, n, d, dt, p, X.data(), S, out);
 }
 
 }  // namespace fa

@@ -852,6 +852,60 @@ fa_status fa_build_index(const void *base, int64_t n, int32_t d, fa_dtype dt,
     return FA_OK;
 }
 
+fa_status fa_build_index_lists(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                               const float *centroids, int32_t nlist, const int32_t *primary,
+                               const fa_build_params *p, fa_index **out) {
+    if (!out) {
+        set_error("null output pointer");
+        return FA_ERR_ARG;
+    }
+    *out = nullptr;
+    fa_build_params bp;
+    if (p)
+        bp = *p;
+    else
+        fa_build_params_init(&bp);
+    bp.nlist = nlist;
+    fa_index *ix = nullptr;
+    fa_status s = guarded(nullptr, [&] {
+        FA_REQUIRE(base && centroids && primary, FA_ERR_ARG, "null input");
+        FA_REQUIRE(dt == FA_F32 || dt == FA_U8, FA_ERR_ARG, "bad dtype");
+        FA_REQUIRE(n >= 1 && n < (1ll << 32) - 64 && nlist >= 1, FA_ERR_ARG, "bad shape");
+        FA_REQUIRE(bp.M >= 1 && d % bp.M == 0, FA_ERR_ARG, "d must be a multiple of M");
+        if (bp.use_gpu) current_device();
+        BuildOut bo;
+        bo.centroids.assign(centroids, centroids + (size_t)nlist * d);
+        bo.primary.assign(primary, primary + n);
+        bo.rep_off.assign(nlist + 1, 0);
+        encode_with_lists(base, n, d, dt, bp, bo);
+        fa_index_parts parts{};
+        parts.n = n;
+        parts.d = d;
+        parts.nlist = nlist;
+        parts.M = bp.M;
+        parts.raw_dtype = dt;
+        parts.raw_location = bp.raw_location;
+        parts.centroids = bo.centroids.data();
+        parts.codebooks = bo.codebooks.data();
+        parts.codes = bo.codes.data();
+        parts.primary = bo.primary.data();
+        parts.rep_off = bo.rep_off.data();
+        parts.rep_ids = bo.rep_ids.data();
+        parts.raw = bp.raw_location != FA_RAW_NONE ? base : nullptr;
+        check_parts(&parts);
+        ix = new fa_index();
+        ix->device = current_device();
+        copy_parts(ix, &parts);
+        upload_index(ix);
+    });
+    if (s != FA_OK) {
+        destroy(ix);
+        return s;
+    }
+    *out = ix;
+    return FA_OK;
+}
+
 fa_status fa_index_get_parts(const fa_index *ix, fa_index_parts *out) {
     if (!ix || !out) {
         set_error("null argument");

@@ -190,6 +190,11 @@ struct BuildOut {
 void train_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
                       const fa_build_params &p, BuildOut &out);
 
+void train_pq_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                         const fa_build_params &p, const float *X, int64_t S, BuildOut &out);
+void encode_with_lists(const void *base, int64_t n, int32_t d, fa_dtype dt,
+                       const fa_build_params &p, BuildOut &out);
+
 // Uploads the logical parts to the device (renumbering, rotated codes, CSR).
 void upload_index(fa_index *ix);
 void free_device_index(fa_index *ix);

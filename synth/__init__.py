@@ -165,6 +165,82 @@ def zipf_sizes(nlist: int, n: int, s: float = 1.1) -> np.ndarray:
     return base + 1
 
 
+@dataclass(frozen=True)
+class ZipfLists:
+    """Unit-norm vectors grouped, by construction, into nlist lists of Zipf(s)
+    sizes (DEEP-like d=96 float32). List centres are drawn from an isotropic
+    ``ncomp``-component mixture (component means N(0, 1)^d, centre spread
+    ``centre_sigma``); a vector is its list's centre plus N(0, sigma^2)
+    noise, scaled to unit norm. Rows are ordered by list: row i belongs to the
+    list whose size prefix covers i. The normalised centres serve as the IVF
+    centroids and ``primary()`` as the assignment (no clustering)."""
+    n: int
+    d: int = 96
+    nlist: int = 65536
+    ncomp: int = 1024
+    s: float = 1.1
+    centre_sigma: float = 0.35
+    sigma: float = 0.2
+    seed: int = BASE_SEED
+
+    def sizes(self) -> np.ndarray:
+        return zipf_sizes(self.nlist, self.n, self.s)
+
+    def _centres_raw(self) -> np.ndarray:
+        g = philox(self.seed, STREAM_MEANS, 1)
+        means = g.standard_normal(size=(self.ncomp, self.d))
+        comp = g.integers(0, self.ncomp, size=self.nlist)
+        return means[comp] + self.centre_sigma * g.standard_normal(size=(self.nlist, self.d))
+
+    def centroids(self) -> np.ndarray:
+        c = self._centres_raw()
+        return (c / np.linalg.norm(c, axis=1, keepdims=True)).astype(np.float32)
+
+    def primary(self) -> np.ndarray:
+        return np.repeat(np.arange(self.nlist, dtype=np.int32), self.sizes())
+
+    def _make(self, stream, chunk, lists, centres):
+        g = philox(self.seed, stream, chunk)
+        x = centres[lists] + self.sigma * g.standard_normal(size=(lists.shape[0], self.d))
+        x /= np.linalg.norm(x, axis=1, keepdims=True)
+        return x.astype(np.float32)
+
+    def rows(self, start: int, stop: int) -> np.ndarray:
+        centres = self._centres_raw()
+        bounds = np.concatenate([[0], np.cumsum(self.sizes())])
+        out = np.empty((max(0, stop - start), self.d), dtype=np.float32)
+        if stop <= start:
+            return out
+        c0, c1 = start // CHUNK, (stop - 1) // CHUNK
+
+        def work(c):
+            lo, hi = c * CHUNK, min((c + 1) * CHUNK, self.n)
+            lists = np.searchsorted(bounds, np.arange(lo, hi), side="right") - 1
+            blk = self._make(STREAM_BASE, c, lists, centres)
+            a, b = max(lo, start), min(hi, stop)
+            out[a - start:b - start] = blk[a - lo:b - lo]
+
+        with ThreadPoolExecutor(_threads()) as ex:
+            list(ex.map(work, range(c0, c1 + 1)))
+        return out
+
+    def base(self) -> np.ndarray:
+        return self.rows(0, self.n)
+
+    def queries(self, nq: int) -> np.ndarray:
+        """Queries drawn like the base: a uniformly chosen row's list, fresh noise."""
+        centres = self._centres_raw()
+        bounds = np.concatenate([[0], np.cumsum(self.sizes())])
+        g = philox(self.seed, STREAM_QUERIES, 1 << 20)
+        lists = np.searchsorted(bounds, g.integers(0, self.n, size=nq), side="right") - 1
+        return self._make(STREAM_QUERIES, 1 << 21, lists, centres)
+
+
+def zipf_unit_100m() -> "ZipfLists":
+    """100M unit-norm d=96 vectors, 65536 Zipf(1.1) lists, 1024-component mixture."""
+    return ZipfLists(100_000_000)
+
+
 def poisson_arrivals(rate_qps: float, count: int, seed: int = BASE_SEED) -> np.ndarray:
     """Arrival times (s) of an open-loop Poisson process: exponential gaps."""
     g = philox(seed, STREAM_ARRIVALS, int(rate_qps) & 0xFFFFFFFF)
