@@ -368,6 +368,23 @@ def test_graph_capture_replays_the_search(fa, zipf_small, flags):
     assert e.value.status == fa.FA_ERR_ARG
 
 
+def test_build_with_given_lists(fa):
+    """fa_build_index_lists keeps the caller's lists and centroids and trains
+    only PQ; searches on it match the oracle on the exported parts."""
+    z = synth.ZipfLists(40_000, d=32, nlist=128, ncomp=16)
+    base, cent, prim = z.base(), z.centroids(), z.primary()
+    ix = fa.fa_build_index_lists(base, cent, prim, fa.build_params(M=16, kmeans_iters=4))
+    parts = ix.parts()
+    assert np.array_equal(parts["primary"], prim) and np.array_equal(parts["centroids"], cent)
+    q = z.queries(30)
+    off, ids = _oracle_lists(parts)
+    probes = oracle.coarse(q, cent, 8)
+    gi, gd = fa.fa_search_ex(ix, q, 10, 8, probes=probes)
+    oi, od = oracle.search(q, cent, parts["codebooks"], parts["codes"], off, ids, 8, 11, probes=probes)
+    for i in range(q.shape[0]):
+        _check_topk(gi[i], gd[i], oi[i, :10], od[i, :10], od[i, 10], 10, what=str(i))
+
+
 def test_per_query_k_and_nprobe(fa, f32_small):
     s = f32_small
     q = s["q"][:20]
