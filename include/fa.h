@@ -245,6 +245,60 @@ fa_status fa_autotune(fa_index *ix, const float *queries, int64_t nq, int32_t d,
                       int32_t nprobe, const fa_search_params *sp, fa_tune_result *out);
 
 /* ------------------------------------------------------------------------- */
+/* Serving form: continuous batching of single-query requests                */
+/* ------------------------------------------------------------------------- */
+
+typedef struct fa_server fa_server; /* opaque, owned by the library */
+
+typedef struct fa_server_params {
+    int32_t max_batch;        /* requests per batch at most */
+    int32_t window_us;        /* a batch closes when its oldest request waited this long */
+    int32_t slots;            /* batches in flight at most (device memory blocks) */
+    int32_t kmax;             /* largest k a request may ask for (<= 256) */
+    int32_t nprobe_max;       /* larger per-request nprobe values are clamped to this */
+    int32_t pad0;
+    int64_t mem_budget_bytes; /* > 0: cap on the slots' device memory (fewer slots) */
+} fa_server_params;
+
+typedef struct fa_server_stats_t {
+    int64_t batches, requests, pending, device_bytes;
+    int32_t inflight_batches, slots;
+} fa_server_stats_t;
+
+/* Defaults: batches of up to 1024 requests, 200 us window, 4 slots, kmax 100,
+ * nprobe_max 256, no memory cap. */
+void fa_server_params_init(fa_server_params *p);
+
+/* Starts a request loop over ix with the search parameters sp (precision,
+ * re-rank, ...; buffer flags and per-query pointers are set by the loop). The
+ * loop (a host thread) closes a batch when it is full or its oldest request
+ * has waited window_us, admits it when one of the `slots` device memory blocks
+ * is free (blocks are allocated here, none in the loop), and launches it
+ * without waiting, so batches overlap on the device. The paper runs one CPU
+ * thread per query against a pool of per-query GPU blocks (§5); here requests
+ * share batches and a block serves one batch. */
+fa_status fa_server_create(fa_index *ix, const fa_server_params *p, const fa_search_params *sp,
+                           fa_server **out);
+
+/* Queues n requests: queries[n][d] (host), k[n] in 1..kmax, nprobe[n] >= 1.
+ * out_request_ids (optional) receives each request's id. */
+fa_status fa_server_submit(fa_server *sv, const float *queries, int64_t n, const int32_t *k,
+                           const int32_t *nprobe, int64_t *out_request_ids);
+
+/* Takes up to max_results completed requests (waits up to timeout_us for the
+ * first): request id, ids and distances [max_results][kstride] (padded with
+ * -1 / +inf past each request's k), latency from submit to completion in us,
+ * and status. Returns how many were written. */
+int64_t fa_server_poll(fa_server *sv, int64_t max_results, int32_t timeout_us, int64_t *request_ids,
+                       int64_t *ids, float *dist, int32_t kstride, double *latency_us,
+                       int32_t *status);
+
+fa_status fa_server_stats(fa_server *sv, fa_server_stats_t *out);
+
+/* Finishes every queued request, then stops the loop and frees its memory. */
+void fa_server_destroy(fa_server *sv);
+
+/* ------------------------------------------------------------------------- */
 /* Test hooks (host buffers)                                                 */
 /* ------------------------------------------------------------------------- */
 

@@ -64,6 +64,16 @@ class fa_tune_result(C.Structure):
                 ("persistent", i32 * 8), ("tile_chunks", i32 * 8), ("ms", f32 * 8)]
 
 
+class fa_server_params(C.Structure):
+    _fields_ = [("max_batch", i32), ("window_us", i32), ("slots", i32), ("kmax", i32),
+                ("nprobe_max", i32), ("pad0", i32), ("mem_budget_bytes", i64)]
+
+
+class fa_server_stats_t(C.Structure):
+    _fields_ = [("batches", i64), ("requests", i64), ("pending", i64), ("device_bytes", i64),
+                ("inflight_batches", i32), ("slots", i32)]
+
+
 class fa_search_params(C.Structure):
     _fields_ = [("lut_prec", i32), ("lut_gemm", i32), ("probe_gemm", i32), ("rerank_n", i32),
                 ("rerank_batch", i32), ("rerank_beta", i32), ("rerank_eps", f32), ("flags", i32),
@@ -95,6 +105,12 @@ _sig("fa_debug_probes", i32, P, P, i64, i32, P, P)
 _sig("fa_debug_candidates", i32, P, P, i32, P, P, i64, P)
 _sig("fa_debug_lut", i32, P, P, P, P)
 _sig("fa_coarse_probe_noalloc", i32, P, i64, i32, P, i32, i32, P, P)
+_sig("fa_server_params_init", None, P)
+_sig("fa_server_create", i32, P, P, P, P)
+_sig("fa_server_submit", i32, P, P, i64, P, P, P)
+_sig("fa_server_poll", i64, P, i64, i32, P, P, P, i32, P, P)
+_sig("fa_server_stats", i32, P, P)
+_sig("fa_server_destroy", None, P)
 _sig("fa_last_error", C.c_char_p)
 _sig("fa_status_str", C.c_char_p, i32)
 _sig("fa_version", C.c_char_p)
@@ -104,7 +120,9 @@ EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_build_index_lists", "fa
            "fa_index_get_parts",
            "fa_index_info_get", "fa_save_index", "fa_load_index", "fa_free_index",
            "fa_search_params_init", "fa_search", "fa_search_ex", "fa_autotune", "fa_debug_probes",
-           "fa_debug_candidates", "fa_debug_lut", "fa_coarse_probe_noalloc", "fa_last_error",
+           "fa_debug_candidates", "fa_debug_lut", "fa_coarse_probe_noalloc", "fa_server_params_init",
+           "fa_server_create", "fa_server_submit", "fa_server_poll", "fa_server_stats",
+           "fa_server_destroy", "fa_last_error",
            "fa_status_str", "fa_version")
 
 
@@ -385,6 +403,54 @@ def fa_coarse_probe_noalloc(queries, centroids, nprobe: int, out=None, stream=No
     _check(_lib.fa_coarse_probe_noalloc(_ptr(queries), nq, d, _ptr(centroids), nl, nprobe,
                                         _ptr(out), stream))
     return out
+
+
+class Server:
+    """Request loop with continuous batching (fa_server_*)."""
+
+    def __init__(self, ix: Index, params: fa_search_params | None = None, **kw):
+        p = fa_server_params()
+        _lib.fa_server_params_init(C.byref(p))
+        for key, v in kw.items():
+            setattr(p, key, v)
+        self.kmax = p.kmax
+        self.ix = ix  # keeps the index alive
+        h = P()
+        _check(_lib.fa_server_create(ix.handle, C.byref(p),
+                                     C.byref(params) if params is not None else None, C.byref(h)))
+        self.handle = h
+
+    def submit(self, queries, k, nprobe) -> np.ndarray:
+        q = np.ascontiguousarray(queries, dtype=np.float32).reshape(-1, queries.shape[-1])
+        n = q.shape[0]
+        kk = np.ascontiguousarray(np.broadcast_to(k, (n,)), dtype=np.int32)
+        nn = np.ascontiguousarray(np.broadcast_to(nprobe, (n,)), dtype=np.int32)
+        rid = np.empty(n, dtype=np.int64)
+        _check(_lib.fa_server_submit(self.handle, _ptr(q), n, _ptr(kk), _ptr(nn), _ptr(rid)))
+        return rid
+
+    def poll(self, max_results=4096, timeout_us=1000):
+        rid = np.empty(max_results, dtype=np.int64)
+        ids = np.empty((max_results, self.kmax), dtype=np.int64)
+        dist = np.empty((max_results, self.kmax), dtype=np.float32)
+        lat = np.empty(max_results, dtype=np.float64)
+        st = np.empty(max_results, dtype=np.int32)
+        n = _lib.fa_server_poll(self.handle, max_results, timeout_us, _ptr(rid), _ptr(ids),
+                                _ptr(dist), self.kmax, _ptr(lat), _ptr(st))
+        return rid[:n], ids[:n], dist[:n], lat[:n], st[:n]
+
+    def stats(self) -> fa_server_stats_t:
+        out = fa_server_stats_t()
+        _check(_lib.fa_server_stats(self.handle, C.byref(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value:
+            _lib.fa_server_destroy(self.handle)
+            self.handle = P(None)
+
+    def __del__(self):
+        self.close()
 
 
 def fa_last_error() -> str:

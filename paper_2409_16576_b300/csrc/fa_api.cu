@@ -381,13 +381,6 @@ struct WsLease {
     }
 };
 
-static int32_t max_changed_for(float eps, int32_t k) {
-    // largest c in [0, k] with c / k <= eps (Algorithm 1's test on Eq. 3)
-    int32_t best = -1;
-    for (int32_t c = 0; c <= k; ++c)
-        if ((double)c / (double)k <= (double)eps) best = c;
-    return best;
-}
 
 // CUDA-event marks between the stages of one call (only when a trace is asked).
 struct Tracer {
@@ -559,7 +552,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
 
         if (rerank)
             launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
-                          max_changed_for(sp.rerank_eps, k), oid, odist, sp.stats ? w->stats : nullptr, st);
+                          sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, st);
         else
             launch_finish(D, w->topkeys, nq, ntop, k, kq, oid, odist, st);
         tr.launches += 1;

@@ -181,7 +181,7 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
 template <int R, typename T>
 __global__ void __launch_bounds__(256) k_rerank(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
-    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, int32_t max_changed,
+    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
     const int64_t *__restrict__ perm, const T *__restrict__ raw, int64_t *__restrict__ out_ids,
     float *__restrict__ out_dist, int32_t *stats) {
     extern __shared__ float qsm[];
@@ -237,7 +237,8 @@ __global__ void __launch_bounds__(256) k_rerank(
                 }
             changed += __popc(__ballot_sync(FULL, fresh));
         }
-        if (changed <= max_changed) {
+        // Algorithm 1's test on Eq. 3, with this query's own k
+        if ((double)changed / (double)kk <= (double)eps) {
             ++counter;
             if (counter >= beta) break;
         } else {
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(256) k_rerank(
 template <typename T>
 static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_t *topkeys,
                             int64_t nq, int32_t ntop, int32_t k, const int32_t *kq, int32_t batch,
-                            int32_t beta, int32_t max_changed, int64_t *out_ids, float *out_dist,
+                            int32_t beta, float eps, int64_t *out_ids, float *out_dist,
                             int32_t *stats, cudaStream_t st) {
     const dim3 grid((unsigned)((nq + 7) / 8));
     const int smem = 8 * ix.d * 4;
@@ -272,7 +273,7 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
         FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T>,                                       \
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
         k_rerank<RR, T><<<grid, 256, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, batch, beta,  \
-                                                 max_changed, ix.perm, raw, out_ids, out_dist,    \
+                                                 eps, ix.perm, raw, out_ids, out_dist,            \
                                                  stats);                                          \
     } while (0)
     if (k <= 32)
@@ -289,16 +290,16 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
 
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
-                   int32_t max_changed, int64_t *out_ids, float *out_dist, int32_t *stats,
+                   float eps, int64_t *out_ids, float *out_dist, int32_t *stats,
                    cudaStream_t st) {
     if (nq == 0) return;
     FA_REQUIRE(ix.raw != nullptr, FA_ERR_ARG, "re-rank needs raw vectors in the index");
     if (ix.raw_dtype == FA_U8) {
         FA_REQUIRE(ix.d % 4 == 0, FA_ERR_ARG, "uint8 re-rank needs d % 4 == 0");
-        launch_rerank_t<uint8_t>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, max_changed,
+        launch_rerank_t<uint8_t>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
                                  out_ids, out_dist, stats, st);
     } else {
-        launch_rerank_t<float>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, max_changed,
+        launch_rerank_t<float>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
                                out_ids, out_dist, stats, st);
     }
 }

@@ -385,6 +385,63 @@ def test_build_with_given_lists(fa):
         _check_topk(gi[i], gd[i], oi[i, :10], od[i, :10], od[i, 10], 10, what=str(i))
 
 
+def _serve_all(srv, n):
+    got = {}
+    while len(got) < n:
+        rid, ids, dist, lat, st = srv.poll(timeout_us=20000)
+        for j in range(rid.shape[0]):
+            assert st[j] == 0
+            got[int(rid[j])] = (ids[j], dist[j], lat[j])
+    return got
+
+
+@pytest.mark.parametrize("lowp", [False, True])
+def test_serving_result_same_alone_and_in_the_mix(fa, u8_repl, lowp):
+    """Continuous batching: every request's result equals the result of the
+    same query searched alone (same k, nprobe and parameters), bit for bit."""
+    s = u8_repl
+    tc = fa.FA_GEMM_BF16_TC
+    p = fa.search_params(lut_prec=fa.FA_LUT_F16, lut_gemm=tc, probe_gemm=tc, rerank_n=50,
+                         rerank_eps=0.0) if lowp else fa.search_params()
+    rng = np.random.default_rng(4)
+    n = 120
+    q = np.concatenate([s["q"]] * 3)[:n]
+    ks = rng.choice([1, 10, 32], size=n).astype(np.int32)
+    nps = rng.integers(1, 33, size=n).astype(np.int32)
+    srv = fa.Server(s["ix"], p, max_batch=16, window_us=300, slots=3, kmax=32, nprobe_max=32)
+    try:
+        rid = np.concatenate([srv.submit(q[i:i + 10], ks[i:i + 10], nps[i:i + 10])
+                              for i in range(0, n, 10)])
+        got = _serve_all(srv, n)
+        st = srv.stats()
+        assert st.requests == n and st.batches >= n // 16
+    finally:
+        srv.close()
+    for i in range(n):
+        ids, dist, _ = got[int(rid[i])]
+        ai, ad = fa.fa_search_ex(s["ix"], q[i:i + 1], int(ks[i]), int(nps[i]), p)
+        assert np.array_equal(ids[:ks[i]], ai[0]) and np.array_equal(dist[:ks[i]], ad[0]), i
+        assert np.all(ids[ks[i]:] == -1)
+
+
+def test_serving_admits_by_slots(fa, f32_small):
+    """One memory slot: batches run one after another, every request completes."""
+    s = f32_small
+    srv = fa.Server(s["ix"], None, max_batch=8, window_us=50, slots=1, kmax=10, nprobe_max=8)
+    try:
+        q = np.concatenate([s["q"]] * 6)
+        rid = srv.submit(q, 10, 8)
+        got = _serve_all(srv, q.shape[0])
+        st = srv.stats()
+        assert st.slots == 1 and st.batches >= q.shape[0] // 8
+        assert all(got[int(r)][2] > 0 for r in rid)
+    finally:
+        srv.close()
+    ref = fa.fa_search(s["ix"], q[:5], 10, 8)
+    for i in range(5):
+        assert np.array_equal(got[int(rid[i])][0], ref[0][i])
+
+
 def test_per_query_k_and_nprobe(fa, f32_small):
     s = f32_small
     q = s["q"][:20]
