@@ -68,6 +68,11 @@ def parse():
     ap.add_argument("--workload", default="sift10m", choices=["sift10m", "zipf"],
                     help="zipf: the batching-form workload (Zipf lists, per-query nprobe)")
     ap.add_argument("--zipf-n", type=int, default=100_000_000)
+    ap.add_argument("--serve", action="store_true",
+                    help="serving form: open-loop Poisson arrivals on the Zipf-lists index")
+    ap.add_argument("--rates", default="5000,10000,20000,50000,100000")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--window-us", type=int, default=500)
     return ap.parse_args()
 
 
@@ -277,6 +282,8 @@ def main():
 
     if args.impl == "reference":
         return reference_arm(args, wl, rank, world)
+    if args.serve:
+        return bench_serve(args)
     if args.workload == "zipf":
         return bench_zipf(args)
 
@@ -518,6 +525,78 @@ def bench_zipf(args):
                      "algorithmic_bytes_per_launch": scan_bytes},
         "clocks": clk, "build_s": t_build, "gen_s": t_gen,
     }))
+
+
+def bench_serve(args):
+    """Serving form on the Zipf-lists index: requests with k uniform in
+    {1, 10, 100} and nprobe uniform in 32..256 arrive as an open-loop Poisson
+    process at each offered rate; the request loop batches them continuously.
+    Reports sustained QPS (completed / elapsed), p50 and p99 latency from
+    submit to completion."""
+    import threading as th
+    import paper_2409_16576_b300 as fa
+    import torch
+    torch.cuda.set_device(0)
+    z = synth.ZipfLists(args.zipf_n)
+    t0 = time.perf_counter()
+    base = z.base()
+    ix = fa.fa_build_index_lists(base, z.centroids(), z.primary(), fa.build_params(M=48, kmeans_iters=10))
+    del base
+    t_build = time.perf_counter() - t0
+    pool = z.queries(20000)
+    tc = fa.FA_GEMM_BF16_TC
+    sp = fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc)
+    srv = fa.Server(ix, sp, max_batch=4096, window_us=args.window_us, slots=4, kmax=100,
+                    nprobe_max=256)
+    results = []
+    for rate in [float(r) for r in args.rates.split(",")]:
+        count = int(rate * args.serve_seconds)
+        arr = synth.poisson_arrivals(rate, count)
+        ks = np.array([1, 10, 100], dtype=np.int32)[synth.uniform_ints(0, 2, count, tag=11)]
+        nps = synth.uniform_ints(32, 256, count, tag=12)
+        qi = np.arange(count) % pool.shape[0]
+        lat = np.empty(count)
+        done_t = [0.0]
+        got = [0]
+
+        def collect():
+            while got[0] < count:
+                rid, _, _, l, st = srv.poll(max_results=8192, timeout_us=2000)
+                if rid.shape[0]:
+                    lat[got[0]:got[0] + rid.shape[0]] = l
+                    got[0] += rid.shape[0]
+                    done_t[0] = time.perf_counter()
+
+        c = th.Thread(target=collect)
+        c.start()
+        start = time.perf_counter()
+        i = 0
+        while i < count:
+            now = time.perf_counter() - start
+            j = int(np.searchsorted(arr, now, side="right"))
+            if j > i:
+                srv.submit(pool[qi[i:j]], ks[i:j], nps[i:j])
+                i = j
+            else:
+                time.sleep(min(2e-4, max(0.0, arr[i] - now)))
+        c.join()
+        elapsed = done_t[0] - start
+        results.append({"offered_qps": rate, "requests": count,
+                        "sustained_qps": count / elapsed, "p50_ms": float(np.percentile(lat, 50)) / 1e3,
+                        "p99_ms": float(np.percentile(lat, 99)) / 1e3,
+                        "mean_ms": float(lat.mean()) / 1e3})
+        print(json.dumps(results[-1]), flush=True)
+        if results[-1]["sustained_qps"] < 0.5 * rate:
+            break  # far beyond capacity: higher rates only grow the queue
+    st = srv.stats()
+    srv.close()
+    print(json.dumps({"serving": results, "batches": st.batches, "requests": st.requests,
+                      "slots": st.slots, "slot_device_bytes": st.device_bytes,
+                      "config": {"workload": "ivfpq-f32unit-%dm-d96-zipf65536-M48" % (args.zipf_n // 1_000_000),
+                                 "k": "uniform {1,10,100}", "nprobe": "uniform 32..256",
+                                 "window_us": args.window_us, "max_batch": 4096, "slots": 4,
+                                 "form": "fp8 LUT, BF16 tensor-core probe and LUT"},
+                      "build_s": t_build}))
 
 
 def sweep(args, wl, fa, torch, oracle, ix, base, queries, qd, flush, gt, t_build):
