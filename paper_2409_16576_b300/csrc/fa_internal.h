@@ -129,6 +129,8 @@ struct Workspace {
     float *lut_scale = nullptr;    // [cap_nq][2M] per subspace: scale, offset
     float *coarse_d = nullptr;     // coarse distance scratch [coarse_rows][nlist]
     int64_t coarse_rows = 0;
+    uint64_t *probe_lists = nullptr;  // fused tensor-core probe: per-query key queues
+    size_t probe_bytes = 0;
     uint32_t *err = nullptr;       // device error word
     uint32_t *tile_ctr = nullptr;  // persistent-kernel work counters
     // pinned host staging for host-buffer calls
@@ -235,13 +237,17 @@ struct ScanLaunch {
 void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
                    int32_t probe_stride, int gemm, Workspace &ws, int32_t *probes,
                    cudaStream_t st);
-int coarse_launches(const DeviceIndex &ix, int64_t nq, const Workspace &ws);
+int coarse_launches(const DeviceIndex &ix, int64_t nq, int gemm, const Workspace &ws);
 void prepare_centroid_tiles(const float *cent, int32_t nlist, int32_t d, std::vector<uint16_t> &out,
                             int32_t &Kp, int32_t &ntiles);
 void prepare_codebook_tiles(const float *cb, int32_t M, int32_t d, std::vector<uint16_t> &tiles,
                             std::vector<float> &norms);
 void launch_coarse_tc_dist(const DeviceIndex &ix, const float *q, int64_t rows, float *D,
                            int64_t ldd, uint32_t *err, cudaStream_t st);
+size_t probe_tc_scratch_bytes(const DeviceIndex &ix, int64_t nq, int32_t ntop);
+void launch_probe_tc(const DeviceIndex &ix, const float *q, int64_t nq, int32_t ntop, int32_t *probes,
+                     int32_t probe_stride, uint64_t *scratch, size_t scratch_bytes, uint32_t *err,
+                     cudaStream_t st);
 void launch_query_order(const int32_t *probes, int64_t nq, int32_t stride, int32_t nlist,
                         uint32_t *cnt, int32_t *order, cudaStream_t st);
 void launch_tile_plan(const DeviceIndex &ix, const int32_t *probes, const int32_t *npq, int64_t nq,

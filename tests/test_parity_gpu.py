@@ -195,6 +195,46 @@ def test_coarse_probe_tc_matches_oracle(fa, f32_small, u8_repl, which):
         assert np.all(gd2 <= d2[i, npb - 1] + 4e-5 * mag), i
 
 
+def _probe_index(fa, d, nlist, nq, seed):
+    """An index over clustered centroids (d <= 128) that only the probe reads."""
+    mix = synth.Mixture(d, 32, 4.0, lo=-20.0, hi=20.0, seed=seed)
+    cent = mix.base(nlist)
+    M = d // 4
+    cb = np.zeros((M, 256, 4), np.float32)
+    codes = np.zeros((64, M), np.uint8)
+    prim = (np.arange(64) % nlist).astype(np.int32)
+    return fa.fa_index_from_parts(cent, cb, codes, prim), cent, mix.queries(nq)
+
+
+@pytest.mark.parametrize("d,nlist,nq,n", [
+    (128, 1000, 300, 1), (128, 1000, 300, 8), (128, 1000, 300, 33), (128, 1000, 300, 64),
+    (128, 1000, 300, 100), (128, 1000, 300, 256), (128, 1000, 300, 512),
+    (96, 5000, 1000, 40), (64, 8192, 2000, 128), (32, 300, 129, 200), (128, 16384, 1, 64)])
+def test_fused_tc_probe_shapes(fa, d, nlist, nq, n):
+    """Fused tensor-core probe (distances and top-nprobe in one kernel) over
+    ragged query and centroid tiles, CTA ranges that cross query tiles, and
+    queues that fill and compact: n distinct lists per query, in distance
+    order, each within the expanded form's rounding of the oracle's n-th
+    distance, and every oracle list it leaves out at that boundary."""
+    ix, cent, q = _probe_index(fa, d, nlist, nq, seed=d + nlist + n)
+    got = fa.fa_debug_probes(ix, q, n, fa.search_params(probe_gemm=fa.FA_GEMM_BF16_TC))
+    ref, d2 = oracle.coarse(q, cent, n, with_d2=True)
+    c64 = cent.astype(np.float64)
+    cn = (c64 ** 2).sum(1)
+    for i in range(nq):
+        g = got[i]
+        assert g.min() >= 0 and g.max() < nlist and len(set(g.tolist())) == n, i
+        q64 = q[i].astype(np.float64)
+        tol = 4e-5 * ((q64 ** 2).sum() + cn.max())
+        gd = ((c64[g] - q64) ** 2).sum(1)
+        kth = d2[i, n - 1]
+        assert np.all(gd <= kth + tol), i
+        assert np.all(np.diff(gd) >= -tol), i
+        missing = np.array(sorted(set(ref[i].tolist()) - set(g.tolist())), dtype=np.int64)
+        if missing.size:
+            assert np.all(((c64[missing] - q64) ** 2).sum(1) >= kth - tol), i
+
+
 # ---------------------------------------------------------------------------
 # steps 3-5: gather + dedup (bit-exact)
 # ---------------------------------------------------------------------------
