@@ -199,8 +199,8 @@ def _probe_index(fa, d, nlist, nq, seed):
     """An index over clustered centroids (d <= 128) that only the probe reads."""
     mix = synth.Mixture(d, 32, 4.0, lo=-20.0, hi=20.0, seed=seed)
     cent = mix.base(nlist)
-    M = d // 4
-    cb = np.zeros((M, 256, 4), np.float32)
+    M = {128: 32, 96: 48, 64: 16, 32: 8}[d]
+    cb = np.zeros((M, 256, d // M), np.float32)
     codes = np.zeros((64, M), np.uint8)
     prim = (np.arange(64) % nlist).astype(np.int32)
     return fa.fa_index_from_parts(cent, cb, codes, prim), cent, mix.queries(nq)
