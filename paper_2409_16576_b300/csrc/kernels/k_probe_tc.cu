@@ -18,11 +18,11 @@
 //   - meanwhile all 8 warps run the epilogue of tile i-1 from the other
 //     accumulator. Warps w and w+4 read the same 32 TMEM lanes (queries) and
 //     split the 128 columns in halves.
-// Selection: each (query, column half) keeps a threshold, the current n-th
-// smallest key (distance, list id) it has seen, and appends keys below it to
-// a private queue in global memory. A full queue is cut back to its n smallest
-// by the warp together (the bitonic top-n of warp_topk.cuh), which also
-// tightens the threshold. At the end of a range every queue holds its n
+// Selection: each (query, column half) appends the keys (distance, list id)
+// below the query's threshold to a private queue in global memory. A full
+// queue is cut back to its n smallest by the warp together (the bitonic top-n
+// of warp_topk.cuh); its n-th smallest then bounds the query's threshold,
+// which the two halves share in shared memory. At the end of a range every queue holds its n
 // smallest keys, sorted; k_probe_merge takes each query's n smallest over its
 // queues. Keys order by (distance, list id), so the result is the same set
 // and order as a full sort of the distance row.
@@ -58,21 +58,36 @@ struct ProbeArgs {
     uint32_t *err;
 };
 
-// Cuts the queue of lane `src` back to its n smallest keys (sorted, padded
-// with KEY_INF to n) and returns the new threshold to that lane.
+// Cuts the queue of lane `src` back to its n smallest keys, sorted and padded
+// with KEY_INF to n. The queue is its sorted part [0, nsorted) followed by the
+// keys appended since [nsorted, cnt); both are loaded at once, the sorted part
+// straight into the top-n registers, and only the new keys are merged. The
+// new n-th smallest tightens the query's shared threshold.
 template <int R>
-__device__ __forceinline__ void compact(uint64_t *myq, int &cnt, uint64_t &tau, float &tau_d,
-                                        int src, int n, uint64_t *wbuf) {
+__device__ __forceinline__ void compact(uint64_t *myq, int &cnt, int &nsorted,
+                                        unsigned long long *tsh, int src, int n, uint64_t *wbuf) {
     const int lane = threadIdx.x & 31;
     uint64_t *base = reinterpret_cast<uint64_t *>(shfl64(reinterpret_cast<uint64_t>(myq), src));
     const int c = __shfl_sync(FULL, cnt, src);
+    const int ns = __shfl_sync(FULL, nsorted, src);
     __syncwarp();
     WarpTopK<R> tk;
     tk.init(wbuf, n);
-    for (int o = 0; o < c; o += 32) {
-        const bool ok = o + lane < c;
-        tk.push(ok ? base[o + lane] : KEY_INF, ok);
+    uint64_t nk[R + 2];  // c - ns <= 32 R + 64 new keys
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        tk.L[r] = e < ns ? base[e] : KEY_INF;
     }
+#pragma unroll
+    for (int b = 0; b < R + 2; ++b) {
+        const int e = ns + b * 32 + lane;
+        nk[b] = e < c ? base[e] : KEY_INF;
+    }
+    if (ns >= n) tk.thr = warp_elem<R>(tk.L, n - 1);
+#pragma unroll
+    for (int b = 0; b < R + 2; ++b)
+        if (ns + b * 32 < c) tk.push(nk[b], ns + b * 32 + lane < c);
     tk.finish();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -80,12 +95,9 @@ __device__ __forceinline__ void compact(uint64_t *myq, int &cnt, uint64_t &tau, 
         if (e < n) base[e] = tk.L[r];
     }
     const uint64_t kth = warp_elem<R>(tk.L, n - 1);
+    if (lane == 0 && kth != KEY_INF) atomicMin(tsh + src, (unsigned long long)kth);
     __syncwarp();
-    if (lane == src) {
-        cnt = c < n ? c : n;
-        tau = kth;
-        tau_d = kth == KEY_INF ? INFINITY : o2f((uint32_t)(kth >> 32));
-    }
+    if (lane == src) cnt = nsorted = c < n ? c : n;
 }
 
 template <int R>
@@ -94,6 +106,9 @@ __global__ void __launch_bounds__(PT, 1) k_probe_tc(const ProbeArgs a) {
     __shared__ __align__(8) uint64_t full[2], mdone[2];
     __shared__ uint32_t tmem_base;
     __shared__ uint64_t wbuf[PT / 32][64];
+    // per query of the tile: the smallest n-th-smallest key over its two queues;
+    // no key at or above it can be among the query's n nearest lists
+    __shared__ unsigned long long tau_sh[PQ];
     const int Kp = a.Kp;
     const uint32_t half_bytes = (uint32_t)PN * Kp * 2;  // hi (or lo) of one 128-centroid tile
     __nv_bfloat16 *Ahi = reinterpret_cast<__nv_bfloat16 *>(sm);
@@ -162,9 +177,9 @@ __global__ void __launch_bounds__(PT, 1) k_probe_tc(const ProbeArgs a) {
                 qn = fmaf(x, x, qn);
             }
         uint64_t *myq = rv ? a.lists + (((size_t)row * a.segmax + seg) * 2 + colh) * a.cap : nullptr;
-        int cnt = 0;
-        uint64_t tau = KEY_INF;
-        float tau_d = INFINITY;
+        unsigned long long *tsh = tau_sh + quad * 32;
+        int cnt = 0, nsorted = 0;
+        if (tid < PQ) tau_sh[tid] = KEY_INF;
         tc::fence_proxy_async();
         __syncthreads();
         if (tid == 0) {
@@ -222,9 +237,11 @@ __global__ void __launch_bounds__(PT, 1) k_probe_tc(const ProbeArgs a) {
                 uint32_t need = __ballot_sync(FULL, rv && cnt + 32 > a.cap);
                 while (need) {
                     const int src = __ffs(need) - 1;
-                    compact<R>(myq, cnt, tau, tau_d, src, a.n, wbuf[warp]);
+                    compact<R>(myq, cnt, nsorted, tsh, src, a.n, wbuf[warp]);
                     need &= need - 1;
                 }
+                const uint64_t tau = *reinterpret_cast<volatile unsigned long long *>(tsh + lane);
+                const float tau_d = tau == KEY_INF ? INFINITY : o2f((uint32_t)(tau >> 32));
                 if (rv) {
                     const int l0 = lbase + c0;
 #pragma unroll
@@ -248,9 +265,11 @@ __global__ void __launch_bounds__(PT, 1) k_probe_tc(const ProbeArgs a) {
         uint32_t m = __ballot_sync(FULL, rv);
         while (m) {
             const int src = __ffs(m) - 1;
-            compact<R>(myq, cnt, tau, tau_d, src, a.n, wbuf[warp]);
+            compact<R>(myq, cnt, nsorted, tsh, src, a.n, wbuf[warp]);
             m &= m - 1;
         }
+        // the thresholds are reset for the next query tile only after every warp is done
+        __syncthreads();
         g = s_end;
     }
     if (failed && tid == 0) {
@@ -317,7 +336,7 @@ ProbePlan probe_plan(int32_t nlist, int64_t nq, int32_t ntop) {
     p.grid = (int32_t)((p.total + p.per - 1) / p.per);
     p.segmax = std::min<int32_t>(p.grid, (p.nt + p.per - 1) / p.per + 1);
     p.R = ntop <= 32 ? 1 : ntop <= 64 ? 2 : ntop <= 128 ? 4 : ntop <= 256 ? 8 : 16;
-    p.cap = 2 * 32 * p.R + 64;
+    p.cap = 32 * p.R + 64;
     p.bytes = (size_t)nq * p.segmax * 2 * p.cap * sizeof(uint64_t);
     return p;
 }
