@@ -55,6 +55,7 @@ struct ProbeArgs {
     int32_t cap;                 // queue capacity (keys)
     int32_t n;                   // lists wanted per query
     uint64_t *lists;             // [rows][segmax][2][cap]
+    unsigned long long *gtau;    // [rows] per-query threshold shared by the CTAs on its tile
     uint32_t *err;
 };
 
@@ -65,9 +66,12 @@ struct ProbeArgs {
 // new n-th smallest tightens the query's shared threshold.
 template <int R>
 __device__ __forceinline__ void compact(uint64_t *myq, int &cnt, int &nsorted,
-                                        unsigned long long *tsh, int src, int n, uint64_t *wbuf) {
+                                        unsigned long long *tsh, unsigned long long *gt, int src,
+                                        int n, uint64_t *wbuf) {
     const int lane = threadIdx.x & 31;
     uint64_t *base = reinterpret_cast<uint64_t *>(shfl64(reinterpret_cast<uint64_t>(myq), src));
+    unsigned long long *gsrc =
+        reinterpret_cast<unsigned long long *>(shfl64(reinterpret_cast<uint64_t>(gt), src));
     const int c = __shfl_sync(FULL, cnt, src);
     const int ns = __shfl_sync(FULL, nsorted, src);
     __syncwarp();
@@ -95,18 +99,25 @@ __device__ __forceinline__ void compact(uint64_t *myq, int &cnt, int &nsorted,
         if (e < n) base[e] = tk.L[r];
     }
     const uint64_t kth = warp_elem<R>(tk.L, n - 1);
-    if (lane == 0 && kth != KEY_INF) atomicMin(tsh + src, (unsigned long long)kth);
+    if (lane == 0 && kth != KEY_INF) {
+        atomicMin(tsh + src, (unsigned long long)kth);
+        atomicMin(gsrc, (unsigned long long)kth);
+    }
     __syncwarp();
     if (lane == src) cnt = nsorted = c < n ? c : n;
 }
 
 template <int R>
-__global__ void __launch_bounds__(PT, 1) k_probe_tc(const ProbeArgs a) {
+__global__ void __launch_bounds__(PT + 32, 1) k_probe_tc(const ProbeArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t full[2], mdone[2];
+    // full[s]: centroid stage s loaded; accf[b]: accumulator b written (MMAs
+    // done, which also frees the stage they read); acce[b]: accumulator b read
+    // by all 8 epilogue warps; aready: the query tile is in shared memory
+    __shared__ __align__(8) uint64_t full[2], accf[2], acce[2], aready;
     __shared__ uint32_t tmem_base;
+    __shared__ volatile int abort_flag;
     __shared__ uint64_t wbuf[PT / 32][64];
-    // per query of the tile: the smallest n-th-smallest key over its two queues;
+    // per query of the tile: the smallest n-th-smallest key over its queues;
     // no key at or above it can be among the query's n nearest lists
     __shared__ unsigned long long tau_sh[PQ];
     const int Kp = a.Kp;
@@ -115,170 +126,208 @@ __global__ void __launch_bounds__(PT, 1) k_probe_tc(const ProbeArgs a) {
     __nv_bfloat16 *Alo = Ahi + PQ * Kp;
     unsigned char *Bs = sm + (size_t)2 * PQ * Kp * 2;  // 2 stages x (hi, lo)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int quad = warp & 3, colh = warp >> 2;
     const int64_t g0 = (int64_t)blockIdx.x * a.per;
     const int64_t g1 = min(a.total, g0 + a.per);
     if (g0 >= g1) return;
+    const int ntiles = (int)(g1 - g0);
 
     if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * PN);
     if (tid == 0) {
-        tc::mbar_init(&full[0], 1);
-        tc::mbar_init(&full[1], 1);
-        tc::mbar_init(&mdone[0], 1);
-        tc::mbar_init(&mdone[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&accf[i], 1);
+            tc::mbar_init(&acce[i], PT / 32);
+        }
+        tc::mbar_init(&aready, 1);
+        abort_flag = 0;
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = tmem_base;
-    const uint32_t idesc = tc::idesc_bf16_f32(PQ, PN);
-    const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
-    const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
-    // bit s: phase parity to wait for next on full[s] / mdone[s]; copies and
-    // MMAs in flight (thread 0's view), kept as bit masks so nothing is indexed
-    // at run time
-    uint32_t fph = 0u, mph = 0u, lpend = 0u, mpend = 0u;
-    bool failed = false;
 
-    auto issue_load = [&](int s, int64_t gi) {
-        const int t128 = (int)(gi % a.nt);
-        const __nv_bfloat16 *hi = a.tiles + (size_t)(t128 >> 1) * 2 * 256 * Kp + (size_t)(t128 & 1) * PN * Kp;
-        const __nv_bfloat16 *lo = hi + (size_t)256 * Kp;
-        unsigned char *dst = Bs + (size_t)s * 2 * half_bytes;
-        tc::mbar_expect_tx(&full[s], 2 * half_bytes);
-        tc::bulk_g2s(dst, hi, half_bytes, &full[s]);
-        tc::bulk_g2s(dst + half_bytes, lo, half_bytes, &full[s]);
-        lpend |= 1u << s;
-    };
-
-    int64_t g = g0;
-    while (g < g1 && !failed) {
-        const int64_t qt = g / a.nt;
-        const int64_t s_end = min(g1, (qt + 1) * a.nt);
-        const int nseg = (int)(s_end - g);
-        const int seg = (int)(blockIdx.x - (qt * a.nt) / a.per);
-        const int64_t r0 = qt * PQ;
-        // A: this query tile as bf16 hi/lo (every MMA on the previous tile is done)
-        for (int e = tid; e < PQ * Kp; e += PT) {
-            const int r = e / Kp, k = e - r * Kp;
-            const float x = (r0 + r < a.rows && k < a.d) ? a.q[(r0 + r) * a.d + k] : 0.f;
-            __nv_bfloat16 h, l;
-            tc::split_bf16(x, h, l);
-            const uint32_t o = tc::core_offset(r, k, Kp) >> 1;
-            Ahi[o] = h;
-            Alo[o] = l;
-        }
-        const int64_t row = r0 + quad * 32 + lane;
-        const bool rv = row < a.rows;
-        float qn = 0.f;
-        if (rv)
-            for (int k = 0; k < a.d; ++k) {
-                const float x = a.q[row * a.d + k];
-                qn = fmaf(x, x, qn);
-            }
-        uint64_t *myq = rv ? a.lists + (((size_t)row * a.segmax + seg) * 2 + colh) * a.cap : nullptr;
-        unsigned long long *tsh = tau_sh + quad * 32;
-        int cnt = 0, nsorted = 0;
-        if (tid < PQ) tau_sh[tid] = KEY_INF;
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            issue_load(0, g);
-            if (nseg > 1) issue_load(1, g + 1);
-        }
-        for (int i = 0; i <= nseg; ++i) {
+    if (warp == PT / 32) {
+        // ---- producer: centroid tiles in, MMAs out (one thread) ----
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(PQ, PN);
+            const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
+            const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
+            int kl0 = -1, kl1 = -1;  // tile whose copy into stage 0 / 1 is in flight
+            int committed = -1;      // last tile whose MMAs were committed
             bool ok = true;
-            if (i < nseg && tid == 0) {
-                const int s = i & 1;
-                ok = tc::mbar_wait(&full[s], (fph >> s) & 1u, PWAIT);
-                if (ok) {
-                    fph ^= 1u << s;
-                    lpend &= ~(1u << s);
+            auto issue_load = [&](int s, int kt) {
+                const int t128 = (int)((g0 + kt) % a.nt);
+                const __nv_bfloat16 *hi =
+                    a.tiles + (size_t)(t128 >> 1) * 2 * 256 * Kp + (size_t)(t128 & 1) * PN * Kp;
+                unsigned char *dst = Bs + (size_t)s * 2 * half_bytes;
+                tc::mbar_expect_tx(&full[s], 2 * half_bytes);
+                tc::bulk_g2s(dst, hi, half_bytes, &full[s]);
+                tc::bulk_g2s(dst + half_bytes, hi + (size_t)256 * Kp, half_bytes, &full[s]);
+                if (s == 0) kl0 = kt;
+                else kl1 = kt;
+            };
+            issue_load(0, 0);
+            if (ntiles > 1) issue_load(1, 1);
+            int segi = 0;
+            int64_t seg_end = g0;  // first tile past the current query tile
+            for (int k = 0; k < ntiles && ok; ++k) {
+                const int64_t g = g0 + k;
+                if (g >= seg_end) {  // a new query tile: wait until its queries are in place
+                    seg_end = (g / a.nt + 1) * a.nt;
+                    ok = tc::mbar_wait(&aready, segi & 1, PWAIT);
+                    ++segi;
+                    if (!ok) break;
                     tc::fence_after();
-                    const uint32_t bh = tc::smem_u32(Bs + (size_t)s * 2 * half_bytes), bl = bh + half_bytes;
-                    const uint32_t acc = tbase + (uint32_t)(i & 1) * PN;
-                    for (int ks = 0; ks < Kp / 16; ++ks) {
-                        const uint32_t off = 256u * ks;
-                        const uint64_t dah = tc::smem_desc(ah + off, 128, sbo);
-                        const uint64_t dal = tc::smem_desc(al + off, 128, sbo);
-                        const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
-                        const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
-                        tc::mma_bf16(acc, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                        tc::mma_bf16(acc, dah, dbl, idesc, 1u);
-                        tc::mma_bf16(acc, dal, dbh, idesc, 1u);
-                    }
-                    tc::mma_commit(&mdone[i & 1]);
-                    mpend |= 1u << (i & 1);
+                }
+                const int s = k & 1;
+                ok = tc::mbar_wait(&full[s], (k >> 1) & 1, PWAIT);
+                if (ok && k >= 2) ok = tc::mbar_wait(&acce[s], ((k - 2) >> 1) & 1, PWAIT);
+                if (!ok || abort_flag) break;
+                if (s == 0) kl0 = -1;
+                else kl1 = -1;
+                tc::fence_after();
+                const uint32_t bh = tc::smem_u32(Bs + (size_t)s * 2 * half_bytes), bl = bh + half_bytes;
+                const uint32_t acc = tbase + (uint32_t)s * PN;
+                for (int ks = 0; ks < Kp / 16; ++ks) {
+                    const uint32_t off = 256u * ks;
+                    const uint64_t dah = tc::smem_desc(ah + off, 128, sbo);
+                    const uint64_t dal = tc::smem_desc(al + off, 128, sbo);
+                    const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
+                    const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
+                    tc::mma_bf16(acc, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_bf16(acc, dah, dbl, idesc, 1u);
+                    tc::mma_bf16(acc, dal, dbh, idesc, 1u);
+                }
+                tc::mma_commit(&accf[s]);
+                committed = k;
+                // the other stage (tile k - 1) takes tile k + 1 once MMA k - 1 is done
+                if (k >= 1 && k + 1 < ntiles) {
+                    ok = tc::mbar_wait(&accf[s ^ 1], ((k - 1) >> 1) & 1, PWAIT);
+                    if (!ok) break;
+                    issue_load(s ^ 1, k + 1);
                 }
             }
-            if (i >= 1) {
-                const int b = (i - 1) & 1;
-                ok = ok && tc::mbar_wait(&mdone[b], (mph >> b) & 1u, PWAIT);
-                if (ok) {
-                    mph ^= 1u << b;
-                    mpend &= ~(1u << b);
+            if (!ok) {
+                atomicOr(a.err, DEV_ERR_TIMEOUT);
+                abort_flag = 1;
+            }
+            // nothing may be in flight when shared and tensor memory are released
+            if (committed >= 0) tc::mbar_wait(&accf[committed & 1], (committed >> 1) & 1, PWAIT);
+            if (kl0 >= 0) tc::mbar_wait(&full[0], (kl0 >> 1) & 1, PWAIT);
+            if (kl1 >= 0) tc::mbar_wait(&full[1], (kl1 >> 1) & 1, PWAIT);
+        }
+    } else {
+        // ---- epilogue: 8 warps, two per lane quadrant, one column half each ----
+        const int quad = warp & 3, colh = warp >> 2;
+        unsigned long long *tsh = tau_sh + quad * 32;
+        int segi = 0;
+        int k = 0;
+        bool failed = false;
+        while (k < ntiles && !failed) {
+            const int64_t g = g0 + k;
+            const int64_t qt = g / a.nt;
+            const int nseg = (int)(min(g1, (qt + 1) * a.nt) - g);
+            const int seg = (int)(blockIdx.x - (qt * a.nt) / a.per);
+            const int64_t r0 = qt * PQ;
+            // A: this query tile as bf16 hi/lo (every MMA of the previous tile is done:
+            // its last accumulator was read above)
+            for (int e = tid; e < PQ * Kp; e += PT) {
+                const int r = e / Kp, kk = e - r * Kp;
+                const float x = (r0 + r < a.rows && kk < a.d) ? a.q[(r0 + r) * a.d + kk] : 0.f;
+                __nv_bfloat16 h, l;
+                tc::split_bf16(x, h, l);
+                const uint32_t o = tc::core_offset(r, kk, Kp) >> 1;
+                Ahi[o] = h;
+                Alo[o] = l;
+            }
+            if (tid < PQ) tau_sh[tid] = KEY_INF;
+            tc::fence_proxy_async();
+            asm volatile("bar.sync 1, %0;" ::"n"(PT) : "memory");
+            if (tid == 0) tc::mbar_arrive(&aready);
+            ++segi;
+            const int64_t row = r0 + quad * 32 + lane;
+            const bool rv = row < a.rows;
+            float qn = 0.f;
+            if (rv)
+                for (int kk = 0; kk < a.d; ++kk) {
+                    const float x = a.q[row * a.d + kk];
+                    qn = fmaf(x, x, qn);
                 }
-            }
-            if (__syncthreads_or(!ok)) {
-                failed = true;
-                break;
-            }
-            if (i == 0) continue;
-            // tile j = i - 1: its MMAs are done, so its stage takes tile j + 2
-            const int j = i - 1, b = j & 1;
-            tc::fence_after();
-            if (tid == 0 && j + 2 < nseg) issue_load(b, g + j + 2);
-            const int lbase = (int)((g + j) % a.nt) * PN + colh * 64;
-            const uint32_t taddr = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * PN + colh * 64;
-#pragma unroll 1
-            for (int c0 = 0; c0 < 64; c0 += 32) {
-                float v[32];
-                tc::tmem_ld32(taddr + c0, v);
+            uint64_t *myq = rv ? a.lists + (((size_t)row * a.segmax + seg) * 2 + colh) * a.cap : nullptr;
+            unsigned long long *gt = rv ? a.gtau + row : nullptr;
+            int cnt = 0, nsorted = 0;
+            // one 32-column chunk of this thread's row: make room, then append
+            // every key below the query's threshold
+            auto chunk = [&](float(&v)[32], float cl, int l0) {
                 uint32_t need = __ballot_sync(FULL, rv && cnt + 32 > a.cap);
                 while (need) {
                     const int src = __ffs(need) - 1;
-                    compact<R>(myq, cnt, nsorted, tsh, src, a.n, wbuf[warp]);
+                    compact<R>(myq, cnt, nsorted, tsh, gt, src, a.n, wbuf[warp]);
                     need &= need - 1;
                 }
                 const uint64_t tau = *reinterpret_cast<volatile unsigned long long *>(tsh + lane);
                 const float tau_d = tau == KEY_INF ? INFINITY : o2f((uint32_t)(tau >> 32));
-                if (rv) {
-                    const int l0 = lbase + c0;
+                const uint32_t vmask =
+                    l0 + 32 <= a.nlist ? FULL : (l0 >= a.nlist ? 0u : (1u << (a.nlist - l0)) - 1u);
+                uint32_t pass = 0;
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) {
-                        const int l = l0 + e;
-                        if (l < a.nlist) {
-                            const float dd = qn - 2.f * v[e] + __ldg(a.cnorm + l);
-                            if (dd <= tau_d) {
-                                const uint64_t key = make_key(dd, (uint32_t)l);
-                                if (key < tau) myq[cnt++] = key;
-                            }
+                for (int e = 0; e < 32; ++e) {
+                    v[e] = qn - 2.f * v[e] + __shfl_sync(FULL, cl, e);
+                    pass |= (v[e] <= tau_d ? 1u : 0u) << e;
+                }
+                pass &= rv ? vmask : 0u;
+                if (pass) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if ((pass >> e) & 1u) {
+                            const uint64_t key = make_key(v[e], (uint32_t)(l0 + e));
+                            if (key < tau) myq[cnt++] = key;
                         }
-                    }
+                }
+            };
+            for (int i = 0; i < nseg; ++i, ++k) {
+                const int b = k & 1;
+                const int lbase = (int)((g0 + k) % a.nt) * PN + colh * 64;
+                // |c|^2 of this lane's column in each 32-column chunk, and the
+                // query's threshold from the other CTAs on its query tile
+                const float cl0 = lbase + lane < a.nlist ? __ldg(a.cnorm + lbase + lane) : 0.f;
+                const float cl1 = lbase + 32 + lane < a.nlist ? __ldg(a.cnorm + lbase + 32 + lane) : 0.f;
+                const unsigned long long gtv = (rv && colh == 0) ? *(volatile unsigned long long *)gt : KEY_INF;
+                bool ok = tc::mbar_wait(&accf[b], (k >> 1) & 1, PWAIT);
+                ok = __all_sync(FULL, ok) && !abort_flag;
+                if (!ok) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after();
+                float v0[32], v1[32];
+                const uint32_t taddr = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * PN + colh * 64;
+                tc::tmem_ld32(taddr, v0);
+                tc::tmem_ld32(taddr + 32, v1);
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acce[b]);
+                if (gtv != KEY_INF) atomicMin(tsh + lane, gtv);
+                chunk(v0, cl0, lbase);
+                chunk(v1, cl1, lbase + 32);
+            }
+            if (failed) {
+                abort_flag = 1;
+                if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+            } else {
+                // every queue of this range down to its sorted n smallest
+                uint32_t m = __ballot_sync(FULL, rv);
+                while (m) {
+                    const int src = __ffs(m) - 1;
+                    compact<R>(myq, cnt, nsorted, tsh, gt, src, a.n, wbuf[warp]);
+                    m &= m - 1;
                 }
             }
-            tc::fence_before();
-            __syncthreads();
+            // the thresholds and the queries are replaced only after every epilogue
+            // warp is done; a failure anywhere ends every epilogue warp here
+            asm volatile("bar.sync 1, %0;" ::"n"(PT) : "memory");
+            failed = abort_flag != 0;
         }
-        if (failed) break;
-        // every queue of this range down to its sorted n smallest
-        uint32_t m = __ballot_sync(FULL, rv);
-        while (m) {
-            const int src = __ffs(m) - 1;
-            compact<R>(myq, cnt, nsorted, tsh, src, a.n, wbuf[warp]);
-            m &= m - 1;
-        }
-        // the thresholds are reset for the next query tile only after every warp is done
-        __syncthreads();
-        g = s_end;
-    }
-    if (failed && tid == 0) {
-        atomicOr(a.err, DEV_ERR_TIMEOUT);
-        // copies and MMAs still in flight finish before shared and tensor memory go
-        for (int s = 0; s < 2; ++s)
-            if ((lpend >> s) & 1u) tc::mbar_wait(&full[s], (fph >> s) & 1u, PWAIT);
-        for (int b = 0; b < 2; ++b)
-            if ((mpend >> b) & 1u) tc::mbar_wait(&mdone[b], (mph >> b) & 1u, PWAIT);
     }
     tc::fence_before();
     __syncthreads();
@@ -337,7 +386,7 @@ ProbePlan probe_plan(int32_t nlist, int64_t nq, int32_t ntop) {
     p.segmax = std::min<int32_t>(p.grid, (p.nt + p.per - 1) / p.per + 1);
     p.R = ntop <= 32 ? 1 : ntop <= 64 ? 2 : ntop <= 128 ? 4 : ntop <= 256 ? 8 : 16;
     p.cap = 32 * p.R + 64;
-    p.bytes = (size_t)nq * p.segmax * 2 * p.cap * sizeof(uint64_t);
+    p.bytes = (size_t)nq * p.segmax * 2 * p.cap * sizeof(uint64_t) + (size_t)nq * sizeof(uint64_t);
     return p;
 }
 
@@ -345,7 +394,7 @@ template <int R>
 void launch_r(const ProbeArgs &a, const ProbePlan &p, int smem, int32_t *probes, int32_t stride,
               cudaStream_t st) {
     FA_CHECK_CUDA(cudaFuncSetAttribute(k_probe_tc<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_probe_tc<R><<<p.grid, PT, smem, st>>>(a);
+    k_probe_tc<R><<<p.grid, PT + 32, smem, st>>>(a);
     FA_CHECK_CUDA(cudaGetLastError());
     k_probe_merge<R><<<(unsigned)((a.rows + 7) / 8), 256, 0, st>>>(a.lists, a.rows, p.nt, p.per, p.segmax,
                                                                    p.cap, a.n, probes, stride);
@@ -382,7 +431,9 @@ void launch_probe_tc(const DeviceIndex &ix, const float *q, int64_t nq, int32_t 
     a.cap = p.cap;
     a.n = ntop;
     a.lists = scratch;
+    a.gtau = reinterpret_cast<unsigned long long *>(scratch + (size_t)nq * p.segmax * 2 * p.cap);
     a.err = err;
+    FA_CHECK_CUDA(cudaMemsetAsync(a.gtau, 0xFF, sizeof(uint64_t) * nq, st));
     // queries + two centroid stages; at least 116 KB so that one CTA (256 TMEM
     // columns) runs per SM and tensor-memory allocation never waits
     const int smem = std::max(3 * 2 * PQ * a.Kp * 2, 116 * 1024);
