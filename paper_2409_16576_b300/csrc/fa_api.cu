@@ -250,7 +250,7 @@ static void ws_free_buffers(Workspace *w) {
     ws_drop_graph(w);
     void *dp[] = {w->q, w->probes, w->kq, w->npq, w->order, w->bucket, w->tchunks, w->tprefix,
                   w->tmisc, w->partial, w->topkeys, w->out_ids, w->out_dist,
-                  w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr, w->probe_lists};
+                  w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr};
     for (void *p : dp)
         if (p) cudaFree(p);
     void *hp[] = {w->h_err, w->h_stats, w->h_small};
@@ -268,8 +268,6 @@ static void ws_free_buffers(Workspace *w) {
     w->lut = nullptr;
     w->lut_scale = nullptr;
     w->coarse_d = nullptr;
-    w->probe_lists = nullptr;
-    w->probe_bytes = 0;
     w->err = w->tile_ctr = nullptr;
     w->h_err = nullptr;
     w->h_stats = nullptr;
@@ -318,8 +316,10 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
         dalloc(p, (size_t)cq * cl);
         w->lut = p;
     }
-    w->coarse_rows = std::max<int64_t>(64, std::min<int64_t>(cq, (256ll << 20) / (4ll * D.nlist)));
-    dalloc(w->coarse_d, (size_t)w->coarse_rows * D.nlist);
+    // distance block of the coarse probe: up to 1 GiB of rows at a time
+    const int64_t ldd = coarse_tc_ldd(D.nlist);
+    w->coarse_rows = std::max<int64_t>(128, std::min<int64_t>(cq, (1ll << 30) / (4ll * ldd)));
+    dalloc(w->coarse_d, (size_t)w->coarse_rows * ldd);
     dalloc(w->err, 4);
     dalloc(w->tile_ctr, 4);
     FA_CHECK_CUDA(cudaHostAlloc((void **)&w->h_err, 16, cudaHostAllocDefault));
@@ -344,21 +344,6 @@ static void ws_ensure_partial(Workspace *w, int64_t nq, int32_t ntop) {
     w->partial = nullptr;
     dalloc(w->partial, (size_t)cap * std::max(ntop, w->cap_ntop));
     w->tile_cap = cap;
-}
-
-// Key queues of the fused tensor-core coarse probe for a call of nq queries.
-static void ws_ensure_probe(fa_index *ix, Workspace *w, int64_t nq, int32_t nprobe, int gemm) {
-    if (gemm != FA_GEMM_BF16_TC || !ix->dev.centroids_bf16) return;
-    const size_t need = probe_tc_scratch_bytes(ix->dev, nq, nprobe);
-    if (w->probe_lists && w->probe_bytes >= need) return;
-    if (w->pending) FA_CHECK_CUDA(cudaEventSynchronize(w->done));
-    FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
-    ws_drop_graph(w);
-    if (w->probe_lists) cudaFree(w->probe_lists);
-    w->probe_lists = nullptr;
-    w->probe_bytes = 0;
-    dalloc(w->probe_lists, (need + 7) / 8);
-    w->probe_bytes = need;
 }
 
 struct WsLease {
@@ -486,7 +471,6 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     if ((sp.flags & FA_PERSISTENT) && tile_chunks == 0) tile_chunks = 256;
     if (ntop > 256) tile_chunks = 0;  // the CTA-wide top-n runs one CTA per query
     if (tile_chunks > 0) ws_ensure_partial(w, nq, ntop);
-    if (!sp.probes) ws_ensure_probe(ix, w, nq, nprobe, sp.probe_gemm);
 
     auto enqueue = [&]() {
         FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
@@ -1181,7 +1165,6 @@ fa_status fa_debug_probes(fa_index *ix, const float *queries, int64_t nq, int32_
         WsLease lease(ix, false);
         Workspace *w = lease.w;
         ws_ensure(ix, w, nq, 1, nprobe, 1, 0);
-        ws_ensure_probe(ix, w, nq, nprobe, sp.probe_gemm);
         FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * ix->d, cudaMemcpyHostToDevice, w->stream));
         launch_coarse(ix->dev, w->q, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, w->stream);
         FA_CHECK_CUDA(cudaMemcpyAsync(out_probes, w->probes, sizeof(int32_t) * nq * nprobe,

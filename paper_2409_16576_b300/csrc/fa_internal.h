@@ -80,7 +80,7 @@ struct DeviceIndex {
     void *raw_dev_alloc = nullptr;
     void *raw_host_alloc = nullptr;
     // bf16 operands for the tensor-core paths (allocated on first use)
-    void *centroids_bf16 = nullptr; // tensor-core tiles [ntiles][hi, lo][256 x tc_kp]
+    void *centroids_bf16 = nullptr; // tensor-core tiles [ntiles][hi, lo][128 x tc_kp]
     int32_t tc_kp = 0, tc_ntiles = 0;
     void *codebooks_bf16 = nullptr; // tensor-core B tiles [M][hi, lo][256 x 16]
     float *cbnorm = nullptr;        // [M][256] |C_m[c]|^2 (FP32)
@@ -127,10 +127,8 @@ struct Workspace {
     int32_t *stats = nullptr;      // [cap_nq][4]
     void *lut = nullptr;           // [cap_nq][lut_bytes] global LUT (precision form)
     float *lut_scale = nullptr;    // [cap_nq][2M] per subspace: scale, offset
-    float *coarse_d = nullptr;     // coarse distance scratch [coarse_rows][nlist]
+    float *coarse_d = nullptr;     // coarse distance scratch [coarse_rows][nlist rounded up to 4]
     int64_t coarse_rows = 0;
-    uint64_t *probe_lists = nullptr;  // fused tensor-core probe: per-query key queues
-    size_t probe_bytes = 0;
     uint32_t *err = nullptr;       // device error word
     uint32_t *tile_ctr = nullptr;  // persistent-kernel work counters
     // pinned host staging for host-buffer calls
@@ -242,12 +240,9 @@ void prepare_centroid_tiles(const float *cent, int32_t nlist, int32_t d, std::ve
                             int32_t &Kp, int32_t &ntiles);
 void prepare_codebook_tiles(const float *cb, int32_t M, int32_t d, std::vector<uint16_t> &tiles,
                             std::vector<float> &norms);
-void launch_coarse_tc_dist(const DeviceIndex &ix, const float *q, int64_t rows, float *D,
-                           int64_t ldd, uint32_t *err, cudaStream_t st);
-size_t probe_tc_scratch_bytes(const DeviceIndex &ix, int64_t nq, int32_t ntop);
-void launch_probe_tc(const DeviceIndex &ix, const float *q, int64_t nq, int32_t ntop, int32_t *probes,
-                     int32_t probe_stride, uint64_t *scratch, size_t scratch_bytes, uint32_t *err,
-                     cudaStream_t st);
+int64_t coarse_tc_ldd(int32_t nlist);
+void launch_coarse_tc(const DeviceIndex &ix, const float *q, int64_t rows, int32_t ntop, float *D,
+                      int32_t *probes, int32_t probe_stride, uint32_t *err, cudaStream_t st);
 void launch_query_order(const int32_t *probes, int64_t nq, int32_t stride, int32_t nlist,
                         uint32_t *cnt, int32_t *order, cudaStream_t st);
 void launch_tile_plan(const DeviceIndex &ix, const int32_t *probes, const int32_t *npq, int64_t nq,

@@ -142,9 +142,12 @@ void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t np
                    cudaStream_t st) {
     if (nq == 0) return;
     if (gemm == FA_GEMM_BF16_TC && ix.centroids_bf16) {
-        // fused: tensor-core distances and the top-nprobe selection in one pass
-        launch_probe_tc(ix, q, nq, nprobe, probes, probe_stride, ws.probe_lists, ws.probe_bytes,
-                        ws.err, st);
+        // distances on the tensor cores, then the per-row top-nprobe
+        for (int64_t r0 = 0; r0 < nq; r0 += ws.coarse_rows) {
+            const int64_t rows = std::min(ws.coarse_rows, nq - r0);
+            launch_coarse_tc(ix, q + r0 * ix.d, rows, nprobe, ws.coarse_d, probes + r0 * probe_stride,
+                             probe_stride, ws.err, st);
+        }
         return;
     }
     l2_topn(q, nq, ix.d, ix.centroids, ix.nlist, nprobe, ws.coarse_d, ws.coarse_rows, probes,
@@ -153,7 +156,7 @@ void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t np
 
 int coarse_launches(const DeviceIndex &ix, int64_t nq, int gemm, const Workspace &ws) {
     if (nq == 0) return 0;
-    if (gemm == FA_GEMM_BF16_TC && ix.centroids_bf16) return 2;
+    (void)gemm;
     return (int)(2 * ((nq + ws.coarse_rows - 1) / ws.coarse_rows));
 }
 

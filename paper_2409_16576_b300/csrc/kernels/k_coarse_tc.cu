@@ -1,171 +1,315 @@
-// Coarse probe (step 2) distances on the tensor cores:
-//   d2(q, c_l) = |q|^2 - 2 q.c_l + |c_l|^2
-// for a tile of 128 queries x 256 centroids per MMA (M = 128, N = 256,
-// K = 16 per instruction), accumulated in FP32 in tensor memory.
+// Coarse probe (step 2) on the tensor cores, as two kernels:
 //
-// Queries and centroids are both split into a bf16 pair hi + lo (x ~= hi +
-// lo to ~16 significant bits) and the dot product takes three MMAs per K-step
-// (hi.hi + hi.lo + lo.hi), so the product is close to FP32 accuracy while the
-// contraction runs at bf16 tensor rate. The distances go to the per-call
-// distance block and k_select picks the top-nprobe lists, as in the FP32 form.
+//   k_coarse_dist_tc   d2(q, c_l) = |q|^2 - 2 q.c_l + |c_l|^2 for a block of
+//                      queries and every centroid, into a distance block in HBM;
+//   k_select_rows      each query's nprobe nearest lists from its row.
 //
-// One CTA = 4 warps = 128 threads (one TMEM lane per thread). Thread 0 issues
-// the MMAs and commits them to an mbarrier; every thread waits on it (with a
-// bound) and reads its row's 256 accumulators back with tcgen05.ld.
+// Distances: queries and centroids are split into bf16 pairs hi + lo
+// (x ~= hi + lo to about 16 significant bits); each K-step takes three MMAs
+// (hi.hi + hi.lo + lo.hi) with FP32 accumulation in tensor memory, close to
+// FP32 accuracy at bf16 tensor rate. The (query tile, centroid tile) pairs of
+// the block are laid out query-tile major and cut into one contiguous range
+// per CTA, so every SM gets the same number of MMA tiles; a CTA whose range
+// crosses into the next query tile reloads its queries there.
+//
+// The CTA is warp-specialized:
+//   - one producer thread streams 128-centroid tiles into a two-stage shared-
+//     memory ring with bulk copies and issues the MMAs of each tile into one
+//     of two tensor-memory accumulators; mbarriers order the copies, the MMAs
+//     and the epilogue, so the MMAs of tile i run while tile i-1 is written;
+//   - 8 epilogue warps, two per tensor-memory lane quadrant and one column
+//     half each, read an accumulator into registers, hand it back at once,
+//     and store the distances of their 32 queries x 64 centroids.
+//
+// Selection reads each row once with several 16-byte loads in flight per lane
+// and keeps the row's n smallest keys (distance, list id) in the warp's
+// registers (warp_topk.cuh): the result is the sorted top-n, ties by list id.
 #include <algorithm>
 #include <vector>
 
 #include "../fa_internal.h"
 #include "tc_util.cuh"
+#include "warp_topk.cuh"
 
 namespace fa {
 
-constexpr int TCQ = 128;                 // queries per tile (MMA M)
-constexpr int TCN = 256;                 // centroids per tile (MMA N)
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
+namespace {
 
-struct CoarseTcArgs {
-    const float *q;              // [rows][d] queries of this block
+constexpr int PQ = 128;  // queries per tile (MMA M = tensor-memory lanes)
+constexpr int PN = 128;  // centroids per tile (MMA N)
+constexpr int PT = 256;  // epilogue threads: 8 warps
+constexpr uint32_t PWAIT = 1u << 22;
+
+struct DistArgs {
+    const float *q;              // [rows][d] the block's queries
     int64_t rows;
-    int32_t d, Kp;               // Kp = d rounded up to 16
-    const __nv_bfloat16 *tiles;  // [ntiles][2][TCN * Kp] hi, lo in core-matrix layout
-    const float *cnorm;          // [nlist]
-    int32_t nlist, ntiles, tiles_per_cta;
-    float *D;                    // [rows][ldd] squared distances out
+    int32_t d, Kp;
+    const __nv_bfloat16 *tiles;  // [nt][hi, lo][PN * Kp], core-matrix layout
+    const float *cnorm;          // [nlist] |c|^2
+    int32_t nlist, nt;
+    int64_t total;               // query tiles * nt
+    int32_t per;                 // (query tile, centroid tile) pairs per CTA
+    float *D;                    // [rows][ldd], ldd a multiple of 4
     int64_t ldd;
     uint32_t *err;
 };
 
-__global__ void __launch_bounds__(TCQ, 1) k_coarse_tc(const CoarseTcArgs a) {
+__global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int Kp = a.Kp;
-    __nv_bfloat16 *Ahi = reinterpret_cast<__nv_bfloat16 *>(sm);
-    __nv_bfloat16 *Alo = Ahi + TCQ * Kp;
-    __nv_bfloat16 *Bt = Alo + TCQ * Kp;  // hi then lo, 2 * TCN * Kp
-    __shared__ uint64_t mbar;
+    // full[s]: centroid stage s loaded; accf[b]: accumulator b written (its
+    // MMAs are done, which also frees the stage they read); acce[b]:
+    // accumulator b read by all 8 epilogue warps; aready: queries in place
+    __shared__ __align__(8) uint64_t full[2], accf[2], acce[2], aready;
     __shared__ uint32_t tmem_base;
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * TCQ;
+    __shared__ volatile int abort_flag;
+    const int Kp = a.Kp;
+    const uint32_t stage_bytes = (uint32_t)2 * PN * Kp * 2;  // hi + lo of one tile
+    __nv_bfloat16 *Ahi = reinterpret_cast<__nv_bfloat16 *>(sm);
+    __nv_bfloat16 *Alo = Ahi + PQ * Kp;
+    unsigned char *Bs = sm + (size_t)2 * PQ * Kp * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t g0 = (int64_t)blockIdx.x * a.per;
+    const int64_t g1 = min(a.total, g0 + a.per);
+    if (g0 >= g1) return;
+    const int ntiles = (int)(g1 - g0);
 
-    // A: this CTA's queries as bf16 hi/lo; |q|^2 of the thread's own row
-    for (int e = tid; e < TCQ * Kp; e += TCQ) {
-        const int r = e / Kp, k = e - r * Kp;
-        const float x = (r0 + r < a.rows && k < a.d) ? a.q[(r0 + r) * a.d + k] : 0.f;
-        __nv_bfloat16 h, l;
-        tc::split_bf16(x, h, l);
-        const uint32_t o = tc::core_offset(r, k, Kp) >> 1;
-        Ahi[o] = h;
-        Alo[o] = l;
-    }
-    float qn = 0.f;
-    if (r0 + tid < a.rows)
-        for (int k = 0; k < a.d; ++k) {
-            const float x = a.q[(r0 + tid) * a.d + k];
-            qn = fmaf(x, x, qn);
+    if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * PN);
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&accf[i], 1);
+            tc::mbar_init(&acce[i], PT / 32);
         }
-    if (warp == 0) tc::tmem_alloc(&tmem_base, TCN);
-    if (tid == 0) tc::mbar_init(&mbar, 1);
-    tc::fence_proxy_async();
+        tc::mbar_init(&aready, 1);
+        abort_flag = 0;
+    }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
     const uint32_t tbase = tmem_base;
-    const uint32_t idesc = tc::idesc_bf16_f32(TCQ, TCN);
-    const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
-    uint32_t parity = 0;
-    bool failed = false;
 
-    const int t0 = blockIdx.y * a.tiles_per_cta;
-    const int t1 = min(a.ntiles, t0 + a.tiles_per_cta);
-    for (int t = t0; t < t1; ++t) {
-        // B: centroid tile t (hi, lo), already in core-matrix layout
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.tiles + (size_t)t * 2 * TCN * Kp);
-        uint4 *dst = reinterpret_cast<uint4 *>(Bt);
-        const int n16 = 2 * TCN * Kp * 2 / 16;
-        for (int i = tid; i < n16; i += TCQ) dst[i] = __ldg(src + i);
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc::fence_after();
+    if (warp == PT / 32) {
+        // ---- producer: centroid tiles in, MMAs out (one thread) ----
+        if (lane == 0) {
+            const uint32_t idesc = tc::idesc_bf16_f32(PQ, PN);
+            const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
             const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
-            const uint32_t bh = tc::smem_u32(Bt), bl = bh + TCN * Kp * 2;
-            for (int ks = 0; ks < Kp / 16; ++ks) {
-                const uint32_t off = 256u * ks;
-                const uint64_t dah = tc::smem_desc(ah + off, 128, sbo);
-                const uint64_t dal = tc::smem_desc(al + off, 128, sbo);
-                const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
-                const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
-                tc::mma_bf16(tbase, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                tc::mma_bf16(tbase, dah, dbl, idesc, 1u);
-                tc::mma_bf16(tbase, dal, dbh, idesc, 1u);
-            }
-            tc::mma_commit(&mbar);
-        }
-        const bool ok = tc::mbar_wait(&mbar, parity, WAIT_LIMIT);
-        if (__syncthreads_or(!ok)) {
-            failed = true;
-            break;
-        }
-        parity ^= 1u;
-        tc::fence_after();
-        // epilogue: this thread's row, 256 columns in 8 loads of 32
-        const int64_t row = r0 + tid;
-        const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int c0 = 0; c0 < TCN; c0 += 32) {
-            float v[32];
-            tc::tmem_ld32(lane_addr + c0, v);
-            const int l0 = t * TCN + c0;
-            if (row < a.rows) {
-                float *out = a.D + row * a.ldd + l0;
-                if (l0 + 32 <= a.nlist) {
-#pragma unroll
-                    for (int i = 0; i < 32; i += 4) {
-                        float4 o;
-                        o.x = qn - 2.f * v[i + 0] + __ldg(a.cnorm + l0 + i + 0);
-                        o.y = qn - 2.f * v[i + 1] + __ldg(a.cnorm + l0 + i + 1);
-                        o.z = qn - 2.f * v[i + 2] + __ldg(a.cnorm + l0 + i + 2);
-                        o.w = qn - 2.f * v[i + 3] + __ldg(a.cnorm + l0 + i + 3);
-                        if (((a.ldd | l0) & 3) == 0)
-                            *reinterpret_cast<float4 *>(out + i) = o;
-                        else {
-                            out[i] = o.x;
-                            out[i + 1] = o.y;
-                            out[i + 2] = o.z;
-                            out[i + 3] = o.w;
-                        }
-                    }
-                } else {
-                    for (int i = 0; i < 32 && l0 + i < a.nlist; ++i)
-                        out[i] = qn - 2.f * v[i] + __ldg(a.cnorm + l0 + i);
+            int kl0 = -1, kl1 = -1;  // tile whose copy into stage 0 / 1 is in flight
+            int committed = -1;      // last tile whose MMAs were committed
+            bool ok = true;
+            auto issue_load = [&](int s, int kt) {
+                const int t = (int)((g0 + kt) % a.nt);
+                tc::mbar_expect_tx(&full[s], stage_bytes);
+                tc::bulk_g2s(Bs + (size_t)s * stage_bytes, a.tiles + (size_t)t * 2 * PN * Kp, stage_bytes,
+                             &full[s]);
+                if (s == 0) kl0 = kt;
+                else kl1 = kt;
+            };
+            issue_load(0, 0);
+            if (ntiles > 1) issue_load(1, 1);
+            int segi = 0;
+            int64_t seg_end = g0;  // first pair past the current query tile
+            for (int k = 0; k < ntiles; ++k) {
+                const int64_t g = g0 + k;
+                if (g >= seg_end) {  // a new query tile: wait until its queries are in place
+                    seg_end = (g / a.nt + 1) * a.nt;
+                    ok = tc::mbar_wait(&aready, segi & 1, PWAIT);
+                    ++segi;
+                    if (!ok) break;
+                    tc::fence_after();
+                }
+                const int s = k & 1;
+                ok = tc::mbar_wait(&full[s], (k >> 1) & 1, PWAIT);
+                if (ok && k >= 2) ok = tc::mbar_wait(&acce[s], ((k - 2) >> 1) & 1, PWAIT);
+                if (!ok || abort_flag) break;
+                if (s == 0) kl0 = -1;
+                else kl1 = -1;
+                tc::fence_after();
+                const uint32_t bh = tc::smem_u32(Bs + (size_t)s * stage_bytes), bl = bh + stage_bytes / 2;
+                const uint32_t acc = tbase + (uint32_t)s * PN;
+                for (int ks = 0; ks < Kp / 16; ++ks) {
+                    const uint32_t off = 256u * ks;
+                    const uint64_t dah = tc::smem_desc(ah + off, 128, sbo);
+                    const uint64_t dal = tc::smem_desc(al + off, 128, sbo);
+                    const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
+                    const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
+                    tc::mma_bf16(acc, dah, dbh, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_bf16(acc, dah, dbl, idesc, 1u);
+                    tc::mma_bf16(acc, dal, dbh, idesc, 1u);
+                }
+                tc::mma_commit(&accf[s]);
+                committed = k;
+                // the other stage (tile k - 1) takes tile k + 1 once MMA k - 1 is done
+                if (k >= 1 && k + 1 < ntiles) {
+                    ok = tc::mbar_wait(&accf[s ^ 1], ((k - 1) >> 1) & 1, PWAIT);
+                    if (!ok) break;
+                    issue_load(s ^ 1, k + 1);
                 }
             }
+            if (!ok) {
+                atomicOr(a.err, DEV_ERR_TIMEOUT);
+                abort_flag = 1;
+            }
+            // nothing may be in flight when shared and tensor memory are released
+            if (committed >= 0) tc::mbar_wait(&accf[committed & 1], (committed >> 1) & 1, PWAIT);
+            if (kl0 >= 0) tc::mbar_wait(&full[0], (kl0 >> 1) & 1, PWAIT);
+            if (kl1 >= 0) tc::mbar_wait(&full[1], (kl1 >> 1) & 1, PWAIT);
         }
-        tc::fence_before();
-        __syncthreads();
-    }
-    if (failed) {
-        if (tid == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
-        // let an MMA still in flight finish before the tensor memory is freed
-        tc::mbar_wait(&mbar, parity, WAIT_LIMIT);
+    } else {
+        // ---- epilogue: 8 warps, two per lane quadrant, one column half each ----
+        const int quad = warp & 3, colh = warp >> 2;
+        int k = 0;
+        bool failed = false;
+        while (k < ntiles && !failed) {
+            const int64_t qt = (g0 + k) / a.nt;
+            const int nseg = (int)(min(g1, (qt + 1) * a.nt) - (g0 + k));
+            const int64_t r0 = qt * PQ;
+            // A: this query tile as bf16 hi/lo; every MMA on the previous one
+            // is done (its last accumulator was read below)
+            for (int e = tid; e < PQ * Kp; e += PT) {
+                const int r = e / Kp, kk = e - r * Kp;
+                const float x = (r0 + r < a.rows && kk < a.d) ? a.q[(r0 + r) * a.d + kk] : 0.f;
+                __nv_bfloat16 h, l;
+                tc::split_bf16(x, h, l);
+                const uint32_t o = tc::core_offset(r, kk, Kp) >> 1;
+                Ahi[o] = h;
+                Alo[o] = l;
+            }
+            tc::fence_proxy_async();
+            asm volatile("bar.sync 1, %0;" ::"n"(PT) : "memory");
+            if (tid == 0) tc::mbar_arrive(&aready);
+            const int64_t row = r0 + quad * 32 + lane;
+            const bool rv = row < a.rows;
+            float qn = 0.f;
+            if (rv)
+                for (int kk = 0; kk < a.d; ++kk) {
+                    const float x = a.q[row * a.d + kk];
+                    qn = fmaf(x, x, qn);
+                }
+            float *drow = a.D + (rv ? row : 0) * a.ldd;
+            // 32 distances of this row from one chunk: |c|^2 of column l0 + e sits in lane e
+            auto store_chunk = [&](float(&v)[32], float cl, int l0) {
+#pragma unroll
+                for (int e = 0; e < 32; ++e) v[e] = qn - 2.f * v[e] + __shfl_sync(FULL, cl, e);
+                if (!rv) return;
+                if (l0 + 32 <= a.nlist) {
+#pragma unroll
+                    for (int e = 0; e < 32; e += 4)
+                        *reinterpret_cast<float4 *>(drow + l0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if (l0 + e < a.nlist) drow[l0 + e] = v[e];
+                }
+            };
+            for (int i = 0; i < nseg; ++i, ++k) {
+                const int b = k & 1;
+                const int lbase = (int)((g0 + k) % a.nt) * PN + colh * 64;
+                const float cl0 = lbase + lane < a.nlist ? __ldg(a.cnorm + lbase + lane) : 0.f;
+                const float cl1 = lbase + 32 + lane < a.nlist ? __ldg(a.cnorm + lbase + 32 + lane) : 0.f;
+                bool ok = tc::mbar_wait(&accf[b], (k >> 1) & 1, PWAIT);
+                ok = __all_sync(FULL, ok) && !abort_flag;
+                if (!ok) {
+                    failed = true;
+                    break;
+                }
+                tc::fence_after();
+                float v0[32], v1[32];
+                const uint32_t taddr = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * PN + colh * 64;
+                tc::tmem_ld32(taddr, v0);
+                tc::tmem_ld32(taddr + 32, v1);
+                tc::fence_before();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(&acce[b]);
+                store_chunk(v0, cl0, lbase);
+                store_chunk(v1, cl1, lbase + 32);
+            }
+            if (failed) {
+                abort_flag = 1;
+                if (lane == 0) atomicOr(a.err, DEV_ERR_TIMEOUT);
+            }
+            // the queries are replaced only after every epilogue warp is done;
+            // a failure anywhere ends every epilogue warp here
+            asm volatile("bar.sync 1, %0;" ::"n"(PT) : "memory");
+            failed = abort_flag != 0;
+        }
     }
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_free(tbase, TCN);
+    if (warp == 0) tc::tmem_free(tbase, 2 * PN);
 }
 
-// Centroids as TC tiles: [ntiles][hi, lo][TCN rows x Kp] in core-matrix layout,
-// rows past nlist zero. Host-side preparation at index upload.
+// One warp per row: the n smallest (distance, column) keys of D[row][0, nc).
+// Rows are 16-byte aligned (ldd a multiple of 4); each lane keeps U 16-byte
+// loads of the next batch in flight while it offers the current one.
+template <int R>
+__global__ void __launch_bounds__(256) k_select_rows(const float *__restrict__ D, int64_t ldd, int64_t nrows,
+                                                     int32_t nc, int32_t ntop, int32_t *__restrict__ out_ids,
+                                                     int32_t out_stride) {
+    constexpr int U = 4;
+    __shared__ uint64_t wbuf[8][64];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t row = (int64_t)blockIdx.x * 8 + warp;
+    if (row >= nrows) return;
+    WarpTopK<R> tk;
+    tk.init(wbuf[warp], ntop);
+    const float4 *d4 = reinterpret_cast<const float4 *>(D + row * ldd);
+    const int n4 = (nc + 3) >> 2;
+    float4 cur[U], nxt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int i = lane + 32 * u;
+        cur[u] = i < n4 ? __ldg(d4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int base = 0; base < n4; base += 32 * U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int i = base + 32 * U + lane + 32 * u;
+            nxt[u] = i < n4 ? __ldg(d4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int c = 4 * (base + lane + 32 * u);
+            tk.push(make_key(cur[u].x, (uint32_t)c), c < nc);
+            tk.push(make_key(cur[u].y, (uint32_t)(c + 1)), c + 1 < nc);
+            tk.push(make_key(cur[u].z, (uint32_t)(c + 2)), c + 2 < nc);
+            tk.push(make_key(cur[u].w, (uint32_t)(c + 3)), c + 3 < nc);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+    }
+    tk.finish();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int e = r * 32 + lane;
+        if (e < ntop) {
+            const uint64_t k = tk.L[r];
+            out_ids[row * out_stride + e] = k == KEY_INF ? -1 : (int32_t)(k & 0xffffffffu);
+        }
+    }
+}
+
+template <int R>
+void select_r(const float *D, int64_t ldd, int64_t rows, int32_t nc, int32_t ntop, int32_t *out,
+              int32_t stride, cudaStream_t st) {
+    k_select_rows<R><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(D, ldd, rows, nc, ntop, out, stride);
+    FA_CHECK_CUDA(cudaGetLastError());
+}
+
+}  // namespace
+
+// Centroids as tensor-core tiles: [nt][hi, lo][PN rows x Kp] in core-matrix
+// layout, rows past nlist zero. Host-side preparation at index upload.
 void prepare_centroid_tiles(const float *cent, int32_t nlist, int32_t d, std::vector<uint16_t> &out,
                             int32_t &Kp, int32_t &ntiles) {
     Kp = (d + 15) / 16 * 16;
-    ntiles = (nlist + TCN - 1) / TCN;
-    out.assign((size_t)ntiles * 2 * TCN * Kp, 0);
+    ntiles = (nlist + PN - 1) / PN;
+    out.assign((size_t)ntiles * 2 * PN * Kp, 0);
     for (int l = 0; l < nlist; ++l) {
-        const int t = l / TCN, r = l % TCN;
-        uint16_t *hi = out.data() + (size_t)t * 2 * TCN * Kp;
-        uint16_t *lo = hi + (size_t)TCN * Kp;
+        const int t = l / PN, r = l % PN;
+        uint16_t *hi = out.data() + (size_t)t * 2 * PN * Kp;
+        uint16_t *lo = hi + (size_t)PN * Kp;
         for (int k = 0; k < d; ++k) {
             const float x = cent[(size_t)l * d + k];
             const uint16_t h = tc::host_bf16_bits(x);
@@ -176,11 +320,14 @@ void prepare_centroid_tiles(const float *cent, int32_t nlist, int32_t d, std::ve
     }
 }
 
-// Distances of `rows` queries to every centroid into D[rows][ldd].
-void launch_coarse_tc_dist(const DeviceIndex &ix, const float *q, int64_t rows, float *D,
-                           int64_t ldd, uint32_t *err, cudaStream_t st) {
+int64_t coarse_tc_ldd(int32_t nlist) { return ((int64_t)nlist + 3) & ~3ll; }
+
+void launch_coarse_tc(const DeviceIndex &ix, const float *q, int64_t rows, int32_t ntop, float *D,
+                      int32_t *probes, int32_t probe_stride, uint32_t *err, cudaStream_t st) {
+    if (rows == 0) return;
     FA_REQUIRE(ix.centroids_bf16 != nullptr, FA_ERR_ARG, "tensor-core centroid tiles missing");
-    CoarseTcArgs a{};
+    FA_REQUIRE(ntop >= 1 && ntop <= 512, FA_ERR_ARG, "top-n of the coarse probe must be in 1..512");
+    DistArgs a{};
     a.q = q;
     a.rows = rows;
     a.d = ix.d;
@@ -188,22 +335,26 @@ void launch_coarse_tc_dist(const DeviceIndex &ix, const float *q, int64_t rows, 
     a.tiles = reinterpret_cast<const __nv_bfloat16 *>(ix.centroids_bf16);
     a.cnorm = ix.cnorm;
     a.nlist = ix.nlist;
-    a.ntiles = ix.tc_ntiles;
+    a.nt = ix.tc_ntiles;
+    a.total = (rows + PQ - 1) / PQ * (int64_t)a.nt;
+    a.per = (int32_t)((a.total + num_sms(0) - 1) / num_sms(0));
     a.D = D;
-    a.ldd = ldd;
+    a.ldd = coarse_tc_ldd(ix.nlist);
     a.err = err;
-    const int qtiles = (int)((rows + TCQ - 1) / TCQ);
-    // enough CTAs for a few waves over the SMs, each reusing its query tile
-    int ysplit = std::max(1, std::min(a.ntiles, (num_sms(0) * 4 + qtiles - 1) / qtiles));
-    a.tiles_per_cta = (a.ntiles + ysplit - 1) / ysplit;
-    ysplit = (a.ntiles + a.tiles_per_cta - 1) / a.tiles_per_cta;
-    // at least 116 KB so that no more than one CTA (256 TMEM columns) and at most
-    // two share an SM: TMEM allocation never has to wait
-    const int smem = std::max((2 * TCQ * a.Kp + 2 * TCN * a.Kp) * 2, 116 * 1024);
-    FA_REQUIRE(smem <= 220 * 1024, FA_ERR_ARG, "tensor-core coarse probe supports d <= 128");
-    FA_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    k_coarse_tc<<<dim3(qtiles, ysplit), TCQ, smem, st>>>(a);
+    const int grid = (int)((a.total + a.per - 1) / a.per);
+    // queries + two centroid stages; at least 116 KB so that one CTA (256
+    // tensor-memory columns) runs per SM and allocation never waits
+    FA_REQUIRE(a.Kp <= 128, FA_ERR_ARG, "tensor-core coarse probe supports d <= 128");
+    const int smem = std::max(3 * 2 * PQ * a.Kp * 2, 116 * 1024);
+    FA_CHECK_CUDA(cudaFuncSetAttribute(k_coarse_dist_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    k_coarse_dist_tc<<<grid, PT + 32, smem, st>>>(a);
     FA_CHECK_CUDA(cudaGetLastError());
+    const int64_t ldd = a.ldd;
+    if (ntop <= 32) select_r<1>(D, ldd, rows, ix.nlist, ntop, probes, probe_stride, st);
+    else if (ntop <= 64) select_r<2>(D, ldd, rows, ix.nlist, ntop, probes, probe_stride, st);
+    else if (ntop <= 128) select_r<4>(D, ldd, rows, ix.nlist, ntop, probes, probe_stride, st);
+    else if (ntop <= 256) select_r<8>(D, ldd, rows, ix.nlist, ntop, probes, probe_stride, st);
+    else select_r<16>(D, ldd, rows, ix.nlist, ntop, probes, probe_stride, st);
 }
 
 }  // namespace fa
