@@ -12,14 +12,18 @@
 // per CTA, so every SM gets the same number of MMA tiles; a CTA whose range
 // crosses into the next query tile reloads its queries there.
 //
+// The MMA takes the centroid tile as its M side and the query tile as its N
+// side, so tensor-memory lane i holds centroid i's dot products with the 128
+// queries: for each query the 32 lanes of a warp then store 32 consecutive
+// distances of that query's row, one full 128-byte line per store.
 // The CTA is warp-specialized:
 //   - one producer thread streams 128-centroid tiles into a two-stage shared-
 //     memory ring with bulk copies and issues the MMAs of each tile into one
 //     of two tensor-memory accumulators; mbarriers order the copies, the MMAs
 //     and the epilogue, so the MMAs of tile i run while tile i-1 is written;
-//   - 8 epilogue warps, two per tensor-memory lane quadrant and one column
-//     half each, read an accumulator into registers, hand it back at once,
-//     and store the distances of their 32 queries x 64 centroids.
+//   - 8 epilogue warps, two per tensor-memory lane quadrant (32 centroids)
+//     and one half of the queries each, read an accumulator into registers,
+//     hand it back at once, and store their 32 centroids x 64 queries.
 //
 // Selection reads each row once with several 16-byte loads in flight per lane
 // and keeps the row's n smallest keys (distance, list id) in the warp's
@@ -35,8 +39,8 @@ namespace fa {
 
 namespace {
 
-constexpr int PQ = 128;  // queries per tile (MMA M = tensor-memory lanes)
-constexpr int PN = 128;  // centroids per tile (MMA N)
+constexpr int PQ = 128;  // queries per tile (MMA N)
+constexpr int PN = 128;  // centroids per tile (MMA M = tensor-memory lanes)
 constexpr int PT = 256;  // epilogue threads: 8 warps
 constexpr uint32_t PWAIT = 1u << 22;
 
@@ -62,6 +66,7 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
     __shared__ __align__(8) uint64_t full[2], accf[2], acce[2], aready;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
+    __shared__ float qn_sh[PQ];  // |q|^2 of the current query tile
     const int Kp = a.Kp;
     const uint32_t stage_bytes = (uint32_t)2 * PN * Kp * 2;  // hi + lo of one tile
     __nv_bfloat16 *Ahi = reinterpret_cast<__nv_bfloat16 *>(sm);
@@ -91,7 +96,7 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
     if (warp == PT / 32) {
         // ---- producer: centroid tiles in, MMAs out (one thread) ----
         if (lane == 0) {
-            const uint32_t idesc = tc::idesc_bf16_f32(PQ, PN);
+            const uint32_t idesc = tc::idesc_bf16_f32(PN, PQ);
             const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
             const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
             int kl0 = -1, kl1 = -1;  // tile whose copy into stage 0 / 1 is in flight
@@ -133,9 +138,10 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
                     const uint64_t dal = tc::smem_desc(al + off, 128, sbo);
                     const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
                     const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
-                    tc::mma_bf16(acc, dah, dbh, idesc, ks > 0 ? 1u : 0u);
-                    tc::mma_bf16(acc, dah, dbl, idesc, 1u);
-                    tc::mma_bf16(acc, dal, dbh, idesc, 1u);
+                    // centroids (stage) as A, queries as B
+                    tc::mma_bf16(acc, dbh, dah, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_bf16(acc, dbh, dal, idesc, 1u);
+                    tc::mma_bf16(acc, dbl, dah, idesc, 1u);
                 }
                 tc::mma_commit(&accf[s]);
                 committed = k;
@@ -156,7 +162,7 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
             if (kl1 >= 0) tc::mbar_wait(&full[1], (kl1 >> 1) & 1, PWAIT);
         }
     } else {
-        // ---- epilogue: 8 warps, two per lane quadrant, one column half each ----
+        // ---- epilogue: 8 warps; lane quadrant = 32 centroids, half = 64 queries ----
         const int quad = warp & 3, colh = warp >> 2;
         int k = 0;
         bool failed = false;
@@ -164,8 +170,8 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
             const int64_t qt = (g0 + k) / a.nt;
             const int nseg = (int)(min(g1, (qt + 1) * a.nt) - (g0 + k));
             const int64_t r0 = qt * PQ;
-            // A: this query tile as bf16 hi/lo; every MMA on the previous one
-            // is done (its last accumulator was read below)
+            // this query tile as bf16 hi/lo, and |q|^2; every MMA on the
+            // previous one is done (its last accumulator was read below)
             for (int e = tid; e < PQ * Kp; e += PT) {
                 const int r = e / Kp, kk = e - r * Kp;
                 const float x = (r0 + r < a.rows && kk < a.d) ? a.q[(r0 + r) * a.d + kk] : 0.f;
@@ -175,38 +181,39 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
                 Ahi[o] = h;
                 Alo[o] = l;
             }
+            if (tid < PQ) {
+                float qn = 0.f;
+                if (r0 + tid < a.rows)
+                    for (int kk = 0; kk < a.d; ++kk) {
+                        const float x = a.q[(r0 + tid) * a.d + kk];
+                        qn = fmaf(x, x, qn);
+                    }
+                qn_sh[tid] = qn;
+            }
             tc::fence_proxy_async();
             asm volatile("bar.sync 1, %0;" ::"n"(PT) : "memory");
             if (tid == 0) tc::mbar_arrive(&aready);
-            const int64_t row = r0 + quad * 32 + lane;
-            const bool rv = row < a.rows;
-            float qn = 0.f;
-            if (rv)
-                for (int kk = 0; kk < a.d; ++kk) {
-                    const float x = a.q[row * a.d + kk];
-                    qn = fmaf(x, x, qn);
-                }
-            float *drow = a.D + (rv ? row : 0) * a.ldd;
-            // 32 distances of this row from one chunk: |c|^2 of column l0 + e sits in lane e
-            auto store_chunk = [&](float(&v)[32], float cl, int l0) {
+            // |q|^2 of query colh * 64 + 32 c + lane, for the broadcasts below
+            const float qn0 = qn_sh[colh * 64 + lane], qn1 = qn_sh[colh * 64 + 32 + lane];
+            const int64_t rq = r0 + colh * 64;  // first query of this warp's half
+            // 32 queries (j0 + e) x this lane's centroid l: row j0 + e, column l
+            auto store_chunk = [&](const float(&v)[32], float qnl, int j0, int l, float cn) {
+                const int64_t first = rq + j0;
+                const int64_t left = a.rows - first;
+                const int nrow = left <= 0 ? 0 : (left >= 32 ? 32 : (int)left);
+                float *p = a.D + first * a.ldd + l;
+                const bool lv = l < a.nlist;
 #pragma unroll
-                for (int e = 0; e < 32; ++e) v[e] = qn - 2.f * v[e] + __shfl_sync(FULL, cl, e);
-                if (!rv) return;
-                if (l0 + 32 <= a.nlist) {
-#pragma unroll
-                    for (int e = 0; e < 32; e += 4)
-                        *reinterpret_cast<float4 *>(drow + l0 + e) = make_float4(v[e], v[e + 1], v[e + 2], v[e + 3]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        if (l0 + e < a.nlist) drow[l0 + e] = v[e];
+                for (int e = 0; e < 32; ++e) {
+                    const float dd = __shfl_sync(FULL, qnl, e) - 2.f * v[e] + cn;
+                    if (lv && e < nrow) *p = dd;
+                    p += a.ldd;
                 }
             };
             for (int i = 0; i < nseg; ++i, ++k) {
                 const int b = k & 1;
-                const int lbase = (int)((g0 + k) % a.nt) * PN + colh * 64;
-                const float cl0 = lbase + lane < a.nlist ? __ldg(a.cnorm + lbase + lane) : 0.f;
-                const float cl1 = lbase + 32 + lane < a.nlist ? __ldg(a.cnorm + lbase + 32 + lane) : 0.f;
+                const int l = (int)((g0 + k) % a.nt) * PN + quad * 32 + lane;
+                const float cn = l < a.nlist ? __ldg(a.cnorm + l) : 0.f;
                 bool ok = tc::mbar_wait(&accf[b], (k >> 1) & 1, PWAIT);
                 ok = __all_sync(FULL, ok) && !abort_flag;
                 if (!ok) {
@@ -214,15 +221,17 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
                     break;
                 }
                 tc::fence_after();
-                float v0[32], v1[32];
+                // read, store, read the next 32 columns: the accumulator goes
+                // back after both, well within the next tile's MMA time
                 const uint32_t taddr = tbase + ((uint32_t)(quad * 32) << 16) + (uint32_t)b * PN + colh * 64;
-                tc::tmem_ld32(taddr, v0);
-                tc::tmem_ld32(taddr + 32, v1);
+                float v[32];
+                tc::tmem_ld32(taddr, v);
+                store_chunk(v, qn0, 0, l, cn);
+                tc::tmem_ld32(taddr + 32, v);
+                store_chunk(v, qn1, 32, l, cn);
                 tc::fence_before();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(&acce[b]);
-                store_chunk(v0, cl0, lbase);
-                store_chunk(v1, cl1, lbase + 32);
             }
             if (failed) {
                 abort_flag = 1;
@@ -257,6 +266,7 @@ __global__ void __launch_bounds__(256) k_select_rows(const float *__restrict__ D
     const float4 *d4 = reinterpret_cast<const float4 *>(D + row * ldd);
     const int n4 = (nc + 3) >> 2;
     float4 cur[U], nxt[U];
+    float thr_f = INFINITY;  // the distance of the n-th smallest key so far
 #pragma unroll
     for (int u = 0; u < U; ++u) {
         const int i = lane + 32 * u;
@@ -270,11 +280,16 @@ __global__ void __launch_bounds__(256) k_select_rows(const float *__restrict__ D
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
+            // most rows reject most keys: one float test per 16 bytes first
             const int c = 4 * (base + lane + 32 * u);
-            tk.push(make_key(cur[u].x, (uint32_t)c), c < nc);
-            tk.push(make_key(cur[u].y, (uint32_t)(c + 1)), c + 1 < nc);
-            tk.push(make_key(cur[u].z, (uint32_t)(c + 2)), c + 2 < nc);
-            tk.push(make_key(cur[u].w, (uint32_t)(c + 3)), c + 3 < nc);
+            const float mn = fminf(fminf(cur[u].x, cur[u].y), fminf(cur[u].z, cur[u].w));
+            if (__any_sync(FULL, c < nc && mn <= thr_f)) {
+                tk.push(make_key(cur[u].x, (uint32_t)c), c < nc);
+                tk.push(make_key(cur[u].y, (uint32_t)(c + 1)), c + 1 < nc);
+                tk.push(make_key(cur[u].z, (uint32_t)(c + 2)), c + 2 < nc);
+                tk.push(make_key(cur[u].w, (uint32_t)(c + 3)), c + 3 < nc);
+                thr_f = tk.thr == KEY_INF ? INFINITY : o2f((uint32_t)(tk.thr >> 32));
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) cur[u] = nxt[u];
