@@ -44,11 +44,17 @@ constexpr int PN = 128;  // centroids per tile (MMA M = tensor-memory lanes)
 constexpr int PT = 256;  // epilogue threads: 8 warps
 constexpr uint32_t PWAIT = 1u << 22;
 
+// Centroid tiles are cut along K into KC contiguous chunks (two when the
+// padded dimension allows chunks of whole 16-wide K-steps), so that the
+// shared-memory ring of two tiles holds 2 KC chunks and a chunk is refilled
+// as soon as its own MMAs are done.
+__host__ __device__ constexpr int kchunks(int Kp) { return Kp % 32 == 0 ? 2 : 1; }
+
 struct DistArgs {
     const float *q;              // [rows][d] the block's queries
     int64_t rows;
     int32_t d, Kp;
-    const __nv_bfloat16 *tiles;  // [nt][hi, lo][PN * Kp], core-matrix layout
+    const __nv_bfloat16 *tiles;  // [nt][KC][hi, lo][PN * Kp / KC], core-matrix layout
     const float *cnorm;          // [nlist] |c|^2
     int32_t nlist, nt;
     int64_t total;               // query tiles * nt
@@ -60,15 +66,16 @@ struct DistArgs {
 
 __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    // full[s]: centroid stage s loaded; accf[b]: accumulator b written (its
-    // MMAs are done, which also frees the stage they read); acce[b]:
-    // accumulator b read by all 8 epilogue warps; aready: queries in place
-    __shared__ __align__(8) uint64_t full[2], accf[2], acce[2], aready;
+    // full[s] / sfree[s]: centroid chunk stage s loaded / read by its MMAs;
+    // accf[b]: accumulator b written; acce[b]: accumulator b read by all 8
+    // epilogue warps; aready: the query tile is in place
+    __shared__ __align__(8) uint64_t full[4], sfree[4], accf[2], acce[2], aready;
     __shared__ uint32_t tmem_base;
     __shared__ volatile int abort_flag;
     __shared__ float qn_sh[PQ];  // |q|^2 of the current query tile
     const int Kp = a.Kp;
-    const uint32_t stage_bytes = (uint32_t)2 * PN * Kp * 2;  // hi + lo of one tile
+    const int KC = kchunks(Kp), Kc = Kp / KC, S = 2 * KC;
+    const uint32_t chunk_bytes = (uint32_t)2 * PN * Kc * 2;  // hi + lo of one K-chunk
     __nv_bfloat16 *Ahi = reinterpret_cast<__nv_bfloat16 *>(sm);
     __nv_bfloat16 *Alo = Ahi + PQ * Kp;
     unsigned char *Bs = sm + (size_t)2 * PQ * Kp * 2;
@@ -80,8 +87,11 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
 
     if (warp == 0) tc::tmem_alloc(&tmem_base, 2 * PN);
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < 4; ++i) {
             tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&sfree[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&accf[i], 1);
             tc::mbar_init(&acce[i], PT / 32);
         }
@@ -94,62 +104,66 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
     const uint32_t tbase = tmem_base;
 
     if (warp == PT / 32) {
-        // ---- producer: centroid tiles in, MMAs out (one thread) ----
+        // ---- producer: centroid chunks in, MMAs out (one thread) ----
         if (lane == 0) {
             const uint32_t idesc = tc::idesc_bf16_f32(PN, PQ);
-            const uint32_t sbo = (uint32_t)(Kp / 8) * 128u;
+            const uint32_t sbo_q = (uint32_t)(Kp / 8) * 128u, sbo_c = (uint32_t)(Kc / 8) * 128u;
             const uint32_t ah = tc::smem_u32(Ahi), al = tc::smem_u32(Alo);
-            int kl0 = -1, kl1 = -1;  // tile whose copy into stage 0 / 1 is in flight
-            int committed = -1;      // last tile whose MMAs were committed
+            const int nch = ntiles * KC;
+            int issued = 0, consumed = 0;  // chunks copied in / read by MMAs (in order)
+            int committed = -1;            // last tile whose MMAs were committed
             bool ok = true;
-            auto issue_load = [&](int s, int kt) {
-                const int t = (int)((g0 + kt) % a.nt);
-                tc::mbar_expect_tx(&full[s], stage_bytes);
-                tc::bulk_g2s(Bs + (size_t)s * stage_bytes, a.tiles + (size_t)t * 2 * PN * Kp, stage_bytes,
-                             &full[s]);
-                if (s == 0) kl0 = kt;
-                else kl1 = kt;
+            auto issue_load = [&](int c) {
+                const int t = (int)((g0 + c / KC) % a.nt);
+                const int st = c % S;
+                tc::mbar_expect_tx(&full[st], chunk_bytes);
+                tc::bulk_g2s(Bs + (size_t)st * chunk_bytes,
+                             a.tiles + ((size_t)t * KC + c % KC) * 2 * PN * Kc, chunk_bytes, &full[st]);
+                ++issued;
             };
-            issue_load(0, 0);
-            if (ntiles > 1) issue_load(1, 1);
+            while (issued < min(S, nch)) issue_load(issued);
             int segi = 0;
             int64_t seg_end = g0;  // first pair past the current query tile
-            for (int k = 0; k < ntiles; ++k) {
-                const int64_t g = g0 + k;
-                if (g >= seg_end) {  // a new query tile: wait until its queries are in place
-                    seg_end = (g / a.nt + 1) * a.nt;
-                    ok = tc::mbar_wait(&aready, segi & 1, PWAIT);
-                    ++segi;
-                    if (!ok) break;
-                    tc::fence_after();
+            for (int c = 0; c < nch; ++c) {
+                const int k = c / KC, h = c % KC, st = c % S, b = k & 1;
+                if (h == 0) {
+                    const int64_t g = g0 + k;
+                    if (g >= seg_end) {  // a new query tile: wait until its queries are in place
+                        seg_end = (g / a.nt + 1) * a.nt;
+                        ok = tc::mbar_wait(&aready, segi & 1, PWAIT);
+                        ++segi;
+                        if (!ok) break;
+                    }
+                    // accumulator b is free once the epilogue has read tile k - 2
+                    if (k >= 2) ok = tc::mbar_wait(&acce[b], ((k - 2) >> 1) & 1, PWAIT);
                 }
-                const int s = k & 1;
-                ok = tc::mbar_wait(&full[s], (k >> 1) & 1, PWAIT);
-                if (ok && k >= 2) ok = tc::mbar_wait(&acce[s], ((k - 2) >> 1) & 1, PWAIT);
+                if (ok) ok = tc::mbar_wait(&full[st], (c / S) & 1, PWAIT);
                 if (!ok || abort_flag) break;
-                if (s == 0) kl0 = -1;
-                else kl1 = -1;
+                ++consumed;
                 tc::fence_after();
-                const uint32_t bh = tc::smem_u32(Bs + (size_t)s * stage_bytes), bl = bh + stage_bytes / 2;
-                const uint32_t acc = tbase + (uint32_t)s * PN;
-                for (int ks = 0; ks < Kp / 16; ++ks) {
-                    const uint32_t off = 256u * ks;
-                    const uint64_t dah = tc::smem_desc(ah + off, 128, sbo);
-                    const uint64_t dal = tc::smem_desc(al + off, 128, sbo);
-                    const uint64_t dbh = tc::smem_desc(bh + off, 128, sbo);
-                    const uint64_t dbl = tc::smem_desc(bl + off, 128, sbo);
+                const uint32_t ch = tc::smem_u32(Bs + (size_t)st * chunk_bytes), cl = ch + chunk_bytes / 2;
+                const uint32_t acc = tbase + (uint32_t)b * PN;
+                for (int kk = 0; kk < Kc / 16; ++kk) {
+                    const int ks = h * (Kc / 16) + kk;  // K-step within the tile
+                    const uint64_t dch = tc::smem_desc(ch + 256u * kk, 128, sbo_c);
+                    const uint64_t dcl = tc::smem_desc(cl + 256u * kk, 128, sbo_c);
+                    const uint64_t dqh = tc::smem_desc(ah + 256u * ks, 128, sbo_q);
+                    const uint64_t dql = tc::smem_desc(al + 256u * ks, 128, sbo_q);
                     // centroids (stage) as A, queries as B
-                    tc::mma_bf16(acc, dbh, dah, idesc, ks > 0 ? 1u : 0u);
-                    tc::mma_bf16(acc, dbh, dal, idesc, 1u);
-                    tc::mma_bf16(acc, dbl, dah, idesc, 1u);
+                    tc::mma_bf16(acc, dch, dqh, idesc, ks > 0 ? 1u : 0u);
+                    tc::mma_bf16(acc, dch, dql, idesc, 1u);
+                    tc::mma_bf16(acc, dcl, dqh, idesc, 1u);
                 }
-                tc::mma_commit(&accf[s]);
-                committed = k;
-                // the other stage (tile k - 1) takes tile k + 1 once MMA k - 1 is done
-                if (k >= 1 && k + 1 < ntiles) {
-                    ok = tc::mbar_wait(&accf[s ^ 1], ((k - 1) >> 1) & 1, PWAIT);
+                tc::mma_commit(&sfree[st]);
+                if (h == KC - 1) {
+                    tc::mma_commit(&accf[b]);
+                    committed = k;
+                }
+                // the stage of chunk c - 1 takes chunk c - 1 + S once its MMAs are done
+                if (c >= 1 && issued < nch) {
+                    ok = tc::mbar_wait(&sfree[(c - 1) % S], ((c - 1) / S) & 1, PWAIT);
                     if (!ok) break;
-                    issue_load(s ^ 1, k + 1);
+                    issue_load(issued);
                 }
             }
             if (!ok) {
@@ -158,8 +172,7 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
             }
             // nothing may be in flight when shared and tensor memory are released
             if (committed >= 0) tc::mbar_wait(&accf[committed & 1], (committed >> 1) & 1, PWAIT);
-            if (kl0 >= 0) tc::mbar_wait(&full[0], (kl0 >> 1) & 1, PWAIT);
-            if (kl1 >= 0) tc::mbar_wait(&full[1], (kl1 >> 1) & 1, PWAIT);
+            for (int c = consumed; c < issued; ++c) tc::mbar_wait(&full[c % S], (c / S) & 1, PWAIT);
         }
     } else {
         // ---- epilogue: 8 warps; lane quadrant = 32 centroids, half = 64 queries ----
@@ -278,18 +291,27 @@ __global__ void __launch_bounds__(256) k_select_rows(const float *__restrict__ D
             const int i = base + 32 * U + lane + 32 * u;
             nxt[u] = i < n4 ? __ldg(d4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        // most keys lose to the n-th smallest so far: one float test per 16
+        // bytes, and a single (not unrolled) push site for the rest, so the
+        // bitonic merges appear once in the code
+        uint32_t todo = 0;
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            // most rows reject most keys: one float test per 16 bytes first
             const int c = 4 * (base + lane + 32 * u);
             const float mn = fminf(fminf(cur[u].x, cur[u].y), fminf(cur[u].z, cur[u].w));
-            if (__any_sync(FULL, c < nc && mn <= thr_f)) {
-                tk.push(make_key(cur[u].x, (uint32_t)c), c < nc);
-                tk.push(make_key(cur[u].y, (uint32_t)(c + 1)), c + 1 < nc);
-                tk.push(make_key(cur[u].z, (uint32_t)(c + 2)), c + 2 < nc);
-                tk.push(make_key(cur[u].w, (uint32_t)(c + 3)), c + 3 < nc);
-                thr_f = tk.thr == KEY_INF ? INFINITY : o2f((uint32_t)(tk.thr >> 32));
+            todo |= (__any_sync(FULL, c < nc && mn <= thr_f) ? 1u : 0u) << u;
+        }
+#pragma unroll 1
+        for (; todo; todo &= todo - 1) {
+            const int u = __ffs(todo) - 1;
+            const float4 x = u == 0 ? cur[0] : u == 1 ? cur[1] : u == 2 ? cur[2] : cur[3];
+            const int c = 4 * (base + lane + 32 * u);
+#pragma unroll 1
+            for (int j = 0; j < 4; ++j) {
+                const float v = j == 0 ? x.x : j == 1 ? x.y : j == 2 ? x.z : x.w;
+                tk.push(make_key(v, (uint32_t)(c + j)), c + j < nc);
             }
+            thr_f = tk.thr == KEY_INF ? INFINITY : o2f((uint32_t)(tk.thr >> 32));
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) cur[u] = nxt[u];
@@ -314,23 +336,26 @@ void select_r(const float *D, int64_t ldd, int64_t rows, int32_t nc, int32_t nto
 
 }  // namespace
 
-// Centroids as tensor-core tiles: [nt][hi, lo][PN rows x Kp] in core-matrix
-// layout, rows past nlist zero. Host-side preparation at index upload.
+// Centroids as tensor-core tiles: [nt][KC][hi, lo][PN rows x Kp / KC] in
+// core-matrix layout (each K-chunk contiguous), rows past nlist zero.
+// Host-side preparation at index upload.
 void prepare_centroid_tiles(const float *cent, int32_t nlist, int32_t d, std::vector<uint16_t> &out,
                             int32_t &Kp, int32_t &ntiles) {
     Kp = (d + 15) / 16 * 16;
     ntiles = (nlist + PN - 1) / PN;
+    const int KC = kchunks(Kp), Kc = Kp / KC;
     out.assign((size_t)ntiles * 2 * PN * Kp, 0);
     for (int l = 0; l < nlist; ++l) {
         const int t = l / PN, r = l % PN;
-        uint16_t *hi = out.data() + (size_t)t * 2 * PN * Kp;
-        uint16_t *lo = hi + (size_t)PN * Kp;
         for (int k = 0; k < d; ++k) {
+            const int h = k / Kc, kc = k % Kc;
+            uint16_t *hi = out.data() + ((size_t)t * KC + h) * 2 * PN * Kc;
+            uint16_t *lo = hi + (size_t)PN * Kc;
             const float x = cent[(size_t)l * d + k];
-            const uint16_t h = tc::host_bf16_bits(x);
-            const uint32_t o = tc::core_offset(r, k, Kp) >> 1;
-            hi[o] = h;
-            lo[o] = tc::host_bf16_bits(x - tc::host_bf16_float(h));
+            const uint16_t hb = tc::host_bf16_bits(x);
+            const uint32_t o = tc::core_offset(r, kc, Kc) >> 1;
+            hi[o] = hb;
+            lo[o] = tc::host_bf16_bits(x - tc::host_bf16_float(hb));
         }
     }
 }
