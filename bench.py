@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--rates", default="5000,10000,20000,50000,100000")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--window-us", type=int, default=500)
+    ap.add_argument("--serve-form", choices=["tiled", "plain"], default="tiled",
+                    help="scan form of the served batches: tiled persistent (uneven work) or one CTA per query")
     return ap.parse_args()
 
 
@@ -545,7 +547,8 @@ def bench_serve(args):
     t_build = time.perf_counter() - t0
     pool = z.queries(20000)
     tc = fa.FA_GEMM_BF16_TC
-    sp = fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc)
+    flags = fa.FA_PERSISTENT if args.serve_form == "tiled" else 0
+    sp = fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc, flags=flags)
     srv = fa.Server(ix, sp, max_batch=4096, window_us=args.window_us, slots=4, kmax=100,
                     nprobe_max=256)
     results = []
@@ -595,7 +598,7 @@ def bench_serve(args):
                       "config": {"workload": "ivfpq-f32unit-%dm-d96-zipf65536-M48" % (args.zipf_n // 1_000_000),
                                  "k": "uniform {1,10,100}", "nprobe": "uniform 32..256",
                                  "window_us": args.window_us, "max_batch": 4096, "slots": 4,
-                                 "form": "fp8 LUT, BF16 tensor-core probe and LUT"},
+                                 "form": "fp8 LUT, BF16 tensor-core probe and LUT, %s scan" % args.serve_form},
                       "build_s": t_build}))
 
 
