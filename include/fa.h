@@ -270,7 +270,8 @@ typedef struct fa_server_stats_t {
 void fa_server_params_init(fa_server_params *p);
 
 /* Starts a request loop over ix with the search parameters sp (precision,
- * re-rank, ...; buffer flags and per-query pointers are set by the loop). The
+ * re-rank, ...; buffer flags and per-query pointers are set by the loop, and
+ * batches always run the tiled persistent scan of FA_PERSISTENT). The
  * loop (a host thread) closes a batch when it is full or its oldest request
  * has waited window_us, admits it when one of the `slots` device memory blocks
  * is free (blocks are allocated here, none in the loop), and launches it

@@ -151,7 +151,9 @@ static void launch_batch(fa_server *sv, Slot &s) {
     FA_CHECK_CUDA(cudaMemcpyAsync(s.kq, s.h_k, 4 * nb, cudaMemcpyHostToDevice, s.st));
     FA_CHECK_CUDA(cudaMemcpyAsync(s.npq, s.h_np, 4 * nb, cudaMemcpyHostToDevice, s.st));
     fa_search_params sp = sv->sp;
-    sp.flags |= FA_QUERIES_ON_DEVICE | FA_OUTPUTS_ON_DEVICE | FA_NO_SYNC;
+    // the tiled persistent scan: one query with a long probe set spreads over
+    // many CTAs instead of holding its whole batch back
+    sp.flags |= FA_QUERIES_ON_DEVICE | FA_OUTPUTS_ON_DEVICE | FA_NO_SYNC | FA_PERSISTENT;
     sp.k_per_query = s.kq;
     sp.nprobe_per_query = s.npq;
     sp.probes = nullptr;
