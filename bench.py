@@ -233,12 +233,13 @@ def exact_dists(base, q, ids):
 
 def search_params(fa, form, wl, persistent=False):
     """plain: FP32 everywhere (SIMT coarse probe, FP32 LUT built in the scan CTA).
-    lowp: BF16 tensor-core coarse probe and LUT GEMMs, FP16 (or FP8) LUT."""
+    lowp: BF16 tensor-core coarse probe and LUT GEMMs, FP16 (or FP8) LUT.
+    Both forms re-rank the same top-n on exact FP32 distances (Algorithm 1)."""
     lowp = form == "lowp"
     tc = fa.FA_GEMM_BF16_TC if lowp else fa.FA_GEMM_SIMT_F32
     prec = (fa.FA_LUT_FP8 if wl.get("lut") == "fp8" else fa.FA_LUT_F16) if lowp else fa.FA_LUT_F32
     return fa.search_params(lut_prec=prec, lut_gemm=tc, probe_gemm=tc,
-                            rerank_n=wl["rerank_n"] if lowp else 0, rerank_batch=wl["batch"],
+                            rerank_n=wl["rerank_n"], rerank_batch=wl["batch"],
                             rerank_beta=wl["beta"], rerank_eps=wl["eps"],
                             flags=fa.FA_PERSISTENT if persistent else 0)
 
@@ -614,19 +615,13 @@ def sweep(args, wl, fa, torch, oracle, ix, base, queries, qd, flush, gt, t_build
     for npb in (8, 16, 32, 64, 128, 256, 512):
         cov = np.mean([np.isin(primary[gt[0][i]], probes[i, :npb]).mean() for i in range(ns)])
         print(json.dumps({"coverage_nprobe": npb, "coverage": float(cov)}), flush=True)
-    grid = [("lowp", 64, 100, 32, 0.0, 2)]  # the configured operating point
-    for npb in (8, 16, 32, 64, 128, 256):
-        grid.append(("plain", npb, 0, 32, 0.0, 2))
-    for npb in (8, 16, 32, 64):
-        for n in (256, 512, 1024, 2048, 4096):
-            grid.append(("lowp", npb, n, 32, -1.0, 1))
-    for npb in (128, 256, 512):
-        for n in (1024, 4096):
-            grid.append(("lowp", npb, n, 32, -1.0, 1))
-    for npb in (64, 256):
-        for n in (1024, 4096):
-            for batch, beta in ((256, 2), (128, 3), (512, 1)):
-                grid.append(("lowp", npb, n, batch, 0.0, beta))
+    grid = [("lowp", 64, 100, 32, 0.0, 2), ("plain", 64, 100, 32, 0.0, 2)]  # the configured point
+    for form in ("lowp", "plain"):
+        for npb in (64, 128, 256, 512):
+            for n in (1024, 4096):
+                grid.append((form, npb, n, 32, -1.0, 1))
+    for npb in (128, 256):
+        grid.append(("lowp", npb, 4096, 256, 0.0, 2))
     for form, npb, n, batch, eps, beta in grid:
         w = dict(wl, rerank_n=n, batch=batch, eps=eps, beta=beta)
         sp = search_params(fa, form, w)
