@@ -177,6 +177,14 @@ void fa_free_index(fa_index *ix);
                                   * with the same shape, parameters, pointers
                                   * and stream (device queries and outputs, no
                                   * stats or trace) */
+#define FA_SERIAL 0x40           /* re-rank the whole batch after the whole scan.
+                                  * By default a call of >= 4096 queries that
+                                  * re-ranks from host memory is cut into chunks:
+                                  * chunk i's re-rank (a second stream of the
+                                  * library's, waiting on the host link) runs
+                                  * while chunk i+1 is scanned, as the paper
+                                  * overlaps re-ranking with GPU filtering (§5).
+                                  * The results are the same either way. */
 
 /* Optional per-call trace, measured with CUDA events on the call's stream
  * (ms of device time per stage; launches = kernels this call launched). */

@@ -30,7 +30,7 @@ FA_RAW_NONE, FA_RAW_HOST_PINNED, FA_RAW_DEVICE = 0, 1, 2
 FA_LUT_F32, FA_LUT_F16, FA_LUT_FP8 = 0, 1, 2
 FA_GEMM_SIMT_F32, FA_GEMM_BF16_TC = 0, 1
 FA_QUERIES_ON_DEVICE, FA_OUTPUTS_ON_DEVICE, FA_NONBLOCKING = 0x1, 0x2, 0x4
-FA_PERSISTENT, FA_NO_SYNC, FA_GRAPH = 0x8, 0x10, 0x20
+FA_PERSISTENT, FA_NO_SYNC, FA_GRAPH, FA_SERIAL = 0x8, 0x10, 0x20, 0x40
 
 P = C.c_void_p
 i32, i64, u64, f32 = C.c_int32, C.c_int64, C.c_uint64, C.c_float

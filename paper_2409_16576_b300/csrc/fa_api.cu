@@ -346,6 +346,9 @@ static void ws_ensure_partial(Workspace *w, int64_t nq, int32_t ntop) {
     w->tile_cap = cap;
 }
 
+// chunks of a pipelined search (scan of chunk i + 1 beside the re-rank of chunk i)
+constexpr int PIPE_CHUNKS = 4;
+
 struct WsLease {
     fa_index *ix;
     Workspace *w = nullptr;
@@ -361,8 +364,16 @@ struct WsLease {
             if ((int)ix->all_ws.size() < ix->max_ws) {
                 w = new Workspace();
                 w->device = ix->device;
-                if (cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) != cudaSuccess ||
-                    cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) != cudaSuccess) {
+                int prio_lo = 0, prio_hi = 0;
+                cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+                bool ok = cudaStreamCreateWithFlags(&w->stream, cudaStreamNonBlocking) == cudaSuccess &&
+                          cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) == cudaSuccess &&
+                          cudaStreamCreateWithPriority(&w->stream2, cudaStreamNonBlocking, prio_hi) ==
+                              cudaSuccess &&
+                          cudaEventCreateWithFlags(&w->join, cudaEventDisableTiming) == cudaSuccess;
+                for (auto &e : w->fork)
+                    ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+                if (!ok) {
                     cudaGetLastError();
                     delete w;
                     w = nullptr;
@@ -471,6 +482,9 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     if ((sp.flags & FA_PERSISTENT) && tile_chunks == 0) tile_chunks = 256;
     if (ntop > 256) tile_chunks = 0;  // the CTA-wide top-n runs one CTA per query
     if (tile_chunks > 0) ws_ensure_partial(w, nq, ntop);
+    // pipelined re-rank (see FA_SERIAL): large batches re-ranked from host memory
+    const bool pipelined = rerank && tile_chunks == 0 && !(sp.flags & FA_SERIAL) && nq >= 4096 &&
+                           D.raw_location == FA_RAW_HOST_PINNED;
 
     auto enqueue = [&]() {
         FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
@@ -543,6 +557,37 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             launch_scan(D, sl, st);
             launch_tile_merge(w->partial, w->tprefix, nq, ntop, w->topkeys, st);
             tr.launches += 4;
+        } else if (pipelined) {
+            // chunk c's re-rank (on the slot's second stream, waiting on the
+            // host link) runs while chunk c + 1 is scanned; the re-rank CTAs
+            // are one warp each so they fit beside the scan CTAs
+            const int64_t csz = (nq + PIPE_CHUNKS - 1) / PIPE_CHUNKS;
+            int32_t *stt = sp.stats ? w->stats : nullptr;
+            for (int c = 0; c < PIPE_CHUNKS; ++c) {
+                const int64_t q0 = c * csz, qn = std::min(csz, nq - q0);
+                if (qn <= 0) break;
+                ScanLaunch sc = sl;
+                sc.q = qd + q0 * d;
+                sc.probes = probes + q0 * nprobe;
+                sc.npq = npq ? npq + q0 : nullptr;
+                sc.nq = qn;
+                sc.lut = w->lut ? static_cast<char *>(w->lut) + q0 * lut_bytes : nullptr;
+                sc.lut_scale = w->lut_scale + q0 * 2 * D.M;
+                sc.topkeys = w->topkeys + q0 * ntop;
+                sc.stats = stt ? stt + q0 * 4 : nullptr;
+                sc.order = nullptr;
+                if (sc.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
+                launch_scan(D, sc, st);
+                FA_CHECK_CUDA(cudaEventRecord(w->fork[c], st));
+                FA_CHECK_CUDA(cudaStreamWaitEvent(w->stream2, w->fork[c], 0));
+                launch_rerank(D, qd + q0 * d, w->topkeys + q0 * ntop, qn, ntop, k, kq ? kq + q0 : nullptr,
+                              sp.rerank_batch, sp.rerank_beta, sp.rerank_eps, oid + q0 * k, odist + q0 * k,
+                              stt ? stt + q0 * 4 : nullptr, 1, w->stream2);
+                tr.launches += 2;
+            }
+            tr.mark(3);
+            FA_CHECK_CUDA(cudaEventRecord(w->join, w->stream2));
+            FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->join, 0));
         } else {
             launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
             sl.order = w->order;
@@ -550,14 +595,15 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             launch_scan(D, sl, st);
             tr.launches += 4;
         }
-        tr.mark(3);
-
-        if (rerank)
-            launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
-                          sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, st);
-        else
-            launch_finish(D, w->topkeys, nq, ntop, k, kq, oid, odist, st);
-        tr.launches += 1;
+        if (!pipelined) {
+            tr.mark(3);
+            if (rerank)
+                launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
+                              sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, 8, st);
+            else
+                launch_finish(D, w->topkeys, nq, ntop, k, kq, oid, odist, st);
+            tr.launches += 1;
+        }
         tr.mark(4);
 
     };
@@ -584,7 +630,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         key.rerank_batch = sp.rerank_batch;
         key.rerank_beta = sp.rerank_beta;
         key.rerank_eps = sp.rerank_eps;
-        key.flags = sp.flags & (FA_PERSISTENT);
+        key.flags = sp.flags & (FA_PERSISTENT | FA_SERIAL);
         key.threads = tune.threads;
         key.ilp = tune.ilp;
         key.persistent = tune.persistent;
@@ -713,8 +759,13 @@ static void destroy(fa_index *ix) {
         if (w->pending) cudaEventSynchronize(w->done);
         if (w->stream) cudaStreamSynchronize(w->stream);
         ws_free_buffers(w);
+        if (w->stream2) cudaStreamSynchronize(w->stream2);
         if (w->stream) cudaStreamDestroy(w->stream);
+        if (w->stream2) cudaStreamDestroy(w->stream2);
         if (w->done) cudaEventDestroy(w->done);
+        if (w->join) cudaEventDestroy(w->join);
+        for (cudaEvent_t e : w->fork)
+            if (e) cudaEventDestroy(e);
         delete w;
     }
     free_device_index(ix);

@@ -105,6 +105,8 @@ struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;    // end of the last no-sync call on this slot
+    cudaStream_t stream2 = nullptr;       // re-rank stream of the pipelined search (high priority)
+    cudaEvent_t fork[4] = {}, join = nullptr;  // chunk i scanned / every re-rank done
     bool pending = false;
     cudaGraphExec_t gexec = nullptr;  // last captured search (FA_GRAPH)
     GraphKey gkey{};
@@ -259,7 +261,7 @@ void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, i
                    cudaStream_t st);
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
-                   float eps, int64_t *out_ids, float *out_dist, int32_t *stats,
+                   float eps, int64_t *out_ids, float *out_dist, int32_t *stats, int warps,
                    cudaStream_t st);
 void launch_debug_candidates(const DeviceIndex &ix, const int32_t *probes, int32_t nprobe,
                              uint32_t *out, uint32_t *count, uint32_t cap, cudaStream_t st);

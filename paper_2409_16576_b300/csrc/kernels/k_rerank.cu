@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(256) k_rerank(
     float *__restrict__ out_dist, int32_t *stats) {
     extern __shared__ float qsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t qi = (int64_t)blockIdx.x * 8 + warp;
+    const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
     if (qi >= nq) return;
     float *qs = qsm + warp * d;
     for (int j = lane; j < d; j += 32) qs[j] = q[qi * d + j];
@@ -264,17 +264,17 @@ template <typename T>
 static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_t *topkeys,
                             int64_t nq, int32_t ntop, int32_t k, const int32_t *kq, int32_t batch,
                             int32_t beta, float eps, int64_t *out_ids, float *out_dist,
-                            int32_t *stats, cudaStream_t st) {
-    const dim3 grid((unsigned)((nq + 7) / 8));
-    const int smem = 8 * ix.d * 4;
+                            int32_t *stats, int warps, cudaStream_t st) {
+    const dim3 grid((unsigned)((nq + warps - 1) / warps));
+    const int smem = warps * ix.d * 4;
     const T *raw = reinterpret_cast<const T *>(ix.raw);
 #define FA_RR(RR)                                                                                 \
     do {                                                                                          \
         FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T>,                                       \
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
-        k_rerank<RR, T><<<grid, 256, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, batch, beta,  \
-                                                 eps, ix.perm, raw, out_ids, out_dist,            \
-                                                 stats);                                          \
+        k_rerank<RR, T><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, batch, \
+                                                         beta, eps, ix.perm, raw, out_ids, out_dist, \
+                                                         stats);                                  \
     } while (0)
     if (k <= 32)
         FA_RR(1);
@@ -288,19 +288,22 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
     FA_CHECK_CUDA(cudaGetLastError());
 }
 
+// warps: queries per CTA. One warp per CTA lets the re-rank run beside a scan
+// that fills the SMs (it needs one warp's registers and d floats of shared
+// memory), which is how the pipelined search overlaps the two.
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
-                   float eps, int64_t *out_ids, float *out_dist, int32_t *stats,
+                   float eps, int64_t *out_ids, float *out_dist, int32_t *stats, int warps,
                    cudaStream_t st) {
     if (nq == 0) return;
     FA_REQUIRE(ix.raw != nullptr, FA_ERR_ARG, "re-rank needs raw vectors in the index");
     if (ix.raw_dtype == FA_U8) {
         FA_REQUIRE(ix.d % 4 == 0, FA_ERR_ARG, "uint8 re-rank needs d % 4 == 0");
         launch_rerank_t<uint8_t>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
-                                 out_ids, out_dist, stats, st);
+                                 out_ids, out_dist, stats, warps, st);
     } else {
         launch_rerank_t<float>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
-                               out_ids, out_dist, stats, st);
+                               out_ids, out_dist, stats, warps, st);
     }
 }
 

@@ -619,6 +619,28 @@ def test_rerank_matches_oracle(fa, u8_repl, eps, beta, batch, n):
     assert compared >= q.shape[0] // 2
 
 
+@pytest.mark.parametrize("lowp", [False, True])
+def test_pipelined_rerank_equals_serial(fa, u8_repl, lowp):
+    """A batch of >= 4096 queries re-ranked from pinned host memory is scanned
+    and re-ranked in overlapping chunks on two streams; every id, distance and
+    per-query statistic equals the serial order's (FA_SERIAL), on a ragged
+    batch with per-query k and nprobe."""
+    s = u8_repl
+    q = synth.Mixture(128, 16, 8.0, kind="u8").queries(5003).astype(np.float32)
+    kq = synth.uniform_ints(1, 10, q.shape[0], tag=21)
+    npq = synth.uniform_ints(4, 16, q.shape[0], tag=22)
+    extra = dict(lut_prec=fa.FA_LUT_F16, lut_gemm=fa.FA_GEMM_BF16_TC, probe_gemm=fa.FA_GEMM_BF16_TC) if lowp else {}
+    out = []
+    for flags in (0, fa.FA_SERIAL):
+        p = fa.search_params(rerank_n=64, rerank_batch=16, rerank_beta=2, rerank_eps=0.0, flags=flags, **extra)
+        out.append(fa.fa_search_ex(s["ix"], q, 10, 16, p, k_per_query=kq, nprobe_per_query=npq, stats=True))
+    (pi, pd, pst), (si, sd, sst) = out
+    assert np.array_equal(pi, si)
+    assert np.array_equal(pd.view(np.uint32), sd.view(np.uint32))
+    assert np.array_equal(pst, sst)
+    assert np.all(pst[:, 2] >= 1)  # every query re-ranked at least one mini-batch
+
+
 def test_rerank_device_raw_equals_pinned(fa, f32_small):
     s = f32_small
     q = s["q"][:30]
