@@ -582,7 +582,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
                 FA_CHECK_CUDA(cudaStreamWaitEvent(w->stream2, w->fork[c], 0));
                 launch_rerank(D, qd + q0 * d, w->topkeys + q0 * ntop, qn, ntop, k, kq ? kq + q0 : nullptr,
                               sp.rerank_batch, sp.rerank_beta, sp.rerank_eps, oid + q0 * k, odist + q0 * k,
-                              stt ? stt + q0 * 4 : nullptr, 1, w->stream2);
+                              stt ? stt + q0 * 4 : nullptr, 1, w->tile_ctr + 1, w->stream2);
                 tr.launches += 2;
             }
             tr.mark(3);
@@ -599,7 +599,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             tr.mark(3);
             if (rerank)
                 launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
-                              sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, 8, st);
+                              sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, 8, nullptr, st);
             else
                 launch_finish(D, w->topkeys, nq, ntop, k, kq, oid, odist, st);
             tr.launches += 1;

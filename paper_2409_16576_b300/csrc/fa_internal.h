@@ -262,7 +262,7 @@ void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, i
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
                    float eps, int64_t *out_ids, float *out_dist, int32_t *stats, int warps,
-                   cudaStream_t st);
+                   uint32_t *ctr, cudaStream_t st);
 void launch_debug_candidates(const DeviceIndex &ix, const int32_t *probes, int32_t nprobe,
                              uint32_t *out, uint32_t *count, uint32_t cap, cudaStream_t st);
 

@@ -179,16 +179,13 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
 }
 
 template <int R, typename T>
-__global__ void __launch_bounds__(256) k_rerank(
-    const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
+__device__ __forceinline__ void rerank_one(
+    const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t qi,
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
     const int64_t *__restrict__ perm, const T *__restrict__ raw, int64_t *__restrict__ out_ids,
-    float *__restrict__ out_dist, int32_t *stats) {
-    extern __shared__ float qsm[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    if (qi >= nq) return;
-    float *qs = qsm + warp * d;
+    float *__restrict__ out_dist, int32_t *stats, float *qs) {
+    const int lane = threadIdx.x & 31;
+    __syncwarp();  // the previous query of this warp is done with qs
     for (int j = lane; j < d; j += 32) qs[j] = q[qi * d + j];
     __syncwarp();
     int kk = kq ? kq[qi] : k;
@@ -260,12 +257,44 @@ __global__ void __launch_bounds__(256) k_rerank(
     }
 }
 
+// One warp per query. ctr == null: warp w of CTA b takes query b * warps + w.
+// Otherwise the warps are persistent and pull queries from *ctr (zeroed by
+// the caller), so a small grid can run beside another kernel without taking
+// more than its own warps' share of an SM.
+template <int R, typename T>
+__global__ void __launch_bounds__(256) k_rerank(
+    const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
+    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
+    const int64_t *__restrict__ perm, const T *__restrict__ raw, int64_t *__restrict__ out_ids,
+    float *__restrict__ out_dist, int32_t *stats, uint32_t *ctr) {
+    extern __shared__ float qsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *qs = qsm + warp * d;
+    for (int64_t it = 0;; ++it) {
+        int64_t qi;
+        if (ctr) {
+            uint32_t x = 0;
+            if (lane == 0) x = atomicAdd(ctr, 1u);
+            qi = __shfl_sync(FULL, x, 0);
+        } else {
+            if (it > 0) break;
+            qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+        }
+        if (qi >= nq) break;
+        rerank_one<R, T>(q, d, topkeys, qi, ntop, k, kq, batch, beta, eps, perm, raw, out_ids,
+                         out_dist, stats, qs);
+    }
+}
+
 template <typename T>
 static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_t *topkeys,
                             int64_t nq, int32_t ntop, int32_t k, const int32_t *kq, int32_t batch,
                             int32_t beta, float eps, int64_t *out_ids, float *out_dist,
-                            int32_t *stats, int warps, cudaStream_t st) {
-    const dim3 grid((unsigned)((nq + warps - 1) / warps));
+                            int32_t *stats, int warps, uint32_t *ctr, cudaStream_t st) {
+    // persistent: one warp per SM pulls queries; else one warp per query
+    const dim3 grid(ctr ? (unsigned)std::min<int64_t>(nq, num_sms(0))
+                        : (unsigned)((nq + warps - 1) / warps));
+    if (ctr) FA_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 4, st));
     const int smem = warps * ix.d * 4;
     const T *raw = reinterpret_cast<const T *>(ix.raw);
 #define FA_RR(RR)                                                                                 \
@@ -274,7 +303,7 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
         k_rerank<RR, T><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, batch, \
                                                          beta, eps, ix.perm, raw, out_ids, out_dist, \
-                                                         stats);                                  \
+                                                         stats, ctr);                             \
     } while (0)
     if (k <= 32)
         FA_RR(1);
@@ -288,22 +317,23 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
     FA_CHECK_CUDA(cudaGetLastError());
 }
 
-// warps: queries per CTA. One warp per CTA lets the re-rank run beside a scan
-// that fills the SMs (it needs one warp's registers and d floats of shared
-// memory), which is how the pipelined search overlaps the two.
+// warps: queries per CTA. With ctr, a persistent grid of one-warp CTAs (one
+// per SM) pulls queries from the counter: it needs one warp's registers and d
+// floats of shared memory per SM, so it runs beside a scan that fills the SMs,
+// which is how the pipelined search overlaps the two.
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
                    float eps, int64_t *out_ids, float *out_dist, int32_t *stats, int warps,
-                   cudaStream_t st) {
+                   uint32_t *ctr, cudaStream_t st) {
     if (nq == 0) return;
     FA_REQUIRE(ix.raw != nullptr, FA_ERR_ARG, "re-rank needs raw vectors in the index");
     if (ix.raw_dtype == FA_U8) {
         FA_REQUIRE(ix.d % 4 == 0, FA_ERR_ARG, "uint8 re-rank needs d % 4 == 0");
         launch_rerank_t<uint8_t>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
-                                 out_ids, out_dist, stats, warps, st);
+                                 out_ids, out_dist, stats, warps, ctr, st);
     } else {
         launch_rerank_t<float>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
-                               out_ids, out_dist, stats, warps, st);
+                               out_ids, out_dist, stats, warps, ctr, st);
     }
 }
 
