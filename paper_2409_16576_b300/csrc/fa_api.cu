@@ -347,7 +347,7 @@ static void ws_ensure_partial(Workspace *w, int64_t nq, int32_t ntop) {
 }
 
 // chunks of a pipelined search (scan of chunk i + 1 beside the re-rank of chunk i)
-constexpr int PIPE_CHUNKS = 4;
+constexpr int PIPE_CHUNKS = 8;
 
 struct WsLease {
     fa_index *ix;
@@ -370,7 +370,10 @@ struct WsLease {
                           cudaEventCreateWithFlags(&w->done, cudaEventDisableTiming) == cudaSuccess &&
                           cudaStreamCreateWithPriority(&w->stream2, cudaStreamNonBlocking, prio_hi) ==
                               cudaSuccess &&
-                          cudaEventCreateWithFlags(&w->join, cudaEventDisableTiming) == cudaSuccess;
+                          cudaStreamCreateWithFlags(&w->stream3, cudaStreamNonBlocking) == cudaSuccess &&
+                          cudaEventCreateWithFlags(&w->join, cudaEventDisableTiming) == cudaSuccess &&
+                          cudaEventCreateWithFlags(&w->join3, cudaEventDisableTiming) == cudaSuccess &&
+                          cudaEventCreateWithFlags(&w->lut_done, cudaEventDisableTiming) == cudaSuccess;
                 for (auto &e : w->fork)
                     ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
                 if (!ok) {
@@ -558,14 +561,19 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             launch_tile_merge(w->partial, w->tprefix, nq, ntop, w->topkeys, st);
             tr.launches += 4;
         } else if (pipelined) {
-            // chunk c's re-rank (on the slot's second stream, waiting on the
-            // host link) runs while chunk c + 1 is scanned; the re-rank CTAs
-            // are one warp each so they fit beside the scan CTAs
+            // chunk c's re-rank (on the slot's high-priority stream, waiting on
+            // the host link) runs while chunk c + 1 is scanned. Scans alternate
+            // between the call's stream and a second one so that one chunk's
+            // last CTAs overlap the next chunk's first; the re-rank is a
+            // persistent one-warp-per-SM grid, so the scans keep their occupancy.
             const int64_t csz = (nq + PIPE_CHUNKS - 1) / PIPE_CHUNKS;
             int32_t *stt = sp.stats ? w->stats : nullptr;
+            FA_CHECK_CUDA(cudaEventRecord(w->lut_done, st));
+            FA_CHECK_CUDA(cudaStreamWaitEvent(w->stream3, w->lut_done, 0));
             for (int c = 0; c < PIPE_CHUNKS; ++c) {
                 const int64_t q0 = c * csz, qn = std::min(csz, nq - q0);
                 if (qn <= 0) break;
+                cudaStream_t ss = (c & 1) ? w->stream3 : st;
                 ScanLaunch sc = sl;
                 sc.q = qd + q0 * d;
                 sc.probes = probes + q0 * nprobe;
@@ -576,15 +584,17 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
                 sc.topkeys = w->topkeys + q0 * ntop;
                 sc.stats = stt ? stt + q0 * 4 : nullptr;
                 sc.order = nullptr;
-                if (sc.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
-                launch_scan(D, sc, st);
-                FA_CHECK_CUDA(cudaEventRecord(w->fork[c], st));
+                sc.persistent = 0;  // one counter would be shared by the two scan streams
+                launch_scan(D, sc, ss);
+                FA_CHECK_CUDA(cudaEventRecord(w->fork[c], ss));
                 FA_CHECK_CUDA(cudaStreamWaitEvent(w->stream2, w->fork[c], 0));
                 launch_rerank(D, qd + q0 * d, w->topkeys + q0 * ntop, qn, ntop, k, kq ? kq + q0 : nullptr,
                               sp.rerank_batch, sp.rerank_beta, sp.rerank_eps, oid + q0 * k, odist + q0 * k,
                               stt ? stt + q0 * 4 : nullptr, 1, w->tile_ctr + 1, w->stream2);
                 tr.launches += 2;
             }
+            FA_CHECK_CUDA(cudaEventRecord(w->join3, w->stream3));
+            FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->join3, 0));
             tr.mark(3);
             FA_CHECK_CUDA(cudaEventRecord(w->join, w->stream2));
             FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->join, 0));
@@ -760,10 +770,14 @@ static void destroy(fa_index *ix) {
         if (w->stream) cudaStreamSynchronize(w->stream);
         ws_free_buffers(w);
         if (w->stream2) cudaStreamSynchronize(w->stream2);
+        if (w->stream3) cudaStreamSynchronize(w->stream3);
         if (w->stream) cudaStreamDestroy(w->stream);
         if (w->stream2) cudaStreamDestroy(w->stream2);
+        if (w->stream3) cudaStreamDestroy(w->stream3);
         if (w->done) cudaEventDestroy(w->done);
         if (w->join) cudaEventDestroy(w->join);
+        if (w->join3) cudaEventDestroy(w->join3);
+        if (w->lut_done) cudaEventDestroy(w->lut_done);
         for (cudaEvent_t e : w->fork)
             if (e) cudaEventDestroy(e);
         delete w;

@@ -105,8 +105,10 @@ struct Workspace {
     int device = 0;
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;    // end of the last no-sync call on this slot
-    cudaStream_t stream2 = nullptr;       // re-rank stream of the pipelined search (high priority)
-    cudaEvent_t fork[4] = {}, join = nullptr;  // chunk i scanned / every re-rank done
+    cudaStream_t stream2 = nullptr;  // re-rank stream of the pipelined search (high priority)
+    cudaStream_t stream3 = nullptr;  // second scan stream of the pipelined search
+    cudaEvent_t fork[8] = {};        // chunk i scanned
+    cudaEvent_t lut_done = nullptr, join = nullptr, join3 = nullptr;
     bool pending = false;
     cudaGraphExec_t gexec = nullptr;  // last captured search (FA_GRAPH)
     GraphKey gkey{};
