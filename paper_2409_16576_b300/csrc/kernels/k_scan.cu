@@ -110,37 +110,63 @@ struct ScanPtrs {
     }
 };
 
-__device__ __forceinline__ float lut_entry_global(const ScanArgs &a, int64_t qi, int m, int c) {
-    const int64_t base = qi * (int64_t)a.M * 256 + (int64_t)m * 256 + c;
-    const float *sc = a.lut_scale + qi * 2 * a.M + 2 * m;  // (scale, offset) of subspace m
-    if (a.lut_prec == FA_LUT_F32) return reinterpret_cast<const float *>(a.lut)[base];
-    if (a.lut_prec == FA_LUT_F16)
-        return __half2float(reinterpret_cast<const __half *>(a.lut)[base]) * sc[0] + sc[1];
-    __nv_fp8_e4m3 v;
-    v.__x = reinterpret_cast<const uint8_t *>(a.lut)[base];
-    return float(v) * sc[0] + sc[1];
-}
-
 // Builds the LUT of query qi in shared memory (rows of W floats; entry
 // p of row c is LUT[p mod M][c] for p < M + 31).
 template <int M, int W>
 __device__ __forceinline__ void build_lut(const ScanArgs &a, int64_t qi, float *lut, const float *qv) {
     const int dsub = a.dsub;
     constexpr int P = M + 31;
+    if (a.lut_prec >= 0) {
+        // table from HBM ([M][256] per query): each thread takes 8 consecutive
+        // centroids of one subspace with one or two vector loads; the lanes of
+        // a warp hold different subspaces, so the shared-memory stores below
+        // stay conflict-free
+        const int64_t qbase = qi * (int64_t)M * 256;
+        for (int idx = threadIdx.x; idx < M * 32; idx += blockDim.x) {
+            const int m = idx % M, c0 = (idx / M) * 8;
+            const float *sc = a.lut_scale + qi * 2 * M + 2 * m;  // (scale, offset) of subspace m
+            const int64_t e0 = qbase + (int64_t)m * 256 + c0;
+            float v[8];
+            if (a.lut_prec == FA_LUT_F32) {
+                const float4 x0 = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(a.lut) + e0));
+                const float4 x1 = __ldg(reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(a.lut) + e0) + 1);
+                v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
+                v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
+            } else if (a.lut_prec == FA_LUT_F16) {
+                const uint4 u = __ldg(reinterpret_cast<const uint4 *>(reinterpret_cast<const __half *>(a.lut) + e0));
+                const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const __half2 h = *reinterpret_cast<const __half2 *>(&w4[j]);
+                    v[2 * j] = __half2float(__low2half(h)) * sc[0] + sc[1];
+                    v[2 * j + 1] = __half2float(__high2half(h)) * sc[0] + sc[1];
+                }
+            } else {
+                const uint2 u = __ldg(reinterpret_cast<const uint2 *>(reinterpret_cast<const uint8_t *>(a.lut) + e0));
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    __nv_fp8_e4m3 f;
+                    f.__x = (uint8_t)(((j < 4 ? u.x : u.y) >> (8 * (j & 3))) & 0xffu);
+                    v[j] = float(f) * sc[0] + sc[1];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int p = 0; p < P; p += M)
+                    if (p + m < P) lut[(c0 + j) * W + p + m] = v[j];
+        }
+        return;
+    }
     for (int idx = threadIdx.x; idx < 256 * M; idx += blockDim.x) {
         const int c = idx / M, m = idx - c * M;  // M is a compile-time constant
-        float val;
-        if (a.lut_prec < 0) {
-            const float *cw = a.codebooks + ((int64_t)m * 256 + c) * dsub;
-            const float *qm = qv + m * dsub;
-            float s = 0.f;
-            for (int j = 0; j < dsub; ++j) {
-                const float t = qm[j] - cw[j];
-                s = fmaf(t, t, s);
-            }
-            val = s;
-        } else {
-            val = lut_entry_global(a, qi, m, c);
+        // FP32 form: the table built here from the codebooks (Eq. 1)
+        const float *cw = a.codebooks + ((int64_t)m * 256 + c) * dsub;
+        const float *qm = qv + m * dsub;
+        float val = 0.f;
+        for (int j = 0; j < dsub; ++j) {
+            const float t = qm[j] - cw[j];
+            val = fmaf(t, t, val);
         }
 #pragma unroll
         for (int p = 0; p < P; p += M)
@@ -382,6 +408,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
     __shared__ Work s_w;
     __shared__ uint32_t s_kept;
     __shared__ unsigned long long s_thr;
+    __shared__ unsigned long long s_slots[NWARP];  // each warp's ceil(n / NWARP)-th key
     constexpr int NW = M / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -391,6 +418,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
             s_kept = 0;
             s_thr = KEY_INF;
         }
+        if (threadIdx.x < NWARP) s_slots[threadIdx.x] = KEY_INF;
         __syncthreads();
         const Work wk = s_w;
         const int64_t qi = wk.qi;
@@ -403,6 +431,9 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
         WarpTopK<R> tk;
         tk.init(wbuf + warp * 64, ntop);
         tk.sthr = &s_thr;
+        tk.slots = s_slots;
+        tk.nslots = NWARP;
+        tk.slot = warp;
         const uint32_t total = S.pref[2 * np];
         const uint32_t cend = total < wk.climit ? total : wk.climit;
         uint32_t kept = 0;

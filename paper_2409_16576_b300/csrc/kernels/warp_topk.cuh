@@ -138,9 +138,19 @@ struct WarpTopK {
     int cnt;        // keys in buf (warp-uniform)
     int n;          // keys wanted, 1 <= n <= 32*R
     unsigned long long *sthr;  // optional threshold shared by the CTA's warps
+    // Optional, with sthr: one slot per warp of the CTA (nslots of them, all
+    // KEY_INF at the start of a query). Warp w publishes its t-th smallest key,
+    // t = ceil(n / nslots). The nslots warps then hold at least n distinct keys
+    // at or below the largest published key, so that key bounds the CTA's
+    // n-th smallest: a much tighter threshold than any one warp's n-th.
+    unsigned long long *slots;
+    int nslots, slot;
 
     __device__ __forceinline__ void init(uint64_t *wbuf, int n_) {
         sthr = nullptr;
+        slots = nullptr;
+        nslots = 0;
+        slot = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) L[r] = KEY_INF;
         thr = KEY_INF;
@@ -159,6 +169,15 @@ struct WarpTopK {
         thr = warp_elem<R>(L, n - 1);
         // any warp's n-th best bounds the CTA's n-th best from above
         if (sthr && thr != KEY_INF && (threadIdx.x & 31) == 0) atomicMin(sthr, (unsigned long long)thr);
+        if (slots) {
+            const uint64_t mine = warp_elem<R>(L, (n + nslots - 1) / nslots - 1);
+            if (lane == 0) *(volatile unsigned long long *)(slots + slot) = mine;
+            __syncwarp();
+            uint64_t hi = lane < nslots ? *(volatile unsigned long long *)(slots + lane) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) hi = umax64(hi, shfl_xor64(hi, o));
+            if (hi != KEY_INF && lane == 0) atomicMin(sthr, (unsigned long long)hi);
+        }
         int rem = cnt - 32;
         uint64_t x = (rem > 0 && lane < rem) ? buf[32 + lane] : 0;
         __syncwarp();
