@@ -566,12 +566,15 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             // between the call's stream and a second one so that one chunk's
             // last CTAs overlap the next chunk's first; the re-rank is a
             // persistent one-warp-per-SM grid, so the scans keep their occupancy.
-            const int64_t csz = (nq + PIPE_CHUNKS - 1) / PIPE_CHUNKS;
+            // the last chunk is small: its re-rank is the only one left exposed
+            const int64_t last = std::max<int64_t>(128, nq / 32);
+            const int64_t csz = (nq - last + PIPE_CHUNKS - 2) / (PIPE_CHUNKS - 1);
             int32_t *stt = sp.stats ? w->stats : nullptr;
             FA_CHECK_CUDA(cudaEventRecord(w->lut_done, st));
             FA_CHECK_CUDA(cudaStreamWaitEvent(w->stream3, w->lut_done, 0));
             for (int c = 0; c < PIPE_CHUNKS; ++c) {
-                const int64_t q0 = c * csz, qn = std::min(csz, nq - q0);
+                const int64_t q0 = std::min<int64_t>(nq, c * csz);
+                const int64_t qn = c == PIPE_CHUNKS - 1 ? nq - q0 : std::min(csz, nq - q0);
                 if (qn <= 0) break;
                 cudaStream_t ss = (c & 1) ? w->stream3 : st;
                 ScanLaunch sc = sl;
