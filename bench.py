@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recall", type=int, default=1000, help="queries in the recall subsample (0 = off)")
     ap.add_argument("--sweep", action="store_true", help="recall/QPS grid instead of one bench line")
+    ap.add_argument("--serial", action="store_true",
+                    help="re-rank after the whole scan (FA_SERIAL) instead of the pipelined chunks")
     ap.add_argument("--workload", default="sift10m", choices=["sift10m", "zipf"],
                     help="zipf: the batching-form workload (Zipf lists, per-query nprobe)")
     ap.add_argument("--zipf-n", type=int, default=100_000_000)
@@ -231,7 +233,7 @@ def exact_dists(base, q, ids):
     return out
 
 
-def search_params(fa, form, wl, persistent=False):
+def search_params(fa, form, wl, persistent=False, serial=False):
     """plain: FP32 everywhere (SIMT coarse probe, FP32 LUT built in the scan CTA).
     lowp: BF16 tensor-core coarse probe and LUT GEMMs, FP16 (or FP8) LUT.
     Both forms re-rank the same top-n on exact FP32 distances (Algorithm 1)."""
@@ -241,7 +243,7 @@ def search_params(fa, form, wl, persistent=False):
     return fa.search_params(lut_prec=prec, lut_gemm=tc, probe_gemm=tc,
                             rerank_n=wl["rerank_n"], rerank_batch=wl["batch"],
                             rerank_beta=wl["beta"], rerank_eps=wl["eps"],
-                            flags=fa.FA_PERSISTENT if persistent else 0)
+                            flags=(fa.FA_PERSISTENT if persistent else 0) | (fa.FA_SERIAL if serial else 0))
 
 
 def timed_steps(fa, torch, ix, qd, k, nprobe, sp, steps, warmup, flush, oid, odist):
@@ -319,9 +321,14 @@ def main():
         return sweep(args, wl, fa, torch, oracle, ix, base, queries, qd, flush, gt, t_build)
 
     lowp = args.form == "lowp"
-    sp = search_params(fa, args.form, wl, args.persistent)
+    sp = search_params(fa, args.form, wl, args.persistent, args.serial)
+    # the search pipelines scan and re-rank in 8 chunks when it re-ranks a large
+    # batch from host memory (see FA_SERIAL in include/fa.h)
+    pipelined = (wl["rerank_n"] > 0 and args.raw != "device" and not args.serial and not args.persistent
+                 and wl["nq"] >= 4096)
     # autotuner: scan launch shape timed on a 2k-query sample of the batch
     tuned = fa.fa_autotune(ix, queries[:2000], k, wl["nprobe"], sp)["chosen"]
+    pipelined = pipelined and tuned["tile_chunks"] == 0
     oid = torch.empty((nq, k), dtype=torch.int64, device="cuda")
     odist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
 
@@ -413,6 +420,11 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "k_scan", "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": scan_bytes,
+                         "launches_per_step": 8 if pipelined else 1,
+                         "timed_as": ("the step's scan stage: 8 chunk launches on two streams, "
+                                      "with the re-ranks of earlier chunks running beside them; "
+                                      "bytes and traffic are the step's totals") if pipelined
+                         else "the step's single scan launch",
                          "kernel_src_hash": khash},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
