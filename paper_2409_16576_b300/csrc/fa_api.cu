@@ -566,16 +566,18 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             // between the call's stream and a second one so that one chunk's
             // last CTAs overlap the next chunk's first; the re-rank is a
             // persistent one-warp-per-SM grid, so the scans keep their occupancy.
-            // the last chunk is small: its re-rank is the only one left exposed
-            const int64_t last = std::max<int64_t>(128, nq / 32);
-            const int64_t csz = (nq - last + PIPE_CHUNKS - 2) / (PIPE_CHUNKS - 1);
+            // chunk sizes shrink towards the end (weights 4,4,4,4,4,3,2,1): the
+            // re-ranks still running when the last scans finish are short
+            static constexpr int PIPE_W[PIPE_CHUNKS] = {4, 4, 4, 4, 4, 3, 2, 1};
             int32_t *stt = sp.stats ? w->stats : nullptr;
             FA_CHECK_CUDA(cudaEventRecord(w->lut_done, st));
             FA_CHECK_CUDA(cudaStreamWaitEvent(w->stream3, w->lut_done, 0));
+            int64_t q0 = 0, wsum = 0;
             for (int c = 0; c < PIPE_CHUNKS; ++c) {
-                const int64_t q0 = std::min<int64_t>(nq, c * csz);
-                const int64_t qn = c == PIPE_CHUNKS - 1 ? nq - q0 : std::min(csz, nq - q0);
-                if (qn <= 0) break;
+                wsum += PIPE_W[c];
+                const int64_t q1 = c == PIPE_CHUNKS - 1 ? nq : nq * wsum / 26;
+                const int64_t qn = q1 - q0;
+                if (qn <= 0) continue;
                 cudaStream_t ss = (c & 1) ? w->stream3 : st;
                 ScanLaunch sc = sl;
                 sc.q = qd + q0 * d;
@@ -595,6 +597,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
                               sp.rerank_batch, sp.rerank_beta, sp.rerank_eps, oid + q0 * k, odist + q0 * k,
                               stt ? stt + q0 * 4 : nullptr, 1, w->tile_ctr + 1, w->stream2);
                 tr.launches += 2;
+                q0 = q1;
             }
             FA_CHECK_CUDA(cudaEventRecord(w->join3, w->stream3));
             FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->join3, 0));
