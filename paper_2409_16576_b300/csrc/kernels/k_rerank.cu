@@ -261,8 +261,10 @@ __device__ __forceinline__ void rerank_one(
 // Otherwise the warps are persistent and pull queries from *ctr (zeroed by
 // the caller), so a small grid can run beside another kernel without taking
 // more than its own warps' share of an SM.
-template <int R, typename T>
-__global__ void __launch_bounds__(256) k_rerank(
+// LEAN: the persistent form run beside a scan; capped at 64 registers so
+// that two of its warps fit in what three scan CTAs leave of an SM.
+template <int R, typename T, bool LEAN>
+__global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 1) k_rerank(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
     const int64_t *__restrict__ perm, const T *__restrict__ raw, int64_t *__restrict__ out_ids,
@@ -291,19 +293,27 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
                             int64_t nq, int32_t ntop, int32_t k, const int32_t *kq, int32_t batch,
                             int32_t beta, float eps, int64_t *out_ids, float *out_dist,
                             int32_t *stats, int warps, uint32_t *ctr, cudaStream_t st) {
-    // persistent: one warp per SM pulls queries; else one warp per query
-    const dim3 grid(ctr ? (unsigned)std::min<int64_t>(nq, num_sms(0))
+    // persistent: two one-warp CTAs per SM pull queries; else one warp per query
+    const dim3 grid(ctr ? (unsigned)std::min<int64_t>(nq, 2 * num_sms(0))
                         : (unsigned)((nq + warps - 1) / warps));
     if (ctr) FA_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 4, st));
     const int smem = warps * ix.d * 4;
     const T *raw = reinterpret_cast<const T *>(ix.raw);
 #define FA_RR(RR)                                                                                 \
     do {                                                                                          \
-        FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T>,                                       \
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, smem));   \
-        k_rerank<RR, T><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, batch, \
-                                                         beta, eps, ix.perm, raw, out_ids, out_dist, \
-                                                         stats, ctr);                             \
+        if (ctr) {                                                                                \
+            FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T, true>,                             \
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
+            k_rerank<RR, T, true><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, \
+                                                                  batch, beta, eps, ix.perm, raw,   \
+                                                                  out_ids, out_dist, stats, ctr);   \
+        } else {                                                                                  \
+            FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T, false>,                            \
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
+            k_rerank<RR, T, false><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, \
+                                                                   batch, beta, eps, ix.perm, raw,  \
+                                                                   out_ids, out_dist, stats, ctr);  \
+        }                                                                                         \
     } while (0)
     if (k <= 32)
         FA_RR(1);
@@ -317,10 +327,10 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
     FA_CHECK_CUDA(cudaGetLastError());
 }
 
-// warps: queries per CTA. With ctr, a persistent grid of one-warp CTAs (one
-// per SM) pulls queries from the counter: it needs one warp's registers and d
-// floats of shared memory per SM, so it runs beside a scan that fills the SMs,
-// which is how the pipelined search overlaps the two.
+// warps: queries per CTA. With ctr, a persistent grid of one-warp CTAs (two
+// per SM, 64 registers each) pulls queries from the counter: it needs 4096
+// registers and 2 d floats of shared memory per SM, so it runs beside a scan
+// that fills the SMs, which is how the pipelined search overlaps the two.
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
                    float eps, int64_t *out_ids, float *out_dist, int32_t *stats, int warps,
