@@ -182,8 +182,10 @@ void fa_free_index(fa_index *ix);
                                   * re-ranks from host memory is cut into chunks:
                                   * chunk i's re-rank (a second stream of the
                                   * library's, waiting on the host link) runs
-                                  * while chunk i+1 is scanned, as the paper
-                                  * overlaps re-ranking with GPU filtering (§5).
+                                  * while chunk i+1 is scanned, as the paper's
+                                  * concurrent queries (one CPU thread each,
+                                  * §5) overlap one query's re-rank with
+                                  * another's GPU filtering.
                                   * The results are the same either way. */
 
 /* Optional per-call trace, measured with CUDA events on the call's stream
