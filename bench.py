@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--form", default="lowp", choices=["lowp", "plain"],
-                    help="lowp: FP16 LUT + re-rank (precision form); plain: FP32 LUT, no re-rank")
+                    help="lowp: BF16 tensor-core probe and LUT, FP16 LUT (precision form); plain: FP32 "
+                         "everywhere; both re-rank the ADC top-n")
     ap.add_argument("--n", type=int, default=10_000_000)
     ap.add_argument("--nq", type=int, default=10_000)
     ap.add_argument("--nprobe", type=int, default=64)
@@ -84,8 +85,26 @@ def workload(args):
     w = synth.sift_like_10m()
     return dict(name=w.name if args.n == w.n else "ivfpq-u8-%d-d128-nlist16384-M32" % args.n,
                 mix=w.mix, n=args.n, nq=args.nq, nlist=w.nlist, M=w.M, nprobe=args.nprobe, k=w.k,
-                rerank_n=args.rerank_n if args.form == "lowp" else 0, batch=args.batch,
+                rerank_n=args.rerank_n, batch=args.batch,
                 eps=args.eps, beta=args.beta, lut=args.lut)
+
+
+def max_over_ranks(x: float, world: int, device: str) -> float:
+    """The largest x over all ranks: the job takes as long as its slowest
+    replica (x itself on one rank)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_queries(rank: int, nq: int) -> tuple[int, int]:
+    """Query rows of one replica: every rank searches its own batch of nq
+    queries against its own copy of the index (weak scaling, no exchange)."""
+    return rank * nq, nq
 
 
 def dist_env():
@@ -303,7 +322,8 @@ def main():
     # ---- index (synthetic, seeded; the same on every replica) ----
     t0 = time.perf_counter()
     base = wl["mix"].base(wl["n"])
-    queries = wl["mix"].queries(wl["nq"])
+    q0, qn = replica_queries(rank, wl["nq"])
+    queries = wl["mix"].queries(qn, start=q0)
     t_gen = time.perf_counter() - t0
     raw_loc = fa.FA_RAW_DEVICE if args.raw == "device" else fa.FA_RAW_HOST_PINNED
     bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=10, raw_location=raw_loc)
@@ -337,7 +357,7 @@ def main():
     uniq = int(st[:, 1].sum())
     gathered = int(st[:, 0].sum())
     rep_entries = gathered - uniq  # primaries are all distinct; the rest are replica entries
-    ntop = max(wl["rerank_n"], k) if lowp else k
+    ntop = max(wl["rerank_n"], k)
     lut_b = wl["M"] * 256 * (2 if lowp else 0)
     scan_bytes = uniq * wl["M"] + rep_entries * 9 + nq * lut_b + nq * ntop * 8
     reranked = int(st[:, 3].sum())
@@ -349,11 +369,7 @@ def main():
     step_ms, traces = timed_steps(fa, torch, ix, qd, k, wl["nprobe"], sp, args.steps, args.warmup,
                                   flush, oid, odist)
     clk = clocks.stop()
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), world, "cuda")
     value = world * nq / (ms / 1e3)
     scan_ms = statistics.mean(t.scan_ms for t in traces)
     launches = int(traces[0].launches) * args.steps
@@ -372,7 +388,7 @@ def main():
         t0 = time.perf_counter()
         fa.fa_search_ex(ix, qn, k, wl["nprobe"], sp, out_ids=in_, out_dist=dn)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_value = world * nq / (statistics.mean(e2e_ms) / 1e3)
+    e2e_value = world * nq / (max_over_ranks(statistics.mean(e2e_ms), world, "cuda") / 1e3)
 
     recall = recall_of(oracle, base, queries, oid.cpu().numpy(), gt) if gt is not None else None
 
@@ -401,11 +417,11 @@ def main():
             "data": "synthetic",
             "config": {"workload": wl["name"], "n": wl["n"], "nq": nq, "d": d, "nlist": wl["nlist"],
                        "M": wl["M"], "nprobe": wl["nprobe"], "k": k, "form": args.form,
-                       "rerank_n": wl["rerank_n"] if lowp else 0,
+                       "rerank_n": wl["rerank_n"],
                        "rerank": "Algorithm 1, BatchSize %d, eps %g, beta %d" % (
-                           wl["batch"], wl["eps"], wl["beta"]) if lowp else "none",
+                           wl["batch"], wl["eps"], wl["beta"]) if wl["rerank_n"] else "none",
                        "raw_vectors": ("HBM" if args.raw == "device" else "pinned host")
-                       if lowp else "none",
+                       if wl["rerank_n"] else "none",
                        "launch": "autotuned: %d threads/CTA, %d chunk(s) in flight per warp, %s" % (
                            tuned["threads"], tuned["ilp"],
                            "persistent" if (tuned["persistent"] or args.persistent) else "one CTA per query"),

@@ -115,10 +115,10 @@ class Mixture:
     def base(self, n: int) -> np.ndarray:
         return self.rows(0, n, STREAM_BASE)
 
-    def queries(self, nq: int) -> np.ndarray:
-        """Queries drawn like the base, returned as float32 (uint8 values are
-        exact in float32)."""
-        return self.rows(0, nq, STREAM_QUERIES).astype(np.float32)
+    def queries(self, nq: int, start: int = 0) -> np.ndarray:
+        """Queries [start, start + nq) drawn like the base, returned as float32
+        (uint8 values are exact in float32)."""
+        return self.rows(start, start + nq, STREAM_QUERIES).astype(np.float32)
 
 
 # ---------------------------------------------------------------------------
