@@ -641,6 +641,30 @@ def test_pipelined_rerank_equals_serial(fa, u8_repl, lowp):
     assert np.all(pst[:, 2] >= 1)  # every query re-ranked at least one mini-batch
 
 
+def test_pipelined_rerank_under_graph_capture(fa, u8_repl):
+    """The pipelined search (three streams joined by events) captured into a
+    CUDA graph with device buffers replays correctly, also after the query
+    buffer's contents change, and equals the serial order."""
+    import torch
+    s = u8_repl
+    q = synth.Mixture(128, 16, 8.0, kind="u8").queries(4500).astype(np.float32)
+    tc = fa.FA_GEMM_BF16_TC
+    base = dict(rerank_n=48, rerank_batch=16, lut_prec=fa.FA_LUT_F16, lut_gemm=tc, probe_gemm=tc)
+    pg = fa.search_params(flags=fa.FA_GRAPH, **base)
+    ps = fa.search_params(flags=fa.FA_SERIAL, **base)
+    qd = torch.as_tensor(q, device="cuda")
+    oi = torch.empty((q.shape[0], 10), dtype=torch.int64, device="cuda")
+    od = torch.empty((q.shape[0], 10), dtype=torch.float32, device="cuda")
+    for rnd in range(3):
+        if rnd == 2:
+            qd.copy_(torch.flip(qd, [0]))  # new contents, same buffer
+        fa.fa_search_ex(s["ix"], qd, 10, 12, pg, out_ids=oi, out_dist=od)
+        torch.cuda.synchronize()
+        ei, ed = fa.fa_search_ex(s["ix"], qd.cpu().numpy(), 10, 12, ps)
+        assert np.array_equal(oi.cpu().numpy(), ei), rnd
+        assert np.array_equal(od.cpu().numpy().view(np.uint32), ed.view(np.uint32)), rnd
+
+
 def test_rerank_device_raw_equals_pinned(fa, f32_small):
     s = f32_small
     q = s["q"][:30]
