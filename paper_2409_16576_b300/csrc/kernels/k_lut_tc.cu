@@ -9,10 +9,14 @@
 // queries and codebooks are split into bf16 hi + lo pairs and take three MMAs
 // (hi.hi + hi.lo + lo.hi) so the dot products come out near FP32.
 //
+// A CTA takes 128 queries and LSUB subspaces. It converts only the K-blocks
+// those subspaces use, and double-buffers the subspaces' B tiles with bulk
+// copies, so that a tile arrives while the previous subspace's epilogue runs.
 // The epilogue reads each query row's 256 entries back from tensor memory
 // twice: once for the subspace's minimum and maximum, once to store the
 // entries as FP32, or as FP16 / FP8 with that subspace's scale and offset
-// (stored = (LUT - min) / s, s = (max - min) / format max).
+// (stored = (LUT - min) / s, s = (max - min) / format max). FP16 / FP8 rows are
+// staged in shared memory and written back one whole row per warp store.
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -26,7 +30,8 @@ namespace fa {
 
 constexpr int LQ = 128;   // queries per tile
 constexpr int LN = 256;   // centroids per subspace
-constexpr int LSUB = 8;   // subspaces per CTA
+constexpr int LSUB = 4;   // subspaces per CTA
+constexpr int STAGE_PAD = 16;  // bytes after each staged row: rows start in different banks
 constexpr uint32_t LUT_WAIT_LIMIT = 1u << 22;
 
 struct LutTcArgs {
@@ -41,30 +46,46 @@ struct LutTcArgs {
     uint32_t *err;
 };
 
+__host__ __device__ inline int lut_elem(int prec) {
+    return prec == FA_LUT_F16 ? 2 : (prec == FA_LUT_FP8 ? 1 : 4);
+}
+
 __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int Kp = a.Kp;
-    __nv_bfloat16 *Ahi = reinterpret_cast<__nv_bfloat16 *>(sm);
-    __nv_bfloat16 *Alo = Ahi + LQ * Kp;
-    __nv_bfloat16 *Bt = Alo + LQ * Kp;  // hi then lo, 2 * LN * 16
-    __shared__ uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar, full[2];
     __shared__ uint32_t tmem_base;
-    const int tid = threadIdx.x, warp = tid >> 5;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * LSUB, m1 = min(a.M, m0 + LSUB);
+    // only the 16-wide K-blocks this CTA's subspaces use
+    const int kb0 = (m0 * a.dsub) / 16, kb1 = (m1 * a.dsub + 15) / 16;
+    const int Ka = (kb1 - kb0) * 16;
+    const uint32_t btile = 2u * LN * 16 * 2;  // hi + lo of one subspace
+    const bool staged = a.prec != FA_LUT_F32;
+    const int elem = lut_elem(a.prec), srow = LN * elem + STAGE_PAD;
+    __nv_bfloat16 *Ahi = reinterpret_cast<__nv_bfloat16 *>(sm);
+    __nv_bfloat16 *Alo = Ahi + LQ * Ka;
+    unsigned char *Bb = sm + (size_t)2 * LQ * Ka * 2;  // two subspace tiles
+    unsigned char *stage = Bb + 2 * btile;             // [LQ][srow] quantised rows
     const int64_t r0 = (int64_t)blockIdx.x * LQ;
     const int64_t row = r0 + tid;
     const bool row_ok = row < a.nq;
 
-    for (int e = tid; e < LQ * Kp; e += LQ) {
-        const int r = e / Kp, k = e - r * Kp;
-        const float x = (r0 + r < a.nq && k < a.d) ? a.q[(r0 + r) * a.d + k] : 0.f;
+    for (int e = tid; e < LQ * Ka; e += LQ) {
+        const int r = e / Ka, k = e - r * Ka, gk = kb0 * 16 + k;
+        const float x = (r0 + r < a.nq && gk < a.d) ? a.q[(r0 + r) * a.d + gk] : 0.f;
         __nv_bfloat16 h, l;
         tc::split_bf16(x, h, l);
-        const uint32_t o = tc::core_offset(r, k, Kp) >> 1;
+        const uint32_t o = tc::core_offset(r, k, Ka) >> 1;
         Ahi[o] = h;
         Alo[o] = l;
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, LN);
-    if (tid == 0) tc::mbar_init(&mbar, 1);
+    if (tid == 0) {
+        tc::mbar_init(&mbar, 1);
+        tc::mbar_init(&full[0], 1);
+        tc::mbar_init(&full[1], 1);
+    }
     tc::fence_proxy_async();
     tc::fence_before();
     __syncthreads();
@@ -72,32 +93,46 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
     const uint32_t tbase = tmem_base;
     const uint32_t lane_addr = tbase + ((uint32_t)(warp * 32) << 16);
     const uint32_t idesc = tc::idesc_bf16_f32(LQ, LN);
-    const uint32_t sbo_a = (uint32_t)(Kp / 8) * 128u, sbo_b = 256u;
+    const uint32_t sbo_a = (uint32_t)(Ka / 8) * 128u, sbo_b = 256u;
     uint32_t parity = 0;
     bool failed = false;
-    const int m0 = blockIdx.y * LSUB, m1 = min(a.M, m0 + LSUB);
+    int loaded = -1;  // last subspace whose tile copy thread 0 issued
     const float fmax = a.prec == FA_LUT_F16 ? 65504.f : 448.f;
+    if (tid == 0 && m0 < m1) {
+        tc::mbar_expect_tx(&full[0], btile);
+        tc::bulk_g2s(Bb, a.btiles + (size_t)m0 * 2 * LN * 16, btile, &full[0]);
+        loaded = m0;
+    }
 
     for (int m = m0; m < m1; ++m) {
-        const uint4 *src = reinterpret_cast<const uint4 *>(a.btiles + (size_t)m * 2 * LN * 16);
-        uint4 *dst = reinterpret_cast<uint4 *>(Bt);
-        for (int i = tid; i < 2 * LN * 16 * 2 / 16; i += LQ) dst[i] = __ldg(src + i);
-        tc::fence_proxy_async();
-        __syncthreads();
+        const int i = m - m0, b = i & 1;
         if (tid == 0) {
-            tc::fence_after();
-            const uint32_t off = 256u * (uint32_t)((m * a.dsub) / 16);
-            const uint64_t dah = tc::smem_desc(tc::smem_u32(Ahi) + off, 128, sbo_a);
-            const uint64_t dal = tc::smem_desc(tc::smem_u32(Alo) + off, 128, sbo_a);
-            const uint32_t bh = tc::smem_u32(Bt), bl = bh + LN * 16 * 2;
-            const uint64_t dbh = tc::smem_desc(bh, 128, sbo_b);
-            const uint64_t dbl = tc::smem_desc(bl, 128, sbo_b);
-            tc::mma_bf16(tbase, dah, dbh, idesc, 0u);
-            tc::mma_bf16(tbase, dah, dbl, idesc, 1u);
-            tc::mma_bf16(tbase, dal, dbh, idesc, 1u);
-            tc::mma_commit(&mbar);
+            bool ok0 = tc::mbar_wait(&full[b], (i >> 1) & 1, LUT_WAIT_LIMIT);
+            if (ok0) {
+                tc::fence_after();
+                const uint32_t off = 256u * (uint32_t)((m * a.dsub) / 16 - kb0);
+                const uint64_t dah = tc::smem_desc(tc::smem_u32(Ahi) + off, 128, sbo_a);
+                const uint64_t dal = tc::smem_desc(tc::smem_u32(Alo) + off, 128, sbo_a);
+                const uint32_t bh = tc::smem_u32(Bb + (size_t)b * btile), bl = bh + LN * 16 * 2;
+                const uint64_t dbh = tc::smem_desc(bh, 128, sbo_b);
+                const uint64_t dbl = tc::smem_desc(bl, 128, sbo_b);
+                tc::mma_bf16(tbase, dah, dbh, idesc, 0u);
+                tc::mma_bf16(tbase, dah, dbl, idesc, 1u);
+                tc::mma_bf16(tbase, dal, dbh, idesc, 1u);
+                tc::mma_commit(&mbar);
+                // the other tile buffer was read by subspace m - 1, whose MMAs are done
+                if (m + 1 < m1) {
+                    tc::mbar_expect_tx(&full[b ^ 1], btile);
+                    tc::bulk_g2s(Bb + (size_t)(b ^ 1) * btile, a.btiles + (size_t)(m + 1) * 2 * LN * 16,
+                                 btile, &full[b ^ 1]);
+                    loaded = m + 1;
+                }
+            }
+            s_ok = ok0 ? 1 : 0;
         }
-        const bool ok = tc::mbar_wait(&mbar, parity, LUT_WAIT_LIMIT);
+        __syncthreads();
+        bool ok = s_ok != 0;
+        ok = ok && tc::mbar_wait(&mbar, parity, LUT_WAIT_LIMIT);
         if (__syncthreads_or(!ok)) {
             failed = true;
             break;
@@ -113,14 +148,14 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
             }
         const float *cn = a.cbnorm + m * 256;
         float lo = INFINITY, hi = -INFINITY;
-        if (a.prec != FA_LUT_F32) {
+        if (staged) {
 #pragma unroll 1
             for (int c0 = 0; c0 < LN; c0 += 32) {
                 float v[32];
                 tc::tmem_ld32(lane_addr + c0, v);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const float e = qn - 2.f * v[i] + __ldg(cn + c0 + i);
+                for (int j = 0; j < 32; ++j) {
+                    const float e = qn - 2.f * v[j] + __ldg(cn + c0 + j);
                     lo = fminf(lo, e);
                     hi = fmaxf(hi, e);
                 }
@@ -130,62 +165,84 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
         if (!(s > 0.f)) s = 1.f;
         const float inv = 1.f / s;
         const int64_t base = (row * a.M + m) * 256;
+        unsigned char *srw = stage + (size_t)tid * srow;
 #pragma unroll 1
         for (int c0 = 0; c0 < LN; c0 += 32) {
             float v[32];
             tc::tmem_ld32(lane_addr + c0, v);
-            if (!row_ok) continue;
             if (a.prec == FA_LUT_F32) {
+                if (!row_ok) continue;
                 float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.lut) + base + c0);
 #pragma unroll
-                for (int i = 0; i < 32; i += 4)
-                    o[i / 4] = make_float4(qn - 2.f * v[i] + __ldg(cn + c0 + i),
-                                           qn - 2.f * v[i + 1] + __ldg(cn + c0 + i + 1),
-                                           qn - 2.f * v[i + 2] + __ldg(cn + c0 + i + 2),
-                                           qn - 2.f * v[i + 3] + __ldg(cn + c0 + i + 3));
+                for (int j = 0; j < 32; j += 4)
+                    o[j / 4] = make_float4(qn - 2.f * v[j] + __ldg(cn + c0 + j),
+                                           qn - 2.f * v[j + 1] + __ldg(cn + c0 + j + 1),
+                                           qn - 2.f * v[j + 2] + __ldg(cn + c0 + j + 2),
+                                           qn - 2.f * v[j + 3] + __ldg(cn + c0 + j + 3));
             } else if (a.prec == FA_LUT_F16) {
                 uint32_t w[16];
 #pragma unroll
-                for (int i = 0; i < 32; i += 2) {
-                    const float e0 = fminf((qn - 2.f * v[i] + __ldg(cn + c0 + i) - lo) * inv, fmax);
+                for (int j = 0; j < 32; j += 2) {
+                    const float e0 = fminf((qn - 2.f * v[j] + __ldg(cn + c0 + j) - lo) * inv, fmax);
                     const float e1 =
-                        fminf((qn - 2.f * v[i + 1] + __ldg(cn + c0 + i + 1) - lo) * inv, fmax);
+                        fminf((qn - 2.f * v[j + 1] + __ldg(cn + c0 + j + 1) - lo) * inv, fmax);
                     const __half2 h = __floats2half2_rn(e0, e1);
-                    w[i / 2] = *reinterpret_cast<const uint32_t *>(&h);
+                    w[j / 2] = *reinterpret_cast<const uint32_t *>(&h);
                 }
-                uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<__half *>(a.lut) + base + c0);
+                uint4 *o = reinterpret_cast<uint4 *>(srw + c0 * 2);
 #pragma unroll
-                for (int i = 0; i < 4; ++i)
-                    o[i] = make_uint4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+                for (int j = 0; j < 4; ++j)
+                    o[j] = make_uint4(w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
             } else {
                 uint32_t w[8];
 #pragma unroll
-                for (int i = 0; i < 32; i += 4) {
+                for (int j = 0; j < 32; j += 4) {
                     uint32_t pk = 0;
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
+                    for (int t = 0; t < 4; ++t) {
                         const float e =
-                            fminf((qn - 2.f * v[i + j] + __ldg(cn + c0 + i + j) - lo) * inv, fmax);
+                            fminf((qn - 2.f * v[j + t] + __ldg(cn + c0 + j + t) - lo) * inv, fmax);
                         const __nv_fp8_e4m3 f(e);
-                        pk |= (uint32_t)f.__x << (8 * j);
+                        pk |= (uint32_t)f.__x << (8 * t);
                     }
-                    w[i / 4] = pk;
+                    w[j / 4] = pk;
                 }
-                uint4 *o = reinterpret_cast<uint4 *>(reinterpret_cast<uint8_t *>(a.lut) + base + c0);
+                uint4 *o = reinterpret_cast<uint4 *>(srw + c0);
                 o[0] = make_uint4(w[0], w[1], w[2], w[3]);
                 o[1] = make_uint4(w[4], w[5], w[6], w[7]);
             }
         }
         if (row_ok) {
-            a.scale[row * 2 * a.M + 2 * m] = a.prec == FA_LUT_F32 ? 1.f : s;
-            a.scale[row * 2 * a.M + 2 * m + 1] = a.prec == FA_LUT_F32 ? 0.f : lo;
+            a.scale[row * 2 * a.M + 2 * m] = staged ? s : 1.f;
+            a.scale[row * 2 * a.M + 2 * m + 1] = staged ? lo : 0.f;
         }
         tc::fence_before();
-        __syncthreads();
+        __syncthreads();  // the staged tile is complete and the accumulator free
+        if (staged) {
+            // one query row per warp store: a row of the subspace is LN * elem
+            // contiguous bytes in HBM
+            for (int r = warp; r < LQ; r += LQ / 32) {
+                if (r0 + r >= a.nq) break;
+                unsigned char *dst = reinterpret_cast<unsigned char *>(a.lut) + ((r0 + r) * a.M + m) * 256 * elem;
+                const unsigned char *src = stage + (size_t)r * srow;
+                if (elem == 2)
+                    reinterpret_cast<uint4 *>(dst)[lane] = reinterpret_cast<const uint4 *>(src)[lane];
+                else
+                    reinterpret_cast<uint2 *>(dst)[lane] = reinterpret_cast<const uint2 *>(src)[lane];
+            }
+            __syncthreads();  // the stage takes the next subspace
+        }
     }
     if (failed) {
-        if (tid == 0 && a.err) atomicOr(a.err, DEV_ERR_TIMEOUT);
-        tc::mbar_wait(&mbar, parity, LUT_WAIT_LIMIT);
+        if (tid == 0) {
+            if (a.err) atomicOr(a.err, DEV_ERR_TIMEOUT);
+            // copies and MMAs in flight finish before shared and tensor memory go
+            tc::mbar_wait(&mbar, parity, LUT_WAIT_LIMIT);
+            if (loaded >= m0) {
+                const int li = loaded - m0;
+                tc::mbar_wait(&full[li & 1], (li >> 1) & 1, LUT_WAIT_LIMIT);
+            }
+        }
     }
     tc::fence_before();
     __syncthreads();
@@ -236,8 +293,16 @@ void launch_lut_tc(const DeviceIndex &ix, const float *q, int64_t nq, int prec, 
     a.lut = lut;
     a.scale = lut_scale;
     a.err = err;
-    // at least 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM
-    const int smem = std::max((2 * LQ * a.Kp + 2 * LN * 16) * 2, 80 * 1024);
+    // widest K-range of one CTA's subspaces (16-wide blocks), two tile buffers,
+    // the staged rows; at least 80 KB so that at most two CTAs (2 x 256 TMEM
+    // columns) share an SM
+    int ka_max = 16;
+    for (int m0 = 0; m0 < ix.M; m0 += LSUB) {
+        const int m1 = std::min(ix.M, m0 + LSUB);
+        ka_max = std::max(ka_max, ((m1 * ix.dsub + 15) / 16 - (m0 * ix.dsub) / 16) * 16);
+    }
+    const int stage = prec == FA_LUT_F32 ? 0 : LQ * (LN * lut_elem(prec) + STAGE_PAD);
+    const int smem = std::max(2 * LQ * ka_max * 2 + 2 * 2 * LN * 16 * 2 + stage, 80 * 1024);
     FA_CHECK_CUDA(cudaFuncSetAttribute(k_lut_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const dim3 grid((unsigned)((nq + LQ - 1) / LQ), (unsigned)((ix.M + LSUB - 1) / LSUB));
     k_lut_tc<<<grid, LQ, smem, st>>>(a);
