@@ -761,7 +761,7 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
         case 8: launch_scan_m<8, 64>(a, l, st); break;
         case 16: launch_scan_m<16, 64>(a, l, st); break;
         case 32: launch_scan_m<32, 64>(a, l, st); break;
-        case 48: launch_scan_m<48, 80>(a, l, st); break;
+        case 48: launch_scan_m<48, 96>(a, l, st); break;
         case 64: launch_scan_m<64, 128>(a, l, st); break;
         default: FA_REQUIRE(false, FA_ERR_ARG, "M must be one of 8, 16, 32, 48, 64");
     }
