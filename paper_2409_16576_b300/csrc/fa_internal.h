@@ -109,6 +109,7 @@ struct Workspace {
     cudaStream_t stream3 = nullptr;  // second scan stream of the pipelined search
     cudaEvent_t fork[8] = {};        // chunk i scanned
     cudaEvent_t lut_done = nullptr, join = nullptr, join3 = nullptr;
+    cudaEvent_t marks[5] = {};       // stage boundaries of every call (read by fa_search_trace)
     bool pending = false;
     cudaGraphExec_t gexec = nullptr;  // last captured search (FA_GRAPH)
     GraphKey gkey{};
