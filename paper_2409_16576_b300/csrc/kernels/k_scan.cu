@@ -437,7 +437,6 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
         const uint32_t total = S.pref[2 * np];
         const uint32_t cend = total < wk.climit ? total : wk.climit;
         uint32_t kept = 0;
-        float thr_f = INFINITY;  // distance of the threshold as last read (a stale one is looser)
         SegCursor sg;
         uint32_t vc[ILP];
         bool okc[ILP];
@@ -468,13 +467,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
 #pragma unroll
             for (int j = 0; j < ILP; ++j) {
                 kept += okc[j] ? 1u : 0u;
-                // most chunks hold no key below the threshold: test the distances
-                // first, and build keys and push (an exact test) only otherwise
-                if (__any_sync(FULL, okc[j] && dist[j] <= thr_f)) {
-                    tk.push(make_key(dist[j], vc[j]), okc[j]);
-                    const uint64_t t = umin64(tk.thr, *reinterpret_cast<volatile unsigned long long *>(tk.sthr));
-                    thr_f = t == KEY_INF ? INFINITY : o2f((uint32_t)(t >> 32));
-                }
+                tk.push(make_key(dist[j], vc[j]), okc[j]);
                 vc[j] = vn[j];
                 okc[j] = okn[j];
 #pragma unroll
