@@ -330,6 +330,18 @@ fa_status fa_debug_candidates(fa_index *ix, const float *query, int32_t nprobe,
 fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params *sp,
                        float *out_lut);
 
+/* Failure injection on the host (no counterpart in the paper): the n-th next
+ * device allocation of the library (index upload, workspaces, server slots)
+ * fails as if the device were out of memory; the call returns FA_ERR_OOM and
+ * leaves the index usable. n = 0 turns it off. */
+fa_status fa_debug_fail_alloc(int32_t n);
+
+/* Runs one device wait that must run out: a CTA waits, with the library's
+ * bounded mbarrier wait, for a phase nothing completes and polls a flag
+ * nothing sets, `polls` tries each. Returns FA_ERR_TIMEOUT from the device
+ * status word; the CUDA context stays usable. FA_ERR_NODEV without a GPU. */
+fa_status fa_debug_timeout(uint32_t polls);
+
 /* ------------------------------------------------------------------------- */
 /* Coarse probe without allocation                                           */
 /* ------------------------------------------------------------------------- */

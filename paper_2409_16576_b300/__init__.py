@@ -104,6 +104,8 @@ _sig("fa_autotune", i32, P, P, i64, i32, i32, i32, P, P)
 _sig("fa_debug_probes", i32, P, P, i64, i32, P, P)
 _sig("fa_debug_candidates", i32, P, P, i32, P, P, i64, P)
 _sig("fa_debug_lut", i32, P, P, P, P)
+_sig("fa_debug_fail_alloc", i32, i32)
+_sig("fa_debug_timeout", i32, C.c_uint32)
 _sig("fa_coarse_probe_noalloc", i32, P, i64, i32, P, i32, i32, P, P)
 _sig("fa_server_params_init", None, P)
 _sig("fa_server_create", i32, P, P, P, P)
@@ -120,7 +122,8 @@ EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_build_index_lists", "fa
            "fa_index_get_parts",
            "fa_index_info_get", "fa_save_index", "fa_load_index", "fa_free_index",
            "fa_search_params_init", "fa_search", "fa_search_ex", "fa_autotune", "fa_debug_probes",
-           "fa_debug_candidates", "fa_debug_lut", "fa_coarse_probe_noalloc", "fa_server_params_init",
+           "fa_debug_candidates", "fa_debug_lut", "fa_debug_fail_alloc", "fa_debug_timeout",
+           "fa_coarse_probe_noalloc", "fa_server_params_init",
            "fa_server_create", "fa_server_submit", "fa_server_poll", "fa_server_stats",
            "fa_server_destroy", "fa_last_error",
            "fa_status_str", "fa_version")
@@ -403,6 +406,16 @@ def fa_coarse_probe_noalloc(queries, centroids, nprobe: int, out=None, stream=No
     _check(_lib.fa_coarse_probe_noalloc(_ptr(queries), nq, d, _ptr(centroids), nl, nprobe,
                                         _ptr(out), stream))
     return out
+
+
+def fa_debug_fail_alloc(n: int) -> None:
+    """The n-th next device allocation of the library fails (0 turns it off)."""
+    _check(_lib.fa_debug_fail_alloc(n))
+
+
+def fa_debug_timeout(polls: int) -> None:
+    """Runs a device wait that must run out; raises FaError(FA_ERR_TIMEOUT)."""
+    _check(_lib.fa_debug_timeout(polls))
 
 
 class Server:

@@ -69,11 +69,22 @@ static fa_status guarded(fa_index *ix, F &&f) {
     }
 }
 
+// Host-side fault injection (fa_debug_fail_alloc): the n-th next device
+// allocation of the library fails as if the device were out of memory.
+static std::atomic<int32_t> g_fail_alloc{0};
+
+bool alloc_fault() {
+    int32_t c = g_fail_alloc.load();
+    while (c > 0)
+        if (g_fail_alloc.compare_exchange_weak(c, c - 1)) return c == 1;
+    return false;
+}
+
 template <class T>
 static T *dev_upload(const T *src, size_t count, int64_t &bytes) {
     T *p = nullptr;
     const size_t b = sizeof(T) * (count ? count : 1);
-    if (cudaMalloc(&p, b) != cudaSuccess) {
+    if (alloc_fault() || cudaMalloc(&p, b) != cudaSuccess) {
         cudaGetLastError();
         throw Error{FA_ERR_OOM, "device allocation of " + std::to_string(b) + " bytes failed"};
     }
@@ -277,7 +288,7 @@ static void ws_free_buffers(Workspace *w) {
 
 template <class T>
 static void dalloc(T *&p, size_t count) {
-    if (cudaMalloc(&p, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
+    if (alloc_fault() || cudaMalloc(&p, sizeof(T) * (count ? count : 1)) != cudaSuccess) {
         cudaGetLastError();
         p = nullptr;
         throw Error{FA_ERR_OOM, "workspace allocation failed"};
@@ -1289,6 +1300,39 @@ fa_status fa_debug_candidates(fa_index *ix, const float *query, int32_t nprobe,
         FA_REQUIRE((int64_t)ids.size() <= cap, FA_ERR_OVERFLOW, "output capacity too small");
         std::copy(ids.begin(), ids.end(), out_ids);
     });
+}
+
+fa_status fa_debug_fail_alloc(int32_t n) {
+    if (n < 0) {
+        set_error("n must be >= 0");
+        return FA_ERR_ARG;
+    }
+    g_fail_alloc.store(n);
+    return FA_OK;
+}
+
+fa_status fa_debug_timeout(uint32_t polls) {
+    uint32_t *dev = nullptr;  // [0] status word, [1] a flag nothing sets
+    try {
+        int n = 0;
+        if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+            cudaGetLastError();
+            throw Error{FA_ERR_NODEV, "no CUDA device"};
+        }
+        FA_CHECK_CUDA(cudaMalloc(&dev, 8));
+        FA_CHECK_CUDA(cudaMemset(dev, 0, 8));
+        launch_wait_nothing(polls, dev + 1, dev, nullptr);
+        uint32_t st = 0;
+        FA_CHECK_CUDA(cudaMemcpy(&st, dev, 4, cudaMemcpyDeviceToHost));
+        cudaFree(dev);
+        dev = nullptr;
+        if (st & DEV_ERR_TIMEOUT) throw Error{FA_ERR_TIMEOUT, "a device-side wait ran out"};
+        return FA_OK;
+    } catch (const Error &e) {
+        if (dev) cudaFree(dev);
+        set_error("%s", e.msg.c_str());
+        return e.st;
+    }
 }
 
 fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params *spp,

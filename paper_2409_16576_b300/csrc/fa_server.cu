@@ -94,7 +94,7 @@ static void slot_free(Slot &s) {
 
 template <class T>
 static void srv_dalloc(T *&p, size_t n, int64_t &bytes) {
-    if (cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) {
+    if (alloc_fault() || cudaMalloc(&p, sizeof(T) * (n ? n : 1)) != cudaSuccess) {
         cudaGetLastError();
         throw Error{FA_ERR_OOM, "server slot allocation failed"};
     }

@@ -120,3 +120,19 @@ def test_load_rejects_missing_and_foreign_files(tmp_path):
     with pytest.raises(fa.FaError) as e:
         fa.fa_load_index(str(p))
     assert e.value.status == fa.FA_ERR_IO
+
+
+def test_failure_hooks_without_a_device():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    fa.fa_debug_fail_alloc(0)
+    with pytest.raises(fa.FaError) as e:
+        fa.fa_debug_fail_alloc(-1)
+    assert e.value.status == fa.FA_ERR_ARG
+    with pytest.raises(fa.FaError) as e:
+        fa.fa_debug_timeout(16)
+    assert e.value.status == fa.FA_ERR_NODEV
