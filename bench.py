@@ -174,10 +174,11 @@ def src_hash(paths):
     return h.hexdigest()[:16]
 
 
-def profile_traffic(kernel_hash):
+def profile_traffic(kernel_hash, workload):
     """DRAM bytes per scan launch recorded by an ncu capture of this exact
-    kernel source (profiles/*.md carries 'traffic_bytes_per_launch: N' and
-    'kernel_src_hash: H'), or None."""
+    kernel source on this exact workload (profiles/*.md carries
+    'traffic_bytes_per_launch: N', 'kernel_src_hash: H' and
+    'traffic_workload: W'), or None."""
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
@@ -187,7 +188,8 @@ def profile_traffic(kernel_hash):
         txt = open(os.path.join(d, fn)).read()
         mh = re.search(r"kernel_src_hash:\s*([0-9a-f]+)", txt)
         mt = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
-        if mh and mt and mh.group(1) == kernel_hash:
+        mw = re.search(r"traffic_workload:\s*(\S+)", txt)
+        if mh and mt and mw and mh.group(1) == kernel_hash and mw.group(1) == workload:
             return float(mt.group(1))
     return None
 
@@ -396,7 +398,7 @@ def main():
     peak, peak_src = measured_peaks()
     achieved = scan_bytes / (scan_ms / 1e3) / 1e9
     khash = src_hash(SCAN_SOURCES)
-    traffic = profile_traffic(khash)
+    traffic = profile_traffic(khash, "%s-nq%d-nprobe%d" % (wl["name"], nq, wl["nprobe"]))
 
     # ---- CPU baseline: the oracle as it stands on a bounded sample ----
     cpu = None
