@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--recall", type=int, default=1000, help="queries in the recall subsample (0 = off)")
     ap.add_argument("--sweep", action="store_true", help="recall/QPS grid instead of one bench line")
+    ap.add_argument("--points", default="",
+                    help="sweep points form:nprobe:n:batch:eps:beta, comma-separated (default grid if empty)")
+    ap.add_argument("--kmeans-iters", type=int, default=25, help="k-means iterations of the index build")
     ap.add_argument("--serial", action="store_true",
                     help="re-rank after the whole scan (FA_SERIAL) instead of the pipelined chunks")
     ap.add_argument("--workload", default="sift10m", choices=["sift10m", "zipf"],
@@ -328,7 +331,8 @@ def main():
     queries = wl["mix"].queries(qn, start=q0)
     t_gen = time.perf_counter() - t0
     raw_loc = fa.FA_RAW_DEVICE if args.raw == "device" else fa.FA_RAW_HOST_PINNED
-    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=10, raw_location=raw_loc)
+    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=args.kmeans_iters,
+                         raw_location=raw_loc)
     t0 = time.perf_counter()
     ix = fa.fa_build_index(base, bp)
     t_build = time.perf_counter() - t0
@@ -476,7 +480,7 @@ def bench_zipf(args):
     queries = z.queries(nq)
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    ix = fa.fa_build_index_lists(base, cent, prim, fa.build_params(M=M, kmeans_iters=10))
+    ix = fa.fa_build_index_lists(base, cent, prim, fa.build_params(M=M, kmeans_iters=args.kmeans_iters))
     t_build = time.perf_counter() - t0
     npq = synth.uniform_ints(16, 128, nq, tag=3)
     npq_d = torch.as_tensor(npq, device="cuda")
@@ -573,7 +577,7 @@ def bench_serve(args):
     z = synth.ZipfLists(args.zipf_n)
     t0 = time.perf_counter()
     base = z.base()
-    ix = fa.fa_build_index_lists(base, z.centroids(), z.primary(), fa.build_params(M=48, kmeans_iters=10))
+    ix = fa.fa_build_index_lists(base, z.centroids(), z.primary(), fa.build_params(M=48, kmeans_iters=args.kmeans_iters))
     del base
     t_build = time.perf_counter() - t0
     pool = z.queries(20000)
@@ -645,13 +649,19 @@ def sweep(args, wl, fa, torch, oracle, ix, base, queries, qd, flush, gt, t_build
     for npb in (8, 16, 32, 64, 128, 256, 512):
         cov = np.mean([np.isin(primary[gt[0][i]], probes[i, :npb]).mean() for i in range(ns)])
         print(json.dumps({"coverage_nprobe": npb, "coverage": float(cov)}), flush=True)
-    grid = [("lowp", 64, 100, 32, 0.0, 2), ("plain", 64, 100, 32, 0.0, 2)]  # the configured point
-    for form in ("lowp", "plain"):
-        for npb in (64, 128, 256, 512):
-            for n in (1024, 4096):
-                grid.append((form, npb, n, 32, -1.0, 1))
-    for npb in (128, 256):
-        grid.append(("lowp", npb, 4096, 256, 0.0, 2))
+    if args.points:
+        grid = []
+        for pt in args.points.split(","):
+            f, npb, n, batch, eps, beta = pt.split(":")
+            grid.append((f, int(npb), int(n), int(batch), float(eps), int(beta)))
+    else:
+        grid = [("lowp", 64, 100, 32, 0.0, 2), ("plain", 64, 100, 32, 0.0, 2)]  # the configured point
+        for form in ("lowp", "plain"):
+            for npb in (64, 128, 256, 512):
+                for n in (1024, 4096, 16384):
+                    grid.append((form, npb, n, 32, -1.0, 1))
+        for npb in (128, 256):
+            grid.append(("lowp", npb, 16384, 32, 0.0, 2))
     for form, npb, n, batch, eps, beta in grid:
         w = dict(wl, rerank_n=n, batch=batch, eps=eps, beta=beta)
         sp = search_params(fa, form, w)
@@ -677,7 +687,7 @@ def reference_arm(args, wl, rank, world):
     torch.cuda.set_device(0)
     base = wl["mix"].base(wl["n"])
     queries = wl["mix"].queries(wl["nq"])
-    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=10,
+    bp = fa.build_params(nlist=wl["nlist"], M=wl["M"], kmeans_iters=args.kmeans_iters,
                          raw_location=fa.FA_RAW_HOST_PINNED)
     ix = fa.fa_build_index(base, bp)
     parts = ix.parts()

@@ -199,7 +199,9 @@ typedef struct fa_search_params {
     int32_t lut_prec;     /* fa_lut_prec */
     int32_t lut_gemm;     /* fa_gemm for the LUT */
     int32_t probe_gemm;   /* fa_gemm for the coarse probe */
-    int32_t rerank_n;     /* 0: ADC top-k. >0: re-rank the ADC top-rerank_n (<= 4096) */
+    int32_t rerank_n;     /* 0: ADC top-k. >0: re-rank the ADC top-rerank_n (<= 16384;
+                           * above 4096 the scan needs the top-n beside the LUT in
+                           * shared memory, so large M may return FA_ERR_ARG) */
     int32_t rerank_batch; /* Algorithm 1 BatchSize, 1..4096 */
     int32_t rerank_beta;  /* Algorithm 1 beta (>= 1) */
     float rerank_eps;     /* Algorithm 1 epsilon (< 0: never stop early) */
@@ -220,8 +222,9 @@ void fa_search_params_init(fa_search_params *sp);
 
 /* Top-k search for nq host queries[nq][d] (float32) with the plain FP32 form.
  * out_ids [nq][k] and out_dist [nq][k] are host buffers. nprobe is clamped to
- * [1, nlist]. nq == 0 returns FA_OK. d must equal the index's d, 1 <= k <= 4096
- * (k <= 128 when re-ranking). */
+ * [1, nlist]. nq == 0 returns FA_OK. d must equal the index's d, 1 <= k <= 16384
+ * (k <= 128 when re-ranking; k above 4096 needs the top-k beside the LUT in
+ * shared memory, so large M may return FA_ERR_ARG). */
 fa_status fa_search(fa_index *ix, const float *queries, int64_t nq, int32_t d, int32_t k,
                     int32_t nprobe, int64_t *out_ids, float *out_dist);
 

@@ -445,7 +445,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     else
         fa_search_params_init(&sp);
     FA_REQUIRE(d == ix->d, FA_ERR_ARG, "query dimension differs from the index");
-    FA_REQUIRE(k >= 1 && k <= 4096, FA_ERR_ARG, "k must be in 1..4096");
+    FA_REQUIRE(k >= 1 && k <= 16384, FA_ERR_ARG, "k must be in 1..16384");
     FA_REQUIRE(nq >= 0, FA_ERR_ARG, "nq < 0");
     if (nq == 0) return;
     FA_REQUIRE(queries && out_ids && out_dist, FA_ERR_ARG, "null buffer");
@@ -460,7 +460,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         FA_REQUIRE(sp.rerank_batch >= 1 && sp.rerank_batch <= 4096, FA_ERR_ARG, "bad rerank_batch");
         FA_REQUIRE(sp.rerank_beta >= 1, FA_ERR_ARG, "rerank_beta < 1");
         ntop = std::max(sp.rerank_n, k);
-        FA_REQUIRE(ntop <= 4096, FA_ERR_ARG, "rerank_n above 4096");
+        FA_REQUIRE(ntop <= 16384, FA_ERR_ARG, "rerank_n above 16384");
     }
     const bool qdev = sp.flags & FA_QUERIES_ON_DEVICE, odev = sp.flags & FA_OUTPUTS_ON_DEVICE;
     const bool global_lut = sp.lut_prec != FA_LUT_F32 || sp.lut_gemm == FA_GEMM_BF16_TC;

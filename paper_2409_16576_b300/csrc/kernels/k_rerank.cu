@@ -101,7 +101,7 @@ void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, i
                    cudaStream_t st) {
     if (nq == 0) return;
     if (k > 256) {
-        FA_REQUIRE(k <= 4096, FA_ERR_ARG, "k above 4096");
+        FA_REQUIRE(k <= 16384, FA_ERR_ARG, "k above 16384");
         int KP = 1;
         while (KP < k) KP <<= 1;
         FA_CHECK_CUDA(cudaFuncSetAttribute(k_finish_big, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -33,11 +33,11 @@ namespace fa {
 
 constexpr int SCAN_THREADS = 256;  // warp-top-n variant (n <= 256)
 constexpr int SCAN_WARPS = SCAN_THREADS / 32;
-constexpr int BIG_THREADS = 512;   // CTA-top-n variant (256 < n <= 4096)
+constexpr int BIG_THREADS = 512;   // CTA-top-n variant (256 < n <= 16384)
 constexpr int BIG_WARPS = BIG_THREADS / 32;
 constexpr int MAX_PROBE = 512;
 constexpr int MAX_D = 1024;
-constexpr int MAX_TOPN = 4096;
+constexpr int MAX_TOPN = 16384;
 
 struct ScanArgs {
     // index
@@ -216,28 +216,42 @@ __device__ __forceinline__ void load_codes(const uint8_t *codes, uint32_t v, boo
     }
 }
 
-// ADC distance (Eq. 1) of one rotated code row (rotation r = v mod 32).
+// acc += (x0, x1) as two FP32 additions in one packed instruction; each lane
+// of the pair is rounded to nearest, as two separate adds would be.
+__device__ __forceinline__ void add_f32x2(unsigned long long &acc, float x0, float x1) {
+    unsigned long long x;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(x));
+}
+
+// ADC distance (Eq. 1) of one rotated code row (rotation r = v mod 32): even
+// steps sum into acc0, odd steps into acc1 (M is even).
 template <int M, int W>
 __device__ __forceinline__ float adc_words(const uint32_t (&w)[M / 4], uint32_t v, const float *lut) {
+    static_assert(M % 2 == 0, "M must be even");
     const uint32_t r4 = (v & 31u) * 4u;
     const char *lb = reinterpret_cast<const char *>(lut);
-    float acc0 = 0.f, acc1 = 0.f;
+    unsigned long long acc = 0ull;  // (acc0, acc1) = (+0, +0)
 #pragma unroll
-    for (int s = 0; s < M; ++s) {
-        uint32_t off;
-        if (W == 64) {
-            // (code << 8) | r4 in one byte permute: byte0 <- r4, byte1 <- code
-            off = __byte_perm(w[s >> 2], r4, 0x5504u | ((uint32_t)(s & 3) << 4));
-        } else {
-            const uint32_t c = __byte_perm(w[s >> 2], 0u, 0x4440u | (uint32_t)(s & 3));
-            off = c * (uint32_t)(W * 4) + r4;
+    for (int s = 0; s < M; s += 2) {
+        float x[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int t = s + h;
+            uint32_t off;
+            if (W == 64) {
+                // (code << 8) | r4 in one byte permute: byte0 <- r4, byte1 <- code
+                off = __byte_perm(w[t >> 2], r4, 0x5504u | ((uint32_t)(t & 3) << 4));
+            } else {
+                const uint32_t c = __byte_perm(w[t >> 2], 0u, 0x4440u | (uint32_t)(t & 3));
+                off = c * (uint32_t)(W * 4) + r4;
+            }
+            x[h] = *reinterpret_cast<const float *>(lb + off + 4 * t);
         }
-        const float x = *reinterpret_cast<const float *>(lb + off + 4 * s);
-        if (s & 1)
-            acc1 += x;
-        else
-            acc0 += x;
+        add_f32x2(acc, x[0], x[1]);
     }
+    float acc0, acc1;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(acc0), "=f"(acc1) : "l"(acc));
     return acc0 + acc1;
 }
 
@@ -518,12 +532,15 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
 }
 
 // ---------------------------------------------------------------------------
-// Variant 2: 256 < n <= 4096. The CTA keeps region A = its current top-n
+// Variant 2: 256 < n <= 16384. The CTA keeps region A = its current top-n
 // (sorted, NP = next power of two >= n keys) and region B = new keys below the
-// threshold (the n-th key of A). When B may overflow in the next round, B is
-// sorted and merged into A (min(A[i], B[NP-1-i]) is bitonic and holds the NP
-// smallest; a bitonic merge sorts it). Warps scan in lock-step rounds so that
-// every thread reaches the same barriers.
+// threshold (the n-th key of A), NB <= NP keys (a power of two; NB < NP only
+// when two full regions do not fit in shared memory beside the LUT). When B
+// may overflow in the next round, B is sorted and merged into A: with B
+// padded by +inf to NP keys, min(A[i], B[NP-1-i]) is bitonic and holds the NP
+// smallest of both, and only its last NB positions can differ from A; a
+// bitonic merge sorts it. Warps scan in lock-step rounds so that every thread
+// reaches the same barriers.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void smem_bitonic_sort(uint64_t *x, int n) {
     for (int size = 2; size <= n; size <<= 1)
@@ -557,15 +574,16 @@ __device__ __forceinline__ void smem_bitonic_merge(uint64_t *x, int n) {
     }
 }
 
-// Merges the first cntB keys of B into A (both NP long); updates the threshold.
-__device__ __forceinline__ void cta_merge(uint64_t *A, uint64_t *B, int NP, uint32_t cntB, int ntop,
-                                          unsigned long long *s_thr, uint32_t *s_cnt) {
-    for (int i = cntB + threadIdx.x; i < NP; i += blockDim.x) B[i] = KEY_INF;
+// Merges the first cntB keys of B (NB long) into A (NP long, NB <= NP);
+// updates the threshold.
+__device__ __forceinline__ void cta_merge(uint64_t *A, uint64_t *B, int NP, int NB, uint32_t cntB,
+                                          int ntop, unsigned long long *s_thr, uint32_t *s_cnt) {
+    for (int i = cntB + threadIdx.x; i < NB; i += blockDim.x) B[i] = KEY_INF;
     __syncthreads();
-    smem_bitonic_sort(B, NP);
-    for (int i = threadIdx.x; i < NP; i += blockDim.x) {
-        const uint64_t b = B[NP - 1 - i];
-        if (b < A[i]) A[i] = b;
+    smem_bitonic_sort(B, NB);
+    for (int j = threadIdx.x; j < NB; j += blockDim.x) {
+        const uint64_t b = B[j];
+        if (b < A[NP - 1 - j]) A[NP - 1 - j] = b;
     }
     __syncthreads();
     smem_bitonic_merge(A, NP);
@@ -577,9 +595,9 @@ __device__ __forceinline__ void cta_merge(uint64_t *A, uint64_t *B, int NP, uint
 }
 
 template <int M, int W>
-__global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int NP) {
+__global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int NP, int NB) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, 2 * NP * 8);
+    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, (NP + NB) * 8);
     const ScanPtrs S(smem, plan, a.nprobe);
     uint64_t *A = reinterpret_cast<uint64_t *>(S.tail);
     uint64_t *B = A + NP;
@@ -633,11 +651,11 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
             __syncthreads();
             const uint32_t c = s_cnt;
             __syncthreads();  // every thread has read c before the next round adds to it
-            if (c + round > (uint32_t)NP) cta_merge(A, B, NP, c, ntop, &s_thr, &s_cnt);
+            if (c + round > (uint32_t)NB) cta_merge(A, B, NP, NB, c, ntop, &s_thr, &s_cnt);
         }
         __syncthreads();
         const uint32_t c = s_cnt;
-        if (c > 0) cta_merge(A, B, NP, c, ntop, &s_thr, &s_cnt);
+        if (c > 0) cta_merge(A, B, NP, NB, c, ntop, &s_thr, &s_cnt);
         if (a.stats) {
             for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
             if (lane == 0) atomicAdd(&s_kept, kept);
@@ -704,12 +722,19 @@ static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
         else launch_warp_r<M, W, 8>(a, l, st);
     } else {
         const int NP = pow2_at_least(a.ntop < 2 * BIG_WARPS * 32 ? 2 * BIG_WARPS * 32 : a.ntop);
-        const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, 2 * NP * 8);
-        FA_REQUIRE(plan.total <= 227 * 1024, FA_ERR_ARG,
+        // B region: as large as NP while both fit beside the LUT, and at least
+        // two rounds of keys
+        constexpr int budget = 227 * 1024 - 256;  // room for the kernel's static shared variables
+        int NB = NP;
+        while (NB > 2 * BIG_WARPS * 32 &&
+               ScanSmem(W, a.d, a.nlist, a.has_rep, a.nprobe, (NP + NB) * 8).total > budget)
+            NB >>= 1;
+        const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, (NP + NB) * 8);
+        FA_REQUIRE(plan.total <= budget, FA_ERR_ARG,
                    "scan shared memory above 227 KB (top-n too large for this M)");
         const int grid = scan_grid(l, plan.total);
         set_smem(k_scan_cta<M, W>, plan.total);
-        k_scan_cta<M, W><<<grid, BIG_THREADS, plan.total, st>>>(a, NP);
+        k_scan_cta<M, W><<<grid, BIG_THREADS, plan.total, st>>>(a, NP, NB);
     }
     FA_CHECK_CUDA(cudaGetLastError());
 }
@@ -718,7 +743,7 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     if (l.nq == 0) return;
     FA_REQUIRE(l.nprobe <= MAX_PROBE, FA_ERR_ARG, "nprobe above 512");
     FA_REQUIRE(ix.d <= MAX_D, FA_ERR_ARG, "d above 1024");
-    FA_REQUIRE(l.ntop >= 1 && l.ntop <= MAX_TOPN, FA_ERR_ARG, "top-n must be in 1..4096");
+    FA_REQUIRE(l.ntop >= 1 && l.ntop <= MAX_TOPN, FA_ERR_ARG, "top-n must be in 1..16384");
     ScanArgs a{};
     a.codes = ix.codes;
     a.list_beg = ix.list_beg;

@@ -301,6 +301,23 @@ def test_search_with_replication_matches_oracle(fa, u8_repl, k):
         assert len(set(gi[i].tolist())) == k  # no duplicate ids
 
 
+@pytest.mark.parametrize("k", [4097, 6000, 16384])
+def test_large_topn_matches_oracle(fa, f32_small, k):
+    """Top-n above 4096 (the re-rank depths that recall@10 = 0.9 needs): the
+    CTA-wide selection keeps its top-n beside the LUT with a staging region
+    smaller than the top-n once both do not fit in shared memory (nprobe 64 of
+    256 lists: about 25k distinct candidates, so the threshold filter and many
+    merges run)."""
+    s = f32_small
+    gi, gd, oi, od = _search_vs_oracle(fa, s, k, 64, nq=6)
+    for i in range(gi.shape[0]):
+        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
+        fin = np.isfinite(gd[i])
+        keys = list(zip(gd[i][fin].tolist(), gi[i][fin].tolist()))
+        assert keys == sorted(keys)
+        assert len(set(gi[i][fin].tolist())) == int(fin.sum())
+
+
 def test_end_to_end_recall_matches_oracle(fa, f32_small):
     """Whole path (coarse probe included) on the plain FP32 workload: recall@10
     against brute force within 0.005 of the oracle's."""
@@ -617,6 +634,31 @@ def test_rerank_matches_oracle(fa, u8_repl, eps, beta, batch, n):
         assert gi[i].tolist() == oi[i].tolist(), i
         assert st[i, 2] == ost[i, 2], (i, st[i], ost[i])
     assert compared >= q.shape[0] // 2
+
+
+@pytest.mark.parametrize("eps,beta,n", [(-1.0, 1, 8192), (-1.0, 1, 16384), (0.0, 2, 16384)])
+def test_deep_rerank_matches_oracle(fa, f32_small, eps, beta, n):
+    """Algorithm 1 over 8192 or 16384 ADC candidates (raw vectors in HBM).
+    FP32 and FP64 ADC order near ties differently somewhere in lists this
+    long, so the GPU's own ADC top-n (checked against the oracle's as a set)
+    is handed to the oracle's Algorithm 1, which must reproduce the GPU's
+    re-ranked ids, distances and mini-batch count."""
+    s = f32_small
+    k, npb = 10, 64
+    q = s["q"][:6]
+    probes = oracle.coarse(q, s["parts"]["centroids"], npb)
+    p = fa.search_params(rerank_n=n, rerank_batch=32, rerank_beta=beta, rerank_eps=eps)
+    gi, gd, st = fa.fa_search_ex(s["ix"], q, k, npb, p, probes=probes, stats=True)
+    an_i, an_d = fa.fa_search_ex(s["ix"], q, n, npb, probes=probes)
+    ao_i, ao_d = oracle.search(q, s["parts"]["centroids"], s["parts"]["codebooks"],
+                               s["parts"]["codes"], s["off"], s["ids"], npb, n + 1, probes=probes)
+    for i in range(q.shape[0]):
+        _check_topk(an_i[i], an_d[i], ao_i[i, :n], ao_d[i, :n], ao_d[i, n], n, what=str(i))
+        tasks = an_i[i][an_i[i] >= 0]
+        oi, od, nb = oracle.rerank(q[i], s["parts"]["raw"], tasks, k, batch=32, eps=eps, beta=beta)
+        assert gi[i].tolist() == oi.tolist(), i
+        np.testing.assert_allclose(gd[i], od, rtol=RTOL, atol=1e-3)
+        assert st[i, 2] == nb, (i, st[i], nb)
 
 
 @pytest.mark.parametrize("lowp", [False, True])
