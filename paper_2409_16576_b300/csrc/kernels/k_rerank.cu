@@ -11,10 +11,10 @@
 //            is compared with eps: Delta <= eps increments a stability
 //            counter, otherwise it is reset, and the loop ends when the
 //            counter reaches beta.
-// One warp handles one query. Each candidate's raw row is read by the whole
-// warp as one coalesced line (a 128-byte request for d = 128 uint8), so rows in
-// pinned host memory cross the host link in full-line reads; the 32 rows of a
-// mini-batch step are issued back to back before any is summed.
+// One warp handles one query. Eight lanes read a candidate's raw row in
+// consecutive 16-byte pieces (a full 128-byte request for d = 128 uint8), so
+// rows in pinned host memory cross the host link in full-line reads; the 32
+// rows of a mini-batch step are issued back to back before any is summed.
 #include "../fa_internal.h"
 #include "warp_topk.cuh"
 
@@ -125,57 +125,74 @@ void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, i
 
 // Exact squared L2 of the 32 rows ids[0..31] (one per lane, id < 0 = none)
 // against the query in shared memory; lane j returns row j's distance.
-template <typename T>
-__device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d, const float *qs,
-                                            int64_t my_id) {
-    const int lane = threadIdx.x & 31;
-    float p[32];
+// Eight lanes share a row and read consecutive 16-byte pieces of it (4-byte
+// words when a row is not a multiple of 16 bytes), so one load instruction
+// covers four rows with a full 128-byte request each (d = 128 uint8). The
+// loads of all 32 rows are issued before any is summed; the eight partial
+// sums of a row are added with three shuffles.
+template <typename T, typename C>
+__device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d,
+                                            const float *qs, int64_t my_id) {
+    constexpr int EPC = (int)(sizeof(C) / sizeof(T));  // elements per piece
+    constexpr int WPC = (int)(sizeof(C) / 4);          // 32-bit words per piece
+    constexpr int EPW = EPC / WPC;                     // elements per word
+    const int lane = threadIdx.x & 31, r = lane >> 3, c = lane & 7;
+    const int pieces = d / EPC;  // per row
+    float tot[8];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) p[j] = 0.f;
-    constexpr int EPW = sizeof(T) == 1 ? 4 : 1;  // elements per 32-bit word
-    const int words = d / EPW;
-    for (int w0 = 0; w0 < words; w0 += 32) {
-        const int w = w0 + lane;
-        const bool wok = w < words;
-        float qv[EPW];
+    for (int s = 0; s < 8; ++s) tot[s] = 0.f;
+    for (int p0 = 0; p0 < pieces; p0 += 8) {
+        const int pc = p0 + c;
+        C x[8];
 #pragma unroll
-        for (int e = 0; e < EPW; ++e) qv[e] = wok ? qs[w * EPW + e] : 0.f;
-        uint32_t x[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int64_t id = __shfl_sync(FULL, (long long)my_id, j);
-            x[j] = (id >= 0 && wok)
-                       ? reinterpret_cast<const unsigned int *>(raw + id * (int64_t)d)[w]
-                       : 0u;
+        for (int s = 0; s < 8; ++s) {
+            const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
+            if (id >= 0 && pc < pieces)
+                x[s] = reinterpret_cast<const C *>(raw + id * (int64_t)d)[pc];
+            else
+                x[s] = C{};
         }
+        if (pc >= pieces) continue;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int64_t id = __shfl_sync(FULL, (long long)my_id, j);
-            if (id < 0 || !wok) continue;
-            if (EPW == 4) {
+        for (int wd = 0; wd < WPC; ++wd) {
+            float qv[EPW];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    const float t = qv[e] - (float)((x[j] >> (8 * e)) & 0xffu);
-                    p[j] = fmaf(t, t, p[j]);
+            for (int e = 0; e < EPW; ++e) qv[e] = qs[pc * EPC + wd * EPW + e];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t w = reinterpret_cast<const uint32_t *>(&x[s])[wd];
+                float acc = tot[s];
+#pragma unroll
+                for (int e = 0; e < EPW; ++e) {
+                    const float xv = sizeof(T) == 1 ? (float)((w >> (8 * e)) & 0xffu) : __uint_as_float(w);
+                    const float t = qv[e] - xv;
+                    acc = fmaf(t, t, acc);
                 }
-            } else {
-                const float t = qv[0] - __uint_as_float(x[j]);
-                p[j] = fmaf(t, t, p[j]);
+                tot[s] = acc;
             }
         }
     }
-    // transpose-reduce: lane l ends with the sum over lanes of p[l]
+    float out = 0.f;
 #pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-#pragma unroll
-        for (int i = 0; i < o; ++i) {
-            const bool upper = (lane & o) != 0;
-            const float send = upper ? p[i] : p[i + o];
-            const float keep = upper ? p[i + o] : p[i];
-            p[i] = keep + __shfl_xor_sync(FULL, send, o);
-        }
+    for (int s = 0; s < 8; ++s) {
+        float v = tot[s];
+        v += __shfl_xor_sync(FULL, v, 1);
+        v += __shfl_xor_sync(FULL, v, 2);
+        v += __shfl_xor_sync(FULL, v, 4);
+        // row 4s + r' sits on lanes 8r' .. 8r' + 7
+        const float mine = __shfl_sync(FULL, v, 8 * (lane & 3));
+        if ((lane >> 2) == s) out = mine;
     }
-    return p[0];
+    return out;
+}
+
+// Row pieces: 16 bytes when every row is a multiple of 16 bytes long, else
+// 4-byte words.
+template <typename T>
+__device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32_t d,
+                                                const float *qs, int64_t my_id) {
+    if ((d * (int)sizeof(T)) % 16 == 0) return exact_rows<T, uint4>(raw, d, qs, my_id);
+    return exact_rows<T, uint32_t>(raw, d, qs, my_id);
 }
 
 template <int R, typename T>
@@ -198,42 +215,50 @@ __device__ __forceinline__ void rerank_one(
         const bool ok = e < ntop && tk[e] != KEY_INF;
         valid += __popc(__ballot_sync(FULL, ok));
     }
+    // caller id of task e (tasks are internal ids; raw rows are in caller order)
+    auto task_id = [&](int e, int lim) -> int64_t {
+        return e < lim ? perm[(uint32_t)(tk[e] & 0xffffffffu)] : (int64_t)-1;
+    };
     uint64_t Q[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) Q[r] = KEY_INF;
     int counter = 0, batches = 0;
+    // the first step's ids; each step fetches the next one's before its rows
+    int64_t uid = task_id(lane, batch < valid ? batch : valid);
     for (int i = 0; i < valid; i += batch) {
         uint64_t old[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) old[r] = Q[r];
         const int end = i + batch < valid ? i + batch : valid;
         for (int s = i; s < end; s += 32) {
-            const int e = s + lane;
-            int64_t uid = -1;
-            if (e < end) uid = perm[(uint32_t)(tk[e] & 0xffffffffu)];
-            const float dist = exact_rows<T>(raw, d, qs, uid);
+            // next step: the rest of this mini-batch, else the next mini-batch
+            int ns = s + 32, nend = end;
+            if (ns >= end) {
+                ns = end;
+                nend = end + batch < valid ? end + batch : valid;
+            }
+            const int64_t uid_next = task_id(ns + lane, nend);
+            const float dist = exact_rows_any<T>(raw, d, qs, uid);
             uint64_t key[1] = {uid >= 0 ? make_key(dist, (uint32_t)uid) : KEY_INF};
             bitonic_sort<1>(key);
             merge_sorted32<R>(Q, key[0]);
+            uid = uid_next;
         }
         ++batches;
-        // Eq. 3: members of the new top-k that were not in the previous one
-        int changed = 0;
+        if (eps < 0.f) continue;  // Delta <= eps never holds: no early stop
+        // Eq. 3: members of the new top-k that were not in the previous one.
+        // Q is the kk smallest of (old Q and the mini-batch), so an old
+        // member stays iff it is not above the new kk-th key; the change is
+        // the new member count less the members that stayed.
+        const uint64_t newmax = warp_elem<R>(Q, kk - 1);
+        int now = 0, stayed = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int e = r * 32 + lane;
-            const uint64_t nk = Q[r];
-            bool fresh = (e < kk) && nk != KEY_INF;
-            const uint32_t nid = (uint32_t)(nk & 0xffffffffu);
-#pragma unroll
-            for (int rr = 0; rr < R; ++rr)
-                for (int j = 0; j < 32; ++j) {
-                    const uint64_t ok = shfl64(old[rr], j);
-                    if (rr * 32 + j < kk && ok != KEY_INF && (uint32_t)(ok & 0xffffffffu) == nid)
-                        fresh = false;
-                }
-            changed += __popc(__ballot_sync(FULL, fresh));
+            now += __popc(__ballot_sync(FULL, e < kk && Q[r] != KEY_INF));
+            stayed += __popc(__ballot_sync(FULL, e < kk && old[r] != KEY_INF && old[r] <= newmax));
         }
+        const int changed = now - stayed;
         // Algorithm 1's test on Eq. 3, with this query's own k
         if ((double)changed / (double)kk <= (double)eps) {
             ++counter;
@@ -264,7 +289,7 @@ __device__ __forceinline__ void rerank_one(
 // LEAN: the persistent form run beside a scan; capped at 64 registers so
 // that two of its warps fit in what three scan CTAs leave of an SM.
 template <int R, typename T, bool LEAN>
-__global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 1) k_rerank(
+__global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 3) k_rerank(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
     const int64_t *__restrict__ perm, const T *__restrict__ raw, int64_t *__restrict__ out_ids,

@@ -535,12 +535,17 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
 // Variant 2: 256 < n <= 16384. The CTA keeps region A = its current top-n
 // (sorted, NP = next power of two >= n keys) and region B = new keys below the
 // threshold (the n-th key of A), NB <= NP keys (a power of two; NB < NP only
-// when two full regions do not fit in shared memory beside the LUT). When B
-// may overflow in the next round, B is sorted and merged into A: with B
-// padded by +inf to NP keys, min(A[i], B[NP-1-i]) is bitonic and holds the NP
-// smallest of both, and only its last NB positions can differ from A; a
-// bitonic merge sorts it. Warps scan in lock-step rounds so that every thread
-// reaches the same barriers.
+// when two full regions do not fit in shared memory beside the LUT).
+//   * Fill phase: the first keys go straight into A; when A may overflow in
+//     the next round (or the query ends), A is padded with +inf and sorted
+//     once, which sets the threshold.
+//   * Then, when B may overflow in the next round, B is sorted and merged
+//     into A: with B padded by +inf to NP keys, min(A[i], B[NP-1-i]) is
+//     bitonic and holds the NP smallest of both, and only its last NB
+//     positions can differ from A; a bitonic merge sorts it.
+// Warps scan in lock-step rounds so that every thread reaches the same
+// barriers; each warp loads its next round's code rows before it scores the
+// current ones, so the loads are in flight across the barriers.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void smem_bitonic_sort(uint64_t *x, int n) {
     for (int size = 2; size <= n; size <<= 1)
@@ -594,6 +599,22 @@ __device__ __forceinline__ void cta_merge(uint64_t *A, uint64_t *B, int NP, int 
     __syncthreads();
 }
 
+// Pads A[c, NP) with +inf, sorts it and takes the threshold from it: the end
+// of the fill phase, in which new keys go straight into A.
+__device__ __forceinline__ void cta_seal(uint64_t *A, int NP, uint32_t c, int ntop,
+                                         unsigned long long *s_thr, uint32_t *s_cnt,
+                                         uint32_t *s_fill) {
+    for (int i = c + threadIdx.x; i < NP; i += blockDim.x) A[i] = KEY_INF;
+    __syncthreads();
+    smem_bitonic_sort(A, NP);
+    if (threadIdx.x == 0) {
+        *s_thr = A[ntop - 1];
+        *s_cnt = 0;
+        *s_fill = 0;
+    }
+    __syncthreads();
+}
+
 template <int M, int W>
 __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int NP, int NB) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -602,7 +623,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
     uint64_t *A = reinterpret_cast<uint64_t *>(S.tail);
     uint64_t *B = A + NP;
     __shared__ int64_t s_q;
-    __shared__ uint32_t s_kept, s_cnt;
+    __shared__ uint32_t s_kept, s_cnt, s_fill;
     __shared__ unsigned long long s_thr;
     constexpr int NW = M / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -613,9 +634,9 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
             s_q = next_query(a, it);
             s_kept = 0;
             s_cnt = 0;
+            s_fill = 1;
             s_thr = KEY_INF;
         }
-        for (int i = threadIdx.x; i < NP; i += blockDim.x) A[i] = KEY_INF;
         __syncthreads();
         const int64_t qi = s_q;
         if (qi >= a.nq) break;
@@ -628,14 +649,18 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
         const uint32_t total = S.pref[2 * np];
         uint32_t kept = 0;
         SegCursor sg;
+        // the code rows of this warp's chunk are loaded one round ahead
+        uint32_t v = 0, w[NW];
+        bool ok = false;
+        if ((uint32_t)warp < total) locate(a, S, np, warp, sg, v, ok);
+        load_codes<M>(a.codes, v, ok && (uint32_t)warp < total, w);
         for (uint32_t base = 0; base < total; base += BIG_WARPS) {
-            const uint32_t g = base + warp;
+            const uint32_t g = base + warp, gn = g + BIG_WARPS;
+            uint32_t vn = 0, wn[NW];
+            bool okn = false;
+            if (gn < total) locate(a, S, np, gn, sg, vn, okn);
+            load_codes<M>(a.codes, vn, okn && gn < total, wn);
             if (g < total) {
-                uint32_t v;
-                bool ok;
-                locate(a, S, np, g, sg, v, ok);
-                uint32_t w[NW];
-                load_codes<M>(a.codes, v, ok, w);
                 const float dist = adc_words<M, W>(w, v, S.lut);
                 kept += ok ? 1u : 0u;
                 const uint64_t key = make_key(dist, v);
@@ -645,17 +670,28 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
                     uint32_t p0 = 0;
                     if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
                     p0 = __shfl_sync(FULL, p0, 0);
-                    if (pass) B[p0 + __popc(m & ((1u << lane) - 1u))] = key;
+                    // fill phase: straight into A; afterwards into B
+                    uint64_t *dst = *(volatile uint32_t *)&s_fill ? A : B;
+                    if (pass) dst[p0 + __popc(m & ((1u << lane) - 1u))] = key;
                 }
             }
+            v = vn;
+            ok = okn;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) w[i] = wn[i];
             __syncthreads();
-            const uint32_t c = s_cnt;
+            const uint32_t c = s_cnt, fill = s_fill;
             __syncthreads();  // every thread has read c before the next round adds to it
-            if (c + round > (uint32_t)NB) cta_merge(A, B, NP, NB, c, ntop, &s_thr, &s_cnt);
+            if (fill) {
+                if (c + round > (uint32_t)NP) cta_seal(A, NP, c, ntop, &s_thr, &s_cnt, &s_fill);
+            } else if (c + round > (uint32_t)NB) {
+                cta_merge(A, B, NP, NB, c, ntop, &s_thr, &s_cnt);
+            }
         }
         __syncthreads();
         const uint32_t c = s_cnt;
-        if (c > 0) cta_merge(A, B, NP, NB, c, ntop, &s_thr, &s_cnt);
+        if (s_fill) cta_seal(A, NP, c, ntop, &s_thr, &s_cnt, &s_fill);
+        else if (c > 0) cta_merge(A, B, NP, NB, c, ntop, &s_thr, &s_cnt);
         if (a.stats) {
             for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
             if (lane == 0) atomicAdd(&s_kept, kept);
