@@ -345,6 +345,17 @@ fa_status fa_debug_fail_alloc(int32_t n);
  * status word; the CUDA context stays usable. FA_ERR_NODEV without a GPU. */
 fa_status fa_debug_timeout(uint32_t polls);
 
+/* Sets how many standard deviations above the expected count the scan's
+ * sampled threshold estimate sits (a top-n above 256 over many more
+ * candidates first scores a strided sample of them; default 3). The estimate
+ * is only a filter: when fewer than n keys fall below it the query is scanned
+ * again without it, and when more fall below it than shared memory holds the
+ * query is scanned again with the threshold tightening as it goes, so results
+ * do not depend on sigma. A large negative or positive sigma forces those
+ * second scans, which is how tests reach them.
+ * Process-wide; not thread-safe against concurrent searches. */
+fa_status fa_debug_tau_sigma(float sigma);
+
 /* ------------------------------------------------------------------------- */
 /* Coarse probe without allocation                                           */
 /* ------------------------------------------------------------------------- */

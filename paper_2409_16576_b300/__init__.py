@@ -106,6 +106,7 @@ _sig("fa_debug_candidates", i32, P, P, i32, P, P, i64, P)
 _sig("fa_debug_lut", i32, P, P, P, P)
 _sig("fa_debug_fail_alloc", i32, i32)
 _sig("fa_debug_timeout", i32, C.c_uint32)
+_sig("fa_debug_tau_sigma", i32, C.c_float)
 _sig("fa_coarse_probe_noalloc", i32, P, i64, i32, P, i32, i32, P, P)
 _sig("fa_server_params_init", None, P)
 _sig("fa_server_create", i32, P, P, P, P)
@@ -123,6 +124,7 @@ EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_build_index_lists", "fa
            "fa_index_info_get", "fa_save_index", "fa_load_index", "fa_free_index",
            "fa_search_params_init", "fa_search", "fa_search_ex", "fa_autotune", "fa_debug_probes",
            "fa_debug_candidates", "fa_debug_lut", "fa_debug_fail_alloc", "fa_debug_timeout",
+           "fa_debug_tau_sigma",
            "fa_coarse_probe_noalloc", "fa_server_params_init",
            "fa_server_create", "fa_server_submit", "fa_server_poll", "fa_server_stats",
            "fa_server_destroy", "fa_last_error",
@@ -416,6 +418,11 @@ def fa_debug_fail_alloc(n: int) -> None:
 def fa_debug_timeout(polls: int) -> None:
     """Runs a device wait that must run out; raises FaError(FA_ERR_TIMEOUT)."""
     _check(_lib.fa_debug_timeout(polls))
+
+
+def fa_debug_tau_sigma(sigma: float) -> None:
+    """Standard deviations in the scan's sampled threshold estimate (default 3)."""
+    _check(_lib.fa_debug_tau_sigma(float(sigma)))
 
 
 class Server:

@@ -1311,6 +1311,15 @@ fa_status fa_debug_fail_alloc(int32_t n) {
     return FA_OK;
 }
 
+fa_status fa_debug_tau_sigma(float sigma) {
+    if (!(sigma == sigma)) {
+        set_error("sigma is NaN");
+        return FA_ERR_ARG;
+    }
+    fa::set_tau_sigma(sigma);
+    return FA_OK;
+}
+
 fa_status fa_debug_timeout(uint32_t polls) {
     uint32_t *dev = nullptr;  // [0] status word, [1] a flag nothing sets
     try {

@@ -257,6 +257,8 @@ void launch_tile_plan(const DeviceIndex &ix, const int32_t *probes, const int32_
 void launch_tile_merge(const uint64_t *partial, const uint32_t *prefix, int64_t nq, int32_t ntop,
                        uint64_t *topkeys, cudaStream_t st);
 void launch_scan(const DeviceIndex &ix, const ScanLaunch &a, cudaStream_t st);
+// Standard deviations of the CTA top-n threshold estimate (test hook).
+void set_tau_sigma(float sigma);
 void launch_wait_nothing(uint32_t polls, const uint32_t *flag, uint32_t *err, cudaStream_t st);
 // true when an injected allocation failure (fa_debug_fail_alloc) is due now
 bool alloc_fault();

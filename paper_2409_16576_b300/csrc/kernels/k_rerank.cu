@@ -164,7 +164,11 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
                 float acc = tot[s];
 #pragma unroll
                 for (int e = 0; e < EPW; ++e) {
-                    const float xv = sizeof(T) == 1 ? (float)((w >> (8 * e)) & 0xffu) : __uint_as_float(w);
+                    // a byte b placed in the low mantissa bits of 2^23 reads
+                    // as 2^23 + b: one exact subtraction gives b as a float
+                    const float xv = sizeof(T) == 1
+                                         ? __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7640u + e)) - 8388608.0f
+                                         : __uint_as_float(w);
                     const float t = qv[e] - xv;
                     acc = fmaf(t, t, acc);
                 }
@@ -240,8 +244,12 @@ __device__ __forceinline__ void rerank_one(
             const int64_t uid_next = task_id(ns + lane, nend);
             const float dist = exact_rows_any<T>(raw, d, qs, uid);
             uint64_t key[1] = {uid >= 0 ? make_key(dist, (uint32_t)uid) : KEY_INF};
-            bitonic_sort<1>(key);
-            merge_sorted32<R>(Q, key[0]);
+            // only keys below Q's kk-th can change Q's first kk entries (the
+            // output and Eq. 3); a step with none leaves them as they are
+            if (__ballot_sync(FULL, key[0] < warp_elem<R>(Q, kk - 1))) {
+                bitonic_sort<1>(key);
+                merge_sorted32<R>(Q, key[0]);
+            }
             uid = uid_next;
         }
         ++batches;

@@ -25,6 +25,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "../fa_internal.h"
 #include "warp_topk.cuh"
@@ -33,7 +34,7 @@ namespace fa {
 
 constexpr int SCAN_THREADS = 256;  // warp-top-n variant (n <= 256)
 constexpr int SCAN_WARPS = SCAN_THREADS / 32;
-constexpr int BIG_THREADS = 512;   // CTA-top-n variant (256 < n <= 16384)
+constexpr int BIG_THREADS = 1024;  // CTA-top-n variant (256 < n <= 16384)
 constexpr int BIG_WARPS = BIG_THREADS / 32;
 constexpr int MAX_PROBE = 512;
 constexpr int MAX_D = 1024;
@@ -70,6 +71,7 @@ struct ScanArgs {
     const uint32_t *tile_prefix;  // [nq+1] first tile of each query, or null (one CTA per query)
     const uint32_t *tile_T;       // chunks per tile (device scalar)
     uint64_t *partial;            // [tile capacity][ntop] per-tile top-n
+    float tau_sigma;              // standard deviations of the CTA top-n threshold estimate
 };
 
 // One unit of scan work: the chunks [c0, climit) of query qi, written to row
@@ -543,46 +545,95 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 3 : 2) k_scan(const ScanArgs a
 //     into A: with B padded by +inf to NP keys, min(A[i], B[NP-1-i]) is
 //     bitonic and holds the NP smallest of both, and only its last NB
 //     positions can differ from A; a bitonic merge sorts it.
+//   * Threshold estimate: when the query has many more candidates than n, a
+//     strided sample of its chunks is scored first and a high quantile of the
+//     sample (about n/total of it plus four standard deviations) becomes an
+//     initial filter tau. Only keys at or below tau enter A and B, so far
+//     fewer keys are sorted and merged. If fewer than n keys fall below tau,
+//     the query is scanned again without it, so the result is exact either
+//     way.
 // Warps scan in lock-step rounds so that every thread reaches the same
 // barriers; each warp loads its next round's code rows before it scores the
 // current ones, so the loads are in flight across the barriers.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void smem_bitonic_sort(uint64_t *x, int n) {
-    for (int size = 2; size <= n; size <<= 1)
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-                const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const uint64_t p = x[lo], q = x[hi];
-                if ((p > q) == up) {
-                    x[lo] = q;
-                    x[hi] = p;
-                }
-            }
-            __syncthreads();
-        }
-}
-
-__device__ __forceinline__ void smem_bitonic_merge(uint64_t *x, int n) {
-    for (int stride = n >> 1; stride > 0; stride >>= 1) {
-        for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
-            const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
-            const int hi = lo + stride;
-            const uint64_t p = x[lo], q = x[hi];
-            if (p > q) {
-                x[lo] = q;
-                x[hi] = p;
-            }
-        }
-        __syncthreads();
+// In-register bitonic stages of level `size` on the 64-key block starting at
+// e0 (lane holds keys e0 + lane and e0 + 32 + lane), strides `from` (<= 32)
+// down to 1; key e is sorted ascending where (e & size) == 0.
+__device__ __forceinline__ void block64_stages(uint64_t &v0, uint64_t &v1, int e0, int size,
+                                               int from) {
+    const int lane = threadIdx.x & 31;
+    if (from >= 32) {  // partners e and e + 32 sit in one lane
+        const bool up = ((e0 + lane) & size) == 0;
+        const uint64_t lo = umin64(v0, v1), hi = umax64(v0, v1);
+        v0 = up ? lo : hi;
+        v1 = up ? hi : lo;
+        from = 16;
+    }
+    const bool up0 = ((e0 + lane) & size) == 0, up1 = ((e0 + 32 + lane) & size) == 0;
+    for (int t = from; t >= 1; t >>= 1) {
+        const bool lower = (lane & t) == 0;
+        const uint64_t o0 = shfl_xor64(v0, t), o1 = shfl_xor64(v1, t);
+        v0 = (lower == up0) ? umin64(v0, o0) : umax64(v0, o0);
+        v1 = (lower == up1) ? umin64(v1, o1) : umax64(v1, o1);
     }
 }
 
+// One shared-memory bitonic stage (stride >= 64) of level `size` over n keys.
+__device__ __forceinline__ void smem_stage(uint64_t *x, int n, int size, int stride) {
+    for (int i = threadIdx.x; i < n / 2; i += blockDim.x) {
+        const int lo = ((i & ~(stride - 1)) << 1) | (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t p = x[lo], q = x[hi];
+        if ((p > q) == up) {
+            x[lo] = q;
+            x[hi] = p;
+        }
+    }
+    __syncthreads();
+}
+
+// Strides 32..1 of level `size` (>= 64) on every 64-key block, in registers.
+__device__ __forceinline__ void smem_block_tail(uint64_t *x, int n, int size) {
+    const int lane = threadIdx.x & 31;
+    for (int b = threadIdx.x >> 5; b < n / 64; b += blockDim.x >> 5) {
+        uint64_t v0 = x[b * 64 + lane], v1 = x[b * 64 + 32 + lane];
+        block64_stages(v0, v1, b * 64, size, 32);
+        x[b * 64 + lane] = v0;
+        x[b * 64 + 32 + lane] = v1;
+    }
+    __syncthreads();
+}
+
+// Sorts n keys ascending (n a power of two, >= 64). Levels up to 64 keys and
+// the strides below 64 of every later level run in registers, one warp per
+// 64-key block; only the longer strides go through shared memory.
+__device__ __forceinline__ void smem_bitonic_sort(uint64_t *x, int n) {
+    const int lane = threadIdx.x & 31;
+    for (int b = threadIdx.x >> 5; b < n / 64; b += blockDim.x >> 5) {
+        uint64_t v0 = x[b * 64 + lane], v1 = x[b * 64 + 32 + lane];
+        for (int size = 2; size <= 64; size <<= 1) block64_stages(v0, v1, b * 64, size, size >> 1);
+        x[b * 64 + lane] = v0;
+        x[b * 64 + 32 + lane] = v1;
+    }
+    __syncthreads();
+    for (int size = 128; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride >= 64; stride >>= 1) smem_stage(x, n, size, stride);
+        smem_block_tail(x, n, size);
+    }
+}
+
+// Sorts a bitonic sequence of n keys ascending (n a power of two, >= 64).
+__device__ __forceinline__ void smem_bitonic_merge(uint64_t *x, int n) {
+    for (int stride = n >> 1; stride >= 64; stride >>= 1) smem_stage(x, n, n, stride);
+    smem_block_tail(x, n, n);  // every key index is below n: all ascending
+}
+
 // Merges the first cntB keys of B (NB long) into A (NP long, NB <= NP);
-// updates the threshold.
+// updates the threshold (never above tau).
 __device__ __forceinline__ void cta_merge(uint64_t *A, uint64_t *B, int NP, int NB, uint32_t cntB,
-                                          int ntop, unsigned long long *s_thr, uint32_t *s_cnt) {
+                                          int ntop, uint64_t tau, unsigned long long *s_thr,
+                                          uint32_t *s_cnt) {
     for (int i = cntB + threadIdx.x; i < NB; i += blockDim.x) B[i] = KEY_INF;
     __syncthreads();
     smem_bitonic_sort(B, NB);
@@ -593,7 +644,7 @@ __device__ __forceinline__ void cta_merge(uint64_t *A, uint64_t *B, int NP, int 
     __syncthreads();
     smem_bitonic_merge(A, NP);
     if (threadIdx.x == 0) {
-        *s_thr = A[ntop - 1];
+        *s_thr = umin64(A[ntop - 1], tau);
         *s_cnt = 0;
     }
     __syncthreads();
@@ -601,18 +652,56 @@ __device__ __forceinline__ void cta_merge(uint64_t *A, uint64_t *B, int NP, int 
 
 // Pads A[c, NP) with +inf, sorts it and takes the threshold from it: the end
 // of the fill phase, in which new keys go straight into A.
-__device__ __forceinline__ void cta_seal(uint64_t *A, int NP, uint32_t c, int ntop,
+__device__ __forceinline__ void cta_seal(uint64_t *A, int NP, uint32_t c, int ntop, uint64_t tau,
                                          unsigned long long *s_thr, uint32_t *s_cnt,
                                          uint32_t *s_fill) {
     for (int i = c + threadIdx.x; i < NP; i += blockDim.x) A[i] = KEY_INF;
     __syncthreads();
     smem_bitonic_sort(A, NP);
     if (threadIdx.x == 0) {
-        *s_thr = A[ntop - 1];
+        *s_thr = umin64(A[ntop - 1], tau);
         *s_cnt = 0;
         *s_fill = 0;
     }
     __syncthreads();
+}
+
+// Upper-bound estimate tau of the query's ntop-th smallest distance, from a
+// strided sample of `sch` chunks (keys in buf, sch * 32 of them): the m-th
+// smallest sampled distance, m = e + sigma sqrt(e) + 1 (sigma = 3 unless a
+// test sets it) for the e = ntop * sch / total sampled keys expected below
+// the true ntop-th. It is only a filter:
+// the CTA checks afterwards that ntop keys fell below it and otherwise scans
+// the query again without it. Returns the key (tau, max id), or +inf.
+template <int M, int W>
+__device__ __forceinline__ uint64_t sample_tau(const ScanArgs &a, const ScanPtrs &S, int np,
+                                               uint32_t total, int ntop, int sch, uint64_t *buf,
+                                               unsigned long long *s_tau) {
+    constexpr int NW = M / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t stride = total / (uint32_t)sch;
+    SegCursor sc;
+    for (int j = warp; j < sch; j += blockDim.x >> 5) {
+        uint32_t v;
+        bool ok;
+        locate(a, S, np, (uint32_t)j * stride, sc, v, ok);
+        uint32_t w[NW];
+        load_codes<M>(a.codes, v, ok, w);
+        const float dist = adc_words<M, W>(w, v, S.lut);
+        buf[j * 32 + lane] = ok ? ((uint64_t)f2o(dist) << 32) : KEY_INF;
+    }
+    __syncthreads();
+    smem_bitonic_sort(buf, sch * 32);
+    if (threadIdx.x == 0) {
+        const double e = (double)ntop * (double)sch / (double)total;
+        const double me = ceil(e + (double)a.tau_sigma * sqrt(e) + 1.0);
+        const int m = me < 1.0 ? 1 : (me > 1e9 ? 1000000000 : (int)me);
+        uint64_t t = KEY_INF;
+        if (m <= sch * 32 && buf[m - 1] != KEY_INF) t = buf[m - 1] | 0xffffffffull;
+        *s_tau = t;
+    }
+    __syncthreads();
+    return *s_tau;
 }
 
 template <int M, int W>
@@ -623,20 +712,18 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
     uint64_t *A = reinterpret_cast<uint64_t *>(S.tail);
     uint64_t *B = A + NP;
     __shared__ int64_t s_q;
-    __shared__ uint32_t s_kept, s_cnt, s_fill;
-    __shared__ unsigned long long s_thr;
+    __shared__ uint32_t s_kept, s_cnt, s_fill, s_ovf;
+    __shared__ unsigned long long s_thr, s_tau;
     constexpr int NW = M / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t round = BIG_WARPS * 32;  // keys one round can add
+    // sample chunks for the threshold estimate (the sample lives in A and B;
+    // its key count, sch * 32, is a power of two for the sort)
+    int sch_max = 256;
+    while (sch_max * 32 > NP + NB) sch_max >>= 1;
 
     for (int64_t it = 0;; ++it) {
-        if (threadIdx.x == 0) {
-            s_q = next_query(a, it);
-            s_kept = 0;
-            s_cnt = 0;
-            s_fill = 1;
-            s_thr = KEY_INF;
-        }
+        if (threadIdx.x == 0) s_q = next_query(a, it);
         __syncthreads();
         const int64_t qi = s_q;
         if (qi >= a.nq) break;
@@ -647,51 +734,121 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
         query_setup<M, W>(a, S, qi, np);
 
         const uint32_t total = S.pref[2 * np];
+        // a threshold estimate pays off only when most candidates are rejected
+        uint64_t tau = KEY_INF;
+        int sch = sch_max;
+        while (sch > 64 && (uint32_t)(2 * sch) > total) sch >>= 1;
+        if (total >= 2u * (uint32_t)sch && (uint64_t)total * 32 >= 3ull * (uint64_t)ntop)
+            tau = sample_tau<M, W>(a, S, np, total, ntop, sch, A, &s_tau);
+
         uint32_t kept = 0;
-        SegCursor sg;
-        // the code rows of this warp's chunk are loaded one round ahead
-        uint32_t v = 0, w[NW];
-        bool ok = false;
-        if ((uint32_t)warp < total) locate(a, S, np, warp, sg, v, ok);
-        load_codes<M>(a.codes, v, ok && (uint32_t)warp < total, w);
-        for (uint32_t base = 0; base < total; base += BIG_WARPS) {
-            const uint32_t g = base + warp, gn = g + BIG_WARPS;
-            uint32_t vn = 0, wn[NW];
-            bool okn = false;
-            if (gn < total) locate(a, S, np, gn, sg, vn, okn);
-            load_codes<M>(a.codes, vn, okn && gn < total, wn);
-            if (g < total) {
-                const float dist = adc_words<M, W>(w, v, S.lut);
-                kept += ok ? 1u : 0u;
-                const uint64_t key = make_key(dist, v);
-                const bool pass = ok && key < *(volatile unsigned long long *)&s_thr;
-                const uint32_t m = __ballot_sync(FULL, pass);
-                if (m) {
-                    uint32_t p0 = 0;
-                    if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
-                    p0 = __shfl_sync(FULL, p0, 0);
-                    // fill phase: straight into A; afterwards into B
-                    uint64_t *dst = *(volatile uint32_t *)&s_fill ? A : B;
-                    if (pass) dst[p0 + __popc(m & ((1u << lane) - 1u))] = key;
-                }
+        // free: warps scan without barriers and append every key at or below
+        // tau (about n of them) to A and then B, which are sorted and merged
+        // once at the end. Lock-step: the rounds above, with the threshold
+        // tightening as A fills. The lock-step scan runs without tau when
+        // fewer than n keys fell below it, and with tau when more than A and
+        // B hold did.
+        bool free_scan = tau != KEY_INF;
+        for (int pass = 0; pass < 3; ++pass) {
+            if (threadIdx.x == 0) {
+                s_kept = 0;
+                s_cnt = 0;
+                s_fill = 1;
+                s_ovf = 0;
+                s_thr = tau;
             }
-            v = vn;
-            ok = okn;
-#pragma unroll
-            for (int i = 0; i < NW; ++i) w[i] = wn[i];
             __syncthreads();
-            const uint32_t c = s_cnt, fill = s_fill;
-            __syncthreads();  // every thread has read c before the next round adds to it
-            if (fill) {
-                if (c + round > (uint32_t)NP) cta_seal(A, NP, c, ntop, &s_thr, &s_cnt, &s_fill);
-            } else if (c + round > (uint32_t)NB) {
-                cta_merge(A, B, NP, NB, c, ntop, &s_thr, &s_cnt);
+            kept = 0;
+            SegCursor sg;
+            // the code rows of this warp's chunk are loaded one chunk ahead
+            uint32_t v = 0, w[NW];
+            bool ok = false;
+            if ((uint32_t)warp < total) locate(a, S, np, warp, sg, v, ok);
+            load_codes<M>(a.codes, v, ok && (uint32_t)warp < total, w);
+            if (free_scan) {
+                const uint32_t cap = (uint32_t)(NP + NB);
+                for (uint32_t g = warp; g < total; g += BIG_WARPS) {
+                    const uint32_t gn = g + BIG_WARPS;
+                    uint32_t vn = 0, wn[NW];
+                    bool okn = false;
+                    if (gn < total) locate(a, S, np, gn, sg, vn, okn);
+                    load_codes<M>(a.codes, vn, okn && gn < total, wn);
+                    const float dist = adc_words<M, W>(w, v, S.lut);
+                    kept += ok ? 1u : 0u;
+                    const uint64_t key = make_key(dist, v);
+                    const bool pass_ = ok && key < tau;
+                    const uint32_t m = __ballot_sync(FULL, pass_);
+                    if (m) {
+                        uint32_t p0 = 0;
+                        if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+                        p0 = __shfl_sync(FULL, p0, 0);
+                        const uint32_t at = p0 + __popc(m & ((1u << lane) - 1u));
+                        if (pass_) {
+                            if (at < cap) A[at] = key;  // A and B are contiguous
+                            else s_ovf = 1;
+                        }
+                    }
+                    v = vn;
+                    ok = okn;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) w[i] = wn[i];
+                }
+                __syncthreads();
+                const uint32_t c = s_cnt;
+                if (s_ovf) {
+                    free_scan = false;  // more keys below tau than A and B hold
+                    __syncthreads();
+                    continue;
+                }
+                cta_seal(A, NP, c < (uint32_t)NP ? c : (uint32_t)NP, ntop, tau, &s_thr, &s_cnt, &s_fill);
+                if (c > (uint32_t)NP) cta_merge(A, B, NP, NB, c - NP, ntop, tau, &s_thr, &s_cnt);
+            } else {
+                for (uint32_t base = 0; base < total; base += BIG_WARPS) {
+                    const uint32_t g = base + warp, gn = g + BIG_WARPS;
+                    uint32_t vn = 0, wn[NW];
+                    bool okn = false;
+                    if (gn < total) locate(a, S, np, gn, sg, vn, okn);
+                    load_codes<M>(a.codes, vn, okn && gn < total, wn);
+                    if (g < total) {
+                        const float dist = adc_words<M, W>(w, v, S.lut);
+                        kept += ok ? 1u : 0u;
+                        const uint64_t key = make_key(dist, v);
+                        const bool pass_ = ok && key < *(volatile unsigned long long *)&s_thr;
+                        const uint32_t m = __ballot_sync(FULL, pass_);
+                        if (m) {
+                            uint32_t p0 = 0;
+                            if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+                            p0 = __shfl_sync(FULL, p0, 0);
+                            // fill phase: straight into A; afterwards into B
+                            uint64_t *dst = *(volatile uint32_t *)&s_fill ? A : B;
+                            if (pass_) dst[p0 + __popc(m & ((1u << lane) - 1u))] = key;
+                        }
+                    }
+                    v = vn;
+                    ok = okn;
+#pragma unroll
+                    for (int i = 0; i < NW; ++i) w[i] = wn[i];
+                    __syncthreads();
+                    const uint32_t c = s_cnt, fill = s_fill;
+                    __syncthreads();  // every thread has read c before the next round adds to it
+                    if (fill) {
+                        if (c + round > (uint32_t)NP) cta_seal(A, NP, c, ntop, tau, &s_thr, &s_cnt, &s_fill);
+                    } else if (c + round > (uint32_t)NB) {
+                        cta_merge(A, B, NP, NB, c, ntop, tau, &s_thr, &s_cnt);
+                    }
+                }
+                __syncthreads();
+                const uint32_t c = s_cnt;
+                if (s_fill) cta_seal(A, NP, c, ntop, tau, &s_thr, &s_cnt, &s_fill);
+                else if (c > 0) cta_merge(A, B, NP, NB, c, ntop, tau, &s_thr, &s_cnt);
             }
+            // A holds only keys at or below tau: the top-ntop is exact iff
+            // ntop of them were found; otherwise scan again without tau
+            if (tau == KEY_INF || A[ntop - 1] != KEY_INF) break;
+            tau = KEY_INF;
+            free_scan = false;
+            __syncthreads();
         }
-        __syncthreads();
-        const uint32_t c = s_cnt;
-        if (s_fill) cta_seal(A, NP, c, ntop, &s_thr, &s_cnt, &s_fill);
-        else if (c > 0) cta_merge(A, B, NP, NB, c, ntop, &s_thr, &s_cnt);
         if (a.stats) {
             for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
             if (lane == 0) atomicAdd(&s_kept, kept);
@@ -775,6 +932,10 @@ static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
     FA_CHECK_CUDA(cudaGetLastError());
 }
 
+static std::atomic<float> g_tau_sigma{3.0f};
+
+void set_tau_sigma(float sigma) { g_tau_sigma.store(sigma); }
+
 void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     if (l.nq == 0) return;
     FA_REQUIRE(l.nprobe <= MAX_PROBE, FA_ERR_ARG, "nprobe above 512");
@@ -814,6 +975,7 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     a.tile_prefix = l.tile_prefix;
     a.tile_T = l.tile_T;
     a.partial = l.partial;
+    a.tau_sigma = g_tau_sigma.load();
     if (a.tile_prefix) {
         FA_REQUIRE(l.ntop <= 256, FA_ERR_ARG, "the tiled form supports top-n <= 256");
         FA_REQUIRE(l.persistent, FA_ERR_ARG, "the tiled form runs persistent CTAs");

@@ -636,6 +636,24 @@ def test_rerank_matches_oracle(fa, u8_repl, eps, beta, batch, n):
     assert compared >= q.shape[0] // 2
 
 
+@pytest.mark.parametrize("sigma", [-1000.0, 150.0])
+@pytest.mark.parametrize("k", [600, 4097])
+def test_large_topn_exact_whatever_the_estimate(fa, f32_small, k, sigma):
+    """The sampled threshold estimate is only a filter. Forced far below the
+    true n-th distance (sigma -1000), fewer than n keys pass it and every
+    query is scanned again without it; forced high (sigma 150), more keys pass
+    than shared memory holds and the query is scanned again in lock-step
+    rounds. Both give the oracle's result."""
+    s = f32_small
+    fa.fa_debug_tau_sigma(sigma)
+    try:
+        gi, gd, oi, od = _search_vs_oracle(fa, s, k, 64, nq=6)
+    finally:
+        fa.fa_debug_tau_sigma(3.0)
+    for i in range(gi.shape[0]):
+        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
+
+
 @pytest.mark.parametrize("eps,beta,n", [(-1.0, 1, 8192), (-1.0, 1, 16384), (0.0, 2, 16384)])
 def test_deep_rerank_matches_oracle(fa, f32_small, eps, beta, n):
     """Algorithm 1 over 8192 or 16384 ADC candidates (raw vectors in HBM).
