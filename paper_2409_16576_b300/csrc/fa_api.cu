@@ -553,6 +553,9 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         sl.threads = tune.threads;
         sl.ilp = tune.ilp;
         sl.persistent = ((sp.flags & FA_PERSISTENT) || tune.persistent) ? 1 : 0;
+        // only a re-rank that may stop early reads the top-n in order; the
+        // output stage sorts what it returns
+        sl.sorted = (rerank && sp.rerank_eps >= 0.f) ? 1 : 0;
         if (sp.stats) FA_CHECK_CUDA(cudaMemsetAsync(w->stats, 0, sizeof(int32_t) * 4 * nq, st));
         if (tile_chunks > 0) {
             // batching form: uneven queries split into tiles of chunks, planned on the device

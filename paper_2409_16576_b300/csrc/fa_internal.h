@@ -234,6 +234,10 @@ struct ScanLaunch {
     const uint32_t *tile_prefix = nullptr;  // tiled form: [nq+1] tiles per query prefix
     const uint32_t *tile_T = nullptr;       // chunks per tile (device scalar)
     uint64_t *partial = nullptr;            // [tile capacity][ntop]
+    // top-n rows must be sorted ascending (a re-rank that may stop early
+    // reads them in order); otherwise a top-n above 256 may be written in
+    // any order, valid keys first
+    int sorted = 1;
 };
 
 

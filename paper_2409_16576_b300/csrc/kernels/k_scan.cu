@@ -72,6 +72,7 @@ struct ScanArgs {
     const uint32_t *tile_T;       // chunks per tile (device scalar)
     uint64_t *partial;            // [tile capacity][ntop] per-tile top-n
     float tau_sigma;              // standard deviations of the CTA top-n threshold estimate
+    int32_t sorted_out;           // CTA top-n rows must come out sorted
 };
 
 // One unit of scan work: the chunks [c0, climit) of query qi, written to row
@@ -666,17 +667,109 @@ __device__ __forceinline__ void cta_seal(uint64_t *A, int NP, uint32_t c, int nt
     __syncthreads();
 }
 
+// Bits of k at and above bit b (b <= 64).
+__device__ __forceinline__ uint64_t high_bits(uint64_t k, int b) { return b >= 64 ? 0ull : k >> b; }
+
+// The r-th smallest (1-based, 1 <= r <= n) of the n keys x[0, n) in shared
+// memory, by radix selection: digits of up to 11 bits from the highest bit
+// in which the smallest and largest keys differ, each pass counting the keys
+// that share the digits chosen so far (hist: 2048 counters). It stops as soon
+// as the chosen digits single out one key. Every thread returns the key.
+__device__ uint64_t cta_select_rth(const uint64_t *x, int n, int r, uint32_t *hist,
+                                   unsigned long long *s_lo, unsigned long long *s_hi,
+                                   uint32_t *s_dig, uint32_t *s_want, uint32_t *s_cnt) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        *s_lo = ~0ull;
+        *s_hi = 0ull;
+    }
+    __syncthreads();
+    uint64_t lo = ~0ull, hi = 0ull;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        lo = umin64(lo, x[i]);
+        hi = umax64(hi, x[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = umin64(lo, shfl_xor64(lo, o));
+        hi = umax64(hi, shfl_xor64(hi, o));
+    }
+    if (lane == 0) {
+        atomicMin(s_lo, (unsigned long long)lo);
+        atomicMax(s_hi, (unsigned long long)hi);
+    }
+    __syncthreads();
+    lo = *s_lo;
+    hi = *s_hi;
+    __syncthreads();
+    if (lo == hi) return lo;
+    int bound = 64 - __clzll((long long)(lo ^ hi));  // bits >= bound are shared by all keys
+    uint64_t prefix = high_bits(lo, bound);
+    uint32_t want = (uint32_t)r;
+    for (;;) {
+        const int width = bound < 11 ? bound : 11, shift = bound - width;
+        const uint32_t nb = 1u << width;
+        for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const uint64_t k = x[i];
+            if (high_bits(k, bound) == prefix) atomicAdd(&hist[(uint32_t)(k >> shift) & (nb - 1)], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            // lane j sums bins [j * per, (j + 1) * per); the lane whose range
+            // holds the want-th key walks its bins
+            const uint32_t per = (nb + 31) / 32;
+            uint32_t sum = 0;
+            for (uint32_t b = lane * per; b < (lane + 1) * per && b < nb; ++b) sum += hist[b];
+            uint32_t inc = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, inc, o);
+                if (lane >= o) inc += t;
+            }
+            const uint32_t before = inc - sum;
+            if (before < want && want <= inc) {
+                uint32_t run = before;
+                for (uint32_t b = lane * per; b < (lane + 1) * per && b < nb; ++b) {
+                    if (run + hist[b] >= want) {
+                        *s_dig = b;
+                        *s_want = want - run;
+                        *s_cnt = hist[b];
+                        break;
+                    }
+                    run += hist[b];
+                }
+            }
+        }
+        __syncthreads();
+        prefix = (prefix << width) | *s_dig;
+        want = *s_want;
+        const uint32_t cnt = *s_cnt;
+        bound = shift;
+        __syncthreads();
+        if (bound == 0) return prefix;
+        if (cnt == 1) {  // the one key with these high bits
+            for (int i = threadIdx.x; i < n; i += blockDim.x)
+                if (high_bits(x[i], bound) == prefix) *s_lo = x[i];
+            __syncthreads();
+            const uint64_t k = *s_lo;
+            __syncthreads();
+            return k;
+        }
+    }
+}
+
 // Upper-bound estimate tau of the query's ntop-th smallest distance, from a
 // strided sample of `sch` chunks (keys in buf, sch * 32 of them): the m-th
 // smallest sampled distance, m = e + sigma sqrt(e) + 1 (sigma = 3 unless a
 // test sets it) for the e = ntop * sch / total sampled keys expected below
-// the true ntop-th. It is only a filter:
+// the true ntop-th (found by radix selection). It is only a filter:
 // the CTA checks afterwards that ntop keys fell below it and otherwise scans
 // the query again without it. Returns the key (tau, max id), or +inf.
 template <int M, int W>
 __device__ __forceinline__ uint64_t sample_tau(const ScanArgs &a, const ScanPtrs &S, int np,
                                                uint32_t total, int ntop, int sch, uint64_t *buf,
-                                               unsigned long long *s_tau) {
+                                               uint32_t *hist, unsigned long long *s_tau,
+                                               uint32_t *sel) {
     constexpr int NW = M / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t stride = total / (uint32_t)sch;
@@ -691,17 +784,12 @@ __device__ __forceinline__ uint64_t sample_tau(const ScanArgs &a, const ScanPtrs
         buf[j * 32 + lane] = ok ? ((uint64_t)f2o(dist) << 32) : KEY_INF;
     }
     __syncthreads();
-    smem_bitonic_sort(buf, sch * 32);
-    if (threadIdx.x == 0) {
-        const double e = (double)ntop * (double)sch / (double)total;
-        const double me = ceil(e + (double)a.tau_sigma * sqrt(e) + 1.0);
-        const int m = me < 1.0 ? 1 : (me > 1e9 ? 1000000000 : (int)me);
-        uint64_t t = KEY_INF;
-        if (m <= sch * 32 && buf[m - 1] != KEY_INF) t = buf[m - 1] | 0xffffffffull;
-        *s_tau = t;
-    }
-    __syncthreads();
-    return *s_tau;
+    const double e = (double)ntop * (double)sch / (double)total;
+    const double me = ceil(e + (double)a.tau_sigma * sqrt(e) + 1.0);
+    const int m = me < 1.0 ? 1 : (me > 1e9 ? 1000000000 : (int)me);
+    if (m > sch * 32) return KEY_INF;
+    const uint64_t t = cta_select_rth(buf, sch * 32, m, hist, s_tau, s_tau + 1, sel, sel + 1, sel + 2);
+    return t == KEY_INF ? KEY_INF : (t | 0xffffffffull);
 }
 
 template <int M, int W>
@@ -712,15 +800,15 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
     uint64_t *A = reinterpret_cast<uint64_t *>(S.tail);
     uint64_t *B = A + NP;
     __shared__ int64_t s_q;
-    __shared__ uint32_t s_kept, s_cnt, s_fill, s_ovf;
-    __shared__ unsigned long long s_thr, s_tau;
+    __shared__ uint32_t s_kept, s_cnt, s_fill, s_ovf, s_sel[3];
+    __shared__ unsigned long long s_thr, s_sel64[2];
     constexpr int NW = M / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t round = BIG_WARPS * 32;  // keys one round can add
     // sample chunks for the threshold estimate (the sample lives in A and B;
     // its key count, sch * 32, is a power of two for the sort)
     int sch_max = 256;
-    while (sch_max * 32 > NP + NB) sch_max >>= 1;
+    while (sch_max * 32 + 1024 > NP + NB) sch_max >>= 1;  // 1024 keys' room for the histogram
 
     for (int64_t it = 0;; ++it) {
         if (threadIdx.x == 0) s_q = next_query(a, it);
@@ -739,7 +827,8 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
         int sch = sch_max;
         while (sch > 64 && (uint32_t)(2 * sch) > total) sch >>= 1;
         if (total >= 2u * (uint32_t)sch && (uint64_t)total * 32 >= 3ull * (uint64_t)ntop)
-            tau = sample_tau<M, W>(a, S, np, total, ntop, sch, A, &s_tau);
+            tau = sample_tau<M, W>(a, S, np, total, ntop, sch, A,
+                                   reinterpret_cast<uint32_t *>(A + sch * 32), s_sel64, s_sel);
 
         uint32_t kept = 0;
         // free: warps scan without barriers and append every key at or below
@@ -749,6 +838,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
         // fewer than n keys fell below it, and with tau when more than A and
         // B hold did.
         bool free_scan = tau != KEY_INF;
+        bool written = false;  // the row went out unsorted, straight from the selection
         for (int pass = 0; pass < 3; ++pass) {
             if (threadIdx.x == 0) {
                 s_kept = 0;
@@ -799,6 +889,31 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
                     free_scan = false;  // more keys below tau than A and B hold
                     __syncthreads();
                     continue;
+                }
+                if (!a.sorted_out && c >= (uint32_t)ntop) {
+                    // the ntop smallest of the c keys, in any order: select the
+                    // ntop-th (the table's shared memory is free now) and keep
+                    // every key up to it
+                    const uint64_t kth = cta_select_rth(A, (int)c, ntop, reinterpret_cast<uint32_t *>(S.lut),
+                                                        s_sel64, s_sel64 + 1, s_sel, s_sel + 1, s_sel + 2);
+                    uint64_t *out = a.topkeys + qi * (int64_t)a.ntop;
+                    if (threadIdx.x == 0) s_cnt = 0;
+                    __syncthreads();
+                    for (uint32_t i0 = 0; i0 < c; i0 += blockDim.x) {
+                        const uint32_t i = i0 + threadIdx.x;
+                        const bool keep = i < c && A[i] <= kth;
+                        const uint32_t m = __ballot_sync(FULL, keep);
+                        if (m) {
+                            uint32_t p0 = 0;
+                            if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+                            p0 = __shfl_sync(FULL, p0, 0);
+                            if (keep) out[p0 + __popc(m & ((1u << lane) - 1u))] = A[i];
+                        }
+                    }
+                    for (int e = ntop + threadIdx.x; e < a.ntop; e += blockDim.x) out[e] = KEY_INF;
+                    written = true;
+                    __syncthreads();
+                    break;
                 }
                 cta_seal(A, NP, c < (uint32_t)NP ? c : (uint32_t)NP, ntop, tau, &s_thr, &s_cnt, &s_fill);
                 if (c > (uint32_t)NP) cta_merge(A, B, NP, NB, c - NP, ntop, tau, &s_thr, &s_cnt);
@@ -853,8 +968,10 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
             for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
             if (lane == 0) atomicAdd(&s_kept, kept);
         }
-        uint64_t *out = a.topkeys + qi * (int64_t)a.ntop;
-        for (int e = threadIdx.x; e < a.ntop; e += blockDim.x) out[e] = e < ntop ? A[e] : KEY_INF;
+        if (!written) {
+            uint64_t *out = a.topkeys + qi * (int64_t)a.ntop;
+            for (int e = threadIdx.x; e < a.ntop; e += blockDim.x) out[e] = e < ntop ? A[e] : KEY_INF;
+        }
         __syncthreads();
         if (a.stats && threadIdx.x == 0) write_stats(a, S, qi, np, s_kept);
         __syncthreads();
@@ -976,6 +1093,7 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     a.tile_T = l.tile_T;
     a.partial = l.partial;
     a.tau_sigma = g_tau_sigma.load();
+    a.sorted_out = l.sorted;
     if (a.tile_prefix) {
         FA_REQUIRE(l.ntop <= 256, FA_ERR_ARG, "the tiled form supports top-n <= 256");
         FA_REQUIRE(l.persistent, FA_ERR_ARG, "the tiled form runs persistent CTAs");
