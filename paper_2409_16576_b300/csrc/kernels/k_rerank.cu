@@ -190,11 +190,66 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
     return out;
 }
 
+// The same for uint8 rows when the query is integral with every coordinate in
+// 0..255 (its bytes packed in qp, its squared norm in qq): with integers,
+// |q - x|^2 = |q|^2 - 2 q.x + |x|^2, and four-byte dot products (dp4a) give
+// q.x and |x|^2 four coordinates per instruction. Every term is an integer
+// below 2^24 for d <= 258, so the float returned equals the FP32 sum of
+// squared differences exactly.
+template <typename C>
+__device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ raw, int32_t d,
+                                                  const uint32_t *qp, int32_t qq, int64_t my_id) {
+    constexpr int WPC = (int)(sizeof(C) / 4);  // 32-bit words per piece
+    const int lane = threadIdx.x & 31, r = lane >> 3, c = lane & 7;
+    const int pieces = d / (4 * WPC);
+    int xx[8], qx[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) xx[s] = qx[s] = 0;
+    for (int p0 = 0; p0 < pieces; p0 += 8) {
+        const int pc = p0 + c;
+        C x[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
+            if (id >= 0 && pc < pieces)
+                x[s] = reinterpret_cast<const C *>(raw + id * (int64_t)d)[pc];
+            else
+                x[s] = C{};
+        }
+        if (pc >= pieces) continue;
+#pragma unroll
+        for (int wd = 0; wd < WPC; ++wd) {
+            const uint32_t qw = qp[pc * WPC + wd];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t w = reinterpret_cast<const uint32_t *>(&x[s])[wd];
+                xx[s] = (int)__dp4a(w, w, (unsigned)xx[s]);
+                qx[s] = (int)__dp4a(qw, w, (unsigned)qx[s]);
+            }
+        }
+    }
+    float out = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        int v = xx[s] - 2 * qx[s];
+        v += __shfl_xor_sync(FULL, v, 1);
+        v += __shfl_xor_sync(FULL, v, 2);
+        v += __shfl_xor_sync(FULL, v, 4);
+        const int mine = __shfl_sync(FULL, v, 8 * (lane & 3));
+        if ((lane >> 2) == s) out = (float)(qq + mine);
+    }
+    return out;
+}
+
 // Row pieces: 16 bytes when every row is a multiple of 16 bytes long, else
 // 4-byte words.
 template <typename T>
 __device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32_t d,
-                                                const float *qs, int64_t my_id) {
+                                                const float *qs, const uint32_t *qp, int32_t qq,
+                                                bool qint, int64_t my_id) {
+    if constexpr (sizeof(T) == 1) {
+        if (qint) return exact_rows_u8int<uint4>(raw, d, qp, qq, my_id);  // qint needs d % 16 == 0
+    }
     if ((d * (int)sizeof(T)) % 16 == 0) return exact_rows<T, uint4>(raw, d, qs, my_id);
     return exact_rows<T, uint32_t>(raw, d, qs, my_id);
 }
@@ -209,6 +264,30 @@ __device__ __forceinline__ void rerank_one(
     __syncwarp();  // the previous query of this warp is done with qs
     for (int j = lane; j < d; j += 32) qs[j] = q[qi * d + j];
     __syncwarp();
+    // uint8 rows: an integral query with coordinates in 0..255 takes the
+    // integer form (its bytes packed after the floats in qs)
+    bool qint = false;
+    int32_t qq = 0;
+    uint32_t *qp = reinterpret_cast<uint32_t *>(qs + d);
+    if (sizeof(T) == 1 && d <= 258 && d % 16 == 0) {
+        bool ok = true;
+        int32_t part = 0;
+        for (int j4 = lane; j4 < d / 4; j4 += 32) {
+            uint32_t wq = 0;
+            for (int e = 0; e < 4; ++e) {
+                const float v = qs[4 * j4 + e];
+                ok = ok && v >= 0.f && v <= 255.f && v == rintf(v);
+                const uint32_t b = ok ? (uint32_t)v : 0u;
+                wq |= b << (8 * e);
+                part += (int32_t)(b * b);
+            }
+            qp[j4] = wq;
+        }
+        qint = __all_sync(FULL, ok);
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+        qq = part;
+        __syncwarp();
+    }
     int kk = kq ? kq[qi] : k;
     kk = kk < 1 ? 1 : (kk > k ? k : kk);
     const uint64_t *tk = topkeys + qi * ntop;
@@ -242,7 +321,7 @@ __device__ __forceinline__ void rerank_one(
                 nend = end + batch < valid ? end + batch : valid;
             }
             const int64_t uid_next = task_id(ns + lane, nend);
-            const float dist = exact_rows_any<T>(raw, d, qs, uid);
+            const float dist = exact_rows_any<T>(raw, d, qs, qp, qq, qint, uid);
             uint64_t key[1] = {uid >= 0 ? make_key(dist, (uint32_t)uid) : KEY_INF};
             // only keys below Q's kk-th can change Q's first kk entries (the
             // output and Eq. 3); a step with none leaves them as they are
@@ -304,7 +383,7 @@ __global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 3) k_rerank(
     float *__restrict__ out_dist, int32_t *stats, uint32_t *ctr) {
     extern __shared__ float qsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *qs = qsm + warp * d;
+    float *qs = qsm + warp * (d + d / 4 + 1);  // the query, then its packed bytes
     for (int64_t it = 0;; ++it) {
         int64_t qi;
         if (ctr) {
@@ -330,7 +409,7 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
     const dim3 grid(ctr ? (unsigned)std::min<int64_t>(nq, 2 * num_sms(0))
                         : (unsigned)((nq + warps - 1) / warps));
     if (ctr) FA_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 4, st));
-    const int smem = warps * ix.d * 4;
+    const int smem = warps * (ix.d + ix.d / 4 + 1) * 4;
     const T *raw = reinterpret_cast<const T *>(ix.raw);
 #define FA_RR(RR)                                                                                 \
     do {                                                                                          \

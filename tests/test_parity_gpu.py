@@ -636,6 +636,28 @@ def test_rerank_matches_oracle(fa, u8_repl, eps, beta, batch, n):
     assert compared >= q.shape[0] // 2
 
 
+@pytest.mark.parametrize("shift", [0.0, 0.3, -1.0])
+def test_rerank_uint8_rows_any_query(fa, u8_repl, shift):
+    """uint8 raw rows: integral queries in 0..255 take the integer (dp4a)
+    distance form, other queries (fractional, or below 0) the float form;
+    both give the oracle's exact distances (the integer form exactly)."""
+    s = u8_repl
+    k, npb, n = 10, 16, 200
+    q = (s["q"][:16] + np.float32(shift)).astype(np.float32)
+    probes = oracle.coarse(q, s["parts"]["centroids"], npb)
+    p = fa.search_params(rerank_n=n, rerank_eps=-1.0)
+    gi, gd = fa.fa_search_ex(s["ix"], q, k, npb, p, probes=probes)
+    an_i, _ = fa.fa_search_ex(s["ix"], q, n, npb, probes=probes)
+    for i in range(q.shape[0]):
+        tasks = an_i[i][an_i[i] >= 0]
+        oi, od, _ = oracle.rerank(q[i], s["parts"]["raw"], tasks, k, batch=32, eps=-1.0, beta=1)
+        if shift == 0.0:
+            assert gd[i].tolist() == od.astype(np.float32).tolist(), i
+            assert gi[i].tolist() == oi.tolist(), i
+        else:
+            _check_topk(gi[i], gd[i], oi, od, od[-1], k, what=str(i))
+
+
 @pytest.mark.parametrize("sigma", [-1000.0, 150.0])
 @pytest.mark.parametrize("k", [600, 4097])
 def test_large_topn_exact_whatever_the_estimate(fa, f32_small, k, sigma):
