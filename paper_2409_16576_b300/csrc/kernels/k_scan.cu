@@ -670,12 +670,13 @@ __device__ __forceinline__ void cta_seal(uint64_t *A, int NP, uint32_t c, int nt
 // Bits of k at and above bit b (b <= 64).
 __device__ __forceinline__ uint64_t high_bits(uint64_t k, int b) { return b >= 64 ? 0ull : k >> b; }
 
-// The r-th smallest (1-based, 1 <= r <= n) of the n keys x[0, n) in shared
-// memory, by radix selection: digits of up to 11 bits from the highest bit
+// The r-th smallest (1-based, 1 <= r <= n1 + n2) of the keys x1[0, n1) and
+// x2[0, n2) in shared memory, by radix selection: digits of up to 11 bits from the highest bit
 // in which the smallest and largest keys differ, each pass counting the keys
 // that share the digits chosen so far (hist: 2048 counters). It stops as soon
 // as the chosen digits single out one key. Every thread returns the key.
-__device__ uint64_t cta_select_rth(const uint64_t *x, int n, int r, uint32_t *hist,
+__device__ uint64_t cta_select_rth(const uint64_t *x1, int n1, const uint64_t *x2, int n2, int r,
+                                   uint32_t *hist,
                                    unsigned long long *s_lo, unsigned long long *s_hi,
                                    uint32_t *s_dig, uint32_t *s_want, uint32_t *s_cnt) {
     const int lane = threadIdx.x & 31;
@@ -685,9 +686,10 @@ __device__ uint64_t cta_select_rth(const uint64_t *x, int n, int r, uint32_t *hi
     }
     __syncthreads();
     uint64_t lo = ~0ull, hi = 0ull;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        lo = umin64(lo, x[i]);
-        hi = umax64(hi, x[i]);
+    for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+        const uint64_t k = i < n1 ? x1[i] : x2[i - n1];
+        lo = umin64(lo, k);
+        hi = umax64(hi, k);
     }
     for (int o = 16; o > 0; o >>= 1) {
         lo = umin64(lo, shfl_xor64(lo, o));
@@ -710,8 +712,8 @@ __device__ uint64_t cta_select_rth(const uint64_t *x, int n, int r, uint32_t *hi
         const uint32_t nb = 1u << width;
         for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
         __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            const uint64_t k = x[i];
+        for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+            const uint64_t k = i < n1 ? x1[i] : x2[i - n1];
             if (high_bits(k, bound) == prefix) atomicAdd(&hist[(uint32_t)(k >> shift) & (nb - 1)], 1u);
         }
         __syncthreads();
@@ -748,8 +750,10 @@ __device__ uint64_t cta_select_rth(const uint64_t *x, int n, int r, uint32_t *hi
         __syncthreads();
         if (bound == 0) return prefix;
         if (cnt == 1) {  // the one key with these high bits
-            for (int i = threadIdx.x; i < n; i += blockDim.x)
-                if (high_bits(x[i], bound) == prefix) *s_lo = x[i];
+            for (int i = threadIdx.x; i < n1 + n2; i += blockDim.x) {
+                const uint64_t k = i < n1 ? x1[i] : x2[i - n1];
+                if (high_bits(k, bound) == prefix) *s_lo = k;
+            }
             __syncthreads();
             const uint64_t k = *s_lo;
             __syncthreads();
@@ -788,7 +792,8 @@ __device__ __forceinline__ uint64_t sample_tau(const ScanArgs &a, const ScanPtrs
     const double me = ceil(e + (double)a.tau_sigma * sqrt(e) + 1.0);
     const int m = me < 1.0 ? 1 : (me > 1e9 ? 1000000000 : (int)me);
     if (m > sch * 32) return KEY_INF;
-    const uint64_t t = cta_select_rth(buf, sch * 32, m, hist, s_tau, s_tau + 1, sel, sel + 1, sel + 2);
+    const uint64_t t =
+        cta_select_rth(buf, sch * 32, nullptr, 0, m, hist, s_tau, s_tau + 1, sel, sel + 1, sel + 2);
     return t == KEY_INF ? KEY_INF : (t | 0xffffffffull);
 }
 
@@ -856,7 +861,14 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
             if ((uint32_t)warp < total) locate(a, S, np, warp, sg, v, ok);
             load_codes<M>(a.codes, v, ok && (uint32_t)warp < total, w);
             if (free_scan) {
+                // keys beyond A and B spill to the query's output row and, once
+                // the scan is done, to the table's shared memory (less 8 KB for
+                // the selection's histogram)
                 const uint32_t cap = (uint32_t)(NP + NB);
+                const uint32_t lut_keys = (uint32_t)(plan.lut / 8) - 1024u;
+                uint32_t spill = lut_keys < (uint32_t)a.ntop ? lut_keys : (uint32_t)a.ntop;
+                spill = spill < (uint32_t)NP ? spill : (uint32_t)NP;  // merged as a region of <= NP
+                uint64_t *row = a.topkeys + qi * (int64_t)a.ntop;
                 for (uint32_t g = warp; g < total; g += BIG_WARPS) {
                     const uint32_t gn = g + BIG_WARPS;
                     uint32_t vn = 0, wn[NW];
@@ -875,6 +887,7 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
                         const uint32_t at = p0 + __popc(m & ((1u << lane) - 1u));
                         if (pass_) {
                             if (at < cap) A[at] = key;  // A and B are contiguous
+                            else if (at < cap + spill) row[at - cap] = key;
                             else s_ovf = 1;
                         }
                     }
@@ -886,37 +899,47 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
                 __syncthreads();
                 const uint32_t c = s_cnt;
                 if (s_ovf) {
-                    free_scan = false;  // more keys below tau than A and B hold
+                    free_scan = false;  // more keys below tau than shared memory holds
                     __syncthreads();
                     continue;
                 }
+                // the spilled keys move into the table's shared memory
+                const uint32_t c1 = c < cap ? c : cap, c2 = c - c1;
+                uint64_t *X2 = reinterpret_cast<uint64_t *>(S.lut);
+                for (uint32_t i = threadIdx.x; i < c2; i += blockDim.x) X2[i] = row[i];
+                __syncthreads();
                 if (!a.sorted_out && c >= (uint32_t)ntop) {
                     // the ntop smallest of the c keys, in any order: select the
-                    // ntop-th (the table's shared memory is free now) and keep
-                    // every key up to it
-                    const uint64_t kth = cta_select_rth(A, (int)c, ntop, reinterpret_cast<uint32_t *>(S.lut),
-                                                        s_sel64, s_sel64 + 1, s_sel, s_sel + 1, s_sel + 2);
-                    uint64_t *out = a.topkeys + qi * (int64_t)a.ntop;
+                    // ntop-th and keep every key up to it
+                    const uint64_t kth =
+                        cta_select_rth(A, (int)c1, X2, (int)c2, ntop, reinterpret_cast<uint32_t *>(X2 + spill),
+                                       s_sel64, s_sel64 + 1, s_sel, s_sel + 1, s_sel + 2);
                     if (threadIdx.x == 0) s_cnt = 0;
                     __syncthreads();
                     for (uint32_t i0 = 0; i0 < c; i0 += blockDim.x) {
                         const uint32_t i = i0 + threadIdx.x;
-                        const bool keep = i < c && A[i] <= kth;
+                        const uint64_t k = i < c1 ? A[i] : (i < c ? X2[i - c1] : KEY_INF);
+                        const bool keep = i < c && k <= kth;
                         const uint32_t m = __ballot_sync(FULL, keep);
                         if (m) {
                             uint32_t p0 = 0;
                             if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
                             p0 = __shfl_sync(FULL, p0, 0);
-                            if (keep) out[p0 + __popc(m & ((1u << lane) - 1u))] = A[i];
+                            if (keep) row[p0 + __popc(m & ((1u << lane) - 1u))] = k;
                         }
                     }
-                    for (int e = ntop + threadIdx.x; e < a.ntop; e += blockDim.x) out[e] = KEY_INF;
+                    for (int e = ntop + threadIdx.x; e < a.ntop; e += blockDim.x) row[e] = KEY_INF;
                     written = true;
                     __syncthreads();
                     break;
                 }
-                cta_seal(A, NP, c < (uint32_t)NP ? c : (uint32_t)NP, ntop, tau, &s_thr, &s_cnt, &s_fill);
-                if (c > (uint32_t)NP) cta_merge(A, B, NP, NB, c - NP, ntop, tau, &s_thr, &s_cnt);
+                cta_seal(A, NP, c1 < (uint32_t)NP ? c1 : (uint32_t)NP, ntop, tau, &s_thr, &s_cnt, &s_fill);
+                if (c1 > (uint32_t)NP) cta_merge(A, B, NP, NB, c1 - NP, ntop, tau, &s_thr, &s_cnt);
+                if (c2 > 0) {
+                    int N2 = 64;
+                    while ((uint32_t)N2 < c2) N2 <<= 1;  // <= spill < the table's keys
+                    cta_merge(A, X2, NP, N2, c2, ntop, tau, &s_thr, &s_cnt);
+                }
             } else {
                 for (uint32_t base = 0; base < total; base += BIG_WARPS) {
                     const uint32_t g = base + warp, gn = g + BIG_WARPS;

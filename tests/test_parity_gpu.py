@@ -658,14 +658,16 @@ def test_rerank_uint8_rows_any_query(fa, u8_repl, shift):
             _check_topk(gi[i], gd[i], oi, od, od[-1], k, what=str(i))
 
 
-@pytest.mark.parametrize("sigma", [-1000.0, 150.0])
-@pytest.mark.parametrize("k", [600, 4097])
+@pytest.mark.parametrize("k,sigma", [(600, -1000.0), (600, 44.0), (600, 150.0),
+                                     (4097, -1000.0), (4097, 125.0), (4097, 150.0)])
 def test_large_topn_exact_whatever_the_estimate(fa, f32_small, k, sigma):
     """The sampled threshold estimate is only a filter. Forced far below the
     true n-th distance (sigma -1000), fewer than n keys pass it and every
-    query is scanned again without it; forced high (sigma 150), more keys pass
-    than shared memory holds and the query is scanned again in lock-step
-    rounds. Both give the oracle's result."""
+    query is scanned again without it. Set a little high (sigma 44 for n 600,
+    125 for n 4097, on about 25k candidates), more keys pass than the two
+    shared-memory regions hold and the rest spill through the output row.
+    Forced high (sigma 150), more pass than that too and the query is scanned
+    again in lock-step rounds. All give the oracle's result."""
     s = f32_small
     fa.fa_debug_tau_sigma(sigma)
     try:
