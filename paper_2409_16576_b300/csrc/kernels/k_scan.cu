@@ -777,15 +777,24 @@ __device__ __forceinline__ uint64_t sample_tau(const ScanArgs &a, const ScanPtrs
     constexpr int NW = M / 4;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t stride = total / (uint32_t)sch;
+    const int nw = blockDim.x >> 5;
     SegCursor sc;
-    for (int j = warp; j < sch; j += blockDim.x >> 5) {
-        uint32_t v;
-        bool ok;
+    // two chunks per warp at a time, both loaded before either is scored
+    for (int j = warp; j < sch; j += 2 * nw) {
+        const int j2 = j + nw;
+        uint32_t v, v2 = 0;
+        bool ok, ok2 = false;
         locate(a, S, np, (uint32_t)j * stride, sc, v, ok);
-        uint32_t w[NW];
+        if (j2 < sch) locate(a, S, np, (uint32_t)j2 * stride, sc, v2, ok2);
+        uint32_t w[NW], w2[NW];
         load_codes<M>(a.codes, v, ok, w);
+        load_codes<M>(a.codes, v2, ok2, w2);
         const float dist = adc_words<M, W>(w, v, S.lut);
         buf[j * 32 + lane] = ok ? ((uint64_t)f2o(dist) << 32) : KEY_INF;
+        if (j2 < sch) {
+            const float dist2 = adc_words<M, W>(w2, v2, S.lut);
+            buf[j2 * 32 + lane] = ok2 ? ((uint64_t)f2o(dist2) << 32) : KEY_INF;
+        }
     }
     __syncthreads();
     const double e = (double)ntop * (double)sch / (double)total;
@@ -869,16 +878,12 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
                 uint32_t spill = lut_keys < (uint32_t)a.ntop ? lut_keys : (uint32_t)a.ntop;
                 spill = spill < (uint32_t)NP ? spill : (uint32_t)NP;  // merged as a region of <= NP
                 uint64_t *row = a.topkeys + qi * (int64_t)a.ntop;
-                for (uint32_t g = warp; g < total; g += BIG_WARPS) {
-                    const uint32_t gn = g + BIG_WARPS;
-                    uint32_t vn = 0, wn[NW];
-                    bool okn = false;
-                    if (gn < total) locate(a, S, np, gn, sg, vn, okn);
-                    load_codes<M>(a.codes, vn, okn && gn < total, wn);
-                    const float dist = adc_words<M, W>(w, v, S.lut);
-                    kept += ok ? 1u : 0u;
-                    const uint64_t key = make_key(dist, v);
-                    const bool pass_ = ok && key < tau;
+                // scores one chunk's keys and appends those at or below tau
+                auto score = [&](const uint32_t (&wc)[NW], uint32_t vc, bool okc) {
+                    const float dist = adc_words<M, W>(wc, vc, S.lut);
+                    kept += okc ? 1u : 0u;
+                    const uint64_t key = make_key(dist, vc);
+                    const bool pass_ = okc && key < tau;
                     const uint32_t m = __ballot_sync(FULL, pass_);
                     if (m) {
                         uint32_t p0 = 0;
@@ -891,10 +896,22 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
                             else s_ovf = 1;
                         }
                     }
-                    v = vn;
-                    ok = okn;
-#pragma unroll
-                    for (int i = 0; i < NW; ++i) w[i] = wn[i];
+                };
+                // two code buffers in turn: each chunk's rows load while the
+                // previous chunk is scored
+                for (uint32_t g = warp; g < total; g += 2 * BIG_WARPS) {
+                    const uint32_t g1 = g + BIG_WARPS, g2 = g1 + BIG_WARPS;
+                    uint32_t v1 = 0, w1[NW];
+                    bool ok1 = false;
+                    if (g1 < total) locate(a, S, np, g1, sg, v1, ok1);
+                    load_codes<M>(a.codes, v1, ok1 && g1 < total, w1);
+                    score(w, v, ok);
+                    if (g1 >= total) break;
+                    ok = false;
+                    v = 0;
+                    if (g2 < total) locate(a, S, np, g2, sg, v, ok);
+                    load_codes<M>(a.codes, v, ok && g2 < total, w);
+                    score(w1, v1, ok1);
                 }
                 __syncthreads();
                 const uint32_t c = s_cnt;
