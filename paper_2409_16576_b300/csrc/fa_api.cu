@@ -237,8 +237,19 @@ void upload_index(fa_index *ix) {
     if (ix->h_raw) {
         const size_t rb = (size_t)n * d * (ix->raw_dtype == FA_U8 ? 1 : 4);
         if (ix->raw_location == FA_RAW_DEVICE) {
-            D.raw_dev_alloc = dev_upload((const uint8_t *)ix->h_raw, rb, bytes);
+            // the HBM copy is in internal order (row v holds the vector with
+            // internal id v), so the re-rank reads rows by the ids the scan
+            // hands it and maps ids to the caller's only for the few keys
+            // that can enter the top-k
+            const size_t rowb = rb / (size_t)n;
+            std::vector<uint8_t> rows(rb);
+            const uint8_t *src = (const uint8_t *)ix->h_raw;
+#pragma omp parallel for schedule(static)
+            for (int64_t iv = 0; iv < n; ++iv)
+                memcpy(rows.data() + (size_t)iv * rowb, src + (size_t)perm[iv] * rowb, rowb);
+            D.raw_dev_alloc = dev_upload(rows.data(), rb, bytes);
             D.raw = D.raw_dev_alloc;
+            D.raw_internal = 1;
         } else {
             void *dp = nullptr;
             FA_CHECK_CUDA(cudaHostGetDevicePointer(&dp, ix->h_raw, 0));
@@ -261,7 +272,8 @@ static void ws_free_buffers(Workspace *w) {
     ws_drop_graph(w);
     void *dp[] = {w->q, w->probes, w->kq, w->npq, w->order, w->bucket, w->tchunks, w->tprefix,
                   w->tmisc, w->partial, w->topkeys, w->out_ids, w->out_dist,
-                  w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr};
+                  w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr, w->selbuf,
+                  w->redo};
     for (void *p : dp)
         if (p) cudaFree(p);
     void *hp[] = {w->h_err, w->h_stats, w->h_small};
@@ -280,6 +292,8 @@ static void ws_free_buffers(Workspace *w) {
     w->lut_scale = nullptr;
     w->coarse_d = nullptr;
     w->err = w->tile_ctr = nullptr;
+    w->selbuf = nullptr;
+    w->redo = nullptr;
     w->h_err = nullptr;
     w->h_stats = nullptr;
     w->h_small = nullptr;
@@ -333,6 +347,10 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
     dalloc(w->coarse_d, (size_t)w->coarse_rows * ldd);
     dalloc(w->err, 4);
     dalloc(w->tile_ctr, 4);
+    if (ct > 256) {
+        dalloc(w->selbuf, (size_t)2 * num_sms(ix->device) * 2 * ct);
+        dalloc(w->redo, (size_t)cq);
+    }
     FA_CHECK_CUDA(cudaHostAlloc((void **)&w->h_err, 16, cudaHostAllocDefault));
     FA_CHECK_CUDA(cudaHostAlloc((void **)&w->h_stats, sizeof(int32_t) * (size_t)cq * 4, cudaHostAllocDefault));
     FA_CHECK_CUDA(cudaHostAlloc((void **)&w->h_small, sizeof(int32_t) * (size_t)cq * 2, cudaHostAllocDefault));
@@ -617,6 +635,8 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         } else {
             launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
             sl.order = w->order;
+            sl.selbuf = w->selbuf;
+            sl.redo = w->redo;
             if (sl.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
             launch_scan(D, sl, st);
             tr.launches += 4;

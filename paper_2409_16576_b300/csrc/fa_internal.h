@@ -76,7 +76,8 @@ struct DeviceIndex {
     uint8_t *rep_t = nullptr;     // [n_rep] position of this list in that row (>= 1)
     uint32_t *mem = nullptr;      // [n_mem] membership rows: primary, then replicas
     int64_t *perm = nullptr;      // [n] internal id -> caller id
-    const void *raw = nullptr;    // [n][d] raw vectors (caller order), device-visible
+    const void *raw = nullptr;    // [n][d] raw vectors, device-visible
+    int32_t raw_internal = 0;     // rows in internal order (HBM copy) rather than caller order
     void *raw_dev_alloc = nullptr;
     void *raw_host_alloc = nullptr;
     // bf16 operands for the tensor-core paths (allocated on first use)
@@ -135,7 +136,9 @@ struct Workspace {
     float *coarse_d = nullptr;     // coarse distance scratch [coarse_rows][nlist rounded up to 4]
     int64_t coarse_rows = 0;
     uint32_t *err = nullptr;       // device error word
-    uint32_t *tile_ctr = nullptr;  // persistent-kernel work counters
+    uint32_t *tile_ctr = nullptr;  // [4] persistent-kernel work counters
+    uint64_t *selbuf = nullptr;    // [2 per SM][2 * cap_ntop] keys below the scan's threshold estimate
+    int32_t *redo = nullptr;       // [cap_nq] queries the selecting scan hands to the CTA top-n
     // pinned host staging for host-buffer calls
     float *h_q = nullptr;
     int64_t *h_ids = nullptr;
@@ -238,6 +241,12 @@ struct ScanLaunch {
     // reads them in order); otherwise a top-n above 256 may be written in
     // any order, valid keys first
     int sorted = 1;
+    // top-n above 256, unsorted, one stream: two CTAs per SM keep the keys
+    // below a sampled threshold in selbuf and select from there; queries it
+    // cannot finish are listed in redo for the one-CTA-per-SM kernel. Needs
+    // tile_ctr[0..3] to itself.
+    uint64_t *selbuf = nullptr;
+    int32_t *redo = nullptr;
 };
 
 

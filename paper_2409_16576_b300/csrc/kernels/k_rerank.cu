@@ -258,8 +258,8 @@ template <int R, typename T>
 __device__ __forceinline__ void rerank_one(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t qi,
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
-    const int64_t *__restrict__ perm, const T *__restrict__ raw, int64_t *__restrict__ out_ids,
-    float *__restrict__ out_dist, int32_t *stats, float *qs) {
+    const int64_t *__restrict__ perm, const T *__restrict__ raw, int raw_internal,
+    int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, float *qs) {
     const int lane = threadIdx.x & 31;
     __syncwarp();  // the previous query of this warp is done with qs
     for (int j = lane; j < d; j += 32) qs[j] = q[qi * d + j];
@@ -298,9 +298,12 @@ __device__ __forceinline__ void rerank_one(
         const bool ok = e < ntop && tk[e] != KEY_INF;
         valid += __popc(__ballot_sync(FULL, ok));
     }
-    // caller id of task e (tasks are internal ids; raw rows are in caller order)
+    // row of task e: its internal id when the rows are in internal order,
+    // else its caller id (tasks are internal ids)
     auto task_id = [&](int e, int lim) -> int64_t {
-        return e < lim ? perm[(uint32_t)(tk[e] & 0xffffffffu)] : (int64_t)-1;
+        if (e >= lim) return (int64_t)-1;
+        const uint32_t v = (uint32_t)(tk[e] & 0xffffffffu);
+        return raw_internal ? (int64_t)v : perm[v];
     };
     uint64_t Q[R];
 #pragma unroll
@@ -322,10 +325,17 @@ __device__ __forceinline__ void rerank_one(
             }
             const int64_t uid_next = task_id(ns + lane, nend);
             const float dist = exact_rows_any<T>(raw, d, qs, qp, qq, qint, uid);
-            uint64_t key[1] = {uid >= 0 ? make_key(dist, (uint32_t)uid) : KEY_INF};
             // only keys below Q's kk-th can change Q's first kk entries (the
-            // output and Eq. 3); a step with none leaves them as they are
-            if (__ballot_sync(FULL, key[0] < warp_elem<R>(Q, kk - 1))) {
+            // output and Eq. 3); a step with none leaves them as they are.
+            // Keys carry caller ids (ties break by them, as in the oracle):
+            // with rows in internal order the id is looked up only when the
+            // distance alone does not already rule the key out
+            const uint64_t kth = warp_elem<R>(Q, kk - 1);
+            int64_t cid = uid;
+            if (raw_internal && uid >= 0 && f2o(dist) <= (uint32_t)(kth >> 32)) cid = perm[uid];
+            uint64_t key[1] = {uid >= 0 ? make_key(dist, (uint32_t)cid) : KEY_INF};
+            if (raw_internal && uid >= 0 && f2o(dist) > (uint32_t)(kth >> 32)) key[0] = KEY_INF;
+            if (__ballot_sync(FULL, key[0] < kth)) {
                 bitonic_sort<1>(key);
                 merge_sorted32<R>(Q, key[0]);
             }
@@ -379,8 +389,8 @@ template <int R, typename T, bool LEAN>
 __global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 3) k_rerank(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
-    const int64_t *__restrict__ perm, const T *__restrict__ raw, int64_t *__restrict__ out_ids,
-    float *__restrict__ out_dist, int32_t *stats, uint32_t *ctr) {
+    const int64_t *__restrict__ perm, const T *__restrict__ raw, int raw_internal,
+    int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, uint32_t *ctr) {
     extern __shared__ float qsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *qs = qsm + warp * (d + d / 4 + 1);  // the query, then its packed bytes
@@ -395,8 +405,8 @@ __global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 3) k_rerank(
             qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
         }
         if (qi >= nq) break;
-        rerank_one<R, T>(q, d, topkeys, qi, ntop, k, kq, batch, beta, eps, perm, raw, out_ids,
-                         out_dist, stats, qs);
+        rerank_one<R, T>(q, d, topkeys, qi, ntop, k, kq, batch, beta, eps, perm, raw, raw_internal,
+                         out_ids, out_dist, stats, qs);
     }
 }
 
@@ -418,12 +428,14 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
             k_rerank<RR, T, true><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, \
                                                                   batch, beta, eps, ix.perm, raw,   \
+                                                                  ix.raw_internal,                  \
                                                                   out_ids, out_dist, stats, ctr);   \
         } else {                                                                                  \
             FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T, false>,                            \
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
             k_rerank<RR, T, false><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, \
                                                                    batch, beta, eps, ix.perm, raw,  \
+                                                                   ix.raw_internal,                 \
                                                                    out_ids, out_dist, stats, ctr);  \
         }                                                                                         \
     } while (0)

@@ -73,6 +73,10 @@ struct ScanArgs {
     uint64_t *partial;            // [tile capacity][ntop] per-tile top-n
     float tau_sigma;              // standard deviations of the CTA top-n threshold estimate
     int32_t sorted_out;           // CTA top-n rows must come out sorted
+    const uint32_t *nq_dev;       // device-side query count (slots >= it are done), or null
+    uint64_t *selbuf;             // selecting scan: [grid][sel_cap] keys per CTA
+    uint32_t sel_cap;
+    int32_t *redo;                // selecting scan: queries left to the CTA top-n
 };
 
 // One unit of scan work: the chunks [c0, climit) of query qi, written to row
@@ -369,7 +373,7 @@ __device__ __forceinline__ void write_stats(const ScanArgs &a, const ScanPtrs &S
 __device__ __forceinline__ int64_t next_query(const ScanArgs &a, int64_t it) {
     const int64_t slot =
         a.persistent ? (int64_t)atomicAdd(a.tile_ctr, 1u) : (int64_t)blockIdx.x + it * gridDim.x;
-    if (slot >= a.nq) return a.nq;
+    if (slot >= a.nq || (a.nq_dev && slot >= (int64_t)*a.nq_dev)) return a.nq;
     return a.order ? (int64_t)a.order[slot] : slot;
 }
 
@@ -1019,6 +1023,129 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
 }
 
 // ---------------------------------------------------------------------------
+// Variant 3 (selecting scan): 256 < n <= 16384 with rows that may come out
+// unsorted. Two 512-thread CTAs per SM, so that one CTA's per-query set-up,
+// sampling and selection overlap the other's scan. Per query: the sampled
+// threshold estimate tau (as in variant 2), a barrier-free scan that appends
+// every key at or below tau to this CTA's region of selbuf in global memory
+// (L2-resident; about 1.1 n keys, room for 2 n), a radix selection of the
+// n-th key over that region and a compaction of the n keys up to it into the
+// output row. A query it cannot finish this way (too few candidates for a
+// useful sample, fewer than n keys below tau, or more than the region holds)
+// is appended to the redo list, which variant 2 then scans.
+// ---------------------------------------------------------------------------
+constexpr int SEL_THREADS = 512;
+constexpr int SEL_WARPS = SEL_THREADS / 32;
+
+template <int M, int W>
+__global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, int sch_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, sch_max * 32 * 8 + 8192);
+    const ScanPtrs S(smem, plan, a.nprobe);
+    uint64_t *samp = reinterpret_cast<uint64_t *>(S.tail);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(samp + sch_max * 32);
+    uint64_t *buf = a.selbuf + (int64_t)blockIdx.x * a.sel_cap;
+    __shared__ int64_t s_q;
+    __shared__ uint32_t s_cnt, s_kept, s_sel[3];
+    __shared__ unsigned long long s_sel64[2];
+    constexpr int NW = M / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    for (int64_t it = 0;; ++it) {
+        if (threadIdx.x == 0) {
+            s_q = next_query(a, it);
+            s_cnt = 0;
+            s_kept = 0;
+        }
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi >= a.nq) break;
+        int np = a.npq ? a.npq[qi] : a.nprobe;
+        np = np < 1 ? 1 : (np > a.nprobe ? a.nprobe : np);
+        int ntop = a.ntopq ? a.ntopq[qi] : a.ntop;
+        ntop = ntop < 1 ? 1 : (ntop > a.ntop ? a.ntop : ntop);
+        query_setup<M, W>(a, S, qi, np);  // ends with a barrier
+        const uint32_t total = S.pref[2 * np];
+        int sch = sch_max;
+        while (sch > 64 && (uint32_t)(2 * sch) > total) sch >>= 1;
+        uint64_t tau = KEY_INF;
+        if (total >= 2u * (uint32_t)sch && (uint64_t)total * 32 >= 3ull * (uint64_t)ntop)
+            tau = sample_tau<M, W>(a, S, np, total, ntop, sch, samp, hist, s_sel64, s_sel);
+        if (tau == KEY_INF) {  // no useful estimate: variant 2 takes the query
+            if (threadIdx.x == 0) a.redo[atomicAdd(a.tile_ctr + 3, 1u)] = (int32_t)qi;
+            __syncthreads();
+            continue;
+        }
+        uint32_t kept = 0;
+        SegCursor sg;
+        uint32_t v = 0, w[NW];
+        bool ok = false;
+        if ((uint32_t)warp < total) locate(a, S, np, warp, sg, v, ok);
+        load_codes<M>(a.codes, v, ok && (uint32_t)warp < total, w);
+        auto score = [&](const uint32_t (&wc)[NW], uint32_t vc, bool okc) {
+            const float dist = adc_words<M, W>(wc, vc, S.lut);
+            kept += okc ? 1u : 0u;
+            const uint64_t key = make_key(dist, vc);
+            const bool pass_ = okc && key < tau;
+            const uint32_t m = __ballot_sync(FULL, pass_);
+            if (m) {
+                uint32_t p0 = 0;
+                if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+                p0 = __shfl_sync(FULL, p0, 0);
+                const uint32_t at = p0 + __popc(m & ((1u << lane) - 1u));
+                if (pass_ && at < a.sel_cap) buf[at] = key;
+            }
+        };
+        for (uint32_t g = warp; g < total; g += 2 * SEL_WARPS) {
+            const uint32_t g1 = g + SEL_WARPS, g2 = g1 + SEL_WARPS;
+            uint32_t v1 = 0, w1[NW];
+            bool ok1 = false;
+            if (g1 < total) locate(a, S, np, g1, sg, v1, ok1);
+            load_codes<M>(a.codes, v1, ok1 && g1 < total, w1);
+            score(w, v, ok);
+            if (g1 >= total) break;
+            ok = false;
+            v = 0;
+            if (g2 < total) locate(a, S, np, g2, sg, v, ok);
+            load_codes<M>(a.codes, v, ok && g2 < total, w);
+            score(w1, v1, ok1);
+        }
+        if (a.stats) {
+            for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
+            if (lane == 0) atomicAdd(&s_kept, kept);
+        }
+        __syncthreads();
+        const uint32_t c = s_cnt;
+        if (c < (uint32_t)ntop || c > a.sel_cap) {  // tau too low or too high
+            if (threadIdx.x == 0) a.redo[atomicAdd(a.tile_ctr + 3, 1u)] = (int32_t)qi;
+            __syncthreads();
+            continue;
+        }
+        const uint64_t kth = cta_select_rth(buf, (int)c, nullptr, 0, ntop, hist, s_sel64, s_sel64 + 1,
+                                            s_sel, s_sel + 1, s_sel + 2);
+        uint64_t *row = a.topkeys + qi * (int64_t)a.ntop;
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        for (uint32_t i0 = 0; i0 < c; i0 += blockDim.x) {
+            const uint32_t i = i0 + threadIdx.x;
+            const uint64_t k = i < c ? buf[i] : KEY_INF;
+            const bool keep = i < c && k <= kth;
+            const uint32_t m = __ballot_sync(FULL, keep);
+            if (m) {
+                uint32_t p0 = 0;
+                if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+                p0 = __shfl_sync(FULL, p0, 0);
+                if (keep) row[p0 + __popc(m & ((1u << lane) - 1u))] = k;
+            }
+        }
+        for (int e = ntop + threadIdx.x; e < a.ntop; e += blockDim.x) row[e] = KEY_INF;
+        __syncthreads();
+        if (a.stats && threadIdx.x == 0) write_stats(a, S, qi, np, s_kept);
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static int pow2_at_least(int x) {
@@ -1071,6 +1198,28 @@ static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
         else if (a.ntop <= 128) launch_warp_r<M, W, 4>(a, l, st);
         else launch_warp_r<M, W, 8>(a, l, st);
     } else {
+        // selecting scan (two CTAs per SM) when the rows may come out unsorted
+        // and its buffers are there; variant 2 then takes what it hands back
+        const ScanSmem sel_plan(W, a.d, a.nlist, a.has_rep, a.nprobe, 128 * 32 * 8 + 8192);
+        const ScanSmem sel_small(W, a.d, a.nlist, a.has_rep, a.nprobe, 64 * 32 * 8 + 8192);
+        const bool sel = !a.sorted_out && a.selbuf && a.redo && sel_small.total <= 113 * 1024;
+        ScanArgs b = a;  // variant 2's arguments
+        if (sel) {
+            const int sch_max = sel_plan.total <= 113 * 1024 ? 128 : 64;
+            const int smem_sel = sch_max == 128 ? sel_plan.total : sel_small.total;
+            ScanArgs c = a;
+            c.persistent = 1;
+            c.sel_cap = 2u * (uint32_t)a.ntop;
+            FA_CHECK_CUDA(cudaMemsetAsync(a.tile_ctr, 0, 4 * sizeof(uint32_t), st));
+            set_smem(k_scan_sel<M, W>, smem_sel);
+            k_scan_sel<M, W><<<2 * num_sms(0), SEL_THREADS, smem_sel, st>>>(c, sch_max);
+            FA_CHECK_CUDA(cudaGetLastError());
+            // variant 2 over the redo list (its length is on the device)
+            b.order = a.redo;
+            b.nq_dev = a.tile_ctr + 3;
+            b.tile_ctr = a.tile_ctr + 2;
+            b.persistent = 1;
+        }
         const int NP = pow2_at_least(a.ntop < 2 * BIG_WARPS * 32 ? 2 * BIG_WARPS * 32 : a.ntop);
         // B region: as large as NP while both fit beside the LUT, and at least
         // two rounds of keys
@@ -1082,9 +1231,9 @@ static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
         const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, (NP + NB) * 8);
         FA_REQUIRE(plan.total <= budget, FA_ERR_ARG,
                    "scan shared memory above 227 KB (top-n too large for this M)");
-        const int grid = scan_grid(l, plan.total);
+        const int grid = sel ? num_sms(0) : scan_grid(l, plan.total);
         set_smem(k_scan_cta<M, W>, plan.total);
-        k_scan_cta<M, W><<<grid, BIG_THREADS, plan.total, st>>>(a, NP, NB);
+        k_scan_cta<M, W><<<grid, BIG_THREADS, plan.total, st>>>(b, NP, NB);
     }
     FA_CHECK_CUDA(cudaGetLastError());
 }
@@ -1134,6 +1283,10 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     a.partial = l.partial;
     a.tau_sigma = g_tau_sigma.load();
     a.sorted_out = l.sorted;
+    a.nq_dev = nullptr;
+    a.selbuf = l.selbuf;
+    a.sel_cap = 0;
+    a.redo = l.redo;
     if (a.tile_prefix) {
         FA_REQUIRE(l.ntop <= 256, FA_ERR_ARG, "the tiled form supports top-n <= 256");
         FA_REQUIRE(l.persistent, FA_ERR_ARG, "the tiled form runs persistent CTAs");
