@@ -408,7 +408,12 @@ def main():
     achieved = scan_bytes / (scan_ms / 1e3) / 1e9
     khash = src_hash(SCAN_SOURCES)
     traffic = profile_traffic(khash, "%s-nq%d-nprobe%d-n%d" % (wl["name"], nq, wl["nprobe"], ntop))
-    scan_kernel = "k_scan_cta" if ntop > 256 else "k_scan"
+    if ntop <= 256:
+        scan_kernel = "k_scan"
+    elif wl["rerank_n"] > 0 and wl["eps"] >= 0:
+        scan_kernel = "k_scan_cta"  # an early-stopping re-rank reads sorted rows
+    else:
+        scan_kernel = "k_scan_sel + k_scan_cta (the queries it hands back)"
 
     # ---- the plain FP32 form at the same operating point (same index) ----
     plain = None

@@ -347,7 +347,7 @@ fa_status fa_debug_timeout(uint32_t polls);
 
 /* Sets how many standard deviations above the expected count the scan's
  * sampled threshold estimate sits (a top-n above 256 over many more
- * candidates first scores a strided sample of them; default 3). The estimate
+ * candidates first scores a strided sample of them; default 4). The estimate
  * is only a filter: when fewer than n keys fall below it the query is scanned
  * again without it, and when more fall below it than shared memory holds the
  * query is scanned again with the threshold tightening as it goes, so results

@@ -421,7 +421,7 @@ def fa_debug_timeout(polls: int) -> None:
 
 
 def fa_debug_tau_sigma(sigma: float) -> None:
-    """Standard deviations in the scan's sampled threshold estimate (default 3)."""
+    """Standard deviations in the scan's sampled threshold estimate (default 4)."""
     _check(_lib.fa_debug_tau_sigma(float(sigma)))
 
 

@@ -768,7 +768,7 @@ __device__ uint64_t cta_select_rth(const uint64_t *x1, int n1, const uint64_t *x
 
 // Upper-bound estimate tau of the query's ntop-th smallest distance, from a
 // strided sample of `sch` chunks (keys in buf, sch * 32 of them): the m-th
-// smallest sampled distance, m = e + sigma sqrt(e) + 1 (sigma = 3 unless a
+// smallest sampled distance, m = e + sigma sqrt(e) + 1 (sigma = 4 unless a
 // test sets it) for the e = ntop * sch / total sampled keys expected below
 // the true ntop-th (found by radix selection). It is only a filter:
 // the CTA checks afterwards that ntop keys fell below it and otherwise scans
@@ -1030,7 +1030,8 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
 // every key at or below tau to this CTA's region of selbuf in global memory
 // (L2-resident; about 1.1 n keys, room for 2 n), a radix selection of the
 // n-th key over that region and a compaction of the n keys up to it into the
-// output row. A query it cannot finish this way (too few candidates for a
+// output row; a query with no more candidates than the region holds keeps
+// them all, without an estimate. A query it cannot finish this way (no
 // useful sample, fewer than n keys below tau, or more than the region holds)
 // is appended to the redo list, which variant 2 then scans.
 // ---------------------------------------------------------------------------
@@ -1068,10 +1069,12 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
         const uint32_t total = S.pref[2 * np];
         int sch = sch_max;
         while (sch > 64 && (uint32_t)(2 * sch) > total) sch >>= 1;
+        // every candidate fits the buffer: keep them all, no estimate needed
+        const bool all = (uint64_t)total * 32 <= (uint64_t)a.sel_cap;
         uint64_t tau = KEY_INF;
-        if (total >= 2u * (uint32_t)sch && (uint64_t)total * 32 >= 3ull * (uint64_t)ntop)
+        if (!all && total >= 2u * (uint32_t)sch)
             tau = sample_tau<M, W>(a, S, np, total, ntop, sch, samp, hist, s_sel64, s_sel);
-        if (tau == KEY_INF) {  // no useful estimate: variant 2 takes the query
+        if (!all && tau == KEY_INF) {  // no useful estimate: variant 2 takes the query
             if (threadIdx.x == 0) a.redo[atomicAdd(a.tile_ctr + 3, 1u)] = (int32_t)qi;
             __syncthreads();
             continue;
@@ -1116,13 +1119,16 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
         }
         __syncthreads();
         const uint32_t c = s_cnt;
-        if (c < (uint32_t)ntop || c > a.sel_cap) {  // tau too low or too high
+        if ((!all && c < (uint32_t)ntop) || c > a.sel_cap) {  // tau too low or too high
             if (threadIdx.x == 0) a.redo[atomicAdd(a.tile_ctr + 3, 1u)] = (int32_t)qi;
             __syncthreads();
             continue;
         }
-        const uint64_t kth = cta_select_rth(buf, (int)c, nullptr, 0, ntop, hist, s_sel64, s_sel64 + 1,
-                                            s_sel, s_sel + 1, s_sel + 2);
+        // the ntop-th key, or every key when the query has no more than ntop
+        const uint64_t kth = c > (uint32_t)ntop
+                                 ? cta_select_rth(buf, (int)c, nullptr, 0, ntop, hist, s_sel64, s_sel64 + 1,
+                                                  s_sel, s_sel + 1, s_sel + 2)
+                                 : KEY_INF;
         uint64_t *row = a.topkeys + qi * (int64_t)a.ntop;
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
@@ -1138,7 +1144,8 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
                 if (keep) row[p0 + __popc(m & ((1u << lane) - 1u))] = k;
             }
         }
-        for (int e = ntop + threadIdx.x; e < a.ntop; e += blockDim.x) row[e] = KEY_INF;
+        const int kept_n = c < (uint32_t)ntop ? (int)c : ntop;
+        for (int e = kept_n + threadIdx.x; e < a.ntop; e += blockDim.x) row[e] = KEY_INF;
         __syncthreads();
         if (a.stats && threadIdx.x == 0) write_stats(a, S, qi, np, s_kept);
         __syncthreads();
@@ -1238,7 +1245,7 @@ static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
     FA_CHECK_CUDA(cudaGetLastError());
 }
 
-static std::atomic<float> g_tau_sigma{3.0f};
+static std::atomic<float> g_tau_sigma{4.0f};
 
 void set_tau_sigma(float sigma) { g_tau_sigma.store(sigma); }
 

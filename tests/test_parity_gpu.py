@@ -673,7 +673,7 @@ def test_large_topn_exact_whatever_the_estimate(fa, f32_small, k, sigma):
     try:
         gi, gd, oi, od = _search_vs_oracle(fa, s, k, 64, nq=6)
     finally:
-        fa.fa_debug_tau_sigma(3.0)
+        fa.fa_debug_tau_sigma(4.0)
     for i in range(gi.shape[0]):
         _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
 
