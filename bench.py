@@ -471,11 +471,13 @@ def main():
             "roofline": {"bound": "hbm", "kernel": scan_kernel, "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": traffic, "algorithmic_bytes_per_launch": scan_bytes,
-                         "launches_per_step": 8 if pipelined else 1,
+                         "launches_per_step": 8 if pipelined else (2 if "k_scan_sel" in scan_kernel else 1),
                          "timed_as": ("the step's scan stage: 8 chunk launches on two streams, "
                                       "with the re-ranks of earlier chunks running beside them; "
                                       "bytes and traffic are the step's totals") if pipelined
-                         else "the step's single scan launch",
+                         else ("the step's scan stage: k_scan_sel and the k_scan_cta launch over the "
+                               "queries it hands back; bytes and traffic are the stage's totals")
+                         if "k_scan_sel" in scan_kernel else "the step's single scan launch",
                          "kernel_src_hash": khash},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "queries/s", "h2d_bytes_per_step": nq * d * 4,
