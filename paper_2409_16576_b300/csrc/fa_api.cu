@@ -552,6 +552,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         }
         tr.mark(2);
 
+        bool fused = false;  // the re-rank ran inside the scan
         ScanLaunch sl{};
         sl.q = qd;
         sl.probes = probes;
@@ -637,13 +638,24 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             sl.order = w->order;
             sl.selbuf = w->selbuf;
             sl.redo = w->redo;
+            // an exhaustive re-rank (eps < 0) runs inside the selecting scan
+            sl.fuse_rerank = (rerank && sp.rerank_eps < 0.f) ? 1 : 0;
+            sl.k = k;
+            sl.kq = kq;
+            sl.rerank_batch = sp.rerank_batch;
+            sl.out_ids = oid;
+            sl.out_dist = odist;
             if (sl.persistent) FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr, 0, 4, st));
-            launch_scan(D, sl, st);
-            tr.launches += 4;
+            fused = launch_scan(D, sl, st);
+            tr.launches += 4 + ((ntop > 256 && !sl.sorted && w->selbuf) ? 1 : 0);
         }
         if (!pipelined) {
             tr.mark(3);
-            if (rerank)
+            if (rerank && fused)  // only the queries the selecting scan handed back
+                launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
+                              sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, 1,
+                              w->tile_ctr + 1, st, w->redo, w->tile_ctr + 3);
+            else if (rerank)
                 launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
                               sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, 8, nullptr, st);
             else

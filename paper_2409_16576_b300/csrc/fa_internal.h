@@ -247,6 +247,15 @@ struct ScanLaunch {
     // tile_ctr[0..3] to itself.
     uint64_t *selbuf = nullptr;
     int32_t *redo = nullptr;
+    // exhaustive re-rank (Algorithm 1 with eps < 0) fused into the selecting
+    // scan: each query's top-k goes straight to out_ids / out_dist (caller
+    // ids, sorted); queries handed back keep their top-n row for k_rerank.
+    // Needs raw rows in HBM in internal order and k <= 32.
+    int fuse_rerank = 0;
+    int32_t k = 0, rerank_batch = 32;
+    const int32_t *kq = nullptr;
+    int64_t *out_ids = nullptr;
+    float *out_dist = nullptr;
 };
 
 
@@ -269,7 +278,10 @@ void launch_tile_plan(const DeviceIndex &ix, const int32_t *probes, const int32_
                       uint32_t *prefix, cudaStream_t st);
 void launch_tile_merge(const uint64_t *partial, const uint32_t *prefix, int64_t nq, int32_t ntop,
                        uint64_t *topkeys, cudaStream_t st);
-void launch_scan(const DeviceIndex &ix, const ScanLaunch &a, cudaStream_t st);
+// Returns true when the exhaustive re-rank ran fused in the scan (outputs
+// written for every query the selecting scan finished; the rest are listed
+// in ScanLaunch::redo, their count in tile_ctr[3]).
+bool launch_scan(const DeviceIndex &ix, const ScanLaunch &a, cudaStream_t st);
 // Standard deviations of the CTA top-n threshold estimate (test hook).
 void set_tau_sigma(float sigma);
 void launch_wait_nothing(uint32_t polls, const uint32_t *flag, uint32_t *err, cudaStream_t st);
@@ -283,7 +295,8 @@ void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, i
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
                    float eps, int64_t *out_ids, float *out_dist, int32_t *stats, int warps,
-                   uint32_t *ctr, cudaStream_t st);
+                   uint32_t *ctr, cudaStream_t st, const int32_t *qlist = nullptr,
+                   const uint32_t *qcount = nullptr);
 void launch_debug_candidates(const DeviceIndex &ix, const int32_t *probes, int32_t nprobe,
                              uint32_t *out, uint32_t *count, uint32_t cap, cudaStream_t st);
 

@@ -16,6 +16,7 @@
 // rows in pinned host memory cross the host link in full-line reads; the 32
 // rows of a mini-batch step are issued back to back before any is summed.
 #include "../fa_internal.h"
+#include "rerank_rows.cuh"
 #include "warp_topk.cuh"
 
 namespace fa {
@@ -123,137 +124,6 @@ void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, i
     FA_CHECK_CUDA(cudaGetLastError());
 }
 
-// Exact squared L2 of the 32 rows ids[0..31] (one per lane, id < 0 = none)
-// against the query in shared memory; lane j returns row j's distance.
-// Eight lanes share a row and read consecutive 16-byte pieces of it (4-byte
-// words when a row is not a multiple of 16 bytes), so one load instruction
-// covers four rows with a full 128-byte request each (d = 128 uint8). The
-// loads of all 32 rows are issued before any is summed; the eight partial
-// sums of a row are added with three shuffles.
-template <typename T, typename C>
-__device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d,
-                                            const float *qs, int64_t my_id) {
-    constexpr int EPC = (int)(sizeof(C) / sizeof(T));  // elements per piece
-    constexpr int WPC = (int)(sizeof(C) / 4);          // 32-bit words per piece
-    constexpr int EPW = EPC / WPC;                     // elements per word
-    const int lane = threadIdx.x & 31, r = lane >> 3, c = lane & 7;
-    const int pieces = d / EPC;  // per row
-    float tot[8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) tot[s] = 0.f;
-    for (int p0 = 0; p0 < pieces; p0 += 8) {
-        const int pc = p0 + c;
-        C x[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
-            if (id >= 0 && pc < pieces)
-                x[s] = reinterpret_cast<const C *>(raw + id * (int64_t)d)[pc];
-            else
-                x[s] = C{};
-        }
-        if (pc >= pieces) continue;
-#pragma unroll
-        for (int wd = 0; wd < WPC; ++wd) {
-            float qv[EPW];
-#pragma unroll
-            for (int e = 0; e < EPW; ++e) qv[e] = qs[pc * EPC + wd * EPW + e];
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const uint32_t w = reinterpret_cast<const uint32_t *>(&x[s])[wd];
-                float acc = tot[s];
-#pragma unroll
-                for (int e = 0; e < EPW; ++e) {
-                    // a byte b placed in the low mantissa bits of 2^23 reads
-                    // as 2^23 + b: one exact subtraction gives b as a float
-                    const float xv = sizeof(T) == 1
-                                         ? __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7640u + e)) - 8388608.0f
-                                         : __uint_as_float(w);
-                    const float t = qv[e] - xv;
-                    acc = fmaf(t, t, acc);
-                }
-                tot[s] = acc;
-            }
-        }
-    }
-    float out = 0.f;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        float v = tot[s];
-        v += __shfl_xor_sync(FULL, v, 1);
-        v += __shfl_xor_sync(FULL, v, 2);
-        v += __shfl_xor_sync(FULL, v, 4);
-        // row 4s + r' sits on lanes 8r' .. 8r' + 7
-        const float mine = __shfl_sync(FULL, v, 8 * (lane & 3));
-        if ((lane >> 2) == s) out = mine;
-    }
-    return out;
-}
-
-// The same for uint8 rows when the query is integral with every coordinate in
-// 0..255 (its bytes packed in qp, its squared norm in qq): with integers,
-// |q - x|^2 = |q|^2 - 2 q.x + |x|^2, and four-byte dot products (dp4a) give
-// q.x and |x|^2 four coordinates per instruction. Every term is an integer
-// below 2^24 for d <= 258, so the float returned equals the FP32 sum of
-// squared differences exactly.
-template <typename C>
-__device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ raw, int32_t d,
-                                                  const uint32_t *qp, int32_t qq, int64_t my_id) {
-    constexpr int WPC = (int)(sizeof(C) / 4);  // 32-bit words per piece
-    const int lane = threadIdx.x & 31, r = lane >> 3, c = lane & 7;
-    const int pieces = d / (4 * WPC);
-    int xx[8], qx[8];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) xx[s] = qx[s] = 0;
-    for (int p0 = 0; p0 < pieces; p0 += 8) {
-        const int pc = p0 + c;
-        C x[8];
-#pragma unroll
-        for (int s = 0; s < 8; ++s) {
-            const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
-            if (id >= 0 && pc < pieces)
-                x[s] = reinterpret_cast<const C *>(raw + id * (int64_t)d)[pc];
-            else
-                x[s] = C{};
-        }
-        if (pc >= pieces) continue;
-#pragma unroll
-        for (int wd = 0; wd < WPC; ++wd) {
-            const uint32_t qw = qp[pc * WPC + wd];
-#pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const uint32_t w = reinterpret_cast<const uint32_t *>(&x[s])[wd];
-                xx[s] = (int)__dp4a(w, w, (unsigned)xx[s]);
-                qx[s] = (int)__dp4a(qw, w, (unsigned)qx[s]);
-            }
-        }
-    }
-    float out = 0.f;
-#pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        int v = xx[s] - 2 * qx[s];
-        v += __shfl_xor_sync(FULL, v, 1);
-        v += __shfl_xor_sync(FULL, v, 2);
-        v += __shfl_xor_sync(FULL, v, 4);
-        const int mine = __shfl_sync(FULL, v, 8 * (lane & 3));
-        if ((lane >> 2) == s) out = (float)(qq + mine);
-    }
-    return out;
-}
-
-// Row pieces: 16 bytes when every row is a multiple of 16 bytes long, else
-// 4-byte words.
-template <typename T>
-__device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32_t d,
-                                                const float *qs, const uint32_t *qp, int32_t qq,
-                                                bool qint, int64_t my_id) {
-    if constexpr (sizeof(T) == 1) {
-        if (qint) return exact_rows_u8int<uint4>(raw, d, qp, qq, my_id);  // qint needs d % 16 == 0
-    }
-    if ((d * (int)sizeof(T)) % 16 == 0) return exact_rows<T, uint4>(raw, d, qs, my_id);
-    return exact_rows<T, uint32_t>(raw, d, qs, my_id);
-}
-
 template <int R, typename T>
 __device__ __forceinline__ void rerank_one(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t qi,
@@ -269,25 +139,7 @@ __device__ __forceinline__ void rerank_one(
     bool qint = false;
     int32_t qq = 0;
     uint32_t *qp = reinterpret_cast<uint32_t *>(qs + d);
-    if (sizeof(T) == 1 && d <= 258 && d % 16 == 0) {
-        bool ok = true;
-        int32_t part = 0;
-        for (int j4 = lane; j4 < d / 4; j4 += 32) {
-            uint32_t wq = 0;
-            for (int e = 0; e < 4; ++e) {
-                const float v = qs[4 * j4 + e];
-                ok = ok && v >= 0.f && v <= 255.f && v == rintf(v);
-                const uint32_t b = ok ? (uint32_t)v : 0u;
-                wq |= b << (8 * e);
-                part += (int32_t)(b * b);
-            }
-            qp[j4] = wq;
-        }
-        qint = __all_sync(FULL, ok);
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-        qq = part;
-        __syncwarp();
-    }
+    if (sizeof(T) == 1 && d <= 258 && d % 16 == 0) qint = pack_u8_query(qs, d, qp, qq);
     int kk = kq ? kq[qi] : k;
     kk = kk < 1 ? 1 : (kk > k ? k : kk);
     const uint64_t *tk = topkeys + qi * ntop;
@@ -390,7 +242,8 @@ __global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 3) k_rerank(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
     const int64_t *__restrict__ perm, const T *__restrict__ raw, int raw_internal,
-    int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, uint32_t *ctr) {
+    int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, uint32_t *ctr,
+    const int32_t *qlist, const uint32_t *qcount) {
     extern __shared__ float qsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *qs = qsm + warp * (d + d / 4 + 1);  // the query, then its packed bytes
@@ -400,6 +253,10 @@ __global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 3) k_rerank(
             uint32_t x = 0;
             if (lane == 0) x = atomicAdd(ctr, 1u);
             qi = __shfl_sync(FULL, x, 0);
+            if (qlist) {  // slot x of a list whose length is on the device
+                if (qi >= (int64_t)*qcount) break;
+                qi = qlist[qi];
+            }
         } else {
             if (it > 0) break;
             qi = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
@@ -414,7 +271,8 @@ template <typename T>
 static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_t *topkeys,
                             int64_t nq, int32_t ntop, int32_t k, const int32_t *kq, int32_t batch,
                             int32_t beta, float eps, int64_t *out_ids, float *out_dist,
-                            int32_t *stats, int warps, uint32_t *ctr, cudaStream_t st) {
+                            int32_t *stats, int warps, uint32_t *ctr, const int32_t *qlist,
+                            const uint32_t *qcount, cudaStream_t st) {
     // persistent: two one-warp CTAs per SM pull queries; else one warp per query
     const dim3 grid(ctr ? (unsigned)std::min<int64_t>(nq, 2 * num_sms(0))
                         : (unsigned)((nq + warps - 1) / warps));
@@ -429,14 +287,16 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
             k_rerank<RR, T, true><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, \
                                                                   batch, beta, eps, ix.perm, raw,   \
                                                                   ix.raw_internal,                  \
-                                                                  out_ids, out_dist, stats, ctr);   \
+                                                                  out_ids, out_dist, stats, ctr,    \
+                                                                  qlist, qcount);                   \
         } else {                                                                                  \
             FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T, false>,                            \
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
             k_rerank<RR, T, false><<<grid, 32 * warps, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, \
                                                                    batch, beta, eps, ix.perm, raw,  \
                                                                    ix.raw_internal,                 \
-                                                                   out_ids, out_dist, stats, ctr);  \
+                                                                   out_ids, out_dist, stats, ctr,   \
+                                                                   nullptr, nullptr);               \
         }                                                                                         \
     } while (0)
     if (k <= 32)
@@ -451,23 +311,25 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
     FA_CHECK_CUDA(cudaGetLastError());
 }
 
-// warps: queries per CTA. With ctr, a persistent grid of one-warp CTAs (two
+// warps: queries per CTA. qlist (with ctr): re-rank only queries qlist[0,
+// *qcount), the length read on the device. With ctr, a persistent grid of one-warp CTAs (two
 // per SM, 64 registers each) pulls queries from the counter: it needs 4096
 // registers and 2 d floats of shared memory per SM, so it runs beside a scan
 // that fills the SMs, which is how the pipelined search overlaps the two.
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
                    float eps, int64_t *out_ids, float *out_dist, int32_t *stats, int warps,
-                   uint32_t *ctr, cudaStream_t st) {
+                   uint32_t *ctr, cudaStream_t st, const int32_t *qlist, const uint32_t *qcount) {
     if (nq == 0) return;
+    FA_REQUIRE(!qlist || (ctr && warps == 1), FA_ERR_ARG, "a query list needs the persistent form");
     FA_REQUIRE(ix.raw != nullptr, FA_ERR_ARG, "re-rank needs raw vectors in the index");
     if (ix.raw_dtype == FA_U8) {
         FA_REQUIRE(ix.d % 4 == 0, FA_ERR_ARG, "uint8 re-rank needs d % 4 == 0");
         launch_rerank_t<uint8_t>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
-                                 out_ids, out_dist, stats, warps, ctr, st);
+                                 out_ids, out_dist, stats, warps, ctr, qlist, qcount, st);
     } else {
         launch_rerank_t<float>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
-                               out_ids, out_dist, stats, warps, ctr, st);
+                               out_ids, out_dist, stats, warps, ctr, qlist, qcount, st);
     }
 }
 

@@ -28,6 +28,7 @@
 #include <atomic>
 
 #include "../fa_internal.h"
+#include "rerank_rows.cuh"
 #include "warp_topk.cuh"
 
 namespace fa {
@@ -77,6 +78,13 @@ struct ScanArgs {
     uint64_t *selbuf;             // selecting scan: [grid][sel_cap] keys per CTA
     uint32_t sel_cap;
     int32_t *redo;                // selecting scan: queries left to the CTA top-n
+    // selecting scan with the exhaustive re-rank fused (rows in internal order)
+    int32_t fuse_rr, raw_u8, k, rr_batch;
+    const void *raw;
+    const int64_t *perm;
+    const int32_t *kq;
+    int64_t *out_ids;
+    float *out_dist;
 };
 
 // One unit of scan work: the chunks [c0, climit) of query qi, written to row
@@ -1038,6 +1046,68 @@ __global__ void __launch_bounds__(BIG_THREADS) k_scan_cta(const ScanArgs a, int 
 constexpr int SEL_THREADS = 512;
 constexpr int SEL_WARPS = SEL_THREADS / 32;
 
+// Algorithm 1 with eps < 0 (no early stop) on the query's kept candidates
+// (the keys of buf[0, c) up to kth, kept_n of them), fused into the scan:
+// the result is the exact top-k by (squared L2, caller id) of all of them,
+// so the order they are taken in does not matter. Each warp re-ranks every
+// 16th group of 32 into its own sorted top-32 (raw rows in HBM in internal
+// order; the caller id is looked up only for keys that can enter it), then
+// warp 0 merges the 16 lists and writes the caller ids and distances. Ends
+// with a CTA barrier. uint8 rows of a multiple of 16 bytes only.
+__device__ __forceinline__ void rerank_fused(const ScanArgs &a, const ScanPtrs &S, int64_t qi,
+                                          const uint64_t *buf, uint32_t c, uint64_t kth, int kept_n,
+                                          uint32_t *scratch, uint32_t *s_small) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint64_t *wq = reinterpret_cast<uint64_t *>(scratch);            // [SEL_WARPS][32]
+    uint32_t *qp = reinterpret_cast<uint32_t *>(wq + SEL_WARPS * 32);  // [d / 4]
+    if (warp == 0) {
+        int32_t qq = 0;
+        bool qint = false;
+        if (a.d <= 258 && a.d % 16 == 0) qint = pack_u8_query(S.qv, a.d, qp, qq);
+        if (lane == 0) {
+            s_small[0] = (uint32_t)qq;
+            s_small[1] = qint ? 1u : 0u;
+        }
+    }
+    __syncthreads();
+    const int32_t qq = (int32_t)s_small[0];
+    const bool qint = s_small[1] != 0;
+    int kk = a.kq ? a.kq[qi] : a.k;
+    kk = kk < 1 ? 1 : (kk > a.k ? a.k : kk);
+    uint64_t Q[1] = {KEY_INF};
+    for (uint32_t i0 = (uint32_t)warp * 32; i0 < c; i0 += SEL_THREADS) {
+        const uint32_t i = i0 + lane;
+        const uint64_t key = i < c ? buf[i] : KEY_INF;
+        const int64_t v = (i < c && key <= kth) ? (int64_t)(uint32_t)(key & 0xffffffffu) : (int64_t)-1;
+        const uint8_t *raw = static_cast<const uint8_t *>(a.raw);
+        const float dist = qint ? exact_rows_u8int<uint4>(raw, a.d, qp, qq, v)
+                                : exact_rows<uint8_t, uint4>(raw, a.d, S.qv, v);
+        const uint64_t kthq = shfl64(Q[0], kk - 1);
+        const bool maybe = v >= 0 && f2o(dist) <= (uint32_t)(kthq >> 32);
+        uint64_t nk[1] = {maybe ? make_key(dist, (uint32_t)a.perm[v]) : KEY_INF};
+        if (__ballot_sync(FULL, nk[0] < kthq)) {
+            bitonic_sort<1>(nk);
+            merge_sorted32<1>(Q, nk[0]);
+        }
+    }
+    wq[warp * 32 + lane] = Q[0];
+    __syncthreads();
+    if (warp == 0) {
+        uint64_t L[1] = {wq[lane]};
+        for (int w2 = 1; w2 < SEL_WARPS; ++w2) merge_sorted32<1>(L, wq[w2 * 32 + lane]);
+        if (lane < a.k) {
+            const uint64_t key = lane < kk ? L[0] : KEY_INF;
+            a.out_ids[qi * a.k + lane] = key == KEY_INF ? -1 : (int64_t)(key & 0xffffffffu);
+            a.out_dist[qi * a.k + lane] = key == KEY_INF ? INFINITY : o2f((uint32_t)(key >> 32));
+        }
+        if (a.stats && lane == 0) {
+            a.stats[qi * 4 + 2] = (kept_n + a.rr_batch - 1) / a.rr_batch;
+            a.stats[qi * 4 + 3] = kept_n;
+        }
+    }
+    __syncthreads();
+}
+
 template <int M, int W>
 __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, int sch_max) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1129,6 +1199,12 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
                                  ? cta_select_rth(buf, (int)c, nullptr, 0, ntop, hist, s_sel64, s_sel64 + 1,
                                                   s_sel, s_sel + 1, s_sel + 2)
                                  : KEY_INF;
+        const int kept_n = c < (uint32_t)ntop ? (int)c : ntop;
+        if (a.fuse_rr) {
+            if (a.stats && threadIdx.x == 0) write_stats(a, S, qi, np, s_kept);
+            rerank_fused(a, S, qi, buf, c, kth, kept_n, hist, s_sel);
+            continue;
+        }
         uint64_t *row = a.topkeys + qi * (int64_t)a.ntop;
         if (threadIdx.x == 0) s_cnt = 0;
         __syncthreads();
@@ -1144,7 +1220,6 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
                 if (keep) row[p0 + __popc(m & ((1u << lane) - 1u))] = k;
             }
         }
-        const int kept_n = c < (uint32_t)ntop ? (int)c : ntop;
         for (int e = kept_n + threadIdx.x; e < a.ntop; e += blockDim.x) row[e] = KEY_INF;
         __syncthreads();
         if (a.stats && threadIdx.x == 0) write_stats(a, S, qi, np, s_kept);
@@ -1198,7 +1273,8 @@ static void launch_warp_r(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
 }
 
 template <int M, int W>
-static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t st) {
+static bool launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t st) {
+    bool fused = false;
     if (a.ntop <= 256) {
         if (a.ntop <= 32) launch_warp_r<M, W, 1>(a, l, st);
         else if (a.ntop <= 64) launch_warp_r<M, W, 2>(a, l, st);
@@ -1217,6 +1293,11 @@ static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
             ScanArgs c = a;
             c.persistent = 1;
             c.sel_cap = 2u * (uint32_t)a.ntop;
+            // the exhaustive re-rank rides along when its rows are in HBM in
+            // internal order and k fits one warp list
+            fused = l.fuse_rerank && a.raw && a.raw_u8 && a.d % 16 == 0 && l.k >= 1 && l.k <= 32 &&
+                    l.out_ids && l.out_dist;
+            c.fuse_rr = fused ? 1 : 0;
             FA_CHECK_CUDA(cudaMemsetAsync(a.tile_ctr, 0, 4 * sizeof(uint32_t), st));
             set_smem(k_scan_sel<M, W>, smem_sel);
             k_scan_sel<M, W><<<2 * num_sms(0), SEL_THREADS, smem_sel, st>>>(c, sch_max);
@@ -1243,14 +1324,15 @@ static void launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
         k_scan_cta<M, W><<<grid, BIG_THREADS, plan.total, st>>>(b, NP, NB);
     }
     FA_CHECK_CUDA(cudaGetLastError());
+    return fused;
 }
 
 static std::atomic<float> g_tau_sigma{4.0f};
 
 void set_tau_sigma(float sigma) { g_tau_sigma.store(sigma); }
 
-void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
-    if (l.nq == 0) return;
+bool launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
+    if (l.nq == 0) return false;
     FA_REQUIRE(l.nprobe <= MAX_PROBE, FA_ERR_ARG, "nprobe above 512");
     FA_REQUIRE(ix.d <= MAX_D, FA_ERR_ARG, "d above 1024");
     FA_REQUIRE(l.ntop >= 1 && l.ntop <= MAX_TOPN, FA_ERR_ARG, "top-n must be in 1..16384");
@@ -1294,18 +1376,28 @@ void launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     a.selbuf = l.selbuf;
     a.sel_cap = 0;
     a.redo = l.redo;
+    a.fuse_rr = 0;
+    a.raw_u8 = ix.raw_dtype == FA_U8 ? 1 : 0;
+    a.k = l.k;
+    a.rr_batch = l.rerank_batch;
+    a.raw = ix.raw_internal ? ix.raw : nullptr;  // fusion reads rows by internal id
+    a.perm = ix.perm;
+    a.kq = l.kq;
+    a.out_ids = l.out_ids;
+    a.out_dist = l.out_dist;
     if (a.tile_prefix) {
         FA_REQUIRE(l.ntop <= 256, FA_ERR_ARG, "the tiled form supports top-n <= 256");
         FA_REQUIRE(l.persistent, FA_ERR_ARG, "the tiled form runs persistent CTAs");
     }
     switch (ix.M) {
-        case 8: launch_scan_m<8, 64>(a, l, st); break;
-        case 16: launch_scan_m<16, 64>(a, l, st); break;
-        case 32: launch_scan_m<32, 64>(a, l, st); break;
-        case 48: launch_scan_m<48, 96>(a, l, st); break;
-        case 64: launch_scan_m<64, 128>(a, l, st); break;
+        case 8: return launch_scan_m<8, 64>(a, l, st);
+        case 16: return launch_scan_m<16, 64>(a, l, st);
+        case 32: return launch_scan_m<32, 64>(a, l, st);
+        case 48: return launch_scan_m<48, 96>(a, l, st);
+        case 64: return launch_scan_m<64, 128>(a, l, st);
         default: FA_REQUIRE(false, FA_ERR_ARG, "M must be one of 8, 16, 32, 48, 64");
     }
+    return false;
 }
 
 // ---------------------------------------------------------------------------

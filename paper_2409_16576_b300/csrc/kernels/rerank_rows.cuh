@@ -1,0 +1,167 @@
+// Exact squared L2 distances of raw rows against a query, one warp for 32
+// rows at a time: shared by the re-rank kernel (step 8) and the scan kernel
+// that fuses its exhaustive form.
+#pragma once
+
+#include "../fa_internal.h"
+#include "warp_topk.cuh"
+
+namespace fa {
+
+// Exact squared L2 of the 32 rows ids[0..31] (one per lane, id < 0 = none)
+// against the query in shared memory; lane j returns row j's distance.
+// Eight lanes share a row and read consecutive 16-byte pieces of it (4-byte
+// words when a row is not a multiple of 16 bytes), so one load instruction
+// covers four rows with a full 128-byte request each (d = 128 uint8). The
+// loads of all 32 rows are issued before any is summed; the eight partial
+// sums of a row are added with three shuffles.
+template <typename T, typename C>
+__device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d,
+                                            const float *qs, int64_t my_id) {
+    constexpr int EPC = (int)(sizeof(C) / sizeof(T));  // elements per piece
+    constexpr int WPC = (int)(sizeof(C) / 4);          // 32-bit words per piece
+    constexpr int EPW = EPC / WPC;                     // elements per word
+    const int lane = threadIdx.x & 31, r = lane >> 3, c = lane & 7;
+    const int pieces = d / EPC;  // per row
+    float tot[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) tot[s] = 0.f;
+    for (int p0 = 0; p0 < pieces; p0 += 8) {
+        const int pc = p0 + c;
+        C x[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
+            if (id >= 0 && pc < pieces)
+                x[s] = reinterpret_cast<const C *>(raw + id * (int64_t)d)[pc];
+            else
+                x[s] = C{};
+        }
+        if (pc >= pieces) continue;
+#pragma unroll
+        for (int wd = 0; wd < WPC; ++wd) {
+            float qv[EPW];
+#pragma unroll
+            for (int e = 0; e < EPW; ++e) qv[e] = qs[pc * EPC + wd * EPW + e];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t w = reinterpret_cast<const uint32_t *>(&x[s])[wd];
+                float acc = tot[s];
+#pragma unroll
+                for (int e = 0; e < EPW; ++e) {
+                    // a byte b placed in the low mantissa bits of 2^23 reads
+                    // as 2^23 + b: one exact subtraction gives b as a float
+                    const float xv = sizeof(T) == 1
+                                         ? __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7640u + e)) - 8388608.0f
+                                         : __uint_as_float(w);
+                    const float t = qv[e] - xv;
+                    acc = fmaf(t, t, acc);
+                }
+                tot[s] = acc;
+            }
+        }
+    }
+    float out = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        float v = tot[s];
+        v += __shfl_xor_sync(FULL, v, 1);
+        v += __shfl_xor_sync(FULL, v, 2);
+        v += __shfl_xor_sync(FULL, v, 4);
+        // row 4s + r' sits on lanes 8r' .. 8r' + 7
+        const float mine = __shfl_sync(FULL, v, 8 * (lane & 3));
+        if ((lane >> 2) == s) out = mine;
+    }
+    return out;
+}
+
+// The same for uint8 rows when the query is integral with every coordinate in
+// 0..255 (its bytes packed in qp, its squared norm in qq): with integers,
+// |q - x|^2 = |q|^2 - 2 q.x + |x|^2, and four-byte dot products (dp4a) give
+// q.x and |x|^2 four coordinates per instruction. Every term is an integer
+// below 2^24 for d <= 258, so the float returned equals the FP32 sum of
+// squared differences exactly.
+template <typename C>
+__device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ raw, int32_t d,
+                                                  const uint32_t *qp, int32_t qq, int64_t my_id) {
+    constexpr int WPC = (int)(sizeof(C) / 4);  // 32-bit words per piece
+    const int lane = threadIdx.x & 31, r = lane >> 3, c = lane & 7;
+    const int pieces = d / (4 * WPC);
+    int xx[8], qx[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) xx[s] = qx[s] = 0;
+    for (int p0 = 0; p0 < pieces; p0 += 8) {
+        const int pc = p0 + c;
+        C x[8];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
+            if (id >= 0 && pc < pieces)
+                x[s] = reinterpret_cast<const C *>(raw + id * (int64_t)d)[pc];
+            else
+                x[s] = C{};
+        }
+        if (pc >= pieces) continue;
+#pragma unroll
+        for (int wd = 0; wd < WPC; ++wd) {
+            const uint32_t qw = qp[pc * WPC + wd];
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const uint32_t w = reinterpret_cast<const uint32_t *>(&x[s])[wd];
+                xx[s] = (int)__dp4a(w, w, (unsigned)xx[s]);
+                qx[s] = (int)__dp4a(qw, w, (unsigned)qx[s]);
+            }
+        }
+    }
+    float out = 0.f;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+        int v = xx[s] - 2 * qx[s];
+        v += __shfl_xor_sync(FULL, v, 1);
+        v += __shfl_xor_sync(FULL, v, 2);
+        v += __shfl_xor_sync(FULL, v, 4);
+        const int mine = __shfl_sync(FULL, v, 8 * (lane & 3));
+        if ((lane >> 2) == s) out = (float)(qq + mine);
+    }
+    return out;
+}
+
+// Row pieces: 16 bytes when every row is a multiple of 16 bytes long, else
+// 4-byte words.
+template <typename T>
+__device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32_t d,
+                                                const float *qs, const uint32_t *qp, int32_t qq,
+                                                bool qint, int64_t my_id) {
+    if constexpr (sizeof(T) == 1) {
+        if (qint) return exact_rows_u8int<uint4>(raw, d, qp, qq, my_id);  // qint needs d % 16 == 0
+    }
+    if ((d * (int)sizeof(T)) % 16 == 0) return exact_rows<T, uint4>(raw, d, qs, my_id);
+    return exact_rows<T, uint32_t>(raw, d, qs, my_id);
+}
+
+// Packs an integral query with every coordinate in 0..255 (the uint8 rows'
+// integer form) from its floats qs[0, d) into qp[0, d/4) and returns whether
+// it qualifies; qq receives |q|^2. One warp; d % 16 == 0 and d <= 258.
+__device__ __forceinline__ bool pack_u8_query(const float *qs, int32_t d, uint32_t *qp, int32_t &qq) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    int32_t part = 0;
+    for (int j4 = lane; j4 < d / 4; j4 += 32) {
+        uint32_t wq = 0;
+        for (int e = 0; e < 4; ++e) {
+            const float v = qs[4 * j4 + e];
+            ok = ok && v >= 0.f && v <= 255.f && v == rintf(v);
+            const uint32_t b = ok ? (uint32_t)v : 0u;
+            wq |= b << (8 * e);
+            part += (int32_t)(b * b);
+        }
+        qp[j4] = wq;
+    }
+    const bool all = __all_sync(FULL, ok);
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
+    qq = part;
+    __syncwarp();
+    return all;
+}
+
+}  // namespace fa

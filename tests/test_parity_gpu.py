@@ -658,6 +658,54 @@ def test_rerank_uint8_rows_any_query(fa, u8_repl, shift):
             _check_topk(gi[i], gd[i], oi, od, od[-1], k, what=str(i))
 
 
+@pytest.fixture(scope="module")
+def u8_dev(fa):
+    """uint8 d=128 vectors with raw rows in HBM (internal order), where an
+    exhaustive re-rank of a top-n above 256 runs fused into the scan."""
+    mix = synth.Mixture(128, 16, 8.0, kind="u8")
+    base = mix.base(40_000)
+    q = mix.queries(24)
+    ix = fa.fa_build_index(base, fa.build_params(nlist=64, M=32, kmeans_iters=6,
+                                                 raw_location=fa.FA_RAW_DEVICE))
+    parts = ix.parts()
+    off, ids = _oracle_lists(parts)
+    return dict(base=base, q=q, ix=ix, parts=parts, off=off, ids=ids)
+
+
+@pytest.mark.parametrize("shift,sigma", [(0.0, 4.0), (0.3, 4.0), (0.0, -1000.0)])
+@pytest.mark.parametrize("n", [1000, 3000])
+def test_fused_exhaustive_rerank_matches_oracle(fa, u8_dev, n, shift, sigma):
+    """Exhaustive Algorithm 1 (eps < 0) over a top-n above 256 with raw rows
+    in HBM runs inside the selecting scan: integral queries take the integer
+    distance form, shifted ones the float form; with the threshold estimate
+    forced low (sigma -1000) every query is handed back and re-ranked by the
+    separate kernel over the device-side list. The GPU's own ADC top-n
+    (checked against the oracle's as a set) fed to the oracle's Algorithm 1
+    must give the GPU's ids, distances and mini-batch counts."""
+    s = u8_dev
+    k, npb = 10, 24
+    q = (s["q"] + np.float32(shift)).astype(np.float32)
+    probes = oracle.coarse(q, s["parts"]["centroids"], npb)
+    p = fa.search_params(rerank_n=n, rerank_batch=32, rerank_eps=-1.0, lut_prec=fa.FA_LUT_F16,
+                         lut_gemm=fa.FA_GEMM_BF16_TC)
+    fa.fa_debug_tau_sigma(sigma)
+    try:
+        gi, gd, st = fa.fa_search_ex(s["ix"], q, k, npb, p, probes=probes, stats=True)
+        pa = fa.search_params(lut_prec=fa.FA_LUT_F16, lut_gemm=fa.FA_GEMM_BF16_TC)
+        an_i, an_d = fa.fa_search_ex(s["ix"], q, n, npb, pa, probes=probes)
+    finally:
+        fa.fa_debug_tau_sigma(4.0)
+    for i in range(q.shape[0]):
+        tasks = an_i[i][an_i[i] >= 0]
+        oi, od, nb = oracle.rerank(q[i], s["parts"]["raw"], tasks, k, batch=32, eps=-1.0, beta=1)
+        if shift == 0.0:
+            assert gd[i].tolist() == od.astype(np.float32).tolist(), i
+            assert gi[i].tolist() == oi.tolist(), i
+        else:
+            _check_topk(gi[i], gd[i], oi, od, od[-1], k, what=str(i))
+        assert st[i, 2] == nb and st[i, 3] == len(tasks), (i, st[i], nb)
+
+
 @pytest.mark.parametrize("k,sigma", [(600, -1000.0), (600, 44.0), (600, 150.0),
                                      (4097, -1000.0), (4097, 125.0), (4097, 150.0)])
 def test_large_topn_exact_whatever_the_estimate(fa, f32_small, k, sigma):
