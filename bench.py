@@ -370,8 +370,13 @@ def main():
     rep_entries = gathered - uniq  # primaries are all distinct; the rest are replica entries
     ntop = max(wl["rerank_n"], k)
     lut_b = wl["M"] * 256 * (2 if lowp else 0)
-    scan_bytes = uniq * wl["M"] + rep_entries * 9 + nq * lut_b + nq * ntop * 8
     reranked = int(st[:, 3].sum())
+    # an exhaustive re-rank of uint8 rows in HBM runs inside the selecting scan:
+    # the stage then reads the re-ranked rows and writes no top-n rows
+    fused = (wl["rerank_n"] > 256 and wl["eps"] < 0 and args.raw == "device" and k <= 32
+             and not pipelined)
+    scan_bytes = uniq * wl["M"] + rep_entries * 9 + nq * lut_b + (
+        reranked * d if fused else nq * ntop * 8)
 
     if world > 1:
         dist.barrier()
@@ -412,6 +417,9 @@ def main():
         scan_kernel = "k_scan"
     elif wl["rerank_n"] > 0 and wl["eps"] >= 0:
         scan_kernel = "k_scan_cta"  # an early-stopping re-rank reads sorted rows
+    elif fused:
+        scan_kernel = ("k_scan_sel with the exhaustive re-rank fused (+ k_scan_cta and k_rerank "
+                       "for the queries it hands back)")
     else:
         scan_kernel = "k_scan_sel + k_scan_cta (the queries it hands back)"
 
@@ -475,8 +483,10 @@ def main():
                          "timed_as": ("the step's scan stage: 8 chunk launches on two streams, "
                                       "with the re-ranks of earlier chunks running beside them; "
                                       "bytes and traffic are the step's totals") if pipelined
-                         else ("the step's scan stage: k_scan_sel and the k_scan_cta launch over the "
-                               "queries it hands back; bytes and traffic are the stage's totals")
+                         else ("the step's scan stage: k_scan_sel (with the re-rank when fused) and "
+                               "the k_scan_cta launch over the queries it hands back; bytes and "
+                               "traffic are the stage's totals (candidate codes, LUT, and either "
+                               "the re-ranked raw rows or the top-n rows)")
                          if "k_scan_sel" in scan_kernel else "the step's single scan launch",
                          "kernel_src_hash": khash},
             "cpu_baseline": cpu,
@@ -738,7 +748,10 @@ def reference_arm(args, wl, rank, world):
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": wl["name"], "n": wl["n"], "nq": wl["nq"], "nlist": wl["nlist"],
-                   "M": wl["M"], "nprobe": wl["nprobe"], "k": wl["k"], "form": args.form},
+                   "M": wl["M"], "nprobe": wl["nprobe"], "k": wl["k"], "form": args.form,
+                   "rerank_n": wl["rerank_n"],
+                   "rerank": "Algorithm 1, BatchSize %d, eps %g, beta %d" % (
+                       wl["batch"], wl["eps"], wl["beta"]) if wl["rerank_n"] else "none"},
         "cpu_baseline": {"value": v, "unit": "queries/s", "kind": "oracle", "cores": cpu_cores(),
                          "sample": "%d queries per step" % ns},
         "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
