@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--workload", default="sift10m", choices=["sift10m", "zipf"],
                     help="zipf: the batching-form workload (Zipf lists, per-query nprobe)")
     ap.add_argument("--zipf-n", type=int, default=100_000_000)
+    ap.add_argument("--zipf-rerank", type=int, default=0,
+                    help="batching form: re-rank the ADC top-n exhaustively on raw rows in HBM (0 = off)")
     ap.add_argument("--serve", action="store_true",
                     help="serving form: open-loop Poisson arrivals on the Zipf-lists index")
     ap.add_argument("--rates", default="5000,10000,20000,50000,100000")
@@ -521,7 +523,9 @@ def bench_zipf(args):
     queries = z.queries(nq)
     t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
-    ix = fa.fa_build_index_lists(base, cent, prim, fa.build_params(M=M, kmeans_iters=args.kmeans_iters))
+    rr = args.zipf_rerank
+    ix = fa.fa_build_index_lists(base, cent, prim, fa.build_params(
+        M=M, kmeans_iters=args.kmeans_iters, raw_location=fa.FA_RAW_DEVICE if rr else fa.FA_RAW_NONE))
     t_build = time.perf_counter() - t0
     npq = synth.uniform_ints(16, 128, nq, tag=3)
     npq_d = torch.as_tensor(npq, device="cuda")
@@ -532,9 +536,10 @@ def bench_zipf(args):
     tc = fa.FA_GEMM_BF16_TC
 
     def params(batch, extra=0):
+        r = dict(rerank_n=rr, rerank_eps=-1.0) if rr else {}
         if batch:
-            return fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc, flags=extra)
-        return fa.search_params(flags=extra)
+            return fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc, flags=extra, **r)
+        return fa.search_params(flags=extra, **r)
 
     # autotune the batching form (tile size, threads) on host copies of a sample
     sp_t = params(True)
@@ -590,6 +595,7 @@ def bench_zipf(args):
         "config": {"workload": "ivfpq-f32unit-%dm-d96-zipf65536-M48" % (args.zipf_n // 1_000_000),
                    "n": args.zipf_n, "nq": nq, "nlist": 65536, "M": M, "k": k,
                    "nprobe": "uniform 16..128 per query", "form": "batched (tiled persistent, CUDA graph)",
+                   "rerank_n": rr, "rerank": "Algorithm 1 exhaustive (eps < 0), raw rows in HBM" if rr else "none",
                    "tuned": tuned, "l2": "flushed between timed steps"},
         "plain_fp32_qps": nq / (ms_plain / 1e3), "speedup_vs_plain": ms_plain / ms_batch,
         "recall_at_10": rec_b, "recall_at_10_plain": rec_p,
