@@ -3,7 +3,12 @@
 //   gather (3-4)       the probed lists' primary ranges and replica slices
 //   dedup (5)          each distinct vector once (probe-set rule below)
 //   ADC (6, Eq. 1)     dist(q, v) = sum_i LUT[i][code_i(v)], FP32
-//   top-n (7)          per-warp running selection, merged per CTA
+//   top-n (7)          variant 1 (n <= 256): per-warp running selection,
+//                      merged per CTA; variant 2 (n <= 16384): one CTA per
+//                      SM keeps the top-n in shared memory; variant 3 (n <=
+//                      16384, rows that may come out unsorted): two CTAs
+//                      per SM select below a sampled threshold, and can run
+//                      the exhaustive re-rank of step 8 on the result
 //
 // Layout choices (all made at index upload):
 //   * vectors are renumbered so each list's primary members are a contiguous
@@ -33,8 +38,6 @@
 
 namespace fa {
 
-constexpr int SCAN_THREADS = 256;  // warp-top-n variant (n <= 256)
-constexpr int SCAN_WARPS = SCAN_THREADS / 32;
 constexpr int BIG_THREADS = 1024;  // CTA-top-n variant (256 < n <= 16384)
 constexpr int BIG_WARPS = BIG_THREADS / 32;
 constexpr int MAX_PROBE = 512;
