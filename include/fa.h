@@ -189,7 +189,10 @@ void fa_free_index(fa_index *ix);
                                   * The results are the same either way. */
 
 /* Optional per-call trace, measured with CUDA events on the call's stream
- * (ms of device time per stage; launches = kernels this call launched). */
+ * (ms of device time per stage; launches = kernels this call launched). An
+ * exhaustive re-rank (rerank_eps < 0, k <= 32) of uint8 raw rows held in HBM
+ * runs inside the scan kernel for a top-n above 256, so its time is then part
+ * of scan_ms and post_ms covers only the queries the scan handed back. */
 typedef struct fa_search_trace {
     float coarse_ms, lut_ms, scan_ms, post_ms, total_ms;
     int32_t launches;
