@@ -39,7 +39,8 @@ import synth  # noqa: E402
 
 L2_BYTES = 126 * 1024 * 1024
 SCAN_SOURCES = ["paper_2409_16576_b300/csrc/kernels/k_scan.cu",
-                "paper_2409_16576_b300/csrc/kernels/warp_topk.cuh"]
+                "paper_2409_16576_b300/csrc/kernels/warp_topk.cuh",
+                "paper_2409_16576_b300/csrc/kernels/rerank_rows.cuh"]
 
 
 def parse():

@@ -137,9 +137,8 @@ __device__ __forceinline__ void rerank_one(
     // uint8 rows: an integral query with coordinates in 0..255 takes the
     // integer form (its bytes packed after the floats in qs)
     bool qint = false;
-    int32_t qq = 0;
     uint32_t *qp = reinterpret_cast<uint32_t *>(qs + d);
-    if (sizeof(T) == 1 && d <= 258 && d % 16 == 0) qint = pack_u8_query(qs, d, qp, qq);
+    if (sizeof(T) == 1 && d <= 258 && d % 16 == 0) qint = pack_u8_query(qs, d, qp);
     int kk = kq ? kq[qi] : k;
     kk = kk < 1 ? 1 : (kk > k ? k : kk);
     const uint64_t *tk = topkeys + qi * ntop;
@@ -176,7 +175,7 @@ __device__ __forceinline__ void rerank_one(
                 nend = end + batch < valid ? end + batch : valid;
             }
             const int64_t uid_next = task_id(ns + lane, nend);
-            const float dist = exact_rows_any<T>(raw, d, qs, qp, qq, qint, uid);
+            const float dist = exact_rows_any<T>(raw, d, qs, qp, qint, uid);
             // only keys below Q's kk-th can change Q's first kk entries (the
             // output and Eq. 3); a step with none leaves them as they are.
             // Keys carry caller ids (ties break by them, as in the oracle):

@@ -1064,16 +1064,11 @@ __device__ __forceinline__ void rerank_fused(const ScanArgs &a, const ScanPtrs &
     uint64_t *wq = reinterpret_cast<uint64_t *>(scratch);            // [SEL_WARPS][32]
     uint32_t *qp = reinterpret_cast<uint32_t *>(wq + SEL_WARPS * 32);  // [d / 4]
     if (warp == 0) {
-        int32_t qq = 0;
         bool qint = false;
-        if (a.d <= 258 && a.d % 16 == 0) qint = pack_u8_query(S.qv, a.d, qp, qq);
-        if (lane == 0) {
-            s_small[0] = (uint32_t)qq;
-            s_small[1] = qint ? 1u : 0u;
-        }
+        if (a.d <= 258 && a.d % 16 == 0) qint = pack_u8_query(S.qv, a.d, qp);
+        if (lane == 0) s_small[1] = qint ? 1u : 0u;
     }
     __syncthreads();
-    const int32_t qq = (int32_t)s_small[0];
     const bool qint = s_small[1] != 0;
     int kk = a.kq ? a.kq[qi] : a.k;
     kk = kk < 1 ? 1 : (kk > a.k ? a.k : kk);
@@ -1083,7 +1078,7 @@ __device__ __forceinline__ void rerank_fused(const ScanArgs &a, const ScanPtrs &
         const uint64_t key = i < c ? buf[i] : KEY_INF;
         const int64_t v = (i < c && key <= kth) ? (int64_t)(uint32_t)(key & 0xffffffffu) : (int64_t)-1;
         const uint8_t *raw = static_cast<const uint8_t *>(a.raw);
-        const float dist = qint ? exact_rows_u8int<uint4>(raw, a.d, qp, qq, v)
+        const float dist = qint ? exact_rows_u8int<uint4>(raw, a.d, qp, v)
                                 : exact_rows<uint8_t, uint4>(raw, a.d, S.qv, v);
         const uint64_t kthq = shfl64(Q[0], kk - 1);
         const bool maybe = v >= 0 && f2o(dist) <= (uint32_t)(kthq >> 32);

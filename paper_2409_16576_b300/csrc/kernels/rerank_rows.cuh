@@ -76,20 +76,20 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
 }
 
 // The same for uint8 rows when the query is integral with every coordinate in
-// 0..255 (its bytes packed in qp, its squared norm in qq): with integers,
-// |q - x|^2 = |q|^2 - 2 q.x + |x|^2, and four-byte dot products (dp4a) give
-// q.x and |x|^2 four coordinates per instruction. Every term is an integer
+// 0..255 (its bytes packed in qp): |x - q| per byte is exact in 8 bits
+// (__vabsdiffu4), and a four-byte dot product of it with itself (dp4a) adds
+// four squared differences per instruction. Every partial sum is an integer
 // below 2^24 for d <= 258, so the float returned equals the FP32 sum of
 // squared differences exactly.
 template <typename C>
 __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ raw, int32_t d,
-                                                  const uint32_t *qp, int32_t qq, int64_t my_id) {
+                                                  const uint32_t *qp, int64_t my_id) {
     constexpr int WPC = (int)(sizeof(C) / 4);  // 32-bit words per piece
     const int lane = threadIdx.x & 31, r = lane >> 3, c = lane & 7;
     const int pieces = d / (4 * WPC);
-    int xx[8], qx[8];
+    unsigned dd[8];
 #pragma unroll
-    for (int s = 0; s < 8; ++s) xx[s] = qx[s] = 0;
+    for (int s = 0; s < 8; ++s) dd[s] = 0u;
     for (int p0 = 0; p0 < pieces; p0 += 8) {
         const int pc = p0 + c;
         C x[8];
@@ -108,20 +108,20 @@ __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ ra
 #pragma unroll
             for (int s = 0; s < 8; ++s) {
                 const uint32_t w = reinterpret_cast<const uint32_t *>(&x[s])[wd];
-                xx[s] = (int)__dp4a(w, w, (unsigned)xx[s]);
-                qx[s] = (int)__dp4a(qw, w, (unsigned)qx[s]);
+                const unsigned ad = __vabsdiffu4(w, qw);  // |x - q| per byte, exact
+                dd[s] = __dp4a(ad, ad, dd[s]);
             }
         }
     }
     float out = 0.f;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-        int v = xx[s] - 2 * qx[s];
+        int v = (int)dd[s];
         v += __shfl_xor_sync(FULL, v, 1);
         v += __shfl_xor_sync(FULL, v, 2);
         v += __shfl_xor_sync(FULL, v, 4);
         const int mine = __shfl_sync(FULL, v, 8 * (lane & 3));
-        if ((lane >> 2) == s) out = (float)(qq + mine);
+        if ((lane >> 2) == s) out = (float)mine;
     }
     return out;
 }
@@ -130,10 +130,10 @@ __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ ra
 // 4-byte words.
 template <typename T>
 __device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32_t d,
-                                                const float *qs, const uint32_t *qp, int32_t qq,
+                                                const float *qs, const uint32_t *qp,
                                                 bool qint, int64_t my_id) {
     if constexpr (sizeof(T) == 1) {
-        if (qint) return exact_rows_u8int<uint4>(raw, d, qp, qq, my_id);  // qint needs d % 16 == 0
+        if (qint) return exact_rows_u8int<uint4>(raw, d, qp, my_id);  // qint needs d % 16 == 0
     }
     if ((d * (int)sizeof(T)) % 16 == 0) return exact_rows<T, uint4>(raw, d, qs, my_id);
     return exact_rows<T, uint32_t>(raw, d, qs, my_id);
@@ -141,25 +141,20 @@ __device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32
 
 // Packs an integral query with every coordinate in 0..255 (the uint8 rows'
 // integer form) from its floats qs[0, d) into qp[0, d/4) and returns whether
-// it qualifies; qq receives |q|^2. One warp; d % 16 == 0 and d <= 258.
-__device__ __forceinline__ bool pack_u8_query(const float *qs, int32_t d, uint32_t *qp, int32_t &qq) {
+// it qualifies. One warp; d % 16 == 0 and d <= 258.
+__device__ __forceinline__ bool pack_u8_query(const float *qs, int32_t d, uint32_t *qp) {
     const int lane = threadIdx.x & 31;
     bool ok = true;
-    int32_t part = 0;
     for (int j4 = lane; j4 < d / 4; j4 += 32) {
         uint32_t wq = 0;
         for (int e = 0; e < 4; ++e) {
             const float v = qs[4 * j4 + e];
             ok = ok && v >= 0.f && v <= 255.f && v == rintf(v);
-            const uint32_t b = ok ? (uint32_t)v : 0u;
-            wq |= b << (8 * e);
-            part += (int32_t)(b * b);
+            wq |= (ok ? (uint32_t)v : 0u) << (8 * e);
         }
         qp[j4] = wq;
     }
     const bool all = __all_sync(FULL, ok);
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(FULL, part, o);
-    qq = part;
     __syncwarp();
     return all;
 }
