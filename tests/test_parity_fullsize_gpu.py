@@ -1,6 +1,6 @@
 """Parity at the full size of the precision workload, in the launch
 configuration bench.py times: 10M uint8 d=128 vectors, 16384 lists, M 32,
-10k queries, nprobe 128, the ADC top-16384 re-ranked exhaustively on raw rows
+10k queries, nprobe 144, the ADC top-12288 re-ranked exhaustively on raw rows
 in HBM (the selecting scan with the re-rank fused into it). The oracle checks
 a sample of queries one by one; the rest of the batch runs in the same calls,
 so the sampled rows come out of the full-size launches.
@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 RTOL = 1e-4
 SAMPLE = [0, 1111, 4242, 9999]
+NPROBE, NTOP = 144, 12288  # the bench's operating point
 
 
 @pytest.fixture(scope="module")
@@ -31,7 +32,7 @@ def full(request):
     parts = ix.parts()
     off, ids = oracle.lists_from_parts(parts["primary"], parts["rep_off"], parts["rep_ids"],
                                        parts["nlist"])
-    probes = oracle.coarse(q[SAMPLE], parts["centroids"], 128)
+    probes = oracle.coarse(q[SAMPLE], parts["centroids"], NPROBE)
     return dict(fa=fa, w=w, base=base, q=q, ix=ix, parts=parts, off=off, ids=ids, probes=probes)
 
 
@@ -39,20 +40,20 @@ def _batch_probes(s):
     """Probe lists for the whole batch: the GPU's own, with the sampled rows
     replaced by the oracle's exact FP64 ones (so coarse-probe rounding cannot
     leak into the comparison of those rows)."""
-    pr = s["fa"].fa_debug_probes(s["ix"], s["q"], 128).astype(np.int32)
+    pr = s["fa"].fa_debug_probes(s["ix"], s["q"], NPROBE).astype(np.int32)
     pr[SAMPLE] = s["probes"]
     return np.ascontiguousarray(pr)
 
 
-def test_fullsize_adc_top16384_matches_oracle(full):
+def test_fullsize_adc_topn_matches_oracle(full):
     """Plain FP32 form (FP32 LUT in the scan): each sampled row's ADC
-    top-16384 equals the oracle's FP64 one except at boundary near-ties."""
+    top-12288 equals the oracle's FP64 one except at boundary near-ties."""
     s, fa = full, full["fa"]
-    n = 16384
+    n = NTOP
     pr = _batch_probes(s)
-    gi, gd = fa.fa_search_ex(s["ix"], s["q"], n, 128, fa.search_params(), probes=pr)
+    gi, gd = fa.fa_search_ex(s["ix"], s["q"], n, NPROBE, fa.search_params(), probes=pr)
     oi, od = oracle.search(s["q"][SAMPLE], s["parts"]["centroids"], s["parts"]["codebooks"],
-                           s["parts"]["codes"], s["off"], s["ids"], 128, n + 1, probes=s["probes"])
+                           s["parts"]["codes"], s["off"], s["ids"], NPROBE, n + 1, probes=s["probes"])
     for j, i in enumerate(SAMPLE):
         g_i, g_d = gi[i], np.asarray(gd[i], np.float64)
         np.testing.assert_allclose(g_d, od[j, :n], rtol=RTOL, atol=1e-3, err_msg=str(i))
@@ -68,20 +69,20 @@ def test_fullsize_adc_top16384_matches_oracle(full):
 
 def test_fullsize_recall_point_matches_oracle(full):
     """Precision form at the bench's operating point (BF16 tensor-core probe
-    and LUT, FP16 LUT, exhaustive re-rank of the ADC top-16384 fused into the
+    and LUT, FP16 LUT, exhaustive re-rank of the ADC top-12288 fused into the
     scan): each sampled row equals the oracle's Algorithm 1 applied to the
-    GPU's own ADC top-16384 (checked above for the FP32 form), bit for bit
+    GPU's own ADC top-12288 (checked above for the FP32 form), bit for bit
     (uint8 data and integral queries: exact distances are integers), with
-    every one of the 16384 handed to the re-rank."""
+    every one of the 12288 handed to the re-rank."""
     s, fa = full, full["fa"]
-    n = 16384
+    n = NTOP
     pr = _batch_probes(s)
     tc = fa.FA_GEMM_BF16_TC
     p = fa.search_params(lut_prec=fa.FA_LUT_F16, lut_gemm=tc, probe_gemm=tc, rerank_n=n,
                          rerank_batch=32, rerank_eps=-1.0, rerank_beta=1)
-    gi, gd, st = fa.fa_search_ex(s["ix"], s["q"], 10, 128, p, probes=pr, stats=True)
+    gi, gd, st = fa.fa_search_ex(s["ix"], s["q"], 10, NPROBE, p, probes=pr, stats=True)
     pa = fa.search_params(lut_prec=fa.FA_LUT_F16, lut_gemm=tc, probe_gemm=tc)
-    an_i, _ = fa.fa_search_ex(s["ix"], s["q"], n, 128, pa, probes=pr)
+    an_i, _ = fa.fa_search_ex(s["ix"], s["q"], n, NPROBE, pa, probes=pr)
     raw = s["parts"]["raw"]
     for i in SAMPLE:
         tasks = an_i[i][an_i[i] >= 0]
