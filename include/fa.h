@@ -369,7 +369,8 @@ fa_status fa_debug_tau_sigma(float sigma);
  * allocator or a fixed budget, and latency-bound code that cannot afford the
  * synchronisation and unbounded time of a cudaMalloc in the middle of its work.
  *
- * queries[nq][d] and centroids[nlist][d] are float32 device pointers;
+ * queries[nq][d] and centroids[nlist][d] are float32 device pointers on the
+ * current device (make the device that owns the buffers current first);
  * probes[nq][nprobe] (int32, device) receives each query's nprobe nearest
  * centroids by squared L2, ascending by (distance, centroid index), computed
  * by the same kernels as the coarse probe of fa_search. The work is enqueued

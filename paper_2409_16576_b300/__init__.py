@@ -394,19 +394,40 @@ def fa_debug_lut(ix: Index, query, params=None) -> np.ndarray:
 def fa_coarse_probe_noalloc(queries, centroids, nprobe: int, out=None, stream=None, nlist=None):
     """Coarse probe that allocates nothing inside the library, for callers
     that cannot allocate device memory. CUDA torch tensors queries [nq][d] and
-    centroids [nlist][d] (float32); output int32 [nq][nprobe] in ``out`` (a
-    caller that cannot allocate passes its own; None lets torch allocate one
-    here). Runs on ``stream`` (default: torch's current stream). ``nlist``
-    overrides the row count passed to the C call (used to test its checks)."""
+    centroids [nlist][d] (float32, contiguous, on one device); output int32
+    [nq][nprobe] in ``out`` (a caller that cannot allocate passes its own;
+    None lets torch allocate one here). Runs on ``stream`` (default: torch's
+    current stream) with the tensors' device current. ``nlist`` overrides the
+    row count passed to the C call (used to test its checks; it may only be
+    smaller than the centroid rows or rejected by the library before any
+    launch). Raises ValueError for tensors the kernels cannot read safely."""
     import torch
+    for name, t in (("queries", queries), ("centroids", centroids)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise ValueError("%s must be a CUDA tensor" % name)
+        if t.dtype != torch.float32 or not t.is_contiguous() or t.dim() != 2:
+            raise ValueError("%s must be a contiguous 2-D float32 tensor" % name)
+    dev = queries.device
+    if centroids.device != dev:
+        raise ValueError("queries and centroids must be on the same device")
     nq, d = queries.shape
-    nl = centroids.shape[0] if nlist is None else nlist
+    if centroids.shape[1] != d:
+        raise ValueError("centroids have d=%d, queries d=%d" % (centroids.shape[1], d))
+    nl = centroids.shape[0] if nlist is None else int(nlist)
+    if nlist is not None and nl > centroids.shape[0] and nl <= (4 << 20):
+        # within the library's capacity the kernels would read nl rows
+        raise ValueError("nlist above the centroid rows")
     if out is None:
-        out = torch.empty((nq, nprobe), dtype=torch.int32, device=queries.device)
-    if stream is None:
-        stream = torch.cuda.current_stream(queries.device).cuda_stream
-    _check(_lib.fa_coarse_probe_noalloc(_ptr(queries), nq, d, _ptr(centroids), nl, nprobe,
-                                        _ptr(out), stream))
+        out = torch.empty((nq, nprobe), dtype=torch.int32, device=dev)
+    if not (isinstance(out, torch.Tensor) and out.device == dev and out.dtype == torch.int32
+            and out.is_contiguous() and tuple(out.shape) == (nq, nprobe)):
+        raise ValueError("out must be a contiguous int32 CUDA tensor of shape (nq, nprobe) "
+                         "on the queries' device")
+    with torch.cuda.device(dev):
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        _check(_lib.fa_coarse_probe_noalloc(_ptr(queries), nq, d, _ptr(centroids), nl, nprobe,
+                                            _ptr(out), stream))
     return out
 
 

@@ -301,5 +301,7 @@ void launch_debug_candidates(const DeviceIndex &ix, const int32_t *probes, int32
                              uint32_t *out, uint32_t *count, uint32_t cap, cudaStream_t st);
 
 int num_sms(int device);
+// SM count of the current device (every launch runs with the index's device current)
+int cur_num_sms();
 
 }  // namespace fa

@@ -127,6 +127,8 @@ static void select_rows(const float *D, int64_t ldd, int64_t nrows, int32_t nc, 
 static void l2_topn(const float *X, int64_t nx, int32_t d, const float *C, int32_t nc,
                     int32_t ntop, float *scratch, int64_t scratch_rows, int32_t *out_ids,
                     int32_t out_stride, float *out_d2, cudaStream_t st) {
+    // a block of rows spans at most 65535 tiles in y (the grid's y limit)
+    if (scratch_rows > (int64_t)65535 * TILE) scratch_rows = (int64_t)65535 * TILE;
     for (int64_t r0 = 0; r0 < nx; r0 += scratch_rows) {
         const int64_t rows = nx - r0 < scratch_rows ? nx - r0 : scratch_rows;
         const dim3 grid((unsigned)((nc + TILE - 1) / TILE), (unsigned)((rows + TILE - 1) / TILE));
@@ -278,6 +280,12 @@ int num_sms(int device) {
         cached[device] = v;
     }
     return cached[device];
+}
+
+int cur_num_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    return num_sms(dev);
 }
 
 // ---------------------------------------------------------------------------

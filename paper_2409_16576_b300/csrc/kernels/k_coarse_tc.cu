@@ -377,7 +377,7 @@ void launch_coarse_tc(const DeviceIndex &ix, const float *q, int64_t rows, int32
     a.nlist = ix.nlist;
     a.nt = ix.tc_ntiles;
     a.total = (rows + PQ - 1) / PQ * (int64_t)a.nt;
-    a.per = (int32_t)((a.total + num_sms(0) - 1) / num_sms(0));
+    a.per = (int32_t)((a.total + cur_num_sms() - 1) / cur_num_sms());
     a.D = D;
     a.ldd = coarse_tc_ldd(ix.nlist);
     a.err = err;

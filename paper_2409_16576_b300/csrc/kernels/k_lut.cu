@@ -111,7 +111,7 @@ void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int pr
     }
     const int smem = (ix.M * 256 + ix.d + 2 * ix.M) * 4;
     FA_CHECK_CUDA(cudaFuncSetAttribute(k_lut_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    const int grid = (int)std::min<int64_t>(nq, (int64_t)num_sms(0) * 4);
+    const int grid = (int)std::min<int64_t>(nq, (int64_t)cur_num_sms() * 4);
     k_lut_simt<<<grid, 256, smem, st>>>(q, nq, ix.d, ix.codebooks, ix.M, prec, lut, lut_scale);
     FA_CHECK_CUDA(cudaGetLastError());
 }

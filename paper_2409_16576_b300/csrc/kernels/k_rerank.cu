@@ -273,7 +273,7 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
                             int32_t *stats, int warps, uint32_t *ctr, const int32_t *qlist,
                             const uint32_t *qcount, cudaStream_t st) {
     // persistent: two one-warp CTAs per SM pull queries; else one warp per query
-    const dim3 grid(ctr ? (unsigned)std::min<int64_t>(nq, 2 * num_sms(0))
+    const dim3 grid(ctr ? (unsigned)std::min<int64_t>(nq, 2 * cur_num_sms())
                         : (unsigned)((nq + warps - 1) / warps));
     if (ctr) FA_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 4, st));
     const int smem = warps * (ix.d + ix.d / 4 + 1) * 4;

@@ -1243,7 +1243,7 @@ static int scan_grid(const ScanLaunch &l, int smem_total) {
     if (!l.persistent) return (int)(l.nq < (int64_t)INT32_MAX ? l.nq : INT32_MAX);
     int per_sm = (227 * 1024) / (smem_total + 1024);
     per_sm = per_sm < 1 ? 1 : (per_sm > 8 ? 8 : per_sm);
-    int grid = num_sms(0) * per_sm;
+    int grid = cur_num_sms() * per_sm;
     if (l.tile_prefix) return grid;  // tiles outnumber queries
     return (int64_t)grid > l.nq ? (int)l.nq : grid;
 }
@@ -1299,7 +1299,7 @@ static bool launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
             c.fuse_rr = fused ? 1 : 0;
             FA_CHECK_CUDA(cudaMemsetAsync(a.tile_ctr, 0, 4 * sizeof(uint32_t), st));
             set_smem(k_scan_sel<M, W>, smem_sel);
-            k_scan_sel<M, W><<<2 * num_sms(0), SEL_THREADS, smem_sel, st>>>(c, sch_max);
+            k_scan_sel<M, W><<<2 * cur_num_sms(), SEL_THREADS, smem_sel, st>>>(c, sch_max);
             FA_CHECK_CUDA(cudaGetLastError());
             // variant 2 over the redo list (its length is on the device)
             b.order = a.redo;
@@ -1318,7 +1318,7 @@ static bool launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
         const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, (NP + NB) * 8);
         FA_REQUIRE(plan.total <= budget, FA_ERR_ARG,
                    "scan shared memory above 227 KB (top-n too large for this M)");
-        const int grid = sel ? num_sms(0) : scan_grid(l, plan.total);
+        const int grid = sel ? cur_num_sms() : scan_grid(l, plan.total);
         set_smem(k_scan_cta<M, W>, plan.total);
         k_scan_cta<M, W><<<grid, BIG_THREADS, plan.total, st>>>(b, NP, NB);
     }

@@ -14,10 +14,10 @@ from scipy.spatial.distance import cdist
 
 import oracle
 import synth
+from parity_checks import (RTOL, _adc_ref, _check_topk, _expanded_magnitude, _l2_ref,
+                           _lowp_adc_bound, _lowp_lut_bound)
 
 pytestmark = pytest.mark.gpu
-
-RTOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -32,25 +32,6 @@ def fa():
 def _oracle_lists(parts):
     return oracle.lists_from_parts(parts["primary"], parts["rep_off"], parts["rep_ids"],
                                    parts["nlist"])
-
-
-def _check_topk(gi, gd, oi, od, o_next, k, rtol=RTOL, what=""):
-    """gi/gd: GPU ids/dists of one query; oi/od: oracle's top-k; o_next: the
-    oracle's (k+1)-th distance (inf if none)."""
-    gd = np.asarray(gd, dtype=np.float64)
-    fin = np.isfinite(od)
-    assert np.array_equal(np.isfinite(gd), fin), what
-    np.testing.assert_allclose(gd[fin], od[fin], rtol=rtol, atol=1e-3, err_msg=what)
-    assert np.all(gi[~fin] == -1), what
-    # ids: equal sets unless the boundary is a near tie
-    kth = od[fin][-1] if fin.any() else np.inf
-    if set(gi[fin].tolist()) != set(oi[fin].tolist()):
-        assert np.isfinite(o_next) and abs(o_next - kth) <= rtol * max(kth, 1.0) + 1e-3, what
-        # every id that is not in the oracle's set must sit at the boundary distance
-        extra = set(gi[fin].tolist()) - set(oi[fin].tolist())
-        for t, x in enumerate(gi):
-            if x in extra:
-                assert abs(gd[t] - kth) <= rtol * max(kth, 1.0) + 1e-3, what
 
 
 # ---------------------------------------------------------------------------
@@ -113,14 +94,6 @@ def test_lut_f32_matches_oracle(fa, f32_small):
         got = fa.fa_debug_lut(s["ix"], s["q"][i])
         ref = oracle.lut(s["q"][i], s["parts"]["codebooks"])
         np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-2)
-
-
-def _expanded_magnitude(q, cb):
-    """|q_m|^2 + |C_m[c]|^2 per entry: the size of the terms the expanded
-    (tensor-core) form adds, which bounds its rounding."""
-    M, _, dsub = cb.shape
-    qn = np.array([(q[m * dsub:(m + 1) * dsub].astype(np.float64) ** 2).sum() for m in range(M)])
-    return qn[:, None] + (cb.astype(np.float64) ** 2).sum(2)
 
 
 @pytest.mark.parametrize("which", ["f32", "u8"])
@@ -286,7 +259,8 @@ def test_search_given_probes_matches_oracle(fa, f32_small, k):
     s = f32_small
     gi, gd, oi, od = _search_vs_oracle(fa, s, k, 8)
     for i in range(gi.shape[0]):
-        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
+        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i),
+                    ref_of=_adc_ref(s["q"][i], s["parts"]))
         # rows ascending by (distance, id)
         fin = np.isfinite(gd[i])
         keys = list(zip(gd[i][fin].tolist(), gi[i][fin].tolist()))
@@ -295,9 +269,11 @@ def test_search_given_probes_matches_oracle(fa, f32_small, k):
 
 @pytest.mark.parametrize("k", [10, 600])
 def test_search_with_replication_matches_oracle(fa, u8_repl, k):
-    gi, gd, oi, od = _search_vs_oracle(fa, u8_repl, k, 16)
+    s = u8_repl
+    gi, gd, oi, od = _search_vs_oracle(fa, s, k, 16)
     for i in range(gi.shape[0]):
-        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
+        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i),
+                    ref_of=_adc_ref(s["q"][i], s["parts"]))
         assert len(set(gi[i].tolist())) == k  # no duplicate ids
 
 
@@ -311,7 +287,8 @@ def test_large_topn_matches_oracle(fa, f32_small, k):
     s = f32_small
     gi, gd, oi, od = _search_vs_oracle(fa, s, k, 64, nq=6)
     for i in range(gi.shape[0]):
-        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
+        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i),
+                    ref_of=_adc_ref(s["q"][i], s["parts"]))
         fin = np.isfinite(gd[i])
         keys = list(zip(gd[i][fin].tolist(), gi[i][fin].tolist()))
         assert keys == sorted(keys)
@@ -396,7 +373,8 @@ def test_tiled_batching_form_on_uneven_lists(fa, zipf_small, k):
         oi, od = oracle.search(s["q"][i:i + 1], s["parts"]["centroids"], s["parts"]["codebooks"],
                                s["parts"]["codes"], s["off"], s["ids"], int(npq[i]), k + 1,
                                probes=probes[i:i + 1, :npq[i]])
-        _check_topk(tiled[0][i], tiled[1][i], oi[0, :k], od[0, :k], od[0, k], k, what=str(i))
+        _check_topk(tiled[0][i], tiled[1][i], oi[0, :k], od[0, :k], od[0, k], k, what=str(i),
+                    ref_of=_adc_ref(s["q"][i], s["parts"]))
 
 
 @pytest.mark.parametrize("flags", ["eager_graph", "tiled_graph"])
@@ -439,7 +417,8 @@ def test_build_with_given_lists(fa):
     gi, gd = fa.fa_search_ex(ix, q, 10, 8, probes=probes)
     oi, od = oracle.search(q, cent, parts["codebooks"], parts["codes"], off, ids, 8, 11, probes=probes)
     for i in range(q.shape[0]):
-        _check_topk(gi[i], gd[i], oi[i, :10], od[i, :10], od[i, 10], 10, what=str(i))
+        _check_topk(gi[i], gd[i], oi[i, :10], od[i, :10], od[i, 10], 10, what=str(i),
+                    ref_of=_adc_ref(q[i], parts))
 
 
 def _serve_all(srv, n):
@@ -479,6 +458,40 @@ def test_serving_result_same_alone_and_in_the_mix(fa, u8_repl, lowp):
         ai, ad = fa.fa_search_ex(s["ix"], q[i:i + 1], int(ks[i]), int(nps[i]), p)
         assert np.array_equal(ids[:ks[i]], ai[0]) and np.array_equal(dist[:ks[i]], ad[0]), i
         assert np.all(ids[ks[i]:] == -1)
+    # each request against the oracle: the served row equals the row searched
+    # alone (above), and that row is checked here against the FP64 oracle
+    compared = 0
+    for i in range(n):
+        ids, dist, _ = got[int(rid[i])]
+        k, npb = int(ks[i]), int(nps[i])
+        gprobe = fa.fa_debug_probes(s["ix"], q[i:i + 1], npb, p)[0]
+        oprobe = oracle.coarse(q[i:i + 1], s["parts"]["centroids"], npb)[0]
+        if sorted(gprobe.tolist()) != sorted(oprobe.tolist()):
+            continue  # a near tie in the probe set changes the scanned lists
+        if not lowp:
+            oi, od = oracle.search(q[i:i + 1], s["parts"]["centroids"], s["parts"]["codebooks"],
+                                   s["parts"]["codes"], s["off"], s["ids"], npb, k + 1,
+                                   probes=oprobe[None])
+            _check_topk(ids[:k], dist[:k], oi[0, :k], od[0, :k], od[0, k], k, what=str(i),
+                        ref_of=_adc_ref(q[i], s["parts"]))
+        else:
+            # the FP16 table's ADC top-50 (each distance within the table's
+            # error bound of the oracle's), handed to the oracle's Algorithm 1,
+            # must give the served ids and exact distances
+            pa = fa.search_params(lut_prec=fa.FA_LUT_F16, lut_gemm=fa.FA_GEMM_BF16_TC,
+                                  probe_gemm=fa.FA_GEMM_BF16_TC)
+            an_i, an_d = fa.fa_search_ex(s["ix"], q[i:i + 1], 50, npb, pa, probes=gprobe[None])
+            tasks = an_i[0][an_i[0] >= 0]
+            bound = _lowp_adc_bound(q[i], s["parts"], "F16", True)(tasks)
+            ref = _adc_ref(q[i], s["parts"])(tasks)
+            assert np.all(np.abs(an_d[0][:len(tasks)] - ref) <= bound), i
+            if len(np.unique(an_d[0][:len(tasks)])) != len(tasks):
+                continue  # equal ADC keys: the re-rank's order among them is the GPU's
+            oi, od, _ = oracle.rerank(q[i], s["parts"]["raw"], tasks, k, batch=32, eps=0.0, beta=2)
+            assert ids[:k].tolist() == oi.tolist(), i
+            assert dist[:k].tolist() == od.astype(np.float32).tolist(), i
+        compared += 1
+    assert compared >= n // 2, compared
 
 
 def test_serving_admits_by_slots(fa, f32_small):
@@ -514,7 +527,8 @@ def test_per_query_k_and_nprobe(fa, f32_small):
         gprobe = fa.fa_debug_probes(s["ix"], q[i:i + 1], 8)[0]
         if gprobe[:npq[i]].tolist() != probes[i, :npq[i]].tolist():
             continue  # a near tie in the probe order changes the scanned lists
-        _check_topk(gi[i, :kq[i]], gd[i, :kq[i]], oi[0, :kq[i]], od[0, :kq[i]], od[0, kq[i]], kq[i])
+        _check_topk(gi[i, :kq[i]], gd[i, :kq[i]], oi[0, :kq[i]], od[0, :kq[i]], od[0, kq[i]], kq[i],
+                    ref_of=_adc_ref(q[i], s["parts"]))
         assert np.all(gi[i, kq[i]:] == -1) and np.all(np.isinf(gd[i, kq[i]:]))
 
 
@@ -555,7 +569,9 @@ def test_identity_codebook_full_probe_equals_knn(fa, M):
     gi, gd = fa.fa_search(ix, q, 10, 16)
     ti, td = oracle.knn(q, x, 11)
     for i in range(q.shape[0]):
-        _check_topk(gi[i], gd[i], ti[i, :10], td[i, :10], td[i, 10], 10, what="M%d q%d" % (M, i))
+        # the identity codebook makes the ADC distance the exact distance
+        _check_topk(gi[i], gd[i], ti[i, :10], td[i, :10], td[i, 10], 10, what="M%d q%d" % (M, i),
+                    ref_of=_l2_ref(q[i], x))
 
 
 def test_fewer_candidates_than_k_and_empty_lists(fa):
@@ -655,7 +671,8 @@ def test_rerank_uint8_rows_any_query(fa, u8_repl, shift):
             assert gd[i].tolist() == od.astype(np.float32).tolist(), i
             assert gi[i].tolist() == oi.tolist(), i
         else:
-            _check_topk(gi[i], gd[i], oi, od, od[-1], k, what=str(i))
+            _check_topk(gi[i], gd[i], oi, od, od[-1], k, what=str(i),
+                        ref_of=_l2_ref(q[i], s["parts"]["raw"]))
 
 
 @pytest.fixture(scope="module")
@@ -702,7 +719,8 @@ def test_fused_exhaustive_rerank_matches_oracle(fa, u8_dev, n, shift, sigma):
             assert gd[i].tolist() == od.astype(np.float32).tolist(), i
             assert gi[i].tolist() == oi.tolist(), i
         else:
-            _check_topk(gi[i], gd[i], oi, od, od[-1], k, what=str(i))
+            _check_topk(gi[i], gd[i], oi, od, od[-1], k, what=str(i),
+                        ref_of=_l2_ref(q[i], s["parts"]["raw"]))
         assert st[i, 2] == nb and st[i, 3] == len(tasks), (i, st[i], nb)
 
 
@@ -723,7 +741,8 @@ def test_large_topn_exact_whatever_the_estimate(fa, f32_small, k, sigma):
     finally:
         fa.fa_debug_tau_sigma(4.0)
     for i in range(gi.shape[0]):
-        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i))
+        _check_topk(gi[i], gd[i], oi[i, :k], od[i, :k], od[i, k], k, what=str(i),
+                    ref_of=_adc_ref(s["q"][i], s["parts"]))
 
 
 @pytest.mark.parametrize("eps,beta,n", [(-1.0, 1, 8192), (-1.0, 1, 16384), (0.0, 2, 16384)])
@@ -743,7 +762,8 @@ def test_deep_rerank_matches_oracle(fa, f32_small, eps, beta, n):
     ao_i, ao_d = oracle.search(q, s["parts"]["centroids"], s["parts"]["codebooks"],
                                s["parts"]["codes"], s["off"], s["ids"], npb, n + 1, probes=probes)
     for i in range(q.shape[0]):
-        _check_topk(an_i[i], an_d[i], ao_i[i, :n], ao_d[i, :n], ao_d[i, n], n, what=str(i))
+        _check_topk(an_i[i], an_d[i], ao_i[i, :n], ao_d[i, :n], ao_d[i, n], n, what=str(i),
+                    ref_of=_adc_ref(q[i], s["parts"]))
         tasks = an_i[i][an_i[i] >= 0]
         oi, od, nb = oracle.rerank(q[i], s["parts"]["raw"], tasks, k, batch=32, eps=eps, beta=beta)
         assert gi[i].tolist() == oi.tolist(), i
