@@ -2,13 +2,14 @@
 
 Workload (default): 10M uint8 d=128 vectors from a 64-component Gaussian
 mixture clipped to 0..255 (SIFT-like, the paper's Table 1 shape), 16384 lists,
-PQ M=32 x 256, 10k queries, nprobe 64, k 10, the precision form (FP16 LUT with
-a per-query scale, exact FP32 re-rank of the ADC top 10k = 100 in mini-batches
-of 32 with Algorithm 1, raw vectors in pinned host memory). recall@10 is
-measured on a 1k-query subsample in every run and reported beside the QPS;
-``--sweep`` prints the recall/QPS curve over nprobe, n and Algorithm 1's
-parameters (on this isotropic mixture recall@10 stays far below 0.9 at these
-PQ settings, see the design notes).
+PQ M=32 x 256, 10k queries, k 10. Operating point (default): nprobe 144 and an
+exhaustive Algorithm 1 re-rank (eps < 0) of the ADC top-12288 on raw rows held
+in HBM, the fastest measured point whose recall@10 is safely above 0.9 (the
+configured nprobe 64 with a re-rank of the top 10k = 100 reaches 0.18 on this
+data). ``value`` is the precision form (BF16 tensor-core probe and LUT, FP16
+table); the plain FP32 form runs on the same index and point beside it.
+recall@10 is measured on a 1k-query subsample in every run; ``--sweep`` prints
+the recall/QPS curve over nprobe, n and Algorithm 1's parameters.
 
 A step is one batch of 10k queries through the whole path: coarse probe, LUT,
 gather + dedup, ADC scan + top-n, re-rank. ``value`` is queries per second
@@ -38,6 +39,7 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 L2_BYTES = 126 * 1024 * 1024
+NOMINAL_HBM_GBS = 7700.0  # B300 HBM3e nominal; the measured copy bandwidth is the roofline peak
 SCAN_SOURCES = ["paper_2409_16576_b300/csrc/kernels/k_scan.cu",
                 "paper_2409_16576_b300/csrc/kernels/warp_topk.cuh",
                 "paper_2409_16576_b300/csrc/kernels/rerank_rows.cuh"]
@@ -267,6 +269,36 @@ def exact_dists(base, q, ids):
     return out
 
 
+def err_vs_fp64(fa, oracle, ix, parts, base, queries, nprobe, sp, found_ids, found_dist, ns=16):
+    """Error of the GPU's distances against the FP64 oracle on the first ns
+    queries: the form's ADC distances (its table precision, re-rank off, top
+    100) against the oracle's ADC of the same ids (Eq. 1 in FP64), and the
+    re-ranked distances of the bench's own results against the oracle's exact
+    squared L2 of the same ids. Both as the largest relative error."""
+    import ctypes
+    p = fa.fa_search_params.from_buffer_copy(sp)
+    p.rerank_n = 0
+    p.flags &= ~fa.FA_GRAPH
+    q = np.ascontiguousarray(queries[:ns])
+    gi, gd = fa.fa_search_ex(ix, q, 100, nprobe, p)
+    adc = 0.0
+    for i in range(ns):
+        ok = gi[i] >= 0
+        ref = oracle.adc(oracle.lut(q[i], parts["codebooks"]), parts["codes"],
+                         gi[i][ok].astype(np.uint32))
+        adc = max(adc, float(np.max(np.abs(gd[i][ok] - ref) / np.maximum(ref, 1e-30))))
+    out = {"adc_max_rel": adc, "sample": "first %d queries, ADC top-100 of the form's table" % ns}
+    if sp.rerank_n > 0:
+        rr = 0.0
+        for i in range(ns):
+            ok = found_ids[i] >= 0
+            ref = oracle.exact_l2(q[i], base, found_ids[i][ok].astype(np.int64))
+            rr = max(rr, float(np.max(np.abs(found_dist[i][ok] - ref) / np.maximum(ref, 1e-30))))
+        out["rerank_max_rel"] = rr
+        out["rerank"] = "exact (equal to FP64)" if rr == 0.0 else "FP32"
+    return out
+
+
 def search_params(fa, form, wl, persistent=False, serial=False):
     """plain: FP32 everywhere (SIMT coarse probe, FP32 LUT built in the scan CTA).
     lowp: BF16 tensor-core coarse probe and LUT GEMMs, FP16 (or FP8) LUT.
@@ -412,6 +444,9 @@ def main():
     e2e_value = world * nq / (max_over_ranks(statistics.mean(e2e_ms), world, "cuda") / 1e3)
 
     recall = recall_of(oracle, base, queries, oid.cpu().numpy(), gt) if gt is not None else None
+    parts = ix.parts()
+    err = err_vs_fp64(fa, oracle, ix, parts, base, queries, wl["nprobe"], sp, oid[:16].cpu().numpy(),
+                      odist[:16].cpu().numpy()) if rank == 0 else None
 
     # ---- roofline of the scan (dominant kernel) ----
     peak, peak_src = measured_peaks()
@@ -447,7 +482,6 @@ def main():
     # ---- CPU baseline: the oracle as it stands on a bounded sample ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        parts = ix.parts()
         ns = args.cpu_sample or 100
         secs, cores, _ = run_oracle_sample(wl, base, queries, parts, ns)
         cpu = {"value": ns / secs, "unit": "queries/s", "cores": cores, "kind": "oracle",
@@ -483,12 +517,13 @@ def main():
                            wl["batch"], wl["eps"], wl["beta"]) if wl["rerank_n"] else "none",
                        "raw_vectors": ("HBM" if args.raw == "device" else "pinned host")
                        if wl["rerank_n"] else "none",
-                       "launch": "autotuned: %d threads/CTA, %d chunk(s) in flight per warp, %s" % (
-                           tuned["threads"], tuned["ilp"],
-                           "persistent" if (tuned["persistent"] or args.persistent) else "one CTA per query"),
-                       "l2": "flushed between timed steps (256 MB write); codes 320 MB > L2",
                        "parallelism": "replicas" if world > 1 else "single"},
+            "l2": "flushed between timed steps (256 MB write); codes 320 MB > L2",
+            "launch": "autotuned: %d threads/CTA, %d chunk(s) in flight per warp, %s" % (
+                tuned["threads"], tuned["ilp"],
+                "persistent" if (tuned["persistent"] or args.persistent) else "one CTA per query"),
             "recall_at_10": recall,
+            "err_vs_fp64": err,
             "candidates_per_query": uniq / nq,
             "reranked_per_query": reranked / nq,
             "stage_ms": {"coarse": statistics.mean(t.coarse_ms for t in traces),
@@ -499,6 +534,7 @@ def main():
             "batching_form": batching,
             "roofline": {"bound": "hbm", "kernel": scan_kernel, "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                          "traffic": traffic, "algorithmic_bytes_per_launch": scan_bytes,
                          "launches_per_step": 8 if pipelined else (2 if "k_scan_sel" in scan_kernel else 1),
                          "timed_as": ("the step's scan stage: 8 chunk launches on two streams, "
@@ -776,11 +812,14 @@ def reference_arm(args, wl, rank, world):
         "value": v, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wl["name"], "n": wl["n"], "nq": wl["nq"], "nlist": wl["nlist"],
-                   "M": wl["M"], "nprobe": wl["nprobe"], "k": wl["k"], "form": args.form,
-                   "rerank_n": wl["rerank_n"],
+        "config": {"workload": wl["name"], "n": wl["n"], "nq": wl["nq"], "d": 128,
+                   "nlist": wl["nlist"], "M": wl["M"], "nprobe": wl["nprobe"], "k": wl["k"],
+                   "form": args.form, "rerank_n": wl["rerank_n"],
                    "rerank": "Algorithm 1, BatchSize %d, eps %g, beta %d" % (
-                       wl["batch"], wl["eps"], wl["beta"]) if wl["rerank_n"] else "none"},
+                       wl["batch"], wl["eps"], wl["beta"]) if wl["rerank_n"] else "none",
+                   "raw_vectors": ("HBM" if args.raw == "device" else "pinned host")
+                   if wl["rerank_n"] else "none",
+                   "parallelism": "single"},
         "cpu_baseline": {"value": v, "unit": "queries/s", "kind": "oracle", "cores": cpu_cores(),
                          "sample": "%d queries per step" % ns},
         "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -64,3 +64,17 @@ def test_noalloc_probe_rejects_oversized_and_bad_arguments(fa):
     assert e.value.status == fa.FA_ERR_ARG
     out = fa.fa_coarse_probe_noalloc(q[:0], c, 4)
     assert out.shape == (0, 4)
+
+
+def test_noalloc_probe_single_list_many_queries(fa):
+    """One list and more query rows than one grid of distance tiles spans in
+    y (4194240 rows): the probe runs in row blocks and every query gets list 0."""
+    import torch
+    nq, d = (4 << 20) + 77, 4
+    q = torch.ones((nq, d), dtype=torch.float32, device="cuda")
+    c = torch.zeros((1, d), dtype=torch.float32, device="cuda")
+    out = torch.full((nq, 1), -7, dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        fa.fa_coarse_probe_noalloc(q, c, 1, out=out)
+        torch.cuda.synchronize()
+        assert int((out != 0).sum().item()) == 0
