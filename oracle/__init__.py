@@ -22,6 +22,10 @@ function cites the step of the paper it follows:
   ``search``      the pipeline (pinned: identity codebook + nprobe = nlist
                   equals brute-force k-NN)
   ``knn``         brute-force ground truth (pinned: numpy on tiny inputs)
+
+Every step also takes ``metric=IP`` (the negated inner product -<q, x>, the
+second metric of the SPACEV-like workload) and int8 raw rows; those forms are
+pinned against numpy inner products, an identity codebook and brute force.
 """
 from __future__ import annotations
 
@@ -37,6 +41,10 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 RAW_F32 = 0
 RAW_U8 = 1
+RAW_I8 = 2
+
+L2 = 0   # squared L2 distance
+IP = 1   # negated inner product: -<q, x> (smallest first)
 
 
 def build(force: bool = False) -> str:
@@ -73,6 +81,15 @@ def lib():
         _lib.or_knn.argtypes = [P, i64, P, i32, i64, i32, i32, P, P]
         _lib.or_num_threads.restype = i32
         _lib.or_set_threads.argtypes = [i32]
+        _lib.or_coarse_m.argtypes = [P, i64, i32, P, i32, i32, P, P, i32]
+        _lib.or_lut_m.argtypes = [P, i32, i32, P, P, i32]
+        _lib.or_exact_m.argtypes = [P, i32, P, i32, P, i64, P, i32]
+        _lib.or_rerank_m.argtypes = [P, i32, P, i32, P, i32, i32, i32, f32, i32, P, P, i32]
+        _lib.or_rerank_m.restype = i32
+        _lib.or_search_m.argtypes = [P, i64, i32, P, i32, i32, P, P, P, P, P, i32, i32, i32, P,
+                                     i32, i32, f32, i32, P, P, P, i32]
+        _lib.or_search_m.restype = i32
+        _lib.or_knn_m.argtypes = [P, i64, P, i32, i64, i32, i32, P, P, i32]
     return _lib
 
 
@@ -93,7 +110,11 @@ def set_threads(t: int) -> None:
 
 
 def raw_kind(raw: np.ndarray) -> int:
-    return RAW_U8 if raw.dtype == np.uint8 else RAW_F32
+    if raw.dtype == np.uint8:
+        return RAW_U8
+    if raw.dtype == np.int8:
+        return RAW_I8
+    return RAW_F32
 
 
 # ---------------------------------------------------------------------------
@@ -126,23 +147,23 @@ def lists_from_parts(primary, rep_off, rep_ids, nlist):
 # step wrappers
 # ---------------------------------------------------------------------------
 
-def coarse(queries, centroids, nprobe, with_d2=False):
+def coarse(queries, centroids, nprobe, with_d2=False, metric=L2):
     q = _c(queries, np.float32)
     c = _c(centroids, np.float32)
     nq, d = q.shape
     nlist = c.shape[0]
     probes = np.empty((nq, nprobe), dtype=np.int32)
     d2 = np.empty((nq, nprobe), dtype=np.float64) if with_d2 else None
-    lib().or_coarse(_p(q), nq, d, _p(c), nlist, nprobe, _p(probes), _p(d2))
+    lib().or_coarse_m(_p(q), nq, d, _p(c), nlist, nprobe, _p(probes), _p(d2), metric)
     return (probes, d2) if with_d2 else probes
 
 
-def lut(query, codebooks):
+def lut(query, codebooks, metric=L2):
     q = _c(query, np.float32).reshape(-1)
     cb = _c(codebooks, np.float32)
     M = cb.shape[0]
     out = np.empty((M, 256), dtype=np.float64)
-    lib().or_lut(_p(q), q.shape[0], M, _p(cb), _p(out))
+    lib().or_lut_m(_p(q), q.shape[0], M, _p(cb), _p(out), metric)
     return out
 
 
@@ -177,29 +198,34 @@ def topn(dist, ids, n):
     return oi, od
 
 
-def exact_l2(query, raw, ids):
+def exact(query, raw, ids, metric=L2):
+    """Exact distances of the given rows: squared L2, or -<q, x> for IP."""
     q = _c(query, np.float32).reshape(-1)
     r = np.ascontiguousarray(raw)
     ii = _c(ids, np.int64)
     out = np.empty(ii.shape[0], dtype=np.float64)
-    lib().or_exact_l2(_p(q), q.shape[0], _p(r), raw_kind(r), _p(ii), ii.shape[0], _p(out))
+    lib().or_exact_m(_p(q), q.shape[0], _p(r), raw_kind(r), _p(ii), ii.shape[0], _p(out), metric)
     return out
 
 
-def rerank(query, raw, tasks, k, batch=32, eps=0.0, beta=2):
+def exact_l2(query, raw, ids):
+    return exact(query, raw, ids, L2)
+
+
+def rerank(query, raw, tasks, k, batch=32, eps=0.0, beta=2, metric=L2):
     """Algorithm 1 on one query: (ids, exact dists, mini-batches run)."""
     q = _c(query, np.float32).reshape(-1)
     r = np.ascontiguousarray(raw)
     t = _c(tasks, np.int64)
     oi = np.empty(k, dtype=np.int64)
     od = np.empty(k, dtype=np.float64)
-    nb = lib().or_rerank(_p(q), q.shape[0], _p(r), raw_kind(r), _p(t), t.shape[0], k, batch,
-                         float(eps), beta, _p(oi), _p(od))
+    nb = lib().or_rerank_m(_p(q), q.shape[0], _p(r), raw_kind(r), _p(t), t.shape[0], k, batch,
+                           float(eps), beta, _p(oi), _p(od), metric)
     return oi, od, int(nb)
 
 
 def search(queries, centroids, codebooks, codes, list_off, list_ids, nprobe, k, raw=None,
-           probes=None, rerank_n=0, batch=32, eps=0.0, beta=2, stats=False):
+           probes=None, rerank_n=0, batch=32, eps=0.0, beta=2, stats=False, metric=L2):
     """The whole filtering path for every query: (ids [nq][k], dists, stats?)."""
     q = _c(queries, np.float32)
     nq, d = q.shape
@@ -217,22 +243,22 @@ def search(queries, centroids, codebooks, codes, list_off, list_ids, nprobe, k, 
     oi = np.empty((nq, k), dtype=np.int64)
     od = np.empty((nq, k), dtype=np.float64)
     st = np.empty((nq, 4), dtype=np.int64)
-    rc = lib().or_search(_p(q), nq, d, _p(cent), nlist, M, _p(cb), _p(cd), _p(off), _p(ids),
-                         _p(r), 0 if r is None else raw_kind(r), nprobe, k, _p(pr), rerank_n,
-                         batch, float(eps), beta, _p(oi), _p(od), _p(st))
+    rc = lib().or_search_m(_p(q), nq, d, _p(cent), nlist, M, _p(cb), _p(cd), _p(off), _p(ids),
+                           _p(r), 0 if r is None else raw_kind(r), nprobe, k, _p(pr), rerank_n,
+                           batch, float(eps), beta, _p(oi), _p(od), _p(st), metric)
     if rc != 0:
         raise RuntimeError("oracle search failed")
     return (oi, od, st) if stats else (oi, od)
 
 
-def knn(queries, base, k):
+def knn(queries, base, k, metric=L2):
     """Brute-force exact k-NN (FP64, ties by smaller id): (ids, dists)."""
     q = _c(queries, np.float32)
     b = np.ascontiguousarray(base)
     nq, d = q.shape
     oi = np.empty((nq, k), dtype=np.int64)
     od = np.empty((nq, k), dtype=np.float64)
-    lib().or_knn(_p(q), nq, _p(b), raw_kind(b), b.shape[0], d, k, _p(oi), _p(od))
+    lib().or_knn_m(_p(q), nq, _p(b), raw_kind(b), b.shape[0], d, k, _p(oi), _p(od), metric)
     return oi, od
 
 

@@ -35,6 +35,11 @@
  *     mini-batch stops at the end of the task list.
  *   - Delta keeps k as its denominator even while the heap holds fewer than k.
  *   - rows with fewer than k results are padded with (id -1, +inf).
+ *   - inner-product search (the second metric of the SPACEV-like workload,
+ *     Table 1) ranks by the smallest -<q, x>: the coarse probe by -<q, c>,
+ *     the table entries are -<q_i, C_i[c]> (which Eq. 1 adds up like the L2
+ *     terms, since the inner product also splits over subspaces), and the
+ *     re-rank and the ground truth use the exact -<q, x>.
  */
 #include <math.h>
 #include <stdint.h>
@@ -47,6 +52,10 @@
 
 #define OR_RAW_U8 1
 #define OR_RAW_F32 0
+#define OR_RAW_I8 2
+
+#define OR_L2 0
+#define OR_IP 1
 
 typedef struct {
     double d;
@@ -97,14 +106,19 @@ void or_set_threads(int t)
  * and the nprobe smallest by (distance, list id).
  * ------------------------------------------------------------------------- */
 static void coarse_one(const float *q, int32_t d, const float *cent, int32_t nlist,
-                       int32_t nprobe, int32_t *probes, double *d2out, pair_t *scratch)
+                       int32_t nprobe, int32_t *probes, double *d2out, pair_t *scratch,
+                       int32_t metric)
 {
     for (int32_t l = 0; l < nlist; ++l) {
         double s = 0.0;
         const float *c = cent + (int64_t)l * d;
-        for (int32_t j = 0; j < d; ++j) {
-            double t = (double)q[j] - (double)c[j];
-            s += t * t;
+        if (metric == OR_IP) {
+            for (int32_t j = 0; j < d; ++j) s -= (double)q[j] * (double)c[j];
+        } else {
+            for (int32_t j = 0; j < d; ++j) {
+                double t = (double)q[j] - (double)c[j];
+                s += t * t;
+            }
         }
         scratch[l].d = s;
         scratch[l].id = l;
@@ -116,8 +130,8 @@ static void coarse_one(const float *q, int32_t d, const float *cent, int32_t nli
     }
 }
 
-void or_coarse(const float *q, int64_t nq, int32_t d, const float *cent, int32_t nlist,
-               int32_t nprobe, int32_t *probes, double *d2out)
+void or_coarse_m(const float *q, int64_t nq, int32_t d, const float *cent, int32_t nlist,
+                 int32_t nprobe, int32_t *probes, double *d2out, int32_t metric)
 {
 #pragma omp parallel
     {
@@ -125,9 +139,15 @@ void or_coarse(const float *q, int64_t nq, int32_t d, const float *cent, int32_t
 #pragma omp for schedule(dynamic, 4)
         for (int64_t i = 0; i < nq; ++i)
             coarse_one(q + i * d, d, cent, nlist, nprobe, probes + i * nprobe,
-                       d2out ? d2out + i * nprobe : NULL, scratch);
+                       d2out ? d2out + i * nprobe : NULL, scratch, metric);
         free(scratch);
     }
+}
+
+void or_coarse(const float *q, int64_t nq, int32_t d, const float *cent, int32_t nlist,
+               int32_t nprobe, int32_t *probes, double *d2out)
+{
+    or_coarse_m(q, nq, d, cent, nlist, nprobe, probes, d2out, OR_L2);
 }
 
 /* ---------------------------------------------------------------------------
@@ -135,19 +155,29 @@ void or_coarse(const float *q, int64_t nq, int32_t d, const float *cent, int32_t
  * i of (q_j - C_i[c][j])^2, the dist(q_i, c_i) terms that Eq. 1 adds up.
  * codebooks is [M][256][dsub]; lut is [M][256].
  * ------------------------------------------------------------------------- */
-void or_lut(const float *q, int32_t d, int32_t M, const float *codebooks, double *lut)
+void or_lut_m(const float *q, int32_t d, int32_t M, const float *codebooks, double *lut,
+              int32_t metric)
 {
     int32_t dsub = d / M;
     for (int32_t i = 0; i < M; ++i)
         for (int32_t c = 0; c < 256; ++c) {
             const float *cw = codebooks + ((int64_t)i * 256 + c) * dsub;
             double s = 0.0;
-            for (int32_t j = 0; j < dsub; ++j) {
-                double t = (double)q[i * dsub + j] - (double)cw[j];
-                s += t * t;
+            if (metric == OR_IP) {
+                for (int32_t j = 0; j < dsub; ++j) s -= (double)q[i * dsub + j] * (double)cw[j];
+            } else {
+                for (int32_t j = 0; j < dsub; ++j) {
+                    double t = (double)q[i * dsub + j] - (double)cw[j];
+                    s += t * t;
+                }
             }
             lut[i * 256 + c] = s;
         }
+}
+
+void or_lut(const float *q, int32_t d, int32_t M, const float *codebooks, double *lut)
+{
+    or_lut_m(q, d, M, codebooks, lut, OR_L2);
 }
 
 /* ---------------------------------------------------------------------------
@@ -211,30 +241,41 @@ void or_topn(const double *dist, const uint32_t *ids, int64_t cnt, int32_t n,
     free(p);
 }
 
-/* Exact squared L2 between q and raw vector v (uint8 or float32 rows). */
-static double exact_l2(const float *q, int32_t d, const void *raw, int32_t raw_dtype, int64_t v)
+/* Coordinate j of raw vector v (uint8, int8 or float32 rows). */
+static double raw_at(const void *raw, int32_t raw_dtype, int32_t d, int64_t v, int32_t j)
+{
+    if (raw_dtype == OR_RAW_U8) return (double)((const uint8_t *)raw)[v * d + j];
+    if (raw_dtype == OR_RAW_I8) return (double)((const int8_t *)raw)[v * d + j];
+    return (double)((const float *)raw)[v * d + j];
+}
+
+/* Exact distance between q and raw vector v: squared L2, or -<q, x>. */
+static double exact_dist(const float *q, int32_t d, const void *raw, int32_t raw_dtype, int64_t v,
+                         int32_t metric)
 {
     double s = 0.0;
-    if (raw_dtype == OR_RAW_U8) {
-        const uint8_t *x = (const uint8_t *)raw + v * d;
-        for (int32_t j = 0; j < d; ++j) {
-            double t = (double)q[j] - (double)x[j];
-            s += t * t;
-        }
-    } else {
-        const float *x = (const float *)raw + v * d;
-        for (int32_t j = 0; j < d; ++j) {
-            double t = (double)q[j] - (double)x[j];
+    for (int32_t j = 0; j < d; ++j) {
+        const double x = raw_at(raw, raw_dtype, d, v, j);
+        if (metric == OR_IP) {
+            s -= (double)q[j] * x;
+        } else {
+            double t = (double)q[j] - x;
             s += t * t;
         }
     }
     return s;
 }
 
+void or_exact_m(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
+                const int64_t *ids, int64_t n, double *out, int32_t metric)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = exact_dist(q, d, raw, raw_dtype, ids[i], metric);
+}
+
 void or_exact_l2(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
                  const int64_t *ids, int64_t n, double *out)
 {
-    for (int64_t i = 0; i < n; ++i) out[i] = exact_l2(q, d, raw, raw_dtype, ids[i]);
+    or_exact_m(q, d, raw, raw_dtype, ids, n, out, OR_L2);
 }
 
 /* ---------------------------------------------------------------------------
@@ -250,9 +291,9 @@ static int in_set(const int64_t *s, int32_t n, int64_t id)
     return 0;
 }
 
-int32_t or_rerank(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
-                  const int64_t *tasks, int32_t ntasks, int32_t k, int32_t batch,
-                  float eps, int32_t beta, int64_t *out_ids, double *out_dist)
+int32_t or_rerank_m(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
+                    const int64_t *tasks, int32_t ntasks, int32_t k, int32_t batch,
+                    float eps, int32_t beta, int64_t *out_ids, double *out_dist, int32_t metric)
 {
     pair_t *Q = (pair_t *)malloc(sizeof(pair_t) * (size_t)(k + 1));
     int64_t *prev = (int64_t *)malloc(sizeof(int64_t) * (size_t)(k > 0 ? k : 1));
@@ -268,7 +309,7 @@ int32_t or_rerank(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
         for (int32_t j = i; j < end; ++j) {
             pair_t c;
             c.id = tasks[j];
-            c.d = exact_l2(q, d, raw, raw_dtype, tasks[j]);
+            c.d = exact_dist(q, d, raw, raw_dtype, tasks[j], metric);
             if (qn < k || pair_less(&c, &Q[qn - 1])) {
                 /* insert in order, drop the maximum when over k */
                 int32_t pos = qn < k ? qn : k - 1;
@@ -307,6 +348,14 @@ int32_t or_rerank(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
     return batches;
 }
 
+int32_t or_rerank(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
+                  const int64_t *tasks, int32_t ntasks, int32_t k, int32_t batch,
+                  float eps, int32_t beta, int64_t *out_ids, double *out_dist)
+{
+    return or_rerank_m(q, d, raw, raw_dtype, tasks, ntasks, k, batch, eps, beta, out_ids,
+                       out_dist, OR_L2);
+}
+
 /* ---------------------------------------------------------------------------
  * The whole filtering path for nq queries (steps 1-8 of §3), one query per
  * OpenMP iteration.
@@ -317,11 +366,11 @@ int32_t or_rerank(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
  *   stats      optional [nq][4]: gathered ids, distinct ids, mini-batches run,
  *              candidates handed to the re-rank.
  * ------------------------------------------------------------------------- */
-int32_t or_search(const float *queries, int64_t nq, int32_t d, const float *cent, int32_t nlist,
-                  int32_t M, const float *codebooks, const uint8_t *codes, const int64_t *list_off,
-                  const int64_t *list_ids, const void *raw, int32_t raw_dtype, int32_t nprobe,
-                  int32_t k, const int32_t *probes_in, int32_t rerank_n, int32_t batch, float eps,
-                  int32_t beta, int64_t *out_ids, double *out_dist, int64_t *stats)
+int32_t or_search_m(const float *queries, int64_t nq, int32_t d, const float *cent, int32_t nlist,
+                    int32_t M, const float *codebooks, const uint8_t *codes, const int64_t *list_off,
+                    const int64_t *list_ids, const void *raw, int32_t raw_dtype, int32_t nprobe,
+                    int32_t k, const int32_t *probes_in, int32_t rerank_n, int32_t batch, float eps,
+                    int32_t beta, int64_t *out_ids, double *out_dist, int64_t *stats, int32_t metric)
 {
     if (nprobe > nlist) nprobe = nlist;
     if (nprobe < 1) nprobe = 1;
@@ -347,8 +396,8 @@ int32_t or_search(const float *queries, int64_t nq, int32_t d, const float *cent
             if (probes_in)
                 memcpy(probes, probes_in + qi * nprobe, sizeof(int32_t) * (size_t)nprobe);
             else
-                coarse_one(q, d, cent, nlist, nprobe, probes, NULL, scratch);
-            or_lut(q, d, M, codebooks, lut);
+                coarse_one(q, d, cent, nlist, nprobe, probes, NULL, scratch, metric);
+            or_lut_m(q, d, M, codebooks, lut, metric);
             int64_t gathered = 0;
             int64_t u = or_candidates(probes, nprobe, list_off, list_ids, cand, cap, &gathered);
             if (u < 0) {
@@ -359,8 +408,8 @@ int32_t or_search(const float *queries, int64_t nq, int32_t d, const float *cent
             or_topn(dist, cand, u, n_top, top_ids, top_d);
             int32_t batches = 0;
             if (rerank_n > 0) {
-                batches = or_rerank(q, d, raw, raw_dtype, top_ids, n_top, k, batch, eps, beta,
-                                    out_ids + qi * k, out_dist + qi * k);
+                batches = or_rerank_m(q, d, raw, raw_dtype, top_ids, n_top, k, batch, eps, beta,
+                                      out_ids + qi * k, out_dist + qi * k, metric);
             } else {
                 memcpy(out_ids + qi * k, top_ids, sizeof(int64_t) * (size_t)k);
                 memcpy(out_dist + qi * k, top_d, sizeof(double) * (size_t)k);
@@ -383,12 +432,23 @@ int32_t or_search(const float *queries, int64_t nq, int32_t d, const float *cent
     return err ? -1 : 0;
 }
 
+int32_t or_search(const float *queries, int64_t nq, int32_t d, const float *cent, int32_t nlist,
+                  int32_t M, const float *codebooks, const uint8_t *codes, const int64_t *list_off,
+                  const int64_t *list_ids, const void *raw, int32_t raw_dtype, int32_t nprobe,
+                  int32_t k, const int32_t *probes_in, int32_t rerank_n, int32_t batch, float eps,
+                  int32_t beta, int64_t *out_ids, double *out_dist, int64_t *stats)
+{
+    return or_search_m(queries, nq, d, cent, nlist, M, codebooks, codes, list_off, list_ids, raw,
+                       raw_dtype, nprobe, k, probes_in, rerank_n, batch, eps, beta, out_ids, out_dist,
+                       stats, OR_L2);
+}
+
 /* ---------------------------------------------------------------------------
  * Ground truth: brute-force k nearest neighbours by exact squared L2 in FP64
  * (exact for uint8 data), ties by smaller id. Used for Recall@k (§6).
  * ------------------------------------------------------------------------- */
-void or_knn(const float *queries, int64_t nq, const void *base, int32_t raw_dtype, int64_t n,
-            int32_t d, int32_t k, int64_t *out_ids, double *out_dist)
+void or_knn_m(const float *queries, int64_t nq, const void *base, int32_t raw_dtype, int64_t n,
+              int32_t d, int32_t k, int64_t *out_ids, double *out_dist, int32_t metric)
 {
 #pragma omp parallel
     {
@@ -400,7 +460,7 @@ void or_knn(const float *queries, int64_t nq, const void *base, int32_t raw_dtyp
             for (int64_t v = 0; v < n; ++v) {
                 pair_t c;
                 c.id = v;
-                c.d = exact_l2(q, d, base, raw_dtype, v);
+                c.d = exact_dist(q, d, base, raw_dtype, v, metric);
                 if (qn < k || pair_less(&c, &Q[qn - 1])) {
                     int32_t pos = qn < k ? qn : k - 1;
                     if (qn < k) ++qn;
@@ -418,4 +478,10 @@ void or_knn(const float *queries, int64_t nq, const void *base, int32_t raw_dtyp
         }
         free(Q);
     }
+}
+
+void or_knn(const float *queries, int64_t nq, const void *base, int32_t raw_dtype, int64_t n,
+            int32_t d, int32_t k, int64_t *out_ids, double *out_dist)
+{
+    or_knn_m(queries, nq, base, raw_dtype, n, d, k, out_ids, out_dist, OR_L2);
 }

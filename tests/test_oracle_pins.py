@@ -341,3 +341,86 @@ def test_recall_helper():
     # 9 ties the 4th neighbour's distance: counts when exact distances are given
     assert oracle.recall_at(np.array([[1, 2, 9, 8]]), gt, gd,
                             exact_found_dist=np.array([[1.0, 2.0, 3.0, 5.0]]), at=4) == 0.75
+
+
+# ---------------------------------------------------------------------------
+# Inner-product metric and int8 rows (the SPACEV-like workload of Table 1:
+# int8 vectors, d = 100, M in {20, 25, 50})
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("d,M", [(100, 20), (100, 25), (100, 50), (128, 32)])
+def test_lut_ip_matches_numpy_dot_per_subspace(d, M):
+    """Eq. 1's terms for the inner product: LUT[m][c] = -<q_m, C_m[c]>."""
+    rng = _rng(d + M)
+    q = rng.normal(size=d).astype(np.float32)
+    cb = rng.normal(size=(M, 256, d // M)).astype(np.float32)
+    t = oracle.lut(q, cb, metric=oracle.IP)
+    ref = -np.einsum("mj,mcj->mc", q.reshape(M, d // M).astype(np.float64), cb.astype(np.float64))
+    np.testing.assert_allclose(t, ref, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("M", [20, 25, 50])
+def test_identity_codebook_ip_full_probe_equals_brute_force(M):
+    """Every vector its own PQ centroid and every list probed: the oracle's
+    IVF-PQ top-k by -<q, x> equals brute force by numpy (int8 rows)."""
+    rng = _rng(300 + M)
+    d, n, nlist = 100, 200, 6
+    x = rng.integers(-128, 128, size=(n, d)).astype(np.int8)
+    dsub = d // M
+    cb = np.zeros((M, 256, dsub), np.float32)
+    for m in range(M):
+        cb[m, :n] = x[:, m * dsub:(m + 1) * dsub]
+    codes = np.repeat(np.arange(n, dtype=np.uint8)[:, None], M, axis=1)
+    primary = rng.integers(0, nlist, size=n).astype(np.int32)
+    off, ids = oracle.lists_from_parts(primary, np.zeros(nlist + 1, np.int64), np.zeros(0, np.int64), nlist)
+    cent = rng.normal(size=(nlist, d)).astype(np.float32)
+    q = rng.integers(-128, 128, size=(7, d)).astype(np.float32)
+    oi, od = oracle.search(q, cent, cb, codes, off, ids, nlist, 10, metric=oracle.IP)
+    for i in range(q.shape[0]):
+        ip = -(x.astype(np.float64) @ q[i].astype(np.float64))
+        order = np.lexsort((np.arange(n), ip))[:10]
+        assert oi[i].tolist() == order.tolist(), i
+        np.testing.assert_allclose(od[i], ip[order], rtol=0, atol=1e-9)
+
+
+@pytest.mark.parametrize("metric", ["L2", "IP"])
+def test_knn_int8_matches_numpy(metric):
+    rng = _rng(17)
+    x = rng.integers(-128, 128, size=(500, 100)).astype(np.int8)
+    q = rng.integers(-128, 128, size=(5, 100)).astype(np.float32)
+    m = getattr(oracle, metric)
+    oi, od = oracle.knn(q, x, 7, metric=m)
+    x64, q64 = x.astype(np.float64), q.astype(np.float64)
+    for i in range(5):
+        dist = ((x64 - q64[i]) ** 2).sum(1) if metric == "L2" else -(x64 @ q64[i])
+        order = np.lexsort((np.arange(500), dist))[:7]
+        assert oi[i].tolist() == order.tolist()
+        np.testing.assert_allclose(od[i], dist[order], rtol=0, atol=1e-9)
+        np.testing.assert_allclose(oracle.exact(q[i], x, order, metric=m), dist[order], rtol=0, atol=1e-9)
+
+
+def test_coarse_ip_matches_numpy_lexsort():
+    rng = _rng(23)
+    c = rng.normal(size=(300, 100)).astype(np.float32)
+    q = rng.normal(size=(9, 100)).astype(np.float32)
+    pr, d2 = oracle.coarse(q, c, 12, with_d2=True, metric=oracle.IP)
+    for i in range(9):
+        ip = -(c.astype(np.float64) @ q[i].astype(np.float64))
+        order = np.lexsort((np.arange(300), ip))[:12]
+        assert pr[i].tolist() == order.tolist()
+        np.testing.assert_allclose(d2[i], ip[order], rtol=0, atol=1e-9)
+
+
+def test_rerank_ip_never_stopping_is_exact_topk():
+    """Algorithm 1 with eps < 0 over int8 rows by -<q, x>: the exact top-k of
+    the candidates (numpy)."""
+    rng = _rng(31)
+    x = rng.integers(-128, 128, size=(300, 100)).astype(np.int8)
+    q = rng.integers(-128, 128, size=100).astype(np.float32)
+    tasks = rng.permutation(300)[:120].astype(np.int64)
+    oi, od, nb = oracle.rerank(q, x, tasks, 10, batch=32, eps=-1.0, beta=1, metric=oracle.IP)
+    ip = -(x[tasks].astype(np.float64) @ q.astype(np.float64))
+    order = np.lexsort((tasks, ip))[:10]
+    assert oi.tolist() == tasks[order].tolist()
+    np.testing.assert_allclose(od, ip[order], rtol=0, atol=1e-9)
+    assert nb == 4  # ceil(120 / 32) mini-batches
