@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--form", default="lowp", choices=["lowp", "plain"],
-                    help="lowp: BF16 tensor-core probe and LUT, FP16 LUT (precision form); plain: FP32 "
-                         "everywhere; both re-rank the ADC top-n")
+    ap.add_argument("--form", default="lowp", choices=["lowp", "plain", "batched"],
+                    help="lowp: BF16 tensor-core probe and LUT, FP16 LUT (precision form); batched: the "
+                         "same table scanned list by list over the whole batch (FA_BATCHED); plain: FP32 "
+                         "everywhere; all re-rank the ADC top-n")
     ap.add_argument("--n", type=int, default=10_000_000)
     ap.add_argument("--nq", type=int, default=10_000)
     # default operating point: the fastest measured (nprobe, re-rank depth) with
@@ -86,10 +87,17 @@ def parse():
     ap.add_argument("--zipf-n", type=int, default=100_000_000)
     ap.add_argument("--zipf-rerank", type=int, default=0,
                     help="batching form: re-rank the ADC top-n exhaustively on raw rows in HBM (0 = off)")
+    ap.add_argument("--batching-n", type=int, default=100_000_000,
+                    help="base size of the batching form's workload in the default line")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="skip the serving form (request loop under Poisson load) on the batching index")
+    ap.add_argument("--zipf-form", default="batched", choices=["tiled", "batched"],
+                    help="batching form's scan: tiled persistent per-query scan (FP8 table) or the "
+                         "list-major batched scan (FA_BATCHED, FP16 table)")
     ap.add_argument("--serve", action="store_true",
                     help="serving form: open-loop Poisson arrivals on the Zipf-lists index")
-    ap.add_argument("--rates", default="5000,10000,20000,50000,100000")
-    ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--rates", default="5000,10000,20000,40000,80000")
+    ap.add_argument("--serve-seconds", type=float, default=4.0)
     ap.add_argument("--window-us", type=int, default=500)
     ap.add_argument("--serve-form", choices=["tiled", "plain"], default="tiled",
                     help="scan form of the served batches: tiled persistent (uneven work) or one CTA per query")
@@ -269,7 +277,7 @@ def exact_dists(base, q, ids):
     return out
 
 
-def err_vs_fp64(fa, oracle, ix, parts, base, queries, nprobe, sp, found_ids, found_dist, ns=16):
+def err_vs_fp64(fa, oracle, ix, parts, base, queries, nprobe, sp, found_ids, found_dist, ns=16, npq=None):
     """Error of the GPU's distances against the FP64 oracle on the first ns
     queries: the form's ADC distances (its table precision, re-rank off, top
     100) against the oracle's ADC of the same ids (Eq. 1 in FP64), and the
@@ -280,7 +288,7 @@ def err_vs_fp64(fa, oracle, ix, parts, base, queries, nprobe, sp, found_ids, fou
     p.rerank_n = 0
     p.flags &= ~fa.FA_GRAPH
     q = np.ascontiguousarray(queries[:ns])
-    gi, gd = fa.fa_search_ex(ix, q, 100, nprobe, p)
+    gi, gd = fa.fa_search_ex(ix, q, 100, nprobe, p, nprobe_per_query=npq)
     adc = 0.0
     for i in range(ns):
         ok = gi[i] >= 0
@@ -288,7 +296,7 @@ def err_vs_fp64(fa, oracle, ix, parts, base, queries, nprobe, sp, found_ids, fou
                          gi[i][ok].astype(np.uint32))
         adc = max(adc, float(np.max(np.abs(gd[i][ok] - ref) / np.maximum(ref, 1e-30))))
     out = {"adc_max_rel": adc, "sample": "first %d queries, ADC top-100 of the form's table" % ns}
-    if sp.rerank_n > 0:
+    if sp.rerank_n > 0 and base is not None:
         rr = 0.0
         for i in range(ns):
             ok = found_ids[i] >= 0
@@ -303,13 +311,15 @@ def search_params(fa, form, wl, persistent=False, serial=False):
     """plain: FP32 everywhere (SIMT coarse probe, FP32 LUT built in the scan CTA).
     lowp: BF16 tensor-core coarse probe and LUT GEMMs, FP16 (or FP8) LUT.
     Both forms re-rank the same top-n on exact FP32 distances (Algorithm 1)."""
-    lowp = form == "lowp"
+    lowp = form in ("lowp", "batched")
     tc = fa.FA_GEMM_BF16_TC if lowp else fa.FA_GEMM_SIMT_F32
-    prec = (fa.FA_LUT_FP8 if wl.get("lut") == "fp8" else fa.FA_LUT_F16) if lowp else fa.FA_LUT_F32
+    prec = (fa.FA_LUT_FP8 if wl.get("lut") == "fp8" and form == "lowp" else fa.FA_LUT_F16) \
+        if lowp else fa.FA_LUT_F32
     return fa.search_params(lut_prec=prec, lut_gemm=tc, probe_gemm=tc,
                             rerank_n=wl["rerank_n"], rerank_batch=wl["batch"],
                             rerank_beta=wl["beta"], rerank_eps=wl["eps"],
-                            flags=(fa.FA_PERSISTENT if persistent else 0) | (fa.FA_SERIAL if serial else 0))
+                            flags=(fa.FA_PERSISTENT if persistent else 0) | (fa.FA_SERIAL if serial else 0)
+                            | (fa.FA_BATCHED if form == "batched" else 0))
 
 
 def timed_steps(fa, torch, ix, qd, k, nprobe, sp, steps, warmup, flush, oid, odist):
@@ -388,7 +398,7 @@ def main():
     if args.sweep:
         return sweep(args, wl, fa, torch, oracle, ix, base, queries, qd, flush, gt, t_build)
 
-    lowp = args.form == "lowp"
+    lowp = args.form in ("lowp", "batched")
     sp = search_params(fa, args.form, wl, args.persistent, args.serial)
     # the search pipelines scan and re-rank in 8 chunks when it re-ranks a large
     # batch from host memory (see FA_SERIAL in include/fa.h)
@@ -492,15 +502,22 @@ def main():
     if rank == 0 and world == 1 and not args.no_batching and args.workload == "sift10m":
         import copy
         za = copy.copy(args)
-        za.zipf_n, za.zipf_rerank, za.steps, za.nq = 10_000_000, 100, min(args.steps, 10), 10_000
+        # the batching workload at its configured size; an exhaustive re-rank of
+        # the ADC top-256 on raw rows in HBM reaches recall@10 above 0.9 there
+        za.zipf_n, za.zipf_rerank, za.steps, za.nq = args.batching_n, 256, min(args.steps, 5), 10_000
+        za.with_serving = not args.no_serve
+        za.recall = 1000
         zl = bench_zipf(za, emit=False)
         batching = {"workload": zl["config"]["workload"], "value": zl["value"], "unit": "queries/s",
                     "ms_per_step": zl["ms_per_step"], "recall_at_10": zl["recall_at_10"],
                     "plain_fp32": zl["plain_fp32_qps"], "recall_at_10_plain": zl["recall_at_10_plain"],
                     "lowp_over_plain": zl["speedup_vs_plain"],
-                    "form": "FP8 LUT, BF16 tensor-core probe and LUT, autotuned launch, CUDA graph; "
-                            "exhaustive re-rank of the ADC top-100 on raw rows in HBM",
-                    "nprobe": "uniform 16..128 per query", "stage_ms": zl["stage_ms"]}
+                    "form": zl["config"]["form"] + "; BF16 tensor-core probe and LUT; exhaustive "
+                            "re-rank of the ADC top-256 on raw rows in HBM",
+                    "nprobe": "uniform 16..128 per query", "stage_ms": zl["stage_ms"],
+                    "candidates_per_query": zl["candidates_per_query"],
+                    "roofline": zl["roofline"], "err_vs_fp64": zl["err_vs_fp64"],
+                    "serving_form": zl["serving_form"], "build_s": zl["build_s"]}
 
     if rank == 0:
         line = {
@@ -559,6 +576,33 @@ def main():
         dist.destroy_process_group()
 
 
+def zipf_form_name(args):
+    return getattr(args, "zipf_form", "batched")
+
+
+def zipf_form_desc(args):
+    if zipf_form_name(args) == "batched":
+        return ("batched list-major scan (FA_BATCHED: FP8 table, four queries per table word), "
+                "CUDA graph")
+    return "tiled persistent per-query scan (FP8 table expanded to FP32), CUDA graph, autotuned tiles"
+
+
+def zipf_search_params(fa, args, rr, batch, extra=0):
+    """The batching workload's forms: batch=True is the low-precision batched
+    form (BF16 tensor-core probe and LUT, FP8 table; list-major or tiled
+    scan), batch=False the plain FP32 form; both re-rank the ADC top-rr
+    exhaustively when rr > 0."""
+    tc = fa.FA_GEMM_BF16_TC
+    r = dict(rerank_n=rr, rerank_eps=-1.0) if rr else {}
+    if batch and zipf_form_name(args) == "batched":
+        return fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc,
+                                flags=extra | fa.FA_BATCHED, **r)
+    if batch:
+        return fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc,
+                                flags=extra | fa.FA_PERSISTENT, **r)
+    return fa.search_params(flags=extra, **r)
+
+
 def bench_zipf(args, emit=True):
     """Batching form on uneven work: unit-norm d=96 vectors in 65536 lists of
     Zipf(1.1) sizes (the largest holds ~14% of the base), 10k queries with
@@ -591,10 +635,7 @@ def bench_zipf(args, emit=True):
     tc = fa.FA_GEMM_BF16_TC
 
     def params(batch, extra=0):
-        r = dict(rerank_n=rr, rerank_eps=-1.0) if rr else {}
-        if batch:
-            return fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc, flags=extra, **r)
-        return fa.search_params(flags=extra, **r)
+        return zipf_search_params(fa, args, rr, batch, extra)
 
     # autotune the batching form (tile size, threads) on host copies of a sample
     sp_t = params(True)
@@ -629,6 +670,7 @@ def bench_zipf(args, emit=True):
     ms_batch = timed(params(True, fa.FA_GRAPH), args.steps)
     clk = clocks.stop()
     ids_batch = oid.cpu().numpy()
+    dist_batch = odist.cpu().numpy()
     ms_plain = timed(params(False), max(3, args.steps // 4))
     ids_plain = oid.cpu().numpy()
     tr = fa.fa_search_trace()
@@ -636,20 +678,40 @@ def bench_zipf(args, emit=True):
                     nprobe_per_query=npq_d, trace=tr)
     ns = min(args.recall, nq) if args.recall else 0
     rec_b = rec_p = None
+    gt = None
     if ns:
         gt = ground_truth(base, queries[:ns], 10)
         rec_b = recall_of(oracle, base, queries, ids_batch, gt)
         rec_p = recall_of(oracle, base, queries, ids_plain, gt)
     peak, peak_src = measured_peaks()
     scan_bytes = int(cand.sum()) * M + nq * M * 256 + nq * 10 * 8
+    err = None
+    if getattr(args, "zipf_err", True):
+        parts = ix.parts(with_raw=False)
+        err = err_vs_fp64(fa, oracle, ix, parts, base if rr else None, queries, 128, params(True),
+                          ids_batch[:16], dist_batch[:16], npq=npq[:16])
+        del parts
+    serving = None
+    if getattr(args, "with_serving", False):
+        pool = z.queries(20000)
+        srv, sres, sstats = serve_load(fa, ix, params(True), pool,
+                                       [float(r) for r in args.rates.split(",")],
+                                       args.serve_seconds, args.window_us)
+        srec = serve_recall(srv, pool, gt) if ns else None
+        srv.close()
+        serving = {"loads": sres, **sstats, "recall_at_10": srec, "k": "uniform {1,10,100}",
+                   "nprobe": "uniform 32..256", "window_us": args.window_us, "max_batch": 4096,
+                   "rerank_n": rr, "recall_requests": "k 10, nprobe uniform 32..256, %d queries" % ns}
     line = {
         "metric": "QPS at recall@10=0.9 on 1 B300, low-prec batched vs FP32 plain; % HBM roofline",
         "value": nq / (ms_batch / 1e3), "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
         "warmup": 3, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "fp8-lut/bf16-tc-gemm/f32-acc", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": "fp8-lut/bf16-tc-gemm/f16x2-then-f32-acc" if zipf_form_name(args) == "batched"
+        else "fp8-lut/bf16-tc-gemm/f32-acc", "data": "synthetic",
         "config": {"workload": "ivfpq-f32unit-%dm-d96-zipf65536-M48" % (args.zipf_n // 1_000_000),
                    "n": args.zipf_n, "nq": nq, "nlist": 65536, "M": M, "k": k,
-                   "nprobe": "uniform 16..128 per query", "form": "batched (tiled persistent, CUDA graph)",
+                   "nprobe": "uniform 16..128 per query", "form": zipf_form_desc(args),
                    "rerank_n": rr, "rerank": "Algorithm 1 exhaustive (eps < 0), raw rows in HBM" if rr else "none",
                    "tuned": tuned, "l2": "flushed between timed steps"},
         "plain_fp32_qps": nq / (ms_plain / 1e3), "speedup_vs_plain": ms_plain / ms_batch,
@@ -662,6 +724,7 @@ def bench_zipf(args, emit=True):
                      scan_bytes / (tr.scan_ms / 1e3) / 1e9, "peak": peak, "peak_source": peak_src,
                      "unit": "GB/s", "frac": scan_bytes / (tr.scan_ms / 1e3) / 1e9 / peak,
                      "algorithmic_bytes_per_launch": scan_bytes},
+        "err_vs_fp64": err, "serving_form": serving,
         "clocks": clk, "build_s": t_build, "gen_s": t_gen,
     }
     ix.free()
@@ -670,31 +733,18 @@ def bench_zipf(args, emit=True):
     return line
 
 
-def bench_serve(args):
-    """Serving form on the Zipf-lists index: requests with k uniform in
-    {1, 10, 100} and nprobe uniform in 32..256 arrive as an open-loop Poisson
-    process at each offered rate; the request loop batches them continuously.
-    Reports sustained QPS (completed / elapsed), p50 and p99 latency from
-    submit to completion."""
+def serve_load(fa, ix, sp, pool, rates, seconds, window_us, max_batch=4096, slots=4):
+    """Open-loop Poisson load on the request loop (fa_server_*) over ix: at
+    each offered rate, requests with k uniform in {1, 10, 100} and nprobe
+    uniform in 32..256 arrive with seeded exponential gaps; returns sustained
+    QPS (completed / elapsed), p50, p99 and mean latency from submit to
+    completion per rate, and the loop's statistics."""
     import threading as th
-    import paper_2409_16576_b300 as fa
-    import torch
-    torch.cuda.set_device(0)
-    z = synth.ZipfLists(args.zipf_n)
-    t0 = time.perf_counter()
-    base = z.base()
-    ix = fa.fa_build_index_lists(base, z.centroids(), z.primary(), fa.build_params(M=48, kmeans_iters=args.kmeans_iters))
-    del base
-    t_build = time.perf_counter() - t0
-    pool = z.queries(20000)
-    tc = fa.FA_GEMM_BF16_TC
-    flags = fa.FA_PERSISTENT if args.serve_form == "tiled" else 0
-    sp = fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc, flags=flags)
-    srv = fa.Server(ix, sp, max_batch=4096, window_us=args.window_us, slots=4, kmax=100,
+    srv = fa.Server(ix, sp, max_batch=max_batch, window_us=window_us, slots=slots, kmax=100,
                     nprobe_max=256)
     results = []
-    for rate in [float(r) for r in args.rates.split(",")]:
-        count = int(rate * args.serve_seconds)
+    for rate in rates:
+        count = int(rate * seconds)
         arr = synth.poisson_arrivals(rate, count)
         ks = np.array([1, 10, 100], dtype=np.int32)[synth.uniform_ints(0, 2, count, tag=11)]
         nps = synth.uniform_ints(32, 256, count, tag=12)
@@ -729,17 +779,57 @@ def bench_serve(args):
                         "sustained_qps": count / elapsed, "p50_ms": float(np.percentile(lat, 50)) / 1e3,
                         "p99_ms": float(np.percentile(lat, 99)) / 1e3,
                         "mean_ms": float(lat.mean()) / 1e3})
-        print(json.dumps(results[-1]), flush=True)
         if results[-1]["sustained_qps"] < 0.5 * rate:
             break  # far beyond capacity: higher rates only grow the queue
     st = srv.stats()
+    stats = {"batches": st.batches, "requests": st.requests, "slots": st.slots,
+             "slot_device_bytes": st.device_bytes}
+    return srv, results, stats
+
+
+def serve_recall(srv, queries, gt, k=10, nprobe=None):
+    """recall@10 of requests served by srv (k 10, nprobe uniform in 32..256)
+    on the ground-truth subsample."""
+    import oracle
+    ns = gt[0].shape[0]
+    nps = synth.uniform_ints(32, 256, ns, tag=13) if nprobe is None else np.full(ns, nprobe, np.int32)
+    rid = srv.submit(queries[:ns], np.full(ns, k, np.int32), nps)
+    pos = {int(r): i for i, r in enumerate(rid)}
+    found = np.full((ns, k), -1, np.int64)
+    got = 0
+    while got < ns:
+        r, ids, _, _, st = srv.poll(max_results=8192, timeout_us=20000)
+        for j in range(r.shape[0]):
+            found[pos[int(r[j])]] = ids[j][:k]
+        got += r.shape[0]
+    return oracle.recall_at(found, gt[0], gt[1], at=10)
+
+
+def bench_serve(args):
+    """Serving form on the Zipf-lists index (standalone): see serve_load."""
+    import paper_2409_16576_b300 as fa
+    import torch
+    torch.cuda.set_device(0)
+    z = synth.ZipfLists(args.zipf_n)
+    t0 = time.perf_counter()
+    base = z.base()
+    rr = args.zipf_rerank
+    ix = fa.fa_build_index_lists(base, z.centroids(), z.primary(), fa.build_params(
+        M=48, kmeans_iters=args.kmeans_iters, raw_location=fa.FA_RAW_DEVICE if rr else fa.FA_RAW_NONE))
+    t_build = time.perf_counter() - t0
+    pool = z.queries(20000)
+    sp = zipf_search_params(fa, args, rr, batch=True)
+    gt = ground_truth(base, pool[:min(args.recall, 1000)], 10) if args.recall else None
+    del base
+    srv, results, stats = serve_load(fa, ix, sp, pool, [float(r) for r in args.rates.split(",")],
+                                     args.serve_seconds, args.window_us)
+    rec = serve_recall(srv, pool, gt) if gt is not None else None
     srv.close()
-    print(json.dumps({"serving": results, "batches": st.batches, "requests": st.requests,
-                      "slots": st.slots, "slot_device_bytes": st.device_bytes,
+    print(json.dumps({"serving": results, **stats, "recall_at_10": rec,
                       "config": {"workload": "ivfpq-f32unit-%dm-d96-zipf65536-M48" % (args.zipf_n // 1_000_000),
                                  "k": "uniform {1,10,100}", "nprobe": "uniform 32..256",
                                  "window_us": args.window_us, "max_batch": 4096, "slots": 4,
-                                 "form": "fp8 LUT, BF16 tensor-core probe and LUT, %s scan" % args.serve_form},
+                                 "rerank_n": rr, "form": zipf_form_name(args)},
                       "build_s": t_build}))
 
 

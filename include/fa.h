@@ -187,6 +187,19 @@ void fa_free_index(fa_index *ix);
                                   * §5) overlap one query's re-rank with
                                   * another's GPU filtering.
                                   * The results are the same either way. */
+#define FA_BATCHED 0x80          /* batched form: the whole batch is scanned list
+                                  * by list. The (query, probed list) pairs are
+                                  * grouped by list; the queries that probe a
+                                  * list share each 32-bit word of a shared-
+                                  * memory table (two FP16 or four FP8 entries),
+                                  * so one lookup per code byte serves two or
+                                  * four queries, and a list's codes are read
+                                  * once for all of them. Needs lut_prec
+                                  * FA_LUT_F16 or FA_LUT_FP8; the table then
+                                  * carries one scale per query (fa_debug_lut
+                                  * with this flag returns that table). FP16
+                                  * entries are summed in FP32; FP8 entries in
+                                  * half2 over 8 subspaces, then in FP32. */
 
 /* Optional per-call trace, measured with CUDA events on the call's stream
  * (ms of device time per stage; launches = kernels this call launched). An

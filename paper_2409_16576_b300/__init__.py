@@ -30,7 +30,7 @@ FA_RAW_NONE, FA_RAW_HOST_PINNED, FA_RAW_DEVICE = 0, 1, 2
 FA_LUT_F32, FA_LUT_F16, FA_LUT_FP8 = 0, 1, 2
 FA_GEMM_SIMT_F32, FA_GEMM_BF16_TC = 0, 1
 FA_QUERIES_ON_DEVICE, FA_OUTPUTS_ON_DEVICE, FA_NONBLOCKING = 0x1, 0x2, 0x4
-FA_PERSISTENT, FA_NO_SYNC, FA_GRAPH, FA_SERIAL = 0x8, 0x10, 0x20, 0x40
+FA_PERSISTENT, FA_NO_SYNC, FA_GRAPH, FA_SERIAL, FA_BATCHED = 0x8, 0x10, 0x20, 0x40, 0x80
 
 P = C.c_void_p
 i32, i64, u64, f32 = C.c_int32, C.c_int64, C.c_uint64, C.c_float
@@ -194,8 +194,9 @@ class Index:
         _check(_lib.fa_index_info_get(self.handle, C.byref(out)))
         return out
 
-    def parts(self) -> dict:
-        """Copies of the logical index (host arrays, caller order)."""
+    def parts(self, with_raw: bool = True) -> dict:
+        """Copies of the logical index (host arrays, caller order); the raw
+        vectors only when with_raw."""
         p = fa_index_parts()
         _check(_lib.fa_index_get_parts(self.handle, C.byref(p)))
         n, d, nl, M = p.n, p.d, p.nlist, p.M
@@ -215,7 +216,7 @@ class Index:
                    primary=arr(p.primary, np.int32, (n,)),
                    rep_off=rep_off, rep_ids=arr(p.rep_ids, np.int64, (int(rep_off[-1]),)))
         out["raw"] = arr(p.raw, np.uint8 if p.raw_dtype == FA_U8 else np.float32, (n, d)) \
-            if p.raw else None
+            if (p.raw and with_raw) else None
         return out
 
 

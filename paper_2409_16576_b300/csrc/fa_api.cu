@@ -97,7 +97,7 @@ void free_device_index(fa_index *ix) {
     DeviceIndex &d = ix->dev;
     void *ptrs[] = {d.centroids, d.cnorm, d.codebooks, d.codes, d.list_beg, d.rep_off,
                     d.rep_v, d.rep_mo, d.rep_t, d.mem, d.perm, d.raw_dev_alloc,
-                    d.centroids_bf16, d.codebooks_bf16, d.cbnorm};
+                    d.centroids_bf16, d.codebooks_bf16, d.cbnorm, d.lorder};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceIndex{};
@@ -222,6 +222,29 @@ void upload_index(fa_index *ix) {
     D.rep_t = dev_upload(rt.data(), rt.size(), bytes);
     D.mem = dev_upload(mem.data(), mem.size(), bytes);
     D.perm = dev_upload(perm.data(), perm.size(), bytes);
+    {
+        // lists by decreasing chunk count (primary range and replica slice), so
+        // that the batched scan starts the longest lists first
+        std::vector<uint32_t> order(nlist), chunks(nlist);
+        for (int l = 0; l < nlist; ++l) {
+            order[l] = (uint32_t)l;
+            chunks[l] = (beg[l + 1] - beg[l] + 31u) / 32u + (uint32_t)((roff[l + 1] - roff[l] + 31u) / 32u);
+        }
+        std::stable_sort(order.begin(), order.end(),
+                         [&](uint32_t x, uint32_t y) { return chunks[x] > chunks[y]; });
+        D.lorder = dev_upload(order.data(), order.size(), bytes);
+        double cm = 0;
+        for (int m = 0; m < M; ++m)
+            for (int c = 0; c < 256; ++c) {
+                double s2 = 0;
+                for (int j = 0; j < d / M; ++j) {
+                    const double x = ix->codebooks[((size_t)m * 256 + c) * (d / M) + j];
+                    s2 += x * x;
+                }
+                cm = std::max(cm, s2);
+            }
+        D.cb_max_norm2 = (float)(cm * (1.0 + 1e-6));
+    }
     if (d <= 128) {  // tensor-core operand tiles (BF16 hi/lo) for the coarse probe and the LUT
         std::vector<uint16_t> tiles;
         prepare_centroid_tiles(ix->centroids.data(), nlist, d, tiles, D.tc_kp, D.tc_ntiles);
@@ -273,9 +296,17 @@ static void ws_free_buffers(Workspace *w) {
     void *dp[] = {w->q, w->probes, w->kq, w->npq, w->order, w->bucket, w->tchunks, w->tprefix,
                   w->tmisc, w->partial, w->topkeys, w->out_ids, w->out_dist,
                   w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr, w->selbuf,
-                  w->redo};
+                  w->redo, w->bq_lcnt, w->bq_lqoff, w->bq_lcur, w->bq_upre, w->bq_lq, w->bq_pbits,
+                  w->bq_tau, w->bq_cnt, w->bq_qsum, w->bq_buf, w->bq_ctr};
     for (void *p : dp)
         if (p) cudaFree(p);
+    w->bq_lcnt = w->bq_lqoff = w->bq_lcur = w->bq_upre = w->bq_pbits = w->bq_cnt = w->bq_ctr = nullptr;
+    w->bq_lq = nullptr;
+    w->bq_tau = w->bq_buf = nullptr;
+    w->bq_qsum = nullptr;
+    w->bq_cap_nq = 0;
+    w->bq_cap_pairs_np = 0;
+    w->bq_cap = 0;
     void *hp[] = {w->h_err, w->h_stats, w->h_small};
     for (void *p : hp)
         if (p) cudaFreeHost(p);
@@ -359,6 +390,48 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
     w->cap_nprobe = cp;
     w->cap_ntop = ct;
     w->cap_lut_bytes = cl;
+}
+
+// Buffers of the batched form: (query, list) pairs by list, per-query
+// thresholds and key buffers of cap keys (twice the top-n, at least 16384).
+static uint32_t bq_key_cap(int32_t ntop) { return (uint32_t)std::max(2 * ntop, 16384); }
+
+static void ws_ensure_batched(fa_index *ix, Workspace *w, int64_t nq, int32_t nprobe, int32_t ntop) {
+    const DeviceIndex &D = ix->dev;
+    const uint32_t cap = bq_key_cap(ntop);
+    if (w->bq_buf && w->bq_cap_nq >= nq && w->bq_cap_pairs_np >= nprobe && w->bq_cap >= cap && w->redo)
+        return;
+    if (w->pending) FA_CHECK_CUDA(cudaEventSynchronize(w->done));
+    w->pending = false;
+    FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
+    ws_drop_graph(w);
+    const int64_t cq = std::max(nq, w->bq_cap_nq);
+    const int32_t cp = std::max(nprobe, w->bq_cap_pairs_np);
+    const uint32_t cc = std::max(cap, w->bq_cap);
+    void *old[] = {w->bq_lcnt, w->bq_lqoff, w->bq_lcur, w->bq_upre, w->bq_lq, w->bq_pbits,
+                   w->bq_tau, w->bq_cnt, w->bq_qsum, w->bq_buf, w->bq_ctr};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    w->bq_lcnt = w->bq_lqoff = w->bq_lcur = w->bq_upre = w->bq_pbits = w->bq_cnt = w->bq_ctr = nullptr;
+    w->bq_lq = nullptr;
+    w->bq_tau = w->bq_buf = nullptr;
+    w->bq_qsum = nullptr;
+    w->bq_cap_nq = 0;
+    dalloc(w->bq_lcnt, (size_t)D.nlist);
+    dalloc(w->bq_lqoff, (size_t)D.nlist + 1);
+    dalloc(w->bq_lcur, (size_t)D.nlist);
+    dalloc(w->bq_upre, (size_t)D.nlist + 1);
+    dalloc(w->bq_lq, (size_t)cq * cp);
+    dalloc(w->bq_pbits, D.n_rep > 0 ? (size_t)cq * ((D.nlist + 31) / 32) : 1);
+    dalloc(w->bq_tau, (size_t)cq);
+    dalloc(w->bq_cnt, (size_t)cq);
+    dalloc(w->bq_qsum, (size_t)cq * 2);
+    dalloc(w->bq_buf, (size_t)cq * cc);
+    dalloc(w->bq_ctr, 8);
+    if (!w->redo) dalloc(w->redo, (size_t)std::max(cq, w->cap_nq));
+    w->bq_cap_nq = cq;
+    w->bq_cap_pairs_np = cp;
+    w->bq_cap = cc;
 }
 
 // Per-tile top-n buffer of the tiled form: 16 tiles per query on average,
@@ -481,6 +554,9 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         FA_REQUIRE(ntop <= 16384, FA_ERR_ARG, "rerank_n above 16384");
     }
     const bool qdev = sp.flags & FA_QUERIES_ON_DEVICE, odev = sp.flags & FA_OUTPUTS_ON_DEVICE;
+    const bool batched = (sp.flags & FA_BATCHED) != 0;
+    FA_REQUIRE(!batched || sp.lut_prec == FA_LUT_F16 || sp.lut_prec == FA_LUT_FP8, FA_ERR_ARG,
+               "the batched form (FA_BATCHED) reads the FP16 or FP8 table");
     const bool global_lut = sp.lut_prec != FA_LUT_F32 || sp.lut_gemm == FA_GEMM_BF16_TC;
     const int elem = sp.lut_prec == FA_LUT_F32 ? 4 : (sp.lut_prec == FA_LUT_F16 ? 2 : 1);
     const int lut_bytes = global_lut ? ix->M * 256 * elem : 0;
@@ -489,6 +565,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     WsLease lease(ix, sp.flags & FA_NONBLOCKING);
     Workspace *w = lease.w;
     ws_ensure(ix, w, nq, k, nprobe, ntop, lut_bytes);
+    if (batched) ws_ensure_batched(ix, w, nq, nprobe, ntop);
     cudaStream_t st = sp.stream ? (cudaStream_t)sp.stream : w->stream;
     if (w->pending) FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->done, 0));
     const DeviceIndex &D = ix->dev;
@@ -508,11 +585,11 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     }
     int tile_chunks = tune.tile_chunks;
     if ((sp.flags & FA_PERSISTENT) && tile_chunks == 0) tile_chunks = 256;
-    if (ntop > 256) tile_chunks = 0;  // the CTA-wide top-n runs one CTA per query
+    if (ntop > 256 || batched) tile_chunks = 0;  // the CTA-wide top-n runs one CTA per query
     if (tile_chunks > 0) ws_ensure_partial(w, nq, ntop);
     // pipelined re-rank (see FA_SERIAL): large batches re-ranked from host memory
-    const bool pipelined = rerank && tile_chunks == 0 && !(sp.flags & FA_SERIAL) && nq >= 4096 &&
-                           D.raw_location == FA_RAW_HOST_PINNED;
+    const bool pipelined = rerank && tile_chunks == 0 && !batched && !(sp.flags & FA_SERIAL) &&
+                           nq >= 4096 && D.raw_location == FA_RAW_HOST_PINNED;
 
     auto enqueue = [&]() {
         FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
@@ -547,7 +624,8 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         }
         tr.mark(1);
         if (global_lut) {
-            launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st);
+            launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st,
+                              batched ? 1 : 0);
             tr.launches += 1;
         }
         tr.mark(2);
@@ -589,6 +667,37 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             launch_scan(D, sl, st);
             launch_tile_merge(w->partial, w->tprefix, nq, ntop, w->topkeys, st);
             tr.launches += 4;
+        } else if (batched) {
+            // batched form: the whole batch scanned list by list (queries
+            // grouped by their first list only orders the threshold sample)
+            launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
+            sl.order = w->order;
+            sl.redo = w->redo;
+            sl.fuse_rerank = (rerank && sp.rerank_eps < 0.f) ? 1 : 0;
+            sl.k = k;
+            sl.kq = kq;
+            sl.rerank_batch = sp.rerank_batch;
+            sl.out_ids = oid;
+            sl.out_dist = odist;
+            BatchBufs bb{};
+            bb.lcnt = w->bq_lcnt;
+            bb.lqoff = w->bq_lqoff;
+            bb.lcur = w->bq_lcur;
+            bb.upre = w->bq_upre;
+            bb.pbits = w->bq_pbits;
+            bb.cnt = w->bq_cnt;
+            bb.ctr = w->bq_ctr;
+            bb.lq = w->bq_lq;
+            bb.tau = w->bq_tau;
+            bb.buf = w->bq_buf;
+            bb.qsum = w->bq_qsum;
+            bb.cap = w->bq_cap;
+            bb.tile_chunks = 1024;
+            // sub-batches whose tables (M x 256 entries a query) fit in ~40 MB of L2
+            bb.qsub = std::max<int64_t>(1024, (40ll << 20) / ((int64_t)D.M * 256 * elem));
+            fused = launch_batched(D, sl, bb, st);
+            const int64_t nsub = (nq + bb.qsub - 1) / bb.qsub;
+            tr.launches += 2 + (int)(4 * nsub) + 2;
         } else if (pipelined) {
             // chunk c's re-rank (on the slot's high-priority stream, waiting on
             // the host link) runs while chunk c + 1 is scanned. Scans alternate
@@ -688,7 +797,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         key.rerank_batch = sp.rerank_batch;
         key.rerank_beta = sp.rerank_beta;
         key.rerank_eps = sp.rerank_eps;
-        key.flags = sp.flags & (FA_PERSISTENT | FA_SERIAL);
+        key.flags = sp.flags & (FA_PERSISTENT | FA_SERIAL | FA_BATCHED);
         key.threads = tune.threads;
         key.ilp = tune.ilp;
         key.persistent = tune.persistent;
@@ -1398,7 +1507,8 @@ fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params 
         cudaStream_t st = w->stream;
         FA_CHECK_CUDA(cudaMemcpyAsync(w->q, query, sizeof(float) * ix->d, cudaMemcpyHostToDevice, st));
         FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
-        launch_lut_global(ix->dev, w->q, 1, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st);
+        launch_lut_global(ix->dev, w->q, 1, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st,
+                          (sp.flags & FA_BATCHED) ? 1 : 0);
         std::vector<uint8_t> raw((size_t)M * 256 * elem);
         std::vector<float> sc(2 * M);
         FA_CHECK_CUDA(cudaMemcpyAsync(raw.data(), w->lut, raw.size(), cudaMemcpyDeviceToHost, st));

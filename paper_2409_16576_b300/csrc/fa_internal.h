@@ -85,6 +85,8 @@ struct DeviceIndex {
     int32_t tc_kp = 0, tc_ntiles = 0;
     void *codebooks_bf16 = nullptr; // tensor-core B tiles [M][hi, lo][256 x 16]
     float *cbnorm = nullptr;        // [M][256] |C_m[c]|^2 (FP32)
+    float cb_max_norm2 = 0.f;       // largest |C_m[c]|^2 (bounds every table entry)
+    uint32_t *lorder = nullptr;     // [nlist] lists by decreasing chunk count (batched form)
     int64_t device_bytes = 0;
     int64_t pinned_bytes = 0;
 };
@@ -139,6 +141,18 @@ struct Workspace {
     uint32_t *tile_ctr = nullptr;  // [4] persistent-kernel work counters
     uint64_t *selbuf = nullptr;    // [2 per SM][2 * cap_ntop] keys below the scan's threshold estimate
     int32_t *redo = nullptr;       // [cap_nq] queries the selecting scan hands to the CTA top-n
+    // batched form (FA_BATCHED): pairs by list, thresholds, per-query key buffers
+    int64_t bq_cap_nq = 0;
+    int32_t bq_cap_pairs_np = 0;
+    uint32_t bq_cap = 0;
+    uint32_t *bq_lcnt = nullptr, *bq_lqoff = nullptr, *bq_lcur = nullptr, *bq_upre = nullptr;
+    int32_t *bq_lq = nullptr;      // [cap_nq * cap_nprobe]
+    uint32_t *bq_pbits = nullptr;  // [cap_nq][nlist / 32]
+    uint64_t *bq_tau = nullptr;    // [cap_nq]
+    uint32_t *bq_cnt = nullptr;    // [cap_nq]
+    float *bq_qsum = nullptr;      // [cap_nq][2]
+    uint64_t *bq_buf = nullptr;    // [cap_nq][bq_cap]
+    uint32_t *bq_ctr = nullptr;    // [8]
     // pinned host staging for host-buffer calls
     float *h_q = nullptr;
     int64_t *h_ids = nullptr;
@@ -282,13 +296,28 @@ void launch_tile_merge(const uint64_t *partial, const uint32_t *prefix, int64_t 
 // written for every query the selecting scan finished; the rest are listed
 // in ScanLaunch::redo, their count in tile_ctr[3]).
 bool launch_scan(const DeviceIndex &ix, const ScanLaunch &a, cudaStream_t st);
+// Buffers of the batched form (list-major scan over the whole batch).
+struct BatchBufs {
+    uint32_t *lcnt, *lqoff, *lcur, *upre, *pbits, *cnt, *ctr;
+    int32_t *lq;
+    uint64_t *tau, *buf;
+    float *qsum;
+    uint32_t cap;          // keys per query buffer
+    uint32_t tile_chunks;  // chunks per unit of a long list
+    int64_t qsub;          // queries per sub-batch
+};
+// Batched form of launch_scan (FP16 table with one scale per query): the
+// same results contract, the same redo list and fused re-rank.
+bool launch_batched(const DeviceIndex &ix, const ScanLaunch &a, const BatchBufs &bb, cudaStream_t st);
 // Standard deviations of the CTA top-n threshold estimate (test hook).
 void set_tau_sigma(float sigma);
 void launch_wait_nothing(uint32_t polls, const uint32_t *flag, uint32_t *err, cudaStream_t st);
 // true when an injected allocation failure (fa_debug_fail_alloc) is due now
 bool alloc_fault();
+// uniform != 0: one scale per query for all subspaces (the batched form sums
+// the stored entries directly)
 void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int prec, int gemm,
-                       void *lut, float *lut_scale, uint32_t *err, cudaStream_t st);
+                       void *lut, float *lut_scale, uint32_t *err, cudaStream_t st, int uniform = 0);
 void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, int32_t ntop,
                    int32_t k, const int32_t *kq, int64_t *out_ids, float *out_dist,
                    cudaStream_t st);

@@ -9,7 +9,10 @@
 // FP32; each entry is off by at most half a unit in the last place of the
 // stored value times s_m.
 //
-// lut_scale row layout per query: [2m] = s_m, [2m + 1] = o_m.
+// lut_scale row layout per query: [2m] = s_m, [2m + 1] = o_m. With a uniform
+// scale (the batched form, which adds stored entries directly) every s_m is
+// the same per-query s_q: here the largest subspace scale, in the tensor-core
+// kernel a bound that needs no pass over the other subspaces.
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
@@ -23,7 +26,7 @@ constexpr float FP8_MAX = 448.f;
 // Stores a FP32 table held in shared memory (t[m*256 + c]) in the requested
 // precision with a per-subspace scale and offset.
 __device__ void store_lut(const float *t, int M, int prec, void *lut, float *scale, int64_t qi,
-                          float *offs, float *scl) {
+                          float *offs, float *scl, int uniform) {
     const int64_t base = qi * (int64_t)M * 256;
     float *sc = scale + qi * 2 * M;
     if (prec == FA_LUT_F32) {
@@ -53,9 +56,18 @@ __device__ void store_lut(const float *t, int M, int prec, void *lut, float *sca
         if (lane == 0) {
             offs[m] = lo;
             scl[m] = s;
-            sc[2 * m] = s;
-            sc[2 * m + 1] = lo;
         }
+    }
+    __syncthreads();
+    // uniform: the largest subspace scale serves every subspace
+    float su = 0.f;
+    if (uniform)
+        for (int m = 0; m < M; ++m) su = fmaxf(su, scl[m]);
+    __syncthreads();
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        if (uniform) scl[m] = su;
+        sc[2 * m] = scl[m];
+        sc[2 * m + 1] = offs[m];
     }
     __syncthreads();
     for (int i = threadIdx.x; i < M * 256; i += blockDim.x) {
@@ -73,7 +85,7 @@ __device__ void store_lut(const float *t, int M, int prec, void *lut, float *sca
 // FP32 direct differences, one CTA per query.
 __global__ void __launch_bounds__(256) k_lut_simt(const float *__restrict__ q, int64_t nq, int32_t d,
                                                   const float *__restrict__ cb, int32_t M, int prec,
-                                                  void *lut, float *scale) {
+                                                  void *lut, float *scale, int uniform) {
     extern __shared__ float sm[];
     float *t = sm;                 // [M][256]
     float *qv = t + M * 256;       // [d]
@@ -94,25 +106,25 @@ __global__ void __launch_bounds__(256) k_lut_simt(const float *__restrict__ q, i
             t[i] = s;
         }
         __syncthreads();
-        store_lut(t, M, prec, lut, scale, qi, offs, scl);
+        store_lut(t, M, prec, lut, scale, qi, offs, scl, uniform);
         __syncthreads();
     }
 }
 
 void launch_lut_tc(const DeviceIndex &ix, const float *q, int64_t nq, int prec, void *lut,
-                   float *lut_scale, uint32_t *err, cudaStream_t st);
+                   float *lut_scale, uint32_t *err, cudaStream_t st, int uniform);
 
 void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int prec, int gemm,
-                       void *lut, float *lut_scale, uint32_t *err, cudaStream_t st) {
+                       void *lut, float *lut_scale, uint32_t *err, cudaStream_t st, int uniform) {
     if (nq == 0) return;
     if (gemm == FA_GEMM_BF16_TC) {
-        launch_lut_tc(ix, q, nq, prec, lut, lut_scale, err, st);
+        launch_lut_tc(ix, q, nq, prec, lut, lut_scale, err, st, uniform);
         return;
     }
     const int smem = (ix.M * 256 + ix.d + 2 * ix.M) * 4;
     FA_CHECK_CUDA(cudaFuncSetAttribute(k_lut_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int grid = (int)std::min<int64_t>(nq, (int64_t)cur_num_sms() * 4);
-    k_lut_simt<<<grid, 256, smem, st>>>(q, nq, ix.d, ix.codebooks, ix.M, prec, lut, lut_scale);
+    k_lut_simt<<<grid, 256, smem, st>>>(q, nq, ix.d, ix.codebooks, ix.M, prec, lut, lut_scale, uniform);
     FA_CHECK_CUDA(cudaGetLastError());
 }
 

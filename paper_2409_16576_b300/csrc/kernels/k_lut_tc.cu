@@ -44,6 +44,8 @@ struct LutTcArgs {
     void *lut;                    // [nq][M][256]
     float *scale;                 // [nq][2M]: (s_m, o_m)
     uint32_t *err;
+    int32_t uniform;              // one scale per query: s_q = 2 (|q|^2 + max |C_m[c]|^2) / format max
+    float cmax2;                  // max over m, c of |C_m[c]|^2
 };
 
 __host__ __device__ inline int lut_elem(int prec) {
@@ -98,6 +100,18 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
     bool failed = false;
     int loaded = -1;  // last subspace whose tile copy thread 0 issued
     const float fmax = a.prec == FA_LUT_F16 ? 65504.f : 448.f;
+    // uniform scale: every entry |q_m - C_m[c]|^2 is at most 2 (|q_m|^2 + |C_m[c]|^2)
+    // <= 2 (|q|^2 + cmax2), so the stored residuals stay within the format
+    float su = 1.f;
+    if (a.uniform && row_ok) {
+        float qq = 0.f;
+        for (int j = 0; j < a.d; ++j) {
+            const float x = a.q[row * a.d + j];
+            qq = fmaf(x, x, qq);
+        }
+        su = 2.f * (qq + a.cmax2) / fmax;
+        if (!(su > 0.f)) su = 1.f;
+    }
     if (tid == 0 && m0 < m1) {
         tc::mbar_expect_tx(&full[0], btile);
         tc::bulk_g2s(Bb, a.btiles + (size_t)m0 * 2 * LN * 16, btile, &full[0]);
@@ -161,7 +175,7 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
                 }
             }
         }
-        float s = (hi - lo) / fmax;
+        float s = a.uniform ? su : (hi - lo) / fmax;
         if (!(s > 0.f)) s = 1.f;
         const float inv = 1.f / s;
         const int64_t base = (row * a.M + m) * 256;
@@ -277,7 +291,7 @@ void prepare_codebook_tiles(const float *cb, int32_t M, int32_t d, std::vector<u
 }
 
 void launch_lut_tc(const DeviceIndex &ix, const float *q, int64_t nq, int prec, void *lut,
-                   float *lut_scale, uint32_t *err, cudaStream_t st) {
+                   float *lut_scale, uint32_t *err, cudaStream_t st, int uniform) {
     FA_REQUIRE(ix.codebooks_bf16 != nullptr, FA_ERR_ARG,
                "the tensor-core LUT needs d <= 128 and d / M dividing 16");
     LutTcArgs a{};
@@ -293,6 +307,8 @@ void launch_lut_tc(const DeviceIndex &ix, const float *q, int64_t nq, int prec, 
     a.lut = lut;
     a.scale = lut_scale;
     a.err = err;
+    a.uniform = uniform;
+    a.cmax2 = ix.cb_max_norm2;
     // widest K-range of one CTA's subspaces (16-wide blocks), two tile buffers,
     // the staged rows; at least 80 KB so that at most two CTAs (2 x 256 TMEM
     // columns) share an SM

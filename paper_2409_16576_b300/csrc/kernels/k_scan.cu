@@ -1226,6 +1226,575 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
 }
 
 // ---------------------------------------------------------------------------
+// Batched form: the whole batch scanned list by list (steps 3-7 for many
+// queries at once). Each (query, probed list) pair of the batch goes in its
+// list's bucket; a unit of work is one list (or a tile of T chunks of a long
+// list) with two of the queries that probe it. The unit's CTA builds a
+// shared-memory table whose 32-bit words hold both queries' FP16 entries, in
+// the rotated layout of the scans above, reads each code row of the list once
+// and takes both queries' distances from one lookup per code byte, adding the
+// FP16 entries in FP32. The entries share one scale per query (s_q) beside a
+// per-subspace offset o_q[m], so that
+//   ADC(q, v) = s_q * sum_m e_q[m][code_m(v)] + sum_m o_q[m].
+// Every key at or below the query's sampled threshold is appended to the
+// query's buffer in global memory; a per-query kernel then selects the top-n
+// by radix selection and, for an exhaustive re-rank of uint8 rows in HBM,
+// re-ranks them. Queries the threshold does not serve (fewer than n keys or
+// more than the buffer below it, or no useful sample) go on the redo list,
+// which the per-query scans take.
+//
+// Dedup (step 5) follows the same probe-set rule: a replica entry (v, l) is
+// kept for a query unless one of v's earlier lists is in that query's probe
+// bitmap (global memory here, one bit per list).
+// ---------------------------------------------------------------------------
+constexpr int BQ_THREADS = 384;  // list scan: 12 warps per CTA
+constexpr int BQ_GMAX = 4;       // queries per unit: two FP16 or four FP8 entries per table word
+
+struct BatchArgs {
+    const uint8_t *codes;
+    const uint32_t *list_beg;
+    const uint64_t *rep_off;
+    const uint32_t *rep_v, *rep_mo;
+    const uint8_t *rep_t;
+    const uint32_t *mem;
+    const uint32_t *lorder;  // [nlist] lists by decreasing chunk count
+    int32_t M, nlist, has_rep, nlw;
+    // the sub-batch: queries q0 .. q0 + nq - 1 of the call
+    const int32_t *probes;  // [call nq][stride]
+    const int32_t *npq;
+    int64_t q0, nq;
+    int32_t nprobe, stride;
+    const void *lut;        // [call nq][M][256] FP16 or FP8, one scale per query
+    int32_t G;              // queries per unit (entries per table word): 2 FP16, 4 FP8
+    const float *qsum;      // [call nq][2]: s_q, sum of the offsets
+    const uint64_t *tau;    // [call nq] threshold keys (0: the query is redone)
+    uint32_t *lcnt, *lqoff, *lcur;  // [nlist], [nlist + 1], [nlist]
+    int32_t *lq;            // queries of each list, bucket by bucket
+    uint32_t *upre;         // [nlist + 1] units before each list rank
+    uint32_t *pbits;        // [call nq][nlw] probed lists
+    uint32_t *cnt;          // [call nq] keys appended
+    uint64_t *buf;          // [call nq][cap]
+    uint32_t cap, T;
+    int32_t *stats;
+    uint32_t *err;
+    uint32_t *ctr;          // unit counter
+};
+
+__device__ __forceinline__ int bq_np(const BatchArgs &b, int64_t q) {
+    int np = b.npq ? b.npq[q] : b.nprobe;
+    return np < 1 ? 1 : (np > b.nprobe ? b.nprobe : np);
+}
+
+// one thread per (query, probe rank): bucket sizes and probe bitmaps
+__global__ void k_bq_count(const BatchArgs b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.nq * b.nprobe) return;
+    const int64_t q = b.q0 + i / b.nprobe;
+    const int j = (int)(i % b.nprobe);
+    if (j >= bq_np(b, q)) return;
+    const int l = b.probes[q * b.stride + j];
+    if (l < 0 || l >= b.nlist) {
+        atomicOr(b.err, DEV_ERR_BOUNDS);
+        return;
+    }
+    atomicAdd(&b.lcnt[l], 1u);
+    if (b.has_rep) atomicOr(&b.pbits[q * b.nlw + (l >> 5)], 1u << (l & 31));
+}
+
+__global__ void k_bq_scatter(const BatchArgs b) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= b.nq * b.nprobe) return;
+    const int64_t q = b.q0 + i / b.nprobe;
+    const int j = (int)(i % b.nprobe);
+    if (j >= bq_np(b, q)) return;
+    const int l = b.probes[q * b.stride + j];
+    if (l < 0 || l >= b.nlist) return;
+    b.lq[atomicAdd(&b.lcur[l], 1u)] = (int32_t)q;
+}
+
+__device__ __forceinline__ uint32_t bq_chunks(const BatchArgs &b, int l) {
+    uint32_t c = (b.list_beg[l + 1] - b.list_beg[l] + 31u) >> 5;
+    if (b.has_rep) c += (uint32_t)((b.rep_off[l + 1] - b.rep_off[l] + 31u) >> 5);
+    return c;
+}
+
+// Exclusive scan of f(i), i < n, by one CTA: out[i] (and out2[i]) = sum of
+// f(j) for j < i, out[n] = the total.
+template <class F>
+__device__ void cta_excl_scan(int n, F f, uint32_t *out, uint32_t *out2, uint32_t *ws) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (n + blockDim.x - 1) / blockDim.x;
+    const int i0 = threadIdx.x * per, i1 = min(n, i0 + per);
+    uint32_t loc = 0;
+    for (int i = i0; i < i1; ++i) loc += f(i);
+    uint32_t inc = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) ws[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t x = lane < nw ? ws[lane] : 0u;
+        uint32_t xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, xi, o);
+            if (lane >= o) xi += y;
+        }
+        ws[lane] = xi - x;
+        if (lane == 31) ws[32] = xi;
+    }
+    __syncthreads();
+    uint32_t run = ws[warp] + inc - loc;
+    for (int i = i0; i < i1; ++i) {
+        out[i] = run;
+        if (out2) out2[i] = run;
+        run += f(i);
+    }
+    if (threadIdx.x == 0) out[n] = ws[32];
+    __syncthreads();
+}
+
+// One CTA: bucket offsets, and units per list rank (query groups x chunk tiles).
+__global__ void __launch_bounds__(1024) k_bq_plan(const BatchArgs b) {
+    __shared__ uint32_t ws[33];
+    cta_excl_scan(b.nlist, [&](int l) { return b.lcnt[l]; }, b.lqoff, b.lcur, ws);
+    cta_excl_scan(
+        b.nlist,
+        [&](int r) {
+            const int l = (int)b.lorder[r];
+            const uint32_t nql = b.lcnt[l], nch = bq_chunks(b, l);
+            if (nql == 0 || nch == 0) return 0u;
+            return ((nql + b.G - 1) / b.G) * ((nch + b.T - 1) / b.T);
+        },
+        b.upre, nullptr, ws);
+}
+
+// Per-query threshold estimate from a strided sample of the query's
+// candidates (as in the selecting scan), and the per-query constants of the
+// table: s_q and the sum of the offsets. A threshold of 0 marks a query the
+// list scan cannot serve (no useful sample); +inf keeps every candidate.
+template <int M, int W>
+__global__ void __launch_bounds__(SEL_THREADS, 2) k_bq_tau(const ScanArgs a, uint64_t *tau,
+                                                           uint32_t *cnt, float *qsum, uint32_t cap,
+                                                           int sch_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, sch_max * 32 * 8 + 8192);
+    const ScanPtrs S(smem, plan, a.nprobe);
+    uint64_t *samp = reinterpret_cast<uint64_t *>(S.tail);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(samp + sch_max * 32);
+    __shared__ int64_t s_q;
+    __shared__ uint32_t s_sel[3];
+    __shared__ unsigned long long s_sel64[2];
+    for (int64_t it = 0;; ++it) {
+        if (threadIdx.x == 0) s_q = next_query(a, it);
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi >= a.nq) break;
+        int np = a.npq ? a.npq[qi] : a.nprobe;
+        np = np < 1 ? 1 : (np > a.nprobe ? a.nprobe : np);
+        int ntop = a.ntopq ? a.ntopq[qi] : a.ntop;
+        ntop = ntop < 1 ? 1 : (ntop > a.ntop ? a.ntop : ntop);
+        query_setup<M, W>(a, S, qi, np);  // ends with a barrier
+        const uint32_t total = S.pref[2 * np];
+        int sch = sch_max;
+        while (sch > 64 && (uint32_t)(2 * sch) > total) sch >>= 1;
+        const bool all = (uint64_t)total * 32 <= (uint64_t)cap;
+        uint64_t t = KEY_INF;
+        if (!all) {
+            t = total >= 2u * (uint32_t)sch
+                    ? sample_tau<M, W>(a, S, np, total, ntop, sch, samp, hist, s_sel64, s_sel)
+                    : KEY_INF;
+            if (t == KEY_INF) t = 0;
+        }
+        if (threadIdx.x == 0) {
+            tau[qi] = t;
+            cnt[qi] = 0;
+            const float *sc = a.lut_scale + qi * 2 * a.M;
+            float o = 0.f;
+            for (int m = 0; m < a.M; ++m) o += sc[2 * m + 1];
+            qsum[2 * qi] = sc[0];
+            qsum[2 * qi + 1] = o;
+            if (a.stats) {
+                int64_t gathered = 0;
+                for (int sgi = 0; sgi < 2 * np; ++sgi) gathered += S.seg_end[sgi] - S.seg_beg[sgi];
+                a.stats[qi * 4 + 0] = (int32_t)gathered;
+                a.stats[qi * 4 + 1] = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Appends the keys of one chunk at or below the query's threshold to its buffer.
+__device__ __forceinline__ void bq_append(const BatchArgs &b, int64_t q, float dist, uint32_t v,
+                                          bool ok, uint32_t thi, int lane) {
+    const uint32_t od = f2o(dist);
+    const bool pass = ok && od <= thi;
+    const uint32_t msk = __ballot_sync(FULL, pass);
+    if (msk) {
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(&b.cnt[q], (uint32_t)__popc(msk));
+        base = __shfl_sync(FULL, base, 0);
+        const uint32_t pos = base + __popc(msk & ((1u << lane) - 1u));
+        if (pass && pos < b.cap) b.buf[q * (int64_t)b.cap + pos] = ((uint64_t)od << 32) | v;
+    }
+}
+
+// Unit u of the plan: its list, first and last chunk, and its queries.
+struct BqUnit {
+    int64_t q[BQ_GMAX];
+    uint32_t thi[BQ_GMAX];
+    float sc[BQ_GMAX], of[BQ_GMAX];
+    uint32_t u, l, c0, c1, nprim;
+};
+
+__device__ __forceinline__ void bq_decode(const BatchArgs &b, uint32_t u, uint32_t total_units,
+                                          BqUnit &x) {
+    x.u = u;
+    if (u >= total_units) return;
+    int lo = 0, hi = b.nlist - 1;  // the last list rank r with upre[r] <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (b.upre[mid] <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    const int l = (int)b.lorder[lo];
+    const uint32_t r = u - b.upre[lo];
+    const uint32_t nql = b.lcnt[l];
+    const uint32_t ngrp = (nql + b.G - 1) / b.G;
+    const uint32_t grp = r % ngrp, tile = r / ngrp;  // groups of one tile run side by side
+    const uint32_t nch = bq_chunks(b, l);
+    x.l = (uint32_t)l;
+    x.nprim = (b.list_beg[l + 1] - b.list_beg[l] + 31u) >> 5;
+    x.c0 = tile * b.T;
+    x.c1 = min(nch, (tile + 1) * b.T);
+    for (int j = 0; j < BQ_GMAX; ++j) {
+        const uint32_t k = grp * b.G + j;
+        if (j < b.G && k < nql) {
+            const int64_t q = b.lq[b.lqoff[l] + k];
+            x.q[j] = q;
+            x.thi[j] = (uint32_t)(b.tau[q] >> 32);
+            x.sc[j] = b.qsum[2 * q];
+            x.of[j] = b.qsum[2 * q + 1];
+        } else {
+            x.q[j] = -1;
+            x.thi[j] = 0;
+            x.sc[j] = 0.f;
+            x.of[j] = 0.f;
+        }
+    }
+}
+
+// The E queries' ADC sums of one rotated code row, E entries per table word:
+// E = 2, FP16 entries added in FP32; E = 4, FP8 (e4m3) entries converted in
+// pairs to half2 and added as half2 over 8 subspaces (at most 8 x 448, well
+// inside FP16), then in FP32.
+template <int M, int W, int E>
+__device__ __forceinline__ void adc_multi(const uint32_t (&w)[M / 4], uint32_t v, const uint32_t *tbl,
+                                          float (&acc)[E]) {
+    const uint32_t r4 = (v & 31u) * 4u;
+    const char *tb = reinterpret_cast<const char *>(tbl);
+    if (E == 2) {
+        float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+        for (int t = 0; t < M; ++t) {
+            uint32_t off;
+            if (W == 64) {
+                off = __byte_perm(w[t >> 2], r4, 0x5504u | ((uint32_t)(t & 3) << 4));
+            } else {
+                const uint32_t c = __byte_perm(w[t >> 2], 0u, 0x4440u | (uint32_t)(t & 3));
+                off = c * (uint32_t)(W * 4) + r4;
+            }
+            const uint32_t x = *reinterpret_cast<const uint32_t *>(tb + off + 4 * t);
+            if (t & 1)
+                asm("{.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tadd.rn.f32.f16 %0, lo, %0;\n\t"
+                    "add.rn.f32.f16 %1, hi, %1;}"
+                    : "+f"(b0), "+f"(b1)
+                    : "r"(x));
+            else
+                asm("{.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\tadd.rn.f32.f16 %0, lo, %0;\n\t"
+                    "add.rn.f32.f16 %1, hi, %1;}"
+                    : "+f"(a0), "+f"(a1)
+                    : "r"(x));
+        }
+        acc[0] = a0 + b0;
+        acc[1] = a1 + b1;
+    } else {
+        float f[4] = {0.f, 0.f, 0.f, 0.f};
+        uint32_t h01 = 0u, h23 = 0u;  // half2 partial sums of queries (0, 1) and (2, 3)
+#pragma unroll
+        for (int t = 0; t < M; ++t) {
+            uint32_t off;
+            if (W == 64) {
+                off = __byte_perm(w[t >> 2], r4, 0x5504u | ((uint32_t)(t & 3) << 4));
+            } else {
+                const uint32_t c = __byte_perm(w[t >> 2], 0u, 0x4440u | (uint32_t)(t & 3));
+                off = c * (uint32_t)(W * 4) + r4;
+            }
+            const uint32_t x = *reinterpret_cast<const uint32_t *>(tb + off + 4 * t);
+            asm("{.reg .b16 lo, hi;\n\t.reg .b32 p, r;\n\tmov.b32 {lo, hi}, %2;\n\t"
+                "cvt.rn.f16x2.e4m3x2 p, lo;\n\tcvt.rn.f16x2.e4m3x2 r, hi;\n\t"
+                "add.rn.f16x2 %0, %0, p;\n\tadd.rn.f16x2 %1, %1, r;}"
+                : "+r"(h01), "+r"(h23)
+                : "r"(x));
+            if ((t & 7) == 7 || t == M - 1) {
+                float x0, x1, x2, x3;
+                asm("{.reg .b16 a, b, c, d;\n\tmov.b32 {a, b}, %4;\n\tmov.b32 {c, d}, %5;\n\t"
+                    "cvt.f32.f16 %0, a;\n\tcvt.f32.f16 %1, b;\n\tcvt.f32.f16 %2, c;\n\tcvt.f32.f16 %3, d;}"
+                    : "=f"(x0), "=f"(x1), "=f"(x2), "=f"(x3)
+                    : "r"(h01), "r"(h23));
+                f[0] += x0;
+                f[1] += x1;
+                f[2] += x2;
+                f[3] += x3;
+                h01 = h23 = 0u;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < E; ++j) acc[j] = f[j];
+    }
+}
+
+template <int M, int W, int E>
+__global__ void __launch_bounds__(BQ_THREADS) k_bq_scan(const BatchArgs b) {
+    extern __shared__ __align__(16) uint32_t tbl[];  // [256][W] words of the E queries' entries
+    __shared__ BqUnit s_unit[2];  // the current unit and the next one
+    constexpr int NW = M / 4;
+    constexpr int P = M + 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t total_units = b.upre[b.nlist];
+    if (threadIdx.x == 0) bq_decode(b, atomicAdd(b.ctr, 1u), total_units, s_unit[0]);
+    __syncthreads();
+    for (int cur = 0;; cur ^= 1) {
+        const BqUnit &U = s_unit[cur];
+        if (U.u >= total_units) break;
+        const int l = (int)U.l;
+        int64_t qs[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) qs[j] = U.q[j];
+        // table word (c, p), p < M + 31: entry [p mod M][c] of each of the E
+        // queries (query j in byte lane j of the word for FP8, half j for
+        // FP16); a thread takes 16 centroids of one subspace, so the lanes of
+        // a warp store consecutive words
+        for (int idx = threadIdx.x; idx < M * 16; idx += blockDim.x) {
+            const int m = idx % M, c0 = (idx / M) * 16;
+            uint32_t wd[16];
+            if (E == 2) {
+                uint32_t h[2][8];
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) h[j][i] = 0u;
+                    if (qs[j] >= 0) {
+                        const uint4 *p = reinterpret_cast<const uint4 *>(
+                            static_cast<const __half *>(b.lut) + (qs[j] * M + m) * 256 + c0);
+                        const uint4 x0 = __ldg(p), x1 = __ldg(p + 1);
+                        h[j][0] = x0.x; h[j][1] = x0.y; h[j][2] = x0.z; h[j][3] = x0.w;
+                        h[j][4] = x1.x; h[j][5] = x1.y; h[j][6] = x1.z; h[j][7] = x1.w;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    wd[i] = __byte_perm(h[0][i >> 1], h[1][i >> 1], (i & 1) ? 0x7632u : 0x5410u);
+            } else {
+                uint32_t e[4][4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    e[j][0] = e[j][1] = e[j][2] = e[j][3] = 0u;
+                    if (qs[j] >= 0) {
+                        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(
+                            static_cast<const uint8_t *>(b.lut) + (qs[j] * M + m) * 256 + c0));
+                        e[j][0] = x.x; e[j][1] = x.y; e[j][2] = x.z; e[j][3] = x.w;
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {  // entries 4i .. 4i + 3 of the four queries
+                    const uint32_t t0 = __byte_perm(e[0][i], e[1][i], 0x5140u);
+                    const uint32_t t1 = __byte_perm(e[2][i], e[3][i], 0x5140u);
+                    const uint32_t t2 = __byte_perm(e[0][i], e[1][i], 0x7362u);
+                    const uint32_t t3 = __byte_perm(e[2][i], e[3][i], 0x7362u);
+                    wd[4 * i + 0] = __byte_perm(t0, t1, 0x5410u);
+                    wd[4 * i + 1] = __byte_perm(t0, t1, 0x7632u);
+                    wd[4 * i + 2] = __byte_perm(t2, t3, 0x5410u);
+                    wd[4 * i + 3] = __byte_perm(t2, t3, 0x7632u);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+#pragma unroll
+                for (int p = 0; p < P; p += M)
+                    if (p + m < P) tbl[(c0 + j) * W + p + m] = wd[j];
+        }
+        __syncthreads();
+        // the next unit is claimed and decoded while this one is scanned
+        if (threadIdx.x == 0) bq_decode(b, atomicAdd(b.ctr, 1u), total_units, s_unit[cur ^ 1]);
+        uint32_t thi[E];
+        float sc[E], of[E];
+        uint32_t kept[E];
+#pragma unroll
+        for (int j = 0; j < E; ++j) {
+            thi[j] = U.thi[j];
+            sc[j] = U.sc[j];
+            of[j] = U.of[j];
+            kept[j] = 0u;
+        }
+        const uint32_t nprim = U.nprim, c1 = U.c1;
+        const uint32_t lb0 = b.list_beg[l], lb1 = b.list_beg[l + 1];
+        // candidate of this lane in chunk g: primary ids directly, replica
+        // entries through the probe-set rule of each query
+        auto locate_bq = [&](uint32_t g, uint32_t &v, bool (&ok)[E]) -> bool {
+            v = 0;
+            bool any = false;
+            if (g < nprim) {
+                v = lb0 + (g << 5) + lane;
+                any = v < lb1;
+#pragma unroll
+                for (int j = 0; j < E; ++j) ok[j] = any && qs[j] >= 0;
+                return any;
+            }
+            const uint64_t e = b.rep_off[l] + ((uint64_t)(g - nprim) << 5) + lane;
+            const bool in = e < b.rep_off[l + 1];
+#pragma unroll
+            for (int j = 0; j < E; ++j) ok[j] = in && qs[j] >= 0;
+            if (in) {
+                v = b.rep_v[e];
+                const uint32_t mo = b.rep_mo[e];
+                const int t = b.rep_t[e];
+                for (int u = 0; u < t; ++u) {
+                    const uint32_t ll = b.mem[mo + u];
+#pragma unroll
+                    for (int j = 0; j < E; ++j)
+                        if (ok[j] && ((b.pbits[qs[j] * b.nlw + (ll >> 5)] >> (ll & 31)) & 1u)) ok[j] = false;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < E; ++j) any = any || ok[j];
+            return any;
+        };
+        constexpr int NWARP = BQ_THREADS / 32;
+        // each warp loads the code rows of its next chunk before it scores the current one
+        uint32_t g = U.c0 + warp;
+        uint32_t v = 0, w[NW];
+        bool ok[E];
+        {
+            const bool any = g < c1 && locate_bq(g, v, ok);
+            if (g >= c1)
+#pragma unroll
+                for (int j = 0; j < E; ++j) ok[j] = false;
+            load_codes<M>(b.codes, v, any, w);
+        }
+        for (; g < c1; g += NWARP) {
+            const uint32_t gn = g + NWARP;
+            uint32_t vn = 0, wn[NW];
+            bool okn[E];
+            const bool anyn = gn < c1 && locate_bq(gn, vn, okn);
+            load_codes<M>(b.codes, vn, anyn, wn);
+            float acc[E];
+            adc_multi<M, W, E>(w, v, tbl, acc);
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                kept[j] += ok[j] ? 1u : 0u;
+                bq_append(b, qs[j], fmaf(acc[j], sc[j], of[j]), v, ok[j], thi[j], lane);
+            }
+            v = vn;
+#pragma unroll
+            for (int i = 0; i < NW; ++i) w[i] = wn[i];
+#pragma unroll
+            for (int j = 0; j < E; ++j) ok[j] = gn < c1 && okn[j];
+        }
+        if (b.stats) {
+#pragma unroll
+            for (int j = 0; j < E; ++j) {
+                uint32_t k = kept[j];
+                for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(FULL, k, o);
+                if (lane == 0 && qs[j] >= 0 && k) atomicAdd(&b.stats[qs[j] * 4 + 1], (int32_t)k);
+            }
+        }
+        __syncthreads();  // the table takes the next unit's queries
+    }
+}
+
+// Per query: the top-n of its buffer (radix selection of the n-th key), then
+// the exhaustive re-rank (fused) or the top-n row (unsorted, or sorted when
+// sort_np > 0: an early-stopping re-rank reads it in order). Queries whose
+// buffer does not hold their top-n go on the redo list.
+__global__ void __launch_bounds__(SEL_THREADS) k_bq_select(const ScanArgs a, const uint64_t *tau,
+                                                           const uint32_t *cnt, const uint64_t *bufs,
+                                                           uint32_t cap, int sort_np, uint32_t *qctr,
+                                                           uint32_t *nredo) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const ScanSmem plan(0, a.d, a.nlist, 0, 1, 8192 + sort_np * 8);
+    const ScanPtrs S(smem, plan, 1);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(S.tail);
+    uint64_t *X = reinterpret_cast<uint64_t *>(S.tail + 8192);
+    __shared__ int64_t s_q;
+    __shared__ uint32_t s_cnt, s_sel[3];
+    __shared__ unsigned long long s_sel64[2];
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const uint32_t slot = atomicAdd(qctr, 1u);
+            s_q = slot < a.nq ? (int64_t)slot : a.nq;
+        }
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi >= a.nq) break;
+        int ntop = a.ntopq ? a.ntopq[qi] : a.ntop;
+        ntop = ntop < 1 ? 1 : (ntop > a.ntop ? a.ntop : ntop);
+        const uint64_t t = tau[qi];
+        const uint32_t c = cnt[qi];
+        const bool all = t == KEY_INF;
+        if (t == 0 || c > cap || (!all && c < (uint32_t)ntop)) {
+            if (threadIdx.x == 0) a.redo[atomicAdd(nredo, 1u)] = (int32_t)qi;
+            __syncthreads();
+            continue;
+        }
+        const uint64_t *buf = bufs + qi * (int64_t)cap;
+        const uint64_t kth = c > (uint32_t)ntop
+                                 ? cta_select_rth(buf, (int)c, nullptr, 0, ntop, hist, s_sel64,
+                                                  s_sel64 + 1, s_sel, s_sel + 1, s_sel + 2)
+                                 : KEY_INF;
+        const int kept_n = c < (uint32_t)ntop ? (int)c : ntop;
+        if (a.fuse_rr) {
+            for (int j = threadIdx.x; j < a.d; j += blockDim.x) S.qv[j] = a.q[qi * a.d + j];
+            __syncthreads();
+            rerank_fused(a, S, qi, buf, c, kth, kept_n, hist, s_sel);
+            continue;
+        }
+        uint64_t *row = a.topkeys + qi * (int64_t)a.ntop;
+        if (threadIdx.x == 0) s_cnt = 0;
+        __syncthreads();
+        for (uint32_t i0 = 0; i0 < c; i0 += blockDim.x) {
+            const uint32_t i = i0 + threadIdx.x;
+            const uint64_t k = i < c ? buf[i] : KEY_INF;
+            const bool keep = i < c && k <= kth;
+            const uint32_t m = __ballot_sync(FULL, keep);
+            if (m) {
+                uint32_t p0 = 0;
+                if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
+                p0 = __shfl_sync(FULL, p0, 0);
+                const uint32_t at = p0 + __popc(m & ((1u << lane) - 1u));
+                if (keep && at < (uint32_t)ntop) {  // keys are distinct: at most ntop pass
+                    if (sort_np) X[at] = k;
+                    else row[at] = k;
+                }
+            }
+        }
+        __syncthreads();
+        if (sort_np) {
+            for (int e = kept_n + threadIdx.x; e < sort_np; e += blockDim.x) X[e] = KEY_INF;
+            __syncthreads();
+            smem_bitonic_sort(X, sort_np);
+            for (int e = threadIdx.x; e < a.ntop; e += blockDim.x) row[e] = e < kept_n ? X[e] : KEY_INF;
+        } else {
+            for (int e = kept_n + threadIdx.x; e < a.ntop; e += blockDim.x) row[e] = KEY_INF;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static int pow2_at_least(int x) {
@@ -1330,8 +1899,7 @@ static std::atomic<float> g_tau_sigma{4.0f};
 
 void set_tau_sigma(float sigma) { g_tau_sigma.store(sigma); }
 
-bool launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
-    if (l.nq == 0) return false;
+static ScanArgs scan_args(const DeviceIndex &ix, const ScanLaunch &l) {
     FA_REQUIRE(l.nprobe <= MAX_PROBE, FA_ERR_ARG, "nprobe above 512");
     FA_REQUIRE(ix.d <= MAX_D, FA_ERR_ARG, "d above 1024");
     FA_REQUIRE(l.ntop >= 1 && l.ntop <= MAX_TOPN, FA_ERR_ARG, "top-n must be in 1..16384");
@@ -1384,6 +1952,12 @@ bool launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
     a.kq = l.kq;
     a.out_ids = l.out_ids;
     a.out_dist = l.out_dist;
+    return a;
+}
+
+bool launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
+    if (l.nq == 0) return false;
+    const ScanArgs a = scan_args(ix, l);
     if (a.tile_prefix) {
         FA_REQUIRE(l.ntop <= 256, FA_ERR_ARG, "the tiled form supports top-n <= 256");
         FA_REQUIRE(l.persistent, FA_ERR_ARG, "the tiled form runs persistent CTAs");
@@ -1394,6 +1968,152 @@ bool launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
         case 32: return launch_scan_m<32, 64>(a, l, st);
         case 48: return launch_scan_m<48, 96>(a, l, st);
         case 64: return launch_scan_m<64, 128>(a, l, st);
+        default: FA_REQUIRE(false, FA_ERR_ARG, "M must be one of 8, 16, 32, 48, 64");
+    }
+    return false;
+}
+
+// Per-query scans of the queries on the redo list (its length on the
+// device): the CTA top-n for n above 256, the per-warp top-n below.
+template <int M, int W>
+static void launch_redo_m(const ScanArgs &b, cudaStream_t st) {
+    ScanLaunch l{};
+    l.persistent = 1;
+    l.nq = b.nq;
+    if (b.ntop <= 256) {
+        if (b.ntop <= 32) launch_warp_variant<M, W, 1, 256, 1>(b, l, st);
+        else if (b.ntop <= 64) launch_warp_variant<M, W, 2, 256, 1>(b, l, st);
+        else if (b.ntop <= 128) launch_warp_variant<M, W, 4, 256, 1>(b, l, st);
+        else launch_warp_variant<M, W, 8, 256, 1>(b, l, st);
+        return;
+    }
+    const int NP = pow2_at_least(b.ntop < 2 * BIG_WARPS * 32 ? 2 * BIG_WARPS * 32 : b.ntop);
+    constexpr int budget = 227 * 1024 - 256;
+    int NB = NP;
+    while (NB > 2 * BIG_WARPS * 32 &&
+           ScanSmem(W, b.d, b.nlist, b.has_rep, b.nprobe, (NP + NB) * 8).total > budget)
+        NB >>= 1;
+    const ScanSmem plan(W, b.d, b.nlist, b.has_rep, b.nprobe, (NP + NB) * 8);
+    FA_REQUIRE(plan.total <= budget, FA_ERR_ARG,
+               "scan shared memory above 227 KB (top-n too large for this M)");
+    set_smem(k_scan_cta<M, W>, plan.total);
+    k_scan_cta<M, W><<<cur_num_sms(), BIG_THREADS, plan.total, st>>>(b, NP, NB);
+    FA_CHECK_CUDA(cudaGetLastError());
+}
+
+template <int M, int W>
+static bool launch_batched_m(const DeviceIndex &ix, const ScanLaunch &l, const BatchBufs &bb,
+                             cudaStream_t st) {
+    const ScanArgs a = scan_args(ix, l);
+    const int nlw = (ix.nlist + 31) / 32;
+    FA_CHECK_CUDA(cudaMemsetAsync(bb.ctr, 0, 8 * sizeof(uint32_t), st));
+    FA_CHECK_CUDA(cudaMemsetAsync(l.tile_ctr, 0, 4 * sizeof(uint32_t), st));
+    if (a.has_rep) FA_CHECK_CUDA(cudaMemsetAsync(bb.pbits, 0, sizeof(uint32_t) * l.nq * nlw, st));
+    // 1. per-query thresholds (a larger sample when the top-n is small)
+    {
+        const int sch_max = l.ntop <= 256 ? 256 : 64;
+        ScanArgs t = a;
+        t.persistent = 1;
+        t.tile_ctr = bb.ctr;
+        t.order = l.order;
+        const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, sch_max * 32 * 8 + 8192);
+        FA_REQUIRE(plan.total <= 227 * 1024, FA_ERR_ARG, "threshold sample above 227 KB");
+        set_smem(k_bq_tau<M, W>, plan.total);
+        k_bq_tau<M, W><<<2 * cur_num_sms(), SEL_THREADS, plan.total, st>>>(t, bb.tau, bb.cnt, bb.qsum,
+                                                                          bb.cap, sch_max);
+        FA_CHECK_CUDA(cudaGetLastError());
+    }
+    // 2. the list scan, sub-batch by sub-batch (the sub-batch's tables stay in L2)
+    BatchArgs b{};
+    b.codes = ix.codes;
+    b.list_beg = ix.list_beg;
+    b.rep_off = ix.rep_off;
+    b.rep_v = ix.rep_v;
+    b.rep_mo = ix.rep_mo;
+    b.rep_t = ix.rep_t;
+    b.mem = ix.mem;
+    b.lorder = ix.lorder;
+    b.M = ix.M;
+    b.nlist = ix.nlist;
+    b.has_rep = a.has_rep;
+    b.nlw = nlw;
+    b.probes = l.probes;
+    b.npq = l.npq;
+    b.nprobe = l.nprobe;
+    b.stride = l.probe_stride;
+    b.lut = l.lut;
+    b.G = l.lut_prec == FA_LUT_FP8 ? 4 : 2;
+    b.qsum = bb.qsum;
+    b.tau = bb.tau;
+    b.lcnt = bb.lcnt;
+    b.lqoff = bb.lqoff;
+    b.lcur = bb.lcur;
+    b.lq = bb.lq;
+    b.upre = bb.upre;
+    b.pbits = bb.pbits;
+    b.cnt = bb.cnt;
+    b.buf = bb.buf;
+    b.cap = bb.cap;
+    b.T = bb.tile_chunks;
+    b.stats = l.stats;
+    b.err = l.err;
+    b.ctr = bb.ctr + 1;
+    const int tsmem = 256 * W * 4;
+    auto kscan = b.G == 4 ? k_bq_scan<M, W, 4> : k_bq_scan<M, W, 2>;
+    set_smem(kscan, tsmem);
+    int per_sm = 0;
+    FA_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kscan, BQ_THREADS, tsmem));
+    FA_REQUIRE(per_sm >= 1, FA_ERR_ARG, "the batched scan's table does not fit shared memory");
+    const int gscan = per_sm * cur_num_sms();
+    for (int64_t q0 = 0; q0 < l.nq; q0 += bb.qsub) {
+        b.q0 = q0;
+        b.nq = std::min<int64_t>(bb.qsub, l.nq - q0);
+        FA_CHECK_CUDA(cudaMemsetAsync(bb.lcnt, 0, sizeof(uint32_t) * ix.nlist, st));
+        FA_CHECK_CUDA(cudaMemsetAsync(bb.ctr + 1, 0, sizeof(uint32_t), st));
+        const int64_t pairs = b.nq * b.nprobe;
+        const unsigned g = (unsigned)((pairs + 255) / 256);
+        k_bq_count<<<g, 256, 0, st>>>(b);
+        k_bq_plan<<<1, 1024, 0, st>>>(b);
+        k_bq_scatter<<<g, 256, 0, st>>>(b);
+        kscan<<<gscan, BQ_THREADS, tsmem, st>>>(b);
+        FA_CHECK_CUDA(cudaGetLastError());
+    }
+    // 3. selection of each query's top-n, and the exhaustive re-rank fused
+    ScanArgs c = a;
+    const bool fused = l.fuse_rerank && a.raw && a.raw_u8 && a.d % 16 == 0 && l.k >= 1 && l.k <= 32 &&
+                       l.out_ids && l.out_dist;
+    c.fuse_rr = fused ? 1 : 0;
+    const int sort_np = (!fused && l.sorted) ? pow2_at_least(std::max(64, l.ntop)) : 0;
+    const int ssmem = ScanSmem(0, a.d, a.nlist, 0, 1, 8192 + sort_np * 8).total;
+    FA_REQUIRE(ssmem <= 227 * 1024, FA_ERR_ARG, "selection shared memory above 227 KB");
+    set_smem(k_bq_select, ssmem);
+    int sel_sm = 0;
+    FA_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sel_sm, k_bq_select, SEL_THREADS, ssmem));
+    k_bq_select<<<std::max(1, sel_sm) * cur_num_sms(), SEL_THREADS, ssmem, st>>>(
+        c, bb.tau, bb.cnt, bb.buf, bb.cap, sort_np, bb.ctr + 2, l.tile_ctr + 3);
+    FA_CHECK_CUDA(cudaGetLastError());
+    // 4. the queries handed back, scanned one CTA per query
+    ScanArgs r = a;
+    r.order = l.redo;
+    r.nq_dev = l.tile_ctr + 3;
+    r.tile_ctr = l.tile_ctr + 2;
+    r.persistent = 1;
+    r.fuse_rr = 0;
+    launch_redo_m<M, W>(r, st);
+    return fused;
+}
+
+bool launch_batched(const DeviceIndex &ix, const ScanLaunch &l, const BatchBufs &bb, cudaStream_t st) {
+    if (l.nq == 0) return false;
+    FA_REQUIRE((l.lut_prec == FA_LUT_F16 || l.lut_prec == FA_LUT_FP8) && l.lut, FA_ERR_ARG,
+               "the batched form reads the FP16 or FP8 table");
+    FA_REQUIRE(l.redo && l.tile_ctr, FA_ERR_ARG, "the batched form needs its redo list");
+    switch (ix.M) {
+        case 8: return launch_batched_m<8, 64>(ix, l, bb, st);
+        case 16: return launch_batched_m<16, 64>(ix, l, bb, st);
+        case 32: return launch_batched_m<32, 64>(ix, l, bb, st);
+        case 48: return launch_batched_m<48, 96>(ix, l, bb, st);
+        case 64: return launch_batched_m<64, 128>(ix, l, bb, st);
         default: FA_REQUIRE(false, FA_ERR_ARG, "M must be one of 8, 16, 32, 48, 64");
     }
     return false;

@@ -81,3 +81,61 @@ def _lowp_adc_bound(q, parts, prec, tc):
         u = np.asarray(ids, np.int64).astype(np.uint32)
         return oracle.adc(b, parts["codes"], u) + 2e-6 * oracle.adc(t, parts["codes"], u) + 1e-3
     return f
+
+
+def _batched_entry_bound(q, parts, tc, prec="F16"):
+    """Per-entry bound [M][256] on |entry - FP64 value| of the batched form's
+    table, which has one scale per query, at most s_q = 2 (|q|^2 + max
+    |C_m[c]|^2) / format max (every entry |q_m - C_m[c]|^2 is below 2 (|q_m|^2
+    + |C_m[c]|^2)): half an ulp of the stored residual (2^-11 relative for
+    FP16, 2^-4 for FP8 e4m3), the subnormal step below the normal range, an
+    FP32 margin, and the tensor-core form's rounding."""
+    cb = parts["codebooks"]
+    ref = oracle.lut(q, cb)
+    resid = ref - ref.min(axis=1, keepdims=True)
+    q64 = np.asarray(q, np.float64)
+    fmax, rel, sub = (65504.0, 2.0 ** -11, 2.0 ** -25) if prec == "F16" else (448.0, 2.0 ** -4, 2.0 ** -10)
+    sq = 2.0 * ((q64 ** 2).sum() + (cb.astype(np.float64) ** 2).sum(2).max()) / fmax * (1 + 1e-6)
+    b = resid * rel + sq * sub + 1e-5 * np.abs(ref) + 1e-3
+    if tc:
+        b = b + 4e-5 * _expanded_magnitude(q, cb) * (1 + rel)
+    return ref, resid, b
+
+
+def _batched_adc_bound(q, parts, tc, prec="F16"):
+    """ids -> bound on |batched-form ADC - FP64 ADC|: the entry bounds the ids'
+    codes pick; for FP8, half2 sums over 8 subspaces (7 roundings of 2^-11
+    relative to a partial sum of stored residuals); FP32 sums of the entries
+    and the offsets, 1e-5 relative."""
+    ref, resid, b = _batched_entry_bound(q, parts, tc, prec)
+
+    def f(ids):
+        u = np.asarray(ids, np.int64).astype(np.uint32)
+        out = oracle.adc(b, parts["codes"], u) + 1e-5 * np.abs(oracle.adc(ref, parts["codes"], u)) + 1e-3
+        if prec == "FP8":
+            out = out + 7 * 2.0 ** -11 * (1 + 2.0 ** -4) * oracle.adc(resid, parts["codes"], u)
+        return out
+    return f
+
+
+def _check_bounded_topn(gi, gd, oi, ref_of, bound_of, what=""):
+    """A top-n computed with perturbed distances (each within bound_of(id) of
+    the oracle's ref_of(id)): ids distinct, keys ascending, every distance
+    within its bound of the oracle's, and every id of the oracle's top-n it
+    leaves out at or beyond its n-th key by that bound."""
+    gi = np.asarray(gi)
+    g = np.asarray(gd, np.float64)
+    ok = gi >= 0
+    assert np.all(np.isfinite(g[ok])) and np.all(~np.isfinite(g[~ok])), what
+    ids = gi[ok]
+    assert len(set(ids.tolist())) == ids.size, what
+    keys = list(zip(g[ok].tolist(), ids.tolist()))
+    assert keys == sorted(keys), what
+    r, b = ref_of(ids), bound_of(ids)
+    assert np.all(np.abs(g[ok] - r) <= b), (what, float(np.max(np.abs(g[ok] - r) - b)))
+    oset = set(int(x) for x in np.asarray(oi) if x >= 0)
+    missing = np.array(sorted(oset - set(ids.tolist())), np.int64)
+    if missing.size:
+        assert ok.all(), what  # a short row must hold every candidate
+        T = g[ok][-1]
+        assert np.all(ref_of(missing) + bound_of(missing) >= T), what
