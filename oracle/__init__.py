@@ -90,6 +90,10 @@ def lib():
                                      i32, i32, f32, i32, P, P, P, i32]
         _lib.or_search_m.restype = i32
         _lib.or_knn_m.argtypes = [P, i64, P, i32, i64, i32, i32, P, P, i32]
+        _lib.or_page_layout.argtypes = [P, i64, i32, i32, P, P]
+        _lib.or_page_layout.restype = i64
+        _lib.or_rerank_pages.argtypes = [P, i32, P, i32, P, i32, i32, i32, f32, i32, P, P, P, i32, P]
+        _lib.or_rerank_pages.restype = i32
     return _lib
 
 
@@ -281,3 +285,29 @@ def recall_at(found_ids, gt_ids, gt_dist, exact_found_dist=None, at=10):
                 h += 1
         hits[i] = min(h, at) / at
     return float(hits.mean())
+
+
+def page_layout(primary, nlist, cap):
+    """§4.3's storage layout: (page of each vector, slot in its page, pages)."""
+    pr = _c(primary, np.int32)
+    n = pr.shape[0]
+    page_of = np.empty(n, dtype=np.int64)
+    slot_of = np.empty(n, dtype=np.int32)
+    np_ = lib().or_page_layout(_p(pr), n, nlist, cap, _p(page_of), _p(slot_of))
+    return page_of, slot_of, int(np_)
+
+
+def rerank_pages(query, raw, tasks, k, page_of, batch=32, eps=0.0, beta=2, metric=L2):
+    """Algorithm 1 with §4.3's intra- and inter-mini-batch I/O deduplication:
+    (ids, exact dists, mini-batches run, pages read)."""
+    q = _c(query, np.float32).reshape(-1)
+    r = np.ascontiguousarray(raw)
+    t = _c(tasks, np.int64)
+    pg = _c(page_of, np.int64)
+    oi = np.empty(k, dtype=np.int64)
+    od = np.empty(k, dtype=np.float64)
+    reads = C.c_int64(0)
+    nb = lib().or_rerank_pages(_p(q), q.shape[0], _p(r), raw_kind(r), _p(t), t.shape[0], k, batch,
+                               float(eps), beta, _p(pg), _p(oi), _p(od), metric, C.byref(reads))
+    return oi, od, int(nb), int(reads.value)
+

@@ -485,3 +485,121 @@ void or_knn(const float *queries, int64_t nq, const void *base, int32_t raw_dtyp
 {
     or_knn_m(queries, nq, base, raw_dtype, n, d, k, out_ids, out_dist, OR_L2);
 }
+
+/* ---------------------------------------------------------------------------
+ * Redundancy-aware I/O deduplication (§4.3).
+ *
+ * Storage layout: list l's bucket holds the raw vectors whose primary list is
+ * l (a vector is stored once, in one bucket), in ascending id order. A page
+ * holds cap vectors. Each bucket first fills whole pages of its own; the
+ * rest of it (its unaligned portion, 0 < size < cap) is a tail, and tails are
+ * combined into shared pages by a max-min rule: the largest tail not yet
+ * placed opens a page, then the smallest remaining tails join it in
+ * ascending size while they fit; ties by list id. Pages are numbered in the
+ * order they are created: every bucket's whole pages first (by list id),
+ * then the shared pages. page_of[v] and slot_of[v] give a vector's page and
+ * position in it. Returns the number of pages.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int64_t size;
+    int32_t list;
+} tail_t;
+
+static int tail_desc(const void *pa, const void *pb)
+{
+    const tail_t *a = (const tail_t *)pa, *b = (const tail_t *)pb;
+    if (a->size != b->size) return a->size > b->size ? -1 : 1;
+    return (a->list > b->list) - (a->list < b->list);
+}
+
+int64_t or_page_layout(const int32_t *primary, int64_t n, int32_t nlist, int32_t cap,
+                       int64_t *page_of, int32_t *slot_of)
+{
+    int64_t *cnt = (int64_t *)calloc((size_t)nlist + 1, sizeof(int64_t));
+    for (int64_t v = 0; v < n; ++v) cnt[primary[v] + 1]++;
+    for (int32_t l = 0; l < nlist; ++l) cnt[l + 1] += cnt[l];
+    int64_t *mem = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)nlist);
+    for (int32_t l = 0; l < nlist; ++l) fill[l] = cnt[l];
+    for (int64_t v = 0; v < n; ++v) mem[fill[primary[v]]++] = v; /* ascending ids per bucket */
+    int64_t page = 0;
+    tail_t *tails = (tail_t *)malloc(sizeof(tail_t) * (size_t)(nlist > 0 ? nlist : 1));
+    int32_t nt = 0;
+    for (int32_t l = 0; l < nlist; ++l) {
+        const int64_t b = cnt[l], e = cnt[l + 1], whole = (e - b) / cap;
+        for (int64_t t = 0; t < whole * cap; ++t) {
+            page_of[mem[b + t]] = page + t / cap;
+            slot_of[mem[b + t]] = (int32_t)(t % cap);
+        }
+        page += whole;
+        if ((e - b) % cap) {
+            tails[nt].size = (e - b) % cap;
+            tails[nt].list = l;
+            ++nt;
+        }
+    }
+    qsort(tails, (size_t)nt, sizeof(tail_t), tail_desc);
+    char *used = (char *)calloc((size_t)(nt > 0 ? nt : 1), 1);
+    int32_t hi = 0, lo = nt - 1; /* largest and smallest unplaced tails */
+    while (hi <= lo) {
+        if (used[hi]) { ++hi; continue; }
+        int64_t room = cap, slot = 0;
+        int32_t pick = hi;
+        for (;;) {
+            const int32_t l = tails[pick].list;
+            const int64_t b = cnt[l + 1] - tails[pick].size;
+            for (int64_t t = 0; t < tails[pick].size; ++t) {
+                page_of[mem[b + t]] = page;
+                slot_of[mem[b + t]] = (int32_t)(slot + t);
+            }
+            slot += tails[pick].size;
+            room -= tails[pick].size;
+            used[pick] = 1;
+            while (lo > hi && used[lo]) --lo;
+            if (lo <= hi || tails[lo].size > room) break;
+            pick = lo;
+        }
+        ++page;
+        ++hi;
+    }
+    free(used);
+    free(tails);
+    free(fill);
+    free(mem);
+    free(cnt);
+    return page;
+}
+
+/* Algorithm 1 (as or_rerank_m) counting page reads: each mini-batch reads
+ * the distinct pages of its tasks once (intra-mini-batch merge), except pages
+ * the query read in an earlier mini-batch, which its buffer holds
+ * (inter-mini-batch deduplication); *pages_read receives the total. */
+int32_t or_rerank_pages(const float *q, int32_t d, const void *raw, int32_t raw_dtype,
+                        const int64_t *tasks, int32_t ntasks, int32_t k, int32_t batch, float eps,
+                        int32_t beta, const int64_t *page_of, int64_t *out_ids, double *out_dist,
+                        int32_t metric, int64_t *pages_read)
+{
+    int32_t valid = 0;
+    while (valid < ntasks && tasks[valid] >= 0) ++valid;
+    int32_t nb = or_rerank_m(q, d, raw, raw_dtype, tasks, ntasks, k, batch, eps, beta, out_ids,
+                             out_dist, metric);
+    int64_t *buf = (int64_t *)malloc(sizeof(int64_t) * (size_t)(valid > 0 ? valid : 1));
+    int64_t nbuf = 0, reads = 0;
+    for (int32_t b = 0; b < nb; ++b) {
+        const int32_t i0 = b * batch, i1 = i0 + batch < valid ? i0 + batch : valid;
+        for (int32_t j = i0; j < i1; ++j) {
+            const int64_t pg = page_of[tasks[j]];
+            int seen = 0;
+            for (int64_t t = 0; t < nbuf; ++t)
+                if (buf[t] == pg) { seen = 1; break; }
+            if (!seen) {
+                buf[nbuf++] = pg;
+                ++reads;
+            }
+        }
+    }
+    free(buf);
+    *pages_read = reads;
+    return nb;
+}
+

@@ -424,3 +424,81 @@ def test_rerank_ip_never_stopping_is_exact_topk():
     assert oi.tolist() == tasks[order].tolist()
     np.testing.assert_allclose(od, ip[order], rtol=0, atol=1e-9)
     assert nb == 4  # ceil(120 / 32) mini-batches
+
+
+# ---------------------------------------------------------------------------
+# §4.3: storage layout and redundancy-aware I/O deduplication
+# ---------------------------------------------------------------------------
+
+def test_io_dedup_worked_example(golden_dir):
+    """The paper's example: mini-batch 0 merges V2 and V6 into one read of P0
+    and reads P2 for V4 (2 I/Os); mini-batch 1 finds P2 in the buffer for V5
+    and reads P1 and P3 (2 I/Os)."""
+    g = json.load(open(os.path.join(golden_dir, "io_dedup_example.json")))
+    page_of = np.full(10, 7, np.int64)
+    for v, p in g["page_of"].items():
+        page_of[int(v)] = p
+    raw = np.arange(40, dtype=np.float32).reshape(10, 4)
+    q = np.zeros(4, np.float32)
+    for nb_wanted, reads_wanted in ((1, g["pages_read_per_mini_batch"][0]), (2, g["pages_read"])):
+        tasks = np.array(g["tasks"][:nb_wanted * g["batch"]], np.int64)
+        _, _, nb, reads = oracle.rerank_pages(q, raw, tasks, 2, page_of, batch=g["batch"], eps=-1.0, beta=1)
+        assert (nb, reads) == (nb_wanted, reads_wanted)
+
+
+def test_page_layout_hand_example():
+    """Buckets of 40, 20, 10 and 5 vectors, 32 a page: list 0 fills page 0
+    and leaves a tail of 8; the tails (20, 10, 8, 5) pair max with min: page 1
+    = {20, 5}, page 2 = {10, 8} (8 + 20 would not fit)."""
+    prim = np.repeat(np.arange(4), [40, 20, 10, 5]).astype(np.int32)
+    page_of, slot_of, npg = oracle.page_layout(prim, 4, 32)
+    assert npg == 3
+    pages = [sorted(set(page_of[prim == l].tolist())) for l in range(4)]
+    assert pages == [[0, 2], [1], [2], [1]]
+    # list 0's first 32 vectors (ascending ids) fill page 0 in order
+    assert page_of[:32].tolist() == [0] * 32 and slot_of[:32].tolist() == list(range(32))
+
+
+def test_page_layout_is_a_packing():
+    """Random buckets: every vector has one (page, slot), no slot twice, no
+    page above its capacity, every bucket's whole pages its own, and no more
+    pages than the whole pages plus the tails need (each shared page holds at
+    least one tail; a tail never splits)."""
+    rng = _rng(41)
+    nlist, cap = 50, 32
+    sizes = rng.integers(0, 90, size=nlist)
+    prim = np.repeat(np.arange(nlist), sizes).astype(np.int32)
+    rng.shuffle(prim)
+    page_of, slot_of, npg = oracle.page_layout(prim, nlist, cap)
+    n = prim.shape[0]
+    pairs = set(zip(page_of.tolist(), slot_of.tolist()))
+    assert len(pairs) == n and slot_of.min() >= 0 and slot_of.max() < cap
+    assert page_of.min() == 0 and page_of.max() == npg - 1
+    per_page = np.bincount(page_of, minlength=npg)
+    assert per_page.max() <= cap
+    whole = int((sizes // cap).sum())
+    tails = int((sizes % cap > 0).sum())
+    assert -(-n // cap) <= npg <= whole + tails
+    for l in range(nlist):  # a bucket's tail sits in one page
+        t = sizes[l] % cap
+        if t:
+            pg = page_of[prim == l]
+            vals, cnts = np.unique(pg, return_counts=True)
+            assert (cnts == t).sum() >= 1 or t == cap
+
+
+def test_io_dedup_counts_distinct_new_pages():
+    """One mini-batch reads exactly the distinct pages of its tasks; with the
+    buffer, a re-rank reads each distinct page once in all; Algorithm 1's
+    results do not change."""
+    rng = _rng(43)
+    raw = rng.integers(0, 256, size=(400, 16)).astype(np.uint8)
+    page_of = rng.integers(0, 40, size=400).astype(np.int64)
+    q = rng.integers(0, 256, size=16).astype(np.float32)
+    tasks = rng.permutation(400)[:96].astype(np.int64)
+    oi, od, nb, reads = oracle.rerank_pages(q, raw, tasks, 10, page_of, batch=96, eps=-1.0, beta=1)
+    assert nb == 1 and reads == len(set(page_of[tasks].tolist()))
+    oi2, od2, nb2, reads2 = oracle.rerank_pages(q, raw, tasks, 10, page_of, batch=16, eps=-1.0, beta=1)
+    assert nb2 == 6 and reads2 == reads
+    ri, rd, _ = oracle.rerank(q, raw, tasks, 10, batch=16, eps=-1.0, beta=1)
+    assert oi2.tolist() == ri.tolist() and np.array_equal(od2, rd)
