@@ -56,7 +56,9 @@ typedef enum fa_status {
     FA_ERR_NODEV = 9     /* no usable CUDA device */
 } fa_status;
 
-typedef enum fa_dtype { FA_F32 = 0, FA_U8 = 1 } fa_dtype;
+/* Element type of base and raw vectors: float32, uint8 (SIFT-like) or int8
+ * (SPACEV-like, Table 1). Queries are always float32. */
+typedef enum fa_dtype { FA_F32 = 0, FA_U8 = 1, FA_I8 = 2 } fa_dtype;
 
 /* Where the raw vectors used by the re-rank live. The paper keeps them on SSD
  * (§4.1 "Raw Vectors on SSDs"); pinned host memory read by the GPU over the
@@ -66,6 +68,13 @@ typedef enum fa_raw_location {
     FA_RAW_HOST_PINNED = 1,
     FA_RAW_DEVICE = 2
 } fa_raw_location;
+
+/* Distance of the search. L2: squared L2 (Eq. 1 as the paper writes it). IP:
+ * the negated inner product -<q, x>, which also splits over subspaces, so
+ * the table entries are -<q_m, C_m[c]>, the coarse probe ranks lists by
+ * -<q, c> and the re-rank uses the exact -<q, x>; the lists themselves come
+ * from L2 k-means either way (the SPACEV-like workload's second metric). */
+typedef enum fa_metric { FA_METRIC_L2 = 0, FA_METRIC_IP = 1 } fa_metric;
 
 /* Storage precision of the per-query lookup table (step 1). The scan always
  * accumulates in FP32; F16 and FP8 (e4m3) tables carry a per-query scale and
@@ -86,14 +95,20 @@ typedef enum fa_gemm { FA_GEMM_SIMT_F32 = 0, FA_GEMM_BF16_TC = 1 } fa_gemm;
 
 typedef struct fa_build_params {
     int32_t nlist;             /* posting lists (IVF cells), >= 1 */
-    int32_t M;                 /* PQ subspaces; d % M == 0; M in {8,16,32,48,64} */
+    int32_t M;                 /* PQ subspaces; d % M == 0, d / M <= 16, M <= 64 (the
+                                * scans run 8, 16, 32, 48 or 64 subspaces; a
+                                * smaller M is padded with subspaces whose codes
+                                * and table entries are 0) */
     int32_t kmeans_iters;      /* Lloyd iterations of the coarse and PQ k-means */
     int32_t max_lists_per_vec; /* Eq. 2 cap on lists per vector, 1..8 */
     int64_t train_sample;      /* rows sampled for training; 0 = automatic */
     uint64_t seed;             /* seed of every random choice of the build */
-    float repl_eps;            /* Eq. 2 epsilon; 0 = each vector in one list */
+    float repl_eps;            /* Eq. 2 epsilon; 0 = each vector in one list; < 0 =
+                                * chosen by bisection so that a vector joins
+                                * -repl_eps lists on average (e.g. -1.08) */
     int32_t raw_location;      /* fa_raw_location: keep raw vectors for re-rank */
     int32_t use_gpu;           /* 1 = run assignment and encoding on the GPU */
+    int32_t metric;            /* fa_metric of the searches on this index */
 } fa_build_params;
 
 /* Fills p with defaults: nlist 256, M 16, 10 iterations, 1 list per vector,
@@ -106,7 +121,11 @@ void fa_build_params_init(fa_build_params *p);
  * boundary replication (a vector joins every list C_i with
  * |v - C_i| <= (1 + repl_eps) |v - C_1|, at most max_lists_per_vec lists),
  * PQ training (M sub-codebooks of 256 centroids over contiguous blocks of
- * d/M coordinates, §2.2) and encoding. n must be below 2^32.
+ * d/M coordinates, §2.2) and encoding. n must be below 2^32. With use_gpu and
+ * nlist >= 32768 the lists come from two-level k-means (about sqrt(nlist)
+ * top-level clusters, each split into its share of the lists, as the paper's
+ * hierarchical clustering of §4.1), and a vector's lists are looked up among
+ * the lists of its three nearest top-level clusters.
  * Returns FA_ERR_ARG for bad shapes, FA_ERR_OOM / FA_ERR_CUDA on failure. */
 fa_status fa_build_index(const void *base, int64_t n, int32_t d, fa_dtype dt,
                          const fa_build_params *p, fa_index **out);
@@ -135,6 +154,8 @@ typedef struct fa_index_parts {
     const int64_t *rep_off;   /* [nlist+1] replica slice offsets, or NULL */
     const int64_t *rep_ids;   /* [rep_off[nlist]] replicated vector ids */
     const void *raw;          /* [n][d] raw vectors, or NULL */
+    int32_t metric;           /* fa_metric */
+    int32_t pad1;
 } fa_index_parts;
 
 /* Builds an index from given parts (no training): list l holds the vectors
@@ -199,7 +220,7 @@ void fa_free_index(fa_index *ix);
                                   * carries one scale per query (fa_debug_lut
                                   * with this flag returns that table). FP16
                                   * entries are summed in FP32; FP8 entries in
-                                  * half2 over 8 subspaces, then in FP32. */
+                                  * half2 over 16 subspaces, then in FP32. */
 
 /* Optional per-call trace, measured with CUDA events on the call's stream
  * (ms of device time per stage; launches = kernels this call launched). An

@@ -25,10 +25,11 @@ _lib = C.CDLL(LIB_PATH)
 # --- enums and flags (include/fa.h) ----------------------------------------
 FA_OK, FA_ERR_ARG, FA_ERR_OOM, FA_ERR_CUDA, FA_ERR_TIMEOUT = 0, 1, 2, 3, 4
 FA_ERR_OVERFLOW, FA_ERR_STATE, FA_ERR_BUSY, FA_ERR_IO, FA_ERR_NODEV = 5, 6, 7, 8, 9
-FA_F32, FA_U8 = 0, 1
+FA_F32, FA_U8, FA_I8 = 0, 1, 2
 FA_RAW_NONE, FA_RAW_HOST_PINNED, FA_RAW_DEVICE = 0, 1, 2
 FA_LUT_F32, FA_LUT_F16, FA_LUT_FP8 = 0, 1, 2
 FA_GEMM_SIMT_F32, FA_GEMM_BF16_TC = 0, 1
+FA_METRIC_L2, FA_METRIC_IP = 0, 1
 FA_QUERIES_ON_DEVICE, FA_OUTPUTS_ON_DEVICE, FA_NONBLOCKING = 0x1, 0x2, 0x4
 FA_PERSISTENT, FA_NO_SYNC, FA_GRAPH, FA_SERIAL, FA_BATCHED = 0x8, 0x10, 0x20, 0x40, 0x80
 
@@ -39,13 +40,14 @@ i32, i64, u64, f32 = C.c_int32, C.c_int64, C.c_uint64, C.c_float
 class fa_build_params(C.Structure):
     _fields_ = [("nlist", i32), ("M", i32), ("kmeans_iters", i32), ("max_lists_per_vec", i32),
                 ("train_sample", i64), ("seed", u64), ("repl_eps", f32), ("raw_location", i32),
-                ("use_gpu", i32)]
+                ("use_gpu", i32), ("metric", i32)]
 
 
 class fa_index_parts(C.Structure):
     _fields_ = [("n", i64), ("d", i32), ("nlist", i32), ("M", i32), ("raw_dtype", i32),
                 ("raw_location", i32), ("pad0", i32), ("centroids", P), ("codebooks", P),
-                ("codes", P), ("primary", P), ("rep_off", P), ("rep_ids", P), ("raw", P)]
+                ("codes", P), ("primary", P), ("rep_off", P), ("rep_ids", P), ("raw", P),
+                ("metric", i32), ("pad1", i32)]
 
 
 class fa_index_info(C.Structure):
@@ -209,20 +211,29 @@ class Index:
             return np.frombuffer(buf, dtype=dt).reshape(shape).copy()
 
         rep_off = arr(p.rep_off, np.int64, (nl + 1,))
-        out = dict(n=n, d=d, nlist=nl, M=M, raw_dtype=p.raw_dtype,
+        out = dict(n=n, d=d, nlist=nl, M=M, raw_dtype=p.raw_dtype, metric=p.metric,
                    centroids=arr(p.centroids, np.float32, (nl, d)),
                    codebooks=arr(p.codebooks, np.float32, (M, 256, d // M)),
                    codes=arr(p.codes, np.uint8, (n, M)),
                    primary=arr(p.primary, np.int32, (n,)),
                    rep_off=rep_off, rep_ids=arr(p.rep_ids, np.int64, (int(rep_off[-1]),)))
-        out["raw"] = arr(p.raw, np.uint8 if p.raw_dtype == FA_U8 else np.float32, (n, d)) \
+        out["raw"] = arr(p.raw, {FA_U8: np.uint8, FA_I8: np.int8}.get(p.raw_dtype, np.float32), (n, d)) \
             if (p.raw and with_raw) else None
         return out
 
 
+def _dtype_of(a: np.ndarray) -> int:
+    """fa_dtype of a base / raw array: uint8, int8, else float32."""
+    if a.dtype == np.uint8:
+        return FA_U8
+    if a.dtype == np.int8:
+        return FA_I8
+    return FA_F32
+
+
 def fa_build_index(base: np.ndarray, params: fa_build_params | None = None) -> Index:
     base = np.ascontiguousarray(base)
-    dt = FA_U8 if base.dtype == np.uint8 else FA_F32
+    dt = _dtype_of(base)
     if dt == FA_F32:
         base = np.ascontiguousarray(base, dtype=np.float32)
     h = P()
@@ -235,7 +246,7 @@ def fa_build_index_lists(base: np.ndarray, centroids: np.ndarray, primary: np.nd
                          params: fa_build_params | None = None) -> Index:
     """Index over lists the caller already has (PQ trained and encoded here)."""
     base = np.ascontiguousarray(base)
-    dt = FA_U8 if base.dtype == np.uint8 else FA_F32
+    dt = _dtype_of(base)
     if dt == FA_F32:
         base = np.ascontiguousarray(base, dtype=np.float32)
     cent = np.ascontiguousarray(centroids, dtype=np.float32)
@@ -248,7 +259,7 @@ def fa_build_index_lists(base: np.ndarray, centroids: np.ndarray, primary: np.nd
 
 
 def fa_index_from_parts(centroids, codebooks, codes, primary, rep_off=None, rep_ids=None,
-                        raw=None, raw_location=FA_RAW_HOST_PINNED) -> Index:
+                        raw=None, raw_location=FA_RAW_HOST_PINNED, metric=FA_METRIC_L2) -> Index:
     cent = np.ascontiguousarray(centroids, dtype=np.float32)
     cb = np.ascontiguousarray(codebooks, dtype=np.float32)
     cd = np.ascontiguousarray(codes, dtype=np.uint8)
@@ -260,10 +271,11 @@ def fa_index_from_parts(centroids, codebooks, codes, primary, rep_off=None, rep_
     p = fa_index_parts()
     p.n, p.d = cd.shape[0], cent.shape[1]
     p.nlist, p.M = cent.shape[0], cd.shape[1]
-    p.raw_dtype = FA_U8 if (rw is not None and rw.dtype == np.uint8) else FA_F32
-    if rw is not None and rw.dtype != np.uint8:
+    p.raw_dtype = _dtype_of(rw) if rw is not None else FA_F32
+    if rw is not None and p.raw_dtype == FA_F32:
         rw = np.ascontiguousarray(rw, dtype=np.float32)
     p.raw_location = raw_location if rw is not None else FA_RAW_NONE
+    p.metric = metric
     p.centroids, p.codebooks, p.codes, p.primary = _ptr(cent), _ptr(cb), _ptr(cd), _ptr(pr)
     p.rep_off, p.rep_ids = _ptr(ro), _ptr(ri)
     p.raw = _ptr(rw)

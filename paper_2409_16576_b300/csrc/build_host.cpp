@@ -21,6 +21,9 @@
 namespace fa {
 namespace {
 
+// lists from which the GPU build clusters in two levels
+constexpr int32_t TWO_LEVEL_LISTS = 32768;
+
 // SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the build's only random source.
 struct SplitMix {
     uint64_t s;
@@ -36,9 +39,12 @@ struct SplitMix {
 };
 
 void row_f32(const void *base, fa_dtype dt, int32_t d, int64_t i, float *out) {
-    if (dt == FA_F32)
+    if (dt == FA_F32) {
         memcpy(out, (const float *)base + i * d, sizeof(float) * d);
-    else {
+    } else if (dt == FA_I8) {
+        const int8_t *p = (const int8_t *)base + i * d;
+        for (int j = 0; j < d; ++j) out[j] = (float)p[j];
+    } else {
         const uint8_t *p = (const uint8_t *)base + i * d;
         for (int j = 0; j < d; ++j) out[j] = (float)p[j];
     }
@@ -145,6 +151,110 @@ std::vector<float> kmeans(const float *X, int64_t n, int32_t d, int32_t K, int i
     return C;
 }
 
+// Two-level k-means for many lists (the paper clusters with a hierarchical
+// balanced algorithm, §4.1): K1 ~ sqrt(nlist) top-level clusters by Lloyd
+// k-means on a sub-sample, then each cluster's share of the nlist lists
+// (proportional to its sample rows, largest remainder, at least one) by Lloyd
+// k-means in which a row looks among the lists of its three nearest
+// top-level clusters. Returns the list centroids grouped by
+// top-level cluster: lists sub_beg[t] .. sub_beg[t + 1] - 1 belong to
+// cluster t, whose centroid is top[t].
+std::vector<float> kmeans_two_level(const float *X, int64_t n, int32_t d, int32_t nlist, int iters,
+                                    uint64_t seed, std::vector<float> &top,
+                                    std::vector<int32_t> &sub_beg) {
+    int32_t K1 = (int32_t)llround(sqrt((double)nlist));
+    K1 = std::max(2, std::min(K1, std::min<int32_t>(nlist, 2048)));
+    const int64_t S1 = std::min<int64_t>(n, 256ll * K1);
+    std::vector<float> X1((size_t)S1 * d);
+    for (int64_t i = 0; i < S1; ++i) memcpy(&X1[(size_t)i * d], X + ((i * n) / S1) * d, sizeof(float) * d);
+    top = kmeans(X1.data(), S1, d, K1, iters, seed ^ 0x746f70ull, true);
+
+    // the sample's top-level clusters and each cluster's list count
+    std::vector<int32_t> cl(n);
+    gpu_assign_topr(X, n, d, FA_F32, top.data(), K1, 1, cl.data(), nullptr);
+    std::vector<int64_t> cnt(K1, 0);
+    for (int64_t i = 0; i < n; ++i) cnt[cl[i]]++;
+    std::vector<int32_t> K2(K1, 1);
+    {
+        const int64_t spare = nlist - K1;  // one list each, then the rest by rows
+        std::vector<std::pair<double, int32_t>> frac(K1);
+        int64_t given = 0;
+        for (int t = 0; t < K1; ++t) {
+            const double share = (double)spare * (double)cnt[t] / (double)n;
+            const int64_t f = (int64_t)share;
+            K2[t] += (int32_t)f;
+            given += f;
+            frac[t] = {share - (double)f, t};
+        }
+        std::sort(frac.begin(), frac.end(), [](const std::pair<double, int32_t> &a,
+                                               const std::pair<double, int32_t> &b) {
+            return a.first != b.first ? a.first > b.first : a.second < b.second;
+        });
+        for (int64_t i = 0; i < spare - given; ++i) K2[frac[(size_t)(i % K1)].second]++;
+    }
+    sub_beg.assign(K1 + 1, 0);
+    for (int t = 0; t < K1; ++t) sub_beg[t + 1] = sub_beg[t] + K2[t];
+
+    // members of each cluster, then the initial lists: evenly spaced members
+    std::vector<int64_t> off(K1 + 1, 0), mem(n);
+    for (int t = 0; t < K1; ++t) off[t + 1] = off[t] + cnt[t];
+    {
+        std::vector<int64_t> fill(off.begin(), off.end() - 1);
+        for (int64_t i = 0; i < n; ++i) mem[fill[cl[i]]++] = i;
+    }
+    std::vector<float> C((size_t)nlist * d);
+    SplitMix rng(seed ^ 0x7375626cull);
+    for (int t = 0; t < K1; ++t)
+        for (int32_t j = 0; j < K2[t]; ++j) {
+            float *c = &C[(size_t)(sub_beg[t] + j) * d];
+            if (cnt[t] > 0) {
+                memcpy(c, X + mem[off[t] + (j * cnt[t]) / K2[t]] * d, sizeof(float) * d);
+                if (j >= cnt[t])  // more lists than rows: jitter the repeats
+                    for (int k = 0; k < d; ++k) c[k] += (float)(1e-3 * (rng.uniform() - 0.5));
+            } else {
+                memcpy(c, &top[(size_t)t * d], sizeof(float) * d);
+            }
+        }
+    std::vector<int32_t> a(n);
+    std::vector<int64_t> lc(nlist);
+    std::vector<double> sum((size_t)nlist * d);
+    for (int it = 0; it < iters; ++it) {
+        gpu_assign_two_level(X, n, d, FA_F32, top.data(), K1, C.data(), nlist, sub_beg.data(), 1,
+                             a.data(), nullptr, nullptr);
+        std::fill(lc.begin(), lc.end(), 0);
+        std::fill(sum.begin(), sum.end(), 0.0);
+        for (int64_t i = 0; i < n; ++i) {
+            const int32_t l = a[i];
+            if (l < 0) continue;
+            lc[l]++;
+            double *sl = &sum[(size_t)l * d];
+            const float *x = X + i * d;
+            for (int k = 0; k < d; ++k) sl[k] += x[k];
+        }
+#pragma omp parallel for schedule(static)
+        for (int32_t l = 0; l < nlist; ++l)
+            if (lc[l] > 0)
+                for (int k = 0; k < d; ++k) C[(size_t)l * d + k] = (float)(sum[(size_t)l * d + k] / lc[l]);
+        // an empty list splits the largest list of its cluster
+        for (int t = 0; t < K1; ++t)
+            for (int32_t l = sub_beg[t]; l < sub_beg[t + 1]; ++l) {
+                if (lc[l] > 0) continue;
+                int32_t big = sub_beg[t];
+                for (int32_t m = sub_beg[t]; m < sub_beg[t + 1]; ++m)
+                    if (lc[m] > lc[big]) big = m;
+                if (lc[big] < 2) continue;
+                for (int k = 0; k < d; ++k) {
+                    const float e = (float)(1e-4 * (rng.uniform() - 0.5)) * (1.f + fabsf(C[(size_t)big * d + k]));
+                    C[(size_t)l * d + k] = C[(size_t)big * d + k] + e;
+                    C[(size_t)big * d + k] -= e;
+                }
+                lc[l] = lc[big] / 2;
+                lc[big] -= lc[l];
+            }
+    }
+    return C;
+}
+
 void host_encode(const void *base, int64_t n, int32_t d, fa_dtype dt, const float *cb, int32_t M,
                  uint8_t *codes) {
     const int dsub = d / M;
@@ -182,21 +292,32 @@ void train_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
     const int32_t nlist = p.nlist, M = p.M, dsub = d / M;
     const bool gpu = p.use_gpu != 0;
     const int iters = p.kmeans_iters;
+    // many lists on the GPU: two-level clustering (hierarchical, §4.1), with
+    // each vector's lists found inside its top-level cluster
+    const bool two_level = gpu && nlist >= TWO_LEVEL_LISTS;
     // training sample: evenly strided rows
     int64_t S = p.train_sample > 0 ? std::min<int64_t>(n, p.train_sample)
-                                   : std::min<int64_t>(n, std::max<int64_t>(65536, 64ll * nlist));
+                                   : std::min<int64_t>(n, std::max<int64_t>(65536, (two_level ? 24ll : 64ll) * nlist));
     std::vector<float> X((size_t)S * d);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < S; ++i) row_f32(base, dt, d, (i * n) / S, &X[(size_t)i * d]);
 
     // coarse quantizer
-    out.centroids = kmeans(X.data(), S, d, nlist, iters, p.seed ^ 0x636f61727365ull, gpu);
+    std::vector<float> top;
+    std::vector<int32_t> sub_beg;
+    if (two_level)
+        out.centroids = kmeans_two_level(X.data(), S, d, nlist, iters, p.seed ^ 0x636f61727365ull, top, sub_beg);
+    else
+        out.centroids = kmeans(X.data(), S, d, nlist, iters, p.seed ^ 0x636f61727365ull, gpu);
 
     // assignment with Eq. 2 replication
-    const int32_t r = p.repl_eps > 0.f ? p.max_lists_per_vec : 1;
+    const int32_t r = p.repl_eps != 0.f ? p.max_lists_per_vec : 1;
     std::vector<int32_t> ids((size_t)n * r);
     std::vector<float> d2((size_t)n * r);
-    if (gpu) {
+    if (two_level) {
+        gpu_assign_two_level(base, n, d, dt, top.data(), (int32_t)top.size() / d, out.centroids.data(),
+                             nlist, sub_beg.data(), r, ids.data(), d2.data(), nullptr);
+    } else if (gpu) {
         gpu_assign_topr(base, n, d, dt, out.centroids.data(), nlist, r, ids.data(), d2.data());
     } else {
         const int64_t chunk = 1 << 16;
@@ -209,11 +330,46 @@ void train_and_encode(const void *base, int64_t n, int32_t d, fa_dtype dt,
                              &d2[(size_t)r0 * r]);
         }
     }
+    // Eq. 2's epsilon: given, or (repl_eps < 0) chosen by bisection so that a
+    // vector joins -repl_eps lists on average, measured on up to 1M vectors
+    // drawn by a multiplicative hash of the row index: a strided sample would
+    // line up with the k-means training rows, which sit closer to the centroids
+    // fitted to them and join fewer lists than the rest
+    double eps = p.repl_eps;
+    if (p.repl_eps < 0.f && r > 1) {
+        const double target = -(double)p.repl_eps;
+        const int64_t ns = std::min<int64_t>(n, 1 << 20);
+        auto mean_lists = [&](double e) {
+            int64_t tot = 0;
+#pragma omp parallel for reduction(+ : tot) schedule(static)
+            for (int64_t s2 = 0; s2 < ns; ++s2) {
+                const int64_t i = ns == n ? s2 : (int64_t)(((uint64_t)s2 * 2654435761ull) % (uint64_t)n);
+                const double lim = (1.0 + e) * sqrt((double)std::max(0.f, d2[(size_t)i * r]));
+                int c = 1;
+                for (int t = 1; t < r; ++t) {
+                    if (ids[(size_t)i * r + t] < 0) break;
+                    if (sqrt((double)std::max(0.f, d2[(size_t)i * r + t])) <= lim) ++c;
+                    else break;
+                }
+                tot += c;
+            }
+            return (double)tot / (double)ns;
+        };
+        double lo = 0.0, hi = 1.0;
+        while (hi < 64.0 && mean_lists(hi) < target) hi *= 2.0;
+        for (int it = 0; it < 40; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            if (mean_lists(mid) < target) lo = mid;
+            else hi = mid;
+        }
+        eps = hi;
+    }
+    out.repl_eps = (float)eps;
     out.primary.resize(n);
     std::vector<std::vector<int64_t>> rep(nlist);
     for (int64_t i = 0; i < n; ++i) {
         out.primary[i] = ids[(size_t)i * r];
-        const double lim = (1.0 + (double)p.repl_eps) * sqrt((double)std::max(0.f, d2[(size_t)i * r]));
+        const double lim = (1.0 + eps) * sqrt((double)std::max(0.f, d2[(size_t)i * r]));
         for (int t = 1; t < r; ++t) {
             const int32_t l = ids[(size_t)i * r + t];
             if (l < 0) break;

@@ -114,8 +114,11 @@ void upload_index(fa_index *ix) {
     D.d = d;
     D.nlist = nlist;
     D.M = M;
+    D.Mp = scan_width(M);
     D.dsub = d / M;
+    const int Mp = D.Mp;
     D.raw_dtype = ix->raw_dtype;
+    D.metric = ix->metric;
     D.raw_location = ix->raw_location;
     int64_t bytes = 0;
 
@@ -136,15 +139,19 @@ void upload_index(fa_index *ix) {
     D.max_list = 0;
     for (int l = 0; l < nlist; ++l) D.max_list = std::max<int64_t>(D.max_list, beg[l + 1] - beg[l]);
 
-    // rotated code rows: byte s of row iv = code of subspace (s + iv mod 32) mod M
+    // rotated code rows of Mp bytes: byte s of row iv = code of subspace
+    // (s + iv mod 32) mod Mp (0 for the padding subspaces M .. Mp - 1)
     const int64_t n_pad = ((n + 31) / 32) * 32 + 32;
-    std::vector<uint8_t> rot((size_t)n_pad * M, 0);
+    std::vector<uint8_t> rot((size_t)n_pad * Mp, 0);
 #pragma omp parallel for schedule(static)
     for (int64_t iv = 0; iv < n; ++iv) {
         const uint8_t *src = ix->codes.data() + (size_t)perm[iv] * M;
-        uint8_t *dst = rot.data() + (size_t)iv * M;
+        uint8_t *dst = rot.data() + (size_t)iv * Mp;
         const int r = (int)(iv & 31);
-        for (int s = 0; s < M; ++s) dst[s] = src[(s + r) % M];
+        for (int s = 0; s < Mp; ++s) {
+            const int m = (s + r) % Mp;
+            dst[s] = m < M ? src[m] : 0;
+        }
     }
 
     // replica tables
@@ -258,7 +265,7 @@ void upload_index(fa_index *ix) {
     }
 
     if (ix->h_raw) {
-        const size_t rb = (size_t)n * d * (ix->raw_dtype == FA_U8 ? 1 : 4);
+        const size_t rb = (size_t)n * d * raw_elem(ix->raw_dtype);
         if (ix->raw_location == FA_RAW_DEVICE) {
             // the HBM copy is in internal order (row v holds the vector with
             // internal id v), so the re-rank reads rows by the ids the scan
@@ -366,7 +373,7 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
     dalloc(w->out_ids, (size_t)cq * ck);
     dalloc(w->out_dist, (size_t)cq * ck);
     dalloc(w->stats, (size_t)cq * 4);
-    dalloc(w->lut_scale, (size_t)cq * 2 * D.M);
+    dalloc(w->lut_scale, (size_t)cq * 2 * D.Mp);
     if (cl > 0) {
         char *p = nullptr;
         dalloc(p, (size_t)cq * cl);
@@ -559,7 +566,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
                "the batched form (FA_BATCHED) reads the FP16 or FP8 table");
     const bool global_lut = sp.lut_prec != FA_LUT_F32 || sp.lut_gemm == FA_GEMM_BF16_TC;
     const int elem = sp.lut_prec == FA_LUT_F32 ? 4 : (sp.lut_prec == FA_LUT_F16 ? 2 : 1);
-    const int lut_bytes = global_lut ? ix->M * 256 * elem : 0;
+    const int lut_bytes = global_lut ? ix->dev.Mp * 256 * elem : 0;
 
     FA_CHECK_CUDA(cudaSetDevice(ix->device));
     WsLease lease(ix, sp.flags & FA_NONBLOCKING);
@@ -694,7 +701,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             bb.cap = w->bq_cap;
             bb.tile_chunks = 1024;
             // sub-batches whose tables (M x 256 entries a query) fit in ~40 MB of L2
-            bb.qsub = std::max<int64_t>(1024, (40ll << 20) / ((int64_t)D.M * 256 * elem));
+            bb.qsub = std::max<int64_t>(1024, (40ll << 20) / ((int64_t)D.Mp * 256 * elem));
             fused = launch_batched(D, sl, bb, st);
             const int64_t nsub = (nq + bb.qsub - 1) / bb.qsub;
             tr.launches += 2 + (int)(4 * nsub) + 2;
@@ -723,7 +730,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
                 sc.npq = npq ? npq + q0 : nullptr;
                 sc.nq = qn;
                 sc.lut = w->lut ? static_cast<char *>(w->lut) + q0 * lut_bytes : nullptr;
-                sc.lut_scale = w->lut_scale + q0 * 2 * D.M;
+                sc.lut_scale = w->lut_scale + q0 * 2 * D.Mp;
                 sc.topkeys = w->topkeys + q0 * ntop;
                 sc.stats = stt ? stt + q0 * 4 : nullptr;
                 sc.order = nullptr;
@@ -858,12 +865,13 @@ static void check_parts(const fa_index_parts *p) {
     FA_REQUIRE(p->n >= 1 && p->n < (1ll << 32) - 64, FA_ERR_ARG, "n must be in 1 .. 2^32-65");
     FA_REQUIRE(p->d >= 1 && p->d <= 1024, FA_ERR_ARG, "d must be in 1..1024");
     FA_REQUIRE(p->nlist >= 1, FA_ERR_ARG, "nlist must be >= 1");
-    FA_REQUIRE(p->M == 8 || p->M == 16 || p->M == 32 || p->M == 48 || p->M == 64, FA_ERR_ARG,
-               "M must be one of 8, 16, 32, 48, 64");
+    FA_REQUIRE(p->M >= 1 && p->M <= 64, FA_ERR_ARG, "M must be in 1..64");
     FA_REQUIRE(p->d % p->M == 0, FA_ERR_ARG, "d must be a multiple of M");
     FA_REQUIRE(p->d / p->M <= 16, FA_ERR_ARG, "d / M must be <= 16");
     FA_REQUIRE(p->centroids && p->codebooks && p->codes && p->primary, FA_ERR_ARG, "null part");
-    FA_REQUIRE(p->raw_dtype == FA_F32 || p->raw_dtype == FA_U8, FA_ERR_ARG, "bad raw dtype");
+    FA_REQUIRE(p->raw_dtype == FA_F32 || p->raw_dtype == FA_U8 || p->raw_dtype == FA_I8, FA_ERR_ARG,
+               "bad raw dtype");
+    FA_REQUIRE(p->metric == FA_METRIC_L2 || p->metric == FA_METRIC_IP, FA_ERR_ARG, "bad metric");
     for (int64_t v = 0; v < p->n; ++v)
         FA_REQUIRE(p->primary[v] >= 0 && p->primary[v] < p->nlist, FA_ERR_ARG, "primary list out of range");
     if (p->rep_off) {
@@ -895,6 +903,7 @@ static void copy_parts(fa_index *ix, const fa_index_parts *p) {
     ix->nlist = p->nlist;
     ix->M = p->M;
     ix->raw_dtype = p->raw_dtype;
+    ix->metric = p->metric;
     ix->raw_location = p->raw ? (p->raw_location ? p->raw_location : FA_RAW_HOST_PINNED) : FA_RAW_NONE;
     ix->centroids.assign(p->centroids, p->centroids + (size_t)p->nlist * p->d);
     ix->codebooks.assign(p->codebooks, p->codebooks + (size_t)p->d * 256);
@@ -907,7 +916,7 @@ static void copy_parts(fa_index *ix, const fa_index_parts *p) {
         ix->rep_off.assign(p->nlist + 1, 0);
     }
     if (p->raw) {
-        const size_t rb = (size_t)p->n * p->d * (p->raw_dtype == FA_U8 ? 1 : 4);
+        const size_t rb = (size_t)p->n * p->d * raw_elem(p->raw_dtype);
         if (ix->raw_location == FA_RAW_HOST_PINNED) {
             FA_CHECK_CUDA(cudaHostAlloc(&ix->h_raw, rb, cudaHostAllocMapped | cudaHostAllocPortable));
             ix->h_raw_pinned = true;
@@ -980,6 +989,7 @@ void fa_build_params_init(fa_build_params *p) {
     p->train_sample = 0;
     p->seed = 20240916ull;
     p->repl_eps = 0.f;
+    p->metric = FA_METRIC_L2;
     p->raw_location = FA_RAW_NONE;
     p->use_gpu = 1;
 }
@@ -1033,7 +1043,7 @@ fa_status fa_build_index(const void *base, int64_t n, int32_t d, fa_dtype dt,
     fa_index *ix = nullptr;
     fa_status s = guarded(nullptr, [&] {
         FA_REQUIRE(base != nullptr, FA_ERR_ARG, "null base");
-        FA_REQUIRE(dt == FA_F32 || dt == FA_U8, FA_ERR_ARG, "bad dtype");
+        FA_REQUIRE(dt == FA_F32 || dt == FA_U8 || dt == FA_I8, FA_ERR_ARG, "bad dtype");
         FA_REQUIRE(n >= 1 && n < (1ll << 32) - 64, FA_ERR_ARG, "n out of range");
         FA_REQUIRE(bp.nlist >= 1 && bp.nlist <= n, FA_ERR_ARG, "nlist must be in 1..n");
         FA_REQUIRE(bp.max_lists_per_vec >= 1 && bp.max_lists_per_vec <= 8, FA_ERR_ARG,
@@ -1049,6 +1059,7 @@ fa_status fa_build_index(const void *base, int64_t n, int32_t d, fa_dtype dt,
         parts.nlist = bp.nlist;
         parts.M = bp.M;
         parts.raw_dtype = dt;
+        parts.metric = bp.metric;
         parts.raw_location = bp.raw_location;
         parts.centroids = bo.centroids.data();
         parts.codebooks = bo.codebooks.data();
@@ -1088,7 +1099,7 @@ fa_status fa_build_index_lists(const void *base, int64_t n, int32_t d, fa_dtype 
     fa_index *ix = nullptr;
     fa_status s = guarded(nullptr, [&] {
         FA_REQUIRE(base && centroids && primary, FA_ERR_ARG, "null input");
-        FA_REQUIRE(dt == FA_F32 || dt == FA_U8, FA_ERR_ARG, "bad dtype");
+        FA_REQUIRE(dt == FA_F32 || dt == FA_U8 || dt == FA_I8, FA_ERR_ARG, "bad dtype");
         FA_REQUIRE(n >= 1 && n < (1ll << 32) - 64 && nlist >= 1, FA_ERR_ARG, "bad shape");
         FA_REQUIRE(bp.M >= 1 && d % bp.M == 0, FA_ERR_ARG, "d must be a multiple of M");
         if (bp.use_gpu) current_device();
@@ -1103,6 +1114,7 @@ fa_status fa_build_index_lists(const void *base, int64_t n, int32_t d, fa_dtype 
         parts.nlist = nlist;
         parts.M = bp.M;
         parts.raw_dtype = dt;
+        parts.metric = bp.metric;
         parts.raw_location = bp.raw_location;
         parts.centroids = bo.centroids.data();
         parts.codebooks = bo.codebooks.data();
@@ -1136,6 +1148,7 @@ fa_status fa_index_get_parts(const fa_index *ix, fa_index_parts *out) {
     out->nlist = ix->nlist;
     out->M = ix->M;
     out->raw_dtype = ix->raw_dtype;
+    out->metric = ix->metric;
     out->raw_location = ix->raw_location;
     out->centroids = ix->centroids.data();
     out->codebooks = ix->codebooks.data();
@@ -1180,7 +1193,8 @@ fa_status fa_save_index(const fa_index *ix, const char *path) {
     }
     bool ok = true;
     auto W = [&](const void *p, size_t b) { ok = ok && (b == 0 || fwrite(p, 1, b, f) == b); };
-    const int64_t hdr[8] = {1, ix->n, ix->d, ix->nlist, ix->M, ix->raw_dtype,
+    const int64_t hdr[8] = {1, ix->n, ix->d, ix->nlist, ix->M,
+                            (int64_t)ix->raw_dtype | ((int64_t)ix->metric << 8),
                             ix->h_raw ? 1 : 0, (int64_t)ix->rep_ids.size()};
     W(MAGIC, 8);
     W(hdr, sizeof hdr);
@@ -1190,7 +1204,7 @@ fa_status fa_save_index(const fa_index *ix, const char *path) {
     W(ix->primary.data(), 4 * ix->primary.size());
     W(ix->rep_off.data(), 8 * ix->rep_off.size());
     W(ix->rep_ids.data(), 8 * ix->rep_ids.size());
-    if (ix->h_raw) W(ix->h_raw, (size_t)ix->n * ix->d * (ix->raw_dtype == FA_U8 ? 1 : 4));
+    if (ix->h_raw) W(ix->h_raw, (size_t)ix->n * ix->d * raw_elem(ix->raw_dtype));
     ok = (fclose(f) == 0) && ok;
     if (!ok) {
         set_error("write to %s failed", path);
@@ -1224,7 +1238,7 @@ fa_status fa_load_index(const char *path, int32_t raw_location, fa_index **out) 
     }
     const int64_t n = hdr[1], nr = hdr[7];
     const int32_t d = (int32_t)hdr[2], nlist = (int32_t)hdr[3], M = (int32_t)hdr[4];
-    const int32_t rdt = (int32_t)hdr[5];
+    const int32_t rdt = (int32_t)(hdr[5] & 0xff);  // the metric sits in the next byte
     std::vector<float> cent, cb;
     std::vector<uint8_t> codes, raw;
     std::vector<int32_t> prim;
@@ -1236,7 +1250,7 @@ fa_status fa_load_index(const char *path, int32_t raw_location, fa_index **out) 
         prim.resize(n);
         roff.resize(nlist + 1);
         rids.resize(nr);
-        if (hdr[6]) raw.resize((size_t)n * d * (rdt == FA_U8 ? 1 : 4));
+        if (hdr[6]) raw.resize((size_t)n * d * raw_elem(rdt));
     } catch (...) {
         fclose(f);
         set_error("host allocation failed");
@@ -1260,6 +1274,7 @@ fa_status fa_load_index(const char *path, int32_t raw_location, fa_index **out) 
     p.nlist = nlist;
     p.M = M;
     p.raw_dtype = rdt;
+    p.metric = (int32_t)((hdr[5] >> 8) & 0xff);
     p.raw_location = hdr[6] ? (raw_location ? raw_location : FA_RAW_HOST_PINNED) : FA_RAW_NONE;
     p.centroids = cent.data();
     p.codebooks = cb.data();
@@ -1502,8 +1517,8 @@ fa_status fa_debug_lut(fa_index *ix, const float *query, const fa_search_params 
         WsLease lease(ix, false);
         Workspace *w = lease.w;
         const int elem = sp.lut_prec == FA_LUT_F32 ? 4 : (sp.lut_prec == FA_LUT_F16 ? 2 : 1);
-        const int M = ix->M;
-        ws_ensure(ix, w, 1, 1, 1, 1, M * 256 * elem);
+        const int M = ix->M;  // the table holds Mp rows; the first M are the subspaces
+        ws_ensure(ix, w, 1, 1, 1, 1, ix->dev.Mp * 256 * elem);
         cudaStream_t st = w->stream;
         FA_CHECK_CUDA(cudaMemcpyAsync(w->q, query, sizeof(float) * ix->d, cudaMemcpyHostToDevice, st));
         FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));

@@ -46,6 +46,14 @@ enum DevErr : uint32_t {
     DEV_ERR_BOUNDS = 4u,
 };
 
+// Bytes of one element of a raw vector.
+inline int raw_elem(int dt) { return dt == FA_F32 ? 4 : 1; }
+
+// Scan width of M subspaces: the smallest of 8, 16, 32, 48, 64 that holds M.
+inline int scan_width(int M) {
+    return M <= 8 ? 8 : (M <= 16 ? 16 : (M <= 32 ? 32 : (M <= 48 ? 48 : 64)));
+}
+
 // LUT row stride (floats) in shared memory for M subspaces: every position
 // p = r + s (r = v mod 32, s < M) must exist, so the row holds M + 31 entries.
 inline int lut_row_words(int M) {
@@ -59,6 +67,10 @@ inline int lut_row_words(int M) {
 struct DeviceIndex {
     int64_t n = 0;
     int32_t d = 0, nlist = 0, M = 0, dsub = 0;
+    // scan width: M rounded up to 8, 16, 32, 48 or 64 (the scan kernels'
+    // widths); the extra subspaces have code 0 and all-zero table rows
+    int32_t Mp = 0;
+    int32_t metric = FA_METRIC_L2;
     int32_t raw_dtype = FA_U8, raw_location = FA_RAW_NONE;
     int64_t n_rep = 0;        // replica entries
     int64_t n_mem = 0;        // membership table entries
@@ -179,6 +191,7 @@ struct fa_index {
     int64_t n = 0;
     int32_t d = 0, nlist = 0, M = 0;
     int32_t raw_dtype = FA_U8, raw_location = FA_RAW_NONE;
+    int32_t metric = FA_METRIC_L2;
     std::vector<float> centroids, codebooks;
     std::vector<uint8_t> codes;
     std::vector<int32_t> primary;
@@ -202,6 +215,7 @@ namespace fa {
 // host-side building blocks
 // -------------------------------------------------------------------------
 struct BuildOut {
+    float repl_eps = 0.f;  // Eq. 2's epsilon as applied
     std::vector<float> centroids, codebooks;
     std::vector<uint8_t> codes;
     std::vector<int32_t> primary;
@@ -226,6 +240,13 @@ void gpu_assign_topr(const void *rows, int64_t n, int32_t d, fa_dtype dt, const 
                      int32_t nlist, int32_t r, int32_t *out_ids, float *out_d2);
 void gpu_encode(const void *rows, int64_t n, int32_t d, fa_dtype dt, const float *codebooks,
                 int32_t M, uint8_t *out_codes);
+// Two-level assignment: each row's three nearest of the ntop top-level
+// centroids, then its r <= 8 nearest lists among those clusters' lists
+// (cluster t holds lists[sub_beg[t] .. sub_beg[t + 1])). out_top (optional)
+// receives the nearest cluster.
+void gpu_assign_two_level(const void *rows, int64_t n, int32_t d, fa_dtype dt, const float *top,
+                          int32_t ntop, const float *lists, int32_t nlist, const int32_t *sub_beg,
+                          int32_t r, int32_t *out_ids, float *out_d2, int32_t *out_top);
 
 // -------------------------------------------------------------------------
 // kernel launchers (kernels/*.cu)

@@ -270,7 +270,7 @@ fa_status fa_server_create(fa_index *ix, const fa_server_params *p, const fa_sea
         FA_CHECK_CUDA(cudaSetDevice(ix->device));
         // admission by memory: the slot count is cut to what the budget holds
         const int64_t per_req = (int64_t)sv->d * 4 + 8 + (int64_t)sv->p.kmax * 12 +
-                                (int64_t)ix->M * 256 * 4 + (int64_t)std::max(sv->p.kmax, sv->sp.rerank_n) * 8;
+                                (int64_t)ix->dev.Mp * 256 * 4 + (int64_t)std::max(sv->p.kmax, sv->sp.rerank_n) * 8;
         int nslots = sv->p.slots;
         if (sv->p.mem_budget_bytes > 0) {
             const int64_t per_slot = per_req * sv->p.max_batch;

@@ -62,6 +62,7 @@ struct DistArgs {
     float *D;                    // [rows][ldd], ldd a multiple of 4
     int64_t ldd;
     uint32_t *err;
+    int32_t ip;                  // the negated inner product -q.c instead of the squared L2
 };
 
 __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a) {
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(PT + 32, 1) k_coarse_dist_tc(const DistArgs a)
                 const bool lv = l < a.nlist;
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
-                    const float dd = __shfl_sync(FULL, qnl, e) - 2.f * v[e] + cn;
+                    const float dd = a.ip ? -v[e] : __shfl_sync(FULL, qnl, e) - 2.f * v[e] + cn;
                     if (lv && e < nrow) *p = dd;
                     p += a.ldd;
                 }
@@ -374,6 +375,7 @@ void launch_coarse_tc(const DeviceIndex &ix, const float *q, int64_t rows, int32
     a.Kp = ix.tc_kp;
     a.tiles = reinterpret_cast<const __nv_bfloat16 *>(ix.centroids_bf16);
     a.cnorm = ix.cnorm;
+    a.ip = ix.metric == FA_METRIC_IP ? 1 : 0;
     a.nlist = ix.nlist;
     a.nt = ix.tc_ntiles;
     a.total = (rows + PQ - 1) / PQ * (int64_t)a.nt;

@@ -25,7 +25,7 @@ constexpr float FP8_MAX = 448.f;
 
 // Stores a FP32 table held in shared memory (t[m*256 + c]) in the requested
 // precision with a per-subspace scale and offset.
-__device__ void store_lut(const float *t, int M, int prec, void *lut, float *scale, int64_t qi,
+__device__ void store_lut(const float *t, int M, int Mr, int prec, void *lut, float *scale, int64_t qi,
                           float *offs, float *scl, int uniform) {
     const int64_t base = qi * (int64_t)M * 256;
     float *sc = scale + qi * 2 * M;
@@ -53,6 +53,7 @@ __device__ void store_lut(const float *t, int M, int prec, void *lut, float *sca
         }
         float s = (hi - lo) / fmax;
         if (!(s > 0.f)) s = 1.f;
+        if (m >= Mr) s = lo = 0.f;  // padding subspace: every entry 0
         if (lane == 0) {
             offs[m] = lo;
             scl[m] = s;
@@ -72,7 +73,7 @@ __device__ void store_lut(const float *t, int M, int prec, void *lut, float *sca
     __syncthreads();
     for (int i = threadIdx.x; i < M * 256; i += blockDim.x) {
         const int m = i >> 8;
-        const float r = fminf((t[i] - offs[m]) / scl[m], fmax);
+        const float r = scl[m] > 0.f ? fminf((t[i] - offs[m]) / scl[m], fmax) : 0.f;
         if (prec == FA_LUT_F16) {
             reinterpret_cast<__half *>(lut)[base + i] = __float2half_rn(r);
         } else {
@@ -84,29 +85,35 @@ __device__ void store_lut(const float *t, int M, int prec, void *lut, float *sca
 
 // FP32 direct differences, one CTA per query.
 __global__ void __launch_bounds__(256) k_lut_simt(const float *__restrict__ q, int64_t nq, int32_t d,
-                                                  const float *__restrict__ cb, int32_t M, int prec,
-                                                  void *lut, float *scale, int uniform) {
+                                                  const float *__restrict__ cb, int32_t M, int32_t Mr,
+                                                  int prec, void *lut, float *scale, int uniform, int ip) {
     extern __shared__ float sm[];
     float *t = sm;                 // [M][256]
     float *qv = t + M * 256;       // [d]
     float *offs = qv + d;          // [M]
     float *scl = offs + M;         // [M]
-    const int dsub = d / M;
+    const int dsub = d / Mr;
     for (int64_t qi = blockIdx.x; qi < nq; qi += gridDim.x) {
         for (int j = threadIdx.x; j < d; j += blockDim.x) qv[j] = q[qi * d + j];
         __syncthreads();
         for (int i = threadIdx.x; i < M * 256; i += blockDim.x) {
             const int m = i >> 8, c = i & 255;
-            const float *w = cb + ((int64_t)m * 256 + c) * dsub;
             float s = 0.f;
-            for (int j = 0; j < dsub; ++j) {
-                const float df = qv[m * dsub + j] - w[j];
-                s = fmaf(df, df, s);
+            if (m < Mr) {  // padding subspaces stay 0
+                const float *w = cb + ((int64_t)m * 256 + c) * dsub;
+                for (int j = 0; j < dsub; ++j) {
+                    if (ip) {  // inner product: -<q_m, C_m[c]>
+                        s = fmaf(-qv[m * dsub + j], w[j], s);
+                    } else {
+                        const float df = qv[m * dsub + j] - w[j];
+                        s = fmaf(df, df, s);
+                    }
+                }
             }
             t[i] = s;
         }
         __syncthreads();
-        store_lut(t, M, prec, lut, scale, qi, offs, scl, uniform);
+        store_lut(t, M, Mr, prec, lut, scale, qi, offs, scl, uniform);
         __syncthreads();
     }
 }
@@ -121,10 +128,11 @@ void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int pr
         launch_lut_tc(ix, q, nq, prec, lut, lut_scale, err, st, uniform);
         return;
     }
-    const int smem = (ix.M * 256 + ix.d + 2 * ix.M) * 4;
+    const int smem = (ix.Mp * 256 + ix.d + 2 * ix.Mp) * 4;
     FA_CHECK_CUDA(cudaFuncSetAttribute(k_lut_simt, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     const int grid = (int)std::min<int64_t>(nq, (int64_t)cur_num_sms() * 4);
-    k_lut_simt<<<grid, 256, smem, st>>>(q, nq, ix.d, ix.codebooks, ix.M, prec, lut, lut_scale, uniform);
+    k_lut_simt<<<grid, 256, smem, st>>>(q, nq, ix.d, ix.codebooks, ix.Mp, ix.M, prec, lut, lut_scale,
+                                        uniform, ix.metric == FA_METRIC_IP ? 1 : 0);
     FA_CHECK_CUDA(cudaGetLastError());
 }
 

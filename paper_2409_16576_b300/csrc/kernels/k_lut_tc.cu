@@ -38,6 +38,7 @@ struct LutTcArgs {
     const float *q;
     int64_t nq;
     int32_t d, Kp, M, dsub;
+    int32_t Mp;                   // table rows per query (M rounded up to the scan width)
     const __nv_bfloat16 *btiles;  // [M][hi, lo][LN x 16] core-matrix layout
     const float *cbnorm;          // [M][256] |C_m[c]|^2
     int32_t prec;
@@ -46,6 +47,7 @@ struct LutTcArgs {
     uint32_t *err;
     int32_t uniform;              // one scale per query: s_q = 2 (|q|^2 + max |C_m[c]|^2) / format max
     float cmax2;                  // max over m, c of |C_m[c]|^2
+    int32_t ip;                   // entries -q_m.C_m[c] (inner product) instead of the squared L2
 };
 
 __host__ __device__ inline int lut_elem(int prec) {
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
                 tc::tmem_ld32(lane_addr + c0, v);
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float e = qn - 2.f * v[j] + __ldg(cn + c0 + j);
+                    const float e = a.ip ? -v[j] : qn - 2.f * v[j] + __ldg(cn + c0 + j);
                     lo = fminf(lo, e);
                     hi = fmaxf(hi, e);
                 }
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
         float s = a.uniform ? su : (hi - lo) / fmax;
         if (!(s > 0.f)) s = 1.f;
         const float inv = 1.f / s;
-        const int64_t base = (row * a.M + m) * 256;
+        const int64_t base = (row * a.Mp + m) * 256;
         unsigned char *srw = stage + (size_t)tid * srow;
 #pragma unroll 1
         for (int c0 = 0; c0 < LN; c0 += 32) {
@@ -189,17 +191,19 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
                 float4 *o = reinterpret_cast<float4 *>(reinterpret_cast<float *>(a.lut) + base + c0);
 #pragma unroll
                 for (int j = 0; j < 32; j += 4)
-                    o[j / 4] = make_float4(qn - 2.f * v[j] + __ldg(cn + c0 + j),
-                                           qn - 2.f * v[j + 1] + __ldg(cn + c0 + j + 1),
-                                           qn - 2.f * v[j + 2] + __ldg(cn + c0 + j + 2),
-                                           qn - 2.f * v[j + 3] + __ldg(cn + c0 + j + 3));
+                    o[j / 4] = a.ip ? make_float4(-v[j], -v[j + 1], -v[j + 2], -v[j + 3])
+                                    : make_float4(qn - 2.f * v[j] + __ldg(cn + c0 + j),
+                                                  qn - 2.f * v[j + 1] + __ldg(cn + c0 + j + 1),
+                                                  qn - 2.f * v[j + 2] + __ldg(cn + c0 + j + 2),
+                                                  qn - 2.f * v[j + 3] + __ldg(cn + c0 + j + 3));
             } else if (a.prec == FA_LUT_F16) {
                 uint32_t w[16];
 #pragma unroll
                 for (int j = 0; j < 32; j += 2) {
-                    const float e0 = fminf((qn - 2.f * v[j] + __ldg(cn + c0 + j) - lo) * inv, fmax);
-                    const float e1 =
-                        fminf((qn - 2.f * v[j + 1] + __ldg(cn + c0 + j + 1) - lo) * inv, fmax);
+                    const float x0 = a.ip ? -v[j] : qn - 2.f * v[j] + __ldg(cn + c0 + j);
+                    const float x1 = a.ip ? -v[j + 1] : qn - 2.f * v[j + 1] + __ldg(cn + c0 + j + 1);
+                    const float e0 = fminf((x0 - lo) * inv, fmax);
+                    const float e1 = fminf((x1 - lo) * inv, fmax);
                     const __half2 h = __floats2half2_rn(e0, e1);
                     w[j / 2] = *reinterpret_cast<const uint32_t *>(&h);
                 }
@@ -214,8 +218,8 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
                     uint32_t pk = 0;
 #pragma unroll
                     for (int t = 0; t < 4; ++t) {
-                        const float e =
-                            fminf((qn - 2.f * v[j + t] + __ldg(cn + c0 + j + t) - lo) * inv, fmax);
+                        const float xe = a.ip ? -v[j + t] : qn - 2.f * v[j + t] + __ldg(cn + c0 + j + t);
+                        const float e = fminf((xe - lo) * inv, fmax);
                         const __nv_fp8_e4m3 f(e);
                         pk |= (uint32_t)f.__x << (8 * t);
                     }
@@ -227,8 +231,8 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
             }
         }
         if (row_ok) {
-            a.scale[row * 2 * a.M + 2 * m] = staged ? s : 1.f;
-            a.scale[row * 2 * a.M + 2 * m + 1] = staged ? lo : 0.f;
+            a.scale[row * 2 * a.Mp + 2 * m] = staged ? s : 1.f;
+            a.scale[row * 2 * a.Mp + 2 * m + 1] = staged ? lo : 0.f;
         }
         tc::fence_before();
         __syncthreads();  // the staged tile is complete and the accumulator free
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(LQ, 1) k_lut_tc(const LutTcArgs a) {
             // contiguous bytes in HBM
             for (int r = warp; r < LQ; r += LQ / 32) {
                 if (r0 + r >= a.nq) break;
-                unsigned char *dst = reinterpret_cast<unsigned char *>(a.lut) + ((r0 + r) * a.M + m) * 256 * elem;
+                unsigned char *dst = reinterpret_cast<unsigned char *>(a.lut) + ((r0 + r) * a.Mp + m) * 256 * elem;
                 const unsigned char *src = stage + (size_t)r * srow;
                 if (elem == 2)
                     reinterpret_cast<uint4 *>(dst)[lane] = reinterpret_cast<const uint4 *>(src)[lane];
@@ -300,6 +304,7 @@ void launch_lut_tc(const DeviceIndex &ix, const float *q, int64_t nq, int prec, 
     a.d = ix.d;
     a.Kp = ix.tc_kp;
     a.M = ix.M;
+    a.Mp = ix.Mp;
     a.dsub = ix.dsub;
     a.btiles = reinterpret_cast<const __nv_bfloat16 *>(ix.codebooks_bf16);
     a.cbnorm = ix.cbnorm;
@@ -309,6 +314,7 @@ void launch_lut_tc(const DeviceIndex &ix, const float *q, int64_t nq, int prec, 
     a.err = err;
     a.uniform = uniform;
     a.cmax2 = ix.cb_max_norm2;
+    a.ip = ix.metric == FA_METRIC_IP ? 1 : 0;
     // widest K-range of one CTA's subspaces (16-wide blocks), two tile buffers,
     // the staged rows; at least 80 KB so that at most two CTAs (2 x 256 TMEM
     // columns) share an SM
@@ -323,6 +329,13 @@ void launch_lut_tc(const DeviceIndex &ix, const float *q, int64_t nq, int prec, 
     const dim3 grid((unsigned)((nq + LQ - 1) / LQ), (unsigned)((ix.M + LSUB - 1) / LSUB));
     k_lut_tc<<<grid, LQ, smem, st>>>(a);
     FA_CHECK_CUDA(cudaGetLastError());
+    if (ix.Mp > ix.M) {  // padding subspaces: zero entries, scale and offset 0
+        const size_t row = (size_t)256 * lut_elem(prec);
+        FA_CHECK_CUDA(cudaMemset2DAsync(static_cast<char *>(lut) + (size_t)ix.M * row, (size_t)ix.Mp * row,
+                                        0, (size_t)(ix.Mp - ix.M) * row, (size_t)nq, st));
+        FA_CHECK_CUDA(cudaMemset2DAsync(lut_scale + 2 * ix.M, sizeof(float) * 2 * ix.Mp, 0,
+                                        sizeof(float) * 2 * (ix.Mp - ix.M), (size_t)nq, st));
+    }
 }
 
 }  // namespace fa

@@ -129,7 +129,7 @@ __device__ __forceinline__ void rerank_one(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t qi,
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
     const int64_t *__restrict__ perm, const T *__restrict__ raw, int raw_internal,
-    int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, float *qs) {
+    int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, float *qs, int ip) {
     const int lane = threadIdx.x & 31;
     __syncwarp();  // the previous query of this warp is done with qs
     for (int j = lane; j < d; j += 32) qs[j] = q[qi * d + j];
@@ -138,7 +138,7 @@ __device__ __forceinline__ void rerank_one(
     // integer form (its bytes packed after the floats in qs)
     bool qint = false;
     uint32_t *qp = reinterpret_cast<uint32_t *>(qs + d);
-    if (sizeof(T) == 1 && d <= 258 && d % 16 == 0) qint = pack_u8_query(qs, d, qp);
+    if (!ip && std::is_same<T, uint8_t>::value && d <= 258 && d % 16 == 0) qint = pack_u8_query(qs, d, qp);
     int kk = kq ? kq[qi] : k;
     kk = kk < 1 ? 1 : (kk > k ? k : kk);
     const uint64_t *tk = topkeys + qi * ntop;
@@ -175,7 +175,7 @@ __device__ __forceinline__ void rerank_one(
                 nend = end + batch < valid ? end + batch : valid;
             }
             const int64_t uid_next = task_id(ns + lane, nend);
-            const float dist = exact_rows_any<T>(raw, d, qs, qp, qint, uid);
+            const float dist = exact_rows_any<T>(raw, d, qs, qp, qint, uid, ip != 0);
             // only keys below Q's kk-th can change Q's first kk entries (the
             // output and Eq. 3); a step with none leaves them as they are.
             // Keys carry caller ids (ties break by them, as in the oracle):
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 3) k_rerank(
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
     const int64_t *__restrict__ perm, const T *__restrict__ raw, int raw_internal,
     int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, uint32_t *ctr,
-    const int32_t *qlist, const uint32_t *qcount) {
+    const int32_t *qlist, const uint32_t *qcount, int ip) {
     extern __shared__ float qsm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *qs = qsm + warp * (d + d / 4 + 1);  // the query, then its packed bytes
@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(LEAN ? 32 : 256, LEAN ? 32 : 3) k_rerank(
         }
         if (qi >= nq) break;
         rerank_one<R, T>(q, d, topkeys, qi, ntop, k, kq, batch, beta, eps, perm, raw, raw_internal,
-                         out_ids, out_dist, stats, qs);
+                         out_ids, out_dist, stats, qs, ip);
     }
 }
 
@@ -278,6 +278,7 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
     if (ctr) FA_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 4, st));
     const int smem = warps * (ix.d + ix.d / 4 + 1) * 4;
     const T *raw = reinterpret_cast<const T *>(ix.raw);
+    const int ip = ix.metric == FA_METRIC_IP ? 1 : 0;
 #define FA_RR(RR)                                                                                 \
     do {                                                                                          \
         if (ctr) {                                                                                \
@@ -287,7 +288,7 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
                                                                   batch, beta, eps, ix.perm, raw,   \
                                                                   ix.raw_internal,                  \
                                                                   out_ids, out_dist, stats, ctr,    \
-                                                                  qlist, qcount);                   \
+                                                                  qlist, qcount, ip);               \
         } else {                                                                                  \
             FA_CHECK_CUDA(cudaFuncSetAttribute(k_rerank<RR, T, false>,                            \
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem)); \
@@ -295,7 +296,7 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
                                                                    batch, beta, eps, ix.perm, raw,  \
                                                                    ix.raw_internal,                 \
                                                                    out_ids, out_dist, stats, ctr,   \
-                                                                   nullptr, nullptr);               \
+                                                                   nullptr, nullptr, ip);           \
         }                                                                                         \
     } while (0)
     if (k <= 32)
@@ -326,6 +327,10 @@ void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkey
         FA_REQUIRE(ix.d % 4 == 0, FA_ERR_ARG, "uint8 re-rank needs d % 4 == 0");
         launch_rerank_t<uint8_t>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
                                  out_ids, out_dist, stats, warps, ctr, qlist, qcount, st);
+    } else if (ix.raw_dtype == FA_I8) {
+        FA_REQUIRE(ix.d % 4 == 0, FA_ERR_ARG, "int8 re-rank needs d % 4 == 0");
+        launch_rerank_t<int8_t>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
+                                out_ids, out_dist, stats, warps, ctr, qlist, qcount, st);
     } else {
         launch_rerank_t<float>(ix, q, topkeys, nq, ntop, k, kq, batch, beta, eps,
                                out_ids, out_dist, stats, warps, ctr, qlist, qcount, st);

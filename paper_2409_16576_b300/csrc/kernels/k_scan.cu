@@ -53,7 +53,9 @@ struct ScanArgs {
     const uint8_t *rep_t;
     const uint32_t *mem;
     const float *codebooks;
-    int32_t d, M, dsub, nlist;
+    int32_t d, M, dsub, nlist;  // M: the scan width (table rows per query)
+    int32_t ip;                 // the negated inner product instead of the squared L2
+    int32_t Mr;                 // subspaces of the index (M rounded up is the scan width)
     int32_t has_rep;
     // batch
     const float *q;
@@ -178,13 +180,20 @@ __device__ __forceinline__ void build_lut(const ScanArgs &a, int64_t qi, float *
     }
     for (int idx = threadIdx.x; idx < 256 * M; idx += blockDim.x) {
         const int c = idx / M, m = idx - c * M;  // M is a compile-time constant
-        // FP32 form: the table built here from the codebooks (Eq. 1)
-        const float *cw = a.codebooks + ((int64_t)m * 256 + c) * dsub;
-        const float *qm = qv + m * dsub;
+        // FP32 form: the table built here from the codebooks (Eq. 1); the
+        // padding subspaces (m >= Mr) add 0
         float val = 0.f;
-        for (int j = 0; j < dsub; ++j) {
-            const float t = qm[j] - cw[j];
-            val = fmaf(t, t, val);
+        if (m < a.Mr) {
+            const float *cw = a.codebooks + ((int64_t)m * 256 + c) * dsub;
+            const float *qm = qv + m * dsub;
+            for (int j = 0; j < dsub; ++j) {
+                if (a.ip) {
+                    val = fmaf(-qm[j], cw[j], val);
+                } else {
+                    const float t = qm[j] - cw[j];
+                    val = fmaf(t, t, val);
+                }
+            }
         }
 #pragma unroll
         for (int p = 0; p < P; p += M)
@@ -1065,7 +1074,7 @@ __device__ __forceinline__ void rerank_fused(const ScanArgs &a, const ScanPtrs &
     uint32_t *qp = reinterpret_cast<uint32_t *>(wq + SEL_WARPS * 32);  // [d / 4]
     if (warp == 0) {
         bool qint = false;
-        if (a.d <= 258 && a.d % 16 == 0) qint = pack_u8_query(S.qv, a.d, qp);
+        if (!a.ip && a.d <= 258 && a.d % 16 == 0) qint = pack_u8_query(S.qv, a.d, qp);
         if (lane == 0) s_small[1] = qint ? 1u : 0u;
     }
     __syncthreads();
@@ -1079,7 +1088,8 @@ __device__ __forceinline__ void rerank_fused(const ScanArgs &a, const ScanPtrs &
         const int64_t v = (i < c && key <= kth) ? (int64_t)(uint32_t)(key & 0xffffffffu) : (int64_t)-1;
         const uint8_t *raw = static_cast<const uint8_t *>(a.raw);
         const float dist = qint ? exact_rows_u8int<uint4>(raw, a.d, qp, v)
-                                : exact_rows<uint8_t, uint4>(raw, a.d, S.qv, v);
+                                : (a.ip ? exact_rows<uint8_t, uint4, true>(raw, a.d, S.qv, v)
+                                        : exact_rows<uint8_t, uint4>(raw, a.d, S.qv, v));
         const uint64_t kthq = shfl64(Q[0], kk - 1);
         const bool maybe = v >= 0 && f2o(dist) <= (uint32_t)(kthq >> 32);
         uint64_t nk[1] = {maybe ? make_key(dist, (uint32_t)a.perm[v]) : KEY_INF};
@@ -1488,7 +1498,7 @@ __device__ __forceinline__ void bq_decode(const BatchArgs &b, uint32_t u, uint32
 
 // The E queries' ADC sums of one rotated code row, E entries per table word:
 // E = 2, FP16 entries added in FP32; E = 4, FP8 (e4m3) entries converted in
-// pairs to half2 and added as half2 over 8 subspaces (at most 8 x 448, well
+// pairs to half2 and added as half2 over 16 subspaces (at most 16 x 448, well
 // inside FP16), then in FP32.
 template <int M, int W, int E>
 __device__ __forceinline__ void adc_multi(const uint32_t (&w)[M / 4], uint32_t v, const uint32_t *tbl,
@@ -1538,7 +1548,7 @@ __device__ __forceinline__ void adc_multi(const uint32_t (&w)[M / 4], uint32_t v
                 "add.rn.f16x2 %0, %0, p;\n\tadd.rn.f16x2 %1, %1, r;}"
                 : "+r"(h01), "+r"(h23)
                 : "r"(x));
-            if ((t & 7) == 7 || t == M - 1) {
+            if ((t & 15) == 15 || t == M - 1) {
                 float x0, x1, x2, x3;
                 asm("{.reg .b16 a, b, c, d;\n\tmov.b32 {a, b}, %4;\n\tmov.b32 {c, d}, %5;\n\t"
                     "cvt.f32.f16 %0, a;\n\tcvt.f32.f16 %1, b;\n\tcvt.f32.f16 %2, c;\n\tcvt.f32.f16 %3, d;}"
@@ -1913,7 +1923,9 @@ static ScanArgs scan_args(const DeviceIndex &ix, const ScanLaunch &l) {
     a.mem = ix.mem;
     a.codebooks = ix.codebooks;
     a.d = ix.d;
-    a.M = ix.M;
+    a.M = ix.Mp;
+    a.Mr = ix.M;
+    a.ip = ix.metric == FA_METRIC_IP ? 1 : 0;
     a.dsub = ix.dsub;
     a.nlist = ix.nlist;
     a.has_rep = ix.n_rep > 0 ? 1 : 0;
@@ -1962,7 +1974,7 @@ bool launch_scan(const DeviceIndex &ix, const ScanLaunch &l, cudaStream_t st) {
         FA_REQUIRE(l.ntop <= 256, FA_ERR_ARG, "the tiled form supports top-n <= 256");
         FA_REQUIRE(l.persistent, FA_ERR_ARG, "the tiled form runs persistent CTAs");
     }
-    switch (ix.M) {
+    switch (ix.Mp) {
         case 8: return launch_scan_m<8, 64>(a, l, st);
         case 16: return launch_scan_m<16, 64>(a, l, st);
         case 32: return launch_scan_m<32, 64>(a, l, st);
@@ -2033,7 +2045,7 @@ static bool launch_batched_m(const DeviceIndex &ix, const ScanLaunch &l, const B
     b.rep_t = ix.rep_t;
     b.mem = ix.mem;
     b.lorder = ix.lorder;
-    b.M = ix.M;
+    b.M = ix.Mp;
     b.nlist = ix.nlist;
     b.has_rep = a.has_rep;
     b.nlw = nlw;
@@ -2108,7 +2120,7 @@ bool launch_batched(const DeviceIndex &ix, const ScanLaunch &l, const BatchBufs 
     FA_REQUIRE((l.lut_prec == FA_LUT_F16 || l.lut_prec == FA_LUT_FP8) && l.lut, FA_ERR_ARG,
                "the batched form reads the FP16 or FP8 table");
     FA_REQUIRE(l.redo && l.tile_ctr, FA_ERR_ARG, "the batched form needs its redo list");
-    switch (ix.M) {
+    switch (ix.Mp) {
         case 8: return launch_batched_m<8, 64>(ix, l, bb, st);
         case 16: return launch_batched_m<16, 64>(ix, l, bb, st);
         case 32: return launch_batched_m<32, 64>(ix, l, bb, st);

@@ -3,6 +3,8 @@
 // that fuses its exhaustive form.
 #pragma once
 
+#include <type_traits>
+
 #include "../fa_internal.h"
 #include "warp_topk.cuh"
 
@@ -15,7 +17,8 @@ namespace fa {
 // covers four rows with a full 128-byte request each (d = 128 uint8). The
 // loads of all 32 rows are issued before any is summed; the eight partial
 // sums of a row are added with three shuffles.
-template <typename T, typename C>
+// IP: the negated inner product -<q, x> instead of the squared L2.
+template <typename T, typename C, bool IP = false>
 __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d,
                                             const float *qs, int64_t my_id) {
     constexpr int EPC = (int)(sizeof(C) / sizeof(T));  // elements per piece
@@ -50,12 +53,22 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
 #pragma unroll
                 for (int e = 0; e < EPW; ++e) {
                     // a byte b placed in the low mantissa bits of 2^23 reads
-                    // as 2^23 + b: one exact subtraction gives b as a float
-                    const float xv = sizeof(T) == 1
-                                         ? __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7640u + e)) - 8388608.0f
-                                         : __uint_as_float(w);
-                    const float t = qv[e] - xv;
-                    acc = fmaf(t, t, acc);
+                    // as 2^23 + b: one exact subtraction gives b as a float;
+                    // an int8 byte flipped in its top bit is b + 128
+                    float xv;
+                    if constexpr (std::is_same<T, int8_t>::value)
+                        xv = __uint_as_float(__byte_perm(w ^ 0x80808080u, 0x4b000000u, 0x7640u + e)) -
+                             8388736.0f;
+                    else if constexpr (sizeof(T) == 1)
+                        xv = __uint_as_float(__byte_perm(w, 0x4b000000u, 0x7640u + e)) - 8388608.0f;
+                    else
+                        xv = __uint_as_float(w);
+                    if (IP) {
+                        acc = fmaf(qv[e], xv, acc);
+                    } else {
+                        const float t = qv[e] - xv;
+                        acc = fmaf(t, t, acc);
+                    }
                 }
                 tot[s] = acc;
             }
@@ -72,7 +85,7 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
         const float mine = __shfl_sync(FULL, v, 8 * (lane & 3));
         if ((lane >> 2) == s) out = mine;
     }
-    return out;
+    return IP ? -out : out;
 }
 
 // The same for uint8 rows when the query is integral with every coordinate in
@@ -131,12 +144,13 @@ __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ ra
 template <typename T>
 __device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32_t d,
                                                 const float *qs, const uint32_t *qp,
-                                                bool qint, int64_t my_id) {
-    if constexpr (sizeof(T) == 1) {
-        if (qint) return exact_rows_u8int<uint4>(raw, d, qp, my_id);  // qint needs d % 16 == 0
+                                                bool qint, int64_t my_id, bool ip = false) {
+    if constexpr (std::is_same<T, uint8_t>::value) {
+        if (qint && !ip) return exact_rows_u8int<uint4>(raw, d, qp, my_id);  // qint needs d % 16 == 0
     }
-    if ((d * (int)sizeof(T)) % 16 == 0) return exact_rows<T, uint4>(raw, d, qs, my_id);
-    return exact_rows<T, uint32_t>(raw, d, qs, my_id);
+    if ((d * (int)sizeof(T)) % 16 == 0)
+        return ip ? exact_rows<T, uint4, true>(raw, d, qs, my_id) : exact_rows<T, uint4>(raw, d, qs, my_id);
+    return ip ? exact_rows<T, uint32_t, true>(raw, d, qs, my_id) : exact_rows<T, uint32_t>(raw, d, qs, my_id);
 }
 
 // Packs an integral query with every coordinate in 0..255 (the uint8 rows'

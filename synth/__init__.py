@@ -58,7 +58,8 @@ class Mixture:
     ``kind`` selects the output form:
       * ``"f32"``   plain float32 samples;
       * ``"u8"``    samples clipped to [0, 255] and rounded (SIFT-like);
-      * ``"unit"``  float32 samples scaled to unit L2 norm (DEEP-like).
+      * ``"unit"``  float32 samples scaled to unit L2 norm (DEEP-like);
+      * ``"i8"``    samples clipped to [-128, 127] and rounded (SPACEV-like).
     """
     d: int
     ncomp: int
@@ -81,6 +82,9 @@ class Mixture:
         if self.kind == "u8":
             np.clip(x, 0.0, 255.0, out=x)
             return np.rint(x).astype(np.uint8)
+        if self.kind == "i8":
+            np.clip(x, -128.0, 127.0, out=x)
+            return np.rint(x).astype(np.int8)
         if self.kind == "unit":
             x /= np.linalg.norm(x, axis=1, keepdims=True)
         return x.astype(np.float32)
@@ -110,7 +114,7 @@ class Mixture:
 
     @property
     def dtype(self):
-        return np.uint8 if self.kind == "u8" else np.float32
+        return {"u8": np.uint8, "i8": np.int8}.get(self.kind, np.float32)
 
     def base(self, n: int) -> np.ndarray:
         return self.rows(0, n, STREAM_BASE)
@@ -150,6 +154,24 @@ def sift_like_10m() -> Workload:
     16384 lists, M=32, 10k queries, nprobe 64, k 10."""
     return Workload("ivfpq-u8-10m-d128-nlist16384-M32", Mixture(128, 64, 8.0, kind="u8"),
                     10_000_000, 10_000, 16384, 32, 64, 10)
+
+
+def billion_like(n: int = 1_000_000_000) -> Workload:
+    """The billion-scale SIFT-like shape: uint8 d=128 vectors from a
+    4096-component mixture (clipped to 0..255 and rounded), 262144 lists,
+    M=32, 10k queries, nprobe 64 (swept over 64..256), k 10. ``n`` below 1e9
+    keeps every other parameter."""
+    return Workload("ivfpq-u8-%dm-d128-nlist262144-M32" % (n // 1_000_000),
+                    Mixture(128, 4096, 8.0, kind="u8"), n, 10_000, 262144, 32, 64, 10)
+
+
+def spacev_like(n: int = 10_000_000, M: int = 25) -> Workload:
+    """The SPACEV-like shape (Table 1): int8 d=100 vectors from a 64-component
+    mixture (means U[-40, 40], sigma 8, clipped to -128..127 and rounded),
+    M in {20, 25, 50} subspaces of 5, 4 or 2 coordinates, 16384 lists, 10k
+    queries, nprobe 64, k 10."""
+    return Workload("ivfpq-i8-%dm-d100-nlist16384-M%d" % (n // 1_000_000, M),
+                    Mixture(100, 64, 8.0, lo=-40.0, hi=40.0, kind="i8"), n, 10_000, 16384, M, 64, 10)
 
 
 def zipf_sizes(nlist: int, n: int, s: float = 1.1) -> np.ndarray:

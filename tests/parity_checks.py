@@ -8,17 +8,23 @@ import oracle
 RTOL = 1e-4
 
 
+def _metric(parts):
+    return oracle.IP if parts.get("metric", 0) == 1 else oracle.L2
+
+
 def _adc_ref(q, parts):
     """The oracle's FP64 ADC distance (Eq. 1) of given vector ids for query q:
-    its own table over the index's codebooks, summed over the ids' codes."""
-    t = oracle.lut(q, parts["codebooks"])
+    its own table over the index's codebooks (the index's metric), summed
+    over the ids' codes."""
+    t = oracle.lut(q, parts["codebooks"], metric=_metric(parts))
     return lambda ids: oracle.adc(t, parts["codes"], np.asarray(ids, np.int64).astype(np.uint32))
 
 
-def _l2_ref(q, raw):
-    """The oracle's FP64 exact squared L2 of given vector ids (the re-rank's
-    distances, Algorithm 1)."""
-    return lambda ids: oracle.exact_l2(q, raw, np.asarray(ids, np.int64))
+def _l2_ref(q, raw, metric=None):
+    """The oracle's FP64 exact distance of given vector ids (the re-rank's
+    distances, Algorithm 1): squared L2, or -<q, x> with metric IP."""
+    m = oracle.L2 if metric is None else metric
+    return lambda ids: oracle.exact(q, raw, np.asarray(ids, np.int64), metric=m)
 
 
 def _check_topk(gi, gd, oi, od, o_next, k, rtol=RTOL, what="", ref_of=None):
@@ -55,14 +61,14 @@ def _expanded_magnitude(q, cb):
     return qn[:, None] + (cb.astype(np.float64) ** 2).sum(2)
 
 
-def _lowp_lut_bound(q, cb, prec, tc):
+def _lowp_lut_bound(q, cb, prec, tc, metric=oracle.L2):
     """Per-entry bound [M][256] on |table entry - FP64 value| of an FP16 / FP8
     table with a per-(query, subspace) scale and offset: half an ulp of the
     stored residual (relative), an FP32 rounding margin, the FP8 subnormal
     step, and the tensor-core form's rounding when the table comes from the
     BF16 GEMM (hi/lo split: 4e-5 of the expanded form's terms)."""
     rel = 2.0 ** -11 if prec == "F16" else 2.0 ** -4
-    ref = oracle.lut(q, cb)
+    ref = oracle.lut(q, cb, metric=metric)
     resid = ref - ref.min(axis=1, keepdims=True)
     scale = resid.max(axis=1, keepdims=True) / (65504.0 if prec == "F16" else 448.0)
     bound = resid * rel + 1e-5 * np.abs(ref) + scale * (2.0 ** -9 if prec == "FP8" else 2.0 ** -24) + 1e-3
@@ -74,12 +80,13 @@ def _lowp_lut_bound(q, cb, prec, tc):
 def _lowp_adc_bound(q, parts, prec, tc):
     """ids -> bound on |low-precision ADC - FP64 ADC|: the sum of the entry
     bounds the ids' codes pick, plus FP32 summation (2e-6 relative)."""
-    b = _lowp_lut_bound(q, parts["codebooks"], prec, tc)
-    t = oracle.lut(q, parts["codebooks"])
+    b = _lowp_lut_bound(q, parts["codebooks"], prec, tc, _metric(parts))
+    t = oracle.lut(q, parts["codebooks"], metric=_metric(parts))
 
     def f(ids):
         u = np.asarray(ids, np.int64).astype(np.uint32)
-        return oracle.adc(b, parts["codes"], u) + 2e-6 * oracle.adc(t, parts["codes"], u) + 1e-3
+        return oracle.adc(b, parts["codes"], u) + 2e-6 * np.abs(oracle.adc(t, parts["codes"], u)) + 1e-3 \
+            + 2e-6 * oracle.adc(np.abs(t), parts["codes"], u)
     return f
 
 
@@ -91,7 +98,7 @@ def _batched_entry_bound(q, parts, tc, prec="F16"):
     FP16, 2^-4 for FP8 e4m3), the subnormal step below the normal range, an
     FP32 margin, and the tensor-core form's rounding."""
     cb = parts["codebooks"]
-    ref = oracle.lut(q, cb)
+    ref = oracle.lut(q, cb, metric=_metric(parts))
     resid = ref - ref.min(axis=1, keepdims=True)
     q64 = np.asarray(q, np.float64)
     fmax, rel, sub = (65504.0, 2.0 ** -11, 2.0 ** -25) if prec == "F16" else (448.0, 2.0 ** -4, 2.0 ** -10)
@@ -104,7 +111,7 @@ def _batched_entry_bound(q, parts, tc, prec="F16"):
 
 def _batched_adc_bound(q, parts, tc, prec="F16"):
     """ids -> bound on |batched-form ADC - FP64 ADC|: the entry bounds the ids'
-    codes pick; for FP8, half2 sums over 8 subspaces (7 roundings of 2^-11
+    codes pick; for FP8, half2 sums over 16 subspaces (15 roundings of 2^-11
     relative to a partial sum of stored residuals); FP32 sums of the entries
     and the offsets, 1e-5 relative."""
     ref, resid, b = _batched_entry_bound(q, parts, tc, prec)
@@ -113,7 +120,7 @@ def _batched_adc_bound(q, parts, tc, prec="F16"):
         u = np.asarray(ids, np.int64).astype(np.uint32)
         out = oracle.adc(b, parts["codes"], u) + 1e-5 * np.abs(oracle.adc(ref, parts["codes"], u)) + 1e-3
         if prec == "FP8":
-            out = out + 7 * 2.0 ** -11 * (1 + 2.0 ** -4) * oracle.adc(resid, parts["codes"], u)
+            out = out + 15 * 2.0 ** -11 * (1 + 2.0 ** -4) * oracle.adc(resid, parts["codes"], u)
         return out
     return f
 

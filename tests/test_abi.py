@@ -42,8 +42,9 @@ def test_struct_layouts_match_header():
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(fa_build_params), sizeof(fa_index_parts),
          sizeof(fa_search_params), sizeof(fa_index_info));
-  printf("%zu %zu %zu\n", offsetof(fa_search_params, stats), offsetof(fa_index_parts, raw),
-         offsetof(fa_build_params, use_gpu));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(fa_search_params, stats), offsetof(fa_index_parts, raw),
+         offsetof(fa_build_params, use_gpu), offsetof(fa_build_params, metric),
+         offsetof(fa_index_parts, metric));
   return 0; }
 '''
     with tempfile.TemporaryDirectory() as t:
@@ -57,7 +58,8 @@ int main(void) {
     assert sizes == [C.sizeof(fa.fa_build_params), C.sizeof(fa.fa_index_parts),
                      C.sizeof(fa.fa_search_params), C.sizeof(fa.fa_index_info)]
     assert offs == [fa.fa_search_params.stats.offset, fa.fa_index_parts.raw.offset,
-                    fa.fa_build_params.use_gpu.offset]
+                    fa.fa_build_params.use_gpu.offset, fa.fa_build_params.metric.offset,
+                    fa.fa_index_parts.metric.offset]
 
 
 def test_status_strings_and_version():
@@ -83,9 +85,9 @@ def _parts(M=16, d=32, nlist=4, n=20):
 def test_parts_validation_rejects_bad_descriptions(bad):
     cent, cb, codes, prim = _parts()
     ro = ri = None
-    if bad == "M":
-        cb, codes = np.zeros((12, 256, 2), np.float32), np.zeros((20, 12), np.uint8)
-        cent = np.zeros((4, 24), np.float32)
+    if bad == "M":  # more subspaces than the widest scan (64)
+        cb, codes = np.zeros((80, 256, 2), np.float32), np.zeros((20, 80), np.uint8)
+        cent = np.zeros((4, 160), np.float32)
     elif bad == "primary":
         prim = prim.copy()
         prim[3] = 7
