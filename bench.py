@@ -90,7 +90,7 @@ def parse():
                          "billion-scale shape (4096-component uint8 mixture, 262144 lists, Eq. 2 "
                          "replication) at --billion-n vectors")
     ap.add_argument("--billion-n", type=int, default=250_000_000)
-    ap.add_argument("--billion-points", default="128:8192,192:8192,256:8192,256:12288",
+    ap.add_argument("--billion-points", default="64:8192,96:8192,128:8192,192:8192,256:8192",
                     help="nprobe:rerank_n operating points of the billion workload")
     ap.add_argument("--repl", type=float, default=1.08,
                     help="billion workload: mean lists per vector of Eq. 2's replication")

@@ -66,7 +66,15 @@ typedef enum fa_dtype { FA_F32 = 0, FA_U8 = 1, FA_I8 = 2 } fa_dtype;
 typedef enum fa_raw_location {
     FA_RAW_NONE = 0,
     FA_RAW_HOST_PINNED = 1,
-    FA_RAW_DEVICE = 2
+    FA_RAW_DEVICE = 2,
+    /* pinned host memory in 4 KB pages with the storage layout of §4.3: each
+     * list's primary members form a bucket, buckets fill pages of their own
+     * and their unaligned tails share pages by a max-min rule. The re-rank
+     * then reads whole pages: a mini-batch reads each distinct page once
+     * (intra-mini-batch merge) and skips the pages the query read in earlier
+     * mini-batches, which a per-query page buffer in HBM holds
+     * (inter-mini-batch deduplication); a row is read from that buffer. */
+    FA_RAW_HOST_PAGED = 3
 } fa_raw_location;
 
 /* Distance of the search. L2: squared L2 (Eq. 1 as the paper writes it). IP:
@@ -251,6 +259,8 @@ typedef struct fa_search_params {
                                         distinct ids, re-rank mini-batches run,
                                         candidates handed to the re-rank */
     fa_search_trace *trace;          /* optional host trace (forces a sync) */
+    int32_t *page_reads;             /* optional host [nq]: pages each query's re-rank
+                                        read (raw vectors in FA_RAW_HOST_PAGED) */
 } fa_search_params;
 
 /* Fills sp with the plain FP32 form: F32 LUT built in the scan CTA, FP32 coarse
@@ -381,6 +391,13 @@ fa_status fa_debug_fail_alloc(int32_t n);
  * nothing sets, `polls` tries each. Returns FA_ERR_TIMEOUT from the device
  * status word; the CUDA context stays usable. FA_ERR_NODEV without a GPU. */
 fa_status fa_debug_timeout(uint32_t polls);
+
+/* The storage layout of FA_RAW_HOST_PAGED raw vectors (§4.3): page_of[v]
+ * and slot_of[v] (host [n], caller ids) receive each vector's page and its
+ * row in that page; *rows_per_page and *pages the page capacity and count.
+ * FA_ERR_ARG when the index's raw vectors are not paged. */
+fa_status fa_debug_page_map(fa_index *ix, int64_t *page_of, int32_t *slot_of, int32_t *rows_per_page,
+                            int64_t *pages);
 
 /* Sets how many standard deviations above the expected count the scan's
  * sampled threshold estimate sits (a top-n above 256 over many more

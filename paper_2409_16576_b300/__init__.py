@@ -26,7 +26,7 @@ _lib = C.CDLL(LIB_PATH)
 FA_OK, FA_ERR_ARG, FA_ERR_OOM, FA_ERR_CUDA, FA_ERR_TIMEOUT = 0, 1, 2, 3, 4
 FA_ERR_OVERFLOW, FA_ERR_STATE, FA_ERR_BUSY, FA_ERR_IO, FA_ERR_NODEV = 5, 6, 7, 8, 9
 FA_F32, FA_U8, FA_I8 = 0, 1, 2
-FA_RAW_NONE, FA_RAW_HOST_PINNED, FA_RAW_DEVICE = 0, 1, 2
+FA_RAW_NONE, FA_RAW_HOST_PINNED, FA_RAW_DEVICE, FA_RAW_HOST_PAGED = 0, 1, 2, 3
 FA_LUT_F32, FA_LUT_F16, FA_LUT_FP8 = 0, 1, 2
 FA_GEMM_SIMT_F32, FA_GEMM_BF16_TC = 0, 1
 FA_METRIC_L2, FA_METRIC_IP = 0, 1
@@ -80,7 +80,7 @@ class fa_search_params(C.Structure):
     _fields_ = [("lut_prec", i32), ("lut_gemm", i32), ("probe_gemm", i32), ("rerank_n", i32),
                 ("rerank_batch", i32), ("rerank_beta", i32), ("rerank_eps", f32), ("flags", i32),
                 ("k_per_query", P), ("nprobe_per_query", P), ("probes", P), ("stream", P),
-                ("stats", P), ("trace", P)]
+                ("stats", P), ("trace", P), ("page_reads", P)]
 
 
 def _sig(name, res, *args):
@@ -109,6 +109,7 @@ _sig("fa_debug_lut", i32, P, P, P, P)
 _sig("fa_debug_fail_alloc", i32, i32)
 _sig("fa_debug_timeout", i32, C.c_uint32)
 _sig("fa_debug_tau_sigma", i32, C.c_float)
+_sig("fa_debug_page_map", i32, P, P, P, P, P)
 _sig("fa_coarse_probe_noalloc", i32, P, i64, i32, P, i32, i32, P, P)
 _sig("fa_server_params_init", None, P)
 _sig("fa_server_create", i32, P, P, P, P)
@@ -126,7 +127,7 @@ EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_build_index_lists", "fa
            "fa_index_info_get", "fa_save_index", "fa_load_index", "fa_free_index",
            "fa_search_params_init", "fa_search", "fa_search_ex", "fa_autotune", "fa_debug_probes",
            "fa_debug_candidates", "fa_debug_lut", "fa_debug_fail_alloc", "fa_debug_timeout",
-           "fa_debug_tau_sigma",
+           "fa_debug_tau_sigma", "fa_debug_page_map",
            "fa_coarse_probe_noalloc", "fa_server_params_init",
            "fa_server_create", "fa_server_submit", "fa_server_poll", "fa_server_stats",
            "fa_server_destroy", "fa_last_error",
@@ -306,10 +307,12 @@ def fa_search(ix: Index, queries: np.ndarray, k: int, nprobe: int):
 
 def fa_search_ex(ix: Index, queries, k: int, nprobe: int, params: fa_search_params | None = None,
                  out_ids=None, out_dist=None, k_per_query=None, nprobe_per_query=None,
-                 probes=None, stats: bool = False, stream=None, trace=None):
+                 probes=None, stats: bool = False, stream=None, trace=None, page_reads=None):
     """Search with explicit parameters. ``queries`` is a float32 numpy array
     (host) or a CUDA torch tensor (device; outputs then default to CUDA
-    tensors). Returns (ids, dists) or (ids, dists, stats)."""
+    tensors). Returns (ids, dists) or (ids, dists, stats). ``page_reads``, a
+    host int32 array of nq, receives the pages each query's re-rank read
+    (raw vectors in FA_RAW_HOST_PAGED)."""
     sp = search_params() if params is None else fa_search_params.from_buffer_copy(params)
     on_dev = _is_cuda(queries)
     keep = []
@@ -356,6 +359,9 @@ def fa_search_ex(ix: Index, queries, k: int, nprobe: int, params: fa_search_para
     sp.stream = stream
     sp.stats = _ptr(st)
     sp.trace = C.cast(C.byref(trace), P) if trace is not None else None
+    if page_reads is not None:
+        assert page_reads.dtype == np.int32 and page_reads.shape == (nq,) and page_reads.flags.c_contiguous
+        sp.page_reads = _ptr(page_reads)
     _check(_lib.fa_search_ex(ix.handle, _ptr(queries), nq, d, k, nprobe, C.byref(sp),
                              _ptr(out_ids), _ptr(out_dist)))
     return (out_ids, out_dist, st) if stats else (out_ids, out_dist)
@@ -447,6 +453,17 @@ def fa_coarse_probe_noalloc(queries, centroids, nprobe: int, out=None, stream=No
 def fa_debug_fail_alloc(n: int) -> None:
     """The n-th next device allocation of the library fails (0 turns it off)."""
     _check(_lib.fa_debug_fail_alloc(n))
+
+
+def fa_debug_page_map(ix: Index) -> dict:
+    """§4.3's storage layout of paged raw vectors: page and slot of each
+    vector (caller ids), rows a page and page count."""
+    n = ix.info().n
+    page_of = np.empty(n, dtype=np.int64)
+    slot_of = np.empty(n, dtype=np.int32)
+    rows, pages = C.c_int32(0), C.c_int64(0)
+    _check(_lib.fa_debug_page_map(ix.handle, _ptr(page_of), _ptr(slot_of), C.byref(rows), C.byref(pages)))
+    return dict(page_of=page_of, slot_of=slot_of, rows_per_page=rows.value, pages=pages.value)
 
 
 def fa_debug_timeout(polls: int) -> None:

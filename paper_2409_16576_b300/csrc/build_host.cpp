@@ -424,4 +424,59 @@ void encode_with_lists(const void *base, int64_t n, int32_t d, fa_dtype dt,
     train_pq_and_encode(base, n, d, dt, p, X.data(), S, out);
 }
 
+// Storage layout of the raw vectors on the slow tier (§4.3): the vectors
+// whose primary list is l form bucket l (ascending ids), a page holds cap
+// of them. Every bucket fills whole pages of its own first (pages numbered by
+// list); the rest of each bucket (a tail shorter than a page) is packed into
+// shared pages by a max-min rule: the largest unplaced tail opens a page and
+// the smallest unplaced tails join it, smallest first, while they fit (ties
+// by list). Returns the page count.
+int64_t page_layout(const std::vector<int32_t> &primary, int32_t nlist, int32_t cap,
+                    std::vector<int64_t> &page_of, std::vector<int32_t> &slot_of) {
+    const int64_t n = (int64_t)primary.size();
+    std::vector<std::vector<int64_t>> bucket(nlist);
+    for (int64_t v = 0; v < n; ++v) bucket[primary[v]].push_back(v);
+    page_of.assign(n, -1);
+    slot_of.assign(n, -1);
+    int64_t page = 0;
+    std::vector<std::pair<int64_t, int32_t>> tails;  // (size, list)
+    for (int32_t l = 0; l < nlist; ++l) {
+        const std::vector<int64_t> &b = bucket[l];
+        const int64_t whole = (int64_t)b.size() / cap;
+        for (int64_t t = 0; t < whole * cap; ++t) {
+            page_of[b[t]] = page + t / cap;
+            slot_of[b[t]] = (int32_t)(t % cap);
+        }
+        page += whole;
+        if (b.size() % cap) tails.push_back({(int64_t)(b.size() % cap), l});
+    }
+    std::sort(tails.begin(), tails.end(), [](const std::pair<int64_t, int32_t> &a,
+                                             const std::pair<int64_t, int32_t> &b) {
+        return a.first != b.first ? a.first > b.first : a.second < b.second;
+    });
+    std::vector<char> placed(tails.size(), 0);
+    int64_t lo = (int64_t)tails.size() - 1;
+    for (size_t hi = 0; hi < tails.size(); ++hi) {
+        if (placed[hi]) continue;
+        int64_t room = cap, slot = 0;
+        size_t pick = hi;
+        for (;;) {
+            const std::vector<int64_t> &b = bucket[tails[pick].second];
+            const int64_t sz = tails[pick].first, from = (int64_t)b.size() - sz;
+            for (int64_t t = 0; t < sz; ++t) {
+                page_of[b[from + t]] = page;
+                slot_of[b[from + t]] = (int32_t)(slot + t);
+            }
+            slot += sz;
+            room -= sz;
+            placed[pick] = 1;
+            while (lo > (int64_t)hi && placed[lo]) --lo;
+            if (lo <= (int64_t)hi || tails[lo].first > room) break;
+            pick = (size_t)lo;
+        }
+        ++page;
+    }
+    return page;
+}
+
 }  // namespace fa

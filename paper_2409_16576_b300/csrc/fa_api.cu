@@ -97,7 +97,7 @@ void free_device_index(fa_index *ix) {
     DeviceIndex &d = ix->dev;
     void *ptrs[] = {d.centroids, d.cnorm, d.codebooks, d.codes, d.list_beg, d.rep_off,
                     d.rep_v, d.rep_mo, d.rep_t, d.mem, d.perm, d.raw_dev_alloc,
-                    d.centroids_bf16, d.codebooks_bf16, d.cbnorm, d.lorder};
+                    d.centroids_bf16, d.codebooks_bf16, d.cbnorm, d.lorder, d.vpage, d.vslot};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceIndex{};
@@ -280,6 +280,38 @@ void upload_index(fa_index *ix) {
             D.raw_dev_alloc = dev_upload(rows.data(), rb, bytes);
             D.raw = D.raw_dev_alloc;
             D.raw_internal = 1;
+        } else if (ix->raw_location == FA_RAW_HOST_PAGED) {
+            // the rows in §4.3's pages in pinned host memory, read by the
+            // paged re-rank through the mapping; page and row of each vector
+            const int64_t rowb = (int64_t)d * raw_elem(ix->raw_dtype);
+            int32_t cap = (int32_t)std::max<int64_t>(1, 4096 / rowb);
+            while (cap > 1 && ((int64_t)cap * rowb) % 16 != 0) --cap;  // 16-byte page copies
+            FA_REQUIRE(rowb % 4 == 0 && ((int64_t)cap * rowb) % 16 == 0 && cap <= 65535, FA_ERR_ARG,
+                       "paged raw vectors need rows of a multiple of 4 bytes");
+            const int64_t np = page_layout(ix->primary, nlist, cap, ix->page_of, ix->slot_of);
+            const size_t pb = (size_t)cap * rowb;
+            FA_CHECK_CUDA(cudaHostAlloc(&ix->h_pages, std::max<size_t>(16, pb * np),
+                                        cudaHostAllocMapped | cudaHostAllocPortable));
+            const uint8_t *src = (const uint8_t *)ix->h_raw;
+#pragma omp parallel for schedule(static)
+            for (int64_t v = 0; v < n; ++v)
+                memcpy((uint8_t *)ix->h_pages + (size_t)ix->page_of[v] * pb + (size_t)ix->slot_of[v] * rowb,
+                       src + (size_t)v * rowb, (size_t)rowb);
+            std::vector<uint32_t> vp(n);
+            std::vector<uint16_t> vs(n);
+            for (int64_t v = 0; v < n; ++v) {
+                vp[v] = (uint32_t)ix->page_of[v];
+                vs[v] = (uint16_t)ix->slot_of[v];
+            }
+            D.vpage = dev_upload(vp.data(), vp.size(), bytes);
+            D.vslot = dev_upload(vs.data(), vs.size(), bytes);
+            D.page_rows = cap;
+            D.page_bytes = (int32_t)pb;
+            D.n_pages = np;
+            void *dp = nullptr;
+            FA_CHECK_CUDA(cudaHostGetDevicePointer(&dp, ix->h_pages, 0));
+            D.raw = dp;
+            D.pinned_bytes = (int64_t)(pb * np);
         } else {
             void *dp = nullptr;
             FA_CHECK_CUDA(cudaHostGetDevicePointer(&dp, ix->h_raw, 0));
@@ -304,9 +336,16 @@ static void ws_free_buffers(Workspace *w) {
                   w->tmisc, w->partial, w->topkeys, w->out_ids, w->out_dist,
                   w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr, w->selbuf,
                   w->redo, w->bq_lcnt, w->bq_lqoff, w->bq_lcur, w->bq_upre, w->bq_lq, w->bq_pbits,
-                  w->bq_tau, w->bq_cnt, w->bq_qsum, w->bq_buf, w->bq_ctr};
+                  w->bq_tau, w->bq_cnt, w->bq_qsum, w->bq_buf, w->bq_ctr, w->pg_cache, w->pg_table,
+                  w->pg_tslot, w->pg_reads};
     for (void *p : dp)
         if (p) cudaFree(p);
+    w->pg_cache = nullptr;
+    w->pg_table = nullptr;
+    w->pg_tslot = nullptr;
+    w->pg_reads = nullptr;
+    w->pg_cap_pages = w->pg_cap_nq = 0;
+    w->pg_tsize = w->pg_warps = 0;
     w->bq_lcnt = w->bq_lqoff = w->bq_lcur = w->bq_upre = w->bq_pbits = w->bq_cnt = w->bq_ctr = nullptr;
     w->bq_lq = nullptr;
     w->bq_tau = w->bq_buf = nullptr;
@@ -441,6 +480,41 @@ static void ws_ensure_batched(fa_index *ix, Workspace *w, int64_t nq, int32_t np
     w->bq_cap = cc;
 }
 
+// Buffers of the paged re-rank: each warp of the persistent grid holds a
+// buffer of top-n pages (every task on its own page at worst, so the buffer
+// never evicts and inter-mini-batch deduplication is complete) and a page
+// table of at least twice as many entries. The warps are capped so the
+// buffers stay within 8 GiB.
+static void ws_ensure_paged(fa_index *ix, Workspace *w, int64_t nq, int32_t ntop) {
+    const DeviceIndex &D = ix->dev;
+    const int64_t pb = D.page_bytes;
+    int32_t tsize = 64;
+    while (tsize < 2 * ntop) tsize *= 2;
+    const int32_t warps = (int32_t)std::max<int64_t>(
+        1, std::min<int64_t>(2ll * num_sms(ix->device), (8ll << 30) / std::max<int64_t>(1, (int64_t)ntop * pb)));
+    if (w->pg_cache && w->pg_cap_nq >= nq && w->pg_cap_pages >= ntop && w->pg_tsize >= tsize) return;
+    if (w->pending) FA_CHECK_CUDA(cudaEventSynchronize(w->done));
+    w->pending = false;
+    FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
+    ws_drop_graph(w);
+    void *old[] = {w->pg_cache, w->pg_table, w->pg_tslot, w->pg_reads};
+    for (void *p : old)
+        if (p) cudaFree(p);
+    w->pg_cache = nullptr;
+    w->pg_table = nullptr;
+    w->pg_tslot = nullptr;
+    w->pg_reads = nullptr;
+    const int64_t cq = std::max(nq, w->pg_cap_nq);
+    dalloc(w->pg_cache, (size_t)warps * ntop * pb);
+    dalloc(w->pg_table, (size_t)warps * tsize);
+    dalloc(w->pg_tslot, (size_t)warps * tsize);
+    dalloc(w->pg_reads, (size_t)cq);
+    w->pg_cap_pages = ntop;
+    w->pg_cap_nq = cq;
+    w->pg_tsize = tsize;
+    w->pg_warps = warps;
+}
+
 // Per-tile top-n buffer of the tiled form: 16 tiles per query on average,
 // the tile size adapts on the device so the plan always fits.
 static void ws_ensure_partial(Workspace *w, int64_t nq, int32_t ntop) {
@@ -573,6 +647,10 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     Workspace *w = lease.w;
     ws_ensure(ix, w, nq, k, nprobe, ntop, lut_bytes);
     if (batched) ws_ensure_batched(ix, w, nq, nprobe, ntop);
+    // raw vectors in §4.3's pages: the re-rank runs on its own, reading pages
+    const bool paged = rerank && ix->dev.raw_location == FA_RAW_HOST_PAGED;
+    if (paged) ws_ensure_paged(ix, w, nq, ntop);
+    FA_REQUIRE(!sp.page_reads || paged, FA_ERR_ARG, "page_reads needs a re-rank of paged raw vectors");
     cudaStream_t st = sp.stream ? (cudaStream_t)sp.stream : w->stream;
     if (w->pending) FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->done, 0));
     const DeviceIndex &D = ix->dev;
@@ -680,7 +758,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             launch_query_order(probes, nq, nprobe, ix->nlist, w->bucket, w->order, st);
             sl.order = w->order;
             sl.redo = w->redo;
-            sl.fuse_rerank = (rerank && sp.rerank_eps < 0.f) ? 1 : 0;
+            sl.fuse_rerank = (rerank && !paged && sp.rerank_eps < 0.f) ? 1 : 0;
             sl.k = k;
             sl.kq = kq;
             sl.rerank_batch = sp.rerank_batch;
@@ -755,7 +833,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             sl.selbuf = w->selbuf;
             sl.redo = w->redo;
             // an exhaustive re-rank (eps < 0) runs inside the selecting scan
-            sl.fuse_rerank = (rerank && sp.rerank_eps < 0.f) ? 1 : 0;
+            sl.fuse_rerank = (rerank && !paged && sp.rerank_eps < 0.f) ? 1 : 0;
             sl.k = k;
             sl.kq = kq;
             sl.rerank_batch = sp.rerank_batch;
@@ -767,7 +845,19 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         }
         if (!pipelined) {
             tr.mark(3);
-            if (rerank && fused)  // only the queries the selecting scan handed back
+            if (paged) {
+                PagedBufs pb{};
+                pb.cache = w->pg_cache;
+                pb.table = w->pg_table;
+                pb.tslot = w->pg_tslot;
+                pb.reads = w->pg_reads;
+                pb.cap_pages = w->pg_cap_pages;
+                pb.tsize = w->pg_tsize;
+                pb.warps = w->pg_warps;
+                launch_rerank_paged(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
+                                    sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, pb,
+                                    w->tile_ctr + 1, st);
+            } else if (rerank && fused)  // only the queries the selecting scan handed back
                 launch_rerank(D, qd, w->topkeys, nq, ntop, k, kq, sp.rerank_batch, sp.rerank_beta,
                               sp.rerank_eps, oid, odist, sp.stats ? w->stats : nullptr, 1,
                               w->tile_ctr + 1, st, w->redo, w->tile_ctr + 3);
@@ -841,6 +931,8 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     }
     if (sp.stats)
         FA_CHECK_CUDA(cudaMemcpyAsync(w->h_stats, w->stats, sizeof(int32_t) * 4 * nq, cudaMemcpyDeviceToHost, st));
+    if (sp.page_reads)  // pageable host memory: the copy completes before it returns
+        FA_CHECK_CUDA(cudaMemcpyAsync(sp.page_reads, w->pg_reads, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, st));
     if (!((sp.flags & FA_NO_SYNC) && odev && !sp.stats && !sp.trace))
         FA_CHECK_CUDA(cudaMemcpyAsync(w->h_err, w->err, 4, cudaMemcpyDeviceToHost, st));
     if ((sp.flags & FA_NO_SYNC) && odev && !sp.stats && !sp.trace) {
@@ -872,6 +964,8 @@ static void check_parts(const fa_index_parts *p) {
     FA_REQUIRE(p->raw_dtype == FA_F32 || p->raw_dtype == FA_U8 || p->raw_dtype == FA_I8, FA_ERR_ARG,
                "bad raw dtype");
     FA_REQUIRE(p->metric == FA_METRIC_L2 || p->metric == FA_METRIC_IP, FA_ERR_ARG, "bad metric");
+    FA_REQUIRE(p->raw_location >= FA_RAW_NONE && p->raw_location <= FA_RAW_HOST_PAGED, FA_ERR_ARG,
+               "bad raw location");
     for (int64_t v = 0; v < p->n; ++v)
         FA_REQUIRE(p->primary[v] >= 0 && p->primary[v] < p->nlist, FA_ERR_ARG, "primary list out of range");
     if (p->rep_off) {
@@ -955,6 +1049,7 @@ static void destroy(fa_index *ix) {
         if (ix->h_raw_pinned) cudaFreeHost(ix->h_raw);
         else free(ix->h_raw);
     }
+    if (ix->h_pages) cudaFreeHost(ix->h_pages);
     delete ix;
 }
 
@@ -1458,6 +1553,21 @@ fa_status fa_debug_candidates(fa_index *ix, const float *query, int32_t nprobe,
         *out_n = (int64_t)ids.size();
         FA_REQUIRE((int64_t)ids.size() <= cap, FA_ERR_OVERFLOW, "output capacity too small");
         std::copy(ids.begin(), ids.end(), out_ids);
+    });
+}
+
+fa_status fa_debug_page_map(fa_index *ix, int64_t *page_of, int32_t *slot_of, int32_t *rows_per_page,
+                            int64_t *pages) {
+    if (!ix) {
+        set_error("null index");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] {
+        FA_REQUIRE(ix->raw_location == FA_RAW_HOST_PAGED, FA_ERR_ARG, "raw vectors are not paged");
+        if (page_of) memcpy(page_of, ix->page_of.data(), sizeof(int64_t) * ix->page_of.size());
+        if (slot_of) memcpy(slot_of, ix->slot_of.data(), sizeof(int32_t) * ix->slot_of.size());
+        if (rows_per_page) *rows_per_page = ix->dev.page_rows;
+        if (pages) *pages = ix->dev.n_pages;
     });
 }
 

@@ -99,6 +99,11 @@ struct DeviceIndex {
     float *cbnorm = nullptr;        // [M][256] |C_m[c]|^2 (FP32)
     float cb_max_norm2 = 0.f;       // largest |C_m[c]|^2 (bounds every table entry)
     uint32_t *lorder = nullptr;     // [nlist] lists by decreasing chunk count (batched form)
+    // raw vectors in pages (FA_RAW_HOST_PAGED): page and row of every caller id
+    uint32_t *vpage = nullptr;      // [n]
+    uint16_t *vslot = nullptr;      // [n]
+    int32_t page_rows = 0, page_bytes = 0;  // rows a page, bytes a page (rows x row bytes)
+    int64_t n_pages = 0;
     int64_t device_bytes = 0;
     int64_t pinned_bytes = 0;
 };
@@ -165,6 +170,13 @@ struct Workspace {
     float *bq_qsum = nullptr;      // [cap_nq][2]
     uint64_t *bq_buf = nullptr;    // [cap_nq][bq_cap]
     uint32_t *bq_ctr = nullptr;    // [8]
+    // paged re-rank (FA_RAW_HOST_PAGED): per-warp page buffers and page tables
+    uint8_t *pg_cache = nullptr;
+    uint64_t *pg_table = nullptr;
+    uint32_t *pg_tslot = nullptr;
+    int32_t *pg_reads = nullptr;   // [cap_nq]
+    int64_t pg_cap_pages = 0, pg_cap_nq = 0;
+    int32_t pg_tsize = 0, pg_warps = 0;
     // pinned host staging for host-buffer calls
     float *h_q = nullptr;
     int64_t *h_ids = nullptr;
@@ -198,6 +210,9 @@ struct fa_index {
     std::vector<int64_t> rep_off, rep_ids;
     void *h_raw = nullptr;        // caller-order raw copy (pinned when HOST_PINNED)
     bool h_raw_pinned = false;
+    void *h_pages = nullptr;      // HOST_PAGED: pinned, mapped pages of rows (§4.3 layout)
+    std::vector<int64_t> page_of; // HOST_PAGED: page of each vector (caller ids)
+    std::vector<int32_t> slot_of; // HOST_PAGED: row of each vector in its page
     int device = 0;
     fa::DeviceIndex dev;
     // workspace pool
@@ -342,6 +357,22 @@ void launch_lut_global(const DeviceIndex &ix, const float *q, int64_t nq, int pr
 void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, int32_t ntop,
                    int32_t k, const int32_t *kq, int64_t *out_ids, float *out_dist,
                    cudaStream_t st);
+// Paged re-rank buffers (one page buffer and page table per warp).
+struct PagedBufs {
+    uint8_t *cache;
+    uint64_t *table;
+    uint32_t *tslot;
+    int32_t *reads;         // [nq] pages each query read
+    int64_t cap_pages;      // pages a warp's buffer holds (>= top-n)
+    int32_t tsize, warps;   // table entries a warp (power of two), warps of the grid
+};
+void launch_rerank_paged(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
+                         int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
+                         float eps, int64_t *out_ids, float *out_dist, int32_t *stats,
+                         const PagedBufs &pb, uint32_t *ctr, cudaStream_t st);
+// Storage layout of §4.3 for vectors of the given primary lists.
+int64_t page_layout(const std::vector<int32_t> &primary, int32_t nlist, int32_t cap,
+                    std::vector<int64_t> &page_of, std::vector<int32_t> &slot_of);
 void launch_rerank(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
                    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
                    float eps, int64_t *out_ids, float *out_dist, int32_t *stats, int warps,

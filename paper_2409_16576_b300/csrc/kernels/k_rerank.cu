@@ -124,12 +124,84 @@ void launch_finish(const DeviceIndex &ix, const uint64_t *topkeys, int64_t nq, i
     FA_CHECK_CUDA(cudaGetLastError());
 }
 
+// Page buffer of one warp for the paged re-rank (§4.3): pages read so far by
+// the warp's current query, found through an open-addressing table whose
+// entries carry the query's generation (so no table clearing per query).
+struct PagedCtx {
+    const uint32_t *vpage;  // [n] page of each caller id
+    const uint16_t *vslot;  // [n] row of each caller id in its page
+    const uint8_t *pages;   // the pages (mapped pinned host memory), page_bytes apart
+    uint8_t *cache;         // this warp's buffer: cap_pages pages
+    uint64_t *table;        // [tsize] (generation << 32) | (page + 1), 0 = empty
+    uint32_t *tslot;        // [tsize] buffer slot of each entry
+    int32_t tsize, page_rows, page_bytes;
+    uint32_t gen;           // generation of the current query
+    int32_t nread;          // pages the current query read
+};
+
+// Rows of the 32 tasks of a step (uid = caller id, < 0 = none) resolved to
+// rows of the warp's page buffer: the distinct pages of the step are looked
+// up once each (one lane per page), the ones not yet buffered are copied
+// from the slow tier by the whole warp, 16 bytes a lane. Warp-collective.
+__device__ __forceinline__ int64_t paged_row(PagedCtx &pg, int64_t uid) {
+    const int lane = threadIdx.x & 31;
+    const bool need = uid >= 0;
+    const uint32_t p = need ? pg.vpage[uid] : 0xffffffffu;
+    const uint32_t peers = __match_any_sync(FULL, p);
+    const int leader = __ffs(peers) - 1;
+    const bool lead = need && lane == leader;
+    const uint64_t key = ((uint64_t)pg.gen << 32) | (uint64_t)(p + 1u);
+    const uint32_t tmask = (uint32_t)(pg.tsize - 1);
+    const uint32_t h0 = (p * 2654435761u) & tmask;
+    int32_t slot = -1;
+    if (lead) {  // lookups in parallel (the table holds at most half its size)
+        uint32_t h = h0;
+        for (int probe = 0; probe < pg.tsize; ++probe) {
+            const uint64_t e = pg.table[h];
+            if (e == key) {
+                slot = (int32_t)pg.tslot[h];
+                break;
+            }
+            if ((uint32_t)(e >> 32) != pg.gen) break;  // empty for this query: p is new
+            h = (h + 1) & tmask;
+        }
+    }
+    const uint32_t miss = __ballot_sync(FULL, lead && slot < 0);
+    if (lead && slot < 0) slot = pg.nread + __popc(miss & ((1u << lane) - 1u));
+    // insertions one lane at a time: two new pages may probe the same entry
+    for (uint32_t mm = miss; mm; mm &= mm - 1) {
+        if (lane == __ffs(mm) - 1) {
+            uint32_t h = h0;
+            for (int probe = 0; probe < pg.tsize; ++probe) {
+                if ((uint32_t)(pg.table[h] >> 32) != pg.gen) break;
+                h = (h + 1) & tmask;
+            }
+            pg.table[h] = key;
+            pg.tslot[h] = (uint32_t)slot;
+        }
+        __syncwarp();
+    }
+    for (uint32_t mm = miss; mm; mm &= mm - 1) {
+        const int src = __ffs(mm) - 1;
+        const uint32_t pp = __shfl_sync(FULL, p, src);
+        const int32_t ss = __shfl_sync(FULL, slot, src);
+        const uint4 *from = reinterpret_cast<const uint4 *>(pg.pages + (size_t)pp * pg.page_bytes);
+        uint4 *to = reinterpret_cast<uint4 *>(pg.cache + (size_t)ss * pg.page_bytes);
+        for (int o = lane; o < pg.page_bytes / 16; o += 32) to[o] = from[o];
+    }
+    pg.nread += __popc(miss);
+    __syncwarp();
+    slot = __shfl_sync(FULL, slot, leader);
+    return need ? (int64_t)slot * pg.page_rows + pg.vslot[uid] : (int64_t)-1;
+}
+
 template <int R, typename T>
 __device__ __forceinline__ void rerank_one(
     const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t qi,
     int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
     const int64_t *__restrict__ perm, const T *__restrict__ raw, int raw_internal,
-    int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, float *qs, int ip) {
+    int64_t *__restrict__ out_ids, float *__restrict__ out_dist, int32_t *stats, float *qs, int ip,
+    PagedCtx *pg = nullptr) {
     const int lane = threadIdx.x & 31;
     __syncwarp();  // the previous query of this warp is done with qs
     for (int j = lane; j < d; j += 32) qs[j] = q[qi * d + j];
@@ -175,7 +247,9 @@ __device__ __forceinline__ void rerank_one(
                 nend = end + batch < valid ? end + batch : valid;
             }
             const int64_t uid_next = task_id(ns + lane, nend);
-            const float dist = exact_rows_any<T>(raw, d, qs, qp, qint, uid, ip != 0);
+            const float dist = pg ? exact_rows_any<T, true>(reinterpret_cast<const T *>(pg->cache), d, qs, qp,
+                                                            qint, paged_row(*pg, uid), ip != 0)
+                                  : exact_rows_any<T>(raw, d, qs, qp, qint, uid, ip != 0);
             // only keys below Q's kk-th can change Q's first kk entries (the
             // output and Eq. 3); a step with none leaves them as they are.
             // Keys carry caller ids (ties break by them, as in the oracle):
@@ -308,6 +382,75 @@ static void launch_rerank_t(const DeviceIndex &ix, const float *q, const uint64_
     else
         FA_REQUIRE(false, FA_ERR_ARG, "re-rank supports k <= 128");
 #undef FA_RR
+    FA_CHECK_CUDA(cudaGetLastError());
+}
+
+// Paged re-rank: persistent one-warp CTAs pull queries; each warp re-reads
+// nothing its query already read (its page buffer), and writes the query's
+// page-read count. Row ids are caller ids (the pages are laid out by them).
+template <int R, typename T>
+__global__ void __launch_bounds__(32) k_rerank_paged(
+    const float *__restrict__ q, int32_t d, const uint64_t *__restrict__ topkeys, int64_t nq,
+    int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta, float eps,
+    const int64_t *__restrict__ perm, int64_t *__restrict__ out_ids, float *__restrict__ out_dist,
+    int32_t *stats, uint32_t *ctr, PagedCtx base, int64_t cap_pages, int32_t *reads, int ip) {
+    extern __shared__ float qsm[];
+    const int lane = threadIdx.x & 31;
+    PagedCtx pg = base;
+    pg.cache = base.cache + (size_t)blockIdx.x * cap_pages * base.page_bytes;
+    pg.table = base.table + (size_t)blockIdx.x * base.tsize;
+    pg.tslot = base.tslot + (size_t)blockIdx.x * base.tsize;
+    for (uint32_t it = 1;; ++it) {
+        uint32_t x = 0;
+        if (lane == 0) x = atomicAdd(ctr, 1u);
+        const int64_t qi = __shfl_sync(FULL, x, 0);
+        if (qi >= nq) break;
+        pg.gen = it;  // a table entry of an earlier query of this warp reads as empty
+        pg.nread = 0;
+        rerank_one<R, T>(q, d, topkeys, qi, ntop, k, kq, batch, beta, eps, perm,
+                         reinterpret_cast<const T *>(pg.cache), 0, out_ids, out_dist, stats, qsm, ip, &pg);
+        if (lane == 0) reads[qi] = pg.nread;
+    }
+}
+
+void launch_rerank_paged(const DeviceIndex &ix, const float *q, const uint64_t *topkeys, int64_t nq,
+                         int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
+                         float eps, int64_t *out_ids, float *out_dist, int32_t *stats,
+                         const PagedBufs &pb, uint32_t *ctr, cudaStream_t st) {
+    if (nq == 0) return;
+    FA_REQUIRE(ix.vpage && ix.raw, FA_ERR_ARG, "paged re-rank needs paged raw vectors");
+    FA_REQUIRE(pb.cap_pages >= ntop, FA_ERR_ARG, "page buffer smaller than the top-n");
+    FA_REQUIRE(ix.d % 4 == 0 || ix.raw_dtype == FA_F32, FA_ERR_ARG, "paged re-rank needs d % 4 == 0");
+    FA_CHECK_CUDA(cudaMemsetAsync(ctr, 0, 4, st));
+    FA_CHECK_CUDA(cudaMemsetAsync(pb.table, 0, sizeof(uint64_t) * (size_t)pb.tsize * pb.warps, st));
+    PagedCtx c{};
+    c.vpage = ix.vpage;
+    c.vslot = ix.vslot;
+    c.pages = static_cast<const uint8_t *>(ix.raw);
+    c.cache = pb.cache;
+    c.table = pb.table;
+    c.tslot = pb.tslot;
+    c.tsize = pb.tsize;
+    c.page_rows = ix.page_rows;
+    c.page_bytes = ix.page_bytes;
+    const int smem = (ix.d + ix.d / 4 + 1) * 4;
+    const int ip = ix.metric == FA_METRIC_IP ? 1 : 0;
+#define FA_RRP(RR, TT)                                                                              \
+    k_rerank_paged<RR, TT><<<pb.warps, 32, smem, st>>>(q, ix.d, topkeys, nq, ntop, k, kq, batch, beta, \
+                                                      eps, ix.perm, out_ids, out_dist, stats, ctr, c,  \
+                                                      pb.cap_pages, pb.reads, ip)
+#define FA_RRP_T(TT)                                                                               \
+    do {                                                                                           \
+        if (k <= 32) FA_RRP(1, TT);                                                                \
+        else if (k <= 64) FA_RRP(2, TT);                                                           \
+        else if (k <= 128) FA_RRP(4, TT);                                                          \
+        else FA_REQUIRE(false, FA_ERR_ARG, "re-rank supports k <= 128");                           \
+    } while (0)
+    if (ix.raw_dtype == FA_U8) FA_RRP_T(uint8_t);
+    else if (ix.raw_dtype == FA_I8) FA_RRP_T(int8_t);
+    else FA_RRP_T(float);
+#undef FA_RRP_T
+#undef FA_RRP
     FA_CHECK_CUDA(cudaGetLastError());
 }
 

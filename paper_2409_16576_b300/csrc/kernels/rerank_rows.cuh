@@ -18,7 +18,15 @@ namespace fa {
 // loads of all 32 rows are issued before any is summed; the eight partial
 // sums of a row are added with three shuffles.
 // IP: the negated inner product -<q, x> instead of the squared L2.
-template <typename T, typename C, bool IP = false>
+// CG: rows written earlier by the same kernel (a page buffer): loads through
+// L2 only, never the non-coherent read-only path.
+template <typename C, bool CG>
+__device__ __forceinline__ C row_piece(const C *p) {
+    if constexpr (CG) return __ldcg(p);
+    else return *p;
+}
+
+template <typename T, typename C, bool IP = false, bool CG = false>
 __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d,
                                             const float *qs, int64_t my_id) {
     constexpr int EPC = (int)(sizeof(C) / sizeof(T));  // elements per piece
@@ -36,7 +44,7 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
         for (int s = 0; s < 8; ++s) {
             const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
             if (id >= 0 && pc < pieces)
-                x[s] = reinterpret_cast<const C *>(raw + id * (int64_t)d)[pc];
+                x[s] = row_piece<C, CG>(reinterpret_cast<const C *>(raw + id * (int64_t)d) + pc);
             else
                 x[s] = C{};
         }
@@ -94,7 +102,7 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
 // four squared differences per instruction. Every partial sum is an integer
 // below 2^24 for d <= 258, so the float returned equals the FP32 sum of
 // squared differences exactly.
-template <typename C>
+template <typename C, bool CG = false>
 __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ raw, int32_t d,
                                                   const uint32_t *qp, int64_t my_id) {
     constexpr int WPC = (int)(sizeof(C) / 4);  // 32-bit words per piece
@@ -110,7 +118,7 @@ __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ ra
         for (int s = 0; s < 8; ++s) {
             const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
             if (id >= 0 && pc < pieces)
-                x[s] = reinterpret_cast<const C *>(raw + id * (int64_t)d)[pc];
+                x[s] = row_piece<C, CG>(reinterpret_cast<const C *>(raw + id * (int64_t)d) + pc);
             else
                 x[s] = C{};
         }
@@ -141,16 +149,17 @@ __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ ra
 
 // Row pieces: 16 bytes when every row is a multiple of 16 bytes long, else
 // 4-byte words.
-template <typename T>
+template <typename T, bool CG = false>
 __device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32_t d,
                                                 const float *qs, const uint32_t *qp,
                                                 bool qint, int64_t my_id, bool ip = false) {
     if constexpr (std::is_same<T, uint8_t>::value) {
-        if (qint && !ip) return exact_rows_u8int<uint4>(raw, d, qp, my_id);  // qint needs d % 16 == 0
+        if (qint && !ip) return exact_rows_u8int<uint4, CG>(raw, d, qp, my_id);  // qint needs d % 16 == 0
     }
     if ((d * (int)sizeof(T)) % 16 == 0)
-        return ip ? exact_rows<T, uint4, true>(raw, d, qs, my_id) : exact_rows<T, uint4>(raw, d, qs, my_id);
-    return ip ? exact_rows<T, uint32_t, true>(raw, d, qs, my_id) : exact_rows<T, uint32_t>(raw, d, qs, my_id);
+        return ip ? exact_rows<T, uint4, true, CG>(raw, d, qs, my_id) : exact_rows<T, uint4, false, CG>(raw, d, qs, my_id);
+    return ip ? exact_rows<T, uint32_t, true, CG>(raw, d, qs, my_id)
+              : exact_rows<T, uint32_t, false, CG>(raw, d, qs, my_id);
 }
 
 // Packs an integral query with every coordinate in 0..255 (the uint8 rows'
