@@ -94,6 +94,8 @@ def lib():
         _lib.or_page_layout.restype = i64
         _lib.or_rerank_pages.argtypes = [P, i32, P, i32, P, i32, i32, i32, f32, i32, P, P, P, i32, P]
         _lib.or_rerank_pages.restype = i32
+        _lib.or_graph_probe.argtypes = [P, i64, i32, P, i32, P, i32, P, i32, i32, i32, i32, i32, P, P, P]
+        _lib.or_graph_heads.argtypes = [P, i32, i32, i32, P]
     return _lib
 
 
@@ -311,3 +313,32 @@ def rerank_pages(query, raw, tasks, k, page_of, batch=32, eps=0.0, beta=2, metri
                                float(eps), beta, _p(pg), _p(oi), _p(od), metric, C.byref(reads))
     return oi, od, int(nb), int(reads.value)
 
+
+
+def graph_heads(centroids, raw_dtype):
+    """The navigation graph's vertex vectors (§4.1): the centroids, rounded
+    and clipped to the data's integer grid for uint8 / int8 vectors.
+    raw_dtype: the numpy dtype of the raw vectors."""
+    c = _c(centroids, np.float32)
+    kind = {np.dtype(np.uint8): 1, np.dtype(np.int8): 2}.get(np.dtype(raw_dtype), 0)
+    h = np.empty(c.shape, dtype=np.float64)
+    lib().or_graph_heads(_p(c), c.shape[0], c.shape[1], kind, _p(h))
+    return h
+
+
+def graph_probe(queries, heads, adj, seeds, beam, max_check, nprobe, metric=L2):
+    """Step 2 by the navigation graph (§3, §4.1): the best-first walk from the
+    seeds with a beam of ``beam`` vertices and at most ``max_check`` checked
+    vertices before an expansion. Returns (lists [nq][nprobe], -1 padded;
+    lists found per query; vertices checked per query)."""
+    q = _c(queries, np.float32)
+    h = _c(heads, np.float64)
+    a = _c(adj, np.int32)
+    sd = _c(seeds, np.int32).reshape(-1)
+    nq, d = q.shape
+    out = np.empty((nq, nprobe), dtype=np.int32)
+    found = np.empty(nq, dtype=np.int32)
+    checks = np.empty(nq, dtype=np.int32)
+    lib().or_graph_probe(_p(q), nq, d, _p(h), h.shape[0], _p(a), a.shape[1], _p(sd), sd.shape[0], beam,
+                         max_check, nprobe, metric, _p(out), _p(found), _p(checks))
+    return out, found, checks

@@ -13,7 +13,8 @@
  * (steps 1-8) and is written as its plain definition in double precision:
  *
  *   coarse probe   the m = nprobe lists whose centroids are nearest to q
- *                  (step 2; exact top-m, where the paper walks a graph)
+ *                  (step 2; exact top-m), or the paper's walk over a
+ *                  navigation graph of the lists (§4.1 "In-memory Indices")
  *   gather         the ids of the probed lists (steps 3-4)
  *   dedup          the set of distinct ids, emitted sorted ascending (step 5)
  *   LUT            dist(q_i, c) for every subspace i and centroid c (step 1)
@@ -603,3 +604,116 @@ int32_t or_rerank_pages(const float *q, int32_t d, const void *raw, int32_t raw_
     return nb;
 }
 
+
+/* ---------------------------------------------------------------------------
+ * Step 2 by the navigation graph (§3 step 2, §4.1 "In-memory Indices"): the
+ * vertices are the lists, each with a vertex vector (its head), and each
+ * vertex has up to R out-edges (adj[v][0..R), -1 = none). A query walks the
+ * graph best first:
+ *   - every seed is evaluated first (a seed already seen is skipped);
+ *   - evaluating a vertex marks it seen, counts one check and offers it to
+ *     the beam, the L best (distance, id) pairs seen so far: it enters when
+ *     the beam holds fewer than L or it is below the beam's last pair;
+ *   - then, while fewer than max_check vertices were checked and the beam
+ *     holds a vertex not yet expanded, the first such vertex (in beam order)
+ *     is expanded: each of its out-neighbours not yet seen is evaluated, in
+ *     the order of its edge list;
+ *   - the top-m lists are the first min(m, beam size) pairs of the beam.
+ * Returns how many lists were written to out. Distances are squared L2 (or
+ * -<q, h> with metric IP) in FP64 against the heads.
+ * ------------------------------------------------------------------------- */
+static void beam_offer(pair_t *beam, int32_t *bn, int32_t L, double dv, int64_t v)
+{
+    pair_t x = {dv, v};
+    if (*bn == L && !pair_less(&x, &beam[L - 1])) return;
+    int32_t i = *bn < L ? *bn : L - 1;  /* slot freed at the end */
+    while (i > 0 && pair_less(&x, &beam[i - 1])) {
+        beam[i] = beam[i - 1];
+        --i;
+    }
+    beam[i] = x;
+    if (*bn < L) ++*bn;
+}
+
+static double head_dist(const float *q, const double *h, int32_t d, int32_t metric)
+{
+    double s = 0.0;
+    for (int32_t j = 0; j < d; ++j) {
+        if (metric == OR_IP) {
+            s -= (double)q[j] * h[j];
+        } else {
+            double t = (double)q[j] - h[j];
+            s += t * t;
+        }
+    }
+    return s;
+}
+
+int32_t or_graph_walk(const float *q, int32_t d, const double *heads, int32_t nlist,
+                      const int32_t *adj, int32_t R, const int32_t *seeds, int32_t S, int32_t L,
+                      int32_t max_check, int32_t nprobe, int32_t metric, int32_t *out,
+                      int32_t *checks_out)
+{
+    char *seen = (char *)calloc((size_t)nlist, 1);
+    char *expanded = (char *)calloc((size_t)nlist, 1);
+    pair_t *beam = (pair_t *)malloc(sizeof(pair_t) * (size_t)L);
+    int32_t bn = 0, checks = 0;
+    for (int32_t s = 0; s < S; ++s) {
+        int32_t v = seeds[s];
+        if (seen[v]) continue;
+        seen[v] = 1;
+        ++checks;
+        beam_offer(beam, &bn, L, head_dist(q, heads + (int64_t)v * d, d, metric), v);
+    }
+    while (checks < max_check) {
+        int32_t i = 0;
+        while (i < bn && expanded[beam[i].id]) ++i;
+        if (i == bn) break;  /* every vertex of the beam is expanded */
+        int64_t p = beam[i].id;
+        expanded[p] = 1;
+        for (int32_t e = 0; e < R; ++e) {
+            int32_t u = adj[p * R + e];
+            if (u < 0 || seen[u]) continue;
+            seen[u] = 1;
+            ++checks;
+            beam_offer(beam, &bn, L, head_dist(q, heads + (int64_t)u * d, d, metric), u);
+        }
+    }
+    int32_t m = nprobe < bn ? nprobe : bn;
+    for (int32_t i = 0; i < m; ++i) out[i] = (int32_t)beam[i].id;
+    if (checks_out) *checks_out = checks;
+    free(seen);
+    free(expanded);
+    free(beam);
+    return m;
+}
+
+void or_graph_probe(const float *queries, int64_t nq, int32_t d, const double *heads, int32_t nlist,
+                    const int32_t *adj, int32_t R, const int32_t *seeds, int32_t S, int32_t L,
+                    int32_t max_check, int32_t nprobe, int32_t metric, int32_t *out, int32_t *found,
+                    int32_t *checks)
+{
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < nq; ++i) {
+        for (int32_t j = 0; j < nprobe; ++j) out[i * nprobe + j] = -1;
+        found[i] = or_graph_walk(queries + i * d, d, heads, nlist, adj, R, seeds, S, L, max_check, nprobe,
+                                 metric, out + i * nprobe, checks ? checks + i : NULL);
+    }
+}
+
+/* The head of each list for the navigation graph: the centroid itself for
+ * float vectors; for integer vectors (uint8, int8) the centroid rounded to
+ * the nearest integer (halves to even) and clipped to the type's range, a
+ * point of the data's own grid. */
+void or_graph_heads(const float *cent, int32_t nlist, int32_t d, int32_t raw_dtype, double *heads)
+{
+    for (int64_t i = 0; i < (int64_t)nlist * d; ++i) {
+        double c = (double)cent[i];
+        if (raw_dtype == OR_RAW_U8 || raw_dtype == OR_RAW_I8) {
+            double lo = raw_dtype == OR_RAW_U8 ? 0.0 : -128.0, hi = raw_dtype == OR_RAW_U8 ? 255.0 : 127.0;
+            c = nearbyint(c);
+            c = c < lo ? lo : (c > hi ? hi : c);
+        }
+        heads[i] = c;
+    }
+}

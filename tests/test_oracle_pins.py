@@ -502,3 +502,68 @@ def test_io_dedup_counts_distinct_new_pages():
     assert nb2 == 6 and reads2 == reads
     ri, rd, _ = oracle.rerank(q, raw, tasks, 10, batch=16, eps=-1.0, beta=1)
     assert oi2.tolist() == ri.tolist() and np.array_equal(od2, rd)
+
+
+# ---------------------------------------------------------------------------
+# coarse probe by the navigation graph (§3 step 2, §4.1 "In-memory Indices")
+# ---------------------------------------------------------------------------
+
+def test_graph_walk_small_golden(golden_dir):
+    """Hand-worked walks on a line graph (the beam, the check budget, seeds
+    only, the greedy walk, ties met in either order) and on a branching
+    graph (which unexpanded vertex goes next)."""
+    g = json.load(open(os.path.join(golden_dir, "graph_walk_small.json")))
+    for gr in g["graphs"]:
+        heads = np.array(gr["positions"], np.float64)[:, None]
+        adj = np.array(gr["adj"], np.int32)
+        for c in gr["cases"]:
+            out, found, checks = oracle.graph_probe(np.array([[c["query"]]], np.float32), heads, adj,
+                                                    c["seeds"], c["beam"], c["max_check"], c["nprobe"])
+            assert out[0, :found[0]].tolist() == c["lists"], c["why"]
+            assert checks[0] == c["checks"], c["why"]
+
+
+def test_graph_walk_complete_graph_is_exact_probe():
+    """Every vertex linked to every other: the first expansion evaluates all
+    lists, so the walk returns the exact top-m (pinned above against cdist)
+    for any budget that lets the seed be expanded (the budget is checked
+    before an expansion, not inside one); a budget of one check stops at
+    the seed."""
+    rng = np.random.default_rng(61)
+    nlist, d, nq, m = 120, 8, 30, 12
+    cent = rng.integers(0, 256, size=(nlist, d)).astype(np.float32)
+    q = rng.integers(0, 256, size=(nq, d)).astype(np.float32)
+    adj = np.array([[u for u in range(nlist) if u != v] for v in range(nlist)], np.int32)
+    ref = oracle.coarse(q, cent, m)
+    for max_check in (2, 3, nlist):
+        out, found, checks = oracle.graph_probe(q, cent.astype(np.float64), adj, [5], 40, max_check, m)
+        assert np.array_equal(out, ref) and np.all(found == m)
+        assert np.all(checks == nlist)
+    out, found, checks = oracle.graph_probe(q, cent.astype(np.float64), adj, [5], 40, 1, m)
+    assert np.all(out[:, 0] == 5) and np.all(found == 1) and np.all(checks == 1)
+
+
+def test_graph_walk_stays_in_the_seeds_component():
+    """Two components: a walk seeded in one never returns a list of the
+    other, and returns fewer than m lists when its component is smaller."""
+    rng = np.random.default_rng(62)
+    d = 4
+    cent = rng.normal(size=(20, d))
+    # component A = 0..4 (a ring), component B = 5..19 (a ring)
+    adj = np.full((20, 2), -1, np.int32)
+    for lo, hi in ((0, 5), (5, 20)):
+        for v in range(lo, hi):
+            adj[v] = [lo + (v - lo - 1) % (hi - lo), lo + (v - lo + 1) % (hi - lo)]
+    q = rng.normal(size=(10, d)).astype(np.float32)
+    out, found, checks = oracle.graph_probe(q, cent, adj, [2], 16, 100, 8)
+    assert np.all(found == 5) and np.all(checks == 5)
+    assert np.all(np.sort(out[:, :5], axis=1) == np.arange(5)) and np.all(out[:, 5:] == -1)
+
+
+def test_graph_heads_rounding():
+    """Heads are the centroids; for integer vectors rounded to the nearest
+    integer (halves to even) and clipped to the type's range."""
+    c = np.array([[0.5, 1.5, 2.5, -0.4, 300.2, -128.7, 127.5, 3.49]], np.float32)
+    assert oracle.graph_heads(c, np.uint8).tolist() == [[0, 2, 2, 0, 255, 0, 128, 3]]
+    assert oracle.graph_heads(c, np.int8).tolist() == [[0, 2, 2, 0, 127, -128, 127, 3]]
+    assert oracle.graph_heads(c, np.float32).tolist() == c.astype(np.float64).tolist()
