@@ -94,7 +94,7 @@ def lib():
         _lib.or_page_layout.restype = i64
         _lib.or_rerank_pages.argtypes = [P, i32, P, i32, P, i32, i32, i32, f32, i32, P, P, P, i32, P]
         _lib.or_rerank_pages.restype = i32
-        _lib.or_graph_probe.argtypes = [P, i64, i32, P, i32, P, i32, P, i32, i32, i32, i32, i32, P, P, P]
+        _lib.or_graph_probe.argtypes = [P, i64, i32, P, i32, P, i32, P, i32, i32, i32, i32, i32, i32, P, P, P]
         _lib.or_graph_heads.argtypes = [P, i32, i32, i32, P]
     return _lib
 
@@ -329,16 +329,31 @@ def graph_heads(centroids, raw_dtype):
 def graph_probe(queries, heads, adj, seeds, beam, max_check, nprobe, metric=L2):
     """Step 2 by the navigation graph (§3, §4.1): the best-first walk from the
     seeds with a beam of ``beam`` vertices and at most ``max_check`` checked
-    vertices before an expansion. Returns (lists [nq][nprobe], -1 padded;
-    lists found per query; vertices checked per query)."""
+    vertices before an expansion. ``seeds``: one list for every query, or a
+    [nq][S] array of each query's own seeds. Returns (lists [nq][nprobe], -1
+    padded; lists found per query; vertices checked per query)."""
     q = _c(queries, np.float32)
     h = _c(heads, np.float64)
     a = _c(adj, np.int32)
-    sd = _c(seeds, np.int32).reshape(-1)
     nq, d = q.shape
+    sd = _c(seeds, np.int32)
+    if sd.ndim == 2:
+        assert sd.shape[0] == nq
+        S, stride = sd.shape[1], sd.shape[1]
+    else:
+        S, stride = sd.shape[0], 0
     out = np.empty((nq, nprobe), dtype=np.int32)
     found = np.empty(nq, dtype=np.int32)
     checks = np.empty(nq, dtype=np.int32)
-    lib().or_graph_probe(_p(q), nq, d, _p(h), h.shape[0], _p(a), a.shape[1], _p(sd), sd.shape[0], beam,
+    lib().or_graph_probe(_p(q), nq, d, _p(h), h.shape[0], _p(a), a.shape[1], _p(sd), S, stride, beam,
                          max_check, nprobe, metric, _p(out), _p(found), _p(checks))
     return out, found, checks
+
+
+def graph_entry(queries, heads, pivots, entry, metric=L2):
+    """Each query's own seeds: the ``entry`` pivot vertices nearest to it
+    (the exact top-entry probe of the pivots' heads, ties by pivot order),
+    as vertex ids [nq][entry]."""
+    pv = _c(pivots, np.int32)
+    near = coarse(queries, np.asarray(heads, np.float64)[pv].astype(np.float32), entry, metric=metric)
+    return pv[near]

@@ -688,16 +688,18 @@ int32_t or_graph_walk(const float *q, int32_t d, const double *heads, int32_t nl
     return m;
 }
 
+/* seeds_stride 0: every query starts from the same S seeds; otherwise query
+ * i starts from seeds[i * seeds_stride, + S) (its own entry vertices). */
 void or_graph_probe(const float *queries, int64_t nq, int32_t d, const double *heads, int32_t nlist,
-                    const int32_t *adj, int32_t R, const int32_t *seeds, int32_t S, int32_t L,
-                    int32_t max_check, int32_t nprobe, int32_t metric, int32_t *out, int32_t *found,
-                    int32_t *checks)
+                    const int32_t *adj, int32_t R, const int32_t *seeds, int32_t S, int32_t seeds_stride,
+                    int32_t L, int32_t max_check, int32_t nprobe, int32_t metric, int32_t *out,
+                    int32_t *found, int32_t *checks)
 {
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < nq; ++i) {
         for (int32_t j = 0; j < nprobe; ++j) out[i * nprobe + j] = -1;
-        found[i] = or_graph_walk(queries + i * d, d, heads, nlist, adj, R, seeds, S, L, max_check, nprobe,
-                                 metric, out + i * nprobe, checks ? checks + i : NULL);
+        found[i] = or_graph_walk(queries + i * d, d, heads, nlist, adj, R, seeds + i * seeds_stride, S, L,
+                                 max_check, nprobe, metric, out + i * nprobe, checks ? checks + i : NULL);
     }
 }
 

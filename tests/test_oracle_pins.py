@@ -567,3 +567,26 @@ def test_graph_heads_rounding():
     assert oracle.graph_heads(c, np.uint8).tolist() == [[0, 2, 2, 0, 255, 0, 128, 3]]
     assert oracle.graph_heads(c, np.int8).tolist() == [[0, 2, 2, 0, 127, -128, 127, 3]]
     assert oracle.graph_heads(c, np.float32).tolist() == c.astype(np.float64).tolist()
+
+
+def test_graph_walk_per_query_seeds():
+    """Each query's own seeds: the same walk as the query alone with that seed
+    list (line graph, hand-worked results), and the nearest-pivot entry is
+    numpy's argmin / argsort over the pivots' heads."""
+    rng = np.random.default_rng(63)
+    heads = np.arange(12, dtype=np.float64)[:, None]
+    adj = np.array([[v - 1 if v > 0 else -1, v + 1 if v < 11 else -1] for v in range(12)], np.int32)
+    q = np.array([[7.3], [2.2], [10.6]], np.float32)
+    seeds = np.array([[0], [11], [4]], np.int32)
+    out, found, checks = oracle.graph_probe(q, heads, adj, seeds, 3, 100, 3)
+    assert out.tolist() == [[7, 8, 6], [2, 3, 1], [11, 10, 9]]
+    for i in range(3):
+        o1, f1, c1 = oracle.graph_probe(q[i:i + 1], heads, adj, seeds[i], 3, 100, 3)
+        assert o1[0].tolist() == out[i].tolist() and c1[0] == checks[i]
+    cent = rng.normal(size=(300, 6))
+    pivots = np.arange(0, 300, 7, dtype=np.int32)
+    qq = rng.normal(size=(40, 6)).astype(np.float32)
+    e = oracle.graph_entry(qq, cent, pivots, 5)
+    d2 = ((qq[:, None, :].astype(np.float64) - cent[pivots][None]) ** 2).sum(-1)
+    assert np.array_equal(e[:, 0], pivots[np.argmin(d2, axis=1)])
+    assert np.array_equal(e, pivots[np.argsort(d2, axis=1, kind="stable")[:, :5]])
