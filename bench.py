@@ -90,7 +90,12 @@ def parse():
                          "billion-scale shape (4096-component uint8 mixture, 262144 lists, Eq. 2 "
                          "replication) at --billion-n vectors")
     ap.add_argument("--billion-n", type=int, default=250_000_000)
-    ap.add_argument("--billion-points", default="64:8192,96:8192,128:8192,192:8192,256:8192",
+    ap.add_argument("--billion-graph", default="64:4096",
+                    help="billion workload: R:S of the navigation graph of the lists (none: no graph probe)")
+    ap.add_argument("--graph-points", default="64:8192:8:64:700,64:8192:16:128:2000,32:8192:8:64:600,"
+                                              "48:8192:16:96:1200",
+                    help="billion workload: nprobe:rerank_n:entry:beam:max_check points of the graph probe")
+    ap.add_argument("--billion-points", default="32:8192,48:8192,64:8192,128:8192",
                     help="nprobe:rerank_n operating points of the billion workload")
     ap.add_argument("--repl", type=float, default=1.08,
                     help="billion workload: mean lists per vector of Eq. 2's replication")
@@ -338,25 +343,41 @@ def bench_billion(args):
     oid = torch.empty((nq, k), dtype=torch.int64, device="cuda")
     odist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    points = []
-    for pt in args.billion_points.split(","):
-        npb, n = (int(x) for x in pt.split(":"))
+    def point(npb, n, graph=None):
         wl = dict(rerank_n=n, batch=32, eps=-1.0, beta=1, lut="fp16")
         sp = search_params(fa, "lowp", wl)
+        if graph:
+            sp.probe_gemm = fa.FA_PROBE_GRAPH
+            sp.graph_entry, sp.graph_beam, sp.graph_max_check = graph
         _, _, st = fa.fa_search_ex(ix, queries[:1000], k, npb, sp, stats=True)
         ms, tr = timed_steps(fa, torch, ix, qd, k, npb, sp, max(3, min(args.steps, 5)), 3, flush, oid, odist)
         rec = recall_of(oracle, base, queries, oid.cpu().numpy(), gt)
-        points.append({"nprobe": npb, "rerank_n": n, "qps": nq / (statistics.mean(ms) / 1e3),
-                       "ms_per_step": statistics.mean(ms), "recall_at_10": rec,
-                       "gathered_per_query": float(st[:, 0].mean()),
-                       "distinct_per_query": float(st[:, 1].mean()),
-                       "stage_ms": {"coarse": statistics.mean(t.coarse_ms for t in tr),
-                                    "lut": statistics.mean(t.lut_ms for t in tr),
-                                    "scan": statistics.mean(t.scan_ms for t in tr),
-                                    "post": statistics.mean(t.post_ms for t in tr)}})
-        print(json.dumps(points[-1]), flush=True)
+        p = {"probe": "graph" if graph else "exact", "nprobe": npb, "rerank_n": n,
+             "qps": nq / (statistics.mean(ms) / 1e3), "ms_per_step": statistics.mean(ms), "recall_at_10": rec,
+             "gathered_per_query": float(st[:, 0].mean()), "distinct_per_query": float(st[:, 1].mean()),
+             "stage_ms": {"coarse": statistics.mean(t.coarse_ms for t in tr),
+                          "lut": statistics.mean(t.lut_ms for t in tr),
+                          "scan": statistics.mean(t.scan_ms for t in tr),
+                          "post": statistics.mean(t.post_ms for t in tr)}}
+        if graph:
+            p.update(entry=graph[0], beam=graph[1], max_check=graph[2])
+        print(json.dumps(p), flush=True)
+        return p
+
+    points = [point(*(int(x) for x in pt.split(":"))) for pt in args.billion_points.split(",")]
+    graph_info = None
+    if args.billion_graph != "none":
+        # the navigation-graph probe (§4.1) against the exact one, same index
+        R, S = (int(x) for x in args.billion_graph.split(":"))
+        t0 = time.perf_counter()
+        fa.fa_build_probe_graph(ix, R, S)
+        graph_info = {"R": R, "S": S, "build_s": time.perf_counter() - t0}
+        for pt in args.graph_points.split(","):
+            npb, n, e, b, mc = (int(x) for x in pt.split(":"))
+            points.append(point(npb, n, (e, b, mc)))
     ok = [p for p in points if p["recall_at_10"] is not None and p["recall_at_10"] >= 0.9]
     best = max(ok, key=lambda p: p["qps"]) if ok else max(points, key=lambda p: p["recall_at_10"] or 0)
+    exact_ok = [p for p in ok if p["probe"] == "exact"]
     peak, peak_src = measured_peaks()
     line = {
         "metric": "QPS at recall@10=0.9 on 1 B300, low-prec batched vs FP32 plain; % HBM roofline",
@@ -365,12 +386,17 @@ def bench_billion(args):
         "vs_baseline": None, "dtype": "fp16-lut/bf16-tc-gemm/f32-acc", "data": "synthetic",
         "config": {"workload": w.name, "n": w.n, "nq": nq, "d": 128, "nlist": w.nlist, "M": w.M,
                    "k": k, "nprobe": best["nprobe"], "rerank_n": best["rerank_n"],
+                   "probe": best["probe"] if best["probe"] == "exact" else
+                   "navigation graph R %d S %d, entry %d, beam %d, max_check %d"
+                   % (graph_info["R"], graph_info["S"], best["entry"], best["beam"], best["max_check"]),
                    "rerank": "Algorithm 1, BatchSize 32, eps -1, beta 1",
                    "raw_vectors": "HBM" if args.raw == "device" else "pinned host",
                    "replication": "Eq. 2, at most 8 lists, mean %.3f lists per vector"
                    % ((info.n + info.n_rep_entries) / info.n),
                    "clustering": "two-level k-means (%d iterations)" % min(args.kmeans_iters, 8)},
         "recall_at_10": best["recall_at_10"], "reaches_0_9": bool(ok),
+        "best_exact_probe_qps": max(p["qps"] for p in exact_ok) if exact_ok else None,
+        "graph": graph_info,
         "points": points,
         "replica_entries": int(info.n_rep_entries),
         "lists_per_vector": (info.n + info.n_rep_entries) / info.n,

@@ -97,6 +97,14 @@ typedef enum fa_lut_prec { FA_LUT_F32 = 0, FA_LUT_F16 = 1, FA_LUT_FP8 = 2 } fa_l
  *                     FP32 accumulation in tensor memory). */
 typedef enum fa_gemm { FA_GEMM_SIMT_F32 = 0, FA_GEMM_BF16_TC = 1 } fa_gemm;
 
+/* probe_gemm may also name the navigation graph (§3 step 2, §4.1 "In-memory
+ * Indices"): the top-nprobe lists come from a best-first walk over the
+ * index's list graph (fa_build_probe_graph) instead of the exact distances
+ * to every centroid, and the LUT (step 1) is built at the same time on a
+ * second stream, as the paper overlaps steps 1 and 2. A query whose walk
+ * finds fewer than nprobe lists scans the ones it found. */
+#define FA_PROBE_GRAPH 2
+
 /* ------------------------------------------------------------------------- */
 /* Index build (offline processing of Section 3, multi-tiered index of §4.1) */
 /* ------------------------------------------------------------------------- */
@@ -261,6 +269,12 @@ typedef struct fa_search_params {
     fa_search_trace *trace;          /* optional host trace (forces a sync) */
     int32_t *page_reads;             /* optional host [nq]: pages each query's re-rank
                                         read (raw vectors in FA_RAW_HOST_PAGED) */
+    int32_t graph_beam;              /* FA_PROBE_GRAPH: beam, nprobe..256 (0: min(256, 2 nprobe)) */
+    int32_t graph_max_check;         /* FA_PROBE_GRAPH: expansions start only while fewer
+                                        vertices were checked (0: 16 nprobe + entry) */
+    int32_t graph_entry;             /* FA_PROBE_GRAPH: the walk starts from the graph_entry
+                                        pivots nearest the query (exact probe of the pivots;
+                                        0: 16; >= S: from every pivot; else <= 64) */
 } fa_search_params;
 
 /* Fills sp with the plain FP32 form: F32 LUT built in the scan CTA, FP32 coarse
@@ -391,6 +405,33 @@ fa_status fa_debug_fail_alloc(int32_t n);
  * nothing sets, `polls` tries each. Returns FA_ERR_TIMEOUT from the device
  * status word; the CUDA context stays usable. FA_ERR_NODEV without a GPU. */
 fa_status fa_debug_timeout(uint32_t polls);
+
+/* Builds the navigation graph of the index's lists (§4.1 "In-memory
+ * Indices") for FA_PROBE_GRAPH, replacing any earlier one. Vertex v is list
+ * v with a head vector: its centroid, rounded to the nearest integer (halves
+ * to even) and clipped to the type's range for uint8 / int8 vectors. Out-edges
+ * of vertex u (squared L2 between heads, ties by id, the nearest found
+ * exactly on the GPU): its ceil(R/2) nearest other vertices; then the
+ * vertices v that have u among their own ceil(R/2) nearest, nearest first
+ * (the neighbours' update when the paper inserts a vertex); then more of
+ * u's nearest, up to R edges. S pivot
+ * vertices i * nlist / S are the walks' seeds: each walk starts from the
+ * pivots nearest its query (graph_entry). R in 1..64 (0: 48), S in
+ * 1..4096 (0: min(4096, max(64, nlist / 64))), both capped by nlist. The
+ * graph is not saved with the index. FA_ERR_ARG on bad sizes. */
+fa_status fa_build_probe_graph(fa_index *ix, int32_t R, int32_t S);
+
+/* Copies the navigation graph out: adj [nlist][R] (-1 = no edge) and seeds
+ * [S] (either may be NULL), *R and *S. FA_ERR_ARG when there is none. */
+fa_status fa_index_get_graph(fa_index *ix, int32_t *adj, int32_t *seeds, int32_t *R, int32_t *S);
+
+/* The graph walk alone for host queries [nq][d]: probes [nq][nprobe] (-1
+ * past the lists found), found [nq] lists found, checks [nq] vertices
+ * checked (either may be NULL). beam, max_check and entry as in
+ * fa_search_params (0 = their defaults). */
+fa_status fa_debug_graph_probe(fa_index *ix, const float *queries, int64_t nq, int32_t nprobe,
+                               int32_t beam, int32_t max_check, int32_t entry, int32_t *probes,
+                               int32_t *found, int32_t *checks);
 
 /* The storage layout of FA_RAW_HOST_PAGED raw vectors (§4.3): page_of[v]
  * and slot_of[v] (host [n], caller ids) receive each vector's page and its

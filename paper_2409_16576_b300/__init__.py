@@ -29,6 +29,7 @@ FA_F32, FA_U8, FA_I8 = 0, 1, 2
 FA_RAW_NONE, FA_RAW_HOST_PINNED, FA_RAW_DEVICE, FA_RAW_HOST_PAGED = 0, 1, 2, 3
 FA_LUT_F32, FA_LUT_F16, FA_LUT_FP8 = 0, 1, 2
 FA_GEMM_SIMT_F32, FA_GEMM_BF16_TC = 0, 1
+FA_PROBE_GRAPH = 2  # probe_gemm: the navigation-graph walk
 FA_METRIC_L2, FA_METRIC_IP = 0, 1
 FA_QUERIES_ON_DEVICE, FA_OUTPUTS_ON_DEVICE, FA_NONBLOCKING = 0x1, 0x2, 0x4
 FA_PERSISTENT, FA_NO_SYNC, FA_GRAPH, FA_SERIAL, FA_BATCHED = 0x8, 0x10, 0x20, 0x40, 0x80
@@ -80,7 +81,8 @@ class fa_search_params(C.Structure):
     _fields_ = [("lut_prec", i32), ("lut_gemm", i32), ("probe_gemm", i32), ("rerank_n", i32),
                 ("rerank_batch", i32), ("rerank_beta", i32), ("rerank_eps", f32), ("flags", i32),
                 ("k_per_query", P), ("nprobe_per_query", P), ("probes", P), ("stream", P),
-                ("stats", P), ("trace", P), ("page_reads", P)]
+                ("stats", P), ("trace", P), ("page_reads", P), ("graph_beam", i32),
+                ("graph_max_check", i32), ("graph_entry", i32)]
 
 
 def _sig(name, res, *args):
@@ -110,6 +112,9 @@ _sig("fa_debug_fail_alloc", i32, i32)
 _sig("fa_debug_timeout", i32, C.c_uint32)
 _sig("fa_debug_tau_sigma", i32, C.c_float)
 _sig("fa_debug_page_map", i32, P, P, P, P, P)
+_sig("fa_build_probe_graph", i32, P, i32, i32)
+_sig("fa_index_get_graph", i32, P, P, P, P, P)
+_sig("fa_debug_graph_probe", i32, P, P, i64, i32, i32, i32, i32, P, P, P)
 _sig("fa_coarse_probe_noalloc", i32, P, i64, i32, P, i32, i32, P, P)
 _sig("fa_server_params_init", None, P)
 _sig("fa_server_create", i32, P, P, P, P)
@@ -127,7 +132,8 @@ EXPORTS = ("fa_build_params_init", "fa_build_index", "fa_build_index_lists", "fa
            "fa_index_info_get", "fa_save_index", "fa_load_index", "fa_free_index",
            "fa_search_params_init", "fa_search", "fa_search_ex", "fa_autotune", "fa_debug_probes",
            "fa_debug_candidates", "fa_debug_lut", "fa_debug_fail_alloc", "fa_debug_timeout",
-           "fa_debug_tau_sigma", "fa_debug_page_map",
+           "fa_debug_tau_sigma", "fa_debug_page_map", "fa_build_probe_graph", "fa_index_get_graph",
+           "fa_debug_graph_probe",
            "fa_coarse_probe_noalloc", "fa_server_params_init",
            "fa_server_create", "fa_server_submit", "fa_server_poll", "fa_server_stats",
            "fa_server_destroy", "fa_last_error",
@@ -453,6 +459,34 @@ def fa_coarse_probe_noalloc(queries, centroids, nprobe: int, out=None, stream=No
 def fa_debug_fail_alloc(n: int) -> None:
     """The n-th next device allocation of the library fails (0 turns it off)."""
     _check(_lib.fa_debug_fail_alloc(n))
+
+
+def fa_build_probe_graph(ix: Index, R: int = 0, S: int = 0) -> None:
+    """Builds the index's navigation graph of lists (§4.1) for FA_PROBE_GRAPH."""
+    _check(_lib.fa_build_probe_graph(ix.handle, R, S))
+
+
+def fa_index_get_graph(ix: Index) -> dict:
+    """The navigation graph: adj [nlist][R] (-1 = no edge), seeds [S]."""
+    R, S = C.c_int32(0), C.c_int32(0)
+    _check(_lib.fa_index_get_graph(ix.handle, None, None, C.byref(R), C.byref(S)))
+    adj = np.empty((ix.info().nlist, R.value), dtype=np.int32)
+    seeds = np.empty(S.value, dtype=np.int32)
+    _check(_lib.fa_index_get_graph(ix.handle, _ptr(adj), _ptr(seeds), None, None))
+    return dict(adj=adj, seeds=seeds, R=R.value, S=S.value)
+
+
+def fa_debug_graph_probe(ix: Index, queries, nprobe: int, beam: int = 0, max_check: int = 0, entry: int = 0):
+    """The graph walk alone: (probes [nq][nprobe], -1 past the lists found;
+    lists found; vertices checked)."""
+    q = np.ascontiguousarray(queries, dtype=np.float32)
+    nq = q.shape[0]
+    out = np.empty((nq, nprobe), dtype=np.int32)
+    found = np.empty(nq, dtype=np.int32)
+    checks = np.empty(nq, dtype=np.int32)
+    _check(_lib.fa_debug_graph_probe(ix.handle, _ptr(q), nq, nprobe, beam, max_check, entry, _ptr(out),
+                                     _ptr(found), _ptr(checks)))
+    return out, found, checks
 
 
 def fa_debug_page_map(ix: Index) -> dict:

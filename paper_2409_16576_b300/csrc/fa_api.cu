@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -97,10 +98,114 @@ void free_device_index(fa_index *ix) {
     DeviceIndex &d = ix->dev;
     void *ptrs[] = {d.centroids, d.cnorm, d.codebooks, d.codes, d.list_beg, d.rep_off,
                     d.rep_v, d.rep_mo, d.rep_t, d.mem, d.perm, d.raw_dev_alloc,
-                    d.centroids_bf16, d.codebooks_bf16, d.cbnorm, d.lorder, d.vpage, d.vslot};
+                    d.centroids_bf16, d.codebooks_bf16, d.cbnorm, d.lorder, d.vpage, d.vslot,
+                    d.graph.heads, d.graph.adj, d.graph.seeds, d.graph.pivots};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceIndex{};
+}
+
+// Navigation graph of the lists (§4.1 "In-memory Indices"). The paper grows
+// it by inserting the centroids one at a time, each linked to its nearest
+// neighbours among those present, the neighbours re-trimming their own
+// lists; with all vertices present the graph that converges to is each
+// vertex's R nearest other vertices, computed here exactly and at once (the
+// all-pairs top-(R + 1) of the heads on the GPU, FP32 direct differences:
+// exact for integer heads). Seeds are spread over the list ids.
+static void build_probe_graph(fa_index *ix, int32_t R, int32_t S) {
+    const int32_t nlist = ix->nlist, d = ix->d;
+    const bool integer = ix->raw_dtype == FA_U8 || ix->raw_dtype == FA_I8;
+    std::vector<float> heads((size_t)nlist * d);
+    for (size_t i = 0; i < heads.size(); ++i) {
+        float c = ix->centroids[i];
+        if (integer) {
+            const float lo = ix->raw_dtype == FA_U8 ? 0.f : -128.f, hi = ix->raw_dtype == FA_U8 ? 255.f : 127.f;
+            c = std::nearbyint(c);
+            c = c < lo ? lo : (c > hi ? hi : c);
+        }
+        heads[i] = c;
+    }
+    R = std::min(R, std::max(1, nlist - 1));
+    S = std::min(S, nlist);
+    const int32_t r = std::min(R + 1, nlist);
+    std::vector<int32_t> nn((size_t)nlist * r);
+    std::vector<float> nd((size_t)nlist * r);
+    gpu_assign_topr(heads.data(), nlist, d, FA_F32, heads.data(), nlist, r, nn.data(), nd.data());
+    // forward edges: the nearest other vertices; each vertex keeps the first
+    // half, then the vertices that chose it among their first half (its
+    // neighbours "updating their nearest neighbours" as the paper inserts a
+    // vertex), nearest first, then more of its own nearest to fill R
+    const int32_t R1 = (R + 1) / 2;
+    std::vector<std::vector<std::pair<float, int32_t>>> rev(nlist);
+    std::vector<int32_t> fwd((size_t)nlist * R, -1);
+    for (int64_t v = 0; v < nlist; ++v) {
+        int e = 0;
+        for (int j = 0; j < r && e < R; ++j) {
+            const int32_t u = nn[v * r + j];
+            if (u < 0 || u == v) continue;
+            fwd[v * R + e] = u;
+            if (e < R1) rev[u].push_back({nd[v * r + j], (int32_t)v});
+            ++e;
+        }
+    }
+    std::vector<int32_t> adj((size_t)nlist * R, -1);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t u = 0; u < nlist; ++u) {
+        std::sort(rev[u].begin(), rev[u].end());
+        int32_t *row = &adj[u * R];
+        int e = 0;
+        auto add = [&](int32_t x) {
+            if (x < 0 || e >= R) return;
+            for (int i = 0; i < e; ++i)
+                if (row[i] == x) return;
+            row[e++] = x;
+        };
+        for (int j = 0; j < R1; ++j) add(fwd[u * R + j]);
+        for (const auto &pv : rev[u]) add(pv.second);
+        for (int j = R1; j < R; ++j) add(fwd[u * R + j]);
+    }
+    std::vector<int32_t> seeds(S);
+    for (int32_t i = 0; i < S; ++i) seeds[i] = (int32_t)(((int64_t)i * nlist) / S);
+    ProbeGraph &g = ix->dev.graph;
+    for (void *p : {g.heads, (void *)g.adj, (void *)g.seeds, (void *)g.pivots})
+        if (p) cudaFree(p);
+    g = ProbeGraph{};
+    int64_t bytes = 0;
+    if (integer) {
+        std::vector<uint8_t> hb(heads.size());
+        for (size_t i = 0; i < heads.size(); ++i) {
+            const int v = (int)heads[i];
+            hb[i] = ix->raw_dtype == FA_U8 ? (uint8_t)v : (uint8_t)(int8_t)v;
+        }
+        g.heads = dev_upload(hb.data(), hb.size(), bytes);
+    } else {
+        g.heads = dev_upload(heads.data(), heads.size(), bytes);
+    }
+    g.head_dtype = integer ? ix->raw_dtype : FA_F32;
+    g.adj = dev_upload(adj.data(), adj.size(), bytes);
+    g.seeds = dev_upload(seeds.data(), seeds.size(), bytes);
+    std::vector<float> piv((size_t)S * d);
+    for (int32_t i = 0; i < S; ++i)
+        std::copy(heads.begin() + (size_t)seeds[i] * d, heads.begin() + (size_t)(seeds[i] + 1) * d,
+                  piv.begin() + (size_t)i * d);
+    g.pivots = dev_upload(piv.data(), piv.size(), bytes);
+    g.R = R;
+    g.S = S;
+    ix->dev.device_bytes += bytes;
+    ix->g_adj = std::move(adj);
+    ix->g_seeds = std::move(seeds);
+}
+
+// Beam, check budget and entry pivots of a graph walk (0 = the defaults).
+static void graph_defaults(const ProbeGraph &g, int32_t nprobe, int32_t beam_in, int32_t max_in,
+                           int32_t entry_in, int32_t &beam, int32_t &max_check, int32_t &entry) {
+    FA_REQUIRE(max_in >= 0 && beam_in >= 0 && entry_in >= 0, FA_ERR_ARG, "graph beam / max_check / entry < 0");
+    beam = beam_in > 0 ? beam_in : std::min(256, 2 * nprobe);
+    entry = std::min(entry_in > 0 ? entry_in : 16, g.S);
+    max_check = max_in > 0 ? max_in : 16 * nprobe + entry;
+    FA_REQUIRE(nprobe <= 256 && beam >= nprobe && beam <= 256, FA_ERR_ARG,
+               "graph probe needs nprobe <= beam <= 256");
+    FA_REQUIRE(entry == g.S || entry <= 64, FA_ERR_ARG, "graph entry must be <= 64 or all pivots");
 }
 
 // Renumbers vectors by primary list, rotates code rows, builds the replica
@@ -332,7 +437,7 @@ static void ws_drop_graph(Workspace *w) {
 
 static void ws_free_buffers(Workspace *w) {
     ws_drop_graph(w);
-    void *dp[] = {w->q, w->probes, w->kq, w->npq, w->order, w->bucket, w->tchunks, w->tprefix,
+    void *dp[] = {w->q, w->probes, w->kq, w->npq, w->gentry, w->order, w->bucket, w->tchunks, w->tprefix,
                   w->tmisc, w->partial, w->topkeys, w->out_ids, w->out_dist,
                   w->stats, w->lut, w->lut_scale, w->coarse_d, w->err, w->tile_ctr, w->selbuf,
                   w->redo, w->bq_lcnt, w->bq_lqoff, w->bq_lcur, w->bq_upre, w->bq_lq, w->bq_pbits,
@@ -357,7 +462,7 @@ static void ws_free_buffers(Workspace *w) {
     for (void *p : hp)
         if (p) cudaFreeHost(p);
     w->q = nullptr;
-    w->probes = w->kq = w->npq = w->order = nullptr;
+    w->probes = w->kq = w->npq = w->gentry = w->order = nullptr;
     w->bucket = w->tchunks = w->tprefix = w->tmisc = nullptr;
     w->partial = nullptr;
     w->tile_cap = 0;
@@ -403,6 +508,7 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
     dalloc(w->probes, (size_t)cq * cp);
     dalloc(w->kq, (size_t)cq);
     dalloc(w->npq, (size_t)cq);
+    dalloc(w->gentry, (size_t)cq * 64);
     dalloc(w->order, (size_t)cq);
     dalloc(w->bucket, (size_t)D.nlist);
     dalloc(w->tchunks, (size_t)cq);
@@ -624,6 +730,14 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     nprobe = std::max(1, std::min(nprobe, ix->nlist));
     FA_REQUIRE(nprobe <= 512, FA_ERR_ARG, "nprobe above 512");
     FA_REQUIRE(sp.lut_prec >= FA_LUT_F32 && sp.lut_prec <= FA_LUT_FP8, FA_ERR_ARG, "bad lut_prec");
+    FA_REQUIRE(sp.probe_gemm >= FA_GEMM_SIMT_F32 && sp.probe_gemm <= FA_PROBE_GRAPH, FA_ERR_ARG, "bad probe_gemm");
+    const bool gprobe = sp.probe_gemm == FA_PROBE_GRAPH && !sp.probes;
+    int32_t gbeam = 0, gmax = 0, gentry = 0;
+    if (gprobe) {
+        FA_REQUIRE(ix->dev.graph.adj != nullptr, FA_ERR_ARG, "FA_PROBE_GRAPH needs fa_build_probe_graph");
+        graph_defaults(ix->dev.graph, nprobe, sp.graph_beam, sp.graph_max_check, sp.graph_entry, gbeam, gmax,
+                       gentry);
+    }
     const bool rerank = sp.rerank_n > 0;
     int32_t ntop = k;
     if (rerank) {
@@ -703,12 +817,29 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             if (qdev) probes = sp.probes;
             else FA_CHECK_CUDA(cudaMemcpyAsync(w->probes, sp.probes, sizeof(int32_t) * nq * nprobe,
                                                cudaMemcpyHostToDevice, st));
+        } else if (gprobe) {
+            // steps 1 and 2 at the same time (§3): the table on a second
+            // stream while the walk runs on the call's stream
+            if (global_lut) {
+                FA_CHECK_CUDA(cudaEventRecord(w->fork[0], st));
+                FA_CHECK_CUDA(cudaStreamWaitEvent(w->stream2, w->fork[0], 0));
+                launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err,
+                                  w->stream2, batched ? 1 : 0);
+                FA_CHECK_CUDA(cudaEventRecord(w->join, w->stream2));
+                tr.launches += 1;
+            }
+            launch_graph_probe(D, qd, nq, nprobe, nprobe, gbeam, gmax, gentry, npq, w->probes, w->npq, nullptr,
+                               w->coarse_d, w->coarse_rows, w->gentry, st);
+            npq = w->npq;
+            tr.launches += gentry < D.graph.S ? 3 : 1;
         } else {
             launch_coarse(D, qd, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, st);
             tr.launches += coarse_launches(D, nq, sp.probe_gemm, *w);
         }
         tr.mark(1);
-        if (global_lut) {
+        if (global_lut && gprobe) {
+            FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->join, 0));
+        } else if (global_lut) {
             launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st,
                               batched ? 1 : 0);
             tr.launches += 1;
@@ -890,6 +1021,9 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
         key.lut_prec = sp.lut_prec;
         key.lut_gemm = sp.lut_gemm;
         key.probe_gemm = sp.probe_gemm;
+        key.graph_beam = gbeam;
+        key.graph_max_check = gmax;
+        key.graph_entry = gentry;
         key.rerank_n = sp.rerank_n;
         key.rerank_batch = sp.rerank_batch;
         key.rerank_beta = sp.rerank_beta;
@@ -1500,7 +1634,15 @@ fa_status fa_debug_probes(fa_index *ix, const float *queries, int64_t nq, int32_
         Workspace *w = lease.w;
         ws_ensure(ix, w, nq, 1, nprobe, 1, 0);
         FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * ix->d, cudaMemcpyHostToDevice, w->stream));
-        launch_coarse(ix->dev, w->q, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, w->stream);
+        if (sp.probe_gemm == FA_PROBE_GRAPH) {
+            FA_REQUIRE(ix->dev.graph.adj != nullptr, FA_ERR_ARG, "FA_PROBE_GRAPH needs fa_build_probe_graph");
+            int32_t gb = 0, gm = 0, ge = 0;
+            graph_defaults(ix->dev.graph, nprobe, sp.graph_beam, sp.graph_max_check, sp.graph_entry, gb, gm, ge);
+            launch_graph_probe(ix->dev, w->q, nq, nprobe, nprobe, gb, gm, ge, nullptr, w->probes, w->npq, nullptr,
+                               w->coarse_d, w->coarse_rows, w->gentry, w->stream);
+        } else {
+            launch_coarse(ix->dev, w->q, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, w->stream);
+        }
         FA_CHECK_CUDA(cudaMemcpyAsync(out_probes, w->probes, sizeof(int32_t) * nq * nprobe,
                                       cudaMemcpyDeviceToHost, w->stream));
         FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
@@ -1553,6 +1695,67 @@ fa_status fa_debug_candidates(fa_index *ix, const float *query, int32_t nprobe,
         *out_n = (int64_t)ids.size();
         FA_REQUIRE((int64_t)ids.size() <= cap, FA_ERR_OVERFLOW, "output capacity too small");
         std::copy(ids.begin(), ids.end(), out_ids);
+    });
+}
+
+fa_status fa_build_probe_graph(fa_index *ix, int32_t R, int32_t S) {
+    if (!ix) {
+        set_error("null index");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] {
+        if (R == 0) R = 48;
+        if (S == 0) S = std::min(4096, std::max(64, ix->nlist / 64));
+        FA_REQUIRE(R >= 1 && R <= 64, FA_ERR_ARG, "graph degree R must be in 1..64");
+        FA_REQUIRE(S >= 1 && S <= 4096, FA_ERR_ARG, "graph seeds S must be in 1..4096");
+        FA_CHECK_CUDA(cudaSetDevice(ix->device));
+        build_probe_graph(ix, R, S);
+    });
+}
+
+fa_status fa_index_get_graph(fa_index *ix, int32_t *adj, int32_t *seeds, int32_t *R, int32_t *S) {
+    if (!ix) {
+        set_error("null index");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] {
+        FA_REQUIRE(ix->dev.graph.adj != nullptr, FA_ERR_ARG, "the index has no navigation graph");
+        if (adj) memcpy(adj, ix->g_adj.data(), sizeof(int32_t) * ix->g_adj.size());
+        if (seeds) memcpy(seeds, ix->g_seeds.data(), sizeof(int32_t) * ix->g_seeds.size());
+        if (R) *R = ix->dev.graph.R;
+        if (S) *S = ix->dev.graph.S;
+    });
+}
+
+fa_status fa_debug_graph_probe(fa_index *ix, const float *queries, int64_t nq, int32_t nprobe,
+                               int32_t beam, int32_t max_check, int32_t entry, int32_t *probes,
+                               int32_t *found, int32_t *checks) {
+    if (!ix) {
+        set_error("null index");
+        return FA_ERR_ARG;
+    }
+    return guarded(ix, [&] {
+        FA_REQUIRE(nq >= 0 && queries && probes, FA_ERR_ARG, "bad arguments");
+        FA_REQUIRE(nprobe >= 1 && nprobe <= std::min(ix->nlist, 256), FA_ERR_ARG,
+                   "nprobe must be in 1..min(nlist, 256)");
+        FA_REQUIRE(ix->dev.graph.adj != nullptr, FA_ERR_ARG, "FA_PROBE_GRAPH needs fa_build_probe_graph");
+        if (nq == 0) return;
+        int32_t gb = 0, gm = 0, ge = 0;
+        graph_defaults(ix->dev.graph, nprobe, beam, max_check, entry, gb, gm, ge);
+        FA_CHECK_CUDA(cudaSetDevice(ix->device));
+        WsLease lease(ix, false);
+        Workspace *w = lease.w;
+        ws_ensure(ix, w, nq, 1, nprobe, 1, 0);
+        FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * ix->d, cudaMemcpyHostToDevice, w->stream));
+        launch_graph_probe(ix->dev, w->q, nq, nprobe, nprobe, gb, gm, ge, nullptr, w->probes, w->npq, w->kq,
+                           w->coarse_d, w->coarse_rows, w->gentry, w->stream);
+        FA_CHECK_CUDA(cudaMemcpyAsync(probes, w->probes, sizeof(int32_t) * nq * nprobe, cudaMemcpyDeviceToHost,
+                                      w->stream));
+        if (found)
+            FA_CHECK_CUDA(cudaMemcpyAsync(found, w->npq, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, w->stream));
+        if (checks)
+            FA_CHECK_CUDA(cudaMemcpyAsync(checks, w->kq, sizeof(int32_t) * nq, cudaMemcpyDeviceToHost, w->stream));
+        FA_CHECK_CUDA(cudaStreamSynchronize(w->stream));
     });
 }
 

@@ -64,6 +64,16 @@ inline int lut_row_words(int M) {
 // -------------------------------------------------------------------------
 // device index
 // -------------------------------------------------------------------------
+// Navigation graph of the lists (§4.1 "In-memory Indices"), device copies.
+struct ProbeGraph {
+    void *heads = nullptr;     // [nlist][d] head vectors (uint8 / int8 / float)
+    int32_t head_dtype = FA_F32;
+    int32_t *adj = nullptr;    // [nlist][R] out-edges, -1 = none
+    int32_t *seeds = nullptr;  // [S] pivot vertices
+    float *pivots = nullptr;   // [S][d] their heads as floats (the entry probe's operand)
+    int32_t R = 0, S = 0;
+};
+
 struct DeviceIndex {
     int64_t n = 0;
     int32_t d = 0, nlist = 0, M = 0, dsub = 0;
@@ -104,6 +114,7 @@ struct DeviceIndex {
     uint16_t *vslot = nullptr;      // [n]
     int32_t page_rows = 0, page_bytes = 0;  // rows a page, bytes a page (rows x row bytes)
     int64_t n_pages = 0;
+    ProbeGraph graph;
     int64_t device_bytes = 0;
     int64_t pinned_bytes = 0;
 };
@@ -114,6 +125,7 @@ struct GraphKey {
     cudaStream_t st;
     int64_t nq;
     int32_t k, nprobe, lut_prec, lut_gemm, probe_gemm, rerank_n, rerank_batch, rerank_beta;
+    int32_t graph_beam, graph_max_check, graph_entry;
     float rerank_eps;
     int32_t flags, threads, ilp, persistent, tile_chunks;
 };
@@ -139,6 +151,7 @@ struct Workspace {
     int32_t *probes = nullptr;     // [cap_nq][cap_nprobe]
     int32_t *kq = nullptr;         // [cap_nq]
     int32_t *npq = nullptr;        // [cap_nq]
+    int32_t *gentry = nullptr;     // [cap_nq][64] graph walk entry pivots
     int32_t *order = nullptr;      // [cap_nq] scan order
     uint32_t *tchunks = nullptr;   // [cap_nq] chunks per query (tiled form)
     uint32_t *tprefix = nullptr;   // [cap_nq + 1] tiles per query prefix
@@ -213,6 +226,7 @@ struct fa_index {
     void *h_pages = nullptr;      // HOST_PAGED: pinned, mapped pages of rows (§4.3 layout)
     std::vector<int64_t> page_of; // HOST_PAGED: page of each vector (caller ids)
     std::vector<int32_t> slot_of; // HOST_PAGED: row of each vector in its page
+    std::vector<int32_t> g_adj, g_seeds;  // navigation graph (host copies), R and S in dev.graph
     int device = 0;
     fa::DeviceIndex dev;
     // workspace pool
@@ -370,6 +384,20 @@ void launch_rerank_paged(const DeviceIndex &ix, const float *q, const uint64_t *
                          int32_t ntop, int32_t k, const int32_t *kq, int32_t batch, int32_t beta,
                          float eps, int64_t *out_ids, float *out_dist, int32_t *stats,
                          const PagedBufs &pb, uint32_t *ctr, cudaStream_t st);
+// Coarse probe by the navigation graph: probes [nq][probe_stride], lists
+// found per query in npq_out (npq_in: optional per-query target).
+// entry < S: each walk starts from the entry pivots nearest its query (an
+// exact probe of the pivots in scratch, then entry_buf [nq][entry]); entry
+// == S: from every pivot.
+void launch_graph_probe(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
+                        int32_t probe_stride, int32_t beam, int32_t max_check, int32_t entry,
+                        const int32_t *npq_in, int32_t *probes, int32_t *npq_out, int32_t *checks,
+                        float *scratch, int64_t scratch_rows, int32_t *entry_buf, cudaStream_t st);
+// rows x centroids -> top-ntop columns per row (FP32 direct differences, or -<x, c>)
+void launch_l2_topn(const float *X, int64_t nx, int32_t d, const float *C, int32_t nc, int32_t ntop,
+                    float *scratch, int64_t scratch_rows, int32_t *out_ids, int32_t out_stride,
+                    cudaStream_t st, int ip);
+int graph_table_bits(int32_t max_check, int32_t R, int32_t S);
 // Storage layout of §4.3 for vectors of the given primary lists.
 int64_t page_layout(const std::vector<int32_t> &primary, int32_t nlist, int32_t cap,
                     std::vector<int64_t> &page_of, std::vector<int32_t> &slot_of);

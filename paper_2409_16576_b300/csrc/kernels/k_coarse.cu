@@ -144,6 +144,12 @@ static void l2_topn(const float *X, int64_t nx, int32_t d, const float *C, int32
     }
 }
 
+void launch_l2_topn(const float *X, int64_t nx, int32_t d, const float *C, int32_t nc, int32_t ntop,
+                    float *scratch, int64_t scratch_rows, int32_t *out_ids, int32_t out_stride,
+                    cudaStream_t st, int ip) {
+    l2_topn(X, nx, d, C, nc, ntop, scratch, scratch_rows, out_ids, out_stride, nullptr, st, ip);
+}
+
 void launch_coarse(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
                    int32_t probe_stride, int gemm, Workspace &ws, int32_t *probes,
                    cudaStream_t st) {

@@ -42,9 +42,10 @@ def test_struct_layouts_match_header():
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(fa_build_params), sizeof(fa_index_parts),
          sizeof(fa_search_params), sizeof(fa_index_info));
-  printf("%zu %zu %zu %zu %zu %zu\n", offsetof(fa_search_params, stats), offsetof(fa_index_parts, raw),
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", offsetof(fa_search_params, stats), offsetof(fa_index_parts, raw),
          offsetof(fa_build_params, use_gpu), offsetof(fa_build_params, metric),
-         offsetof(fa_index_parts, metric), offsetof(fa_search_params, page_reads));
+         offsetof(fa_index_parts, metric), offsetof(fa_search_params, page_reads),
+         offsetof(fa_search_params, graph_max_check));
   return 0; }
 '''
     with tempfile.TemporaryDirectory() as t:
@@ -59,7 +60,8 @@ int main(void) {
                      C.sizeof(fa.fa_search_params), C.sizeof(fa.fa_index_info)]
     assert offs == [fa.fa_search_params.stats.offset, fa.fa_index_parts.raw.offset,
                     fa.fa_build_params.use_gpu.offset, fa.fa_build_params.metric.offset,
-                    fa.fa_index_parts.metric.offset, fa.fa_search_params.page_reads.offset]
+                    fa.fa_index_parts.metric.offset, fa.fa_search_params.page_reads.offset,
+                    fa.fa_search_params.graph_max_check.offset]
 
 
 def test_status_strings_and_version():
