@@ -90,10 +90,10 @@ def parse():
                          "billion-scale shape (4096-component uint8 mixture, 262144 lists, Eq. 2 "
                          "replication) at --billion-n vectors")
     ap.add_argument("--billion-n", type=int, default=250_000_000)
-    ap.add_argument("--billion-graph", default="64:4096",
+    ap.add_argument("--billion-graph", default="32:4096",
                     help="billion workload: R:S of the navigation graph of the lists (none: no graph probe)")
-    ap.add_argument("--graph-points", default="64:8192:8:64:700,64:8192:16:128:2000,32:8192:8:64:600,"
-                                              "48:8192:16:96:1200",
+    ap.add_argument("--graph-points", default="32:8192:8:64:600,48:8192:8:64:700,64:8192:8:64:700,"
+                                              "64:8192:16:128:2000",
                     help="billion workload: nprobe:rerank_n:entry:beam:max_check points of the graph probe")
     ap.add_argument("--billion-points", default="32:8192,48:8192,64:8192,128:8192",
                     help="nprobe:rerank_n operating points of the billion workload")

@@ -410,13 +410,15 @@ fa_status fa_debug_timeout(uint32_t polls);
  * Indices") for FA_PROBE_GRAPH, replacing any earlier one. Vertex v is list
  * v with a head vector: its centroid, rounded to the nearest integer (halves
  * to even) and clipped to the type's range for uint8 / int8 vectors. Out-edges
- * of vertex u (squared L2 between heads, ties by id, the nearest found
- * exactly on the GPU): its ceil(R/2) nearest other vertices; then the
- * vertices v that have u among their own ceil(R/2) nearest, nearest first
- * (the neighbours' update when the paper inserts a vertex); then more of
- * u's nearest, up to R edges. S pivot
+ * of vertex u (squared L2 between heads, ties by id; its K = 3R nearest
+ * other vertices found exactly on the GPU are the candidates): the
+ * candidates kept by relative-neighbourhood pruning (in distance order, one
+ * is dropped when an already kept one is strictly closer to it than u is;
+ * SPTAG prunes its graph this way); then the vertices that kept u, nearest
+ * first (the neighbours' update when the paper inserts a vertex); then
+ * u's nearest candidates, up to R edges. S pivot
  * vertices i * nlist / S are the walks' seeds: each walk starts from the
- * pivots nearest its query (graph_entry). R in 1..64 (0: 48), S in
+ * pivots nearest its query (graph_entry). R in 1..64 (0: 32), S in
  * 1..4096 (0: min(4096, max(64, nlist / 64))), both capped by nlist. The
  * graph is not saved with the index. FA_ERR_ARG on bad sizes. */
 fa_status fa_build_probe_graph(fa_index *ix, int32_t R, int32_t S);

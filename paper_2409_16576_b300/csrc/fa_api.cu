@@ -127,42 +127,61 @@ static void build_probe_graph(fa_index *ix, int32_t R, int32_t S) {
     }
     R = std::min(R, std::max(1, nlist - 1));
     S = std::min(S, nlist);
-    const int32_t r = std::min(R + 1, nlist);
+    // candidates: the K nearest other heads of every vertex, exactly on the GPU
+    const int32_t K = std::min(nlist - 1, 3 * R);
+    const int32_t r = std::min(K + 1, nlist);
     std::vector<int32_t> nn((size_t)nlist * r);
-    std::vector<float> nd((size_t)nlist * r);
-    gpu_assign_topr(heads.data(), nlist, d, FA_F32, heads.data(), nlist, r, nn.data(), nd.data());
-    // forward edges: the nearest other vertices; each vertex keeps the first
-    // half, then the vertices that chose it among their first half (its
-    // neighbours "updating their nearest neighbours" as the paper inserts a
-    // vertex), nearest first, then more of its own nearest to fill R
-    const int32_t R1 = (R + 1) / 2;
-    std::vector<std::vector<std::pair<float, int32_t>>> rev(nlist);
-    std::vector<int32_t> fwd((size_t)nlist * R, -1);
-    for (int64_t v = 0; v < nlist; ++v) {
-        int e = 0;
-        for (int j = 0; j < r && e < R; ++j) {
-            const int32_t u = nn[v * r + j];
-            if (u < 0 || u == v) continue;
-            fwd[v * R + e] = u;
-            if (e < R1) rev[u].push_back({nd[v * r + j], (int32_t)v});
-            ++e;
+    gpu_assign_topr(heads.data(), nlist, d, FA_F32, heads.data(), nlist, r, nn.data(), nullptr);
+    auto hd = [&](int64_t a, int64_t b) {  // squared L2 between heads (exact for integer heads)
+        double s = 0.0;
+        const float *x = &heads[a * d], *y = &heads[b * d];
+        for (int j = 0; j < d; ++j) {
+            const double t = (double)x[j] - (double)y[j];
+            s += t * t;
+        }
+        return s;
+    };
+    // 1. relative-neighbourhood pruning (as SPTAG's graph does): a candidate
+    //    is kept unless an already kept neighbour is closer to it than the
+    //    vertex is; so the kept edges point in different directions
+    std::vector<std::vector<int32_t>> first(nlist);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t p = 0; p < nlist; ++p) {
+        for (int j = 0; j < r && (int)first[p].size() < R; ++j) {
+            const int32_t c = nn[p * r + j];
+            if (c < 0 || c == p) continue;
+            const double dpc = hd(p, c);
+            bool keep = true;
+            for (int32_t n : first[p])
+                if (hd(n, c) < dpc) {
+                    keep = false;
+                    break;
+                }
+            if (keep) first[p].push_back(c);
         }
     }
+    // 2. reverse edges: the vertices that kept u, nearest first (the paper's
+    //    neighbours updating their lists when a vertex is inserted)
+    std::vector<std::vector<std::pair<double, int32_t>>> rev(nlist);
+    for (int64_t v = 0; v < nlist; ++v)
+        for (int32_t u : first[v]) rev[u].push_back({0.0, (int32_t)v});
+    // 3. out-edges: kept, then reverse, then the nearest candidates, up to R
     std::vector<int32_t> adj((size_t)nlist * R, -1);
 #pragma omp parallel for schedule(dynamic, 256)
     for (int64_t u = 0; u < nlist; ++u) {
+        for (auto &pv : rev[u]) pv.first = hd(u, pv.second);
         std::sort(rev[u].begin(), rev[u].end());
         int32_t *row = &adj[u * R];
         int e = 0;
         auto add = [&](int32_t x) {
-            if (x < 0 || e >= R) return;
+            if (x < 0 || x == u || e >= R) return;
             for (int i = 0; i < e; ++i)
                 if (row[i] == x) return;
             row[e++] = x;
         };
-        for (int j = 0; j < R1; ++j) add(fwd[u * R + j]);
+        for (int32_t x : first[u]) add(x);
         for (const auto &pv : rev[u]) add(pv.second);
-        for (int j = R1; j < R; ++j) add(fwd[u * R + j]);
+        for (int j = 0; j < r && e < R; ++j) add(nn[u * r + j]);
     }
     std::vector<int32_t> seeds(S);
     for (int32_t i = 0; i < S; ++i) seeds[i] = (int32_t)(((int64_t)i * nlist) / S);
@@ -1704,7 +1723,7 @@ fa_status fa_build_probe_graph(fa_index *ix, int32_t R, int32_t S) {
         return FA_ERR_ARG;
     }
     return guarded(ix, [&] {
-        if (R == 0) R = 48;
+        if (R == 0) R = 32;
         if (S == 0) S = std::min(4096, std::max(64, ix->nlist / 64));
         FA_REQUIRE(R >= 1 && R <= 64, FA_ERR_ARG, "graph degree R must be in 1..64");
         FA_REQUIRE(S >= 1 && S <= 4096, FA_ERR_ARG, "graph seeds S must be in 1..4096");

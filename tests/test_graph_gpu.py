@@ -72,25 +72,37 @@ def _i8(fa, metric):
 
 def test_graph_edges_follow_the_build_rule(fa):
     """Out-edges of every vertex by the build's rule, from the oracle's exact
-    nearest heads (distance, id): the first half of its own nearest, then
-    the vertices that chose it among theirs (nearest first), then more of its
-    own nearest."""
+    K = 3R nearest heads (distance, id) and FP64 distances between heads:
+    relative-neighbourhood pruning, then the vertices that kept it (nearest
+    first), then its nearest candidates."""
     s = _u8(fa)
     g, heads = s["g"], s["heads"]
     R = g["R"]
     assert R == 24 and g["S"] == 40
     h32 = heads.astype(np.float32)
-    nn, d2 = oracle.coarse(h32, h32, R + 1, with_d2=True)
-    nlist, R1 = heads.shape[0], (R + 1) // 2
-    fwd = [[(float(d2[v, j]), int(u)) for j, u in enumerate(nn[v]) if u != v][:R] for v in range(nlist)]
+    nlist, K = heads.shape[0], 3 * R
+    nn = oracle.coarse(h32, h32, K + 1)
+
+    def hd(a, b):
+        return float(((heads[a] - heads[b]) ** 2).sum())
+    first = []
+    for p in range(nlist):
+        kept = []
+        for c in nn[p].tolist():
+            if c == p or len(kept) >= R:
+                continue
+            dpc = hd(p, c)
+            if all(hd(n, c) >= dpc for n in kept):
+                kept.append(c)
+        first.append(kept)
     rev = [[] for _ in range(nlist)]
     for v in range(nlist):
-        for dv, u in fwd[v][:R1]:
-            rev[u].append((dv, v))
+        for u in first[v]:
+            rev[u].append((hd(u, v), v))
     for u in range(nlist):
         want = []
-        for x in [w for _, w in fwd[u][:R1]] + [w for _, w in sorted(rev[u])] + [w for _, w in fwd[u][R1:]]:
-            if x not in want and len(want) < R:
+        for x in first[u] + [w for _, w in sorted(rev[u])] + nn[u].tolist():
+            if x != u and x not in want and len(want) < R:
                 want.append(x)
         assert g["adj"][u].tolist() == want + [-1] * (R - len(want)), u
     nlist = heads.shape[0]
