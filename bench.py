@@ -104,6 +104,8 @@ def parse():
                     help="batching form: re-rank the ADC top-n exhaustively on raw rows in HBM (0 = off)")
     ap.add_argument("--batching-n", type=int, default=100_000_000,
                     help="base size of the batching form's workload in the default line")
+    ap.add_argument("--no-tiers", action="store_true",
+                    help="skip the re-rank from pinned host rows and from §4.3 pages")
     ap.add_argument("--no-serve", action="store_true",
                     help="skip the serving form (request loop under Poisson load) on the batching index")
     ap.add_argument("--zipf-form", default="batched", choices=["tiled", "batched"],
@@ -696,6 +698,11 @@ def main():
                               "post": statistics.mean(t.post_ms for t in ptr)},
                  "what": "FP32 SIMT coarse probe, FP32 LUT built in the scan CTA, same re-rank"}
 
+    # ---- the re-rank from the slow tier (the SSD stand-in) ----
+    tiers = None
+    if rank == 0 and world == 1 and lowp and wl["rerank_n"] > 0 and args.raw == "device" and not args.no_tiers:
+        tiers = raw_tiers(fa, torch, oracle, parts, base, queries, gt, wl, sp, flush, args)
+
     # ---- CPU baseline: the oracle as it stands on a bounded sample ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -756,6 +763,7 @@ def main():
             "plain_fp32": plain,
             "lowp_over_plain": (value / plain["value"]) if plain else None,
             "batching_form": batching,
+            "raw_tiers": tiers,
             "roofline": {"bound": "hbm", "kernel": scan_kernel, "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s", "frac": achieved / peak,
                          "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
@@ -781,6 +789,59 @@ def main():
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def raw_tiers(fa, torch, oracle, parts, base, queries, gt, wl, sp, flush, args):
+    """The same search with the raw vectors in the slow tier instead of HBM:
+    rows in pinned host memory read over the host link in exact row pieces
+    (the batch's re-ranks pipelined with its scans), and rows in §4.3's 4 KB
+    pages (whole pages read, each page once per query: the paged re-rank) on
+    a 1k-query sample, also at the configured point (top-100, eps 0, beta 2)."""
+    k, nq, d = wl["k"], wl["nq"], 128
+    out = {}
+    pr = parts
+    ixh = fa.fa_index_from_parts(pr["centroids"], pr["codebooks"], pr["codes"], pr["primary"], pr["rep_off"],
+                                 pr["rep_ids"], raw=pr["raw"], raw_location=fa.FA_RAW_HOST_PINNED)
+    qd = torch.as_tensor(queries, device="cuda")
+    oid = torch.empty((nq, k), dtype=torch.int64, device="cuda")
+    odist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    ms, tr = timed_steps(fa, torch, ixh, qd, k, wl["nprobe"], sp, 3, 3, flush, oid, odist)
+    _, _, st = fa.fa_search_ex(ixh, queries[:1000], k, wl["nprobe"], sp, stats=True)
+    rows = float(st[:, 3].mean())
+    t = statistics.mean(ms) / 1e3
+    out["pinned_rows"] = {"qps": nq / t, "ms_per_step": t * 1e3,
+                          "recall_at_10": recall_of(oracle, base, queries, oid.cpu().numpy(), gt),
+                          "rows_per_query": rows, "link_gbs": nq * rows * d / t / 1e9,
+                          "what": "raw rows in pinned host memory, read in 16-byte pieces over the host link; "
+                                  "re-ranks of 8 query chunks pipelined with their scans"}
+    del ixh
+    ixp = fa.fa_index_from_parts(pr["centroids"], pr["codebooks"], pr["codes"], pr["primary"], pr["rep_off"],
+                                 pr["rep_ids"], raw=pr["raw"], raw_location=fa.FA_RAW_HOST_PAGED)
+    pm = fa.fa_debug_page_map(ixp)
+    page_bytes = pm["rows_per_page"] * d
+    ns = 1000
+    for name, npb, spp in (("paged", wl["nprobe"], sp),
+                           ("paged_configured_point", 64,
+                            search_params(fa, "lowp", dict(rerank_n=100, batch=32, eps=0.0, beta=2)))):
+        qs = torch.as_tensor(queries[:ns], device="cuda")
+        o1 = torch.empty((ns, k), dtype=torch.int64, device="cuda")
+        o2 = torch.empty((ns, k), dtype=torch.float32, device="cuda")
+        ms, _ = timed_steps(fa, torch, ixp, qs, k, npb, spp, 2, 3, flush, o1, o2)
+        reads = np.zeros(ns, np.int32)
+        _, _, st = fa.fa_search_ex(ixp, queries[:ns], k, npb, spp, stats=True, page_reads=reads)
+        t = statistics.mean(ms) / 1e3
+        rec = recall_of(oracle, base, queries[:ns], o1.cpu().numpy(), gt) if gt is not None else None
+        out[name] = {"qps": ns / t, "ms_per_step": t * 1e3, "queries_per_step": ns, "nprobe": npb,
+                     "rerank_n": spp.rerank_n, "recall_at_10": rec,
+                     "rows_reranked_per_query": float(st[:, 3].mean()) if spp.rerank_eps < 0 else None,
+                     "minibatches_per_query": float(st[:, 2].mean()),
+                     "pages_read_per_query": float(reads.mean()), "page_bytes": page_bytes,
+                     "link_gbs": ns * float(reads.mean()) * page_bytes / t / 1e9,
+                     "what": "raw rows in 4 KB pages (per-list buckets, max-min tail packing, §4.3); "
+                             "whole pages read, each page once per query (intra- and inter-mini-batch "
+                             "deduplication)"}
+    del ixp
+    return out
 
 
 def zipf_form_name(args):

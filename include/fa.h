@@ -246,6 +246,8 @@ void fa_free_index(fa_index *ix);
 typedef struct fa_search_trace {
     float coarse_ms, lut_ms, scan_ms, post_ms, total_ms;
     int32_t launches;
+    int32_t handed_back;  /* queries the selecting or batched scan handed back to
+                             the per-query scan (0 on the other paths) */
 } fa_search_trace;
 
 typedef struct fa_search_params {

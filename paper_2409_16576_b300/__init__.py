@@ -59,7 +59,7 @@ class fa_index_info(C.Structure):
 
 class fa_search_trace(C.Structure):
     _fields_ = [("coarse_ms", f32), ("lut_ms", f32), ("scan_ms", f32), ("post_ms", f32),
-                ("total_ms", f32), ("launches", i32)]
+                ("total_ms", f32), ("launches", i32), ("handed_back", i32)]
 
 
 class fa_tune_result(C.Structure):

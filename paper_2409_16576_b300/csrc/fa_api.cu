@@ -564,8 +564,10 @@ static void ws_ensure(fa_index *ix, Workspace *w, int64_t nq, int32_t k, int32_t
 }
 
 // Buffers of the batched form: (query, list) pairs by list, per-query
-// thresholds and key buffers of cap keys (twice the top-n, at least 16384).
-static uint32_t bq_key_cap(int32_t ntop) { return (uint32_t)std::max(2 * ntop, 16384); }
+// thresholds and key buffers of cap keys (four times the top-n, at least
+// 65536: 512 KB a query, so a threshold sampled from a query of millions of
+// candidates does not overflow its buffer).
+static uint32_t bq_key_cap(int32_t ntop) { return (uint32_t)std::max(4 * ntop, 65536); }
 
 static void ws_ensure_batched(fa_index *ix, Workspace *w, int64_t nq, int32_t nprobe, int32_t ntop) {
     const DeviceIndex &D = ix->dev;
@@ -811,6 +813,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
 
     auto enqueue = [&]() {
         FA_CHECK_CUDA(cudaMemsetAsync(w->err, 0, 4, st));
+        FA_CHECK_CUDA(cudaMemsetAsync(w->tile_ctr + 3, 0, 4, st));  // queries handed back
         const float *qd = queries;
         if (!qdev) {
             FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * d, cudaMemcpyHostToDevice, st));
@@ -1103,6 +1106,11 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
     if (sp.stats)
         for (int64_t i = 0; i < nq * 4; ++i) sp.stats[i] = w->h_stats[i];
     tr.finish();
+    if (sp.trace) {
+        uint32_t hb = 0;
+        FA_CHECK_CUDA(cudaMemcpy(&hb, w->tile_ctr + 3, 4, cudaMemcpyDeviceToHost));
+        sp.trace->handed_back = (int32_t)hb;
+    }
 }
 
 static void check_parts(const fa_index_parts *p) {

@@ -1380,67 +1380,13 @@ __global__ void __launch_bounds__(1024) k_bq_plan(const BatchArgs b) {
         b.upre, nullptr, ws);
 }
 
-// Per-query threshold estimate from a strided sample of the query's
-// candidates (as in the selecting scan), and the per-query constants of the
-// table: s_q and the sum of the offsets. A threshold of 0 marks a query the
-// list scan cannot serve (no useful sample); +inf keeps every candidate.
-template <int M, int W>
-__global__ void __launch_bounds__(SEL_THREADS, 2) k_bq_tau(const ScanArgs a, uint64_t *tau,
-                                                           uint32_t *cnt, float *qsum, uint32_t cap,
-                                                           int sch_max) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, sch_max * 32 * 8 + 8192);
-    const ScanPtrs S(smem, plan, a.nprobe);
-    uint64_t *samp = reinterpret_cast<uint64_t *>(S.tail);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(samp + sch_max * 32);
-    __shared__ int64_t s_q;
-    __shared__ uint32_t s_sel[3];
-    __shared__ unsigned long long s_sel64[2];
-    for (int64_t it = 0;; ++it) {
-        if (threadIdx.x == 0) s_q = next_query(a, it);
-        __syncthreads();
-        const int64_t qi = s_q;
-        if (qi >= a.nq) break;
-        int np = a.npq ? a.npq[qi] : a.nprobe;
-        np = np < 1 ? 1 : (np > a.nprobe ? a.nprobe : np);
-        int ntop = a.ntopq ? a.ntopq[qi] : a.ntop;
-        ntop = ntop < 1 ? 1 : (ntop > a.ntop ? a.ntop : ntop);
-        query_setup<M, W>(a, S, qi, np);  // ends with a barrier
-        const uint32_t total = S.pref[2 * np];
-        int sch = sch_max;
-        while (sch > 64 && (uint32_t)(2 * sch) > total) sch >>= 1;
-        const bool all = (uint64_t)total * 32 <= (uint64_t)cap;
-        uint64_t t = KEY_INF;
-        if (!all) {
-            t = total >= 2u * (uint32_t)sch
-                    ? sample_tau<M, W>(a, S, np, total, ntop, sch, samp, hist, s_sel64, s_sel)
-                    : KEY_INF;
-            if (t == KEY_INF) t = 0;
-        }
-        if (threadIdx.x == 0) {
-            tau[qi] = t;
-            cnt[qi] = 0;
-            const float *sc = a.lut_scale + qi * 2 * a.M;
-            float o = 0.f;
-            for (int m = 0; m < a.M; ++m) o += sc[2 * m + 1];
-            qsum[2 * qi] = sc[0];
-            qsum[2 * qi + 1] = o;
-            if (a.stats) {
-                int64_t gathered = 0;
-                for (int sgi = 0; sgi < 2 * np; ++sgi) gathered += S.seg_end[sgi] - S.seg_beg[sgi];
-                a.stats[qi * 4 + 0] = (int32_t)gathered;
-                a.stats[qi * 4 + 1] = 0;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // Appends the keys of one chunk at or below the query's threshold to its buffer.
+// The threshold is a full (distance, id) key, so a run of equal distances at
+// the threshold is split by id as the sample split it.
 __device__ __forceinline__ void bq_append(const BatchArgs &b, int64_t q, float dist, uint32_t v,
-                                          bool ok, uint32_t thi, int lane) {
+                                          bool ok, uint64_t tau, int lane) {
     const uint32_t od = f2o(dist);
-    const bool pass = ok && od <= thi;
+    const bool pass = ok && (((uint64_t)od << 32) | v) <= tau;
     const uint32_t msk = __ballot_sync(FULL, pass);
     if (msk) {
         uint32_t base = 0;
@@ -1454,7 +1400,7 @@ __device__ __forceinline__ void bq_append(const BatchArgs &b, int64_t q, float d
 // Unit u of the plan: its list, first and last chunk, and its queries.
 struct BqUnit {
     int64_t q[BQ_GMAX];
-    uint32_t thi[BQ_GMAX];
+    uint64_t tau[BQ_GMAX];
     float sc[BQ_GMAX], of[BQ_GMAX];
     uint32_t u, l, c0, c1, nprim;
 };
@@ -1484,12 +1430,12 @@ __device__ __forceinline__ void bq_decode(const BatchArgs &b, uint32_t u, uint32
         if (j < b.G && k < nql) {
             const int64_t q = b.lq[b.lqoff[l] + k];
             x.q[j] = q;
-            x.thi[j] = (uint32_t)(b.tau[q] >> 32);
+            x.tau[j] = b.tau[q];
             x.sc[j] = b.qsum[2 * q];
             x.of[j] = b.qsum[2 * q + 1];
         } else {
             x.q[j] = -1;
-            x.thi[j] = 0;
+            x.tau[j] = 0;
             x.sc[j] = 0.f;
             x.of[j] = 0.f;
         }
@@ -1566,12 +1512,179 @@ __device__ __forceinline__ void adc_multi(const uint32_t (&w)[M / 4], uint32_t v
     }
 }
 
+// The group table of E queries in shared memory: word (c, p), p < M + 31,
+// holds entry [p mod M][c] of each query (query j in byte lane j of the word
+// for FP8, half j for FP16; a query slot < 0 holds zeros). A thread takes 16
+// centroids of one subspace, so the lanes of a warp store consecutive words.
+template <int M, int W, int E>
+__device__ __forceinline__ void bq_table(const void *lut, const int64_t (&qs)[E], uint32_t *tbl) {
+    constexpr int P = M + 31;
+    for (int idx = threadIdx.x; idx < M * 16; idx += blockDim.x) {
+        const int m = idx % M, c0 = (idx / M) * 16;
+        uint32_t wd[16];
+        if (E == 2) {
+            uint32_t h[2][8];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) h[j][i] = 0u;
+                if (qs[j] >= 0) {
+                    const uint4 *p = reinterpret_cast<const uint4 *>(
+                        static_cast<const __half *>(lut) + (qs[j] * M + m) * 256 + c0);
+                    const uint4 x0 = __ldg(p), x1 = __ldg(p + 1);
+                    h[j][0] = x0.x; h[j][1] = x0.y; h[j][2] = x0.z; h[j][3] = x0.w;
+                    h[j][4] = x1.x; h[j][5] = x1.y; h[j][6] = x1.z; h[j][7] = x1.w;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+                wd[i] = __byte_perm(h[0][i >> 1], h[1][i >> 1], (i & 1) ? 0x7632u : 0x5410u);
+        } else {
+            uint32_t e[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                e[j][0] = e[j][1] = e[j][2] = e[j][3] = 0u;
+                if (qs[j] >= 0) {
+                    const uint4 x = __ldg(reinterpret_cast<const uint4 *>(
+                        static_cast<const uint8_t *>(lut) + (qs[j] * M + m) * 256 + c0));
+                    e[j][0] = x.x; e[j][1] = x.y; e[j][2] = x.z; e[j][3] = x.w;
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {  // entries 4i .. 4i + 3 of the four queries
+                const uint32_t t0 = __byte_perm(e[0][i], e[1][i], 0x5140u);
+                const uint32_t t1 = __byte_perm(e[2][i], e[3][i], 0x5140u);
+                const uint32_t t2 = __byte_perm(e[0][i], e[1][i], 0x7362u);
+                const uint32_t t3 = __byte_perm(e[2][i], e[3][i], 0x7362u);
+                wd[4 * i + 0] = __byte_perm(t0, t1, 0x5410u);
+                wd[4 * i + 1] = __byte_perm(t0, t1, 0x7632u);
+                wd[4 * i + 2] = __byte_perm(t2, t3, 0x5410u);
+                wd[4 * i + 3] = __byte_perm(t2, t3, 0x7632u);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+#pragma unroll
+            for (int p = 0; p < P; p += M)
+                if (p + m < P) tbl[(c0 + j) * W + p + m] = wd[j];
+    }
+}
+
+// The m-th smallest of a sample of the query's candidate keys, with the
+// distances computed exactly as the batched scan computes them (its group
+// table with this query alone, adc_multi, then the query's scale and offset
+// sum). Each of the sch * 32 sample slots takes one candidate from its own
+// chunk, spread evenly over all the query's chunks: the near candidates of a
+// query sit in few lists, and whole sampled chunks would leave the estimate
+// to the luck of which lists they fell in.
+template <int M, int W, int E>
+__device__ __forceinline__ uint64_t sample_tau_bq(const ScanArgs &a, const ScanPtrs &S, int np,
+                                                  uint32_t total, int ntop, int sch, uint64_t *buf,
+                                                  uint32_t *hist, unsigned long long *s_tau,
+                                                  uint32_t *sel, const uint32_t *tbl, float scale,
+                                                  float offset) {
+    constexpr int NW = M / 4;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t ns = (uint64_t)sch * 32;
+    const int nw = blockDim.x >> 5;
+    SegCursor sc;  // each lane's chunks increase from one step to the next
+    for (int j = warp; j < sch; j += nw) {
+        uint32_t v;
+        bool ok;
+        const uint64_t slot = (uint64_t)j * 32 + lane;
+        locate(a, S, np, (uint32_t)(slot * total / ns), sc, v, ok);
+        uint32_t w[NW];
+        load_codes<M>(a.codes, v, ok, w);
+        float acc[E];
+        adc_multi<M, W, E>(w, v, tbl, acc);
+        buf[j * 32 + lane] = ok ? (((uint64_t)f2o(fmaf(acc[0], scale, offset)) << 32) | v) : KEY_INF;
+    }
+    __syncthreads();
+    // e sampled keys are expected below the query's n-th key. A query handed
+    // back costs a whole per-query scan, and for a query of millions of
+    // candidates e is well below 1, where sigma * sqrt(e) alone leaves a
+    // Poisson tail of ~1e-3; the extra sigma keys bring it below ~1e-8 (for
+    // sigma 4) while the keys kept stay a small multiple of n.
+    const double e = (double)ntop * (double)sch / (double)total;
+    const double me = ceil(e + (double)a.tau_sigma * sqrt(e) + 1.0 + (double)a.tau_sigma);
+    const int m = me < 1.0 ? 1 : (me > 1e9 ? 1000000000 : (int)me);
+    if (m > sch * 32) return KEY_INF;
+    // the m-th full key: keys are distinct, so about m / sample of the scan's
+    // keys fall at or below it even where many distances are equal
+    return cta_select_rth(buf, sch * 32, nullptr, 0, m, hist, s_tau, s_tau + 1, sel, sel + 1, sel + 2);
+}
+
+// Per-query threshold estimate from a strided sample of the query's
+// candidates (sample_tau_bq), and the per-query constants the batched scan
+// applies: the table's scale s_q and the sum of its offsets. A threshold of 0
+// marks a query the list scan cannot serve (no useful sample); +inf keeps
+// every candidate.
+template <int M, int W, int E>
+__global__ void __launch_bounds__(SEL_THREADS, 2) k_bq_tau(const ScanArgs a, uint64_t *tau,
+                                                           uint32_t *cnt, float *qsum, uint32_t cap,
+                                                           int sch_max) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, sch_max * 32 * 8 + 8192);
+    const ScanPtrs S(smem, plan, a.nprobe);
+    uint64_t *samp = reinterpret_cast<uint64_t *>(S.tail);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(samp + sch_max * 32);
+    __shared__ int64_t s_q;
+    __shared__ uint32_t s_sel[3];
+    __shared__ unsigned long long s_sel64[2];
+    for (int64_t it = 0;; ++it) {
+        if (threadIdx.x == 0) s_q = next_query(a, it);
+        __syncthreads();
+        const int64_t qi = s_q;
+        if (qi >= a.nq) break;
+        int np = a.npq ? a.npq[qi] : a.nprobe;
+        np = np < 1 ? 1 : (np > a.nprobe ? a.nprobe : np);
+        int ntop = a.ntopq ? a.ntopq[qi] : a.ntop;
+        ntop = ntop < 1 ? 1 : (ntop > a.ntop ? a.ntop : ntop);
+        query_setup<M, W>(a, S, qi, np);  // ends with a barrier
+        const float *sq = a.lut_scale + qi * 2 * a.M;
+        float off = 0.f;
+        for (int m = 0; m < a.M; ++m) off += sq[2 * m + 1];
+        const uint32_t total = S.pref[2 * np];
+        int sch = sch_max;
+        while (sch > 64 && (uint32_t)(2 * sch) > total) sch >>= 1;
+        const bool all = (uint64_t)total * 32 <= (uint64_t)cap;
+        uint64_t t = KEY_INF;
+        if (!all) {
+            if (total >= 2u * (uint32_t)sch) {
+                // this query's group table in place of its FP32 table
+                int64_t qs[E];
+#pragma unroll
+                for (int j = 0; j < E; ++j) qs[j] = j == 0 ? qi : -1;
+                uint32_t *tbl = reinterpret_cast<uint32_t *>(S.lut);
+                __syncthreads();
+                bq_table<M, W, E>(a.lut, qs, tbl);
+                __syncthreads();
+                t = sample_tau_bq<M, W, E>(a, S, np, total, ntop, sch, samp, hist, s_sel64, s_sel, tbl, sq[0],
+                                           off);
+            }
+            if (t == KEY_INF) t = 0;
+        }
+        if (threadIdx.x == 0) {
+            tau[qi] = t;
+            cnt[qi] = 0;
+            qsum[2 * qi] = sq[0];
+            qsum[2 * qi + 1] = off;
+            if (a.stats) {
+                int64_t gathered = 0;
+                for (int sgi = 0; sgi < 2 * np; ++sgi) gathered += S.seg_end[sgi] - S.seg_beg[sgi];
+                a.stats[qi * 4 + 0] = (int32_t)gathered;
+                a.stats[qi * 4 + 1] = 0;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <int M, int W, int E>
 __global__ void __launch_bounds__(BQ_THREADS) k_bq_scan(const BatchArgs b) {
     extern __shared__ __align__(16) uint32_t tbl[];  // [256][W] words of the E queries' entries
     __shared__ BqUnit s_unit[2];  // the current unit and the next one
     constexpr int NW = M / 4;
-    constexpr int P = M + 31;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t total_units = b.upre[b.nlist];
     if (threadIdx.x == 0) bq_decode(b, atomicAdd(b.ctr, 1u), total_units, s_unit[0]);
@@ -1583,68 +1696,16 @@ __global__ void __launch_bounds__(BQ_THREADS) k_bq_scan(const BatchArgs b) {
         int64_t qs[E];
 #pragma unroll
         for (int j = 0; j < E; ++j) qs[j] = U.q[j];
-        // table word (c, p), p < M + 31: entry [p mod M][c] of each of the E
-        // queries (query j in byte lane j of the word for FP8, half j for
-        // FP16); a thread takes 16 centroids of one subspace, so the lanes of
-        // a warp store consecutive words
-        for (int idx = threadIdx.x; idx < M * 16; idx += blockDim.x) {
-            const int m = idx % M, c0 = (idx / M) * 16;
-            uint32_t wd[16];
-            if (E == 2) {
-                uint32_t h[2][8];
-#pragma unroll
-                for (int j = 0; j < 2; ++j) {
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) h[j][i] = 0u;
-                    if (qs[j] >= 0) {
-                        const uint4 *p = reinterpret_cast<const uint4 *>(
-                            static_cast<const __half *>(b.lut) + (qs[j] * M + m) * 256 + c0);
-                        const uint4 x0 = __ldg(p), x1 = __ldg(p + 1);
-                        h[j][0] = x0.x; h[j][1] = x0.y; h[j][2] = x0.z; h[j][3] = x0.w;
-                        h[j][4] = x1.x; h[j][5] = x1.y; h[j][6] = x1.z; h[j][7] = x1.w;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 16; ++i)
-                    wd[i] = __byte_perm(h[0][i >> 1], h[1][i >> 1], (i & 1) ? 0x7632u : 0x5410u);
-            } else {
-                uint32_t e[4][4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    e[j][0] = e[j][1] = e[j][2] = e[j][3] = 0u;
-                    if (qs[j] >= 0) {
-                        const uint4 x = __ldg(reinterpret_cast<const uint4 *>(
-                            static_cast<const uint8_t *>(b.lut) + (qs[j] * M + m) * 256 + c0));
-                        e[j][0] = x.x; e[j][1] = x.y; e[j][2] = x.z; e[j][3] = x.w;
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {  // entries 4i .. 4i + 3 of the four queries
-                    const uint32_t t0 = __byte_perm(e[0][i], e[1][i], 0x5140u);
-                    const uint32_t t1 = __byte_perm(e[2][i], e[3][i], 0x5140u);
-                    const uint32_t t2 = __byte_perm(e[0][i], e[1][i], 0x7362u);
-                    const uint32_t t3 = __byte_perm(e[2][i], e[3][i], 0x7362u);
-                    wd[4 * i + 0] = __byte_perm(t0, t1, 0x5410u);
-                    wd[4 * i + 1] = __byte_perm(t0, t1, 0x7632u);
-                    wd[4 * i + 2] = __byte_perm(t2, t3, 0x5410u);
-                    wd[4 * i + 3] = __byte_perm(t2, t3, 0x7632u);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-#pragma unroll
-                for (int p = 0; p < P; p += M)
-                    if (p + m < P) tbl[(c0 + j) * W + p + m] = wd[j];
-        }
+        bq_table<M, W, E>(b.lut, qs, tbl);
         __syncthreads();
         // the next unit is claimed and decoded while this one is scanned
         if (threadIdx.x == 0) bq_decode(b, atomicAdd(b.ctr, 1u), total_units, s_unit[cur ^ 1]);
-        uint32_t thi[E];
+        uint64_t tq[E];
         float sc[E], of[E];
         uint32_t kept[E];
 #pragma unroll
         for (int j = 0; j < E; ++j) {
-            thi[j] = U.thi[j];
+            tq[j] = U.tau[j];
             sc[j] = U.sc[j];
             of[j] = U.of[j];
             kept[j] = 0u;
@@ -1705,7 +1766,7 @@ __global__ void __launch_bounds__(BQ_THREADS) k_bq_scan(const BatchArgs b) {
 #pragma unroll
             for (int j = 0; j < E; ++j) {
                 kept[j] += ok[j] ? 1u : 0u;
-                bq_append(b, qs[j], fmaf(acc[j], sc[j], of[j]), v, ok[j], thi[j], lane);
+                bq_append(b, qs[j], fmaf(acc[j], sc[j], of[j]), v, ok[j], tq[j], lane);
             }
             v = vn;
 #pragma unroll
@@ -2030,9 +2091,9 @@ static bool launch_batched_m(const DeviceIndex &ix, const ScanLaunch &l, const B
         t.order = l.order;
         const ScanSmem plan(W, a.d, a.nlist, a.has_rep, a.nprobe, sch_max * 32 * 8 + 8192);
         FA_REQUIRE(plan.total <= 227 * 1024, FA_ERR_ARG, "threshold sample above 227 KB");
-        set_smem(k_bq_tau<M, W>, plan.total);
-        k_bq_tau<M, W><<<2 * cur_num_sms(), SEL_THREADS, plan.total, st>>>(t, bb.tau, bb.cnt, bb.qsum,
-                                                                          bb.cap, sch_max);
+        auto ktau = l.lut_prec == FA_LUT_FP8 ? k_bq_tau<M, W, 4> : k_bq_tau<M, W, 2>;
+        set_smem(ktau, plan.total);
+        ktau<<<2 * cur_num_sms(), SEL_THREADS, plan.total, st>>>(t, bb.tau, bb.cnt, bb.qsum, bb.cap, sch_max);
         FA_CHECK_CUDA(cudaGetLastError());
     }
     // 2. the list scan, sub-batch by sub-batch (the sub-batch's tables stay in L2)

@@ -152,18 +152,20 @@ def test_batched_fused_rerank_matches_oracle(fa, u8_dev, n, shift, sigma):
         assert st[i, 3] == len(tasks), (i, st[i])
 
 
-@pytest.mark.parametrize("k,sigma", [(4097, -1000.0), (4097, 4.0), (4097, 150.0), (600, 150.0)])
+@pytest.mark.parametrize("k,sigma", [(4097, -1000.0), (4097, 4.0), (4097, 150.0), (600, 400.0)])
 def test_batched_every_threshold_path(fa, f32_small, k, sigma):
-    """About 25k candidates per query (nprobe 64 of 256 lists), more than a
-    query's key buffer holds: the sampled threshold filters. Forced low
-    (fewer than n keys below it) or high (more keys than the buffer holds),
-    the queries are handed to the per-query scan; all paths meet the bound."""
+    """100k candidates per query (every one of the 256 lists probed), more
+    than a query's key buffer holds (65536 keys): the sampled threshold
+    filters. Forced low (fewer than n keys below it) or high (more keys than
+    the buffer holds), the queries are handed to the per-query scan; all
+    paths meet the bound."""
     s = f32_small
     q = s["q"][:8]
-    probes = oracle.coarse(q, s["parts"]["centroids"], 64)
+    npb = s["parts"]["nlist"]
+    probes = oracle.coarse(q, s["parts"]["centroids"], npb)
     fa.fa_debug_tau_sigma(sigma)
     try:
-        _bounded(fa, s, q, k, 64, _bp(fa), probes, what="sigma%g" % sigma)
+        _bounded(fa, s, q, k, npb, _bp(fa), probes, what="sigma%g" % sigma)
     finally:
         fa.fa_debug_tau_sigma(4.0)
 
