@@ -953,6 +953,20 @@ def bench_zipf(args, emit=True):
         rec_p = recall_of(oracle, base, queries, ids_plain, gt)
     peak, peak_src = measured_peaks()
     scan_bytes = int(cand.sum()) * M + nq * M * 256 + nq * 10 * 8
+    batched = zipf_form_name(args) == "batched"
+    # the scan's bound is its shared-memory table reads, not HBM: one 32-bit
+    # table word per (candidate, subspace) serves G queries (4 FP8 entries in
+    # the batched form, 1 FP32 entry in the tiled per-query scan); the peak is
+    # one 128-byte shared-memory wavefront per clock per SM
+    G = 4 if batched else 1
+    table_bytes = int(cand.sum()) * M * 4 // G
+    props = torch.cuda.get_device_properties(0)
+    sm_mhz = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("sm_max_mhz", 2032.0) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 2032.0
+    smem_peak = props.multi_processor_count * 128 * sm_mhz * 1e6 / 1e9
+    wl_key = "ivfpq-f32unit-%dm-d96-zipf65536-M48-nq%d-rr%d-%s" % (args.zipf_n // 1_000_000, nq, rr,
+                                                                     zipf_form_name(args))
+    dram = profile_traffic(src_hash(SCAN_SOURCES), wl_key)
     err = None
     if getattr(args, "zipf_err", True):
         parts = ix.parts(with_raw=False)
@@ -988,10 +1002,22 @@ def bench_zipf(args, emit=True):
                                  "min": int(cand.min())},
         "largest_list_fraction": float(z.sizes().max() / args.zipf_n),
         "stage_ms": {"coarse": tr.coarse_ms, "lut": tr.lut_ms, "scan": tr.scan_ms, "post": tr.post_ms},
-        "roofline": {"bound": "hbm", "kernel": "k_scan (tiled)", "achieved":
-                     scan_bytes / (tr.scan_ms / 1e3) / 1e9, "peak": peak, "peak_source": peak_src,
-                     "unit": "GB/s", "frac": scan_bytes / (tr.scan_ms / 1e3) / 1e9 / peak,
-                     "algorithmic_bytes_per_launch": scan_bytes},
+        "roofline": {"bound": "alu",
+                     "kernel": "k_bq_scan (+ k_bq_tau, k_bq_select)" if batched else "k_scan (tiled)",
+                     "achieved": table_bytes / (tr.scan_ms / 1e3) / 1e9, "peak": smem_peak,
+                     "peak_source": "derived: %d SMs x 128 B shared-memory wavefront per clock x %.0f MHz"
+                     % (props.multi_processor_count, sm_mhz),
+                     "unit": "GB/s", "frac": table_bytes / (tr.scan_ms / 1e3) / 1e9 / smem_peak,
+                     "traffic": dram,
+                     "what": "shared-memory table bytes the scan stage must read (one 32-bit word per "
+                             "(candidate, subspace) for every %d queries) over the stage's time" % G,
+                     "hbm": {"dram_gbs": (dram / (tr.scan_ms / 1e3) / 1e9) if dram else None,
+                             "peak": peak, "peak_source": peak_src,
+                             "frac": (dram / (tr.scan_ms / 1e3) / 1e9 / peak) if dram else None,
+                             "per_query_code_bytes_gbs": scan_bytes / (tr.scan_ms / 1e3) / 1e9,
+                             "note": "code bytes counted once per (query, candidate) exceed the DRAM "
+                                     "traffic: a list is read once for a group of queries and from L2"},
+                     "algorithmic_bytes_per_launch": table_bytes, "traffic_workload": wl_key},
         "err_vs_fp64": err, "serving_form": serving,
         "clocks": clk, "build_s": t_build, "gen_s": t_gen,
     }

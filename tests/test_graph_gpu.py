@@ -2,9 +2,10 @@
 
 The graph is part of the index (an input to both sides, like the lists): it
 is exported and the oracle walks it. Checked against the oracle:
-  * the build: every vertex's out-edges are its R nearest other heads by
-    (squared L2, id), the oracle's exact probe of the heads against
-    themselves, and the heads are the oracle's rounding of the centroids;
+  * the build: every vertex's out-edges follow the build's rule (pruned
+    nearest heads, reverse edges, nearest fill) computed from the oracle's
+    exact probe of the heads against themselves, and the heads are the
+    oracle's rounding of the centroids;
   * the walk: for integer vectors with integral queries every distance is an
     integer (exact in FP32), so the GPU's walk takes the oracle's FP64
     decisions: the entry pivots, lists, lists found and vertices checked are
