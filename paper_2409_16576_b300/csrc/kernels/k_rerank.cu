@@ -247,6 +247,10 @@ __device__ __forceinline__ void rerank_one(
                 nend = end + batch < valid ? end + batch : valid;
             }
             const int64_t uid_next = task_id(ns + lane, nend);
+            if (!pg && uid_next >= 0) {  // the next step's row into L2 while this step's rows load
+                const char *rn = reinterpret_cast<const char *>(raw + uid_next * (int64_t)d);
+                for (int o = 0; o < d * (int)sizeof(T); o += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(rn + o));
+            }
             const float dist = pg ? exact_rows_any<T, true>(reinterpret_cast<const T *>(pg->cache), d, qs, qp,
                                                             qint, paged_row(*pg, uid), ip != 0)
                                   : exact_rows_any<T>(raw, d, qs, qp, qint, uid, ip != 0);
