@@ -99,7 +99,8 @@ void free_device_index(fa_index *ix) {
     void *ptrs[] = {d.centroids, d.cnorm, d.codebooks, d.codes, d.list_beg, d.rep_off,
                     d.rep_v, d.rep_mo, d.rep_t, d.mem, d.perm, d.raw_dev_alloc,
                     d.centroids_bf16, d.codebooks_bf16, d.cbnorm, d.lorder, d.vpage, d.vslot,
-                    d.graph.heads, d.graph.adj, d.graph.seeds, d.graph.pivots};
+                    d.graph.heads, d.graph.adj, d.graph.seeds, d.graph.pivots, d.graph.pivot_tiles,
+                    d.graph.pivot_norm};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     d = DeviceIndex{};
@@ -186,7 +187,8 @@ static void build_probe_graph(fa_index *ix, int32_t R, int32_t S) {
     std::vector<int32_t> seeds(S);
     for (int32_t i = 0; i < S; ++i) seeds[i] = (int32_t)(((int64_t)i * nlist) / S);
     ProbeGraph &g = ix->dev.graph;
-    for (void *p : {g.heads, (void *)g.adj, (void *)g.seeds, (void *)g.pivots})
+    for (void *p : {g.heads, (void *)g.adj, (void *)g.seeds, (void *)g.pivots, g.pivot_tiles,
+                    (void *)g.pivot_norm})
         if (p) cudaFree(p);
     g = ProbeGraph{};
     int64_t bytes = 0;
@@ -208,6 +210,21 @@ static void build_probe_graph(fa_index *ix, int32_t R, int32_t S) {
         std::copy(heads.begin() + (size_t)seeds[i] * d, heads.begin() + (size_t)(seeds[i] + 1) * d,
                   piv.begin() + (size_t)i * d);
     g.pivots = dev_upload(piv.data(), piv.size(), bytes);
+    if (integer && d <= 128) {
+        // integer heads are exact in bf16 (|value| <= 256) and their products
+        // and sums exact in FP32 for d <= 128, so the tensor cores give the
+        // entry probe the same distances as FP32 direct differences
+        std::vector<uint16_t> tiles;
+        prepare_centroid_tiles(piv.data(), S, d, tiles, g.pivot_kp, g.pivot_nt);
+        g.pivot_tiles = dev_upload(tiles.data(), tiles.size(), bytes);
+        std::vector<float> pn(S);
+        for (int32_t i = 0; i < S; ++i) {
+            double s2 = 0.0;
+            for (int j = 0; j < d; ++j) s2 += (double)piv[(size_t)i * d + j] * piv[(size_t)i * d + j];
+            pn[i] = (float)s2;
+        }
+        g.pivot_norm = dev_upload(pn.data(), pn.size(), bytes);
+    }
     g.R = R;
     g.S = S;
     ix->dev.device_bytes += bytes;
@@ -851,7 +868,7 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
                 tr.launches += 1;
             }
             launch_graph_probe(D, qd, nq, nprobe, nprobe, gbeam, gmax, gentry, npq, w->probes, w->npq, nullptr,
-                               w->coarse_d, w->coarse_rows, w->gentry, st);
+                               w->coarse_d, w->coarse_rows, w->gentry, w->err, st);
             npq = w->npq;
             tr.launches += gentry < D.graph.S ? 3 : 1;
         } else {
@@ -1666,7 +1683,7 @@ fa_status fa_debug_probes(fa_index *ix, const float *queries, int64_t nq, int32_
             int32_t gb = 0, gm = 0, ge = 0;
             graph_defaults(ix->dev.graph, nprobe, sp.graph_beam, sp.graph_max_check, sp.graph_entry, gb, gm, ge);
             launch_graph_probe(ix->dev, w->q, nq, nprobe, nprobe, gb, gm, ge, nullptr, w->probes, w->npq, nullptr,
-                               w->coarse_d, w->coarse_rows, w->gentry, w->stream);
+                               w->coarse_d, w->coarse_rows, w->gentry, w->err, w->stream);
         } else {
             launch_coarse(ix->dev, w->q, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, w->stream);
         }
@@ -1775,7 +1792,7 @@ fa_status fa_debug_graph_probe(fa_index *ix, const float *queries, int64_t nq, i
         ws_ensure(ix, w, nq, 1, nprobe, 1, 0);
         FA_CHECK_CUDA(cudaMemcpyAsync(w->q, queries, sizeof(float) * nq * ix->d, cudaMemcpyHostToDevice, w->stream));
         launch_graph_probe(ix->dev, w->q, nq, nprobe, nprobe, gb, gm, ge, nullptr, w->probes, w->npq, w->kq,
-                           w->coarse_d, w->coarse_rows, w->gentry, w->stream);
+                           w->coarse_d, w->coarse_rows, w->gentry, w->err, w->stream);
         FA_CHECK_CUDA(cudaMemcpyAsync(probes, w->probes, sizeof(int32_t) * nq * nprobe, cudaMemcpyDeviceToHost,
                                       w->stream));
         if (found)

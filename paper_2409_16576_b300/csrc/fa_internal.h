@@ -71,6 +71,11 @@ struct ProbeGraph {
     int32_t *adj = nullptr;    // [nlist][R] out-edges, -1 = none
     int32_t *seeds = nullptr;  // [S] pivot vertices
     float *pivots = nullptr;   // [S][d] their heads as floats (the entry probe's operand)
+    // integer heads: the pivots as tensor-core tiles and their squared norms,
+    // for an entry probe on the tensor cores (exact: see launch_graph_probe)
+    void *pivot_tiles = nullptr;
+    float *pivot_norm = nullptr;
+    int32_t pivot_kp = 0, pivot_nt = 0;
     int32_t R = 0, S = 0;
 };
 
@@ -392,7 +397,8 @@ void launch_rerank_paged(const DeviceIndex &ix, const float *q, const uint64_t *
 void launch_graph_probe(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
                         int32_t probe_stride, int32_t beam, int32_t max_check, int32_t entry,
                         const int32_t *npq_in, int32_t *probes, int32_t *npq_out, int32_t *checks,
-                        float *scratch, int64_t scratch_rows, int32_t *entry_buf, cudaStream_t st);
+                        float *scratch, int64_t scratch_rows, int32_t *entry_buf, uint32_t *err,
+                        cudaStream_t st);
 // rows x centroids -> top-ntop columns per row (FP32 direct differences, or -<x, c>)
 void launch_l2_topn(const float *X, int64_t nx, int32_t d, const float *C, int32_t nc, int32_t ntop,
                     float *scratch, int64_t scratch_rows, int32_t *out_ids, int32_t out_stride,

@@ -184,7 +184,8 @@ int graph_table_bits(int32_t max_check, int32_t R, int32_t S) {
 void launch_graph_probe(const DeviceIndex &ix, const float *q, int64_t nq, int32_t nprobe,
                         int32_t probe_stride, int32_t beam, int32_t max_check, int32_t entry,
                         const int32_t *npq_in, int32_t *probes, int32_t *npq_out, int32_t *checks,
-                        float *scratch, int64_t scratch_rows, int32_t *entry_buf, cudaStream_t st) {
+                        float *scratch, int64_t scratch_rows, int32_t *entry_buf, uint32_t *err,
+                        cudaStream_t st) {
     if (nq == 0) return;
     const ProbeGraph &g = ix.graph;
     FA_REQUIRE(g.adj && g.heads, FA_ERR_ARG, "the index has no navigation graph");
@@ -193,11 +194,26 @@ void launch_graph_probe(const DeviceIndex &ix, const float *q, int64_t nq, int32
     FA_REQUIRE(entry >= 1 && entry <= g.S, FA_ERR_ARG, "graph entry must be in 1..S");
     const bool per_query = entry < g.S;
     if (per_query) {
-        // the entry pivots nearest each query: exact FP32 direct differences
-        // (exact for integer heads and integral queries), ties by pivot order
+        // the entry pivots nearest each query, ties by pivot order. Integer
+        // heads: on the tensor cores (bf16 holds them exactly, and for an
+        // integral query every product, norm and sum is an integer below
+        // 2^24, so the distances are exact); else FP32 direct differences.
         FA_REQUIRE(entry <= 64 && entry_buf && scratch, FA_ERR_ARG, "graph entry above 64");
-        launch_l2_topn(q, nq, ix.d, g.pivots, g.S, entry, scratch, scratch_rows, entry_buf, entry, st,
-                       ix.metric == FA_METRIC_IP ? 1 : 0);
+        if (g.pivot_tiles) {
+            DeviceIndex P = ix;
+            P.centroids_bf16 = g.pivot_tiles;
+            P.cnorm = g.pivot_norm;
+            P.nlist = g.S;
+            P.tc_kp = g.pivot_kp;
+            P.tc_ntiles = g.pivot_nt;
+            for (int64_t r0 = 0; r0 < nq; r0 += scratch_rows) {
+                const int64_t rows = std::min<int64_t>(scratch_rows, nq - r0);
+                launch_coarse_tc(P, q + r0 * ix.d, rows, entry, scratch, entry_buf + r0 * entry, entry, err, st);
+            }
+        } else {
+            launch_l2_topn(q, nq, ix.d, g.pivots, g.S, entry, scratch, scratch_rows, entry_buf, entry, st,
+                           ix.metric == FA_METRIC_IP ? 1 : 0);
+        }
     }
     const int32_t S = per_query ? entry : g.S;
     const int hbits = graph_table_bits(max_check, g.R, S);

@@ -217,3 +217,21 @@ def test_graph_probe_arguments(fa):
     with pytest.raises(fa.FaError) as e:  # no graph built
         fa.fa_search_ex(ix, mix.queries(2), 5, 4, fa.search_params(probe_gemm=fa.FA_PROBE_GRAPH))
     assert e.value.status == fa.FA_ERR_ARG
+
+
+def test_batched_search_with_graph_probe(fa):
+    """The batched form (FA_BATCHED, FP8 table) after the graph walk equals
+    the batched form given the oracle's walk lists."""
+    s = _u8(fa)
+    g = s["g"]
+    nprobe, beam, mc = 32, 64, 600
+    tc = fa.FA_GEMM_BF16_TC
+    base = dict(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, rerank_n=200, rerank_eps=-1.0, rerank_beta=1,
+                flags=fa.FA_BATCHED)
+    p = fa.search_params(probe_gemm=fa.FA_PROBE_GRAPH, graph_beam=beam, graph_max_check=mc, **base)
+    gi, gd = fa.fa_search_ex(s["ix"], s["q"], 10, nprobe, p)
+    ref, rfound, _ = oracle.graph_probe(s["q"], s["heads"], g["adj"], _seeds(s, 16), beam, mc, nprobe)
+    pr = np.where(ref < 0, 0, ref).astype(np.int32)
+    ri, rd = fa.fa_search_ex(s["ix"], s["q"], 10, nprobe, fa.search_params(**base), probes=pr,
+                             nprobe_per_query=rfound)
+    assert np.array_equal(gi, ri) and np.array_equal(gd, rd)
