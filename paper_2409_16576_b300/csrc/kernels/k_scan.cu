@@ -102,14 +102,26 @@ struct Work {
 
 // Shared memory plan (bytes), shared by host and device. `tail` is the
 // per-variant region: per-warp merge buffers, or the CTA key buffer.
+// The probed-list set of a query (the replica dedup rule's lookups): a
+// bitmap of nlist bits up to 65536 lists (8 KB); beyond that an
+// open-addressing table of the probed list ids, 2^pset entries >= 2 nprobe
+// (4 KB at nprobe 512 instead of a 32 KB bitmap at 262144 lists).
+__host__ __device__ inline int pset_bits(int nlist, int nprobe) {
+    if (nlist <= 65536) return 0;
+    int b = 4;
+    while ((1 << b) < 2 * nprobe) ++b;
+    return b;
+}
+
 struct ScanSmem {
-    int lut, qv, pref, seg, bitmap, tail, total;
+    int lut, qv, pref, seg, bitmap, tail, total, pset;
     __host__ __device__ ScanSmem(int W, int d, int nlist, int has_rep, int nprobe, int tail_bytes) {
         lut = 256 * W * 4;
         qv = ((d + 3) & ~3) * 4;
         pref = ((2 * nprobe + 1) * 4 + 15) / 16 * 16;
         seg = 2 * nprobe * 4 * 2;
-        bitmap = has_rep ? ((nlist + 127) / 128) * 16 : 0;
+        pset = pset_bits(nlist, nprobe);
+        bitmap = !has_rep ? 0 : (pset ? ((4 << pset) + 15) / 16 * 16 : ((nlist + 127) / 128) * 16);
         tail = tail_bytes;
         total = lut + qv + pref + seg + bitmap + tail;
     }
@@ -117,9 +129,10 @@ struct ScanSmem {
 
 struct ScanPtrs {
     float *lut, *qv;
-    uint32_t *pref, *seg_beg, *seg_end, *bitmap;
+    uint32_t *pref, *seg_beg, *seg_end, *bitmap;  // bitmap: the probed-list set
     unsigned char *tail;
-    __device__ ScanPtrs(unsigned char *smem, const ScanSmem &p, int nprobe) {
+    int pset;  // 0: bitmap; else log2 of the table's entries
+    __device__ ScanPtrs(unsigned char *smem, const ScanSmem &p, int nprobe) : pset(p.pset) {
         lut = reinterpret_cast<float *>(smem);
         qv = reinterpret_cast<float *>(smem + p.lut);
         pref = reinterpret_cast<uint32_t *>(smem + p.lut + p.qv);
@@ -289,6 +302,20 @@ struct SegCursor {
     uint32_t p0 = 0, p1 = 0, beg = 0, end = 0;
 };
 
+// Whether list l is in the query's probed-list set.
+__device__ __forceinline__ bool pset_has(const ScanPtrs &S, uint32_t l) {
+    if (S.pset == 0) return (S.bitmap[l >> 5] >> (l & 31)) & 1u;
+    const uint32_t mask = (1u << S.pset) - 1u;
+    uint32_t h = (l * 2654435761u) >> (32 - S.pset);
+    for (uint32_t i = 0; i <= mask; ++i) {
+        const uint32_t e = S.bitmap[h];
+        if (e == l + 1u) return true;
+        if (e == 0u) return false;
+        h = (h + 1u) & mask;
+    }
+    return false;
+}
+
 // Candidate of this lane in chunk g (32 consecutive entries of one segment):
 // primary segments give internal ids directly; replica entries apply the dedup
 // rule. Chunks of a warp are visited in increasing order, so the cursor only
@@ -314,7 +341,7 @@ __device__ __forceinline__ void locate(const ScanArgs &a, const ScanPtrs &S, int
         const int t = a.rep_t[pos];
         for (int u = 0; u < t; ++u) {
             const uint32_t l = a.mem[mo + u];
-            if (S.bitmap[l >> 5] & (1u << (l & 31))) valid = false;
+            if (pset_has(S, l)) valid = false;
         }
     }
 }
@@ -327,8 +354,10 @@ __device__ __forceinline__ void query_setup(const ScanArgs &a, const ScanPtrs &S
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int32_t *pr = a.probes + qi * a.probe_stride;
     for (int j = threadIdx.x; j < a.d; j += blockDim.x) S.qv[j] = a.q[qi * a.d + j];
-    if (a.has_rep)
-        for (int j = threadIdx.x; j < (a.nlist + 31) / 32; j += blockDim.x) S.bitmap[j] = 0u;
+    if (a.has_rep) {
+        const int words = S.pset ? (1 << S.pset) : (a.nlist + 31) / 32;
+        for (int j = threadIdx.x; j < words; j += blockDim.x) S.bitmap[j] = 0u;
+    }
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
         const int l = pr[i];
         if (l < 0 || l >= a.nlist) {
@@ -350,7 +379,19 @@ __device__ __forceinline__ void query_setup(const ScanArgs &a, const ScanPtrs &S
     if (a.has_rep)
         for (int i = threadIdx.x; i < np; i += blockDim.x) {
             const int l = pr[i];
-            if (l >= 0 && l < a.nlist) atomicOr(&S.bitmap[l >> 5], 1u << (l & 31));
+            if (l < 0 || l >= a.nlist) continue;
+            if (S.pset == 0) {
+                atomicOr(&S.bitmap[l >> 5], 1u << (l & 31));
+                continue;
+            }
+            // table insert (the set holds at most half its entries)
+            const uint32_t mask = (1u << S.pset) - 1u;
+            uint32_t h = ((uint32_t)l * 2654435761u) >> (32 - S.pset);
+            for (uint32_t t = 0; t <= mask; ++t) {
+                const uint32_t old = atomicCAS(&S.bitmap[h], 0u, (uint32_t)l + 1u);
+                if (old == 0u || old == (uint32_t)l + 1u) break;
+                h = (h + 1u) & mask;
+            }
         }
     if (warp == 0) {
         const int nseg = 2 * np;
