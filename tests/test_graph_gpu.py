@@ -235,3 +235,19 @@ def test_batched_search_with_graph_probe(fa):
     ri, rd = fa.fa_search_ex(s["ix"], s["q"], 10, nprobe, fa.search_params(**base), probes=pr,
                              nprobe_per_query=rfound)
     assert np.array_equal(gi, ri) and np.array_equal(gd, rd)
+
+
+@pytest.mark.parametrize("nlist", [1, 2, 5])
+def test_graph_probe_tiny_indexes(fa, nlist):
+    """A graph of one, two or five lists (every walk reaches them all):
+    FA_PROBE_GRAPH probing every list equals the exact probe of every list."""
+    mix = synth.Mixture(32, 4, 8.0, kind="u8")
+    base = mix.base(3000)
+    q = mix.queries(20)
+    ix = fa.fa_build_index(base, fa.build_params(nlist=nlist, M=8, kmeans_iters=3))
+    fa.fa_build_probe_graph(ix)
+    g = fa.fa_index_get_graph(ix)
+    assert g["adj"].shape == (nlist, max(1, min(32, nlist - 1)))
+    a = fa.fa_search_ex(ix, q, 10, nlist, fa.search_params(probe_gemm=fa.FA_PROBE_GRAPH))
+    b = fa.fa_search_ex(ix, q, 10, nlist)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

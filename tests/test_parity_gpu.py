@@ -431,14 +431,20 @@ def _serve_all(srv, n):
     return got
 
 
-@pytest.mark.parametrize("lowp", [False, True])
+@pytest.mark.parametrize("lowp", [False, True, "batched"])
 def test_serving_result_same_alone_and_in_the_mix(fa, u8_repl, lowp):
     """Continuous batching: every request's result equals the result of the
-    same query searched alone (same k, nprobe and parameters), bit for bit."""
+    same query searched alone (same k, nprobe and parameters), bit for bit;
+    with the batched form (FP8 table, exhaustive re-rank) every served
+    distance is the oracle's exact distance of that id."""
     s = u8_repl
     tc = fa.FA_GEMM_BF16_TC
-    p = fa.search_params(lut_prec=fa.FA_LUT_F16, lut_gemm=tc, probe_gemm=tc, rerank_n=50,
-                         rerank_eps=0.0) if lowp else fa.search_params()
+    if lowp == "batched":
+        p = fa.search_params(lut_prec=fa.FA_LUT_FP8, lut_gemm=tc, probe_gemm=tc, rerank_n=50,
+                             rerank_eps=-1.0, flags=fa.FA_BATCHED)
+    else:
+        p = fa.search_params(lut_prec=fa.FA_LUT_F16, lut_gemm=tc, probe_gemm=tc, rerank_n=50,
+                             rerank_eps=0.0) if lowp else fa.search_params()
     rng = np.random.default_rng(4)
     n = 120
     q = np.concatenate([s["q"]] * 3)[:n]
@@ -458,6 +464,13 @@ def test_serving_result_same_alone_and_in_the_mix(fa, u8_repl, lowp):
         ai, ad = fa.fa_search_ex(s["ix"], q[i:i + 1], int(ks[i]), int(nps[i]), p)
         assert np.array_equal(ids[:ks[i]], ai[0]) and np.array_equal(dist[:ks[i]], ad[0]), i
         assert np.all(ids[ks[i]:] == -1)
+    if lowp == "batched":
+        for i in range(n):
+            ids, dist, _ = got[int(rid[i])]
+            k = int(ks[i])
+            ref = oracle.exact(q[i], s["parts"]["raw"], ids[:k].astype(np.int64))
+            assert np.array_equal(dist[:k], ref.astype(np.float32)) and np.all(np.diff(dist[:k]) >= 0), i
+        return
     # each request against the oracle: the served row equals the row searched
     # alone (above), and that row is checked here against the FP64 oracle
     compared = 0
