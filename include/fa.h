@@ -236,7 +236,11 @@ void fa_free_index(fa_index *ix);
                                   * carries one scale per query (fa_debug_lut
                                   * with this flag returns that table). FP16
                                   * entries are summed in FP32; FP8 entries in
-                                  * half2 over 16 subspaces, then in FP32. */
+                                  * half2 over 16 subspaces, then in FP32.
+                                  * Workspace: a key buffer of max(4 top-n,
+                                  * 65536) keys (8 bytes each) per query of
+                                  * the call, so split very large batches;
+                                  * FA_ERR_OOM when it does not fit. */
 
 /* Optional per-call trace, measured with CUDA events on the call's stream
  * (ms of device time per stage; launches = kernels this call launched). An
