@@ -251,3 +251,42 @@ def test_graph_probe_tiny_indexes(fa, nlist):
     a = fa.fa_search_ex(ix, q, 10, nlist, fa.search_params(probe_gemm=fa.FA_PROBE_GRAPH))
     b = fa.fa_search_ex(ix, q, 10, nlist)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_graph_probe_under_graph_capture(fa):
+    """FA_GRAPH with FA_PROBE_GRAPH: the captured search (the walk on the
+    call's stream, the table on the second stream, joined before the scan)
+    replays to the eager result, also after the queries' contents change."""
+    import torch
+    s = _u8(fa)
+    tc = fa.FA_GEMM_BF16_TC
+    kw = dict(lut_prec=fa.FA_LUT_F16, lut_gemm=tc, probe_gemm=fa.FA_PROBE_GRAPH, graph_beam=64,
+              graph_max_check=600)
+    p = fa.search_params(flags=fa.FA_GRAPH, **kw)
+    ref = fa.search_params(**kw)
+    qd = torch.as_tensor(s["q"], device="cuda")
+    oi = torch.empty((qd.shape[0], 10), dtype=torch.int64, device="cuda")
+    od = torch.empty((qd.shape[0], 10), dtype=torch.float32, device="cuda")
+    for rnd in range(3):
+        if rnd == 2:
+            qd.copy_(torch.flip(qd, [0]))  # new contents in the same buffer
+        fa.fa_search_ex(s["ix"], qd, 10, 32, p, out_ids=oi, out_dist=od)
+        torch.cuda.synchronize()
+        ei, ed = fa.fa_search_ex(s["ix"], qd.cpu().numpy(), 10, 32, ref)
+        assert np.array_equal(oi.cpu().numpy(), ei) and np.array_equal(od.cpu().numpy(), ed), rnd
+
+
+def test_graph_is_not_saved(fa, tmp_path):
+    """The graph is not part of a saved index: a loaded index refuses
+    FA_PROBE_GRAPH until its graph is built again, then walks as before."""
+    s = _u8(fa)
+    path = str(tmp_path / "g.idx")
+    fa.fa_save_index(s["ix"], path)
+    ix2 = fa.fa_load_index(path)
+    with pytest.raises(fa.FaError) as e:
+        fa.fa_debug_graph_probe(ix2, s["q"], 16, 32, 200, 40)
+    assert e.value.status == fa.FA_ERR_ARG
+    fa.fa_build_probe_graph(ix2, 24, 40)
+    a = fa.fa_debug_graph_probe(ix2, s["q"], 16, 32, 200, 40)
+    b = fa.fa_debug_graph_probe(s["ix"], s["q"], 16, 32, 200, 40)
+    assert all(np.array_equal(x, y) for x, y in zip(a, b))
