@@ -264,7 +264,10 @@ __device__ __forceinline__ void rerank_one(
             if (raw_internal && uid >= 0 && f2o(dist) <= (uint32_t)(kth >> 32)) cid = perm[uid];
             uint64_t key[1] = {uid >= 0 ? make_key(dist, (uint32_t)cid) : KEY_INF};
             if (raw_internal && uid >= 0 && f2o(dist) > (uint32_t)(kth >> 32)) key[0] = KEY_INF;
-            if (__ballot_sync(FULL, key[0] < kth)) {
+            const uint32_t in = __ballot_sync(FULL, key[0] < kth);
+            if (R == 1 && in && __popc(in) <= 8) {  // few new keys: insert them one at a time
+                insert_sorted32(Q[0], key[0], in);
+            } else if (in) {
                 bitonic_sort<1>(key);
                 merge_sorted32<R>(Q, key[0]);
             }

@@ -1149,9 +1149,12 @@ __device__ __forceinline__ void rerank_fused(const ScanArgs &a, const ScanPtrs &
         const uint64_t kthq = shfl64(Q[0], kk - 1);
         const bool maybe = v >= 0 && f2o(dist) <= (uint32_t)(kthq >> 32);
         uint64_t nk[1] = {maybe ? make_key(dist, (uint32_t)a.perm[v]) : KEY_INF};
-        if (__ballot_sync(FULL, nk[0] < kthq)) {
+        const uint32_t in = __ballot_sync(FULL, nk[0] < kthq);
+        if (__popc(in) > 8) {  // many new keys (the first groups): sort and merge
             bitonic_sort<1>(nk);
             merge_sorted32<1>(Q, nk[0]);
+        } else if (in) {
+            insert_sorted32(Q[0], nk[0], in);
         }
     }
     wq[warp * 32 + lane] = Q[0];

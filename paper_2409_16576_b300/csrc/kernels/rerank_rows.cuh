@@ -101,13 +101,17 @@ __device__ __forceinline__ float exact_rows(const T *__restrict__ raw, int32_t d
 // (__vabsdiffu4), and a four-byte dot product of it with itself (dp4a) adds
 // four squared differences per instruction. Every partial sum is an integer
 // below 2^24 for d <= 258, so the float returned equals the FP32 sum of
-// squared differences exactly.
+// squared differences exactly, whatever the order of the additions. Row ids
+// travel between lanes as 32 bits (ids below 2^32 - 1); the eight partial
+// sums of the 32 rows are added by a three-stage transposing reduction (each
+// stage halves the sums a lane holds), 7 shuffles instead of 32.
 template <typename C, bool CG = false>
 __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ raw, int32_t d,
                                                   const uint32_t *qp, int64_t my_id) {
     constexpr int WPC = (int)(sizeof(C) / 4);  // 32-bit words per piece
     const int lane = threadIdx.x & 31, r = lane >> 3, c = lane & 7;
     const int pieces = d / (4 * WPC);
+    const uint32_t id32 = my_id < 0 ? 0xffffffffu : (uint32_t)my_id;
     unsigned dd[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) dd[s] = 0u;
@@ -116,9 +120,9 @@ __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ ra
         C x[8];
 #pragma unroll
         for (int s = 0; s < 8; ++s) {
-            const long long id = __shfl_sync(FULL, (long long)my_id, 4 * s + r);
-            if (id >= 0 && pc < pieces)
-                x[s] = row_piece<C, CG>(reinterpret_cast<const C *>(raw + id * (int64_t)d) + pc);
+            const uint32_t id = __shfl_sync(FULL, id32, 4 * s + r);
+            if (id != 0xffffffffu && pc < pieces)
+                x[s] = row_piece<C, CG>(reinterpret_cast<const C *>(raw + (size_t)id * (uint32_t)d) + pc);
             else
                 x[s] = C{};
         }
@@ -134,17 +138,21 @@ __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ ra
             }
         }
     }
-    float out = 0.f;
+    // dd[s] on lane (r, c) is a partial sum of row 4s + r. Stage h (lane bit
+    // b = 4, 2, 1 of c) keeps the half of the sums whose s has bit b equal to
+    // the lane's and sends the other half to lane ^ b; after the three stages
+    // lane (r, c) holds the whole sum of row 4c + r.
+    unsigned e4[4], e2[2];
+    const bool b4 = (c & 4) != 0, b2 = (c & 2) != 0, b1 = (c & 1) != 0;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
-        int v = (int)dd[s];
-        v += __shfl_xor_sync(FULL, v, 1);
-        v += __shfl_xor_sync(FULL, v, 2);
-        v += __shfl_xor_sync(FULL, v, 4);
-        const int mine = __shfl_sync(FULL, v, 8 * (lane & 3));
-        if ((lane >> 2) == s) out = (float)mine;
-    }
-    return out;
+    for (int j = 0; j < 4; ++j)
+        e4[j] = (b4 ? dd[j + 4] : dd[j]) + __shfl_xor_sync(FULL, b4 ? dd[j] : dd[j + 4], 4);
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        e2[j] = (b2 ? e4[j + 2] : e4[j]) + __shfl_xor_sync(FULL, b2 ? e4[j] : e4[j + 2], 2);
+    const unsigned tot = (b1 ? e2[1] : e2[0]) + __shfl_xor_sync(FULL, b1 ? e2[0] : e2[1], 1);
+    // row `lane` = 4 (lane >> 2) + (lane & 3) sits on lane 8 (lane & 3) + (lane >> 2)
+    return (float)(int)__shfl_sync(FULL, tot, 8 * (lane & 3) + (lane >> 2));
 }
 
 // Row pieces: 16 bytes when every row is a multiple of 16 bytes long, else

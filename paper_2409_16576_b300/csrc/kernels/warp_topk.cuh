@@ -115,6 +115,26 @@ __device__ __forceinline__ void merge_sorted32(uint64_t (&L)[R], uint64_t b) {
     bitonic_merge<R>(L);
 }
 
+// The 32 smallest of a sorted warp-wide list of 32 keys (one per lane) and
+// the keys b of the lanes in mask (each below the list's last key and
+// distinct from its keys), inserted one at a time: the result equals
+// sorting b and merging it with merge_sorted32, at about a tenth of the
+// instructions when few lanes are set.
+__device__ __forceinline__ void insert_sorted32(uint64_t &L, uint64_t b, uint32_t mask) {
+    const int lane = threadIdx.x & 31;
+    while (mask) {
+        const int src = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const uint64_t x = shfl64(b, src);
+        const int pos = __popc(__ballot_sync(FULL, L < x));
+        uint32_t lo = (uint32_t)L, hi = (uint32_t)(L >> 32);
+        lo = __shfl_up_sync(FULL, lo, 1);
+        hi = __shfl_up_sync(FULL, hi, 1);
+        const uint64_t up = ((uint64_t)hi << 32) | lo;
+        L = lane < pos ? L : (lane == pos ? x : up);
+    }
+}
+
 // Element e of a warp-wide array (same value on every lane).
 // (a mask blend rather than a select on e / 32, which the compiler may turn
 // into an indexed array in local memory)
