@@ -324,7 +324,16 @@ __device__ __forceinline__ void locate(const ScanArgs &a, const ScanPtrs &S, int
                                        SegCursor &c, uint32_t &v, bool &valid) {
     const int lane = threadIdx.x & 31;
     if (c.sg < 0 || g >= c.p1) {
-        int sg = c.sg < 0 ? 0 : c.sg;
+        int sg = c.sg;
+        if (sg < 0) {  // first chunk: the last segment that starts at or before g
+            int lo = 0, hi = 2 * np - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (S.pref[mid] <= g) lo = mid;
+                else hi = mid - 1;
+            }
+            sg = lo;
+        }
         while (g >= S.pref[sg + 1]) ++sg;
         c.sg = sg;
         c.p0 = S.pref[sg];
@@ -1218,36 +1227,43 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
         }
         uint32_t kept = 0;
         SegCursor sg;
+        // warp w scans the consecutive chunks [g0, gend) of the query, so that
+        // its segment cursor moves on only at the end of a list
+        const uint32_t per = (total + SEL_WARPS - 1) / SEL_WARPS;
+        const uint32_t g0 = min(total, (uint32_t)warp * per), gend = min(total, g0 + per);
         uint32_t v = 0, w[NW];
         bool ok = false;
-        if ((uint32_t)warp < total) locate(a, S, np, warp, sg, v, ok);
-        load_codes<M>(a.codes, v, ok && (uint32_t)warp < total, w);
+        if (g0 < gend) locate(a, S, np, g0, sg, v, ok);
+        load_codes<M>(a.codes, v, ok && g0 < gend, w);
+        // tau = (its distance, the largest id): a key is below it iff its
+        // distance is at or below tau's (internal ids stay below 2^32 - 1)
+        const uint32_t tau_hi = (uint32_t)(tau >> 32);
         auto score = [&](const uint32_t (&wc)[NW], uint32_t vc, bool okc) {
             const float dist = adc_words<M, W>(wc, vc, S.lut);
             kept += okc ? 1u : 0u;
-            const uint64_t key = make_key(dist, vc);
-            const bool pass_ = okc && key < tau;
+            const uint32_t dk = f2o(dist);
+            const bool pass_ = okc && dk <= tau_hi;
             const uint32_t m = __ballot_sync(FULL, pass_);
             if (m) {
                 uint32_t p0 = 0;
                 if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
                 p0 = __shfl_sync(FULL, p0, 0);
                 const uint32_t at = p0 + __popc(m & ((1u << lane) - 1u));
-                if (pass_ && at < a.sel_cap) buf[at] = key;
+                if (pass_ && at < a.sel_cap) buf[at] = ((uint64_t)dk << 32) | vc;
             }
         };
-        for (uint32_t g = warp; g < total; g += 2 * SEL_WARPS) {
-            const uint32_t g1 = g + SEL_WARPS, g2 = g1 + SEL_WARPS;
+        for (uint32_t g = g0; g < gend; g += 2) {
+            const uint32_t g1 = g + 1, g2 = g + 2;
             uint32_t v1 = 0, w1[NW];
             bool ok1 = false;
-            if (g1 < total) locate(a, S, np, g1, sg, v1, ok1);
-            load_codes<M>(a.codes, v1, ok1 && g1 < total, w1);
+            if (g1 < gend) locate(a, S, np, g1, sg, v1, ok1);
+            load_codes<M>(a.codes, v1, ok1 && g1 < gend, w1);
             score(w, v, ok);
-            if (g1 >= total) break;
+            if (g1 >= gend) break;
             ok = false;
             v = 0;
-            if (g2 < total) locate(a, S, np, g2, sg, v, ok);
-            load_codes<M>(a.codes, v, ok && g2 < total, w);
+            if (g2 < gend) locate(a, S, np, g2, sg, v, ok);
+            load_codes<M>(a.codes, v, ok && g2 < gend, w);
             score(w1, v1, ok1);
         }
         if (a.stats) {
