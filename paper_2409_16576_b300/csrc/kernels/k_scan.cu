@@ -256,43 +256,29 @@ __device__ __forceinline__ void load_codes(const uint8_t *codes, uint32_t v, boo
     }
 }
 
-// acc += (x0, x1) as two FP32 additions in one packed instruction; each lane
-// of the pair is rounded to nearest, as two separate adds would be.
-__device__ __forceinline__ void add_f32x2(unsigned long long &acc, float x0, float x1) {
-    unsigned long long x;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(x0), "f"(x1));
-    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(x));
-}
-
-// ADC distance (Eq. 1) of one rotated code row (rotation r = v mod 32): even
-// steps sum into acc0, odd steps into acc1 (M is even).
+// ADC distance (Eq. 1) of one rotated code row (rotation r = v mod 32): step
+// t sums into accumulator t mod 4 (M is even), and the four are added as
+// (a0 + a1) + (a2 + a3). Scalar FP32 adds: the packed two-lane add measured
+// more instructions per lookup (its operand pairs) and a slower scan.
 template <int M, int W>
 __device__ __forceinline__ float adc_words(const uint32_t (&w)[M / 4], uint32_t v, const float *lut) {
     static_assert(M % 2 == 0, "M must be even");
     const uint32_t r4 = (v & 31u) * 4u;
     const char *lb = reinterpret_cast<const char *>(lut);
-    unsigned long long acc = 0ull;  // (acc0, acc1) = (+0, +0)
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int s = 0; s < M; s += 2) {
-        float x[2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int t = s + h;
-            uint32_t off;
-            if (W == 64) {
-                // (code << 8) | r4 in one byte permute: byte0 <- r4, byte1 <- code
-                off = __byte_perm(w[t >> 2], r4, 0x5504u | ((uint32_t)(t & 3) << 4));
-            } else {
-                const uint32_t c = __byte_perm(w[t >> 2], 0u, 0x4440u | (uint32_t)(t & 3));
-                off = c * (uint32_t)(W * 4) + r4;
-            }
-            x[h] = *reinterpret_cast<const float *>(lb + off + 4 * t);
+    for (int t = 0; t < M; ++t) {
+        uint32_t off;
+        if (W == 64) {
+            // (code << 8) | r4 in one byte permute: byte0 <- r4, byte1 <- code
+            off = __byte_perm(w[t >> 2], r4, 0x5504u | ((uint32_t)(t & 3) << 4));
+        } else {
+            const uint32_t c = __byte_perm(w[t >> 2], 0u, 0x4440u | (uint32_t)(t & 3));
+            off = c * (uint32_t)(W * 4) + r4;
         }
-        add_f32x2(acc, x[0], x[1]);
+        acc[t & 3] += *reinterpret_cast<const float *>(lb + off + 4 * t);
     }
-    float acc0, acc1;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(acc0), "=f"(acc1) : "l"(acc));
-    return acc0 + acc1;
+    return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 // Segment walk state of one warp: the bounds of its current segment, kept in
@@ -1238,6 +1224,20 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
         // tau = (its distance, the largest id): a key is below it iff its
         // distance is at or below tau's (internal ids stay below 2^32 - 1)
         const uint32_t tau_hi = (uint32_t)(tau >> 32);
+        // keys below tau gather in the warp's 64-key stage in shared memory
+        // (the sample's room, free until the next query) and go to the CTA
+        // buffer 32 at a time: one slot reservation and one coalesced store
+        // per 32 keys instead of per chunk
+        uint64_t *stage = samp + warp * 64;
+        uint32_t scnt = 0;  // keys in the stage (warp-uniform, < 32 between chunks)
+        const uint32_t lt = (1u << lane) - 1u;
+        auto flush = [&](uint32_t n) {
+            __syncwarp();
+            uint32_t p0 = 0;
+            if (lane == 0) p0 = atomicAdd(&s_cnt, n);
+            p0 = __shfl_sync(FULL, p0, 0);
+            if ((uint32_t)lane < n && p0 + lane < a.sel_cap) buf[p0 + lane] = stage[lane];
+        };
         auto score = [&](const uint32_t (&wc)[NW], uint32_t vc, bool okc) {
             const float dist = adc_words<M, W>(wc, vc, S.lut);
             kept += okc ? 1u : 0u;
@@ -1245,11 +1245,15 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
             const bool pass_ = okc && dk <= tau_hi;
             const uint32_t m = __ballot_sync(FULL, pass_);
             if (m) {
-                uint32_t p0 = 0;
-                if (lane == 0) p0 = atomicAdd(&s_cnt, (uint32_t)__popc(m));
-                p0 = __shfl_sync(FULL, p0, 0);
-                const uint32_t at = p0 + __popc(m & ((1u << lane) - 1u));
-                if (pass_ && at < a.sel_cap) buf[at] = ((uint64_t)dk << 32) | vc;
+                if (pass_) stage[scnt + __popc(m & lt)] = ((uint64_t)dk << 32) | vc;
+                scnt += (uint32_t)__popc(m);
+                if (scnt >= 32) {
+                    flush(32);
+                    const uint64_t rest = stage[lane + 32];  // the scnt - 32 keys after them
+                    __syncwarp();
+                    scnt -= 32;
+                    if ((uint32_t)lane < scnt) stage[lane] = rest;
+                }
             }
         };
         for (uint32_t g = g0; g < gend; g += 2) {
@@ -1266,6 +1270,7 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
             load_codes<M>(a.codes, v, ok && g2 < gend, w);
             score(w1, v1, ok1);
         }
+        if (scnt) flush(scnt);
         if (a.stats) {
             for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
             if (lane == 0) atomicAdd(&s_kept, kept);
@@ -1999,6 +2004,7 @@ static bool launch_scan_m(const ScanArgs &a, const ScanLaunch &l, cudaStream_t s
         // (a 64-chunk sample: 2048 keys; a 128-chunk one measured 1.3 % slower
         // overall, its sampling costing more than its tighter estimate saves)
         constexpr int sch_max = 64;
+        static_assert(sch_max * 32 >= SEL_WARPS * 64, "the sample's room holds the warps' key stages");
         const ScanSmem sel_plan(W, a.d, a.nlist, a.has_rep, a.nprobe, sch_max * 32 * 8 + 8192);
         const bool sel = !a.sorted_out && a.selbuf && a.redo && sel_plan.total <= 113 * 1024;
         ScanArgs b = a;  // variant 2's arguments
