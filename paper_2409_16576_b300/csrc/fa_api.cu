@@ -872,11 +872,22 @@ static void search_impl(fa_index *ix, const float *queries, int64_t nq, int32_t 
             npq = w->npq;
             tr.launches += gentry < D.graph.S ? 3 : 1;
         } else {
+            // the table on the second stream here too: it needs only the
+            // queries, and overlaps the probe's selection
+            if (global_lut) {
+                FA_CHECK_CUDA(cudaEventRecord(w->fork[0], st));
+                FA_CHECK_CUDA(cudaStreamWaitEvent(w->stream2, w->fork[0], 0));
+                launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err,
+                                  w->stream2, batched ? 1 : 0);
+                FA_CHECK_CUDA(cudaEventRecord(w->join, w->stream2));
+                tr.launches += 1;
+            }
             launch_coarse(D, qd, nq, nprobe, nprobe, sp.probe_gemm, *w, w->probes, st);
             tr.launches += coarse_launches(D, nq, sp.probe_gemm, *w);
         }
         tr.mark(1);
-        if (global_lut && gprobe) {
+        const bool lut_forked = global_lut && !sp.probes;
+        if (lut_forked) {
             FA_CHECK_CUDA(cudaStreamWaitEvent(st, w->join, 0));
         } else if (global_lut) {
             launch_lut_global(D, qd, nq, sp.lut_prec, sp.lut_gemm, w->lut, w->lut_scale, w->err, st,
