@@ -1138,7 +1138,8 @@ __device__ __forceinline__ void rerank_fused(const ScanArgs &a, const ScanPtrs &
         const uint64_t key = i < c ? buf[i] : KEY_INF;
         const int64_t v = (i < c && key <= kth) ? (int64_t)(uint32_t)(key & 0xffffffffu) : (int64_t)-1;
         prefetch_row(i + SEL_THREADS);
-        const float dist = qint ? exact_rows_u8int<uint4>(raw, a.d, qp, v)
+        const float dist = qint ? (a.d % 32 == 0 ? exact_rows_u8int32(raw, a.d, qp, v)
+                                                 : exact_rows_u8int<uint4>(raw, a.d, qp, v))
                                 : (a.ip ? exact_rows<uint8_t, uint4, true>(raw, a.d, S.qv, v)
                                         : exact_rows<uint8_t, uint4>(raw, a.d, S.qv, v));
         const uint64_t kthq = shfl64(Q[0], kk - 1);

@@ -155,6 +155,58 @@ __device__ __forceinline__ float exact_rows_u8int(const uint8_t *__restrict__ ra
     return (float)(int)__shfl_sync(FULL, tot, 8 * (lane & 3) + (lane >> 2));
 }
 
+// The same for rows a multiple of 32 bytes long, read in 32-byte pieces
+// (one 256-bit load each): four lanes share a row, one load instruction
+// covers eight rows, and the partial sums take a two-stage transposing
+// reduction. Half the loads, id shuffles and address computations of the
+// 16-byte form per row, and the same exact integer result. Plain (coherent)
+// loads: the rows may sit in mapped host memory.
+__device__ __forceinline__ float exact_rows_u8int32(const uint8_t *__restrict__ raw, int32_t d,
+                                                    const uint32_t *qp, int64_t my_id) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const int pieces = d / 32;
+    const uint32_t id32 = my_id < 0 ? 0xffffffffu : (uint32_t)my_id;
+    unsigned dd[4] = {0u, 0u, 0u, 0u};
+    for (int p0 = 0; p0 < pieces; p0 += 4) {
+        const int pc = p0 + c;
+        uint32_t x[4][8];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const uint32_t id = __shfl_sync(FULL, id32, 8 * s + g);
+            if (id != 0xffffffffu && pc < pieces) {
+                const uint8_t *p = raw + (size_t)id * (uint32_t)d + 32 * pc;
+                asm("ld.global.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                    : "=r"(x[s][0]), "=r"(x[s][1]), "=r"(x[s][2]), "=r"(x[s][3]), "=r"(x[s][4]),
+                      "=r"(x[s][5]), "=r"(x[s][6]), "=r"(x[s][7])
+                    : "l"(p));
+            } else {
+#pragma unroll
+                for (int wd = 0; wd < 8; ++wd) x[s][wd] = 0u;
+            }
+        }
+        if (pc >= pieces) continue;
+#pragma unroll
+        for (int wd = 0; wd < 8; ++wd) {
+            const uint32_t qw = qp[pc * 8 + wd];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                const unsigned ad = __vabsdiffu4(x[s][wd], qw);
+                dd[s] = __dp4a(ad, ad, dd[s]);
+            }
+        }
+    }
+    // dd[s] on lane (g, c) is a partial sum of row 8s + g; after the stages
+    // on lane bits 2 and 1 lane (g, c) holds the whole sum of row 8c + g
+    const bool b2 = (c & 2) != 0, b1 = (c & 1) != 0;
+    unsigned e2[2];
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        e2[j] = (b2 ? dd[j + 2] : dd[j]) + __shfl_xor_sync(FULL, b2 ? dd[j] : dd[j + 2], 2);
+    const unsigned tot = (b1 ? e2[1] : e2[0]) + __shfl_xor_sync(FULL, b1 ? e2[0] : e2[1], 1);
+    // row `lane` = 8 (lane >> 3) + (lane & 7) sits on lane 4 (lane & 7) + (lane >> 3)
+    return (float)(int)__shfl_sync(FULL, tot, 4 * (lane & 7) + (lane >> 3));
+}
+
 // Row pieces: 16 bytes when every row is a multiple of 16 bytes long, else
 // 4-byte words.
 template <typename T, bool CG = false>
@@ -162,7 +214,10 @@ __device__ __forceinline__ float exact_rows_any(const T *__restrict__ raw, int32
                                                 const float *qs, const uint32_t *qp,
                                                 bool qint, int64_t my_id, bool ip = false) {
     if constexpr (std::is_same<T, uint8_t>::value) {
-        if (qint && !ip) return exact_rows_u8int<uint4, CG>(raw, d, qp, my_id);  // qint needs d % 16 == 0
+        if (qint && !ip) {  // qint needs d % 16 == 0
+            if (!CG && d % 32 == 0) return exact_rows_u8int32(raw, d, qp, my_id);
+            return exact_rows_u8int<uint4, CG>(raw, d, qp, my_id);
+        }
     }
     if ((d * (int)sizeof(T)) % 16 == 0)
         return ip ? exact_rows<T, uint4, true, CG>(raw, d, qs, my_id) : exact_rows<T, uint4, false, CG>(raw, d, qs, my_id);
