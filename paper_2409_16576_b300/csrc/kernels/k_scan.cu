@@ -1214,10 +1214,14 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
         }
         uint32_t kept = 0;
         SegCursor sg;
-        // warp w scans the consecutive chunks [g0, gend) of the query, so that
-        // its segment cursor moves on only at the end of a list
-        const uint32_t per = (total + SEL_WARPS - 1) / SEL_WARPS;
-        const uint32_t g0 = min(total, (uint32_t)warp * per), gend = min(total, g0 + per);
+        // warp w scans a consecutive run of the primary chunks, then one of
+        // the replica chunks (an equal share of each: replica entries cost
+        // more, their dedup lookups), so that its segment cursor moves on
+        // only at the end of a list
+        const uint32_t nprim = S.pref[np], nrep = total - nprim;
+        const uint32_t perp = (nprim + SEL_WARPS - 1) / SEL_WARPS, perr = (nrep + SEL_WARPS - 1) / SEL_WARPS;
+        const uint32_t g0 = min(nprim, (uint32_t)warp * perp), gend = min(nprim, g0 + perp);
+        const uint32_t r0 = nprim + min(nrep, (uint32_t)warp * perr), rend = min(total, r0 + perr);
         uint32_t v = 0, w[NW];
         bool ok = false;
         if (g0 < gend) locate(a, S, np, g0, sg, v, ok);
@@ -1270,6 +1274,12 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
             if (g2 < gend) locate(a, S, np, g2, sg, v, ok);
             load_codes<M>(a.codes, v, ok && g2 < gend, w);
             score(w1, v1, ok1);
+        }
+        for (uint32_t g = r0; g < rend; ++g) {  // the replica share, one chunk at a time
+            ok = false;
+            locate(a, S, np, g, sg, v, ok);
+            load_codes<M>(a.codes, v, ok, w);
+            score(w, v, ok);
         }
         if (scnt) flush(scnt);
         if (a.stats) {
