@@ -1245,7 +1245,6 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
         };
         auto score = [&](const uint32_t (&wc)[NW], uint32_t vc, bool okc) {
             const float dist = adc_words<M, W>(wc, vc, S.lut);
-            kept += okc ? 1u : 0u;
             const uint32_t dk = f2o(dist);
             const bool pass_ = okc && dk <= tau_hi;
             const uint32_t m = __ballot_sync(FULL, pass_);
@@ -1275,15 +1274,19 @@ __global__ void __launch_bounds__(SEL_THREADS, 2) k_scan_sel(const ScanArgs a, i
             load_codes<M>(a.codes, v, ok && g2 < gend, w);
             score(w1, v1, ok1);
         }
+        // every primary entry is kept; replica entries are counted as scanned
         for (uint32_t g = r0; g < rend; ++g) {  // the replica share, one chunk at a time
             ok = false;
             locate(a, S, np, g, sg, v, ok);
             load_codes<M>(a.codes, v, ok, w);
+            kept += ok ? 1u : 0u;
             score(w, v, ok);
         }
         if (scnt) flush(scnt);
         if (a.stats) {
             for (int o = 16; o > 0; o >>= 1) kept += __shfl_xor_sync(FULL, kept, o);
+            if (threadIdx.x == 0)
+                for (int sgi = 0; sgi < np; ++sgi) kept += S.seg_end[sgi] - S.seg_beg[sgi];
             if (lane == 0) atomicAdd(&s_kept, kept);
         }
         __syncthreads();
